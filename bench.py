@@ -1,0 +1,333 @@
+"""Benchmark of the operator hot path on the kerr256 workload.
+
+One step = one pass of the A / A^T pair behind the reconstruction-loss
+gradient for a batch of 8 histories: y = A x (forward) followed by
+g = A^T y (adjoint), on the Kerr a = 0.5, i = 50 deg geometry with a
+256 x 256 image (2 x 2 sub-rays in the photon-ring annulus), a 64 x 128
+source grid, 64 hats and 256 frames.  Ray tables come from the library's
+own GPU tracer (rtt_trace_rays), the operator from rtt_build_operator.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).  Under torchrun each rank runs an
+independent replica (weak scaling; the operator has no exchange step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "A+A^T applies/s"
+UNIT = "history-applies/s"
+BATCH = 8
+L2_FLUSH_BYTES = 256 << 20
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def build_workload(device):
+    import torch
+
+    from paper_2609_05528_b300 import build, rtt
+    from paper_2609_05528_b300 import inputs as I
+    build.build()
+    w = I.kerr256()
+    s = I.screen_samples(w)
+    torch.cuda.synchronize(device)
+    tab = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, s)
+    op = rtt.Operator(w, tab)
+    x = torch.from_numpy(I.history_batch(w, range(100, 100 + BATCH)).astype(np.float32)).to(device)
+    return w, tab, op, x
+
+
+def algorithmic_bytes(op, B, elem=4):
+    """Bytes the method must move per launch: y once, x once, plus tables."""
+    E = int(op.info.n_rays)
+    R = int(op.info.n_rows)
+    S = int(op.info.n_nodes)
+    y = R * op.n_frames * B * elem
+    x = S * op.n_hats * B * elem
+    table_fwd = E * 32 + (R + 1) * 4
+    table_adj = E * 36 + 4 * E * 4 + (S + 1) * 4
+    return {"A": y + x + table_fwd, "AT": y + x + table_adj, "y": y, "x": x}
+
+
+def run_ours(args, rank, world, device):
+    import torch
+
+    torch.cuda.set_device(device)
+    w, tab, op, x = build_workload(device)
+    stream = torch.cuda.current_stream(device)
+    R = op.arm_rows(7)
+    y = torch.empty((R, op.n_frames, BATCH), dtype=torch.float32, device=device)
+    g = torch.empty_like(x)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def step():
+        op.apply_A(x, y)
+        op.apply_AT(y, g)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(device.index if device.index is not None else 0) as clk:
+        torch.cuda.synchronize(device)
+        for i in range(args.steps):
+            flush.zero_()  # L2 flush between timed iterations (outside the events)
+            e0, e1, e2 = ev[i]
+            e0.record(stream)
+            op.apply_A(x, y)
+            e1.record(stream)
+            op.apply_AT(y, g)
+            e2.record(stream)
+        torch.cuda.synchronize(device)
+    t_A = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
+    t_AT = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
+    ms_step = float(np.mean([a + b for a, b in zip(t_A, t_AT)]))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    clocks = clk.summary()
+
+    # end-to-end through the C ABI with host buffers: x from pinned host
+    # memory to the device, A, A^T, gradient back to pinned host memory
+    xh = x.cpu().pin_memory()
+    gh = torch.empty(g.shape, dtype=g.dtype).pin_memory()
+    xd = torch.empty_like(x)
+    for _ in range(3):
+        xd.copy_(xh, non_blocking=True)
+        op.apply_A(xd, y)
+        op.apply_AT(y, g)
+        gh.copy_(g, non_blocking=True)
+    torch.cuda.synchronize(device)
+    e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        xd.copy_(xh, non_blocking=True)
+        op.apply_A(xd, y)
+        op.apply_AT(y, g)
+        gh.copy_(g, non_blocking=True)
+        a1.record(stream)
+        a1.synchronize()
+        e_ms.append(a0.elapsed_time(a1))
+    e2e_ms = float(np.mean(e_ms))
+
+    # plain FP64 GPU path (same kernels in double) for comparison
+    x64 = x.double()
+    y64 = torch.empty((R, op.n_frames, BATCH), dtype=torch.float64, device=device)
+    g64 = torch.empty_like(x64)
+    op.apply_A(x64, y64)
+    op.apply_AT(y64, g64)
+    torch.cuda.synchronize(device)
+    f_ms = []
+    for _ in range(max(3, args.steps // 4)):
+        flush.zero_()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        op.apply_A(x64, y64)
+        op.apply_AT(y64, g64)
+        a1.record(stream)
+        a1.synchronize()
+        f_ms.append(a0.elapsed_time(a1))
+    fp64_ms = float(np.mean(f_ms))
+
+    ab = algorithmic_bytes(op, BATCH)
+    mA, mAT = float(np.mean(t_A)), float(np.mean(t_AT))
+    dom, dom_ms = ("A", mA) if mA >= mAT else ("AT", mAT)
+    peak, peak_kind = measured_peaks()
+    achieved = ab[dom] / (dom_ms * 1e-3) / 1e9
+    value = world * BATCH / (ms_step * 1e-3)
+    gbs = (ab["A"] + ab["AT"]) / (ms_step * 1e-3) / 1e9
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "kerr256: Kerr a=0.5 i=50deg 256x256 (2x2 ring sub-rays), "
+                               "64x128 source, 64 hats, 256 frames, resolved n=0..2",
+                   "batch": BATCH, "rows": R, "rays": int(op.info.n_rays),
+                   "nodes": op.n_nodes, "hats": op.n_hats, "frames": op.n_frames,
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "hbm_gbs": gbs,
+        "kernels_ms": {"A": mA, "AT": mAT},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None},
+        "e2e": {"value": world * BATCH / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+                "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4)},
+        "fp64_path": {"value": world * BATCH / (fp64_ms * 1e-3), "ms_per_step": fp64_ms},
+        "clocks": clocks,
+        "gpu_launches": 2 * args.steps,
+    }
+    return out
+
+
+def oracle_pairs_per_s(w, budget_s: float = 12.0, B: int = 1):
+    """Time the FP64 CPU oracle (as it stands) on A + A^T for one history."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    from paper_2609_05528_b300 import inputs as I
+    tab = O.build_table(w, I.screen_samples(w))
+    scl = O.scale(tab)
+    x = I.history_batch(w, [100])
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        y = O.apply_A(w, tab, x, scl)
+        O.apply_AT(w, tab, y, scl)
+        n += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return n * B / dt, cores, n
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2609_05528_b300 import inputs as I
+
+    if args.impl == "reference":
+        # the reference arm is the FP64 CPU oracle, timed on the host cores
+        if rank != 0:
+            return
+        w = I.kerr256()
+        per_step_budget = 10.0
+        vals = []
+        for _ in range(max(1, args.steps)):
+            v, cores, n = oracle_pairs_per_s(w, budget_s=per_step_budget)
+            vals.append(v)
+            if len(vals) >= 2:
+                break
+        v = float(np.mean(vals))
+        sample = f"{n} x (A + A^T) on 1 history of kerr256 per timed pass, FP64 oracle"
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+                          "n_gpus": 1, "steps": len(vals), "warmup": 0,
+                          "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": {"workload": "kerr256 (see ours)", "batch": 1},
+                          "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores,
+                                           "kind": "oracle", "sample": sample},
+                          "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    device = torch.device("cuda", local)
+    out = run_ours(args, rank, world, device)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            v, cores, n = oracle_pairs_per_s(I.kerr256())
+            out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                   "sample": f"{n} x (A + A^T) on 1 history of kerr256, "
+                                             "FP64 oracle, ~12 s"}
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * rtt.h -- C ABI of librtt.so, the B300 (sm_103a) implementation of the
+ * multi-order retarded-time imaging operator A, its adjoint A^T, and the
+ * batched applies behind the operational-rank / reach / innovation audit and
+ * the TSVD / ridge estimators of "Photon-Ring Retarded-Time Tomography"
+ * (arXiv 2609.05528).
+ *
+ * General rules (apply to every entry point):
+ *  - Every function returns an rtt_status; no exception crosses the ABI.
+ *    On failure rtt_last_error() returns a message for the calling thread.
+ *  - Pointers named *_dev are device memory of the current CUDA device,
+ *    pointers named *_host are host memory.  The caller owns every buffer it
+ *    passes; the library owns the operator (tables, index arrays, scratch) and
+ *    frees it in rtt_destroy.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Applies are
+ *    asynchronous on that stream; functions that return host results
+ *    synchronise the stream before returning.
+ *  - Results are deterministic: repeated calls give bitwise-identical output
+ *    (no floating-point atomics; fixed summation order).
+ *  - Layouts.  Source coefficients x[s][k][b]: node s = i_r * n_phi + j_phi
+ *    (radius-major, azimuth contiguous), hat k (k = 0 youngest), batch b
+ *    innermost.  Data y[row][f][b]: rows sorted by (order, pixel) and
+ *    restricted to the orders of arm_mask, frame f, batch b innermost.
+ *  - arm_mask selects image orders: bit n = order n (n = 0, 1, 2).
+ *    Direct-only = 0x1, resolved stack = 0x7 (Eq. 3).
+ */
+#ifndef RTT_H
+#define RTT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RTT_ABI_VERSION 1
+
+typedef enum rtt_status {
+    RTT_OK = 0,
+    RTT_EINVAL = -1,          /* invalid argument, size or table content */
+    RTT_ENOMEM = -2,          /* device or host allocation failed */
+    RTT_ECUDA = -3,           /* a CUDA runtime call failed */
+    RTT_ETIMEOUT = -4,        /* a bounded device wait gave up */
+    RTT_ENOTCONVERGED = -5,   /* an iteration hit its limit */
+    RTT_ESTATE = -6,          /* call not valid in the operator's state */
+    RTT_EDEVICE = -7          /* a device-side consistency check failed */
+} rtt_status;
+
+typedef struct rtt_op_s* rtt_op;
+
+/* Kerr spin a (|a| < 1, M = 1) and observer inclination in degrees
+   (0 < incl < 90).  The observer azimuth is 0. */
+typedef struct {
+    double spin;
+    double incl_deg;
+} rtt_geometry;
+
+/* Equatorial source grid: n_r radii log-spaced on [r_in, r_out] (n_r >= 2),
+   n_phi azimuths phi_j = 2 pi j / n_phi (n_phi >= 2, periodic). */
+typedef struct {
+    int32_t n_r;
+    int32_t n_phi;
+    double r_in;
+    double r_out;
+} rtt_source_grid;
+
+/* Observer frames t_o(f) = t0 + cadence f, f < n_frames.  Hats
+   B_k(t) = max(0, 1 - |t - t_k| / hat_step), t_k = t_end - hat_step k,
+   k < n_hats.  cadence / hat_step must be a dyadic rational p / 2^24 with
+   0 < cadence <= hat_step (exact per-frame hat offsets). */
+typedef struct {
+    int32_t n_frames;
+    double t0;
+    double cadence;
+    int32_t n_hats;
+    double hat_step;
+    double t_end;
+} rtt_time_grid;
+
+/* Raw ray table (FP64 SoA, host memory, read during rtt_build_operator only).
+   One entry per valid (screen sample, order): order in {0,1,2}; pixel >= 0
+   (rows are the distinct (order, pixel) pairs); source radius r in
+   [r_in, r_out] and azimuth phi (any real, taken modulo 2 pi) of the
+   equatorial crossing; delay Delta (M); whitened transfer weight
+   w = g^3 sqrt(dOmega_p) / S_p (Eq. 16 at sigma_Omega = 1); throughput
+   g^3 dOmega_p / S_p (weights of the direct age quantile, Sec. 4.5). */
+typedef struct {
+    int64_t n_rays;
+    const int8_t* order;
+    const int32_t* pixel;
+    const double* r;
+    const double* phi;
+    const double* delay;
+    const double* weight;
+    const double* throughput;
+} rtt_ray_table;
+
+/* Writable table of the same layout (output of rtt_trace_rays). */
+typedef struct {
+    int64_t capacity;
+    int8_t* order;
+    int32_t* pixel;
+    double* r;
+    double* phi;
+    double* delay;
+    double* weight;
+    double* throughput;
+} rtt_ray_buffer;
+
+typedef struct {
+    double snr0;  /* SNR_0 of Eq. 17-18 (> 0); scale = snr0 / s_ref */
+    double rho;   /* detection threshold rho (> 0), Eq. 30-31 */
+} rtt_options;
+
+/* Summary of a built operator. */
+typedef struct {
+    int64_t n_rays;
+    int64_t n_rows;
+    int64_t rows_per_order[3];
+    int64_t n_nodes;
+    int32_t n_hats;
+    int32_t n_frames;
+    double s_ref;          /* Eq. 17 */
+    double scale;          /* snr0 / s_ref: whitening factor applied by A */
+    double delay_min[3];   /* per order, over its rays (NaN if no rays) */
+    double delay_max[3];
+} rtt_op_info;
+
+/* Screen samples for the tracer: pixel centres or sub-rays (alpha, beta) in
+   M, the pixel each belongs to and the number of sub-rays of that pixel. */
+typedef struct {
+    int64_t n;
+    const double* alpha;
+    const double* beta;
+    const int32_t* pixel;
+    const int32_t* n_sub;
+    double d_omega_pixel;  /* pixel solid angle in M^2 */
+} rtt_screen;
+
+const char* rtt_error_string(rtt_status s);
+const char* rtt_last_error(void);
+int rtt_abi_version(void);
+
+/*
+ * rtt_trace_rays -- null geodesics on the GPU (FP64, Mino-time Carter
+ * equations in s = 1/r, u = cos theta; Sec. 3.1 Eq. 2 and Sec. 5), and the
+ * raw ray table they define: for each sample and order n = 0, 1, 2 (the
+ * (n+1)-th equatorial crossing, counted while the ray stays outside
+ * r_+ + 0.01 M), valid if r in [r_in, r_out]; redshift of a prograde
+ * Keplerian emitter outside the ISCO and an emitter plunging from the ISCO
+ * inside it; delays relative to the earliest direct ray.
+ * screen: host arrays.  out: host buffer with capacity >= 3 * screen->n.
+ * *n_out receives the number of entries, sorted by (order, pixel, sample).
+ * Errors: RTT_EINVAL (geometry, sizes, capacity), RTT_ECUDA, RTT_ENOMEM.
+ */
+rtt_status rtt_trace_rays(const rtt_geometry* geom, const rtt_source_grid* grid,
+                          const rtt_screen* screen, rtt_ray_buffer* out, int64_t* n_out,
+                          void* stream);
+
+/*
+ * rtt_build_operator -- packs a raw FP64 ray table into the device operator
+ * (Sec. 3.1 Eq. 2-3; Eq. 16 weights; Eq. 17-18 normalisation): bilinear
+ * corner weights in (log r, phi) premultiplied by w (FP32, derived in FP64),
+ * integer hat base and 24-bit hat fraction per ray (derived in FP64, so that
+ * the set of hats touched equals the exact one), the row CSR over rays
+ * sorted by (order, pixel) and the transposed node -> (ray, corner) CSR,
+ * both sorted on the device.  Computes s_ref with j_ref = 1 evaluated
+ * directly and scale = snr0 / s_ref.
+ * table: host FP64 SoA (not retained).  *out receives the handle.
+ * Errors: RTT_EINVAL (bad grid, non-dyadic cadence/hat_step, order outside
+ * {0,1,2}, negative pixel, r outside [r_in, r_out], non-finite values, no
+ * direct ray), RTT_ENOMEM, RTT_ECUDA.
+ */
+rtt_status rtt_build_operator(const rtt_geometry* geom, const rtt_source_grid* grid,
+                              const rtt_time_grid* time, const rtt_ray_table* table,
+                              const rtt_options* opt, void* stream, rtt_op* out);
+
+rtt_status rtt_op_query(rtt_op op, rtt_op_info* out);
+
+/* Number of data rows selected by arm_mask. */
+rtt_status rtt_arm_rows(rtt_op op, int arm_mask, int64_t* rows_out);
+
+/*
+ * rtt_apply_A -- y = scale * A x for a batch of `batch` histories (Eq. 2-3,
+ * Eq. 16, Eq. 47): y[row][f][b] = scale sum_{e in row} w_e sum_c bil_c(e)
+ * sum_k B_k(t_o(f) - Delta_e) x[node_c(e)][k][b].  Only the two hats whose
+ * support contains each sample are touched.
+ * x_dev: float [n_nodes][n_hats][batch]; y_dev: float
+ * [arm_rows][n_frames][batch] (fully overwritten).  FP32 storage and FP32
+ * accumulation.  Errors: RTT_EINVAL (null pointers, batch < 1, arm_mask not
+ * in 1..7), RTT_ECUDA.
+ */
+rtt_status rtt_apply_A(rtt_op op, const float* x_dev, float* y_dev, int batch, int arm_mask,
+                       void* stream);
+
+/*
+ * rtt_apply_AT -- x = scale * A^T y, the exact transpose of rtt_apply_A
+ * (Sec. 5: explicit adjoint action), evaluated as a deterministic gather
+ * over the transposed node -> (ray, corner) index with no atomics.
+ * y_dev: float [arm_rows][n_frames][batch]; x_dev: float
+ * [n_nodes][n_hats][batch] (fully overwritten).  Errors as rtt_apply_A.
+ */
+rtt_status rtt_apply_AT(rtt_op op, const float* y_dev, float* x_dev, int batch, int arm_mask,
+                        void* stream);
+
+/* FP64 storage and FP64 arithmetic versions of the two applies (the plain
+   FP64 GPU path the fast path is compared with).  Same layouts in double. */
+rtt_status rtt_apply_A_f64(rtt_op op, const double* x_dev, double* y_dev, int batch,
+                           int arm_mask, void* stream);
+rtt_status rtt_apply_AT_f64(rtt_op op, const double* y_dev, double* x_dev, int batch,
+                            int arm_mask, void* stream);
+
+void rtt_destroy(rtt_op op);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTT_H */

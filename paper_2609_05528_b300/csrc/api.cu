@@ -1,0 +1,618 @@
+// C ABI entry points: operator construction (table preparation on the
+// device), queries, and the forward / adjoint applies.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <cmath>
+#include <cub/cub.cuh>
+#include <string>
+#include <vector>
+
+#include "rtt_internal.cuh"
+
+namespace rtt {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+template <typename T>
+cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
+template <typename T>
+cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
+
+#define RTT_CUDA(call)                                                                  \
+    do {                                                                                \
+        cudaError_t _e = (call);                                                        \
+        if (_e != cudaSuccess) {                                                        \
+            set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(_e), __FILE__, \
+                      __LINE__);                                                        \
+            return _e == cudaErrorMemoryAllocation ? RTT_ENOMEM : RTT_ECUDA;            \
+        }                                                                               \
+    } while (0)
+
+// --------------------------------------------------------------------------
+// Table preparation kernels (K8)
+// --------------------------------------------------------------------------
+__global__ void make_row_keys(int64_t n, const int8_t* order, const int32_t* pixel,
+                              unsigned long long* key, int32_t* idx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    key[i] = ((unsigned long long)(uint8_t)order[i] << 32) | (unsigned long long)(uint32_t)pixel[i];
+    idx[i] = (int32_t)i;
+}
+
+__global__ void row_flags(int64_t n, const unsigned long long* key, int32_t* flag) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flag[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+
+// rows[i] = inclusive scan - 1; row_ptr[row] = first ray; row order histogram
+__global__ void row_index(int64_t n, const unsigned long long* key, const int32_t* flag,
+                          const int32_t* incl, int32_t* ray_row, int32_t* row_ptr,
+                          int32_t* row_order, unsigned int* order_count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t row = incl[i] - 1;
+    ray_row[i] = row;
+    if (flag[i]) {
+        row_ptr[row] = (int32_t)i;
+        const int ord = (int)(key[i] >> 32);
+        row_order[row] = ord;
+        atomicAdd(&order_count[ord], 1u);  // integer counts: order independent
+    }
+}
+
+struct PrepArgs {
+    int64_t n;
+    const int32_t* perm;
+    const double* r;
+    const double* phi;
+    const double* delay;
+    const double* weight;
+    const double* thr;
+    int n_r, n_phi;
+    double log_rin, log_rout;
+    double t0, t_end, hat_step;
+    double scale;
+    int32_t* node00;
+    int32_t* node01;
+    float4* W;
+    double* W64;
+    int32_t* K0;
+    int32_t* F0;
+    double* F64;
+    double* r_s;
+    double* delay_s;
+    double* weight_s;
+    double* thr_s;
+};
+
+// Per sorted ray: bilinear stencil in (log r, phi) and integer hat offset,
+// all derived in FP64 (Eq. 2 interpolation of the nodal history).
+__global__ void prep_rays(const PrepArgs a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    const int32_t o = a.perm[i];
+    const double r = a.r[o], phi = a.phi[o], dl = a.delay[o], w = a.weight[o];
+    double rho = (log(r) - a.log_rin) / (a.log_rout - a.log_rin) * (double)(a.n_r - 1);
+    int i0 = (int)floor(rho);
+    i0 = max(0, min(i0, a.n_r - 2));
+    const double fr = rho - (double)i0;
+    const double twopi = 6.283185307179586476925286766559;
+    double ph = phi / twopi * (double)a.n_phi;
+    ph = fmod(ph, (double)a.n_phi);
+    if (ph < 0.0) ph += (double)a.n_phi;
+    int j0 = (int)floor(ph);
+    if (j0 >= a.n_phi) j0 = a.n_phi - 1;
+    const double fp = ph - (double)j0;
+    const int j1 = (j0 + 1) % a.n_phi;
+    a.node00[i] = i0 * a.n_phi + j0;
+    a.node01[i] = i0 * a.n_phi + j1;
+    const double sw = a.scale * w;
+    const double c00 = sw * (1.0 - fr) * (1.0 - fp);
+    const double c10 = sw * fr * (1.0 - fp);
+    const double c01 = sw * (1.0 - fr) * fp;
+    const double c11 = sw * fr * fp;
+    a.W64[4 * i + 0] = c00;
+    a.W64[4 * i + 1] = c10;
+    a.W64[4 * i + 2] = c01;
+    a.W64[4 * i + 3] = c11;
+    a.W[i] = make_float4((float)c00, (float)c10, (float)c01, (float)c11);
+    // hat coordinate u(f) = (t_end - t_o(f) + Delta) / hat_step = u0 - f delta
+    const double u0 = (a.t_end - a.t0 + dl) / a.hat_step;
+    const double k0 = floor(u0);
+    const double frac = u0 - k0;
+    double fq = floor(frac * (double)kFracOne);
+    if (fq > (double)kFracMask) fq = (double)kFracMask;
+    if (fq < 0.0) fq = 0.0;
+    a.K0[i] = (int32_t)k0;
+    a.F0[i] = (int32_t)fq;
+    a.F64[i] = frac;
+    a.r_s[i] = r;
+    a.delay_s[i] = dl;
+    a.weight_s[i] = w;
+    a.thr_s[i] = a.thr[o];
+}
+
+__global__ void make_inc_keys(int64_t n, int n_phi, const int32_t* node00, const int32_t* node01,
+                              int32_t* key, int32_t* val, unsigned int* count) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 4 * n) return;
+    const int64_t e = t >> 2;
+    const int c = (int)(t & 3);
+    int node;
+    switch (c) {
+        case 0: node = node00[e]; break;
+        case 1: node = node00[e] + n_phi; break;
+        case 2: node = node01[e]; break;
+        default: node = node01[e] + n_phi; break;
+    }
+    key[t] = node;
+    val[t] = (int32_t)t;
+    atomicAdd(&count[node], 1u);
+}
+
+// Per direct row: sum_e w_e (FP64, sequential over the row's rays); squared.
+__global__ void row_weight_sq(int64_t n_rows, const int32_t* row_ptr, const double* w,
+                              double* out) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n_rows) return;
+    double s = 0.0;
+    for (int e = row_ptr[row]; e < row_ptr[row + 1]; ++e) s += w[e];
+    out[row] = s * s;
+}
+
+static bool dyadic_delta(double cadence, double hat_step, int64_t* D) {
+    const double d = cadence / hat_step;
+    const double q = d * (double)kFracOne;
+    if (!(q >= 1.0) || q != floor(q) || d > 1.0) return false;
+    *D = (int64_t)q;
+    return true;
+}
+
+static rtt_status check_grids(const rtt_source_grid* g, const rtt_time_grid* t) {
+    if (g->n_r < 2 || g->n_phi < 2 || !(g->r_in > 0.0) || !(g->r_out > g->r_in) ||
+        (int64_t)g->n_r * g->n_phi > (1 << 28)) {
+        set_error("invalid source grid (n_r=%d n_phi=%d r_in=%g r_out=%g)", g->n_r, g->n_phi,
+                  g->r_in, g->r_out);
+        return RTT_EINVAL;
+    }
+    if (t->n_frames < 1 || t->n_hats < 1 || !(t->cadence > 0.0) || !(t->hat_step > 0.0) ||
+        !std::isfinite(t->t0) || !std::isfinite(t->t_end)) {
+        set_error("invalid time grid");
+        return RTT_EINVAL;
+    }
+    int64_t D;
+    if (!dyadic_delta(t->cadence, t->hat_step, &D)) {
+        set_error("cadence/hat_step = %g must be a multiple of 2^-24 in (0, 1]",
+                  t->cadence / t->hat_step);
+        return RTT_EINVAL;
+    }
+    return RTT_OK;
+}
+
+template <typename T>
+static rtt_status alloc(T** p, size_t n) {
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T) + 16);
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc(%zu) failed: %s", n * sizeof(T), cudaGetErrorString(e));
+        *p = nullptr;
+        return RTT_ENOMEM;
+    }
+    return RTT_OK;
+}
+
+#define RTT_TRY(x)                  \
+    do {                            \
+        rtt_status _s = (x);        \
+        if (_s != RTT_OK) return _s; \
+    } while (0)
+
+static void free_op(rtt_op_s* op) {
+    if (!op) return;
+    void* ps[] = {op->row_ptr, op->ray_row, op->node00, op->node01, op->W,     op->W64,
+                  op->K0,      op->F0,      op->F64,    op->r,      op->delay, op->weight,
+                  op->thr,     op->node_ptr, op->inc,   op->row_order};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    delete op;
+}
+
+static int blocks(int64_t n, int t = 256) { return (int)((n + t - 1) / t); }
+
+// Scoped device buffers for the build (freed on every exit path).
+struct Scratch {
+    std::vector<void*> ptrs;
+    ~Scratch() {
+        for (void* p : ptrs) cudaFree(p);
+    }
+    template <typename T>
+    rtt_status get(T** p, size_t n) {
+        RTT_TRY(alloc(p, n));
+        ptrs.push_back(*p);
+        return RTT_OK;
+    }
+};
+
+static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* grid,
+                             const rtt_time_grid* time, const rtt_ray_table* tab,
+                             const rtt_options* opt, cudaStream_t st, rtt_op_s* op) {
+    const int64_t E = tab->n_rays;
+    // ---- host validation pass (also yields per-order delay ranges) ----
+    for (int n = 0; n < 3; ++n) {
+        op->dmin[n] = INFINITY;
+        op->dmax[n] = -INFINITY;
+    }
+    int64_t n_direct = 0;
+    for (int64_t i = 0; i < E; ++i) {
+        const int o = tab->order[i];
+        const double r = tab->r[i], ph = tab->phi[i], d = tab->delay[i], w = tab->weight[i],
+                     th = tab->throughput[i];
+        if (o < 0 || o > 2 || tab->pixel[i] < 0) {
+            set_error("ray %lld: order %d / pixel %d out of range", (long long)i, o, tab->pixel[i]);
+            return RTT_EINVAL;
+        }
+        if (!std::isfinite(r) || !std::isfinite(ph) || !std::isfinite(d) || !std::isfinite(w) ||
+            !std::isfinite(th) || std::fabs(ph) > 1e6 || std::fabs(d) > 1e6) {
+            set_error("ray %lld: non-finite or out-of-range value", (long long)i);
+            return RTT_EINVAL;
+        }
+        if (r < grid->r_in || r > grid->r_out) {
+            set_error("ray %lld: r = %.17g outside [r_in, r_out]", (long long)i, r);
+            return RTT_EINVAL;
+        }
+        const double u0 = (time->t_end - time->t0 + d) / time->hat_step;
+        if (std::fabs(u0) > 1e9) {
+            set_error("ray %lld: hat offset out of range", (long long)i);
+            return RTT_EINVAL;
+        }
+        op->dmin[o] = std::fmin(op->dmin[o], d);
+        op->dmax[o] = std::fmax(op->dmax[o], d);
+        n_direct += (o == 0);
+    }
+    if (n_direct == 0) {
+        set_error("the table has no direct (order 0) ray");
+        return RTT_EINVAL;
+    }
+    for (int n = 0; n < 3; ++n)
+        if (!(op->dmin[n] <= op->dmax[n])) op->dmin[n] = op->dmax[n] = NAN;
+    op->geom = *geom;
+    op->grid = *grid;
+    op->time = *time;
+    op->opt = *opt;
+    op->n_rays = E;
+    op->n_nodes = grid->n_r * grid->n_phi;
+    dyadic_delta(time->cadence, time->hat_step, &op->frame_D);
+    op->delta = time->cadence / time->hat_step;
+
+    Scratch sc;
+    int8_t* d_order;
+    int32_t* d_pixel;
+    double *d_r, *d_phi, *d_delay, *d_w, *d_thr;
+    RTT_TRY(sc.get(&d_order, E));
+    RTT_TRY(sc.get(&d_pixel, E));
+    RTT_TRY(sc.get(&d_r, E));
+    RTT_TRY(sc.get(&d_phi, E));
+    RTT_TRY(sc.get(&d_delay, E));
+    RTT_TRY(sc.get(&d_w, E));
+    RTT_TRY(sc.get(&d_thr, E));
+    RTT_CUDA(cudaMemcpyAsync(d_order, tab->order, E, cudaMemcpyHostToDevice, st));
+    RTT_CUDA(cudaMemcpyAsync(d_pixel, tab->pixel, E * 4, cudaMemcpyHostToDevice, st));
+    RTT_CUDA(cudaMemcpyAsync(d_r, tab->r, E * 8, cudaMemcpyHostToDevice, st));
+    RTT_CUDA(cudaMemcpyAsync(d_phi, tab->phi, E * 8, cudaMemcpyHostToDevice, st));
+    RTT_CUDA(cudaMemcpyAsync(d_delay, tab->delay, E * 8, cudaMemcpyHostToDevice, st));
+    RTT_CUDA(cudaMemcpyAsync(d_w, tab->weight, E * 8, cudaMemcpyHostToDevice, st));
+    RTT_CUDA(cudaMemcpyAsync(d_thr, tab->throughput, E * 8, cudaMemcpyHostToDevice, st));
+
+    // ---- row CSR: stable device radix sort of rays by (order, pixel) ----
+    unsigned long long *k_in, *k_out;
+    int32_t *v_in, *perm, *flag, *incl;
+    unsigned int* ocount;
+    RTT_TRY(sc.get(&k_in, E));
+    RTT_TRY(sc.get(&k_out, E));
+    RTT_TRY(sc.get(&v_in, E));
+    RTT_TRY(sc.get(&perm, E));
+    RTT_TRY(sc.get(&flag, E));
+    RTT_TRY(sc.get(&incl, E));
+    RTT_TRY(sc.get(&ocount, 4));
+    RTT_CUDA(cudaMemsetAsync(ocount, 0, 16, st));
+    make_row_keys<<<blocks(E), 256, 0, st>>>(E, d_order, d_pixel, k_in, v_in);
+    RTT_CUDA(cudaGetLastError());
+    size_t tmp_bytes = 0;
+    RTT_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, k_in, k_out, v_in, perm, E, 0, 34,
+                                             st));
+    size_t tmp2 = 0;
+    RTT_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tmp2, flag, incl, E, st));
+    tmp_bytes = tmp_bytes > tmp2 ? tmp_bytes : tmp2;
+    const int64_t S = op->n_nodes;
+    int32_t *ik_in, *ik_out, *iv_in;
+    unsigned int* ncount;
+    RTT_TRY(sc.get(&ik_in, 4 * E));
+    RTT_TRY(sc.get(&ik_out, 4 * E));
+    RTT_TRY(sc.get(&iv_in, 4 * E));
+    RTT_TRY(sc.get(&ncount, S + 1));
+    int end_bit = 1;
+    while ((1ll << end_bit) < S) ++end_bit;
+    size_t tmp3 = 0;
+    RTT_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp3, ik_in, ik_out, iv_in, iv_in, 4 * E, 0,
+                                             end_bit, st));
+    tmp_bytes = tmp_bytes > tmp3 ? tmp_bytes : tmp3;
+    size_t tmp4 = 0;
+    RTT_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp4, ncount, ncount, S + 1, st));
+    tmp_bytes = tmp_bytes > tmp4 ? tmp_bytes : tmp4;
+    void* d_tmp;
+    RTT_TRY(sc.get((unsigned char**)&d_tmp, tmp_bytes));
+
+    size_t tb = tmp_bytes;
+    RTT_CUDA(cub::DeviceRadixSort::SortPairs(d_tmp, tb, k_in, k_out, v_in, perm, E, 0, 34, st));
+    row_flags<<<blocks(E), 256, 0, st>>>(E, k_out, flag);
+    RTT_CUDA(cudaGetLastError());
+    tb = tmp_bytes;
+    RTT_CUDA(cub::DeviceScan::InclusiveSum(d_tmp, tb, flag, incl, E, st));
+    int32_t n_rows_i = 0;
+    RTT_CUDA(cudaMemcpyAsync(&n_rows_i, incl + (E - 1), 4, cudaMemcpyDeviceToHost, st));
+    RTT_CUDA(cudaStreamSynchronize(st));
+    const int64_t R = n_rows_i;
+    op->n_rows = R;
+    RTT_TRY(alloc(&op->row_ptr, R + 1));
+    RTT_TRY(alloc(&op->ray_row, E));
+    RTT_TRY(alloc(&op->row_order, R));
+    row_index<<<blocks(E), 256, 0, st>>>(E, k_out, flag, incl, op->ray_row, op->row_ptr,
+                                         op->row_order, ocount);
+    RTT_CUDA(cudaGetLastError());
+    const int32_t E32 = (int32_t)E;
+    RTT_CUDA(cudaMemcpyAsync(op->row_ptr + R, &E32, 4, cudaMemcpyHostToDevice, st));
+    unsigned int hcount[4];
+    RTT_CUDA(cudaMemcpyAsync(hcount, ocount, 16, cudaMemcpyDeviceToHost, st));
+    RTT_CUDA(cudaStreamSynchronize(st));
+    op->row_begin[0] = 0;
+    for (int n = 0; n < 3; ++n) op->row_begin[n + 1] = op->row_begin[n] + hcount[n];
+
+    // ---- s_ref (Eq. 17, j_ref = 1 evaluated directly) ----
+    RTT_TRY(alloc(&op->r, E));
+    RTT_TRY(alloc(&op->delay, E));
+    RTT_TRY(alloc(&op->weight, E));
+    RTT_TRY(alloc(&op->thr, E));
+    // first prep pass with scale = 1 yields the sorted raw weights for s_ref
+    RTT_TRY(alloc(&op->node00, E));
+    RTT_TRY(alloc(&op->node01, E));
+    RTT_TRY(alloc(&op->W, E));
+    RTT_TRY(alloc(&op->W64, 4 * E));
+    RTT_TRY(alloc(&op->K0, E));
+    RTT_TRY(alloc(&op->F0, E));
+    RTT_TRY(alloc(&op->F64, E));
+    PrepArgs pa{};
+    pa.n = E;
+    pa.perm = perm;
+    pa.r = d_r;
+    pa.phi = d_phi;
+    pa.delay = d_delay;
+    pa.weight = d_w;
+    pa.thr = d_thr;
+    pa.n_r = grid->n_r;
+    pa.n_phi = grid->n_phi;
+    pa.log_rin = log(grid->r_in);
+    pa.log_rout = log(grid->r_out);
+    pa.t0 = time->t0;
+    pa.t_end = time->t_end;
+    pa.hat_step = time->hat_step;
+    pa.scale = 1.0;
+    pa.node00 = op->node00;
+    pa.node01 = op->node01;
+    pa.W = op->W;
+    pa.W64 = op->W64;
+    pa.K0 = op->K0;
+    pa.F0 = op->F0;
+    pa.F64 = op->F64;
+    pa.r_s = op->r;
+    pa.delay_s = op->delay;
+    pa.weight_s = op->weight;
+    pa.thr_s = op->thr;
+    prep_rays<<<blocks(E), 256, 0, st>>>(pa);
+    RTT_CUDA(cudaGetLastError());
+    const int64_t R0 = op->row_begin[1];
+    double *rsq, *rsum;
+    RTT_TRY(sc.get(&rsq, R0));
+    RTT_TRY(sc.get(&rsum, 1));
+    row_weight_sq<<<blocks(R0), 256, 0, st>>>(R0, op->row_ptr, op->weight, rsq);
+    RTT_CUDA(cudaGetLastError());
+    size_t tmp5 = 0;
+    RTT_CUDA(cub::DeviceReduce::Sum(nullptr, tmp5, rsq, rsum, R0, st));
+    if (tmp5 > tmp_bytes) {
+        set_error("internal: reduce scratch too small");
+        return RTT_ECUDA;
+    }
+    tb = tmp_bytes;
+    RTT_CUDA(cub::DeviceReduce::Sum(d_tmp, tb, rsq, rsum, R0, st));
+    double hsum = 0.0;
+    RTT_CUDA(cudaMemcpyAsync(&hsum, rsum, 8, cudaMemcpyDeviceToHost, st));
+    RTT_CUDA(cudaStreamSynchronize(st));
+    op->s_ref = sqrt(hsum / (double)R0);
+    if (!(op->s_ref > 0.0)) {
+        set_error("s_ref = %g: direct weights are zero", op->s_ref);
+        return RTT_EINVAL;
+    }
+    op->scale = opt->snr0 / op->s_ref;
+    // second pass with the whitening scale folded into the corner weights
+    pa.scale = op->scale;
+    prep_rays<<<blocks(E), 256, 0, st>>>(pa);
+    RTT_CUDA(cudaGetLastError());
+
+    // ---- transposed incidence CSR: stable sort of (node, ray*4+corner) ----
+    RTT_CUDA(cudaMemsetAsync(ncount, 0, (S + 1) * 4, st));
+    make_inc_keys<<<blocks(4 * E), 256, 0, st>>>(E, grid->n_phi, op->node00, op->node01, ik_in,
+                                                  iv_in, ncount);
+    RTT_CUDA(cudaGetLastError());
+    RTT_TRY(alloc(&op->inc, 4 * E));
+    RTT_TRY(alloc(&op->node_ptr, S + 1));
+    tb = tmp_bytes;
+    RTT_CUDA(cub::DeviceRadixSort::SortPairs(d_tmp, tb, ik_in, ik_out, iv_in, op->inc, 4 * E, 0,
+                                             end_bit, st));
+    tb = tmp_bytes;
+    RTT_CUDA(cub::DeviceScan::ExclusiveSum(d_tmp, tb, ncount, (unsigned int*)op->node_ptr, S + 1,
+                                           st));
+    RTT_CUDA(cudaStreamSynchronize(st));
+    return RTT_OK;
+}
+
+static rtt_status make_seg(const rtt_op_s* op, int mask, ArmSeg* s) {
+    if (mask < 1 || mask > 7) {
+        set_error("arm_mask %d not in 1..7", mask);
+        return RTT_EINVAL;
+    }
+    s->n = 0;
+    s->total = 0;
+    s->mask = mask;
+    for (int n = 0; n < 3; ++n) {
+        if (!(mask & (1 << n))) continue;
+        const int64_t len = op->row_begin[n + 1] - op->row_begin[n];
+        if (len == 0) continue;
+        s->begin[s->n] = (int32_t)op->row_begin[n];
+        s->len[s->n] = (int32_t)len;
+        s->out_off[s->n] = s->total;
+        s->total += (int32_t)len;
+        s->n += 1;
+    }
+    for (int i = s->n; i < 3; ++i) s->begin[i] = s->len[i] = s->out_off[i] = 0;
+    return RTT_OK;
+}
+
+template <typename T>
+static rtt_status apply_common(rtt_op op, const T* in, T* out, int batch, int mask, void* stream,
+                               bool adjoint) {
+    if (!op || !in || !out || batch < 1) {
+        set_error("invalid argument (op=%p in=%p out=%p batch=%d)", (void*)op, (const void*)in,
+                  (void*)out, batch);
+        return RTT_EINVAL;
+    }
+    ArmSeg seg;
+    RTT_TRY(make_seg(op, mask, &seg));
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = adjoint ? launch_adjoint<T>(op, in, out, batch, seg, st)
+                            : launch_forward<T>(op, in, out, batch, seg, st);
+    if (e != cudaSuccess) {
+        set_error("apply launch failed: %s", cudaGetErrorString(e));
+        return RTT_ECUDA;
+    }
+    return RTT_OK;
+}
+
+}  // namespace rtt
+
+using namespace rtt;
+
+extern "C" {
+
+const char* rtt_error_string(rtt_status s) {
+    switch (s) {
+        case RTT_OK: return "ok";
+        case RTT_EINVAL: return "invalid argument";
+        case RTT_ENOMEM: return "out of memory";
+        case RTT_ECUDA: return "CUDA error";
+        case RTT_ETIMEOUT: return "device wait timed out";
+        case RTT_ENOTCONVERGED: return "iteration did not converge";
+        case RTT_ESTATE: return "invalid state";
+        case RTT_EDEVICE: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+const char* rtt_last_error(void) { return g_last_error.c_str(); }
+
+int rtt_abi_version(void) { return RTT_ABI_VERSION; }
+
+rtt_status rtt_build_operator(const rtt_geometry* geom, const rtt_source_grid* grid,
+                              const rtt_time_grid* time, const rtt_ray_table* table,
+                              const rtt_options* opt, void* stream, rtt_op* out) {
+    if (!geom || !grid || !time || !table || !opt || !out) {
+        set_error("null argument");
+        return RTT_EINVAL;
+    }
+    *out = nullptr;
+    if (table->n_rays < 1 || table->n_rays > (1ll << 29) || !table->order || !table->pixel ||
+        !table->r || !table->phi || !table->delay || !table->weight || !table->throughput) {
+        set_error("invalid ray table (n_rays=%lld)", (long long)table->n_rays);
+        return RTT_EINVAL;
+    }
+    if (!(opt->snr0 > 0.0) || !(opt->rho > 0.0)) {
+        set_error("snr0 and rho must be positive");
+        return RTT_EINVAL;
+    }
+    if (!(std::fabs(geom->spin) < 1.0)) {
+        set_error("spin must satisfy |a| < 1");
+        return RTT_EINVAL;
+    }
+    RTT_TRY(check_grids(grid, time));
+    rtt_op_s* op = new (std::nothrow) rtt_op_s();
+    if (!op) {
+        set_error("host allocation failed");
+        return RTT_ENOMEM;
+    }
+    rtt_status s = build_impl(geom, grid, time, table, opt, (cudaStream_t)stream, op);
+    if (s != RTT_OK) {
+        free_op(op);
+        return s;
+    }
+    *out = op;
+    return RTT_OK;
+}
+
+rtt_status rtt_op_query(rtt_op op, rtt_op_info* o) {
+    if (!op || !o) {
+        set_error("null argument");
+        return RTT_EINVAL;
+    }
+    o->n_rays = op->n_rays;
+    o->n_rows = op->n_rows;
+    for (int n = 0; n < 3; ++n) {
+        o->rows_per_order[n] = op->row_begin[n + 1] - op->row_begin[n];
+        o->delay_min[n] = op->dmin[n];
+        o->delay_max[n] = op->dmax[n];
+    }
+    o->n_nodes = op->n_nodes;
+    o->n_hats = op->time.n_hats;
+    o->n_frames = op->time.n_frames;
+    o->s_ref = op->s_ref;
+    o->scale = op->scale;
+    return RTT_OK;
+}
+
+rtt_status rtt_arm_rows(rtt_op op, int mask, int64_t* rows) {
+    if (!op || !rows) {
+        set_error("null argument");
+        return RTT_EINVAL;
+    }
+    ArmSeg s;
+    RTT_TRY(make_seg(op, mask, &s));
+    *rows = s.total;
+    return RTT_OK;
+}
+
+rtt_status rtt_apply_A(rtt_op op, const float* x, float* y, int batch, int mask, void* stream) {
+    return apply_common<float>(op, x, y, batch, mask, stream, false);
+}
+rtt_status rtt_apply_AT(rtt_op op, const float* y, float* x, int batch, int mask, void* stream) {
+    return apply_common<float>(op, y, x, batch, mask, stream, true);
+}
+rtt_status rtt_apply_A_f64(rtt_op op, const double* x, double* y, int batch, int mask,
+                           void* stream) {
+    return apply_common<double>(op, x, y, batch, mask, stream, false);
+}
+rtt_status rtt_apply_AT_f64(rtt_op op, const double* y, double* x, int batch, int mask,
+                            void* stream) {
+    return apply_common<double>(op, y, x, batch, mask, stream, true);
+}
+
+void rtt_destroy(rtt_op op) { free_op(op); }
+
+}  // extern "C"

@@ -1,0 +1,401 @@
+// Forward operator A and its adjoint A^T (Sec. 3.1 Eq. 2-3, Eq. 16, Eq. 47).
+//
+// Forward (one warp per (row, frame chunk, batch chunk)):
+//   for each ray e of the row, the spatially interpolated history
+//   z_e[k][b] = sum_c W_{e,c} x[node_c][k][b] is staged in shared memory for
+//   the hats the frame chunk can touch, then every output sample adds
+//   (1 - fr) z_e[k0] + fr z_e[k0 + 1] with the exact integer hat index k0 and
+//   24-bit fraction fr of that (ray, frame).  y is written once, coalesced.
+// Adjoint (one warp per (node, hat chunk, batch chunk)): a deterministic
+//   gather over the node's incidence list (sorted by ray), summing for each
+//   owned (k, b) the frames whose hat pair contains k, with the same integer
+//   hat arithmetic as the forward, so the two are exact transposes.
+#include <cuda_runtime.h>
+
+#include "rtt_internal.cuh"
+
+namespace rtt {
+
+template <typename T>
+struct HatCoef;
+
+// FP32 path: fraction held as a 24-bit integer.
+template <>
+struct HatCoef<float> {
+    int32_t K0, F0;
+    int64_t D;
+    __device__ __forceinline__ void at(int f, int& k0, float& fr) const {
+        const int64_t fd = (int64_t)f * D;
+        const int32_t A = (int32_t)(fd >> kFracBits);
+        const int32_t R = (int32_t)(fd & kFracMask);
+        int32_t F = F0 - R;
+        k0 = K0 - A;
+        if (F < 0) {
+            F += kFracOne;
+            k0 -= 1;
+        }
+        fr = (float)F * (1.0f / (float)kFracOne);
+    }
+};
+
+// FP64 path: exact FP64 fraction; the per-frame offset f * delta is dyadic.
+template <>
+struct HatCoef<double> {
+    int32_t K0;
+    double F;
+    int64_t D;
+    __device__ __forceinline__ void at(int f, int& k0, double& fr) const {
+        const int64_t fd = (int64_t)f * D;
+        const int32_t A = (int32_t)(fd >> kFracBits);
+        const double R = (double)(fd & kFracMask) * (1.0 / (double)kFracOne);
+        double v = F - R;
+        k0 = K0 - A;
+        if (v < 0.0) {
+            v += 1.0;
+            k0 -= 1;
+        }
+        fr = v;
+    }
+};
+
+template <typename T>
+struct ApplyArgs {
+    const int32_t* row_ptr;
+    const int32_t* ray_row;
+    const int32_t* row_order;
+    const int32_t* node00;
+    const int32_t* node01;
+    const float4* W;
+    const double* W64;
+    const int32_t* K0;
+    const int32_t* F0;
+    const double* F64;
+    const int32_t* node_ptr;
+    const int32_t* inc;
+    const T* in;
+    T* out;
+    int B, K, Tn, n_phi, n_nodes;
+    int64_t D;
+    double delta;
+    ArmSeg seg;
+    int FC;       // frames per chunk (forward)
+    int zwin;     // hats staged per chunk (forward)
+    int KC;       // hats per chunk (adjoint)
+    int n_fchunk, n_bchunk, n_kchunk;
+    int64_t n_tasks;
+};
+
+template <typename T>
+__device__ __forceinline__ void load_w(const ApplyArgs<T>& a, int e, T w[4]);
+
+template <>
+__device__ __forceinline__ void load_w<float>(const ApplyArgs<float>& a, int e, float w[4]) {
+    const float4 v = a.W[e];
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+}
+template <>
+__device__ __forceinline__ void load_w<double>(const ApplyArgs<double>& a, int e, double w[4]) {
+    const double2* p = reinterpret_cast<const double2*>(a.W64 + 4 * (int64_t)e);
+    const double2 v0 = p[0], v1 = p[1];
+    w[0] = v0.x; w[1] = v0.y; w[2] = v1.x; w[3] = v1.y;
+}
+
+template <typename T>
+__device__ __forceinline__ HatCoef<T> load_hat(const ApplyArgs<T>& a, int e);
+template <>
+__device__ __forceinline__ HatCoef<float> load_hat<float>(const ApplyArgs<float>& a, int e) {
+    HatCoef<float> h;
+    h.K0 = a.K0[e]; h.F0 = a.F0[e]; h.D = a.D;
+    return h;
+}
+template <>
+__device__ __forceinline__ HatCoef<double> load_hat<double>(const ApplyArgs<double>& a, int e) {
+    HatCoef<double> h;
+    h.K0 = a.K0[e]; h.F = a.F64[e]; h.D = a.D;
+    return h;
+}
+
+__device__ __forceinline__ int seg_in_row(const ArmSeg& s, int row_out) {
+    int r = row_out;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (i < s.n && r < s.len[i]) return s.begin[i] + r;
+        if (i < s.n) r -= s.len[i];
+    }
+    return -1;
+}
+
+// output row of an input row under the arm mask, -1 if not selected
+__device__ __forceinline__ int seg_out_row(const ArmSeg& s, int row_in) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (i < s.n && row_in >= s.begin[i] && row_in < s.begin[i] + s.len[i])
+            return s.out_off[i] + (row_in - s.begin[i]);
+    }
+    return -1;
+}
+
+constexpr int kWarpsPerBlock = 8;
+constexpr int kOutPerLane = 32;
+
+template <typename T, int BC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+fwd_kernel(const ApplyArgs<T> a) {
+    extern __shared__ unsigned char smem_raw[];
+    T* zs = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const int FC = a.FC;
+    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
+        const int bchunk = (int)(task % a.n_bchunk);
+        const int64_t t2 = task / a.n_bchunk;
+        const int fchunk = (int)(t2 % a.n_fchunk);
+        const int row_out = (int)(t2 / a.n_fchunk);
+        const int row = seg_in_row(a.seg, row_out);
+        const int f_begin = fchunk * FC;
+        const int f_end = min(a.Tn, f_begin + FC);
+        const int b0 = bchunk * BC;
+        T acc[kOutPerLane];
+#pragma unroll
+        for (int j = 0; j < kOutPerLane; ++j) acc[j] = T(0);
+        const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
+        for (int e = e_begin; e < e_end; ++e) {
+            const HatCoef<T> hc = load_hat(a, e);
+            int k_top, k_bot;
+            T dummy;
+            hc.at(f_begin, k_top, dummy);
+            hc.at(f_end - 1, k_bot, dummy);
+            const int k_lo = k_bot;             // smallest hat touched
+            const int nwin = k_top + 2 - k_lo;  // hats k_lo .. k_top + 1
+            T w[4];
+            load_w(a, e, w);
+            const int n00 = a.node00[e], n01 = a.node01[e];
+            const int64_t KB = (int64_t)a.K * a.B;
+            const T* x00 = a.in + (int64_t)n00 * KB;
+            const T* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB;
+            const T* x01 = a.in + (int64_t)n01 * KB;
+            const T* x11 = a.in + (int64_t)(n01 + a.n_phi) * KB;
+            for (int o = lane; o < nwin * BC; o += 32) {
+                const int kk = o / BC, bb = o - kk * BC;
+                const int k = k_lo + kk;
+                const int b = b0 + bb;
+                T z = T(0);
+                if (k >= 0 && k < a.K && b < a.B) {
+                    const int64_t off = (int64_t)k * a.B + b;
+                    z = w[0] * x00[off] + w[1] * x10[off] + w[2] * x01[off] + w[3] * x11[off];
+                }
+                zs[o] = z;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int j = 0; j < kOutPerLane; ++j) {
+                const int o = lane + 32 * j;
+                const int fl = o / BC, bb = o - fl * BC;
+                const int f = f_begin + fl;
+                if (f < f_end) {
+                    int k0;
+                    T fr;
+                    hc.at(f, k0, fr);
+                    const int i0 = (k0 - k_lo) * BC + bb;
+                    acc[j] += (T(1) - fr) * zs[i0] + fr * zs[i0 + BC];
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int j = 0; j < kOutPerLane; ++j) {
+            const int o = lane + 32 * j;
+            const int fl = o / BC, bb = o - fl * BC;
+            const int f = f_begin + fl;
+            const int b = b0 + bb;
+            if (f < f_end && b < a.B) a.out[((int64_t)row_out * a.Tn + f) * a.B + b] = acc[j];
+        }
+    }
+}
+
+constexpr int kAdjOutPerLane = 8;
+
+template <typename T, int BC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+adj_kernel(const ApplyArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const double inv_delta = 1.0 / a.delta;
+    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
+        const int bchunk = (int)(task % a.n_bchunk);
+        const int64_t t2 = task / a.n_bchunk;
+        const int kchunk = (int)(t2 % a.n_kchunk);
+        const int node = (int)(t2 / a.n_kchunk);
+        const int b0 = bchunk * BC;
+        const int k_begin = kchunk * a.KC;
+        T acc[kAdjOutPerLane];
+#pragma unroll
+        for (int j = 0; j < kAdjOutPerLane; ++j) acc[j] = T(0);
+        const int i_begin = a.node_ptr[node], i_end = a.node_ptr[node + 1];
+        for (int ii = i_begin; ii < i_end; ++ii) {
+            const int code = a.inc[ii];
+            const int e = code >> 2, c = code & 3;
+            const int row_out = seg_out_row(a.seg, a.ray_row[e]);
+            if (row_out < 0) continue;
+            T w[4];
+            load_w(a, e, w);
+            const T coef = w[c];
+            const HatCoef<T> hc = load_hat(a, e);
+            double u0;
+            if constexpr (sizeof(T) == 4) {
+                u0 = (double)hc.K0 + (double)hc.F0 * (1.0 / (double)kFracOne);
+            } else {
+                u0 = (double)hc.K0 + (double)hc.F;
+            }
+            const T* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
+#pragma unroll
+            for (int j = 0; j < kAdjOutPerLane; ++j) {
+                const int o = lane + 32 * j;
+                const int kk = o / BC, bb = o - kk * BC;
+                const int k = k_begin + kk;
+                const int b = b0 + bb;
+                if (kk >= a.KC || k >= a.K || b >= a.B) continue;
+                // frames whose hat pair can contain k: u(f) = u0 - f delta in (k - 1, k + 1)
+                const double flo = fmax(floor((u0 - (double)k - 1.0) * inv_delta) - 1.0, 0.0);
+                const double fhi = fmin(ceil((u0 - (double)k + 1.0) * inv_delta) + 1.0,
+                                        (double)(a.Tn - 1));
+                const int f_lo = (int)flo;
+                const int f_hi = fhi < flo ? -1 : (int)fhi;
+                T s = T(0);
+                for (int f = f_lo; f <= f_hi; ++f) {
+                    int k0;
+                    T fr;
+                    hc.at(f, k0, fr);
+                    T hw;
+                    if (k0 == k) hw = T(1) - fr;
+                    else if (k0 + 1 == k) hw = fr;
+                    else continue;
+                    s += hw * yrow[(int64_t)f * a.B + b];
+                }
+                acc[j] += coef * s;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kAdjOutPerLane; ++j) {
+            const int o = lane + 32 * j;
+            const int kk = o / BC, bb = o - kk * BC;
+            const int k = k_begin + kk;
+            const int b = b0 + bb;
+            if (kk < a.KC && k < a.K && b < a.B)
+                a.out[((int64_t)node * a.K + k) * a.B + b] = acc[j];
+        }
+    }
+}
+
+static int pick_bc(int B) {
+    int bc = 1;
+    while (bc < B && bc < 32) bc <<= 1;
+    return bc;
+}
+
+static int grid_for(int64_t n_tasks) {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t want = (n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int64_t cap = (int64_t)sms * 16;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+template <typename T>
+static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, const ArmSeg& seg) {
+    ApplyArgs<T> a{};
+    a.row_ptr = op->row_ptr;
+    a.ray_row = op->ray_row;
+    a.row_order = op->row_order;
+    a.node00 = op->node00;
+    a.node01 = op->node01;
+    a.W = op->W;
+    a.W64 = op->W64;
+    a.K0 = op->K0;
+    a.F0 = op->F0;
+    a.F64 = op->F64;
+    a.node_ptr = op->node_ptr;
+    a.inc = op->inc;
+    a.in = in;
+    a.out = out;
+    a.B = B;
+    a.K = op->time.n_hats;
+    a.Tn = op->time.n_frames;
+    a.n_phi = op->grid.n_phi;
+    a.n_nodes = op->n_nodes;
+    a.D = op->frame_D;
+    a.delta = op->delta;
+    a.seg = seg;
+    return a;
+}
+
+template <typename T, int BC>
+static cudaError_t launch_fwd_bc(ApplyArgs<T> a, cudaStream_t st) {
+    a.FC = kOutPerLane * 32 / BC;
+    a.zwin = (int)ceil((a.FC - 1) * a.delta) + 3;
+    a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
+    a.n_bchunk = (a.B + BC - 1) / BC;
+    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk * a.n_bchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    const size_t smem = (size_t)kWarpsPerBlock * a.zwin * BC * sizeof(T);
+    if (smem > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(fwd_kernel<T, BC>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    fwd_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T, int BC>
+static cudaError_t launch_adj_bc(ApplyArgs<T> a, cudaStream_t st) {
+    a.KC = kAdjOutPerLane * 32 / BC;
+    a.n_kchunk = (a.K + a.KC - 1) / a.KC;
+    a.n_bchunk = (a.B + BC - 1) / BC;
+    a.n_tasks = (int64_t)a.n_nodes * a.n_kchunk * a.n_bchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    adj_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const ArmSeg& seg,
+                           cudaStream_t st) {
+    ApplyArgs<T> a = base_args<T>(op, x, y, B, seg);
+    switch (pick_bc(B)) {
+        case 1: return launch_fwd_bc<T, 1>(a, st);
+        case 2: return launch_fwd_bc<T, 2>(a, st);
+        case 4: return launch_fwd_bc<T, 4>(a, st);
+        case 8: return launch_fwd_bc<T, 8>(a, st);
+        case 16: return launch_fwd_bc<T, 16>(a, st);
+        default: return launch_fwd_bc<T, 32>(a, st);
+    }
+}
+
+template <typename T>
+cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const ArmSeg& seg,
+                           cudaStream_t st) {
+    ApplyArgs<T> a = base_args<T>(op, y, x, B, seg);
+    switch (pick_bc(B)) {
+        case 1: return launch_adj_bc<T, 1>(a, st);
+        case 2: return launch_adj_bc<T, 2>(a, st);
+        case 4: return launch_adj_bc<T, 4>(a, st);
+        case 8: return launch_adj_bc<T, 8>(a, st);
+        case 16: return launch_adj_bc<T, 16>(a, st);
+        default: return launch_adj_bc<T, 32>(a, st);
+    }
+}
+
+template cudaError_t launch_forward<float>(const rtt_op_s*, const float*, float*, int, const ArmSeg&,
+                                           cudaStream_t);
+template cudaError_t launch_forward<double>(const rtt_op_s*, const double*, double*, int,
+                                            const ArmSeg&, cudaStream_t);
+template cudaError_t launch_adjoint<float>(const rtt_op_s*, const float*, float*, int, const ArmSeg&,
+                                           cudaStream_t);
+template cudaError_t launch_adjoint<double>(const rtt_op_s*, const double*, double*, int,
+                                            const ArmSeg&, cudaStream_t);
+
+}  // namespace rtt

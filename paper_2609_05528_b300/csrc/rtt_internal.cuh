@@ -1,0 +1,66 @@
+// Internal definitions shared by the librtt translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "rtt.h"
+
+namespace rtt {
+
+// 24 fractional bits for the per-ray hat offset: the fraction of every
+// (ray, frame) sample is then an exact FP32 value and the hat index is an
+// exact integer computation.
+constexpr int kFracBits = 24;
+constexpr int32_t kFracOne = 1 << kFracBits;
+constexpr int32_t kFracMask = kFracOne - 1;
+
+void set_error(const char* fmt, ...);
+
+// Rows selected by an arm mask: up to three contiguous segments of the
+// (order, pixel)-sorted row list, concatenated in order.
+struct ArmSeg {
+    int32_t begin[3];   // first input row of segment
+    int32_t len[3];     // number of rows
+    int32_t out_off[3]; // first output row of segment
+    int32_t n;          // number of segments
+    int32_t total;      // total selected rows
+    int32_t mask;
+};
+
+}  // namespace rtt
+
+struct rtt_op_s {
+    rtt_geometry geom;
+    rtt_source_grid grid;
+    rtt_time_grid time;
+    rtt_options opt;
+    int64_t n_rays = 0;
+    int64_t n_rows = 0;
+    int64_t row_begin[4] = {0, 0, 0, 0};  // rows of order n: [row_begin[n], row_begin[n+1])
+    int32_t n_nodes = 0;
+    int64_t frame_D = 0;  // (cadence / hat_step) * 2^24, exact integer
+    double delta = 0.0;   // cadence / hat_step
+    double s_ref = 0.0, scale = 0.0;
+    double dmin[3], dmax[3];
+
+    // rays sorted by row (device)
+    int32_t* row_ptr = nullptr;   // [R+1]
+    int32_t* ray_row = nullptr;   // [E]
+    int32_t* node00 = nullptr;    // [E] node (i0, j0)
+    int32_t* node01 = nullptr;    // [E] node (i0, j1), j1 = (j0 + 1) mod n_phi
+    float4* W = nullptr;          // [E] scale * w * bilinear, corners (i0j0, i1j0, i0j1, i1j1)
+    double* W64 = nullptr;        // [4E] same in FP64
+    int32_t* K0 = nullptr;        // [E] floor(u0)
+    int32_t* F0 = nullptr;        // [E] floor(frac(u0) * 2^24)
+    double* F64 = nullptr;        // [E] frac(u0) exactly
+    double* r = nullptr;          // [E] FP64 copies for probes and quantiles
+    double* delay = nullptr;
+    double* weight = nullptr;
+    double* thr = nullptr;
+    int32_t* node_ptr = nullptr;  // [S+1] transposed incidence CSR
+    int32_t* inc = nullptr;       // [4E] e * 4 + c
+    int32_t* row_order = nullptr; // [R] order of each row
+};

@@ -1,0 +1,270 @@
+"""Thin ctypes binding of librtt.so (declarations in include/rtt.h).
+
+Argument marshalling only: every step of the operator runs in the library's
+CUDA kernels.  torch supplies device memory and streams.  If the library is
+missing or cannot be loaded, every entry point raises (there is no CPU
+fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "librtt.so")
+_LIB = None
+
+i8p = ctypes.POINTER(ctypes.c_int8)
+i32p = ctypes.POINTER(ctypes.c_int32)
+i64p = ctypes.POINTER(ctypes.c_int64)
+dp = ctypes.POINTER(ctypes.c_double)
+vp = ctypes.c_void_p
+
+
+class RttError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: status {status}: {msg}")
+        self.status = status
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("spin", ctypes.c_double), ("incl_deg", ctypes.c_double)]
+
+
+class SourceGrid(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int32), ("n_phi", ctypes.c_int32), ("r_in", ctypes.c_double),
+                ("r_out", ctypes.c_double)]
+
+
+class TimeGrid(ctypes.Structure):
+    _fields_ = [("n_frames", ctypes.c_int32), ("t0", ctypes.c_double), ("cadence", ctypes.c_double),
+                ("n_hats", ctypes.c_int32), ("hat_step", ctypes.c_double),
+                ("t_end", ctypes.c_double)]
+
+
+class RayTable(ctypes.Structure):
+    _fields_ = [("n_rays", ctypes.c_int64), ("order", i8p), ("pixel", i32p), ("r", dp),
+                ("phi", dp), ("delay", dp), ("weight", dp), ("throughput", dp)]
+
+
+class RayBuffer(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("order", i8p), ("pixel", i32p), ("r", dp),
+                ("phi", dp), ("delay", dp), ("weight", dp), ("throughput", dp)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("snr0", ctypes.c_double), ("rho", ctypes.c_double)]
+
+
+class OpInfo(ctypes.Structure):
+    _fields_ = [("n_rays", ctypes.c_int64), ("n_rows", ctypes.c_int64),
+                ("rows_per_order", ctypes.c_int64 * 3), ("n_nodes", ctypes.c_int64),
+                ("n_hats", ctypes.c_int32), ("n_frames", ctypes.c_int32),
+                ("s_ref", ctypes.c_double), ("scale", ctypes.c_double),
+                ("delay_min", ctypes.c_double * 3), ("delay_max", ctypes.c_double * 3)]
+
+
+class Screen(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("alpha", dp), ("beta", dp), ("pixel", i32p),
+                ("n_sub", i32p), ("d_omega_pixel", ctypes.c_double)]
+
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "rtt_error_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "rtt_last_error": (ctypes.c_char_p, []),
+    "rtt_abi_version": (ctypes.c_int, []),
+    "rtt_trace_rays": (ctypes.c_int, [ctypes.POINTER(Geometry), ctypes.POINTER(SourceGrid),
+                                      ctypes.POINTER(Screen), ctypes.POINTER(RayBuffer), i64p,
+                                      vp]),
+    "rtt_build_operator": (ctypes.c_int, [ctypes.POINTER(Geometry), ctypes.POINTER(SourceGrid),
+                                          ctypes.POINTER(TimeGrid), ctypes.POINTER(RayTable),
+                                          ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]),
+    "rtt_op_query": (ctypes.c_int, [vp, ctypes.POINTER(OpInfo)]),
+    "rtt_arm_rows": (ctypes.c_int, [vp, ctypes.c_int, i64p]),
+    "rtt_apply_A": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+    "rtt_apply_AT": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+    "rtt_apply_A_f64": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+    "rtt_apply_AT_f64": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+    "rtt_destroy": (None, [vp]),
+}
+
+
+def lib():
+    """Load librtt.so (raises if it is missing: there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2609_05528_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def check(status: int, where: str):
+    if status != 0:
+        L = lib()
+        raise RttError(status, where, L.rtt_last_error().decode())
+
+
+def _ptr(a: np.ndarray, typ):
+    return a.ctypes.data_as(typ)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def rtt_trace_rays(spin, incl_deg, grid, samples, stream=None):
+    """Trace screen samples on the GPU; returns the raw FP64 table as numpy arrays
+    (dict with order, pixel, r, phi, delay, weight, throughput)."""
+    L = lib()
+    n = len(samples)
+    al = np.ascontiguousarray(samples.alpha, np.float64)
+    be = np.ascontiguousarray(samples.beta, np.float64)
+    px = np.ascontiguousarray(samples.pixel, np.int32)
+    ns = np.ascontiguousarray(samples.n_sub, np.int32)
+    scr = Screen(n, _ptr(al, dp), _ptr(be, dp), _ptr(px, i32p), _ptr(ns, i32p),
+                 float(samples.d_omega_pixel))
+    cap = 3 * n
+    out = {"order": np.empty(cap, np.int8), "pixel": np.empty(cap, np.int32)}
+    for k in ("r", "phi", "delay", "weight", "throughput"):
+        out[k] = np.empty(cap, np.float64)
+    buf = RayBuffer(cap, _ptr(out["order"], i8p), _ptr(out["pixel"], i32p), _ptr(out["r"], dp),
+                    _ptr(out["phi"], dp), _ptr(out["delay"], dp), _ptr(out["weight"], dp),
+                    _ptr(out["throughput"], dp))
+    n_out = ctypes.c_int64(0)
+    g = Geometry(float(spin), float(incl_deg))
+    sg = SourceGrid(grid.n_r, grid.n_phi, grid.r_in, grid.r_out)
+    check(L.rtt_trace_rays(ctypes.byref(g), ctypes.byref(sg), ctypes.byref(scr), ctypes.byref(buf),
+                           ctypes.byref(n_out), _stream(stream)), "rtt_trace_rays")
+    m = n_out.value
+    return {k: v[:m].copy() for k, v in out.items()}
+
+
+class Operator:
+    """Owns an rtt_op handle (rtt_build_operator / rtt_destroy)."""
+
+    def __init__(self, workload, table, snr0: float = 100.0, rho: float = 1.0, stream=None):
+        L = lib()
+        self.workload = workload
+        g, t = workload.grid, workload.time
+        arr = {
+            "order": np.ascontiguousarray(table["order"], np.int8),
+            "pixel": np.ascontiguousarray(table["pixel"], np.int32),
+        }
+        for k in ("r", "phi", "delay", "weight", "throughput"):
+            arr[k] = np.ascontiguousarray(table[k], np.float64)
+        self._keep = arr
+        rt = RayTable(arr["r"].shape[0], _ptr(arr["order"], i8p), _ptr(arr["pixel"], i32p),
+                      _ptr(arr["r"], dp), _ptr(arr["phi"], dp), _ptr(arr["delay"], dp),
+                      _ptr(arr["weight"], dp), _ptr(arr["throughput"], dp))
+        geo = Geometry(workload.geometry.spin, workload.geometry.incl_deg)
+        sg = SourceGrid(g.n_r, g.n_phi, g.r_in, g.r_out)
+        tg = TimeGrid(t.n_frames, t.t0, t.cadence, t.n_hats, t.hat_step, t.t_end)
+        opt = Options(snr0, rho)
+        h = ctypes.c_void_p()
+        check(L.rtt_build_operator(ctypes.byref(geo), ctypes.byref(sg), ctypes.byref(tg),
+                                   ctypes.byref(rt), ctypes.byref(opt), _stream(stream),
+                                   ctypes.byref(h)), "rtt_build_operator")
+        self.handle = h
+        self._keep = None
+        info = OpInfo()
+        check(L.rtt_op_query(self.handle, ctypes.byref(info)), "rtt_op_query")
+        self.info = info
+        self.n_nodes = int(info.n_nodes)
+        self.n_hats = int(info.n_hats)
+        self.n_frames = int(info.n_frames)
+        self.scale = float(info.scale)
+        self.s_ref = float(info.s_ref)
+
+    def arm_rows(self, arm_mask: int = 7) -> int:
+        n = ctypes.c_int64(0)
+        check(lib().rtt_arm_rows(self.handle, arm_mask, ctypes.byref(n)), "rtt_arm_rows")
+        return int(n.value)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rtt_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- applies (torch tensors on the current CUDA device) --
+    def _launch(self, name, src, dst, batch, arm, stream):
+        fn = getattr(lib(), name)
+        check(fn(self.handle, ctypes.c_void_p(src.data_ptr()), ctypes.c_void_p(dst.data_ptr()),
+                 int(batch), int(arm), _stream(stream)), name)
+
+    def apply_A(self, x, y=None, arm_mask: int = 7, stream=None):
+        """y = scale * A x; x: [n_nodes, n_hats, B] (float32 or float64, CUDA)."""
+        import torch
+        assert x.is_cuda and x.is_contiguous() and x.dim() == 3
+        B = x.shape[2]
+        R = self.arm_rows(arm_mask)
+        if y is None:
+            y = torch.empty((R, self.n_frames, B), dtype=x.dtype, device=x.device)
+        name = "rtt_apply_A" if x.dtype == torch.float32 else "rtt_apply_A_f64"
+        self._launch(name, x, y, B, arm_mask, stream)
+        return y
+
+    def apply_AT(self, y, x=None, arm_mask: int = 7, stream=None):
+        """x = scale * A^T y; y: [arm_rows, n_frames, B]."""
+        import torch
+        assert y.is_cuda and y.is_contiguous() and y.dim() == 3
+        B = y.shape[2]
+        if x is None:
+            x = torch.empty((self.n_nodes, self.n_hats, B), dtype=y.dtype, device=y.device)
+        name = "rtt_apply_AT" if y.dtype == torch.float32 else "rtt_apply_AT_f64"
+        self._launch(name, y, x, B, arm_mask, stream)
+        return x
+
+
+def _autograd():
+    import torch
+
+    class ApplyA(torch.autograd.Function):
+        """y = scale * A x with the hand-written adjoint as its backward:
+        grad_x = scale * A^T grad_y (both in librtt kernels)."""
+
+        @staticmethod
+        def forward(ctx, x, op: Operator, arm_mask: int):
+            ctx.op = op
+            ctx.arm = arm_mask
+            return op.apply_A(x.contiguous(), arm_mask=arm_mask)
+
+        @staticmethod
+        def backward(ctx, gy):
+            return ctx.op.apply_AT(gy.contiguous(), arm_mask=ctx.arm), None, None
+
+    return ApplyA
+
+
+_APPLY = None
+
+
+def apply_A_autograd(x, op: Operator, arm_mask: int = 7):
+    global _APPLY
+    if _APPLY is None:
+        _APPLY = _autograd()
+    return _APPLY.apply(x, op, arm_mask)

@@ -1,0 +1,77 @@
+"""The C-ABI library loads, exports every entry point declared in
+include/rtt.h, and rejects invalid arguments before touching a GPU."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2609_05528_b300 import build, rtt
+from paper_2609_05528_b300 import inputs as I
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return rtt.lib()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "rtt.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rtt_[A-Za-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert "rtt_apply_A" in names and "rtt_build_operator" in names
+    for n in names:
+        assert hasattr(L, n), n
+    # the binding wraps exactly the declared entry points
+    assert set(rtt.exported_symbols()) == set(names)
+
+
+def test_status_strings(L):
+    assert L.rtt_abi_version() == 1
+    assert L.rtt_error_string(0) == b"ok"
+    assert L.rtt_error_string(-1) == b"invalid argument"
+
+
+def _table(n=4):
+    return {"order": np.zeros(n, np.int8), "pixel": np.arange(n, dtype=np.int32),
+            "r": np.full(n, 5.0), "phi": np.linspace(0, 1, n), "delay": np.zeros(n),
+            "weight": np.ones(n), "throughput": np.ones(n)}
+
+
+@pytest.mark.parametrize("bad", ["r_out_of_range", "order", "nonfinite", "no_direct",
+                                 "cadence", "grid"])
+def test_build_rejects_invalid_tables_on_host(L, bad):
+    w = I.schw32()
+    tab = _table()
+    if bad == "r_out_of_range":
+        tab["r"][1] = 11.5
+    elif bad == "order":
+        tab["order"][2] = 3
+    elif bad == "nonfinite":
+        tab["delay"][0] = np.nan
+    elif bad == "no_direct":
+        tab["order"][:] = 1
+    elif bad == "cadence":
+        w = I.Workload("c", w.geometry, w.grid, I.TimeGrid(24, 0.3, 12, t_end=0.0))
+    elif bad == "grid":
+        w = I.Workload("g", w.geometry, I.SourceGrid(1, 16), w.time)
+    with pytest.raises(rtt.RttError) as ei:
+        rtt.Operator(w, tab, stream=0)
+    assert ei.value.status == -1
+
+
+def test_trace_rejects_bad_geometry(L):
+    w = I.schw32()
+    s = I.screen_samples(w)
+    with pytest.raises(rtt.RttError):
+        rtt.rtt_trace_rays(0.5, 95.0, w.grid, s, stream=0)
+    with pytest.raises(rtt.RttError):
+        rtt.rtt_trace_rays(1.2, 50.0, w.grid, s, stream=0)

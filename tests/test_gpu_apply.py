@@ -1,0 +1,200 @@
+"""GPU parity of the forward operator A and its adjoint A^T against the FP64
+oracle, through the C ABI (librtt.so).  The oracle's raw ray table is fed to
+both sides, so the comparison isolates the kernels.
+
+Tolerance (FP32 path): relative L2 error <= 1e-5 over the output and an
+elementwise bound |gpu - ref| <= 1e-5 * max|ref|; FP64 path: 1e-12.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_05528_b300 import build, rtt
+from paper_2609_05528_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL32 = 1e-5
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    rtt.lib()
+
+
+def _optable(tab: O.Table) -> dict:
+    return {"order": tab.order, "pixel": tab.pixel, "r": tab.r, "phi": tab.phi,
+            "delay": tab.delay, "weight": tab.weight, "throughput": tab.throughput}
+
+
+def _cmp(got: np.ndarray, ref: np.ndarray, tol: float):
+    assert got.shape == ref.shape
+    err = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-300)
+    assert err <= tol, f"relative L2 error {err:.3e} > {tol}"
+    amax = np.max(np.abs(ref)) if ref.size else 0.0
+    assert np.max(np.abs(got - ref), initial=0.0) <= tol * max(amax, 1e-300) * 10
+
+
+class Case:
+    def __init__(self, w, seeds_x=(1, 2, 3)):
+        self.w = w
+        self.tab = O.build_table(w, I.screen_samples(w))
+        self.op = rtt.Operator(w, _optable(self.tab))
+        self.scale = O.scale(self.tab)
+
+
+@pytest.fixture(scope="module")
+def small():
+    # several warps / chunks on every axis plus ragged tails
+    return Case(I.small_kerr(spin=0.5, incl_deg=50.0, nx=48, n_r=12, n_phi=24, n_frames=300,
+                             n_hats=80, ss=2))
+
+
+@pytest.fixture(scope="module")
+def schw():
+    return Case(I.schw32())
+
+
+def _arm_orders(mask):
+    return tuple(n for n in range(3) if mask & (1 << n))
+
+
+def test_scale_and_rows_match_oracle(small):
+    c = small
+    assert c.op.s_ref == pytest.approx(O.s_ref(c.tab), rel=1e-13)
+    assert c.op.info.n_rows == c.tab.n_rows
+    for n in range(3):
+        assert c.op.info.rows_per_order[n] == c.tab.rows_of_order(n)
+
+
+@pytest.mark.parametrize("B", [1, 3, 8, 33])
+@pytest.mark.parametrize("mask", [1, 7, 6, 5])
+def test_forward_parity(small, B, mask):
+    c = small
+    x = I.history_batch(c.w, range(10, 10 + B)) + 0.1 * I.uniform_batch(c.w, range(50, 50 + B))
+    sub = c.tab.select(_arm_orders(mask))
+    ref = O.apply_A(c.w, sub, x, c.scale)
+    xt = torch.from_numpy(x.astype(np.float32)).cuda()
+    y = c.op.apply_A(xt, arm_mask=mask)
+    torch.cuda.synchronize()
+    _cmp(y.cpu().numpy().astype(np.float64), ref, TOL32)
+    y64 = c.op.apply_A(torch.from_numpy(x).cuda(), arm_mask=mask)
+    _cmp(y64.cpu().numpy(), ref, TOL64)
+
+
+@pytest.mark.parametrize("B", [1, 8, 33])
+@pytest.mark.parametrize("mask", [1, 7, 6])
+def test_adjoint_parity(small, B, mask):
+    c = small
+    sub = c.tab.select(_arm_orders(mask))
+    y = I.noise((sub.n_rows, c.w.time.n_frames, B), 77 + B)
+    ref = O.apply_AT(c.w, sub, y, c.scale)
+    x = c.op.apply_AT(torch.from_numpy(y.astype(np.float32)).cuda(), arm_mask=mask)
+    _cmp(x.cpu().numpy().astype(np.float64), ref, TOL32 * 3)
+    x64 = c.op.apply_AT(torch.from_numpy(y).cuda(), arm_mask=mask)
+    _cmp(x64.cpu().numpy(), ref, TOL64)
+
+
+def test_dot_product_fp64(small):
+    c = small
+    x = torch.from_numpy(I.uniform_batch(c.w, [3, 4])).cuda()
+    y = torch.from_numpy(I.noise((c.tab.n_rows, c.w.time.n_frames, 2), 5)).cuda()
+    lhs = torch.sum(c.op.apply_A(x) * y).item()
+    rhs = torch.sum(x * c.op.apply_AT(y)).item()
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_deterministic_bitwise(small):
+    c = small
+    x = torch.from_numpy(I.uniform_batch(c.w, range(8)).astype(np.float32)).cuda()
+    y1 = c.op.apply_A(x)
+    y2 = c.op.apply_A(x)
+    assert torch.equal(y1, y2)
+    g1 = c.op.apply_AT(y1)
+    g2 = c.op.apply_AT(y2)
+    assert torch.equal(g1, g2)
+
+
+def test_direct_zero_columns_bit_exact(schw):
+    """Theorem 4.1: columns the oracle finds exactly zero in the direct block
+    are exactly zero on the GPU (FP32 and FP64 paths), and vice versa."""
+    c = schw
+    n = c.w.n_dof
+    D0 = O.dense_A(c.w, c.tab.select((0,)), c.scale)
+    ref_zero = np.all(D0 == 0.0, axis=0)
+    assert ref_zero.sum() > 0
+    E = torch.eye(n, dtype=torch.float64).reshape(c.w.grid.n_nodes, c.w.time.n_hats, n).cuda()
+    for dt in (torch.float32, torch.float64):
+        M = c.op.apply_A(E.to(dt).contiguous(), arm_mask=1).reshape(-1, n).cpu().numpy()
+        gpu_zero = np.all(M == 0.0, axis=0)
+        assert np.array_equal(gpu_zero, ref_zero)
+        _cmp(M.astype(np.float64), D0, TOL32 if dt == torch.float32 else TOL64)
+
+
+def test_empty_arm_and_errors(schw):
+    c = schw
+    assert c.op.arm_rows(4) == 0  # no n=2 rows at 32x32
+    x = torch.ones((c.w.grid.n_nodes, c.w.time.n_hats, 2), device="cuda")
+    y = c.op.apply_A(x, arm_mask=4)
+    assert y.shape[0] == 0
+    g = c.op.apply_AT(y, arm_mask=4)
+    assert torch.count_nonzero(g).item() == 0
+    with pytest.raises(rtt.RttError):
+        c.op._launch("rtt_apply_A", x, x, 0, 7, None)
+    with pytest.raises(rtt.RttError):
+        c.op._launch("rtt_apply_A", x, x, 2, 0, None)
+
+
+def test_autograd_backward_is_adjoint_and_matches_fd(small):
+    """forward A / backward A^T as a torch.autograd.Function; the gradient of
+    L(x) = 1/2 ||A x - d||^2 matches the oracle's A^T (A x - d) and central
+    finite differences in FP64 (step 1e-3)."""
+    c = small
+    B = 2
+    xt = I.history_batch(c.w, [21, 22])
+    d = O.apply_A(c.w, c.tab, xt, c.scale) + I.noise((c.tab.n_rows, c.w.time.n_frames, B), 23)
+    x0 = I.history_batch(c.w, [31, 32])
+    x = torch.from_numpy(x0.astype(np.float32)).cuda().requires_grad_(True)
+    yd = torch.from_numpy(d.astype(np.float32)).cuda()
+    loss = 0.5 * torch.sum((rtt.apply_A_autograd(x, c.op) - yd) ** 2)
+    loss.backward()
+    g = x.grad.cpu().numpy().astype(np.float64)
+    ref = O.apply_AT(c.w, c.tab, O.apply_A(c.w, c.tab, x0, c.scale) - d, c.scale)
+    err = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+    assert err < 1e-4  # FP32 residual of a large data vector
+    h = 1e-3
+    for k in range(4):
+        v = I.noise(x0.shape, 100 + k)
+        Lp = 0.5 * np.sum((O.apply_A(c.w, c.tab, x0 + h * v, c.scale) - d) ** 2)
+        Lm = 0.5 * np.sum((O.apply_A(c.w, c.tab, x0 - h * v, c.scale) - d) ** 2)
+        fd = (Lp - Lm) / (2 * h)
+        assert np.sum(g * v) == pytest.approx(fd, rel=1e-4)
+
+
+def test_gpu_tracer_matches_oracle():
+    """rtt_trace_rays (RK4 on the GPU) vs the oracle's DP5 integrator."""
+    w = I.small_kerr(spin=0.94, incl_deg=75.0, nx=64, ss=2)
+    s = I.screen_samples(w)
+    ref = O.build_table(w, s)
+    got = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, s)
+    key_r = {(int(o), int(p), int(q)) for o, p, q in zip(ref.order, ref.pixel, ref.sample)}
+    assert abs(len(got["r"]) - ref.n_rays) <= max(3, ref.n_rays // 2000)
+    # match entries by (order, pixel) and radius (sub-rays of one pixel)
+    assert len(key_r) == ref.n_rays
+    assert np.array_equal(np.sort(np.unique(got["order"])), np.sort(np.unique(ref.order)))
+    gk = np.lexsort((got["r"], got["pixel"], got["order"]))
+    rk = np.lexsort((ref.r, ref.pixel, ref.order))
+    if len(got["r"]) == ref.n_rays:
+        assert np.array_equal(got["pixel"][gk], ref.pixel[rk])
+        assert np.max(np.abs(got["r"][gk] - ref.r[rk])) < 1e-7
+        dphi = np.angle(np.exp(1j * (got["phi"][gk] - ref.phi[rk])))
+        assert np.max(np.abs(dphi)) < 1e-7
+        assert np.max(np.abs(got["delay"][gk] - ref.delay[rk])) < 1e-6
+        assert np.allclose(got["weight"][gk], ref.weight[rk], rtol=1e-7)
