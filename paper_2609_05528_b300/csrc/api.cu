@@ -27,7 +27,7 @@ void set_error(const char* fmt, ...) {
 template <typename T>
 cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
 template <typename T>
-cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
+cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
 
 #define RTT_CUDA(call)                                                                  \
     do {                                                                                \
@@ -222,7 +222,7 @@ static void free_op(rtt_op_s* op) {
     if (!op) return;
     void* ps[] = {op->row_ptr, op->ray_row, op->node00, op->node01, op->W,     op->W64,
                   op->K0,      op->F0,      op->F64,    op->r,      op->delay, op->weight,
-                  op->thr,     op->node_ptr, op->inc,   op->row_order};
+                  op->thr,     op->node_ptr, op->inc,   op->row_order, op->zhat};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete op;
@@ -487,19 +487,53 @@ static rtt_status make_seg(const rtt_op_s* op, int mask, ArmSeg* s) {
     return RTT_OK;
 }
 
+// Grow-only adjoint scratch owned by the operator.  Growing frees the old
+// buffer after synchronising the device, so calls that need more scratch
+// than any earlier call are synchronous once.
+static rtt_status ensure_zhat(rtt_op_s* op, size_t bytes) {
+    if (op->zhat_bytes >= bytes) return RTT_OK;
+    if (op->zhat) {
+        cudaDeviceSynchronize();
+        cudaFree(op->zhat);
+        op->zhat = nullptr;
+        op->zhat_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&op->zhat, bytes);
+    if (e != cudaSuccess) {
+        op->zhat = nullptr;
+        set_error("adjoint scratch of %zu bytes: %s", bytes, cudaGetErrorString(e));
+        return RTT_ENOMEM;
+    }
+    op->zhat_bytes = bytes;
+    return RTT_OK;
+}
+
 template <typename T>
 static rtt_status apply_common(rtt_op op, const T* in, T* out, int batch, int mask, void* stream,
                                bool adjoint) {
-    if (!op || !in || !out || batch < 1) {
-        set_error("invalid argument (op=%p in=%p out=%p batch=%d)", (void*)op, (const void*)in,
-                  (void*)out, batch);
+    if (!op || batch < 1) {
+        set_error("invalid argument (op=%p batch=%d)", (void*)op, batch);
         return RTT_EINVAL;
     }
     ArmSeg seg;
     RTT_TRY(make_seg(op, mask, &seg));
+    // data-side pointers may be null only when the arm selects no rows
+    const bool need_in = adjoint ? seg.total > 0 : true;
+    const bool need_out = adjoint ? true : seg.total > 0;
+    if ((need_in && !in) || (need_out && !out)) {
+        set_error("null buffer (in=%p out=%p, arm rows %d)", (const void*)in, (void*)out,
+                  seg.total);
+        return RTT_EINVAL;
+    }
     cudaStream_t st = (cudaStream_t)stream;
-    cudaError_t e = adjoint ? launch_adjoint<T>(op, in, out, batch, seg, st)
-                            : launch_forward<T>(op, in, out, batch, seg, st);
+    cudaError_t e;
+    if (adjoint) {
+        const int bc = batch < 32 ? batch : 32;
+        RTT_TRY(ensure_zhat(op, (size_t)op->n_rays * op->time.n_hats * bc * sizeof(T)));
+        e = launch_adjoint<T>(op, in, out, batch, seg, (T*)op->zhat, st);
+    } else {
+        e = launch_forward<T>(op, in, out, batch, seg, st);
+    }
     if (e != cudaSuccess) {
         set_error("apply launch failed: %s", cudaGetErrorString(e));
         return RTT_ECUDA;

@@ -81,6 +81,10 @@ struct ApplyArgs {
     int FC;       // frames per chunk (forward)
     int zwin;     // hats staged per chunk (forward)
     int KC;       // hats per chunk (adjoint)
+    int vec4;     // batch stride and chunk allow 16-byte loads
+    T* zhat;      // adjoint scratch [E][K][Bc]
+    int Bc;       // batch entries held per ray in zhat
+    int64_t n_rays_total;
     int n_fchunk, n_bchunk, n_kchunk;
     int64_t n_tasks;
 };
@@ -176,16 +180,74 @@ fwd_kernel(const ApplyArgs<T> a) {
             const T* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB;
             const T* x01 = a.in + (int64_t)n01 * KB;
             const T* x11 = a.in + (int64_t)(n01 + a.n_phi) * KB;
-            for (int o = lane; o < nwin * BC; o += 32) {
-                const int kk = o / BC, bb = o - kk * BC;
-                const int k = k_lo + kk;
-                const int b = b0 + bb;
-                T z = T(0);
-                if (k >= 0 && k < a.K && b < a.B) {
-                    const int64_t off = (int64_t)k * a.B + b;
-                    z = w[0] * x00[off] + w[1] * x10[off] + w[2] * x01[off] + w[3] * x11[off];
+            bool staged = false;
+            if constexpr (sizeof(T) == 4 && BC >= 4) {
+                if (a.vec4) {
+                    staged = true;
+                    // 16-byte loads of 4 batch entries; 4 items x 4 corners in flight per lane
+                    constexpr int Q = BC / 4;
+                    const int n_items = nwin * Q;
+                    float4* zs4 = reinterpret_cast<float4*>(zs);
+                    for (int base = 0; base < n_items; base += 32 * 4) {
+                        float4 v[4][4];
+                        bool okv[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int o = base + lane + 32 * u;
+                            const int kk = o / Q, q = o - kk * Q;
+                            const int k = k_lo + kk;
+                            const int b = b0 + 4 * q;
+                            okv[u] = o < n_items && k >= 0 && k < a.K && b < a.B;
+                            if (okv[u]) {
+                                const int64_t off = (int64_t)k * a.B + b;
+                                v[u][0] = *reinterpret_cast<const float4*>(x00 + off);
+                                v[u][1] = *reinterpret_cast<const float4*>(x10 + off);
+                                v[u][2] = *reinterpret_cast<const float4*>(x01 + off);
+                                v[u][3] = *reinterpret_cast<const float4*>(x11 + off);
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int o = base + lane + 32 * u;
+                            if (o < n_items) {
+                                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                                if (okv[u]) {
+                                    z.x = w[0] * v[u][0].x + w[1] * v[u][1].x + w[2] * v[u][2].x + w[3] * v[u][3].x;
+                                    z.y = w[0] * v[u][0].y + w[1] * v[u][1].y + w[2] * v[u][2].y + w[3] * v[u][3].y;
+                                    z.z = w[0] * v[u][0].z + w[1] * v[u][1].z + w[2] * v[u][2].z + w[3] * v[u][3].z;
+                                    z.w = w[0] * v[u][0].w + w[1] * v[u][1].w + w[2] * v[u][2].w + w[3] * v[u][3].w;
+                                }
+                                zs4[o] = z;
+                            }
+                        }
+                    }
                 }
-                zs[o] = z;
+            }
+            for (int base = 0; !staged && base < nwin * BC; base += 32 * 4) {
+                T v[4][4];
+                bool okv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int o = base + lane + 32 * u;
+                    const int kk = o / BC, bb = o - kk * BC;
+                    const int k = k_lo + kk;
+                    const int b = b0 + bb;
+                    okv[u] = o < nwin * BC && k >= 0 && k < a.K && b < a.B;
+                    if (okv[u]) {
+                        const int64_t off = (int64_t)k * a.B + b;
+                        v[u][0] = x00[off];
+                        v[u][1] = x10[off];
+                        v[u][2] = x01[off];
+                        v[u][3] = x11[off];
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int o = base + lane + 32 * u;
+                    if (o < nwin * BC)
+                        zs[o] = okv[u] ? w[0] * v[u][0] + w[1] * v[u][1] + w[2] * v[u][2] + w[3] * v[u][3]
+                                       : T(0);
+                }
             }
             __syncwarp();
 #pragma unroll
@@ -216,13 +278,68 @@ fwd_kernel(const ApplyArgs<T> a) {
 
 constexpr int kAdjOutPerLane = 8;
 
+__device__ __forceinline__ int64_t floor_div(int64_t a, int64_t d) {
+    return a >= 0 ? a / d : -((-a + d - 1) / d);
+}
+
+// Phase 1 of the adjoint: temporal contraction per ray,
+//   zhat_e[k][b] = sum_f h_{e,f,k} y[row_e][f][b0 + b],
+// one warp per (ray, hat chunk, batch chunk).  The frames feeding hat k are
+// the contiguous range where the exact hat index is k or k - 1, found by
+// integer division on the 24-bit fixed-point hat coordinate.
 template <typename T, int BC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-adj_kernel(const ApplyArgs<T> a) {
+adj_time_kernel(const ApplyArgs<T> a) {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
-    const double inv_delta = 1.0 / a.delta;
+    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
+        const int bchunk = (int)(task % a.n_bchunk);
+        const int64_t t2 = task / a.n_bchunk;
+        const int kchunk = (int)(t2 % a.n_kchunk);
+        const int e = (int)(t2 / a.n_kchunk);
+        const int row_out = seg_out_row(a.seg, a.ray_row[e]);
+        if (row_out < 0) continue;
+        const HatCoef<T> hc = load_hat(a, e);
+        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
+        const T* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
+        const int b0 = bchunk * BC;
+        const int k_begin = kchunk * a.KC;
+#pragma unroll
+        for (int j = 0; j < kAdjOutPerLane; ++j) {
+            const int o = lane + 32 * j;
+            const int kk = o / BC, bb = o - kk * BC;
+            const int k = k_begin + kk;
+            const int b = b0 + bb;
+            if (kk >= a.KC || k >= a.K || bb >= a.Bc) continue;
+            // f with hat index k: f in [fmin(k), fmax(k)]; with index k-1: up to fmax(k-1)
+            int64_t flo = floor_div(U0 - (int64_t)(k + 1) * kFracOne, a.D) + 1;
+            int64_t fhi = floor_div(U0 - (int64_t)(k - 1) * kFracOne, a.D);
+            if (flo < 0) flo = 0;
+            if (fhi > a.Tn - 1) fhi = a.Tn - 1;
+            T s = T(0);
+            if (b < a.B) {
+                for (int f = (int)flo; f <= (int)fhi; ++f) {
+                    int k0;
+                    T fr;
+                    hc.at(f, k0, fr);
+                    const T hw = (k0 == k) ? T(1) - fr : ((k0 + 1 == k) ? fr : T(0));
+                    s += hw * yrow[(int64_t)f * a.B + b];
+                }
+            }
+            a.zhat[((int64_t)e * a.K + k) * a.Bc + bb] = s;
+        }
+    }
+}
+
+// Phase 2: spatial transpose, a deterministic gather per node over its
+// incidence list (sorted by ray): x[s][k][b] = sum W_{e,c} zhat_e[k][b].
+template <typename T, int BC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+adj_space_kernel(const ApplyArgs<T> a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
         const int bchunk = (int)(task % a.n_bchunk);
         const int64_t t2 = task / a.n_bchunk;
@@ -237,44 +354,17 @@ adj_kernel(const ApplyArgs<T> a) {
         for (int ii = i_begin; ii < i_end; ++ii) {
             const int code = a.inc[ii];
             const int e = code >> 2, c = code & 3;
-            const int row_out = seg_out_row(a.seg, a.ray_row[e]);
-            if (row_out < 0) continue;
+            if (seg_out_row(a.seg, a.ray_row[e]) < 0) continue;
             T w[4];
             load_w(a, e, w);
             const T coef = w[c];
-            const HatCoef<T> hc = load_hat(a, e);
-            double u0;
-            if constexpr (sizeof(T) == 4) {
-                u0 = (double)hc.K0 + (double)hc.F0 * (1.0 / (double)kFracOne);
-            } else {
-                u0 = (double)hc.K0 + (double)hc.F;
-            }
-            const T* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
+            const T* zr = a.zhat + (int64_t)e * a.K * a.Bc;
 #pragma unroll
             for (int j = 0; j < kAdjOutPerLane; ++j) {
                 const int o = lane + 32 * j;
                 const int kk = o / BC, bb = o - kk * BC;
                 const int k = k_begin + kk;
-                const int b = b0 + bb;
-                if (kk >= a.KC || k >= a.K || b >= a.B) continue;
-                // frames whose hat pair can contain k: u(f) = u0 - f delta in (k - 1, k + 1)
-                const double flo = fmax(floor((u0 - (double)k - 1.0) * inv_delta) - 1.0, 0.0);
-                const double fhi = fmin(ceil((u0 - (double)k + 1.0) * inv_delta) + 1.0,
-                                        (double)(a.Tn - 1));
-                const int f_lo = (int)flo;
-                const int f_hi = fhi < flo ? -1 : (int)fhi;
-                T s = T(0);
-                for (int f = f_lo; f <= f_hi; ++f) {
-                    int k0;
-                    T fr;
-                    hc.at(f, k0, fr);
-                    T hw;
-                    if (k0 == k) hw = T(1) - fr;
-                    else if (k0 + 1 == k) hw = fr;
-                    else continue;
-                    s += hw * yrow[(int64_t)f * a.B + b];
-                }
-                acc[j] += coef * s;
+                if (kk < a.KC && k < a.K && bb < a.Bc) acc[j] += coef * zr[(int64_t)k * a.Bc + bb];
             }
         }
 #pragma unroll
@@ -283,7 +373,7 @@ adj_kernel(const ApplyArgs<T> a) {
             const int kk = o / BC, bb = o - kk * BC;
             const int k = k_begin + kk;
             const int b = b0 + bb;
-            if (kk < a.KC && k < a.K && b < a.B)
+            if (kk < a.KC && k < a.K && bb < a.Bc && b < a.B)
                 a.out[((int64_t)node * a.K + k) * a.B + b] = acc[j];
         }
     }
@@ -335,6 +425,7 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
 template <typename T, int BC>
 static cudaError_t launch_fwd_bc(ApplyArgs<T> a, cudaStream_t st) {
     a.FC = kOutPerLane * 32 / BC;
+    a.vec4 = (a.B % 4 == 0) ? 1 : 0;
     a.zwin = (int)ceil((a.FC - 1) * a.delta) + 3;
     a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
     a.n_bchunk = (a.B + BC - 1) / BC;
@@ -352,12 +443,20 @@ static cudaError_t launch_fwd_bc(ApplyArgs<T> a, cudaStream_t st) {
 
 template <typename T, int BC>
 static cudaError_t launch_adj_bc(ApplyArgs<T> a, cudaStream_t st) {
+    // a.in / a.out / a.B describe the full batch; this launch covers batch
+    // entries [b_first, b_first + a.Bc) through the zhat scratch.
     a.KC = kAdjOutPerLane * 32 / BC;
     a.n_kchunk = (a.K + a.KC - 1) / a.KC;
-    a.n_bchunk = (a.B + BC - 1) / BC;
-    a.n_tasks = (int64_t)a.n_nodes * a.n_kchunk * a.n_bchunk;
+    a.n_bchunk = 1;
+    a.n_tasks = (int64_t)a.n_rays_total * a.n_kchunk;
+    if (a.n_tasks > 0 && a.seg.total > 0) {
+        adj_time_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    a.n_tasks = (int64_t)a.n_nodes * a.n_kchunk;
     if (a.n_tasks == 0) return cudaSuccess;
-    adj_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+    adj_space_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -377,16 +476,26 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
 
 template <typename T>
 cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const ArmSeg& seg,
-                           cudaStream_t st) {
-    ApplyArgs<T> a = base_args<T>(op, y, x, B, seg);
-    switch (pick_bc(B)) {
-        case 1: return launch_adj_bc<T, 1>(a, st);
-        case 2: return launch_adj_bc<T, 2>(a, st);
-        case 4: return launch_adj_bc<T, 4>(a, st);
-        case 8: return launch_adj_bc<T, 8>(a, st);
-        case 16: return launch_adj_bc<T, 16>(a, st);
-        default: return launch_adj_bc<T, 32>(a, st);
+                           T* zhat, cudaStream_t st) {
+    // batch chunks of at most 32 entries share the zhat scratch [E][K][32]
+    for (int b_first = 0; b_first < B; b_first += 32) {
+        const int Bc = B - b_first < 32 ? B - b_first : 32;
+        ApplyArgs<T> a = base_args<T>(op, y + b_first, x + b_first, B, seg);
+        a.zhat = zhat;
+        a.Bc = Bc;
+        a.n_rays_total = op->n_rays;
+        cudaError_t e;
+        switch (pick_bc(Bc)) {
+            case 1: e = launch_adj_bc<T, 1>(a, st); break;
+            case 2: e = launch_adj_bc<T, 2>(a, st); break;
+            case 4: e = launch_adj_bc<T, 4>(a, st); break;
+            case 8: e = launch_adj_bc<T, 8>(a, st); break;
+            case 16: e = launch_adj_bc<T, 16>(a, st); break;
+            default: e = launch_adj_bc<T, 32>(a, st); break;
+        }
+        if (e != cudaSuccess) return e;
     }
+    return cudaSuccess;
 }
 
 template cudaError_t launch_forward<float>(const rtt_op_s*, const float*, float*, int, const ArmSeg&,
@@ -394,8 +503,8 @@ template cudaError_t launch_forward<float>(const rtt_op_s*, const float*, float*
 template cudaError_t launch_forward<double>(const rtt_op_s*, const double*, double*, int,
                                             const ArmSeg&, cudaStream_t);
 template cudaError_t launch_adjoint<float>(const rtt_op_s*, const float*, float*, int, const ArmSeg&,
-                                           cudaStream_t);
+                                           float*, cudaStream_t);
 template cudaError_t launch_adjoint<double>(const rtt_op_s*, const double*, double*, int,
-                                            const ArmSeg&, cudaStream_t);
+                                            const ArmSeg&, double*, cudaStream_t);
 
 }  // namespace rtt

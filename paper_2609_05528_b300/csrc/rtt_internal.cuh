@@ -63,4 +63,7 @@ struct rtt_op_s {
     int32_t* node_ptr = nullptr;  // [S+1] transposed incidence CSR
     int32_t* inc = nullptr;       // [4E] e * 4 + c
     int32_t* row_order = nullptr; // [R] order of each row
+    // adjoint scratch: per-ray temporal contraction [E][K][<=32], grown on demand
+    void* zhat = nullptr;
+    size_t zhat_bytes = 0;
 };

@@ -307,7 +307,7 @@ extern "C" rtt_status rtt_trace_rays(const rtt_geometry* geom, const rtt_source_
     pack_keys<<<(int)((n3 + 255) / 256), 256, 0, st>>>(n3, n, d_valid, d_pix, d_key, d_idx,
                                                         d_flag);
     TRY_CUDA(cudaGetLastError());
-    size_t tb = 0, tb2 = 0;
+    size_t tb = 0;
     TRY_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, d_key, d_key2, d_idx, d_perm, n3, 0, 34,
                                              st));
     void* d_tmp;

@@ -179,22 +179,32 @@ def test_autograd_backward_is_adjoint_and_matches_fd(small):
 
 
 def test_gpu_tracer_matches_oracle():
-    """rtt_trace_rays (RK4 on the GPU) vs the oracle's DP5 integrator."""
+    """rtt_trace_rays (RK4 on the GPU) vs the oracle's DP5 integrator: the same
+    valid (order, pixel) entries, and per entry r, phi, delay and weight."""
     w = I.small_kerr(spin=0.94, incl_deg=75.0, nx=64, ss=2)
     s = I.screen_samples(w)
     ref = O.build_table(w, s)
     got = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, s)
-    key_r = {(int(o), int(p), int(q)) for o, p, q in zip(ref.order, ref.pixel, ref.sample)}
-    assert abs(len(got["r"]) - ref.n_rays) <= max(3, ref.n_rays // 2000)
-    # match entries by (order, pixel) and radius (sub-rays of one pixel)
-    assert len(key_r) == ref.n_rays
-    assert np.array_equal(np.sort(np.unique(got["order"])), np.sort(np.unique(ref.order)))
-    gk = np.lexsort((got["r"], got["pixel"], got["order"]))
-    rk = np.lexsort((ref.r, ref.pixel, ref.order))
-    if len(got["r"]) == ref.n_rays:
-        assert np.array_equal(got["pixel"][gk], ref.pixel[rk])
-        assert np.max(np.abs(got["r"][gk] - ref.r[rk])) < 1e-7
-        dphi = np.angle(np.exp(1j * (got["phi"][gk] - ref.phi[rk])))
-        assert np.max(np.abs(dphi)) < 1e-7
-        assert np.max(np.abs(got["delay"][gk] - ref.delay[rk])) < 1e-6
-        assert np.allclose(got["weight"][gk], ref.weight[rk], rtol=1e-7)
+    # rays whose radius sits within 1e-6 M of r_in / r_out may flip validity
+    edge = (np.abs(ref.r - w.grid.r_in) < 1e-6) | (np.abs(ref.r - w.grid.r_out) < 1e-6)
+    assert abs(len(got["r"]) - ref.n_rays) <= int(edge.sum()) + 2
+    groups = {}
+    for i, key in enumerate(zip(ref.order.tolist(), ref.pixel.tolist())):
+        groups.setdefault(key, []).append(i)
+    n_match = 0
+    dr = dphi = ddel = dw = 0.0
+    for j, key in enumerate(zip(got["order"].tolist(), got["pixel"].tolist())):
+        cand = groups.get(key)
+        if not cand:
+            continue
+        # nearest oracle sub-ray of the same (order, pixel)
+        dist = [abs(ref.r[i] - got["r"][j]) + abs(np.angle(np.exp(1j * (ref.phi[i] - got["phi"][j]))))
+                for i in cand]
+        i = cand[int(np.argmin(dist))]
+        n_match += 1
+        dr = max(dr, abs(ref.r[i] - got["r"][j]))
+        dphi = max(dphi, abs(np.angle(np.exp(1j * (ref.phi[i] - got["phi"][j])))))
+        ddel = max(ddel, abs(ref.delay[i] - got["delay"][j]))
+        dw = max(dw, abs(ref.weight[i] / got["weight"][j] - 1.0))
+    assert n_match >= ref.n_rays - int(edge.sum()) - 2
+    assert dr < 1e-7 and dphi < 1e-7 and ddel < 1e-6 and dw < 1e-7, (dr, dphi, ddel, dw)
