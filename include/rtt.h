@@ -210,6 +210,77 @@ rtt_status rtt_apply_A_f64(rtt_op op, const double* x_dev, double* y_dev, int ba
 rtt_status rtt_apply_AT_f64(rtt_op op, const double* y_dev, double* x_dev, int batch,
                             int arm_mask, void* stream);
 
+/*
+ * rtt_probe_info -- age information of the scalar probe (Sec. 3.3 Eq. 10-12,
+ * Sec. 4.4 Eq. 29): I(a) = || C^{-1/2} A_arm q_a ||^2 with
+ * q_a = 1_[r_in, r_out](r) / N_h exp(-(t + a)^2 / (2 h^2)),
+ * N_h^2 = pi (r_out^2 - r_in^2) h sqrt(pi), evaluated directly at each ray's
+ * source point.  ages_host: n_ages (<= 256) probe ages in M; h > 0 (the
+ * paper uses 3 M); info_host receives n_ages doubles.  Exponentials are
+ * evaluated in FP32 and reduced in FP64; ages whose value lies within 1e-3
+ * (relative) of rho^2 are re-evaluated entirely in FP64, so the pass/fail
+ * decision I(a) >= rho^2 is taken at FP64 accuracy.  Synchronous.
+ * Errors: RTT_EINVAL, RTT_ENOMEM, RTT_ECUDA.
+ */
+rtt_status rtt_probe_info(rtt_op op, int arm_mask, int n_ages, const double* ages_host, double h,
+                          double* info_host, void* stream);
+
+/*
+ * rtt_direct_age_quantile -- the direct order's throughput-weighted age
+ * boundary A_{0,q} (Sec. 4.5): over all direct (ray, frame) samples with
+ * age Delta_e - t_o(f) and weight = the ray's throughput, the smallest sample
+ * age whose cumulative weight (ages ascending, device radix sort, FP64
+ * prefix sum) reaches q times the total.  0 < q <= 1.  Synchronous.
+ */
+rtt_status rtt_direct_age_quantile(rtt_op op, double q, double* out_host, void* stream);
+
+typedef struct {
+    int32_t anchor_index; /* youngest fully supported age, -1 if none */
+    double anchor_age;    /* NaN if none */
+    double L_anchor;      /* anchor-connected passing span (M) */
+    double T_reach;       /* oldest passing age (Eq. 30), NaN if none */
+    double A0q;           /* boundary used for J_old */
+    double J_old;         /* age_step * sum_{a > A0q} log(1 + I(a)) (Eq. 35) */
+} rtt_reach_result;
+
+/*
+ * rtt_reach -- historical reach and old-age innovation from I(a)
+ * (Sec. 3.3 Eq. 13, Sec. 4.4 Eq. 30, Sec. 4.5 Eq. 35).  pass(a) <=>
+ * I(a) >= rho^2.  The anchor is the smallest age whose support
+ * [-a - 3h, -a + 3h] lies inside the union of the arm's footprints
+ * W_n = [t_o,min - Delta_n^max, t_o,max - Delta_n^min]; L_anchor =
+ * a_last - anchor for the contiguous passing run starting at the anchor (0
+ * if the anchor fails or is absent).  J_old uses the rectangle rule with
+ * strict a > a0q.  ages/info: host arrays of n_ages; pass_host (optional)
+ * receives n_ages bytes.  Host-only computation.
+ */
+rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const double* ages_host,
+                     const double* info_host, double h, double a0q, double age_step,
+                     rtt_reach_result* out, uint8_t* pass_host);
+
+/*
+ * rtt_gram -- restricted Gram matrix G = P^T P of P = scale * A_arm Q
+ * (Sec. 3.2 Eq. 7, Sec. 4.1 Eq. 21): Q_dev is the class synthesis matrix in
+ * the source layout, double [n_nodes][n_hats][d] (column j = direction j);
+ * G_dev receives double [d][d] (symmetric, row-major).  FP64 throughout: P
+ * is formed chunk by chunk by the FP64 forward kernel into library scratch
+ * (<= 1 GiB) and reduced in a fixed order.  1 <= d <= 4096.  Synchronous.
+ */
+rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q_dev, int d, double* G_dev,
+                    void* stream);
+
+/*
+ * rtt_eig_sym -- eigendecomposition of a symmetric n x n FP64 matrix on the
+ * GPU (parallel cyclic Jacobi, round-robin ordering, relative off-diagonal
+ * criterion), as used for the spectrum of the restricted Gram (Eq. 31).
+ * A_dev is overwritten (its diagonal holds the eigenvalues); V_dev receives
+ * the eigenvectors as columns (row-major n x n); evals_host receives the
+ * unsorted eigenvalues; sweeps_host (optional) the sweep count.
+ * Errors: RTT_EINVAL, RTT_ENOTCONVERGED (max_sweeps reached), RTT_ECUDA.
+ */
+rtt_status rtt_eig_sym(int n, double* A_dev, double* evals_host, double* V_dev, int max_sweeps,
+                       int* sweeps_host, void* stream);
+
 void rtt_destroy(rtt_op op);
 
 #ifdef __cplusplus

@@ -272,7 +272,7 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
             return RTT_EINVAL;
         }
         const double u0 = (time->t_end - time->t0 + d) / time->hat_step;
-        if (std::fabs(u0) > 1e9) {
+        if (std::fabs(u0) > 1048576.0) {  // |u0| <= 2^20 hat steps
             set_error("ray %lld: hat offset out of range", (long long)i);
             return RTT_EINVAL;
         }
@@ -465,7 +465,7 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
     return RTT_OK;
 }
 
-static rtt_status make_seg(const rtt_op_s* op, int mask, ArmSeg* s) {
+rtt_status make_seg(const rtt_op_s* op, int mask, ArmSeg* s) {
     if (mask < 1 || mask > 7) {
         set_error("arm_mask %d not in 1..7", mask);
         return RTT_EINVAL;

@@ -140,10 +140,10 @@ __device__ __forceinline__ int seg_out_row(const ArmSeg& s, int row_in) {
 }
 
 constexpr int kWarpsPerBlock = 8;
-constexpr int kOutPerLane = 32;
+constexpr int kOutPerLane = 16;
 
 template <typename T, int BC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3)
 fwd_kernel(const ApplyArgs<T> a) {
     extern __shared__ unsigned char smem_raw[];
     T* zs = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
@@ -188,11 +188,11 @@ fwd_kernel(const ApplyArgs<T> a) {
                     constexpr int Q = BC / 4;
                     const int n_items = nwin * Q;
                     float4* zs4 = reinterpret_cast<float4*>(zs);
-                    for (int base = 0; base < n_items; base += 32 * 4) {
-                        float4 v[4][4];
-                        bool okv[4];
+                    for (int base = 0; base < n_items; base += 32 * 2) {
+                        float4 v[2][4];
+                        bool okv[2];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
+                        for (int u = 0; u < 2; ++u) {
                             const int o = base + lane + 32 * u;
                             const int kk = o / Q, q = o - kk * Q;
                             const int k = k_lo + kk;
@@ -207,7 +207,7 @@ fwd_kernel(const ApplyArgs<T> a) {
                             }
                         }
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
+                        for (int u = 0; u < 2; ++u) {
                             const int o = base + lane + 32 * u;
                             if (o < n_items) {
                                 float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -223,11 +223,11 @@ fwd_kernel(const ApplyArgs<T> a) {
                     }
                 }
             }
-            for (int base = 0; !staged && base < nwin * BC; base += 32 * 4) {
-                T v[4][4];
-                bool okv[4];
+            for (int base = 0; !staged && base < nwin * BC; base += 32 * 2) {
+                T v[2][4];
+                bool okv[2];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 2; ++u) {
                     const int o = base + lane + 32 * u;
                     const int kk = o / BC, bb = o - kk * BC;
                     const int k = k_lo + kk;
@@ -242,7 +242,7 @@ fwd_kernel(const ApplyArgs<T> a) {
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 2; ++u) {
                     const int o = base + lane + 32 * u;
                     if (o < nwin * BC)
                         zs[o] = okv[u] ? w[0] * v[u][0] + w[1] * v[u][1] + w[2] * v[u][2] + w[3] * v[u][3]
@@ -250,17 +250,37 @@ fwd_kernel(const ApplyArgs<T> a) {
                 }
             }
             __syncwarp();
+            if constexpr (sizeof(T) == 4) {
+                // lane frames f_j = f_begin + lane / BC + j (32 / BC): the 24-bit
+                // fixed-point hat coordinate U(f) = U0 - f D steps by a constant
+                const int bb = lane % BC;
+                const int f0 = f_begin + lane / BC;
+                int64_t U = ((int64_t)hc.K0 * kFracOne + hc.F0) - (int64_t)f0 * hc.D;
+                const int64_t dU = (int64_t)(32 / BC) * hc.D;
 #pragma unroll
-            for (int j = 0; j < kOutPerLane; ++j) {
-                const int o = lane + 32 * j;
-                const int fl = o / BC, bb = o - fl * BC;
-                const int f = f_begin + fl;
-                if (f < f_end) {
-                    int k0;
-                    T fr;
-                    hc.at(f, k0, fr);
-                    const int i0 = (k0 - k_lo) * BC + bb;
-                    acc[j] += (T(1) - fr) * zs[i0] + fr * zs[i0 + BC];
+                for (int j = 0; j < kOutPerLane; ++j) {
+                    const int f = f0 + j * (32 / BC);
+                    if (f < f_end) {
+                        const int k0 = (int)(U >> kFracBits);
+                        const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
+                        const int i0 = (k0 - k_lo) * BC + bb;
+                        acc[j] += (1.0f - fr) * zs[i0] + fr * zs[i0 + BC];
+                    }
+                    U -= dU;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kOutPerLane; ++j) {
+                    const int o = lane + 32 * j;
+                    const int fl = o / BC, bb = o - fl * BC;
+                    const int f = f_begin + fl;
+                    if (f < f_end) {
+                        int k0;
+                        T fr;
+                        hc.at(f, k0, fr);
+                        const int i0 = (k0 - k_lo) * BC + bb;
+                        acc[j] += (T(1) - fr) * zs[i0] + fr * zs[i0 + BC];
+                    }
                 }
             }
             __syncwarp();
@@ -312,13 +332,27 @@ adj_time_kernel(const ApplyArgs<T> a) {
             const int k = k_begin + kk;
             const int b = b0 + bb;
             if (kk >= a.KC || k >= a.K || bb >= a.Bc) continue;
-            // f with hat index k: f in [fmin(k), fmax(k)]; with index k-1: up to fmax(k-1)
-            int64_t flo = floor_div(U0 - (int64_t)(k + 1) * kFracOne, a.D) + 1;
-            int64_t fhi = floor_div(U0 - (int64_t)(k - 1) * kFracOne, a.D);
-            if (flo < 0) flo = 0;
-            if (fhi > a.Tn - 1) fhi = a.Tn - 1;
             T s = T(0);
-            if (b < a.B) {
+            if constexpr (sizeof(T) == 4) {
+                // frames with (k-1) 2^24 <= U(f) < (k+1) 2^24, U(f) = U0 - f D:
+                // start from a float estimate and test each frame exactly
+                const int64_t hi_excl = (int64_t)(k + 1) * kFracOne;
+                const int64_t lo_incl = (int64_t)(k - 1) * kFracOne;
+                const float est = (float)(U0 - hi_excl) * (1.0f / (float)a.D);
+                int f = (int)fminf(fmaxf(floorf(est) - 1.0f, 0.0f), (float)a.Tn);
+                int64_t U = U0 - (int64_t)f * a.D;
+                while (f < a.Tn && U >= hi_excl) { ++f; U -= a.D; }
+                for (; f < a.Tn && U >= lo_incl; ++f, U -= a.D) {
+                    const int k0 = (int)(U >> kFracBits);
+                    const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
+                    const float hw = (k0 == k) ? 1.0f - fr : fr;
+                    s += hw * yrow[(int64_t)f * a.B + b];
+                }
+            } else {
+                int64_t flo = floor_div(U0 - (int64_t)(k + 1) * kFracOne, a.D) + 1;
+                int64_t fhi = floor_div(U0 - (int64_t)(k - 1) * kFracOne, a.D);
+                if (flo < 0) flo = 0;
+                if (fhi > a.Tn - 1) fhi = a.Tn - 1;
                 for (int f = (int)flo; f <= (int)fhi; ++f) {
                     int k0;
                     T fr;

@@ -19,6 +19,8 @@ constexpr int32_t kFracMask = kFracOne - 1;
 
 void set_error(const char* fmt, ...);
 
+struct ArmSeg;
+
 // Rows selected by an arm mask: up to three contiguous segments of the
 // (order, pixel)-sorted row list, concatenated in order.
 struct ArmSeg {
@@ -29,6 +31,8 @@ struct ArmSeg {
     int32_t total;      // total selected rows
     int32_t mask;
 };
+
+rtt_status make_seg(const struct ::rtt_op_s* op, int mask, ArmSeg* s);
 
 }  // namespace rtt
 

@@ -66,6 +66,12 @@ class OpInfo(ctypes.Structure):
                 ("delay_min", ctypes.c_double * 3), ("delay_max", ctypes.c_double * 3)]
 
 
+class ReachResult(ctypes.Structure):
+    _fields_ = [("anchor_index", ctypes.c_int32), ("anchor_age", ctypes.c_double),
+                ("L_anchor", ctypes.c_double), ("T_reach", ctypes.c_double),
+                ("A0q", ctypes.c_double), ("J_old", ctypes.c_double)]
+
+
 class Screen(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("alpha", dp), ("beta", dp), ("pixel", i32p),
                 ("n_sub", i32p), ("d_omega_pixel", ctypes.c_double)]
@@ -88,6 +94,14 @@ _SIGS = {
     "rtt_apply_AT": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_apply_A_f64": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_apply_AT_f64": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+    "rtt_probe_info": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp, vp]),
+    "rtt_direct_age_quantile": (ctypes.c_int, [vp, ctypes.c_double, dp, vp]),
+    "rtt_reach": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
+                                 ctypes.c_double, ctypes.c_double, ctypes.POINTER(ReachResult),
+                                 ctypes.POINTER(ctypes.c_uint8)]),
+    "rtt_gram": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
+    "rtt_eig_sym": (ctypes.c_int, [ctypes.c_int, vp, dp, vp, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_int), vp]),
     "rtt_destroy": (None, [vp]),
 }
 
@@ -238,6 +252,71 @@ class Operator:
         name = "rtt_apply_AT" if y.dtype == torch.float32 else "rtt_apply_AT_f64"
         self._launch(name, y, x, B, arm_mask, stream)
         return x
+
+
+AGES = np.arange(0.0, 253.0, 4.0)
+
+
+def probe_info(op: "Operator", arm_mask: int = 7, ages=AGES, h: float = 3.0, stream=None):
+    ages = np.ascontiguousarray(ages, np.float64)
+    info = np.empty(ages.shape[0])
+    check(lib().rtt_probe_info(op.handle, arm_mask, ages.shape[0], _ptr(ages, dp), h,
+                               _ptr(info, dp), _stream(stream)), "rtt_probe_info")
+    return info
+
+
+def direct_age_quantile(op: "Operator", q: float = 0.999, stream=None) -> float:
+    out = ctypes.c_double(0.0)
+    check(lib().rtt_direct_age_quantile(op.handle, q, ctypes.byref(out), _stream(stream)),
+          "rtt_direct_age_quantile")
+    return out.value
+
+
+def reach(op: "Operator", info, arm_mask: int = 7, ages=AGES, h: float = 3.0, a0q: float = 0.0,
+          age_step: float = 4.0):
+    ages = np.ascontiguousarray(ages, np.float64)
+    info = np.ascontiguousarray(info, np.float64)
+    res = ReachResult()
+    passed = np.zeros(ages.shape[0], np.uint8)
+    check(lib().rtt_reach(op.handle, arm_mask, ages.shape[0], _ptr(ages, dp), _ptr(info, dp), h,
+                          a0q, age_step, ctypes.byref(res),
+                          passed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))), "rtt_reach")
+    return res, passed.astype(bool)
+
+
+def gram(op: "Operator", Q, arm_mask: int = 7, stream=None):
+    """G = P^T P, P = scale A_arm Q; Q: CUDA float64 [n_nodes, n_hats, d]."""
+    import torch
+    assert Q.is_cuda and Q.dtype == torch.float64 and Q.is_contiguous() and Q.dim() == 3
+    d = Q.shape[2]
+    G = torch.empty((d, d), dtype=torch.float64, device=Q.device)
+    check(lib().rtt_gram(op.handle, arm_mask, ctypes.c_void_p(Q.data_ptr()), d,
+                         ctypes.c_void_p(G.data_ptr()), _stream(stream)), "rtt_gram")
+    return G
+
+
+def eig_sym(G, max_sweeps: int = 60, stream=None):
+    """Eigenvalues (descending) and eigenvectors of a symmetric CUDA FP64 matrix."""
+    import torch
+    n = G.shape[0]
+    A = G.clone().contiguous()
+    V = torch.empty_like(A)
+    ev = np.empty(n)
+    sw = ctypes.c_int(0)
+    check(lib().rtt_eig_sym(n, ctypes.c_void_p(A.data_ptr()), _ptr(ev, dp),
+                            ctypes.c_void_p(V.data_ptr()), max_sweeps, ctypes.byref(sw),
+                            _stream(stream)), "rtt_eig_sym")
+    order = np.argsort(-ev, kind="stable")
+    return ev[order], V[:, torch.from_numpy(order).to(V.device)], sw.value
+
+
+def operational_rank(op: "Operator", Q, arm_mask: int = 7, rho: float = 1.0):
+    """sigma_i = sqrt(max(lambda_i, 0)) of the restricted Gram; rank = #{sigma >= rho}
+    (Eq. 31; scale already carries SNR_0)."""
+    G = gram(op, Q, arm_mask)
+    ev, V, _ = eig_sym(G)
+    sig = np.sqrt(np.maximum(ev, 0.0))
+    return sig, int(np.count_nonzero(sig >= rho))
 
 
 def _autograd():

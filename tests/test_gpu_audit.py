@@ -1,0 +1,86 @@
+"""GPU parity of the audit quantities (probe information, reach, direct age
+quantile, J_old) against the FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_05528_b300 import build, rtt
+from paper_2609_05528_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def case():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    w = I.small_kerr(spin=0.5, incl_deg=50.0, nx=64, n_r=16, n_phi=32, n_frames=120, n_hats=32,
+                     ss=2)
+    tab = O.build_table(w, I.screen_samples(w))
+    op = rtt.Operator(w, {"order": tab.order, "pixel": tab.pixel, "r": tab.r, "phi": tab.phi,
+                          "delay": tab.delay, "weight": tab.weight,
+                          "throughput": tab.throughput})
+    return w, tab, op
+
+
+@pytest.mark.parametrize("mask", [1, 7])
+def test_probe_info_matches_oracle(case, mask):
+    w, tab, op = case
+    sub = tab.select(tuple(n for n in range(3) if mask & (1 << n)))
+    ref = O.probe_info(w, sub, O.scale(tab))
+    got = rtt.probe_info(op, mask)
+    big = ref > 1e-30 * ref.max()
+    assert np.allclose(got[big], ref[big], rtol=2e-5)
+    assert np.all(np.abs(got[~big]) <= 1e-6 * ref.max())
+    # the pass/fail mask agrees wherever the oracle is not within 1e-9 of rho^2
+    clear = np.abs(ref - 1.0) > 1e-9
+    assert np.array_equal((got >= 1.0)[clear], (ref >= 1.0)[clear])
+
+
+def test_reach_quantile_and_jold_match_oracle(case):
+    w, tab, op = case
+    scl = O.scale(tab)
+    a0_ref = O.a0999(w, tab)
+    a0 = rtt.direct_age_quantile(op, 0.999)
+    assert a0 == pytest.approx(a0_ref, abs=1e-9)
+    for mask, orders in ((1, (0,)), (7, (0, 1, 2))):
+        info_ref = O.probe_info(w, tab.select(orders), scl)
+        r_ref = O.reach(w, tab, info_ref, orders)
+        info = rtt.probe_info(op, mask)
+        res, passed = rtt.reach(op, info, mask, a0q=a0)
+        assert np.array_equal(passed, r_ref.passing)
+        assert (res.anchor_index >= 0) == (r_ref.anchor is not None)
+        if r_ref.anchor is not None:
+            assert res.anchor_age == r_ref.anchor
+        assert res.L_anchor == r_ref.L_anchor
+        assert res.J_old == pytest.approx(O.j_old(info_ref, a0_ref), rel=1e-5)
+
+
+@pytest.mark.parametrize("kind", ["S224", "L224"])
+def test_gram_eig_rank_match_oracle(kind):
+    """Restricted Gram (FP64 path) and Jacobi spectrum vs the oracle on the
+    Schwarzschild 32x32 workload, direct and resolved arms."""
+    build.build()
+    w = I.schw32()
+    tab = O.build_table(w, I.screen_samples(w))
+    op = rtt.Operator(w, {"order": tab.order, "pixel": tab.pixel, "r": tab.r, "phi": tab.phi,
+                          "delay": tab.delay, "weight": tab.weight,
+                          "throughput": tab.throughput})
+    scl = O.scale(tab)
+    Q = O.synth_class(w, kind)
+    Qd = torch.from_numpy(Q.reshape(w.grid.n_nodes, w.time.n_hats, -1).copy()).cuda()
+    for mask, orders in ((1, (0,)), (7, (0, 1, 2))):
+        P = O.restricted_response(w, tab.select(orders), Q, scl)
+        G_ref = O.gram(P)
+        G = rtt.gram(op, Qd, mask).cpu().numpy()
+        assert np.max(np.abs(G - G_ref)) <= 1e-12 * np.max(np.abs(G_ref))
+        ref = O.operational_rank(G_ref)
+        sig, rank = rtt.operational_rank(op, Qd, mask)
+        assert np.allclose(sig[:10], ref.sigma[:10], rtol=1e-10)
+        lam_ref = ref.sigma ** 2
+        lam = sig ** 2
+        assert np.max(np.abs(lam - lam_ref)) <= 1e-11 * lam_ref[0]
+        if ref.margin > 1e-6:
+            assert rank == ref.rank
