@@ -80,7 +80,8 @@ __global__ void gram_reduce(const double* partial, int n_splits, int n_tiles, co
     for (int e = threadIdx.x; e < kGT * kGT; e += blockDim.x) {
         const int r = e >> 5, c = e & 31;
         const int i = tj.x * kGT + r, j = tj.y * kGT + c;
-        if (i >= d || j >= d) continue;
+        // upper triangle only: each (i, j) and its mirror are owned by one thread
+        if (i >= d || j >= d || i > j) continue;
         double s = 0.0;
         for (int sp = 0; sp < n_splits; ++sp)
             s += partial[((int64_t)sp * n_tiles + tile) * (kGT * kGT) + e];
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
                                                       int* sweeps_out) {
     extern __shared__ unsigned char jsm[];
     int* perm = reinterpret_cast<int*>(jsm);                  // np2 players
-    double* cs = reinterpret_cast<double*>(perm + np2 + (np2 & 1));  // c, s per pair
+    double* cs = reinterpret_cast<double*>(perm + np2 + (np2 & 1));  // 6 values per pair
     __shared__ int rotated;
     __shared__ double floor_abs;
     const int tid = threadIdx.x, nt = blockDim.x;
@@ -125,7 +126,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
             for (int k = tid; k < half; k += nt) {
                 int p = perm[k], q = perm[np2 - 1 - k];
                 if (p > q) { const int t = p; p = q; q = t; }
-                double c = 1.0, s = 0.0;
+                double c = 1.0, s = 0.0, tt = 0.0, apq0 = 0.0, app0 = 0.0, aqq0 = 0.0;
                 if (q < n) {
                     const double apq = A[(int64_t)p * n + q];
                     const double app = A[(int64_t)p * n + p], aqq = A[(int64_t)q * n + q];
@@ -135,11 +136,19 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
                                          (fabs(theta) + sqrt(theta * theta + 1.0));
                         c = 1.0 / sqrt(t * t + 1.0);
                         s = t * c;
+                        tt = t;
+                        apq0 = apq;
+                        app0 = app;
+                        aqq0 = aqq;
                         rotated = 1;
                     }
                 }
-                cs[2 * k] = c;
-                cs[2 * k + 1] = s;
+                cs[6 * k] = c;
+                cs[6 * k + 1] = s;
+                cs[6 * k + 2] = tt;
+                cs[6 * k + 3] = apq0;
+                cs[6 * k + 4] = app0;
+                cs[6 * k + 5] = aqq0;
             }
             __syncthreads();
             // rows: A <- J^T A
@@ -148,7 +157,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
                 int p = perm[k], q = perm[np2 - 1 - k];
                 if (p > q) { const int t = p; p = q; q = t; }
                 if (q >= n) continue;
-                const double c = cs[2 * k], s = cs[2 * k + 1];
+                const double c = cs[6 * k], s = cs[6 * k + 1];
                 if (s == 0.0) continue;
                 const double ap = A[(int64_t)p * n + col], aq = A[(int64_t)q * n + col];
                 A[(int64_t)p * n + col] = c * ap - s * aq;
@@ -161,7 +170,7 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
                 int p = perm[k], q = perm[np2 - 1 - k];
                 if (p > q) { const int t = p; p = q; q = t; }
                 if (q >= n) continue;
-                const double c = cs[2 * k], s = cs[2 * k + 1];
+                const double c = cs[6 * k], s = cs[6 * k + 1];
                 if (s == 0.0) continue;
                 const double ap = A[(int64_t)row * n + p], aq = A[(int64_t)row * n + q];
                 A[(int64_t)row * n + p] = c * ap - s * aq;
@@ -169,6 +178,18 @@ __global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int 
                 const double vp = V[(int64_t)row * n + p], vq = V[(int64_t)row * n + q];
                 V[(int64_t)row * n + p] = c * vp - s * vq;
                 V[(int64_t)row * n + q] = s * vp + c * vq;
+            }
+            __syncthreads();
+            // the rotated 2x2 block exactly: a_pq = 0, a_pp -= t a_pq, a_qq += t a_pq
+            for (int k = tid; k < half; k += nt) {
+                int p = perm[k], q = perm[np2 - 1 - k];
+                if (p > q) { const int t = p; p = q; q = t; }
+                if (q >= n || cs[6 * k + 1] == 0.0) continue;
+                const double t = cs[6 * k + 2], apq = cs[6 * k + 3];
+                A[(int64_t)p * n + q] = 0.0;
+                A[(int64_t)q * n + p] = 0.0;
+                A[(int64_t)p * n + p] = cs[6 * k + 4] - t * apq;
+                A[(int64_t)q * n + q] = cs[6 * k + 5] + t * apq;
             }
             __syncthreads();
             // round-robin: keep player 0, rotate the others by one
@@ -266,7 +287,7 @@ extern "C" rtt_status rtt_eig_sym(int n, double* A, double* evals_host, double* 
     const int np2 = n + (n & 1);
     int* d_sw = nullptr;
     cudaError_t e = cudaMalloc(&d_sw, 4);
-    const size_t smem = (size_t)(np2 + 2) * 4 + (size_t)np2 * 8 + 16;
+    const size_t smem = (size_t)(np2 + 2) * 4 + (size_t)(np2 / 2) * 6 * 8 + 16;
     if (e == cudaSuccess && smem > 48 * 1024)
         e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {

@@ -5,9 +5,9 @@
 // with the regular variables s = 1/r and u = cos(theta):
 //   (ds/dl)^2 = s^4 R(1/s),  (du/dl)^2 = eta - (eta + lam^2 - a^2) u^2 - a^2 u^4,
 // written in second-order form (no sign flips at turning points), starting
-// exactly at the observer (s = 0).  Classic RK4 with a per-ray step scaled
-// by the ray's fastest rate; each sign change of u is refined by Newton
-// iterations on a partial RK4 step.  The travel time is carried with the
+// exactly at the observer (s = 0).  Classic RK4 with adaptive steps chosen by
+// step doubling (Richardson error estimate); each sign change of u is
+// refined by Newton iterations on a partial step.  The travel time is carried with the
 // divergent r + 2 ln r part removed analytically.
 #include <cuda_runtime.h>
 
@@ -86,6 +86,7 @@ struct TraceArgs {
     double r_isco, E_isco, L_isco;
     double sqrt_domega, domega;
     double step_scale;
+    double tol;
     // outputs, order-major [3][n]
     int32_t* valid;
     double* r;
@@ -133,25 +134,43 @@ __global__ void trace_kernel(const TraceArgs A) {
     c.c0 = (c.a * c.a - c.a * c.lam) * (c.a * c.a - c.a * c.lam) - c.a * c.a * c.K;
     c.m2 = c.eta + c.lam * c.lam - c.a * c.a;
     const double rate = sqrt(fmax(fmax(fabs(c.c2), fabs(c.m2)), c.K));
-    const double h = A.step_scale / (1.0 + rate);
+    double h = A.step_scale / (1.0 + rate);
     St y{0.0, 1.0, A.cos_i, be * A.sin_i, 0.0, 0.0};
     int n_cross = 0;
     for (int n = 0; n < 3; ++n) A.valid[n * A.n + i] = 0;
     A.status[i] = 0;
     const double inv_nsub = 1.0 / (double)A.n_sub[i];
+    // adaptive RK4 with step doubling: local error = (two half steps - one
+    // full step) / 15, relative to tol * (1 + |y|); the accepted state is the
+    // Richardson-extrapolated one
+    const double tol = A.tol;
     for (int step = 0; n_cross < 3; ++step) {
-        if (step > 400000) {
+        if (step > 200000) {
             A.status[i] = 1;
             break;
         }
-        const St yn = rk4(c, y, h);
+        const St full = rk4(c, y, h);
+        const St half = rk4(c, rk4(c, y, 0.5 * h), 0.5 * h);
+        const double e[6] = {half.s - full.s, half.vs - full.vs, half.u - full.u,
+                             half.vu - full.vu, half.ph - full.ph, half.Y - full.Y};
+        const double m[6] = {fmax(fabs(y.s), fabs(half.s)),   fmax(fabs(y.vs), fabs(half.vs)),
+                             fmax(fabs(y.u), fabs(half.u)),   fmax(fabs(y.vu), fabs(half.vu)),
+                             fmax(fabs(y.ph), fabs(half.ph)), fmax(fabs(y.Y), fabs(half.Y))};
+        double err = 0.0;
+        for (int q = 0; q < 6; ++q) err = fmax(err, fabs(e[q]) / (15.0 * tol * (1.0 + m[q])));
+        if (err > 1.0) {
+            h *= fmax(0.1, 0.9 * pow(err, -0.2));
+            continue;
+        }
+        const St yn{half.s + e[0] / 15.0, half.vs + e[1] / 15.0, half.u + e[2] / 15.0,
+                    half.vu + e[3] / 15.0, half.ph + e[4] / 15.0, half.Y + e[5] / 15.0};
         if ((y.u > 0.0 && yn.u <= 0.0) || (y.u < 0.0 && yn.u >= 0.0)) {
             double hc = h * y.u / (y.u - yn.u);
-            St yc = rk4(c, y, hc);
+            St yc = rk4(c, rk4(c, y, 0.5 * hc), 0.5 * hc);
             for (int it = 0; it < 8; ++it) {
                 const double dh = -yc.u / yc.vu;
                 hc += dh;
-                yc = rk4(c, y, hc);
+                yc = rk4(c, rk4(c, y, 0.5 * hc), 0.5 * hc);
                 if (fabs(dh) < 1e-15 * h) break;
             }
             if (!(yc.s > 0.0 && yc.s < A.s_cap)) break;
@@ -175,6 +194,7 @@ __global__ void trace_kernel(const TraceArgs A) {
         if (y.s >= A.s_cap) break;                  // captured
         if (y.vs < 0.0 && y.s < A.s_esc) break;     // outgoing beyond r_out
         if (y.s <= 0.0) break;                      // back at infinity
+        h *= fmin(4.0, fmax(0.1, 0.9 * pow(fmax(err, 1e-12), -0.2)));
     }
 }
 
@@ -293,6 +313,7 @@ extern "C" rtt_status rtt_trace_rays(const rtt_geometry* geom, const rtt_source_
     A.domega = scr->d_omega_pixel;
     A.sqrt_domega = std::sqrt(scr->d_omega_pixel);
     A.step_scale = 0.01;
+    A.tol = 1e-12;
     A.valid = d_valid;
     A.r = d_r;
     A.phi = d_phi;

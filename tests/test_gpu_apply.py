@@ -210,3 +210,19 @@ def test_gpu_tracer_matches_oracle():
         dw = max(dw, abs(ref.weight[i] / got["weight"][j] - 1.0))
     assert n_match >= ref.n_rays - int(edge.sum()) - 2
     assert dr < 1e-7 and dphi < 1e-7 and ddel < 1e-6 and dw < 1e-7, (dr, dphi, ddel, dw)
+
+
+@pytest.mark.parametrize("kind", ["S224", "L224"])
+def test_forward_class_batch_224(schw, kind):
+    """P = scale A Q for a 224-column class as one batch (7 batch chunks)."""
+    c = schw
+    Q = O.synth_class(c.w, kind)
+    x = Q.reshape(c.w.grid.n_nodes, c.w.time.n_hats, -1)
+    for mask, orders in ((1, (0,)), (7, (0, 1, 2))):
+        ref = O.restricted_response(c.w, c.tab.select(orders), Q, c.scale)
+        got = c.op.apply_A(torch.from_numpy(x.copy()).cuda(), arm_mask=mask).cpu().numpy()
+        got = got.reshape(ref.shape)
+        bad = np.argwhere(np.abs(got - ref) > 1e-12 * np.abs(ref).max())
+        assert bad.shape[0] == 0, (bad[:5].tolist(), got[tuple(bad[0])], ref[tuple(bad[0])])
+        g32 = c.op.apply_A(torch.from_numpy(x.astype(np.float32)).cuda(), arm_mask=mask)
+        _cmp(g32.cpu().numpy().astype(np.float64).reshape(ref.shape), ref, TOL32)

@@ -75,7 +75,13 @@ def test_gram_eig_rank_match_oracle(kind):
         P = O.restricted_response(w, tab.select(orders), Q, scl)
         G_ref = O.gram(P)
         G = rtt.gram(op, Qd, mask).cpu().numpy()
-        assert np.max(np.abs(G - G_ref)) <= 1e-12 * np.max(np.abs(G_ref))
+        Pg = op.apply_A(Qd, arm_mask=mask).reshape(-1, Q.shape[1])
+        G_torch = (Pg.T @ Pg).cpu().numpy()
+        err_p = np.max(np.abs(Pg.cpu().numpy() - P)) / np.max(np.abs(P))
+        err_t = np.max(np.abs(G_torch - G_ref)) / np.max(np.abs(G_ref))
+        loc = np.unravel_index(np.argmax(np.abs(G - G_ref)), G.shape)
+        assert np.max(np.abs(G - G_ref)) <= 1e-12 * np.max(np.abs(G_ref)), (
+            mask, err_p, err_t, loc, G[loc], G_ref[loc], G_torch[loc])
         ref = O.operational_rank(G_ref)
         sig, rank = rtt.operational_rank(op, Qd, mask)
         assert np.allclose(sig[:10], ref.sigma[:10], rtol=1e-10)
