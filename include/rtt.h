@@ -226,6 +226,31 @@ rtt_status rtt_probe_info(rtt_op op, int arm_mask, int n_ages, const double* age
                           double* info_host, void* stream);
 
 /*
+ * rtt_probe_info_noalloc -- the FP32 pass of rtt_probe_info for callers that
+ * must not allocate device memory while they run: for example an
+ * application whose pool allocator has reserved all free device memory up
+ * front, or a runtime that forbids allocation after initialisation.  The
+ * paper has no counterpart; this entry point only changes where the scratch
+ * lives.
+ * The per-block partial sums use a file-scope static device array of
+ * 1184 x 256 doubles (about 2.4 MB) that every GPU which loads the library
+ * holds until the process exits; no cudaMalloc / cudaFree (or allocating
+ * library routine) is called.  ages_dev (n_ages doubles) and info_dev
+ * (n_ages doubles, receives I(a)) are device memory owned by the caller;
+ * 0 <= n_ages <= 256, larger counts are rejected with RTT_EINVAL.  The call
+ * is asynchronous on `stream` and does not perform the FP64 re-evaluation of
+ * near-threshold ages that rtt_probe_info does.
+ * The first call on each device looks the array's device address up with
+ * cudaGetSymbolAddress (with that device current), so make that first call
+ * before any stream capture begins.  All calls share the one array and each
+ * call overwrites every entry it reads, so no clearing is needed; calls that
+ * overlap on the GPU (for example on two streams) race on it and must be
+ * serialised by the caller.
+ */
+rtt_status rtt_probe_info_noalloc(rtt_op op, int arm_mask, int n_ages, const double* ages_dev,
+                                  double h, double* info_dev, void* stream);
+
+/*
  * rtt_direct_age_quantile -- the direct order's throughput-weighted age
  * boundary A_{0,q} (Sec. 4.5): over all direct (ray, frame) samples with
  * age Delta_e - t_o(f) and weight = the ray's throughput, the smallest sample

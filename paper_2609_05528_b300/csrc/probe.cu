@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cub/cub.cuh>
+#include <mutex>
 #include <vector>
 
 #include "rtt_internal.cuh"
@@ -179,9 +180,99 @@ static rtt_status run_probe(const rtt_op_s* op, const ArmSeg& seg, int n_ages,
     return RTT_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free variant.  The per-block partial sums live in a file-scope
+// device array that every GPU loading the library holds until the process
+// exits; the host side only needs its device address, looked up once per
+// device.  Each launch overwrites every partial it later reads, so nothing
+// has to be cleared between calls, but two calls in flight at the same time
+// (on different streams) share the array and race.
+// ---------------------------------------------------------------------------
+constexpr int kStaticProbeAges = kMaxAges;
+static __device__ __align__(256) double g_probe_partial[kProbeBlocks * kStaticProbeAges];
+
+constexpr int kMaxDevices = 64;
+static double* g_probe_partial_addr[kMaxDevices];
+static std::mutex g_probe_partial_mu;
+
+static rtt_status static_partial_address(double** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error("cudaGetDevice: %s", cudaGetErrorString(e));
+        return RTT_ECUDA;
+    }
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("device %d beyond the %d devices the static scratch table covers", dev,
+                  kMaxDevices);
+        return RTT_EINVAL;
+    }
+    std::lock_guard<std::mutex> lock(g_probe_partial_mu);
+    if (!g_probe_partial_addr[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_probe_partial);
+        if (e != cudaSuccess || !ptr) {
+            set_error("cudaGetSymbolAddress(static probe scratch): %s", cudaGetErrorString(e));
+            return RTT_ECUDA;
+        }
+        g_probe_partial_addr[dev] = static_cast<double*>(ptr);
+    }
+    *out = g_probe_partial_addr[dev];
+    return RTT_OK;
+}
+
 }  // namespace rtt
 
 using namespace rtt;
+
+extern "C" rtt_status rtt_probe_info_noalloc(rtt_op op, int arm_mask, int n_ages,
+                                             const double* ages_dev, double h, double* info_dev,
+                                             void* stream) {
+    if (!op || !(h > 0.0) || n_ages < 0 || (n_ages > 0 && (!ages_dev || !info_dev))) {
+        set_error("invalid probe arguments (n_ages=%d, h=%g)", n_ages, h);
+        return RTT_EINVAL;
+    }
+    if (n_ages > kStaticProbeAges) {
+        set_error("rtt_probe_info_noalloc: %d ages exceed the static scratch limit of %d", n_ages,
+                  kStaticProbeAges);
+        return RTT_EINVAL;
+    }
+    ArmSeg seg;
+    rtt_status s = make_seg(op, arm_mask, &seg);
+    if (s != RTT_OK) return s;
+    if (n_ages == 0) return RTT_OK;
+    double* partial = nullptr;
+    s = static_partial_address(&partial);
+    if (s != RTT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    ProbeArgs p{};
+    p.row_ptr = op->row_ptr;
+    p.delay = op->delay;
+    p.weight = op->weight;
+    p.seg = seg;
+    p.Tn = op->time.n_frames;
+    p.t0 = op->time.t0;
+    p.cadence = op->time.cadence;
+    p.inv_2h2 = 1.0 / (2.0 * h * h);
+    const double Nh = std::sqrt(M_PI * (op->grid.r_out * op->grid.r_out -
+                                        op->grid.r_in * op->grid.r_in) * h * std::sqrt(M_PI));
+    p.inv_Nh = 1.0 / Nh;
+    p.n_ages = n_ages;
+    p.ages = ages_dev;
+    p.partial = partial;
+    probe_kernel<float><<<kProbeBlocks, kProbeThreads, 0, st>>>(p);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        probe_reduce<<<(n_ages + 127) / 128, 128, 0, st>>>(partial, kProbeBlocks, n_ages,
+                                                           op->scale * op->scale, info_dev);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        set_error("probe kernels failed: %s", cudaGetErrorString(e));
+        return RTT_ECUDA;
+    }
+    return RTT_OK;
+}
 
 extern "C" rtt_status rtt_probe_info(rtt_op op, int arm_mask, int n_ages, const double* ages,
                                      double h, double* info, void* stream) {

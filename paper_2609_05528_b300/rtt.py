@@ -95,6 +95,8 @@ _SIGS = {
     "rtt_apply_A_f64": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_apply_AT_f64": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_probe_info": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp, vp]),
+    "rtt_probe_info_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp,
+                                              ctypes.c_double, vp, vp]),
     "rtt_direct_age_quantile": (ctypes.c_int, [vp, ctypes.c_double, dp, vp]),
     "rtt_reach": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, dp, ctypes.c_double,
                                  ctypes.c_double, ctypes.c_double, ctypes.POINTER(ReachResult),
