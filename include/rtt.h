@@ -306,6 +306,41 @@ rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q_dev, int d, double*
 rtt_status rtt_eig_sym(int n, double* A_dev, double* evals_host, double* V_dev, int max_sweeps,
                        int* sweeps_host, void* stream);
 
+/*
+ * rtt_solve_ridge -- ridge / Tikhonov estimator (Sec. 9):
+ * (A^T A + lambda I) x = A^T d, with A the whitened operator of the arm, for
+ * n_rhs data columns and n_lambda values at once (output column
+ * c = rhs * n_lambda + l).  data_dev: float [arm_rows][n_frames][n_rhs];
+ * x_dev: float [n_nodes][n_hats][n_rhs * n_lambda] (overwritten; the
+ * starting guess is 0).  Batched conjugate gradients with FP32 vectors and
+ * applies, FP64 per-column dot products in a fixed order, and the residual
+ * recomputed in FP64 every refresh_every iterations.  A column stops when
+ * its recurrence residual falls below tol * ||A^T d||.  iters_out: host int
+ * (iterations run); relres_out: host double [n_rhs * n_lambda], the final
+ * FP64 relative residual of each column.  Synchronous.
+ * Errors: RTT_EINVAL, RTT_ENOMEM, RTT_ECUDA, RTT_ENOTCONVERGED (max_iter
+ * reached; x and relres_out still hold the last iterate's values).
+ */
+rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data_dev, int n_rhs,
+                           const double* lambdas_host, int n_lambda, int max_iter, double tol,
+                           int refresh_every, float* x_dev, int* iters_out, double* relres_out,
+                           void* stream);
+
+/*
+ * rtt_solve_tsvd -- truncated-SVD estimator in a representation class
+ * (Sec. 9): x = Q V_r L_r^{-1} V_r^T Q^T A^T d, where (V, L) are the
+ * eigenpairs of the restricted Gram G = P^T P (rtt_gram, rtt_eig_sym) sorted
+ * by descending eigenvalue and r = rank (the paper truncates at the
+ * operational rank).  Q_dev: double [n_nodes][n_hats][d]; V_dev: double
+ * [d][d] row-major, eigenvectors as columns; evals_host: d doubles, the first
+ * `rank` positive; data_dev: double [arm_rows][n_frames][n_rhs]; xhat_dev:
+ * double [n_nodes][n_hats][n_rhs].  FP64; the plain GEMMs use cuBLAS.
+ * Synchronous.  Errors: RTT_EINVAL, RTT_ENOMEM, RTT_ECUDA.
+ */
+rtt_status rtt_solve_tsvd(rtt_op op, int arm_mask, const double* Q_dev, int d, const double* V_dev,
+                          const double* evals_host, int rank, const double* data_dev, int n_rhs,
+                          double* xhat_dev, void* stream);
+
 void rtt_destroy(rtt_op op);
 
 #ifdef __cplusplus

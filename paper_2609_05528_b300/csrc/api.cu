@@ -490,7 +490,7 @@ rtt_status make_seg(const rtt_op_s* op, int mask, ArmSeg* s) {
 // Grow-only adjoint scratch owned by the operator.  Growing frees the old
 // buffer after synchronising the device, so calls that need more scratch
 // than any earlier call are synchronous once.
-static rtt_status ensure_zhat(rtt_op_s* op, size_t bytes) {
+rtt_status ensure_zhat_bytes(rtt_op_s* op, size_t bytes) {
     if (op->zhat_bytes >= bytes) return RTT_OK;
     if (op->zhat) {
         cudaDeviceSynchronize();
@@ -529,7 +529,7 @@ static rtt_status apply_common(rtt_op op, const T* in, T* out, int batch, int ma
     cudaError_t e;
     if (adjoint) {
         const int bc = batch < 32 ? batch : 32;
-        RTT_TRY(ensure_zhat(op, (size_t)op->n_rays * op->time.n_hats * bc * sizeof(T)));
+        RTT_TRY(ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * bc * sizeof(T)));
         e = launch_adjoint<T>(op, in, out, batch, seg, (T*)op->zhat, st);
     } else {
         e = launch_forward<T>(op, in, out, batch, seg, st);

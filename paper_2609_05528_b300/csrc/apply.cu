@@ -85,6 +85,7 @@ struct ApplyArgs {
     T* zhat;      // adjoint scratch [E][K][Bc]
     int Bc;       // batch entries held per ray in zhat
     int64_t n_rays_total;
+    int seg_rows_all;  // total rows of the operator (all orders)
     int n_fchunk, n_bchunk, n_kchunk;
     int64_t n_tasks;
 };
@@ -143,7 +144,7 @@ constexpr int kWarpsPerBlock = 8;
 constexpr int kOutPerLane = 16;
 
 template <typename T, int BC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 3)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
 fwd_kernel(const ApplyArgs<T> a) {
     extern __shared__ unsigned char smem_raw[];
     T* zs = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
@@ -319,7 +320,15 @@ adj_time_kernel(const ApplyArgs<T> a) {
         const int kchunk = (int)(t2 % a.n_kchunk);
         const int e = (int)(t2 / a.n_kchunk);
         const int row_out = seg_out_row(a.seg, a.ray_row[e]);
-        if (row_out < 0) continue;
+        if (row_out < 0) {
+            // rays outside the arm contribute nothing: their zhat rows are zero
+            const int k_begin = kchunk * a.KC;
+            for (int o = lane; o < a.KC * a.Bc; o += 32) {
+                const int kk = o / a.Bc, bb = o - kk * a.Bc;
+                if (k_begin + kk < a.K) a.zhat[((int64_t)e * a.K + k_begin + kk) * a.Bc + bb] = T(0);
+            }
+            continue;
+        }
         const HatCoef<T> hc = load_hat(a, e);
         const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
         const T* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
@@ -413,6 +422,312 @@ adj_space_kernel(const ApplyArgs<T> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP32 fast path.  Forward: lane per frame, each lane carries all BC batch
+// entries of its frames, so the exact hat index / fraction of a (ray, frame)
+// is computed once and the staged z rows are read as 16-byte vectors.
+// ---------------------------------------------------------------------------
+template <int BC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
+fwd3_kernel(const ApplyArgs<float> a) {
+    constexpr int FPL = BC >= 32 ? 1 : 32 / BC;  // frames per lane
+    constexpr int FC = 32 * FPL;                 // frames per task
+    extern __shared__ float smem3[];
+    float* zs = smem3 + (threadIdx.x >> 5) * (a.zwin * BC);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const bool vec = (BC >= 4) && a.vec4;
+    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
+        const int bchunk = (int)(task % a.n_bchunk);
+        const int64_t t2 = task / a.n_bchunk;
+        const int fchunk = (int)(t2 % a.n_fchunk);
+        const int row_out = (int)(t2 / a.n_fchunk);
+        const int row = seg_in_row(a.seg, row_out);
+        const int f_begin = fchunk * FC;
+        const int f_end = min(a.Tn, f_begin + FC);
+        const int b0 = bchunk * BC;
+        const int nb = min(BC, a.B - b0);
+        float acc[FPL][BC];
+#pragma unroll
+        for (int j = 0; j < FPL; ++j)
+#pragma unroll
+            for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+        const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
+        for (int e = e_begin; e < e_end; ++e) {
+            const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
+            const int k_top = (int)((U0 - (int64_t)f_begin * a.D) >> kFracBits);
+            const int k_lo = (int)((U0 - (int64_t)(f_end - 1) * a.D) >> kFracBits);
+            const int nwin = k_top + 2 - k_lo;
+            const float4 wv = a.W[e];
+            const int n00 = a.node00[e], n01 = a.node01[e];
+            const int64_t KB = (int64_t)a.K * a.B;
+            const float* x00 = a.in + (int64_t)n00 * KB + b0;
+            const float* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB + b0;
+            const float* x01 = a.in + (int64_t)n01 * KB + b0;
+            const float* x11 = a.in + (int64_t)(n01 + a.n_phi) * KB + b0;
+            if (vec && nb == BC) {
+                constexpr int Q = BC / 4 > 0 ? BC / 4 : 1;
+                float4* zs4 = reinterpret_cast<float4*>(zs);
+                const int n_items = nwin * Q;
+                for (int base = 0; base < n_items; base += 64) {
+                    float4 v[2][4];
+                    bool okv[2];
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int o = base + lane + 32 * u;
+                        const int kk = o / Q, q = o - kk * Q;
+                        const int k = k_lo + kk;
+                        okv[u] = o < n_items && k >= 0 && k < a.K;
+                        if (okv[u]) {
+                            const int64_t off = (int64_t)k * a.B + 4 * q;
+                            v[u][0] = __ldg(reinterpret_cast<const float4*>(x00 + off));
+                            v[u][1] = __ldg(reinterpret_cast<const float4*>(x10 + off));
+                            v[u][2] = __ldg(reinterpret_cast<const float4*>(x01 + off));
+                            v[u][3] = __ldg(reinterpret_cast<const float4*>(x11 + off));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 2; ++u) {
+                        const int o = base + lane + 32 * u;
+                        if (o < n_items) {
+                            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                            if (okv[u]) {
+                                z.x = wv.x * v[u][0].x + wv.y * v[u][1].x + wv.z * v[u][2].x + wv.w * v[u][3].x;
+                                z.y = wv.x * v[u][0].y + wv.y * v[u][1].y + wv.z * v[u][2].y + wv.w * v[u][3].y;
+                                z.z = wv.x * v[u][0].z + wv.y * v[u][1].z + wv.z * v[u][2].z + wv.w * v[u][3].z;
+                                z.w = wv.x * v[u][0].w + wv.y * v[u][1].w + wv.z * v[u][2].w + wv.w * v[u][3].w;
+                            }
+                            zs4[o] = z;
+                        }
+                    }
+                }
+            } else {
+                for (int o = lane; o < nwin * BC; o += 32) {
+                    const int kk = o / BC, bb = o - kk * BC;
+                    const int k = k_lo + kk;
+                    float z = 0.0f;
+                    if (k >= 0 && k < a.K && bb < nb) {
+                        const int64_t off = (int64_t)k * a.B + bb;
+                        z = wv.x * x00[off] + wv.y * x10[off] + wv.z * x01[off] + wv.w * x11[off];
+                    }
+                    zs[o] = z;
+                }
+            }
+            __syncwarp();
+            int64_t U = U0 - (int64_t)(f_begin + lane) * a.D;
+            const int64_t dU = (int64_t)32 * a.D;
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) {
+                const int f = f_begin + lane + 32 * j;
+                if (f < f_end) {
+                    const int k0 = (int)(U >> kFracBits);
+                    const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
+                    const float g = 1.0f - fr;
+                    const float* z0 = zs + (k0 - k_lo) * BC;
+                    if constexpr (BC >= 4) {
+#pragma unroll
+                        for (int q = 0; q < BC / 4; ++q) {
+                            const float4 p0 = reinterpret_cast<const float4*>(z0)[q];
+                            const float4 p1 = reinterpret_cast<const float4*>(z0 + BC)[q];
+                            acc[j][4 * q + 0] += g * p0.x + fr * p1.x;
+                            acc[j][4 * q + 1] += g * p0.y + fr * p1.y;
+                            acc[j][4 * q + 2] += g * p0.z + fr * p1.z;
+                            acc[j][4 * q + 3] += g * p0.w + fr * p1.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < BC; ++b) acc[j][b] += g * z0[b] + fr * z0[BC + b];
+                    }
+                }
+                U -= dU;
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) {
+            const int f = f_begin + lane + 32 * j;
+            if (f >= f_end) continue;
+            float* yo = a.out + ((int64_t)row_out * a.Tn + f) * a.B + b0;
+            if (vec && nb == BC) {
+#pragma unroll
+                for (int q = 0; q < BC / 4; ++q)
+                    reinterpret_cast<float4*>(yo)[q] =
+                        make_float4(acc[j][4 * q], acc[j][4 * q + 1], acc[j][4 * q + 2], acc[j][4 * q + 3]);
+            } else {
+#pragma unroll
+                for (int b = 0; b < BC; ++b)
+                    if (b < nb) yo[b] = acc[j][b];
+            }
+        }
+    }
+}
+
+// Adjoint phase 1, FP32 fast path: lane per hat within a group of 32 hats;
+// the frames feeding the group are staged once in shared memory and each
+// lane accumulates all BC batch entries of its hat.
+constexpr int kAdj3Warps = 4;
+
+template <int BC>
+__global__ void __launch_bounds__(kAdj3Warps * 32)
+adj_time3_kernel(const ApplyArgs<float> a) {
+    extern __shared__ float smem_a3[];
+    float* ys = smem_a3 + (threadIdx.x >> 5) * (a.zwin * BC);  // zwin = staged frames
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kAdj3Warps + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kAdj3Warps;
+    const bool vec = (BC >= 4) && a.vec4 && (a.Bc == BC);
+    for (int64_t e = warp_global; e < a.n_tasks; e += n_warps) {
+        const int row_out = seg_out_row(a.seg, a.ray_row[e]);
+        if (row_out < 0) {
+            // rays outside the arm contribute nothing: their zhat rows are zero
+            float* zo = a.zhat + (int64_t)e * a.K * a.Bc;
+            for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = 0.0f;
+            continue;
+        }
+        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
+        const float* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
+        for (int kg0 = 0; kg0 < a.K; kg0 += 32) {
+            const int kg1 = min(kg0 + 31, a.K - 1);
+            // frames with (kg0 - 1) 2^24 <= U(f) < (kg1 + 1) 2^24
+            const int64_t hiX = (int64_t)(kg1 + 1) * kFracOne;
+            const int64_t loX = (int64_t)(kg0 - 1) * kFracOne;
+            int64_t fA = floor_div(U0 - hiX, a.D) + 1;
+            int64_t fB = floor_div(U0 - loX, a.D);
+            if (fA < 0) fA = 0;
+            if (fB > a.Tn - 1) fB = a.Tn - 1;
+            const int nfr = fB >= fA ? (int)(fB - fA + 1) : 0;
+            // stage y[fA .. fB][0 .. BC)
+            if (vec) {
+                constexpr int Q = BC / 4 > 0 ? BC / 4 : 1;
+                float4* ys4 = reinterpret_cast<float4*>(ys);
+                for (int o = lane; o < nfr * Q; o += 32) {
+                    const int fl = o / Q, q = o - fl * Q;
+                    ys4[o] = __ldg(reinterpret_cast<const float4*>(yrow + (fA + fl) * a.B) + q);
+                }
+            } else {
+                for (int o = lane; o < nfr * BC; o += 32) {
+                    const int fl = o / BC, bb = o - fl * BC;
+                    ys[o] = bb < a.Bc ? yrow[(fA + fl) * a.B + bb] : 0.0f;
+                }
+            }
+            __syncwarp();
+            const int k = kg0 + lane;
+            if (k <= kg1) {
+                float acc[BC];
+#pragma unroll
+                for (int b = 0; b < BC; ++b) acc[b] = 0.0f;
+                const int64_t hi_excl = (int64_t)(k + 1) * kFracOne;
+                const int64_t lo_incl = (int64_t)(k - 1) * kFracOne;
+                const float est = (float)(U0 - hi_excl) * (1.0f / (float)a.D);
+                int f = (int)fminf(fmaxf(floorf(est) - 1.0f, (float)fA), (float)(fB + 1));
+                int64_t U = U0 - (int64_t)f * a.D;
+                while (f <= fB && U >= hi_excl) { ++f; U -= a.D; }
+                for (; f <= fB && U >= lo_incl; ++f, U -= a.D) {
+                    const int k0 = (int)(U >> kFracBits);
+                    const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
+                    const float hw = (k0 == k) ? 1.0f - fr : fr;
+                    const float* yv = ys + (f - fA) * BC;
+                    if constexpr (BC >= 4) {
+#pragma unroll
+                        for (int q = 0; q < BC / 4; ++q) {
+                            const float4 t = reinterpret_cast<const float4*>(yv)[q];
+                            acc[4 * q + 0] += hw * t.x;
+                            acc[4 * q + 1] += hw * t.y;
+                            acc[4 * q + 2] += hw * t.z;
+                            acc[4 * q + 3] += hw * t.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < BC; ++b) acc[b] += hw * yv[b];
+                    }
+                }
+                float* zo = a.zhat + ((int64_t)e * a.K + k) * a.Bc;
+                if (vec) {
+#pragma unroll
+                    for (int q = 0; q < BC / 4; ++q)
+                        reinterpret_cast<float4*>(zo)[q] =
+                            make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+                } else {
+#pragma unroll
+                    for (int b = 0; b < BC; ++b)
+                        if (b < a.Bc) zo[b] = acc[b];
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Adjoint phase 2, FP32 fast path: lanes over (hat, batch) of one node; the
+// incidence loop is unrolled by 4 so that four zhat rows are in flight.
+template <int BC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+adj_space3_kernel(const ApplyArgs<float> a) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
+        const int kchunk = (int)(task % a.n_kchunk);
+        const int node = (int)(task / a.n_kchunk);
+        const int k_begin = kchunk * a.KC;
+        float acc[kAdjOutPerLane];
+#pragma unroll
+        for (int j = 0; j < kAdjOutPerLane; ++j) acc[j] = 0.0f;
+        int off[kAdjOutPerLane];
+        bool live[kAdjOutPerLane];
+#pragma unroll
+        for (int j = 0; j < kAdjOutPerLane; ++j) {
+            const int o = lane + 32 * j;
+            const int kk = o / BC, bb = o - kk * BC;
+            const int k = k_begin + kk;
+            live[j] = kk < a.KC && k < a.K && bb < a.Bc;
+            off[j] = k * a.Bc + bb;
+        }
+        const int i_begin = a.node_ptr[node], i_end = a.node_ptr[node + 1];
+        const float* wf = reinterpret_cast<const float*>(a.W);
+        int ii = i_begin;
+        for (; ii + 4 <= i_end; ii += 4) {
+            int code[4];
+            float coef[4];
+            const float* zr[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) code[u] = a.inc[ii + u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = code[u] >> 2;
+                coef[u] = wf[code[u]];  // W[e] component c = element 4e + c
+                zr[u] = a.zhat + (int64_t)e * a.K * a.Bc;
+            }
+#pragma unroll
+            for (int j = 0; j < kAdjOutPerLane; ++j) {
+                if (!live[j]) continue;
+                float v0 = zr[0][off[j]], v1 = zr[1][off[j]], v2 = zr[2][off[j]], v3 = zr[3][off[j]];
+                acc[j] += coef[0] * v0;
+                acc[j] += coef[1] * v1;
+                acc[j] += coef[2] * v2;
+                acc[j] += coef[3] * v3;
+            }
+        }
+        for (; ii < i_end; ++ii) {
+            const int code = a.inc[ii];
+            const int e = code >> 2;
+            const float coef = wf[code];
+            const float* zr = a.zhat + (int64_t)e * a.K * a.Bc;
+#pragma unroll
+            for (int j = 0; j < kAdjOutPerLane; ++j)
+                if (live[j]) acc[j] += coef * zr[off[j]];
+        }
+#pragma unroll
+        for (int j = 0; j < kAdjOutPerLane; ++j) {
+            if (!live[j]) continue;
+            const int o = lane + 32 * j;
+            const int kk = o / BC, bb = o - kk * BC;
+            a.out[((int64_t)node * a.K + k_begin + kk) * a.B + bb] = acc[j];
+        }
+    }
+}
+
 static int pick_bc(int B) {
     int bc = 1;
     while (bc < B && bc < 32) bc <<= 1;
@@ -453,6 +768,7 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     a.D = op->frame_D;
     a.delta = op->delta;
     a.seg = seg;
+    a.seg_rows_all = (int)op->n_rows;
     return a;
 }
 
@@ -494,23 +810,101 @@ static cudaError_t launch_adj_bc(ApplyArgs<T> a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+template <int BC>
+static cudaError_t launch_fwd3_bc(ApplyArgs<float> a, cudaStream_t st) {
+    constexpr int FPL = BC >= 32 ? 1 : 32 / BC;
+    a.FC = 32 * FPL;
+    a.vec4 = (a.B % 4 == 0) ? 1 : 0;
+    a.zwin = (int)ceil((a.FC - 1) * a.delta) + 3;
+    a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
+    a.n_bchunk = (a.B + BC - 1) / BC;
+    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk * a.n_bchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    const size_t smem = (size_t)kWarpsPerBlock * a.zwin * BC * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(fwd3_kernel<BC>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    fwd3_kernel<BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const ArmSeg& seg,
                            cudaStream_t st) {
     ApplyArgs<T> a = base_args<T>(op, x, y, B, seg);
-    switch (pick_bc(B)) {
-        case 1: return launch_fwd_bc<T, 1>(a, st);
-        case 2: return launch_fwd_bc<T, 2>(a, st);
-        case 4: return launch_fwd_bc<T, 4>(a, st);
-        case 8: return launch_fwd_bc<T, 8>(a, st);
-        case 16: return launch_fwd_bc<T, 16>(a, st);
-        default: return launch_fwd_bc<T, 32>(a, st);
+    if constexpr (sizeof(T) == 4) {
+        switch (pick_bc(B)) {
+            case 1: return launch_fwd3_bc<1>(a, st);
+            case 2: return launch_fwd3_bc<2>(a, st);
+            case 4: return launch_fwd3_bc<4>(a, st);
+            case 8: return launch_fwd3_bc<8>(a, st);
+            case 16: return launch_fwd3_bc<16>(a, st);
+            default: return launch_fwd3_bc<32>(a, st);
+        }
+    } else {
+        switch (pick_bc(B)) {
+            case 1: return launch_fwd_bc<T, 1>(a, st);
+            case 2: return launch_fwd_bc<T, 2>(a, st);
+            case 4: return launch_fwd_bc<T, 4>(a, st);
+            case 8: return launch_fwd_bc<T, 8>(a, st);
+            case 16: return launch_fwd_bc<T, 16>(a, st);
+            default: return launch_fwd_bc<T, 32>(a, st);
+        }
     }
+}
+
+// FP32 adjoint: fast phase 1 when the frames of a 32-hat group fit the
+// staging buffer, otherwise the general per-(hat, batch) kernel.
+template <int BC>
+static cudaError_t launch_adj3_bc(ApplyArgs<float> a, cudaStream_t st) {
+    const int ywin = (int)ceil(33.0 / a.delta) + 2;
+    const size_t smem = (size_t)kAdj3Warps * ywin * BC * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (a.seg.total > 0) {
+        if (smem <= 96 * 1024) {
+            ApplyArgs<float> t = a;
+            t.zwin = ywin;
+            t.vec4 = (a.B % 4 == 0) ? 1 : 0;
+            t.n_tasks = a.n_rays_total;
+            if (smem > 48 * 1024) {
+                e = cudaFuncSetAttribute(adj_time3_kernel<BC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
+            const int64_t want = (t.n_tasks + kAdj3Warps - 1) / kAdj3Warps;
+            int dev = 0, sms = 148;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int grid = (int)(want < (int64_t)sms * 32 ? (want > 0 ? want : 1) : (int64_t)sms * 32);
+            adj_time3_kernel<BC><<<grid, kAdj3Warps * 32, smem, st>>>(t);
+            e = cudaGetLastError();
+        } else {
+            ApplyArgs<float> t = a;
+            t.KC = kAdjOutPerLane * 32 / BC;
+            t.n_kchunk = (a.K + t.KC - 1) / t.KC;
+            t.n_bchunk = 1;
+            t.n_tasks = a.n_rays_total * t.n_kchunk;
+            adj_time_kernel<float, BC><<<grid_for(t.n_tasks), kWarpsPerBlock * 32, 0, st>>>(t);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) return e;
+    }
+    a.KC = kAdjOutPerLane * 32 / BC;
+    a.n_kchunk = (a.K + a.KC - 1) / a.KC;
+    a.n_bchunk = 1;
+    a.n_tasks = (int64_t)a.n_nodes * a.n_kchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    adj_space3_kernel<BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const ArmSeg& seg,
                            T* zhat, cudaStream_t st) {
+    if (seg.total == 0)  // no data rows in the arm: A^T y = 0
+        return cudaMemsetAsync(x, 0, (size_t)op->n_nodes * op->time.n_hats * B * sizeof(T), st);
     // batch chunks of at most 32 entries share the zhat scratch [E][K][32]
     for (int b_first = 0; b_first < B; b_first += 32) {
         const int Bc = B - b_first < 32 ? B - b_first : 32;
@@ -519,13 +913,24 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         a.Bc = Bc;
         a.n_rays_total = op->n_rays;
         cudaError_t e;
-        switch (pick_bc(Bc)) {
-            case 1: e = launch_adj_bc<T, 1>(a, st); break;
-            case 2: e = launch_adj_bc<T, 2>(a, st); break;
-            case 4: e = launch_adj_bc<T, 4>(a, st); break;
-            case 8: e = launch_adj_bc<T, 8>(a, st); break;
-            case 16: e = launch_adj_bc<T, 16>(a, st); break;
-            default: e = launch_adj_bc<T, 32>(a, st); break;
+        if constexpr (sizeof(T) == 4) {
+            switch (pick_bc(Bc)) {
+                case 1: e = launch_adj3_bc<1>(a, st); break;
+                case 2: e = launch_adj3_bc<2>(a, st); break;
+                case 4: e = launch_adj3_bc<4>(a, st); break;
+                case 8: e = launch_adj3_bc<8>(a, st); break;
+                case 16: e = launch_adj3_bc<16>(a, st); break;
+                default: e = launch_adj3_bc<32>(a, st); break;
+            }
+        } else {
+            switch (pick_bc(Bc)) {
+                case 1: e = launch_adj_bc<T, 1>(a, st); break;
+                case 2: e = launch_adj_bc<T, 2>(a, st); break;
+                case 4: e = launch_adj_bc<T, 4>(a, st); break;
+                case 8: e = launch_adj_bc<T, 8>(a, st); break;
+                case 16: e = launch_adj_bc<T, 16>(a, st); break;
+                default: e = launch_adj_bc<T, 32>(a, st); break;
+            }
         }
         if (e != cudaSuccess) return e;
     }

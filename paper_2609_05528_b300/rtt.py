@@ -104,6 +104,11 @@ _SIGS = {
     "rtt_gram": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
     "rtt_eig_sym": (ctypes.c_int, [ctypes.c_int, vp, dp, vp, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int), vp]),
+    "rtt_solve_ridge": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, dp, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
+                                       ctypes.POINTER(ctypes.c_int), dp, vp]),
+    "rtt_solve_tsvd": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, dp, ctypes.c_int, vp,
+                                      ctypes.c_int, vp, vp]),
     "rtt_destroy": (None, [vp]),
 }
 
@@ -319,6 +324,44 @@ def operational_rank(op: "Operator", Q, arm_mask: int = 7, rho: float = 1.0):
     ev, V, _ = eig_sym(G)
     sig = np.sqrt(np.maximum(ev, 0.0))
     return sig, int(np.count_nonzero(sig >= rho))
+
+
+def solve_ridge(op: "Operator", data, lambdas, arm_mask: int = 7, max_iter: int = 500,
+                tol: float = 1e-6, refresh_every: int = 10, raise_on_stall: bool = True,
+                stream=None):
+    """Batched CG ridge solve; data: CUDA float32 [rows, frames, n_rhs].
+    Returns (x [n_nodes, n_hats, n_rhs * n_lambda], iterations, relres)."""
+    import torch
+    assert data.is_cuda and data.dtype == torch.float32 and data.is_contiguous()
+    lam = np.ascontiguousarray(lambdas, np.float64)
+    n_rhs = data.shape[2]
+    ncol = n_rhs * lam.shape[0]
+    x = torch.empty((op.n_nodes, op.n_hats, ncol), dtype=torch.float32, device=data.device)
+    it = ctypes.c_int(0)
+    rel = np.empty(ncol)
+    st = lib().rtt_solve_ridge(op.handle, arm_mask, ctypes.c_void_p(data.data_ptr()), n_rhs,
+                               _ptr(lam, dp), lam.shape[0], max_iter, tol, refresh_every,
+                               ctypes.c_void_p(x.data_ptr()), ctypes.byref(it), _ptr(rel, dp),
+                               _stream(stream))
+    if st != -5 or raise_on_stall:
+        check(st, "rtt_solve_ridge")
+    return x, it.value, rel
+
+
+def solve_tsvd(op: "Operator", Q, V, evals, rank: int, data, arm_mask: int = 7, stream=None):
+    """TSVD in class Q (CUDA float64 [n_nodes, n_hats, d]) with eigenpairs (V, evals)
+    sorted descending; data: CUDA float64 [rows, frames, n_rhs]."""
+    import torch
+    d = Q.shape[2]
+    n_rhs = data.shape[2]
+    ev = np.ascontiguousarray(evals, np.float64)
+    Vc = V.contiguous()
+    xh = torch.empty((op.n_nodes, op.n_hats, n_rhs), dtype=torch.float64, device=data.device)
+    check(lib().rtt_solve_tsvd(op.handle, arm_mask, ctypes.c_void_p(Q.data_ptr()), d,
+                               ctypes.c_void_p(Vc.data_ptr()), _ptr(ev, dp), rank,
+                               ctypes.c_void_p(data.data_ptr()), n_rhs,
+                               ctypes.c_void_p(xh.data_ptr()), _stream(stream)), "rtt_solve_tsvd")
+    return xh
 
 
 def _autograd():

@@ -90,3 +90,46 @@ def test_gram_eig_rank_match_oracle(kind):
         assert np.max(np.abs(lam - lam_ref)) <= 1e-11 * lam_ref[0]
         if ref.margin > 1e-6:
             assert rank == ref.rank
+
+
+def test_ridge_cg_matches_oracle(case):
+    """Batched ridge CG (FP32 with FP64 residual refresh) vs the oracle's FP64
+    CG solution, for two histories x three regularisation values."""
+    w, tab, op = case
+    scl = O.scale(tab)
+    xt = I.history_batch(w, [41, 42])
+    data = O.apply_A(w, tab, xt, scl) + I.noise((tab.n_rows, w.time.n_frames, 2), 43)
+    lams = [30.0, 300.0, 3000.0]
+    x, iters, rel = rtt.solve_ridge(op, torch.from_numpy(data.astype(np.float32)).cuda(), lams,
+                                    tol=1e-7, max_iter=4000, refresh_every=10)
+    assert np.all(rel < 1e-6), rel
+    xg = x.cpu().numpy()
+    for j in range(2):
+        for l, lam in enumerate(lams):
+            ref, _ = O.ridge_cg(w, tab, scl, data[:, :, j:j + 1], lam, tol=1e-12)
+            got = xg[:, :, j * len(lams) + l]
+            err = np.linalg.norm(got - ref[:, :, 0]) / np.linalg.norm(ref)
+            assert err < 1e-4, (j, lam, err)
+
+
+def test_tsvd_matches_oracle():
+    """TSVD in the S224 class truncated at the operational rank vs the oracle."""
+    build.build()
+    w = I.schw32()
+    tab = O.build_table(w, I.screen_samples(w))
+    op = rtt.Operator(w, {"order": tab.order, "pixel": tab.pixel, "r": tab.r, "phi": tab.phi,
+                          "delay": tab.delay, "weight": tab.weight,
+                          "throughput": tab.throughput})
+    scl = O.scale(tab)
+    Q = O.synth_class(w, "S224")
+    Qd = torch.from_numpy(Q.reshape(w.grid.n_nodes, w.time.n_hats, -1).copy()).cuda()
+    xt = I.history_batch(w, [51, 52, 53])
+    data = O.apply_A(w, tab, xt, scl) + I.noise((tab.n_rows, w.time.n_frames, 3), 54)
+    ref, r_ref = O.tsvd_in_class(w, tab, scl, Q, data, None)
+    G = rtt.gram(op, Qd, 7)
+    ev, V, _ = rtt.eig_sym(G)
+    rank = int(np.count_nonzero(np.sqrt(np.maximum(ev, 0)) >= 1.0))
+    assert rank == r_ref
+    xh = rtt.solve_tsvd(op, Qd, V, ev, rank, torch.from_numpy(data).cuda()).cpu().numpy()
+    err = np.linalg.norm(xh - ref) / np.linalg.norm(ref)
+    assert err < 1e-8, err
