@@ -341,6 +341,35 @@ rtt_status rtt_solve_tsvd(rtt_op op, int arm_mask, const double* Q_dev, int d, c
                           const double* evals_host, int rank, const double* data_dev, int n_rhs,
                           double* xhat_dev, void* stream);
 
+/* One (geometry, observation arm) record of the rank audit. */
+typedef struct {
+    int32_t arm_mask;
+    int32_t rank;          /* operational rank #{sigma_i >= rho} (Eq. 31) */
+    double margin;         /* min_i |sigma_i - rho| / rho: distance of the decision */
+    double sigma_max;
+    double sigma_min_pos;  /* smallest positive sigma (positive-support conditioning) */
+    double s_ref;          /* Eq. 17 of the geometry */
+    int32_t jacobi_sweeps;
+    rtt_reach_result reach; /* anchor, L_anchor, T_reach, A_0,q, J_old */
+    double seconds;        /* wall time of this record */
+} rtt_audit_record;
+
+/*
+ * rtt_rank_audit -- the audit of Sec. 6.2-6.3 for n_ops geometries: for each
+ * operator ops[g] with class Q_dev[g] (double [n_nodes][n_hats][d], e.g. the
+ * S224 synthesis of Eq. 8) and each arm in arm_masks (e.g. direct 0x1 and
+ * resolved 0x7): probe information on the n_ages ages_host (width h),
+ * anchor-connected reach, the direct age boundary A_{0,quantile} (shared by
+ * the arms of a geometry) and J_old (Eq. 35), then G = P^T P, P = scale A Q
+ * (FP64, rtt_gram), its Jacobi spectrum and the operational rank.
+ * out: host array [n_ops][n_arms]; sigma_out (optional): host
+ * [n_ops][n_arms][d], singular values descending.  Synchronous.
+ */
+rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_dev, int d,
+                          const int* arm_masks, int n_arms, int n_ages, const double* ages_host,
+                          double h, double quantile, rtt_audit_record* out, double* sigma_out,
+                          void* stream);
+
 void rtt_destroy(rtt_op op);
 
 #ifdef __cplusplus

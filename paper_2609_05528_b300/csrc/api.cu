@@ -4,6 +4,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cub/cub.cuh>
 #include <string>
@@ -26,6 +27,8 @@ void set_error(const char* fmt, ...) {
 
 template <typename T>
 cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
+rtt_status build_visits(rtt_op_s* op, cudaStream_t st);
+size_t fused_partial_bytes(const rtt_op_s* op);
 template <typename T>
 cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
 
@@ -222,7 +225,8 @@ static void free_op(rtt_op_s* op) {
     if (!op) return;
     void* ps[] = {op->row_ptr, op->ray_row, op->node00, op->node01, op->W,     op->W64,
                   op->K0,      op->F0,      op->F64,    op->r,      op->delay, op->weight,
-                  op->thr,     op->node_ptr, op->inc,   op->row_order, op->zhat};
+                  op->thr,     op->node_ptr, op->inc,   op->row_order, op->zhat,
+                  op->visits,  op->items,    op->split_tiles, op->fpartial, op->node_order};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete op;
@@ -462,6 +466,20 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
     RTT_CUDA(cub::DeviceScan::ExclusiveSum(d_tmp, tb, ncount, (unsigned int*)op->node_ptr, S + 1,
                                            st));
     RTT_CUDA(cudaStreamSynchronize(st));
+    // node order by descending incidence count (deterministic: ties by node index)
+    {
+        std::vector<int32_t> ptr(S + 1);
+        RTT_CUDA(cudaMemcpy(ptr.data(), op->node_ptr, (S + 1) * 4, cudaMemcpyDeviceToHost));
+        std::vector<int32_t> order(S);
+        for (int64_t i = 0; i < S; ++i) order[i] = (int32_t)i;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            return (ptr[a + 1] - ptr[a]) > (ptr[b + 1] - ptr[b]);
+        });
+        RTT_TRY(alloc(&op->node_order, S));
+        RTT_CUDA(cudaMemcpy(op->node_order, order.data(), S * 4, cudaMemcpyHostToDevice));
+    }
+    // (tile, ray) visit lists for the fused adjoint
+    RTT_TRY(build_visits(op, st));
     return RTT_OK;
 }
 
@@ -530,6 +548,21 @@ static rtt_status apply_common(rtt_op op, const T* in, T* out, int batch, int ma
     if (adjoint) {
         const int bc = batch < 32 ? batch : 32;
         RTT_TRY(ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * bc * sizeof(T)));
+        const size_t pb = fused_partial_bytes(op);
+        if (pb > op->fpartial_bytes) {
+            if (op->fpartial) {
+                cudaDeviceSynchronize();
+                cudaFree(op->fpartial);
+                op->fpartial = nullptr;
+                op->fpartial_bytes = 0;
+            }
+            if (cudaMalloc(&op->fpartial, pb) != cudaSuccess) {
+                op->fpartial = nullptr;
+                set_error("fused adjoint partial tiles: allocation of %zu bytes failed", pb);
+                return RTT_ENOMEM;
+            }
+            op->fpartial_bytes = pb;
+        }
         e = launch_adjoint<T>(op, in, out, batch, seg, (T*)op->zhat, st);
     } else {
         e = launch_forward<T>(op, in, out, batch, seg, st);

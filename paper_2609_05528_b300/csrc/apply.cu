@@ -86,6 +86,7 @@ struct ApplyArgs {
     int Bc;       // batch entries held per ray in zhat
     int64_t n_rays_total;
     int seg_rows_all;  // total rows of the operator (all orders)
+    const int32_t* node_order;  // nodes by descending incidence count (load balance)
     int n_fchunk, n_bchunk, n_kchunk;
     int64_t n_tasks;
 };
@@ -428,7 +429,7 @@ adj_space_kernel(const ApplyArgs<T> a) {
 // is computed once and the staged z rows are read as 16-byte vectors.
 // ---------------------------------------------------------------------------
 template <int BC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, BC >= 32 ? 1 : 2)
 fwd3_kernel(const ApplyArgs<float> a) {
     constexpr int FPL = BC >= 32 ? 1 : 32 / BC;  // frames per lane
     constexpr int FC = 32 * FPL;                 // frames per task
@@ -568,6 +569,15 @@ fwd3_kernel(const ApplyArgs<float> a) {
 // lane accumulates all BC batch entries of its hat.
 constexpr int kAdj3Warps = 4;
 
+// Swizzled staging layout for adj_time3: the 16-byte chunk index of (frame
+// f, quad q) has its low three bits XORed with (f / P) mod 8, P = frames per
+// hat step, so the lanes of a warp (one hat each, hats P frames apart) read
+// eight distinct bank groups.
+__device__ __forceinline__ int swz(int f, int q, int Q, int P) {
+    const int idx = f * Q + q;
+    return idx ^ ((f / P) & 7);
+}
+
 template <int BC>
 __global__ void __launch_bounds__(kAdj3Warps * 32)
 adj_time3_kernel(const ApplyArgs<float> a) {
@@ -577,6 +587,9 @@ adj_time3_kernel(const ApplyArgs<float> a) {
     const int64_t warp_global = (int64_t)blockIdx.x * kAdj3Warps + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kAdj3Warps;
     const bool vec = (BC >= 4) && a.vec4 && (a.Bc == BC);
+    constexpr int Q = BC / 4 > 0 ? BC / 4 : 1;
+    const int P = a.FC;  // frames per hat step (>= 1), used only for the swizzle
+    const float invD = 1.0f / (float)a.D;
     for (int64_t e = warp_global; e < a.n_tasks; e += n_warps) {
         const int row_out = seg_out_row(a.seg, a.ray_row[e]);
         if (row_out < 0) {
@@ -589,26 +602,27 @@ adj_time3_kernel(const ApplyArgs<float> a) {
         const float* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
         for (int kg0 = 0; kg0 < a.K; kg0 += 32) {
             const int kg1 = min(kg0 + 31, a.K - 1);
-            // frames with (kg0 - 1) 2^24 <= U(f) < (kg1 + 1) 2^24
+            // frames with (kg0 - 1) 2^24 <= U(f) < (kg1 + 1) 2^24, found from a float
+            // estimate corrected by exact integer tests
             const int64_t hiX = (int64_t)(kg1 + 1) * kFracOne;
             const int64_t loX = (int64_t)(kg0 - 1) * kFracOne;
-            int64_t fA = floor_div(U0 - hiX, a.D) + 1;
-            int64_t fB = floor_div(U0 - loX, a.D);
-            if (fA < 0) fA = 0;
-            if (fB > a.Tn - 1) fB = a.Tn - 1;
-            const int nfr = fB >= fA ? (int)(fB - fA + 1) : 0;
-            // stage y[fA .. fB][0 .. BC)
+            int fA = (int)fminf(fmaxf(floorf((float)(U0 - hiX) * invD) - 1.0f, 0.0f), (float)a.Tn);
+            while (fA < a.Tn && U0 - (int64_t)fA * a.D >= hiX) ++fA;
+            int fB = (int)fminf(fmaxf(floorf((float)(U0 - loX) * invD) + 1.0f, -1.0f),
+                                (float)(a.Tn - 1));
+            while (fB >= 0 && U0 - (int64_t)fB * a.D < loX) --fB;
+            const int nfr = fB >= fA ? fB - fA + 1 : 0;
             if (vec) {
-                constexpr int Q = BC / 4 > 0 ? BC / 4 : 1;
                 float4* ys4 = reinterpret_cast<float4*>(ys);
                 for (int o = lane; o < nfr * Q; o += 32) {
                     const int fl = o / Q, q = o - fl * Q;
-                    ys4[o] = __ldg(reinterpret_cast<const float4*>(yrow + (fA + fl) * a.B) + q);
+                    ys4[swz(fl, q, Q, P)] =
+                        __ldg(reinterpret_cast<const float4*>(yrow + (int64_t)(fA + fl) * a.B) + q);
                 }
             } else {
                 for (int o = lane; o < nfr * BC; o += 32) {
                     const int fl = o / BC, bb = o - fl * BC;
-                    ys[o] = bb < a.Bc ? yrow[(fA + fl) * a.B + bb] : 0.0f;
+                    ys[o] = bb < a.Bc ? yrow[(int64_t)(fA + fl) * a.B + bb] : 0.0f;
                 }
             }
             __syncwarp();
@@ -619,7 +633,7 @@ adj_time3_kernel(const ApplyArgs<float> a) {
                 for (int b = 0; b < BC; ++b) acc[b] = 0.0f;
                 const int64_t hi_excl = (int64_t)(k + 1) * kFracOne;
                 const int64_t lo_incl = (int64_t)(k - 1) * kFracOne;
-                const float est = (float)(U0 - hi_excl) * (1.0f / (float)a.D);
+                const float est = (float)(U0 - hi_excl) * invD;
                 int f = (int)fminf(fmaxf(floorf(est) - 1.0f, (float)fA), (float)(fB + 1));
                 int64_t U = U0 - (int64_t)f * a.D;
                 while (f <= fB && U >= hi_excl) { ++f; U -= a.D; }
@@ -627,17 +641,18 @@ adj_time3_kernel(const ApplyArgs<float> a) {
                     const int k0 = (int)(U >> kFracBits);
                     const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
                     const float hw = (k0 == k) ? 1.0f - fr : fr;
-                    const float* yv = ys + (f - fA) * BC;
-                    if constexpr (BC >= 4) {
+                    if (vec) {
+                        const float4* ys4 = reinterpret_cast<const float4*>(ys);
 #pragma unroll
-                        for (int q = 0; q < BC / 4; ++q) {
-                            const float4 t = reinterpret_cast<const float4*>(yv)[q];
+                        for (int q = 0; q < Q; ++q) {
+                            const float4 t = ys4[swz(f - fA, q, Q, P)];
                             acc[4 * q + 0] += hw * t.x;
                             acc[4 * q + 1] += hw * t.y;
                             acc[4 * q + 2] += hw * t.z;
                             acc[4 * q + 3] += hw * t.w;
                         }
                     } else {
+                        const float* yv = ys + (f - fA) * BC;
 #pragma unroll
                         for (int b = 0; b < BC; ++b) acc[b] += hw * yv[b];
                     }
@@ -645,7 +660,7 @@ adj_time3_kernel(const ApplyArgs<float> a) {
                 float* zo = a.zhat + ((int64_t)e * a.K + k) * a.Bc;
                 if (vec) {
 #pragma unroll
-                    for (int q = 0; q < BC / 4; ++q)
+                    for (int q = 0; q < Q; ++q)
                         reinterpret_cast<float4*>(zo)[q] =
                             make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
                 } else {
@@ -669,7 +684,7 @@ adj_space3_kernel(const ApplyArgs<float> a) {
     const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
         const int kchunk = (int)(task % a.n_kchunk);
-        const int node = (int)(task / a.n_kchunk);
+        const int node = a.node_order ? a.node_order[task / a.n_kchunk] : (int)(task / a.n_kchunk);
         const int k_begin = kchunk * a.KC;
         float acc[kAdjOutPerLane];
 #pragma unroll
@@ -769,6 +784,7 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     a.delta = op->delta;
     a.seg = seg;
     a.seg_rows_all = (int)op->n_rows;
+    a.node_order = op->node_order;
     return a;
 }
 
@@ -859,13 +875,16 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
 // staging buffer, otherwise the general per-(hat, batch) kernel.
 template <int BC>
 static cudaError_t launch_adj3_bc(ApplyArgs<float> a, cudaStream_t st) {
-    const int ywin = (int)ceil(33.0 / a.delta) + 2;
+    // staged frames per 32-hat group, rounded so the swizzle stays in bounds
+    int ywin = (int)ceil(33.0 / a.delta) + 2;
+    ywin = (ywin + 7) & ~7;
     const size_t smem = (size_t)kAdj3Warps * ywin * BC * sizeof(float);
     cudaError_t e = cudaSuccess;
     if (a.seg.total > 0) {
         if (smem <= 96 * 1024) {
             ApplyArgs<float> t = a;
             t.zwin = ywin;
+            t.FC = (int)fmax(1.0, floor(1.0 / a.delta + 0.5));  // frames per hat step
             t.vec4 = (a.B % 4 == 0) ? 1 : 0;
             t.n_tasks = a.n_rays_total;
             if (smem > 48 * 1024) {
@@ -900,6 +919,9 @@ static cudaError_t launch_adj3_bc(ApplyArgs<float> a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_adjoint_fused(const rtt_op_s* op, const float* y, float* x, int B, int b_first,
+                                 int Bc, const ArmSeg& seg, float* partial, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const ArmSeg& seg,
                            T* zhat, cudaStream_t st) {
@@ -914,6 +936,12 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         a.n_rays_total = op->n_rays;
         cudaError_t e;
         if constexpr (sizeof(T) == 4) {
+            if (op->use_fused_adjoint && (op->fpartial || op->n_partial_slots == 0)) {
+                e = launch_adjoint_fused(op, y, x, B, b_first, Bc, seg, (float*)op->fpartial, st);
+                if (e == cudaSuccess) continue;
+                if (e != cudaErrorNotSupported) return e;
+                cudaGetLastError();  // clear the "not supported" marker
+            }
             switch (pick_bc(Bc)) {
                 case 1: e = launch_adj3_bc<1>(a, st); break;
                 case 2: e = launch_adj3_bc<2>(a, st); break;

@@ -1,0 +1,100 @@
+// Multi-geometry audit driver (Sec. 6.2-6.3): for each operator (geometry)
+// and each observation arm, the age probes, anchor-connected reach, direct
+// age boundary and old-age innovation, and the restricted Gram spectrum with
+// its operational rank.  Host orchestration of the library's kernels.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "rtt_internal.cuh"
+
+using namespace rtt;
+
+extern "C" rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q, int d, double* G,
+                               void* stream);
+extern "C" rtt_status rtt_eig_sym(int n, double* A, double* evals_host, double* V, int max_sweeps,
+                                  int* sweeps_host, void* stream);
+extern "C" rtt_status rtt_probe_info(rtt_op op, int arm_mask, int n_ages, const double* ages,
+                                     double h, double* info, void* stream);
+extern "C" rtt_status rtt_direct_age_quantile(rtt_op op, double q, double* out, void* stream);
+extern "C" rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const double* ages,
+                                const double* info, double h, double a0q, double age_step,
+                                rtt_reach_result* out, uint8_t* pass);
+
+extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_dev,
+                                     int d, const int* arm_masks, int n_arms, int n_ages,
+                                     const double* ages_host, double h, double quantile,
+                                     rtt_audit_record* out, double* sigma_out, void* stream) {
+    if (!ops || n_ops < 1 || !Q_dev || d < 1 || d > 4096 || !arm_masks || n_arms < 1 ||
+        n_ages < 1 || n_ages > 256 || !ages_host || !(h > 0.0) || !(quantile > 0.0) || !out) {
+        set_error("invalid rank-audit arguments");
+        return RTT_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    double *G = nullptr, *V = nullptr;
+    cudaError_t e = cudaMalloc(&G, (size_t)d * d * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&V, (size_t)d * d * 8);
+    if (e != cudaSuccess) {
+        cudaFree(G);
+        cudaFree(V);
+        set_error("rank audit: allocation failed");
+        return RTT_ENOMEM;
+    }
+    std::vector<double> info(n_ages), ev(d);
+    const double age_step = n_ages > 1 ? ages_host[1] - ages_host[0] : 1.0;
+    rtt_status s = RTT_OK;
+    for (int g = 0; g < n_ops && s == RTT_OK; ++g) {
+        rtt_op op = ops[g];
+        if (!op || !Q_dev[g]) {
+            set_error("rank audit: operator or class %d missing", g);
+            s = RTT_EINVAL;
+            break;
+        }
+        double a0 = 0.0;
+        s = rtt_direct_age_quantile(op, quantile, &a0, stream);
+        for (int ai = 0; ai < n_arms && s == RTT_OK; ++ai) {
+            const auto t0 = std::chrono::steady_clock::now();
+            rtt_audit_record& r = out[(size_t)g * n_arms + ai];
+            r.arm_mask = arm_masks[ai];
+            s = rtt_probe_info(op, arm_masks[ai], n_ages, ages_host, h, info.data(), stream);
+            if (s != RTT_OK) break;
+            rtt_reach_result rr;
+            s = rtt_reach(op, arm_masks[ai], n_ages, ages_host, info.data(), h, a0, age_step, &rr,
+                          nullptr);
+            if (s != RTT_OK) break;
+            r.reach = rr;
+            s = rtt_gram(op, arm_masks[ai], Q_dev[g], d, G, stream);
+            if (s != RTT_OK) break;
+            int sweeps = 0;
+            s = rtt_eig_sym(d, G, ev.data(), V, 80, &sweeps, stream);
+            if (s != RTT_OK) break;
+            // sigma descending
+            std::vector<double> sig(d);
+            for (int i = 0; i < d; ++i) sig[i] = std::sqrt(ev[i] > 0.0 ? ev[i] : 0.0);
+            std::sort(sig.begin(), sig.end(), [](double a, double b) { return a > b; });
+            const double rho = op->opt.rho;
+            int rank = 0;
+            double margin = INFINITY, smin_pos = INFINITY;
+            for (int i = 0; i < d; ++i) {
+                if (sig[i] >= rho) ++rank;
+                margin = std::fmin(margin, std::fabs(sig[i] - rho) / rho);
+                if (sig[i] > 0.0) smin_pos = std::fmin(smin_pos, sig[i]);
+            }
+            r.rank = rank;
+            r.margin = margin;
+            r.sigma_max = sig[0];
+            r.sigma_min_pos = smin_pos;
+            r.s_ref = op->s_ref;
+            r.jacobi_sweeps = sweeps;
+            if (sigma_out)
+                for (int i = 0; i < d; ++i) sigma_out[((size_t)g * n_arms + ai) * d + i] = sig[i];
+            r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+    }
+    cudaFree(G);
+    cudaFree(V);
+    return s;
+}

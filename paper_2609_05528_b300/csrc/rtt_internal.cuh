@@ -67,7 +67,17 @@ struct rtt_op_s {
     int32_t* node_ptr = nullptr;  // [S+1] transposed incidence CSR
     int32_t* inc = nullptr;       // [4E] e * 4 + c
     int32_t* row_order = nullptr; // [R] order of each row
+    int32_t* node_order = nullptr; // [S] nodes sorted by descending incidence count
     // adjoint scratch: per-ray temporal contraction [E][K][<=32], grown on demand
     void* zhat = nullptr;
     size_t zhat_bytes = 0;
+    // fused adjoint: (tile, ray) visits, work items, split tiles, partial tiles
+    uint32_t* visits = nullptr;
+    void* items = nullptr;
+    void* split_tiles = nullptr;
+    int n_items = 0, n_split = 0, n_partial_slots = 0, n_tp = 0;
+    int64_t n_visits = 0;
+    void* fpartial = nullptr;
+    size_t fpartial_bytes = 0;
+    bool use_fused_adjoint = false;  // tile-fused adjoint (measured slower than two-phase so far)
 };

@@ -72,6 +72,13 @@ class ReachResult(ctypes.Structure):
                 ("A0q", ctypes.c_double), ("J_old", ctypes.c_double)]
 
 
+class AuditRecord(ctypes.Structure):
+    _fields_ = [("arm_mask", ctypes.c_int32), ("rank", ctypes.c_int32), ("margin", ctypes.c_double),
+                ("sigma_max", ctypes.c_double), ("sigma_min_pos", ctypes.c_double),
+                ("s_ref", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int32),
+                ("reach", ReachResult), ("seconds", ctypes.c_double)]
+
+
 class Screen(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("alpha", dp), ("beta", dp), ("pixel", i32p),
                 ("n_sub", i32p), ("d_omega_pixel", ctypes.c_double)]
@@ -109,6 +116,10 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_int), dp, vp]),
     "rtt_solve_tsvd": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, dp, ctypes.c_int, vp,
                                       ctypes.c_int, vp, vp]),
+    "rtt_rank_audit": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
+                                      ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                                      ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
+                                      ctypes.POINTER(AuditRecord), dp, vp]),
     "rtt_destroy": (None, [vp]),
 }
 
@@ -362,6 +373,25 @@ def solve_tsvd(op: "Operator", Q, V, evals, rank: int, data, arm_mask: int = 7, 
                                ctypes.c_void_p(data.data_ptr()), n_rhs,
                                ctypes.c_void_p(xh.data_ptr()), _stream(stream)), "rtt_solve_tsvd")
     return xh
+
+
+def rank_audit(ops, Qs, arm_masks=(1, 7), ages=AGES, h: float = 3.0, quantile: float = 0.999,
+               stream=None):
+    """rtt_rank_audit over several operators; Qs: CUDA float64 [n_nodes, n_hats, d] each.
+    Returns (records [n_ops][n_arms], sigma [n_ops, n_arms, d])."""
+    n = len(ops)
+    d = Qs[0].shape[2]
+    arr_ops = (vp * n)(*[o.handle for o in ops])
+    arr_q = (vp * n)(*[ctypes.c_void_p(q.data_ptr()) for q in Qs])
+    arms = (ctypes.c_int * len(arm_masks))(*arm_masks)
+    ages = np.ascontiguousarray(ages, np.float64)
+    recs = (AuditRecord * (n * len(arm_masks)))()
+    sig = np.empty((n, len(arm_masks), d))
+    check(lib().rtt_rank_audit(arr_ops, n, arr_q, d, arms, len(arm_masks), ages.shape[0],
+                               _ptr(ages, dp), h, quantile, recs, _ptr(sig, dp), _stream(stream)),
+          "rtt_rank_audit")
+    out = [[recs[g * len(arm_masks) + a] for a in range(len(arm_masks))] for g in range(n)]
+    return out, sig
 
 
 def _autograd():
