@@ -295,6 +295,17 @@ rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q_dev, int d, double*
                     void* stream);
 
 /*
+ * rtt_gram_normal -- the same G = P^T P computed as G = Q^T (A^T (A Q)) through
+ * the normal operator, FP64 throughout (FP64 forward and adjoint kernels on
+ * 32 columns at a time, then an FP64 GEMM Q^T Z in cuBLAS).  The contraction
+ * runs over n_nodes * n_hats coefficients rather than arm_rows * n_frames
+ * data samples.  Same arguments and result as rtt_gram up to rounding;
+ * library scratch <= 32 columns of data and coefficients.  Synchronous.
+ */
+rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q_dev, int d, double* G_dev,
+                           void* stream);
+
+/*
  * rtt_eig_sym -- eigendecomposition of a symmetric n x n FP64 matrix on the
  * GPU (parallel cyclic Jacobi, round-robin ordering, relative off-diagonal
  * criterion), as used for the spectrum of the restricted Gram (Eq. 31).
@@ -354,6 +365,9 @@ typedef struct {
     double seconds;        /* wall time of this record */
 } rtt_audit_record;
 
+#define RTT_GRAM_DATA 0   /* G = P^T P over data samples (rtt_gram) */
+#define RTT_GRAM_NORMAL 1 /* G = Q^T A^T A Q (rtt_gram_normal) */
+
 /*
  * rtt_rank_audit -- the audit of Sec. 6.2-6.3 for n_ops geometries: for each
  * operator ops[g] with class Q_dev[g] (double [n_nodes][n_hats][d], e.g. the
@@ -361,14 +375,15 @@ typedef struct {
  * resolved 0x7): probe information on the n_ages ages_host (width h),
  * anchor-connected reach, the direct age boundary A_{0,quantile} (shared by
  * the arms of a geometry) and J_old (Eq. 35), then G = P^T P, P = scale A Q
- * (FP64, rtt_gram), its Jacobi spectrum and the operational rank.
+ * (FP64; gram_mode RTT_GRAM_DATA uses rtt_gram, RTT_GRAM_NORMAL uses
+ * rtt_gram_normal), its Jacobi spectrum and the operational rank.
  * out: host array [n_ops][n_arms]; sigma_out (optional): host
  * [n_ops][n_arms][d], singular values descending.  Synchronous.
  */
 rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_dev, int d,
                           const int* arm_masks, int n_arms, int n_ages, const double* ages_host,
-                          double h, double quantile, rtt_audit_record* out, double* sigma_out,
-                          void* stream);
+                          double h, double quantile, int gram_mode, rtt_audit_record* out,
+                          double* sigma_out, void* stream);
 
 void rtt_destroy(rtt_op op);
 

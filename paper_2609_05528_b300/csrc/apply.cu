@@ -142,161 +142,6 @@ __device__ __forceinline__ int seg_out_row(const ArmSeg& s, int row_in) {
 }
 
 constexpr int kWarpsPerBlock = 8;
-constexpr int kOutPerLane = 16;
-
-template <typename T, int BC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
-fwd_kernel(const ApplyArgs<T> a) {
-    extern __shared__ unsigned char smem_raw[];
-    T* zs = reinterpret_cast<T*>(smem_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
-    const int FC = a.FC;
-    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
-        const int bchunk = (int)(task % a.n_bchunk);
-        const int64_t t2 = task / a.n_bchunk;
-        const int fchunk = (int)(t2 % a.n_fchunk);
-        const int row_out = (int)(t2 / a.n_fchunk);
-        const int row = seg_in_row(a.seg, row_out);
-        const int f_begin = fchunk * FC;
-        const int f_end = min(a.Tn, f_begin + FC);
-        const int b0 = bchunk * BC;
-        T acc[kOutPerLane];
-#pragma unroll
-        for (int j = 0; j < kOutPerLane; ++j) acc[j] = T(0);
-        const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
-        for (int e = e_begin; e < e_end; ++e) {
-            const HatCoef<T> hc = load_hat(a, e);
-            int k_top, k_bot;
-            T dummy;
-            hc.at(f_begin, k_top, dummy);
-            hc.at(f_end - 1, k_bot, dummy);
-            const int k_lo = k_bot;             // smallest hat touched
-            const int nwin = k_top + 2 - k_lo;  // hats k_lo .. k_top + 1
-            T w[4];
-            load_w(a, e, w);
-            const int n00 = a.node00[e], n01 = a.node01[e];
-            const int64_t KB = (int64_t)a.K * a.B;
-            const T* x00 = a.in + (int64_t)n00 * KB;
-            const T* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB;
-            const T* x01 = a.in + (int64_t)n01 * KB;
-            const T* x11 = a.in + (int64_t)(n01 + a.n_phi) * KB;
-            bool staged = false;
-            if constexpr (sizeof(T) == 4 && BC >= 4) {
-                if (a.vec4) {
-                    staged = true;
-                    // 16-byte loads of 4 batch entries; 4 items x 4 corners in flight per lane
-                    constexpr int Q = BC / 4;
-                    const int n_items = nwin * Q;
-                    float4* zs4 = reinterpret_cast<float4*>(zs);
-                    for (int base = 0; base < n_items; base += 32 * 2) {
-                        float4 v[2][4];
-                        bool okv[2];
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const int o = base + lane + 32 * u;
-                            const int kk = o / Q, q = o - kk * Q;
-                            const int k = k_lo + kk;
-                            const int b = b0 + 4 * q;
-                            okv[u] = o < n_items && k >= 0 && k < a.K && b < a.B;
-                            if (okv[u]) {
-                                const int64_t off = (int64_t)k * a.B + b;
-                                v[u][0] = *reinterpret_cast<const float4*>(x00 + off);
-                                v[u][1] = *reinterpret_cast<const float4*>(x10 + off);
-                                v[u][2] = *reinterpret_cast<const float4*>(x01 + off);
-                                v[u][3] = *reinterpret_cast<const float4*>(x11 + off);
-                            }
-                        }
-#pragma unroll
-                        for (int u = 0; u < 2; ++u) {
-                            const int o = base + lane + 32 * u;
-                            if (o < n_items) {
-                                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                                if (okv[u]) {
-                                    z.x = w[0] * v[u][0].x + w[1] * v[u][1].x + w[2] * v[u][2].x + w[3] * v[u][3].x;
-                                    z.y = w[0] * v[u][0].y + w[1] * v[u][1].y + w[2] * v[u][2].y + w[3] * v[u][3].y;
-                                    z.z = w[0] * v[u][0].z + w[1] * v[u][1].z + w[2] * v[u][2].z + w[3] * v[u][3].z;
-                                    z.w = w[0] * v[u][0].w + w[1] * v[u][1].w + w[2] * v[u][2].w + w[3] * v[u][3].w;
-                                }
-                                zs4[o] = z;
-                            }
-                        }
-                    }
-                }
-            }
-            for (int base = 0; !staged && base < nwin * BC; base += 32 * 2) {
-                T v[2][4];
-                bool okv[2];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int o = base + lane + 32 * u;
-                    const int kk = o / BC, bb = o - kk * BC;
-                    const int k = k_lo + kk;
-                    const int b = b0 + bb;
-                    okv[u] = o < nwin * BC && k >= 0 && k < a.K && b < a.B;
-                    if (okv[u]) {
-                        const int64_t off = (int64_t)k * a.B + b;
-                        v[u][0] = x00[off];
-                        v[u][1] = x10[off];
-                        v[u][2] = x01[off];
-                        v[u][3] = x11[off];
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    const int o = base + lane + 32 * u;
-                    if (o < nwin * BC)
-                        zs[o] = okv[u] ? w[0] * v[u][0] + w[1] * v[u][1] + w[2] * v[u][2] + w[3] * v[u][3]
-                                       : T(0);
-                }
-            }
-            __syncwarp();
-            if constexpr (sizeof(T) == 4) {
-                // lane frames f_j = f_begin + lane / BC + j (32 / BC): the 24-bit
-                // fixed-point hat coordinate U(f) = U0 - f D steps by a constant
-                const int bb = lane % BC;
-                const int f0 = f_begin + lane / BC;
-                int64_t U = ((int64_t)hc.K0 * kFracOne + hc.F0) - (int64_t)f0 * hc.D;
-                const int64_t dU = (int64_t)(32 / BC) * hc.D;
-#pragma unroll
-                for (int j = 0; j < kOutPerLane; ++j) {
-                    const int f = f0 + j * (32 / BC);
-                    if (f < f_end) {
-                        const int k0 = (int)(U >> kFracBits);
-                        const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
-                        const int i0 = (k0 - k_lo) * BC + bb;
-                        acc[j] += (1.0f - fr) * zs[i0] + fr * zs[i0 + BC];
-                    }
-                    U -= dU;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < kOutPerLane; ++j) {
-                    const int o = lane + 32 * j;
-                    const int fl = o / BC, bb = o - fl * BC;
-                    const int f = f_begin + fl;
-                    if (f < f_end) {
-                        int k0;
-                        T fr;
-                        hc.at(f, k0, fr);
-                        const int i0 = (k0 - k_lo) * BC + bb;
-                        acc[j] += (T(1) - fr) * zs[i0] + fr * zs[i0 + BC];
-                    }
-                }
-            }
-            __syncwarp();
-        }
-#pragma unroll
-        for (int j = 0; j < kOutPerLane; ++j) {
-            const int o = lane + 32 * j;
-            const int fl = o / BC, bb = o - fl * BC;
-            const int f = f_begin + fl;
-            const int b = b0 + bb;
-            if (f < f_end && b < a.B) a.out[((int64_t)row_out * a.Tn + f) * a.B + b] = acc[j];
-        }
-    }
-}
 
 constexpr int kAdjOutPerLane = 8;
 
@@ -376,69 +221,63 @@ adj_time_kernel(const ApplyArgs<T> a) {
     }
 }
 
-// Phase 2: spatial transpose, a deterministic gather per node over its
-// incidence list (sorted by ray): x[s][k][b] = sum W_{e,c} zhat_e[k][b].
-template <typename T, int BC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-adj_space_kernel(const ApplyArgs<T> a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
-        const int bchunk = (int)(task % a.n_bchunk);
-        const int64_t t2 = task / a.n_bchunk;
-        const int kchunk = (int)(t2 % a.n_kchunk);
-        const int node = (int)(t2 / a.n_kchunk);
-        const int b0 = bchunk * BC;
-        const int k_begin = kchunk * a.KC;
-        T acc[kAdjOutPerLane];
-#pragma unroll
-        for (int j = 0; j < kAdjOutPerLane; ++j) acc[j] = T(0);
-        const int i_begin = a.node_ptr[node], i_end = a.node_ptr[node + 1];
-        for (int ii = i_begin; ii < i_end; ++ii) {
-            const int code = a.inc[ii];
-            const int e = code >> 2, c = code & 3;
-            if (seg_out_row(a.seg, a.ray_row[e]) < 0) continue;
-            T w[4];
-            load_w(a, e, w);
-            const T coef = w[c];
-            const T* zr = a.zhat + (int64_t)e * a.K * a.Bc;
-#pragma unroll
-            for (int j = 0; j < kAdjOutPerLane; ++j) {
-                const int o = lane + 32 * j;
-                const int kk = o / BC, bb = o - kk * BC;
-                const int k = k_begin + kk;
-                if (kk < a.KC && k < a.K && bb < a.Bc) acc[j] += coef * zr[(int64_t)k * a.Bc + bb];
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < kAdjOutPerLane; ++j) {
-            const int o = lane + 32 * j;
-            const int kk = o / BC, bb = o - kk * BC;
-            const int k = k_begin + kk;
-            const int b = b0 + bb;
-            if (kk < a.KC && k < a.K && bb < a.Bc && b < a.B)
-                a.out[((int64_t)node * a.K + k) * a.B + b] = acc[j];
-        }
-    }
+// ---------------------------------------------------------------------------
+// Fast paths (FP32 and FP64 storage).  Forward: lane per frame, each lane
+// carries all BC batch entries of its frames, so the exact hat index and
+// fraction of a (ray, frame) are computed once and the staged z rows are read
+// as 16-byte vectors.  FP32 takes the fraction from the 24-bit fixed-point
+// hat coordinate; FP64 takes the exact FP64 fraction (same integer index).
+// ---------------------------------------------------------------------------
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float4; static constexpr int W = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int W = 2; };
+
+template <typename T>
+__device__ __forceinline__ T* comps(typename Vec16<T>::type& v) { return reinterpret_cast<T*>(&v); }
+template <typename T>
+__device__ __forceinline__ const T* comps(const typename Vec16<T>::type& v) {
+    return reinterpret_cast<const T*>(&v);
 }
 
-// ---------------------------------------------------------------------------
-// FP32 fast path.  Forward: lane per frame, each lane carries all BC batch
-// entries of its frames, so the exact hat index / fraction of a (ray, frame)
-// is computed once and the staged z rows are read as 16-byte vectors.
-// ---------------------------------------------------------------------------
-template <int BC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, BC >= 32 ? 1 : 2)
-fwd3_kernel(const ApplyArgs<float> a) {
+// hat fraction of a frame with fixed-point coordinate U = U0 - f D
+template <typename T>
+__device__ __forceinline__ T frac_of(int64_t U, int f, int64_t D, double F64);
+template <>
+__device__ __forceinline__ float frac_of<float>(int64_t U, int, int64_t, double) {
+    return (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
+}
+template <>
+__device__ __forceinline__ double frac_of<double>(int64_t, int f, int64_t D, double F64) {
+    const double R = (double)(((int64_t)f * D) & kFracMask) * (1.0 / (double)kFracOne);
+    const double v = F64 - R;
+    return v < 0.0 ? v + 1.0 : v;
+}
+
+template <typename T>
+__device__ __forceinline__ double exact_frac(const ApplyArgs<T>& a, int e);
+template <>
+__device__ __forceinline__ double exact_frac<float>(const ApplyArgs<float>&, int) { return 0.0; }
+template <>
+__device__ __forceinline__ double exact_frac<double>(const ApplyArgs<double>& a, int e) {
+    return a.F64[e];
+}
+
+template <typename T>
+__device__ __forceinline__ void corner_w(const ApplyArgs<T>& a, int e, T w[4]) { load_w(a, e, w); }
+
+template <typename T, int BC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, (sizeof(T) == 8 || BC >= 32) ? 1 : 2)
+fwd3_kernel(const ApplyArgs<T> a) {
+    using V = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::W;
     constexpr int FPL = BC >= 32 ? 1 : 32 / BC;  // frames per lane
     constexpr int FC = 32 * FPL;                 // frames per task
-    extern __shared__ float smem3[];
-    float* zs = smem3 + (threadIdx.x >> 5) * (a.zwin * BC);
+    extern __shared__ __align__(16) unsigned char smem3_raw[];
+    T* zs = reinterpret_cast<T*>(smem3_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
-    const bool vec = (BC >= 4) && a.vec4;
+    const bool vec = (BC >= VW) && a.vec4;
     for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
         const int bchunk = (int)(task % a.n_bchunk);
         const int64_t t2 = task / a.n_bchunk;
@@ -449,30 +288,32 @@ fwd3_kernel(const ApplyArgs<float> a) {
         const int f_end = min(a.Tn, f_begin + FC);
         const int b0 = bchunk * BC;
         const int nb = min(BC, a.B - b0);
-        float acc[FPL][BC];
+        T acc[FPL][BC];
 #pragma unroll
         for (int j = 0; j < FPL; ++j)
 #pragma unroll
-            for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+            for (int b = 0; b < BC; ++b) acc[j][b] = T(0);
         const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
         for (int e = e_begin; e < e_end; ++e) {
             const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
+            const double F64 = exact_frac(a, e);
             const int k_top = (int)((U0 - (int64_t)f_begin * a.D) >> kFracBits);
             const int k_lo = (int)((U0 - (int64_t)(f_end - 1) * a.D) >> kFracBits);
             const int nwin = k_top + 2 - k_lo;
-            const float4 wv = a.W[e];
+            T w[4];
+            corner_w(a, e, w);
             const int n00 = a.node00[e], n01 = a.node01[e];
             const int64_t KB = (int64_t)a.K * a.B;
-            const float* x00 = a.in + (int64_t)n00 * KB + b0;
-            const float* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB + b0;
-            const float* x01 = a.in + (int64_t)n01 * KB + b0;
-            const float* x11 = a.in + (int64_t)(n01 + a.n_phi) * KB + b0;
+            const T* x00 = a.in + (int64_t)n00 * KB + b0;
+            const T* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB + b0;
+            const T* x01 = a.in + (int64_t)n01 * KB + b0;
+            const T* x11 = a.in + (int64_t)(n01 + a.n_phi) * KB + b0;
             if (vec && nb == BC) {
-                constexpr int Q = BC / 4 > 0 ? BC / 4 : 1;
-                float4* zs4 = reinterpret_cast<float4*>(zs);
+                constexpr int Q = BC / VW > 0 ? BC / VW : 1;
+                V* zsv = reinterpret_cast<V*>(zs);
                 const int n_items = nwin * Q;
                 for (int base = 0; base < n_items; base += 64) {
-                    float4 v[2][4];
+                    V v[2][4];
                     bool okv[2];
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
@@ -481,25 +322,26 @@ fwd3_kernel(const ApplyArgs<float> a) {
                         const int k = k_lo + kk;
                         okv[u] = o < n_items && k >= 0 && k < a.K;
                         if (okv[u]) {
-                            const int64_t off = (int64_t)k * a.B + 4 * q;
-                            v[u][0] = __ldg(reinterpret_cast<const float4*>(x00 + off));
-                            v[u][1] = __ldg(reinterpret_cast<const float4*>(x10 + off));
-                            v[u][2] = __ldg(reinterpret_cast<const float4*>(x01 + off));
-                            v[u][3] = __ldg(reinterpret_cast<const float4*>(x11 + off));
+                            const int64_t off = (int64_t)k * a.B + VW * q;
+                            v[u][0] = __ldg(reinterpret_cast<const V*>(x00 + off));
+                            v[u][1] = __ldg(reinterpret_cast<const V*>(x10 + off));
+                            v[u][2] = __ldg(reinterpret_cast<const V*>(x01 + off));
+                            v[u][3] = __ldg(reinterpret_cast<const V*>(x11 + off));
                         }
                     }
 #pragma unroll
                     for (int u = 0; u < 2; ++u) {
                         const int o = base + lane + 32 * u;
                         if (o < n_items) {
-                            float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                            if (okv[u]) {
-                                z.x = wv.x * v[u][0].x + wv.y * v[u][1].x + wv.z * v[u][2].x + wv.w * v[u][3].x;
-                                z.y = wv.x * v[u][0].y + wv.y * v[u][1].y + wv.z * v[u][2].y + wv.w * v[u][3].y;
-                                z.z = wv.x * v[u][0].z + wv.y * v[u][1].z + wv.z * v[u][2].z + wv.w * v[u][3].z;
-                                z.w = wv.x * v[u][0].w + wv.y * v[u][1].w + wv.z * v[u][2].w + wv.w * v[u][3].w;
+                            V z;
+                            T* zc = comps<T>(z);
+#pragma unroll
+                            for (int c = 0; c < VW; ++c) {
+                                zc[c] = okv[u] ? w[0] * comps<T>(v[u][0])[c] + w[1] * comps<T>(v[u][1])[c] +
+                                                     w[2] * comps<T>(v[u][2])[c] + w[3] * comps<T>(v[u][3])[c]
+                                               : T(0);
                             }
-                            zs4[o] = z;
+                            zsv[o] = z;
                         }
                     }
                 }
@@ -507,10 +349,10 @@ fwd3_kernel(const ApplyArgs<float> a) {
                 for (int o = lane; o < nwin * BC; o += 32) {
                     const int kk = o / BC, bb = o - kk * BC;
                     const int k = k_lo + kk;
-                    float z = 0.0f;
+                    T z = T(0);
                     if (k >= 0 && k < a.K && bb < nb) {
                         const int64_t off = (int64_t)k * a.B + bb;
-                        z = wv.x * x00[off] + wv.y * x10[off] + wv.z * x01[off] + wv.w * x11[off];
+                        z = w[0] * x00[off] + w[1] * x10[off] + w[2] * x01[off] + w[3] * x11[off];
                     }
                     zs[o] = z;
                 }
@@ -523,18 +365,17 @@ fwd3_kernel(const ApplyArgs<float> a) {
                 const int f = f_begin + lane + 32 * j;
                 if (f < f_end) {
                     const int k0 = (int)(U >> kFracBits);
-                    const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
-                    const float g = 1.0f - fr;
-                    const float* z0 = zs + (k0 - k_lo) * BC;
-                    if constexpr (BC >= 4) {
+                    const T fr = frac_of<T>(U, f, a.D, F64);
+                    const T g = T(1) - fr;
+                    const T* z0 = zs + (k0 - k_lo) * BC;
+                    if constexpr (BC >= VW) {
 #pragma unroll
-                        for (int q = 0; q < BC / 4; ++q) {
-                            const float4 p0 = reinterpret_cast<const float4*>(z0)[q];
-                            const float4 p1 = reinterpret_cast<const float4*>(z0 + BC)[q];
-                            acc[j][4 * q + 0] += g * p0.x + fr * p1.x;
-                            acc[j][4 * q + 1] += g * p0.y + fr * p1.y;
-                            acc[j][4 * q + 2] += g * p0.z + fr * p1.z;
-                            acc[j][4 * q + 3] += g * p0.w + fr * p1.w;
+                        for (int q = 0; q < BC / VW; ++q) {
+                            const V p0 = reinterpret_cast<const V*>(z0)[q];
+                            const V p1 = reinterpret_cast<const V*>(z0 + BC)[q];
+#pragma unroll
+                            for (int c = 0; c < VW; ++c)
+                                acc[j][VW * q + c] += g * comps<T>(p0)[c] + fr * comps<T>(p1)[c];
                         }
                     } else {
 #pragma unroll
@@ -549,12 +390,15 @@ fwd3_kernel(const ApplyArgs<float> a) {
         for (int j = 0; j < FPL; ++j) {
             const int f = f_begin + lane + 32 * j;
             if (f >= f_end) continue;
-            float* yo = a.out + ((int64_t)row_out * a.Tn + f) * a.B + b0;
+            T* yo = a.out + ((int64_t)row_out * a.Tn + f) * a.B + b0;
             if (vec && nb == BC) {
 #pragma unroll
-                for (int q = 0; q < BC / 4; ++q)
-                    reinterpret_cast<float4*>(yo)[q] =
-                        make_float4(acc[j][4 * q], acc[j][4 * q + 1], acc[j][4 * q + 2], acc[j][4 * q + 3]);
+                for (int q = 0; q < BC / VW; ++q) {
+                    V o;
+#pragma unroll
+                    for (int c = 0; c < VW; ++c) comps<T>(o)[c] = acc[j][VW * q + c];
+                    reinterpret_cast<V*>(yo)[q] = o;
+                }
             } else {
 #pragma unroll
                 for (int b = 0; b < BC; ++b)
@@ -564,42 +408,45 @@ fwd3_kernel(const ApplyArgs<float> a) {
     }
 }
 
-// Adjoint phase 1, FP32 fast path: lane per hat within a group of 32 hats;
-// the frames feeding the group are staged once in shared memory and each
-// lane accumulates all BC batch entries of its hat.
+// Adjoint phase 1, fast path: lane per hat within a group of 32 hats; the
+// frames feeding the group are staged once in shared memory and each lane
+// accumulates all BC batch entries of its hat.
 constexpr int kAdj3Warps = 4;
 
-// Swizzled staging layout for adj_time3: the 16-byte chunk index of (frame
-// f, quad q) has its low three bits XORed with (f / P) mod 8, P = frames per
-// hat step, so the lanes of a warp (one hat each, hats P frames apart) read
-// eight distinct bank groups.
+// Swizzled staging layout: the 16-byte chunk index of (frame f, chunk q) has
+// its low three bits XORed with (f / P) mod 8, P = frames per hat step, so
+// the lanes of a warp (one hat each, hats P frames apart) read eight distinct
+// bank groups.
 __device__ __forceinline__ int swz(int f, int q, int Q, int P) {
     const int idx = f * Q + q;
     return idx ^ ((f / P) & 7);
 }
 
-template <int BC>
+template <typename T, int BC>
 __global__ void __launch_bounds__(kAdj3Warps * 32)
-adj_time3_kernel(const ApplyArgs<float> a) {
-    extern __shared__ float smem_a3[];
-    float* ys = smem_a3 + (threadIdx.x >> 5) * (a.zwin * BC);  // zwin = staged frames
+adj_time3_kernel(const ApplyArgs<T> a) {
+    using V = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::W;
+    extern __shared__ __align__(16) unsigned char smem_a3_raw[];
+    T* ys = reinterpret_cast<T*>(smem_a3_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = (int64_t)blockIdx.x * kAdj3Warps + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kAdj3Warps;
-    const bool vec = (BC >= 4) && a.vec4 && (a.Bc == BC);
-    constexpr int Q = BC / 4 > 0 ? BC / 4 : 1;
+    const bool vec = (BC >= VW) && a.vec4 && (a.Bc == BC);
+    constexpr int Q = BC / VW > 0 ? BC / VW : 1;
     const int P = a.FC;  // frames per hat step (>= 1), used only for the swizzle
     const float invD = 1.0f / (float)a.D;
     for (int64_t e = warp_global; e < a.n_tasks; e += n_warps) {
         const int row_out = seg_out_row(a.seg, a.ray_row[e]);
         if (row_out < 0) {
             // rays outside the arm contribute nothing: their zhat rows are zero
-            float* zo = a.zhat + (int64_t)e * a.K * a.Bc;
-            for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = 0.0f;
+            T* zo = a.zhat + (int64_t)e * a.K * a.Bc;
+            for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = T(0);
             continue;
         }
         const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
-        const float* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
+        const double F64 = exact_frac(a, (int)e);
+        const T* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
         for (int kg0 = 0; kg0 < a.K; kg0 += 32) {
             const int kg1 = min(kg0 + 31, a.K - 1);
             // frames with (kg0 - 1) 2^24 <= U(f) < (kg1 + 1) 2^24, found from a float
@@ -613,24 +460,24 @@ adj_time3_kernel(const ApplyArgs<float> a) {
             while (fB >= 0 && U0 - (int64_t)fB * a.D < loX) --fB;
             const int nfr = fB >= fA ? fB - fA + 1 : 0;
             if (vec) {
-                float4* ys4 = reinterpret_cast<float4*>(ys);
+                V* ysv = reinterpret_cast<V*>(ys);
                 for (int o = lane; o < nfr * Q; o += 32) {
                     const int fl = o / Q, q = o - fl * Q;
-                    ys4[swz(fl, q, Q, P)] =
-                        __ldg(reinterpret_cast<const float4*>(yrow + (int64_t)(fA + fl) * a.B) + q);
+                    ysv[swz(fl, q, Q, P)] =
+                        __ldg(reinterpret_cast<const V*>(yrow + (int64_t)(fA + fl) * a.B) + q);
                 }
             } else {
                 for (int o = lane; o < nfr * BC; o += 32) {
                     const int fl = o / BC, bb = o - fl * BC;
-                    ys[o] = bb < a.Bc ? yrow[(int64_t)(fA + fl) * a.B + bb] : 0.0f;
+                    ys[o] = bb < a.Bc ? yrow[(int64_t)(fA + fl) * a.B + bb] : T(0);
                 }
             }
             __syncwarp();
             const int k = kg0 + lane;
             if (k <= kg1) {
-                float acc[BC];
+                T acc[BC];
 #pragma unroll
-                for (int b = 0; b < BC; ++b) acc[b] = 0.0f;
+                for (int b = 0; b < BC; ++b) acc[b] = T(0);
                 const int64_t hi_excl = (int64_t)(k + 1) * kFracOne;
                 const int64_t lo_incl = (int64_t)(k - 1) * kFracOne;
                 const float est = (float)(U0 - hi_excl) * invD;
@@ -639,30 +486,31 @@ adj_time3_kernel(const ApplyArgs<float> a) {
                 while (f <= fB && U >= hi_excl) { ++f; U -= a.D; }
                 for (; f <= fB && U >= lo_incl; ++f, U -= a.D) {
                     const int k0 = (int)(U >> kFracBits);
-                    const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
-                    const float hw = (k0 == k) ? 1.0f - fr : fr;
+                    const T fr = frac_of<T>(U, f, a.D, F64);
+                    const T hw = (k0 == k) ? T(1) - fr : fr;
                     if (vec) {
-                        const float4* ys4 = reinterpret_cast<const float4*>(ys);
+                        const V* ysv = reinterpret_cast<const V*>(ys);
 #pragma unroll
                         for (int q = 0; q < Q; ++q) {
-                            const float4 t = ys4[swz(f - fA, q, Q, P)];
-                            acc[4 * q + 0] += hw * t.x;
-                            acc[4 * q + 1] += hw * t.y;
-                            acc[4 * q + 2] += hw * t.z;
-                            acc[4 * q + 3] += hw * t.w;
+                            const V t = ysv[swz(f - fA, q, Q, P)];
+#pragma unroll
+                            for (int c = 0; c < VW; ++c) acc[VW * q + c] += hw * comps<T>(t)[c];
                         }
                     } else {
-                        const float* yv = ys + (f - fA) * BC;
+                        const T* yv = ys + (f - fA) * BC;
 #pragma unroll
                         for (int b = 0; b < BC; ++b) acc[b] += hw * yv[b];
                     }
                 }
-                float* zo = a.zhat + ((int64_t)e * a.K + k) * a.Bc;
+                T* zo = a.zhat + ((int64_t)e * a.K + k) * a.Bc;
                 if (vec) {
 #pragma unroll
-                    for (int q = 0; q < Q; ++q)
-                        reinterpret_cast<float4*>(zo)[q] =
-                            make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+                    for (int q = 0; q < Q; ++q) {
+                        V o;
+#pragma unroll
+                        for (int c = 0; c < VW; ++c) comps<T>(o)[c] = acc[VW * q + c];
+                        reinterpret_cast<V*>(zo)[q] = o;
+                    }
                 } else {
 #pragma unroll
                     for (int b = 0; b < BC; ++b)
@@ -674,11 +522,23 @@ adj_time3_kernel(const ApplyArgs<float> a) {
     }
 }
 
-// Adjoint phase 2, FP32 fast path: lanes over (hat, batch) of one node; the
-// incidence loop is unrolled by 4 so that four zhat rows are in flight.
-template <int BC>
+// Adjoint phase 2, fast path: lanes over (hat, batch) of one node, nodes in
+// descending-load order; the incidence loop is unrolled by 4 so that four
+// zhat rows are in flight.
+template <typename T>
+__device__ __forceinline__ T corner_coef(const ApplyArgs<T>& a, int code);
+template <>
+__device__ __forceinline__ float corner_coef<float>(const ApplyArgs<float>& a, int code) {
+    return reinterpret_cast<const float*>(a.W)[code];  // W[e] component c = element 4e + c
+}
+template <>
+__device__ __forceinline__ double corner_coef<double>(const ApplyArgs<double>& a, int code) {
+    return a.W64[code];
+}
+
+template <typename T, int BC>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
-adj_space3_kernel(const ApplyArgs<float> a) {
+adj_space3_kernel(const ApplyArgs<T> a) {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
@@ -686,9 +546,9 @@ adj_space3_kernel(const ApplyArgs<float> a) {
         const int kchunk = (int)(task % a.n_kchunk);
         const int node = a.node_order ? a.node_order[task / a.n_kchunk] : (int)(task / a.n_kchunk);
         const int k_begin = kchunk * a.KC;
-        float acc[kAdjOutPerLane];
+        T acc[kAdjOutPerLane];
 #pragma unroll
-        for (int j = 0; j < kAdjOutPerLane; ++j) acc[j] = 0.0f;
+        for (int j = 0; j < kAdjOutPerLane; ++j) acc[j] = T(0);
         int off[kAdjOutPerLane];
         bool live[kAdjOutPerLane];
 #pragma unroll
@@ -700,24 +560,22 @@ adj_space3_kernel(const ApplyArgs<float> a) {
             off[j] = k * a.Bc + bb;
         }
         const int i_begin = a.node_ptr[node], i_end = a.node_ptr[node + 1];
-        const float* wf = reinterpret_cast<const float*>(a.W);
         int ii = i_begin;
         for (; ii + 4 <= i_end; ii += 4) {
             int code[4];
-            float coef[4];
-            const float* zr[4];
+            T coef[4];
+            const T* zr[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) code[u] = a.inc[ii + u];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int e = code[u] >> 2;
-                coef[u] = wf[code[u]];  // W[e] component c = element 4e + c
-                zr[u] = a.zhat + (int64_t)e * a.K * a.Bc;
+                coef[u] = corner_coef(a, code[u]);
+                zr[u] = a.zhat + (int64_t)(code[u] >> 2) * a.K * a.Bc;
             }
 #pragma unroll
             for (int j = 0; j < kAdjOutPerLane; ++j) {
                 if (!live[j]) continue;
-                float v0 = zr[0][off[j]], v1 = zr[1][off[j]], v2 = zr[2][off[j]], v3 = zr[3][off[j]];
+                const T v0 = zr[0][off[j]], v1 = zr[1][off[j]], v2 = zr[2][off[j]], v3 = zr[3][off[j]];
                 acc[j] += coef[0] * v0;
                 acc[j] += coef[1] * v1;
                 acc[j] += coef[2] * v2;
@@ -726,9 +584,8 @@ adj_space3_kernel(const ApplyArgs<float> a) {
         }
         for (; ii < i_end; ++ii) {
             const int code = a.inc[ii];
-            const int e = code >> 2;
-            const float coef = wf[code];
-            const float* zr = a.zhat + (int64_t)e * a.K * a.Bc;
+            const T coef = corner_coef(a, code);
+            const T* zr = a.zhat + (int64_t)(code >> 2) * a.K * a.Bc;
 #pragma unroll
             for (int j = 0; j < kAdjOutPerLane; ++j)
                 if (live[j]) acc[j] += coef * zr[off[j]];
@@ -789,9 +646,10 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
 }
 
 template <typename T, int BC>
-static cudaError_t launch_fwd_bc(ApplyArgs<T> a, cudaStream_t st) {
-    a.FC = kOutPerLane * 32 / BC;
-    a.vec4 = (a.B % 4 == 0) ? 1 : 0;
+static cudaError_t launch_fwd3_bc(ApplyArgs<T> a, cudaStream_t st) {
+    constexpr int FPL = BC >= 32 ? 1 : 32 / BC;
+    a.FC = 32 * FPL;
+    a.vec4 = (a.B % Vec16<T>::W == 0) ? 1 : 0;
     a.zwin = (int)ceil((a.FC - 1) * a.delta) + 3;
     a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
     a.n_bchunk = (a.B + BC - 1) / BC;
@@ -799,50 +657,11 @@ static cudaError_t launch_fwd_bc(ApplyArgs<T> a, cudaStream_t st) {
     if (a.n_tasks == 0) return cudaSuccess;
     const size_t smem = (size_t)kWarpsPerBlock * a.zwin * BC * sizeof(T);
     if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(fwd_kernel<T, BC>,
+        cudaError_t err = cudaFuncSetAttribute(fwd3_kernel<T, BC>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
     }
-    fwd_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <typename T, int BC>
-static cudaError_t launch_adj_bc(ApplyArgs<T> a, cudaStream_t st) {
-    // a.in / a.out / a.B describe the full batch; this launch covers batch
-    // entries [b_first, b_first + a.Bc) through the zhat scratch.
-    a.KC = kAdjOutPerLane * 32 / BC;
-    a.n_kchunk = (a.K + a.KC - 1) / a.KC;
-    a.n_bchunk = 1;
-    a.n_tasks = (int64_t)a.n_rays_total * a.n_kchunk;
-    if (a.n_tasks > 0 && a.seg.total > 0) {
-        adj_time_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    a.n_tasks = (int64_t)a.n_nodes * a.n_kchunk;
-    if (a.n_tasks == 0) return cudaSuccess;
-    adj_space_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-template <int BC>
-static cudaError_t launch_fwd3_bc(ApplyArgs<float> a, cudaStream_t st) {
-    constexpr int FPL = BC >= 32 ? 1 : 32 / BC;
-    a.FC = 32 * FPL;
-    a.vec4 = (a.B % 4 == 0) ? 1 : 0;
-    a.zwin = (int)ceil((a.FC - 1) * a.delta) + 3;
-    a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
-    a.n_bchunk = (a.B + BC - 1) / BC;
-    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk * a.n_bchunk;
-    if (a.n_tasks == 0) return cudaSuccess;
-    const size_t smem = (size_t)kWarpsPerBlock * a.zwin * BC * sizeof(float);
-    if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(fwd3_kernel<BC>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-    }
-    fwd3_kernel<BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
+    fwd3_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -850,45 +669,34 @@ template <typename T>
 cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const ArmSeg& seg,
                            cudaStream_t st) {
     ApplyArgs<T> a = base_args<T>(op, x, y, B, seg);
-    if constexpr (sizeof(T) == 4) {
-        switch (pick_bc(B)) {
-            case 1: return launch_fwd3_bc<1>(a, st);
-            case 2: return launch_fwd3_bc<2>(a, st);
-            case 4: return launch_fwd3_bc<4>(a, st);
-            case 8: return launch_fwd3_bc<8>(a, st);
-            case 16: return launch_fwd3_bc<16>(a, st);
-            default: return launch_fwd3_bc<32>(a, st);
-        }
-    } else {
-        switch (pick_bc(B)) {
-            case 1: return launch_fwd_bc<T, 1>(a, st);
-            case 2: return launch_fwd_bc<T, 2>(a, st);
-            case 4: return launch_fwd_bc<T, 4>(a, st);
-            case 8: return launch_fwd_bc<T, 8>(a, st);
-            case 16: return launch_fwd_bc<T, 16>(a, st);
-            default: return launch_fwd_bc<T, 32>(a, st);
-        }
+    switch (pick_bc(B)) {
+        case 1: return launch_fwd3_bc<T, 1>(a, st);
+        case 2: return launch_fwd3_bc<T, 2>(a, st);
+        case 4: return launch_fwd3_bc<T, 4>(a, st);
+        case 8: return launch_fwd3_bc<T, 8>(a, st);
+        case 16: return launch_fwd3_bc<T, 16>(a, st);
+        default: return launch_fwd3_bc<T, 32>(a, st);
     }
 }
 
-// FP32 adjoint: fast phase 1 when the frames of a 32-hat group fit the
-// staging buffer, otherwise the general per-(hat, batch) kernel.
-template <int BC>
-static cudaError_t launch_adj3_bc(ApplyArgs<float> a, cudaStream_t st) {
+// Adjoint: fast phase 1 when the frames of a 32-hat group fit the staging
+// buffer, otherwise the general per-(hat, batch) kernel; then the gather.
+template <typename T, int BC>
+static cudaError_t launch_adj3_bc(ApplyArgs<T> a, cudaStream_t st) {
     // staged frames per 32-hat group, rounded so the swizzle stays in bounds
     int ywin = (int)ceil(33.0 / a.delta) + 2;
     ywin = (ywin + 7) & ~7;
-    const size_t smem = (size_t)kAdj3Warps * ywin * BC * sizeof(float);
+    const size_t smem = (size_t)kAdj3Warps * ywin * BC * sizeof(T);
     cudaError_t e = cudaSuccess;
     if (a.seg.total > 0) {
         if (smem <= 96 * 1024) {
-            ApplyArgs<float> t = a;
+            ApplyArgs<T> t = a;
             t.zwin = ywin;
             t.FC = (int)fmax(1.0, floor(1.0 / a.delta + 0.5));  // frames per hat step
-            t.vec4 = (a.B % 4 == 0) ? 1 : 0;
+            t.vec4 = (a.B % Vec16<T>::W == 0) ? 1 : 0;
             t.n_tasks = a.n_rays_total;
             if (smem > 48 * 1024) {
-                e = cudaFuncSetAttribute(adj_time3_kernel<BC>,
+                e = cudaFuncSetAttribute(adj_time3_kernel<T, BC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
                 if (e != cudaSuccess) return e;
             }
@@ -897,15 +705,15 @@ static cudaError_t launch_adj3_bc(ApplyArgs<float> a, cudaStream_t st) {
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             const int grid = (int)(want < (int64_t)sms * 32 ? (want > 0 ? want : 1) : (int64_t)sms * 32);
-            adj_time3_kernel<BC><<<grid, kAdj3Warps * 32, smem, st>>>(t);
+            adj_time3_kernel<T, BC><<<grid, kAdj3Warps * 32, smem, st>>>(t);
             e = cudaGetLastError();
         } else {
-            ApplyArgs<float> t = a;
+            ApplyArgs<T> t = a;
             t.KC = kAdjOutPerLane * 32 / BC;
             t.n_kchunk = (a.K + t.KC - 1) / t.KC;
             t.n_bchunk = 1;
             t.n_tasks = a.n_rays_total * t.n_kchunk;
-            adj_time_kernel<float, BC><<<grid_for(t.n_tasks), kWarpsPerBlock * 32, 0, st>>>(t);
+            adj_time_kernel<T, BC><<<grid_for(t.n_tasks), kWarpsPerBlock * 32, 0, st>>>(t);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) return e;
@@ -915,7 +723,7 @@ static cudaError_t launch_adj3_bc(ApplyArgs<float> a, cudaStream_t st) {
     a.n_bchunk = 1;
     a.n_tasks = (int64_t)a.n_nodes * a.n_kchunk;
     if (a.n_tasks == 0) return cudaSuccess;
-    adj_space3_kernel<BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+    adj_space3_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -943,21 +751,21 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
                 cudaGetLastError();  // clear the "not supported" marker
             }
             switch (pick_bc(Bc)) {
-                case 1: e = launch_adj3_bc<1>(a, st); break;
-                case 2: e = launch_adj3_bc<2>(a, st); break;
-                case 4: e = launch_adj3_bc<4>(a, st); break;
-                case 8: e = launch_adj3_bc<8>(a, st); break;
-                case 16: e = launch_adj3_bc<16>(a, st); break;
-                default: e = launch_adj3_bc<32>(a, st); break;
+                case 1: e = launch_adj3_bc<T, 1>(a, st); break;
+                case 2: e = launch_adj3_bc<T, 2>(a, st); break;
+                case 4: e = launch_adj3_bc<T, 4>(a, st); break;
+                case 8: e = launch_adj3_bc<T, 8>(a, st); break;
+                case 16: e = launch_adj3_bc<T, 16>(a, st); break;
+                default: e = launch_adj3_bc<T, 32>(a, st); break;
             }
         } else {
             switch (pick_bc(Bc)) {
-                case 1: e = launch_adj_bc<T, 1>(a, st); break;
-                case 2: e = launch_adj_bc<T, 2>(a, st); break;
-                case 4: e = launch_adj_bc<T, 4>(a, st); break;
-                case 8: e = launch_adj_bc<T, 8>(a, st); break;
-                case 16: e = launch_adj_bc<T, 16>(a, st); break;
-                default: e = launch_adj_bc<T, 32>(a, st); break;
+                case 1: e = launch_adj3_bc<T, 1>(a, st); break;
+                case 2: e = launch_adj3_bc<T, 2>(a, st); break;
+                case 4: e = launch_adj3_bc<T, 4>(a, st); break;
+                case 8: e = launch_adj3_bc<T, 8>(a, st); break;
+                case 16: e = launch_adj3_bc<T, 16>(a, st); break;
+                default: e = launch_adj3_bc<T, 32>(a, st); break;
             }
         }
         if (e != cudaSuccess) return e;

@@ -15,6 +15,8 @@ using namespace rtt;
 
 extern "C" rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q, int d, double* G,
                                void* stream);
+extern "C" rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q, int d, double* G,
+                                      void* stream);
 extern "C" rtt_status rtt_eig_sym(int n, double* A, double* evals_host, double* V, int max_sweeps,
                                   int* sweeps_host, void* stream);
 extern "C" rtt_status rtt_probe_info(rtt_op op, int arm_mask, int n_ages, const double* ages,
@@ -27,8 +29,10 @@ extern "C" rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const doubl
 extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_dev,
                                      int d, const int* arm_masks, int n_arms, int n_ages,
                                      const double* ages_host, double h, double quantile,
-                                     rtt_audit_record* out, double* sigma_out, void* stream) {
+                                     int gram_mode, rtt_audit_record* out, double* sigma_out,
+                                     void* stream) {
     if (!ops || n_ops < 1 || !Q_dev || d < 1 || d > 4096 || !arm_masks || n_arms < 1 ||
+        (gram_mode != RTT_GRAM_DATA && gram_mode != RTT_GRAM_NORMAL) ||
         n_ages < 1 || n_ages > 256 || !ages_host || !(h > 0.0) || !(quantile > 0.0) || !out) {
         set_error("invalid rank-audit arguments");
         return RTT_EINVAL;
@@ -66,7 +70,8 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
                           nullptr);
             if (s != RTT_OK) break;
             r.reach = rr;
-            s = rtt_gram(op, arm_masks[ai], Q_dev[g], d, G, stream);
+            s = gram_mode == RTT_GRAM_NORMAL ? rtt_gram_normal(op, arm_masks[ai], Q_dev[g], d, G, stream)
+                                             : rtt_gram(op, arm_masks[ai], Q_dev[g], d, G, stream);
             if (s != RTT_OK) break;
             int sweeps = 0;
             s = rtt_eig_sym(d, G, ev.data(), V, 80, &sweeps, stream);

@@ -10,6 +10,7 @@
 // adds P_chunk^T P_chunk.  Partial sums over fixed row splits are reduced in
 // a fixed order (deterministic).  The eigendecomposition is a parallel
 // cyclic two-sided Jacobi method (round-robin pair ordering) in one CTA.
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -21,6 +22,30 @@ namespace rtt {
 
 template <typename T>
 cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
+template <typename T>
+cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
+rtt_status ensure_zhat_bytes(rtt_op_s* op, size_t bytes);
+
+// dst[n][j] = Q[n][c0 + j], j < w
+__global__ void copy_cols(const double* Q, int64_t n, int d, int c0, int w, double* dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * w) return;
+    const int64_t row = t / w;
+    const int j = (int)(t - row * w);
+    dst[t] = Q[row * d + c0 + j];
+}
+
+// G <- (G + G^T) / 2
+__global__ void symmetrize(double* G, int d) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)d * d) return;
+    const int i = (int)(t / d), j = (int)(t - (int64_t)i * d);
+    if (i < j) {
+        const double v = 0.5 * (G[(int64_t)i * d + j] + G[(int64_t)j * d + i]);
+        G[(int64_t)i * d + j] = v;
+        G[(int64_t)j * d + i] = v;
+    }
+}
 
 constexpr int kGT = 32;        // Gram tile edge
 constexpr int kGramSplits = 64;  // row splits per chunk (partial sums)
@@ -272,6 +297,67 @@ extern "C" rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q, int d, 
     cudaFree(d_tiles);
     if (e != cudaSuccess) {
         set_error("gram: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? RTT_ENOMEM : RTT_ECUDA;
+    }
+    return RTT_OK;
+}
+
+// G = Q^T (A^T (A Q)) through the normal operator, FP64 throughout: the
+// contraction runs over the n_nodes * n_hats source coefficients instead of
+// the rows * frames data samples (about 18x fewer at kerr256 sizes), which is
+// what makes an FP64-accurate Gram affordable on FP64-poor hardware.
+extern "C" rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q, int d, double* G,
+                                      void* stream) {
+    if (!op || !Q || !G || d < 1 || d > 4096) {
+        set_error("invalid gram arguments (d=%d)", d);
+        return RTT_EINVAL;
+    }
+    ArmSeg seg;
+    rtt_status s = make_seg(op, arm_mask, &seg);
+    if (s != RTT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int W = 32;  // columns per pass
+    const int64_t N = (int64_t)op->n_nodes * op->time.n_hats;
+    const int64_t M = (int64_t)seg.total * op->time.n_frames;
+    s = ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * W * sizeof(double));
+    if (s != RTT_OK) return s;
+    double *Qc = nullptr, *Y = nullptr, *Z = nullptr;
+    cudaError_t e = cudaMalloc(&Qc, (size_t)N * W * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&Y, (size_t)(M > 0 ? M : 1) * W * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&Z, (size_t)N * W * 8);
+    cublasHandle_t h = nullptr;
+    if (e == cudaSuccess && cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
+        cudaFree(Qc);
+        cudaFree(Y);
+        cudaFree(Z);
+        set_error("cublasCreate failed");
+        return RTT_ECUDA;
+    }
+    if (h) cublasSetStream(h, st);
+    cublasStatus_t cs = CUBLAS_STATUS_SUCCESS;
+    const double one = 1.0, zero = 0.0;
+    for (int c0 = 0; e == cudaSuccess && cs == CUBLAS_STATUS_SUCCESS && c0 < d; c0 += W) {
+        const int w = d - c0 < W ? d - c0 : W;
+        copy_cols<<<(int)((N * w + 255) / 256), 256, 0, st>>>(Q, N, d, c0, w, Qc);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = launch_forward<double>(op, Qc, Y, w, seg, st);
+        if (e == cudaSuccess) e = launch_adjoint<double>(op, Y, Z, w, seg, (double*)op->zhat, st);
+        // rows c0 .. c0+w of G (symmetric): column-major (d x w) = Q_cm (d x N) Z_cm^T (N x w)
+        if (e == cudaSuccess)
+            cs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, d, w, (int)N, &one, Q, d, Z, w, &zero,
+                             G + (int64_t)c0 * d, d);
+    }
+    if (e == cudaSuccess && cs == CUBLAS_STATUS_SUCCESS) {
+        symmetrize<<<(int)(((int64_t)d * d + 255) / 256), 256, 0, st>>>(G, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (h) cublasDestroy(h);
+    cudaFree(Qc);
+    cudaFree(Y);
+    cudaFree(Z);
+    if (e != cudaSuccess || cs != CUBLAS_STATUS_SUCCESS) {
+        set_error("gram (normal operator): cuda %s, cublas %d", cudaGetErrorString(e), (int)cs);
         return e == cudaErrorMemoryAllocation ? RTT_ENOMEM : RTT_ECUDA;
     }
     return RTT_OK;

@@ -116,10 +116,11 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_int), dp, vp]),
     "rtt_solve_tsvd": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, dp, ctypes.c_int, vp,
                                       ctypes.c_int, vp, vp]),
+    "rtt_gram_normal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
     "rtt_rank_audit": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                       ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
-                                      ctypes.POINTER(AuditRecord), dp, vp]),
+                                      ctypes.c_int, ctypes.POINTER(AuditRecord), dp, vp]),
     "rtt_destroy": (None, [vp]),
 }
 
@@ -302,14 +303,20 @@ def reach(op: "Operator", info, arm_mask: int = 7, ages=AGES, h: float = 3.0, a0
     return res, passed.astype(bool)
 
 
-def gram(op: "Operator", Q, arm_mask: int = 7, stream=None):
-    """G = P^T P, P = scale A_arm Q; Q: CUDA float64 [n_nodes, n_hats, d]."""
+GRAM_DATA = 0
+GRAM_NORMAL = 1
+
+
+def gram(op: "Operator", Q, arm_mask: int = 7, mode: int = GRAM_DATA, stream=None):
+    """G = P^T P, P = scale A_arm Q; Q: CUDA float64 [n_nodes, n_hats, d].
+    mode GRAM_DATA: over data samples; GRAM_NORMAL: Q^T A^T A Q."""
     import torch
     assert Q.is_cuda and Q.dtype == torch.float64 and Q.is_contiguous() and Q.dim() == 3
     d = Q.shape[2]
     G = torch.empty((d, d), dtype=torch.float64, device=Q.device)
-    check(lib().rtt_gram(op.handle, arm_mask, ctypes.c_void_p(Q.data_ptr()), d,
-                         ctypes.c_void_p(G.data_ptr()), _stream(stream)), "rtt_gram")
+    name = "rtt_gram" if mode == GRAM_DATA else "rtt_gram_normal"
+    check(getattr(lib(), name)(op.handle, arm_mask, ctypes.c_void_p(Q.data_ptr()), d,
+                               ctypes.c_void_p(G.data_ptr()), _stream(stream)), name)
     return G
 
 
@@ -328,10 +335,11 @@ def eig_sym(G, max_sweeps: int = 60, stream=None):
     return ev[order], V[:, torch.from_numpy(order).to(V.device)], sw.value
 
 
-def operational_rank(op: "Operator", Q, arm_mask: int = 7, rho: float = 1.0):
+def operational_rank(op: "Operator", Q, arm_mask: int = 7, rho: float = 1.0,
+                     mode: int = GRAM_DATA):
     """sigma_i = sqrt(max(lambda_i, 0)) of the restricted Gram; rank = #{sigma >= rho}
     (Eq. 31; scale already carries SNR_0)."""
-    G = gram(op, Q, arm_mask)
+    G = gram(op, Q, arm_mask, mode)
     ev, V, _ = eig_sym(G)
     sig = np.sqrt(np.maximum(ev, 0.0))
     return sig, int(np.count_nonzero(sig >= rho))
@@ -376,7 +384,7 @@ def solve_tsvd(op: "Operator", Q, V, evals, rank: int, data, arm_mask: int = 7, 
 
 
 def rank_audit(ops, Qs, arm_masks=(1, 7), ages=AGES, h: float = 3.0, quantile: float = 0.999,
-               stream=None):
+               mode: int = GRAM_NORMAL, stream=None):
     """rtt_rank_audit over several operators; Qs: CUDA float64 [n_nodes, n_hats, d] each.
     Returns (records [n_ops][n_arms], sigma [n_ops, n_arms, d])."""
     n = len(ops)
@@ -388,7 +396,8 @@ def rank_audit(ops, Qs, arm_masks=(1, 7), ages=AGES, h: float = 3.0, quantile: f
     recs = (AuditRecord * (n * len(arm_masks)))()
     sig = np.empty((n, len(arm_masks), d))
     check(lib().rtt_rank_audit(arr_ops, n, arr_q, d, arms, len(arm_masks), ages.shape[0],
-                               _ptr(ages, dp), h, quantile, recs, _ptr(sig, dp), _stream(stream)),
+                               _ptr(ages, dp), h, quantile, mode, recs, _ptr(sig, dp),
+                               _stream(stream)),
           "rtt_rank_audit")
     out = [[recs[g * len(arm_masks) + a] for a in range(len(arm_masks))] for g in range(n)]
     return out, sig

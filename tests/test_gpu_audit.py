@@ -133,3 +133,53 @@ def test_tsvd_matches_oracle():
     xh = rtt.solve_tsvd(op, Qd, V, ev, rank, torch.from_numpy(data).cuda()).cpu().numpy()
     err = np.linalg.norm(xh - ref) / np.linalg.norm(ref)
     assert err < 1e-8, err
+
+
+def test_gram_normal_operator_matches_oracle(case):
+    """G = Q^T A^T A Q (normal-operator route, FP64) equals the oracle's P^T P."""
+    w, tab, op = case
+    scl = O.scale(tab)
+    Q = O.synth_class(w, "S224")
+    Qd = torch.from_numpy(Q.reshape(w.grid.n_nodes, w.time.n_hats, -1).copy()).cuda()
+    for mask, orders in ((1, (0,)), (7, (0, 1, 2))):
+        G_ref = O.gram(O.restricted_response(w, tab.select(orders), Q, scl))
+        G = rtt.gram(op, Qd, mask, mode=rtt.GRAM_NORMAL).cpu().numpy()
+        assert np.max(np.abs(G - G_ref)) <= 1e-11 * np.max(np.abs(G_ref))
+        assert np.array_equal(G, G.T)
+
+
+def test_rank_audit_driver_matches_oracle():
+    """rtt_rank_audit over two geometries and two arms: rank, reach, J_old and
+    A_0.999 against the oracle's audit of the same tables."""
+    build.build()
+    ws = [I.small_kerr(spin=0.0, incl_deg=20.0, nx=40, n_r=10, n_phi=20, n_frames=80, n_hats=20),
+          I.small_kerr(spin=0.5, incl_deg=50.0, nx=40, n_r=10, n_phi=20, n_frames=80, n_hats=20)]
+    ops, Qs, refs = [], [], []
+    for w in ws:
+        tab = O.build_table(w, I.screen_samples(w))
+        ops.append(rtt.Operator(w, {"order": tab.order, "pixel": tab.pixel, "r": tab.r,
+                                    "phi": tab.phi, "delay": tab.delay, "weight": tab.weight,
+                                    "throughput": tab.throughput}))
+        Q = O.synth_class(w, "S224")
+        Qs.append(torch.from_numpy(Q.reshape(w.grid.n_nodes, w.time.n_hats, -1).copy()).cuda())
+        scl = O.scale(tab)
+        a0 = O.a0999(w, tab)
+        per_arm = []
+        for orders in ((0,), (0, 1, 2)):
+            info = O.probe_info(w, tab.select(orders), scl)
+            rr = O.reach(w, tab, info, orders)
+            spec = O.operational_rank(O.gram(O.restricted_response(w, tab.select(orders), Q, scl)))
+            per_arm.append((rr, O.j_old(info, a0), spec, a0))
+        refs.append(per_arm)
+    for mode in (rtt.GRAM_DATA, rtt.GRAM_NORMAL):
+        recs, sig = rtt.rank_audit(ops, Qs, (1, 7), mode=mode)
+        for g in range(2):
+            for a in range(2):
+                rr, jo, spec, a0 = refs[g][a]
+                r = recs[g][a]
+                if spec.margin > 1e-6:
+                    assert r.rank == spec.rank
+                assert np.allclose(sig[g, a, :10], spec.sigma[:10], rtol=1e-9)
+                assert r.reach.L_anchor == rr.L_anchor
+                assert r.reach.A0q == pytest.approx(a0, abs=1e-9)
+                assert r.reach.J_old == pytest.approx(jo, rel=1e-5)
