@@ -251,6 +251,53 @@ def run_ours(args, rank, world, device):
     return out
 
 
+def run_audit(device):
+    """The 12-geometry rank audit (Sec. 6.2-6.3): spins {0, .5, .75, .94} x
+    inclinations {20, 50, 75} deg at kerr256 sizes, S224 class, direct and
+    resolved arms.  Times the audit with the FP64 Gram through the normal
+    operator against the plain FP64 path (Gram over data samples)."""
+    import torch
+
+    from paper_2609_05528_b300 import inputs as I
+    from paper_2609_05528_b300 import rtt
+    t0 = time.perf_counter()
+    ops, Qs = [], []
+    for w in I.audit12():
+        tab = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, I.screen_samples(w))
+        op = rtt.Operator(w, tab)
+        ops.append(op)
+        Qs.append(rtt.synth_class(op, rtt.CLASS_S224))
+    torch.cuda.synchronize(device)
+    t_build = time.perf_counter() - t0
+    out = {"workload": "12 geometries: spins {0,0.5,0.75,0.94} x incl {20,50,75} deg, kerr256 sizes, "
+                       "S224 class, arms direct/resolved, SNR0=100, rho=1",
+           "trace_and_build_s": t_build}
+    runs = {}
+    for name, mode in (("normal", rtt.GRAM_NORMAL), ("data", rtt.GRAM_DATA)):
+        torch.cuda.synchronize(device)
+        t = time.perf_counter()
+        recs, sig = rtt.rank_audit(ops, Qs, (1, 7), mode=mode)
+        torch.cuda.synchronize(device)
+        runs[name] = (time.perf_counter() - t, recs)
+    tn, rn = runs["normal"]
+    td, rd = runs["data"]
+    out["seconds"] = tn
+    out["fp64_data_path_seconds"] = td
+    out["speedup_vs_fp64_data_path"] = td / tn
+    out["rank_direct"] = [r[0].rank for r in rn]
+    out["rank_resolved"] = [r[1].rank for r in rn]
+    out["L_anchor_direct"] = [r[0].reach.L_anchor for r in rn]
+    out["L_anchor_resolved"] = [r[1].reach.L_anchor for r in rn]
+    out["J_old_direct"] = [round(r[0].reach.J_old, 3) for r in rn]
+    out["J_old_resolved"] = [round(r[1].reach.J_old, 3) for r in rn]
+    out["min_rank_margin"] = min(min(r[0].margin, r[1].margin) for r in rn)
+    out["ranks_agree_between_paths"] = all(a[i].rank == b[i].rank for a, b in zip(rn, rd)
+                                           for i in range(2))
+    for op in ops:
+        op.close()
+    return out
+
+
 def oracle_pairs_per_s(w, budget_s: float = 12.0, B: int = 1):
     """Time the FP64 CPU oracle (as it stands) on A + A^T for one history."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
@@ -280,6 +327,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-audit", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -317,6 +365,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     device = torch.device("cuda", local)
     out = run_ours(args, rank, world, device)
+    if rank == 0 and world == 1 and not args.no_audit:
+        out["audit"] = run_audit(device)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             v, cores, n = oracle_pairs_per_s(I.kerr256())

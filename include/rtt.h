@@ -283,6 +283,21 @@ rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const double* ages_hos
                      const double* info_host, double h, double a0q, double age_step,
                      rtt_reach_result* out, uint8_t* pass_host);
 
+#define RTT_CLASS_S224 0 /* Eq. 8: 4 radial B-splines x 7 azimuthal x 8 DCT-II */
+#define RTT_CLASS_L224 1 /* Sec. 7: the temporal DCT modes replaced by 8 hats */
+
+/*
+ * rtt_synth_class -- the 224-column representation class at the operator's
+ * source nodes (Sec. 3.2 Eq. 5-8; Sec. 7): Q[(s, k)][c] = R_i(r_s)
+ * Phi_l(phi_s) tau_m(t_k), c = (i * 7 + l) * 8 + m, radial cubic B-splines
+ * on uniform knots in log r (no interior knots), azimuthal {1, cos, sin}
+ * up to m = 3, temporal DCT-II modes (S224) or degree-one B-splines (L224)
+ * on the hat window [t_{K-1}, t_0]; columns unnormalised.  Q_dev: double
+ * [n_nodes][n_hats][224], written asynchronously on `stream`.
+ * Errors: RTT_EINVAL (unknown kind, fewer than 2 hats), RTT_ECUDA.
+ */
+rtt_status rtt_synth_class(rtt_op op, int kind, double* Q_dev, void* stream);
+
 /*
  * rtt_gram -- restricted Gram matrix G = P^T P of P = scale * A_arm Q
  * (Sec. 3.2 Eq. 7, Sec. 4.1 Eq. 21): Q_dev is the class synthesis matrix in
@@ -316,6 +331,12 @@ rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q_dev, int d, 
  */
 rtt_status rtt_eig_sym(int n, double* A_dev, double* evals_host, double* V_dev, int max_sweeps,
                        int* sweeps_host, void* stream);
+
+/* rtt_eig_sym on `batch` matrices at once (A_dev, V_dev: batch consecutive
+   n x n blocks; evals_host: batch * n; sweeps_host: batch ints), one CTA per
+   matrix. */
+rtt_status rtt_eig_sym_batched(int n, int batch, double* A_dev, double* evals_host, double* V_dev,
+                               int max_sweeps, int* sweeps_host, void* stream);
 
 /*
  * rtt_solve_ridge -- ridge / Tikhonov estimator (Sec. 9):

@@ -26,6 +26,10 @@ extern "C" rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const doubl
                                 const double* info, double h, double a0q, double age_step,
                                 rtt_reach_result* out, uint8_t* pass);
 
+extern "C" rtt_status rtt_eig_sym_batched(int n, int batch, double* A, double* evals_host,
+                                          double* V, int max_sweeps, int* sweeps_host,
+                                          void* stream);
+
 extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_dev,
                                      int d, const int* arm_masks, int n_arms, int n_ages,
                                      const double* ages_host, double h, double quantile,
@@ -37,19 +41,21 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
         set_error("invalid rank-audit arguments");
         return RTT_EINVAL;
     }
-    cudaStream_t st = (cudaStream_t)stream;
+    const int nb = n_ops * n_arms;
     double *G = nullptr, *V = nullptr;
-    cudaError_t e = cudaMalloc(&G, (size_t)d * d * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&V, (size_t)d * d * 8);
+    cudaError_t e = cudaMalloc(&G, (size_t)nb * d * d * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&V, (size_t)nb * d * d * 8);
     if (e != cudaSuccess) {
         cudaFree(G);
         cudaFree(V);
         set_error("rank audit: allocation failed");
         return RTT_ENOMEM;
     }
-    std::vector<double> info(n_ages), ev(d);
+    std::vector<double> info(n_ages), ev((size_t)nb * d);
+    std::vector<int> sweeps(nb);
     const double age_step = n_ages > 1 ? ages_host[1] - ages_host[0] : 1.0;
     rtt_status s = RTT_OK;
+    // probes, reach and restricted Grams of every (geometry, arm)
     for (int g = 0; g < n_ops && s == RTT_OK; ++g) {
         rtt_op op = ops[g];
         if (!op || !Q_dev[g]) {
@@ -70,17 +76,27 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
                           nullptr);
             if (s != RTT_OK) break;
             r.reach = rr;
-            s = gram_mode == RTT_GRAM_NORMAL ? rtt_gram_normal(op, arm_masks[ai], Q_dev[g], d, G, stream)
-                                             : rtt_gram(op, arm_masks[ai], Q_dev[g], d, G, stream);
-            if (s != RTT_OK) break;
-            int sweeps = 0;
-            s = rtt_eig_sym(d, G, ev.data(), V, 80, &sweeps, stream);
-            if (s != RTT_OK) break;
-            // sigma descending
+            double* Gi = G + ((size_t)g * n_arms + ai) * d * d;
+            s = gram_mode == RTT_GRAM_NORMAL ? rtt_gram_normal(op, arm_masks[ai], Q_dev[g], d, Gi, stream)
+                                             : rtt_gram(op, arm_masks[ai], Q_dev[g], d, Gi, stream);
+            r.s_ref = op->s_ref;
+            r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        }
+    }
+    // all spectra in one batched Jacobi launch (one CTA per matrix)
+    if (s == RTT_OK) {
+        const auto t0 = std::chrono::steady_clock::now();
+        s = rtt_eig_sym_batched(d, nb, G, ev.data(), V, 80, sweeps.data(), stream);
+        const double te = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        for (int b = 0; s == RTT_OK && b < nb; ++b) {
+            rtt_audit_record& r = out[b];
             std::vector<double> sig(d);
-            for (int i = 0; i < d; ++i) sig[i] = std::sqrt(ev[i] > 0.0 ? ev[i] : 0.0);
-            std::sort(sig.begin(), sig.end(), [](double a, double b) { return a > b; });
-            const double rho = op->opt.rho;
+            for (int i = 0; i < d; ++i) {
+                const double l = ev[(size_t)b * d + i];
+                sig[i] = std::sqrt(l > 0.0 ? l : 0.0);
+            }
+            std::sort(sig.begin(), sig.end(), [](double a, double c) { return a > c; });
+            const double rho = ops[b / n_arms]->opt.rho;
             int rank = 0;
             double margin = INFINITY, smin_pos = INFINITY;
             for (int i = 0; i < d; ++i) {
@@ -92,11 +108,10 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
             r.margin = margin;
             r.sigma_max = sig[0];
             r.sigma_min_pos = smin_pos;
-            r.s_ref = op->s_ref;
-            r.jacobi_sweeps = sweeps;
+            r.jacobi_sweeps = sweeps[b];
+            r.seconds += te / nb;
             if (sigma_out)
-                for (int i = 0; i < d; ++i) sigma_out[((size_t)g * n_arms + ai) * d + i] = sig[i];
-            r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                for (int i = 0; i < d; ++i) sigma_out[(size_t)b * d + i] = sig[i];
         }
     }
     cudaFree(G);

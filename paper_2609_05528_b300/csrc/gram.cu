@@ -122,9 +122,13 @@ __global__ void gram_reduce(const double* partial, int n_splits, int n_tiles, co
 // (p, q) is skipped when |a_pq| <= eps sqrt(|a_pp a_qq|) (relative
 // criterion); the sweep loop ends when a sweep performs no rotation.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) jacobi_kernel(double* A, double* V, int n, int np2,
+__global__ void __launch_bounds__(1024) jacobi_kernel(double* A_all, double* V_all, int n, int np2,
                                                       int max_sweeps, double eps,
-                                                      int* sweeps_out) {
+                                                      int* sweeps_all) {
+    // one CTA per matrix of the batch
+    double* A = A_all + (int64_t)blockIdx.x * n * n;
+    double* V = V_all + (int64_t)blockIdx.x * n * n;
+    int* sweeps_out = sweeps_all + blockIdx.x;
     extern __shared__ unsigned char jsm[];
     int* perm = reinterpret_cast<int*>(jsm);                  // np2 players
     double* cs = reinterpret_cast<double*>(perm + np2 + (np2 & 1));  // 6 values per pair
@@ -363,39 +367,48 @@ extern "C" rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q, 
     return RTT_OK;
 }
 
-extern "C" rtt_status rtt_eig_sym(int n, double* A, double* evals_host, double* V, int max_sweeps,
-                                  int* sweeps_host, void* stream) {
-    if (n < 1 || n > 4096 || !A || !evals_host || !V || max_sweeps < 1) {
-        set_error("invalid eig arguments (n=%d)", n);
+extern "C" rtt_status rtt_eig_sym_batched(int n, int batch, double* A, double* evals_host,
+                                          double* V, int max_sweeps, int* sweeps_host,
+                                          void* stream) {
+    if (n < 1 || n > 4096 || batch < 1 || !A || !evals_host || !V || max_sweeps < 1) {
+        set_error("invalid eig arguments (n=%d, batch=%d)", n, batch);
         return RTT_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
     const int np2 = n + (n & 1);
     int* d_sw = nullptr;
-    cudaError_t e = cudaMalloc(&d_sw, 4);
+    cudaError_t e = cudaMalloc(&d_sw, 4 * batch);
     const size_t smem = (size_t)(np2 + 2) * 4 + (size_t)(np2 / 2) * 6 * 8 + 16;
     if (e == cudaSuccess && smem > 48 * 1024)
         e = cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        jacobi_kernel<<<1, 1024, smem, st>>>(A, V, n, np2, max_sweeps, 2.2e-16, d_sw);
+        jacobi_kernel<<<batch, 1024, smem, st>>>(A, V, n, np2, max_sweeps, 2.2e-16, d_sw);
         e = cudaGetLastError();
     }
-    std::vector<double> diag((size_t)n);
-    int sweeps = 0;
-    if (e == cudaSuccess) e = cudaMemcpy2DAsync(diag.data(), 8, A, (size_t)(n + 1) * 8, 8, n,
-                                                cudaMemcpyDeviceToHost, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&sweeps, d_sw, 4, cudaMemcpyDeviceToHost, st);
+    std::vector<int> sweeps(batch);
+    for (int b = 0; e == cudaSuccess && b < batch; ++b)
+        e = cudaMemcpy2DAsync(evals_host + (int64_t)b * n, 8, A + (int64_t)b * n * n,
+                              (size_t)(n + 1) * 8, 8, n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sweeps.data(), d_sw, 4 * batch, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(d_sw);
     if (e != cudaSuccess) {
         set_error("eig: %s", cudaGetErrorString(e));
         return RTT_ECUDA;
     }
-    for (int i = 0; i < n; ++i) evals_host[i] = diag[i];
-    if (sweeps_host) *sweeps_host = sweeps;
-    if (sweeps >= max_sweeps) {
+    bool ok = true;
+    for (int b = 0; b < batch; ++b) {
+        if (sweeps_host) sweeps_host[b] = sweeps[b];
+        ok = ok && sweeps[b] < max_sweeps;
+    }
+    if (!ok) {
         set_error("Jacobi did not converge in %d sweeps", max_sweeps);
         return RTT_ENOTCONVERGED;
     }
     return RTT_OK;
+}
+
+extern "C" rtt_status rtt_eig_sym(int n, double* A, double* evals_host, double* V, int max_sweeps,
+                                  int* sweeps_host, void* stream) {
+    return rtt_eig_sym_batched(n, 1, A, evals_host, V, max_sweeps, sweeps_host, stream);
 }

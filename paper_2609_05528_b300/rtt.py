@@ -111,12 +111,15 @@ _SIGS = {
     "rtt_gram": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
     "rtt_eig_sym": (ctypes.c_int, [ctypes.c_int, vp, dp, vp, ctypes.c_int,
                                    ctypes.POINTER(ctypes.c_int), vp]),
+    "rtt_eig_sym_batched": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, dp, vp, ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int), vp]),
     "rtt_solve_ridge": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, dp, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
                                        ctypes.POINTER(ctypes.c_int), dp, vp]),
     "rtt_solve_tsvd": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, dp, ctypes.c_int, vp,
                                       ctypes.c_int, vp, vp]),
     "rtt_gram_normal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
+    "rtt_synth_class": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
     "rtt_rank_audit": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                       ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
@@ -305,6 +308,17 @@ def reach(op: "Operator", info, arm_mask: int = 7, ages=AGES, h: float = 3.0, a0
 
 GRAM_DATA = 0
 GRAM_NORMAL = 1
+CLASS_S224 = 0
+CLASS_L224 = 1
+
+
+def synth_class(op: "Operator", kind: int = CLASS_S224, stream=None):
+    """Class matrix Q (CUDA float64 [n_nodes, n_hats, 224]) synthesised on the GPU."""
+    import torch
+    Q = torch.empty((op.n_nodes, op.n_hats, 224), dtype=torch.float64, device="cuda")
+    check(lib().rtt_synth_class(op.handle, kind, ctypes.c_void_p(Q.data_ptr()), _stream(stream)),
+          "rtt_synth_class")
+    return Q
 
 
 def gram(op: "Operator", Q, arm_mask: int = 7, mode: int = GRAM_DATA, stream=None):

@@ -183,3 +183,11 @@ def test_rank_audit_driver_matches_oracle():
                 assert r.reach.L_anchor == rr.L_anchor
                 assert r.reach.A0q == pytest.approx(a0, abs=1e-9)
                 assert r.reach.J_old == pytest.approx(jo, rel=1e-5)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_class_synthesis_matches_oracle(case, kind):
+    w, tab, op = case
+    Q_ref = O.synth_class(w, "S224" if kind == 0 else "L224")
+    Q = rtt.synth_class(op, kind).cpu().numpy().reshape(Q_ref.shape)
+    assert np.max(np.abs(Q - Q_ref)) <= 1e-13
