@@ -118,6 +118,31 @@ def build_workload(device):
     return w, tab, op, x
 
 
+def kernel_source_hash() -> str:
+    """Hash of the apply kernels' source: ncu DRAM traffic recorded in
+    profiles/ is used only while this hash is unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("apply.cu", "rtt_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2609_05528_b300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu record, or None
+    when the record is missing or was taken on other kernel sources."""
+    p = os.path.join(ROOT, "profiles", "traffic_kerr256_b8.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    if rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("traffic_bytes", {}).get(kernel)
+
+
 def algorithmic_bytes(op, B, elem=4):
     """Bytes the method must move per launch: y once, x once, plus tables."""
     E = int(op.info.n_rays)
@@ -241,7 +266,8 @@ def run_ours(args, rank, world, device):
         "kernels_ms": {"A": mA, "AT": mAT},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None},
+                     "traffic": recorded_traffic(dom), "algorithmic_bytes": ab[dom],
+                     "source_hash": kernel_source_hash()},
         "e2e": {"value": world * BATCH / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4)},
         "fp64_path": {"value": world * BATCH / (fp64_ms * 1e-3), "ms_per_step": fp64_ms},

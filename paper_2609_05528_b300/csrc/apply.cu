@@ -417,9 +417,9 @@ constexpr int kAdj3Warps = 4;
 // its low three bits XORed with (f / P) mod 8, P = frames per hat step, so
 // the lanes of a warp (one hat each, hats P frames apart) read eight distinct
 // bank groups.
-__device__ __forceinline__ int swz(int f, int q, int Q, int P) {
+__device__ __forceinline__ int swz(int f, int q, int Q, int pshift) {
     const int idx = f * Q + q;
-    return idx ^ ((f / P) & 7);
+    return idx ^ ((f >> pshift) & 7);
 }
 
 template <typename T, int BC>
@@ -434,8 +434,9 @@ adj_time3_kernel(const ApplyArgs<T> a) {
     const int64_t n_warps = (int64_t)gridDim.x * kAdj3Warps;
     const bool vec = (BC >= VW) && a.vec4 && (a.Bc == BC);
     constexpr int Q = BC / VW > 0 ? BC / VW : 1;
-    const int P = a.FC;  // frames per hat step (>= 1), used only for the swizzle
+    const int P = a.FC;  // log2 of frames per hat step, used only for the swizzle
     const float invD = 1.0f / (float)a.D;
+    const int32_t D32 = (int32_t)a.D;  // D <= 2^24
     for (int64_t e = warp_global; e < a.n_tasks; e += n_warps) {
         const int row_out = seg_out_row(a.seg, a.ray_row[e]);
         if (row_out < 0) {
@@ -478,16 +479,25 @@ adj_time3_kernel(const ApplyArgs<T> a) {
                 T acc[BC];
 #pragma unroll
                 for (int b = 0; b < BC; ++b) acc[b] = T(0);
+                // frames with |U(f) - k 2^24| < 2^24 (hat k's support); in that
+                // window Ur = U(f) - k 2^24 fits 32 bits and the hat weight is
+                // 1 - |Ur| 2^-24 exactly (FP32); FP64 uses the exact fraction
                 const int64_t hi_excl = (int64_t)(k + 1) * kFracOne;
-                const int64_t lo_incl = (int64_t)(k - 1) * kFracOne;
                 const float est = (float)(U0 - hi_excl) * invD;
                 int f = (int)fminf(fmaxf(floorf(est) - 1.0f, (float)fA), (float)(fB + 1));
                 int64_t U = U0 - (int64_t)f * a.D;
                 while (f <= fB && U >= hi_excl) { ++f; U -= a.D; }
-                for (; f <= fB && U >= lo_incl; ++f, U -= a.D) {
-                    const int k0 = (int)(U >> kFracBits);
-                    const T fr = frac_of<T>(U, f, a.D, F64);
-                    const T hw = (k0 == k) ? T(1) - fr : fr;
+                int32_t Ur = (int32_t)(U - (int64_t)k * kFracOne);  // in [-2^24, 2^24) once f <= fB
+                for (; f <= fB && Ur > -kFracOne; ++f, Ur -= D32) {
+                    T hw;
+                    if constexpr (sizeof(T) == 4) {
+                        hw = 1.0f - (float)abs(Ur) * (1.0f / (float)kFracOne);
+                    } else {
+                        const int64_t Uf = (int64_t)k * kFracOne + Ur;
+                        const int k0 = (int)(Uf >> kFracBits);
+                        const T fr = frac_of<T>(Uf, f, a.D, F64);
+                        hw = (k0 == k) ? T(1) - fr : fr;
+                    }
                     if (vec) {
                         const V* ysv = reinterpret_cast<const V*>(ys);
 #pragma unroll
@@ -561,12 +571,19 @@ adj_space3_kernel(const ApplyArgs<T> a) {
         }
         const int i_begin = a.node_ptr[node], i_end = a.node_ptr[node + 1];
         int ii = i_begin;
+        // incidence codes of the next group of 4 are loaded before the current
+        // group's zhat rows are consumed (two loads levels in flight)
+        int nxt[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) nxt[u] = (ii + u < i_end) ? a.inc[ii + u] : 0;
         for (; ii + 4 <= i_end; ii += 4) {
             int code[4];
             T coef[4];
             const T* zr[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) code[u] = a.inc[ii + u];
+            for (int u = 0; u < 4; ++u) code[u] = nxt[u];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) nxt[u] = (ii + 4 + u < i_end) ? a.inc[ii + 4 + u] : 0;
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 coef[u] = corner_coef(a, code[u]);
@@ -692,7 +709,12 @@ static cudaError_t launch_adj3_bc(ApplyArgs<T> a, cudaStream_t st) {
         if (smem <= 96 * 1024) {
             ApplyArgs<T> t = a;
             t.zwin = ywin;
-            t.FC = (int)fmax(1.0, floor(1.0 / a.delta + 0.5));  // frames per hat step
+            {
+                // log2 of the frames per hat step (swizzle key only)
+                int ps = 0;
+                while ((2 << ps) <= (int)floor(1.0 / a.delta + 0.5)) ++ps;
+                t.FC = ps;
+            }
             t.vec4 = (a.B % Vec16<T>::W == 0) ? 1 : 0;
             t.n_tasks = a.n_rays_total;
             if (smem > 48 * 1024) {
