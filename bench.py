@@ -272,9 +272,66 @@ def run_ours(args, rank, world, device):
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4)},
         "fp64_path": {"value": world * BATCH / (fp64_ms * 1e-3), "ms_per_step": fp64_ms},
         "clocks": clocks,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": launches_per_step(BATCH) * args.steps,
     }
     return out
+
+
+def launches_per_step(B: int) -> int:
+    """Kernel launches of one A + A^T pair: one forward launch; per 32-column
+    batch chunk one temporal and one spatial adjoint launch."""
+    return 1 + 2 * ((B + 31) // 32)
+
+
+def run_sweep(device, batches=(1, 2, 4, 8, 16, 32, 64), reps: int = 5):
+    """Throughput sweep on the stress1024 workloads (i=75 deg, 1024x1024,
+    256x512 nodes, 256 hats, 1024 frames; Schwarzschild and Kerr a=0.94):
+    A and A^T achieved GB/s (algorithmic bytes / event time) per batch size.
+    y is >= 1.5 GB per history, far above L2, so no flush is needed."""
+    import torch
+
+    from paper_2609_05528_b300 import inputs as I
+    from paper_2609_05528_b300 import rtt
+    peak, peak_kind = measured_peaks()
+    stream = torch.cuda.current_stream(device)
+    lines = []
+    for spin in (0.94, 0.0):
+        w = I.stress1024(spin)
+        tab = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, I.screen_samples(w))
+        op = rtt.Operator(w, tab)
+        R = op.arm_rows(7)
+        gen = torch.Generator(device=device).manual_seed(1)
+        res = []
+        for B in batches:
+            x = torch.rand((op.n_nodes, op.n_hats, B), generator=gen, device=device)
+            y = torch.empty((R, op.n_frames, B), dtype=torch.float32, device=device)
+            g = torch.empty_like(x)
+            for _ in range(2):
+                op.apply_A(x, y)
+                op.apply_AT(y, g)
+            torch.cuda.synchronize(device)
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(reps)]
+            for e0, e1, e2 in ev:
+                e0.record(stream)
+                op.apply_A(x, y)
+                e1.record(stream)
+                op.apply_AT(y, g)
+                e2.record(stream)
+            torch.cuda.synchronize(device)
+            tA = float(np.mean([a.elapsed_time(b) for a, b, _ in ev]))
+            tT = float(np.mean([b.elapsed_time(c) for _, b, c in ev]))
+            ab = algorithmic_bytes(op, B)
+            res.append({"batch": B, "A_ms": tA, "AT_ms": tT,
+                        "A_gbs": ab["A"] / (tA * 1e-3) / 1e9, "AT_gbs": ab["AT"] / (tT * 1e-3) / 1e9,
+                        "A_frac": ab["A"] / (tA * 1e-3) / 1e9 / peak,
+                        "AT_frac": ab["AT"] / (tT * 1e-3) / 1e9 / peak})
+            del x, y, g
+            torch.cuda.empty_cache()
+        lines.append({"sweep": f"stress1024 a={spin:g} i=75deg", "rows": R,
+                      "rays": int(op.info.n_rays), "peak_gbs": peak, "peak_kind": peak_kind,
+                      "results": res})
+        op.close()
+    return lines
 
 
 def run_audit(device):
@@ -354,6 +411,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-audit", action="store_true")
+    ap.add_argument("--sweep", action="store_true",
+                    help="print the stress1024 batch sweep (one JSON line per geometry) and exit")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -390,6 +449,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     device = torch.device("cuda", local)
+    if args.sweep:
+        if rank == 0:
+            torch.cuda.set_device(device)
+            for line in run_sweep(device):
+                print(json.dumps(line))
+        return
     out = run_ours(args, rank, world, device)
     if rank == 0 and world == 1 and not args.no_audit:
         out["audit"] = run_audit(device)
