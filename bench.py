@@ -115,6 +115,7 @@ def build_workload(device):
     tab = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, s)
     op = rtt.Operator(w, tab)
     x = torch.from_numpy(I.history_batch(w, range(100, 100 + BATCH)).astype(np.float32)).to(device)
+    op.tune = op.autotune(BATCH)  # kernel variants for this batch size (setup, untimed)
     return w, tab, op, x
 
 
@@ -180,6 +181,7 @@ def run_ours(args, rank, world, device):
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(device.index if device.index is not None else 0) as clk:
         torch.cuda.synchronize(device)
+        torch.cuda.nvtx.range_push("bench_timed")  # lets ncu --nvtx-include select these launches
         for i in range(args.steps):
             flush.zero_()  # L2 flush between timed iterations (outside the events)
             e0, e1, e2 = ev[i]
@@ -188,6 +190,7 @@ def run_ours(args, rank, world, device):
             e1.record(stream)
             op.apply_AT(y, g)
             e2.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(device)
     t_A = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
     t_AT = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
@@ -198,6 +201,36 @@ def run_ours(args, rank, world, device):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
     clocks = clk.summary()
+
+    # the same A + A^T pair replayed from a captured CUDA graph (the library
+    # allocates nothing once its adjoint scratch exists, so the calls capture)
+    graph = None
+    try:
+        graph_obj = torch.cuda.CUDAGraph()
+        cap = torch.cuda.Stream(device)
+        cap.wait_stream(stream)
+        with torch.cuda.stream(cap):
+            step()
+        torch.cuda.synchronize(device)
+        with torch.cuda.graph(graph_obj, stream=cap):
+            step()
+        torch.cuda.synchronize(device)
+        for _ in range(3):
+            graph_obj.replay()
+        g_ms = []
+        for _ in range(args.steps):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            graph_obj.replay()
+            a1.record(stream)
+            a1.synchronize()
+            g_ms.append(a0.elapsed_time(a1))
+        graph = {"ms_per_step": float(np.mean(g_ms)),
+                 "value": world * BATCH / (float(np.mean(g_ms)) * 1e-3)}
+    except Exception as exc:  # capture is a measurement extra; report why it failed
+        graph = {"error": str(exc)[:200]}
 
     # end-to-end through the C ABI with host buffers: x from pinned host
     # memory to the device, A, A^T, gradient back to pinned host memory
@@ -261,7 +294,8 @@ def run_ours(args, rank, world, device):
                    "batch": BATCH, "rows": R, "rays": int(op.info.n_rays),
                    "nodes": op.n_nodes, "hats": op.n_hats, "frames": op.n_frames,
                    "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}",
+                   "autotune": op.tune},
         "hbm_gbs": gbs,
         "kernels_ms": {"A": mA, "AT": mAT},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -271,6 +305,7 @@ def run_ours(args, rank, world, device):
         "e2e": {"value": world * BATCH / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4)},
         "fp64_path": {"value": world * BATCH / (fp64_ms * 1e-3), "ms_per_step": fp64_ms},
+        "cuda_graph": graph,
         "clocks": clocks,
         "gpu_launches": launches_per_step(BATCH) * args.steps,
     }
@@ -303,6 +338,7 @@ def run_sweep(device, batches=(1, 2, 4, 8, 16, 32, 64), reps: int = 5):
         gen = torch.Generator(device=device).manual_seed(1)
         res = []
         for B in batches:
+            tune = op.autotune(B)
             x = torch.rand((op.n_nodes, op.n_hats, B), generator=gen, device=device)
             y = torch.empty((R, op.n_frames, B), dtype=torch.float32, device=device)
             g = torch.empty_like(x)
@@ -322,6 +358,9 @@ def run_sweep(device, batches=(1, 2, 4, 8, 16, 32, 64), reps: int = 5):
             tT = float(np.mean([b.elapsed_time(c) for _, b, c in ev]))
             ab = algorithmic_bytes(op, B)
             res.append({"batch": B, "A_ms": tA, "AT_ms": tT,
+                        "variant": [tune["fwd_kernel"], tune["fwd_bc"], tune["time_kernel"],
+                                    tune["space_kernel"]],
+                        "rule_ms": [tune["fwd_ms_rule"], tune["adj_ms_rule"]],
                         "A_gbs": ab["A"] / (tA * 1e-3) / 1e9, "AT_gbs": ab["AT"] / (tT * 1e-3) / 1e9,
                         "A_frac": ab["A"] / (tA * 1e-3) / 1e9 / peak,
                         "AT_frac": ab["AT"] / (tT * 1e-3) / 1e9 / peak})
@@ -374,6 +413,11 @@ def run_audit(device):
     out["J_old_direct"] = [round(r[0].reach.J_old, 3) for r in rn]
     out["J_old_resolved"] = [round(r[1].reach.J_old, 3) for r in rn]
     out["min_rank_margin"] = min(min(r[0].margin, r[1].margin) for r in rn)
+    out["sigma_max_range"] = [min(min(r[0].sigma_max, r[1].sigma_max) for r in rn),
+                              max(max(r[0].sigma_max, r[1].sigma_max) for r in rn)]
+    out["sigma_min_range"] = [min(min(r[0].sigma_min_pos, r[1].sigma_min_pos) for r in rn),
+                              max(max(r[0].sigma_min_pos, r[1].sigma_min_pos) for r in rn)]
+    out["seconds_per_record"] = [round(r[i].seconds, 4) for r in rn for i in range(2)]
     out["ranks_agree_between_paths"] = all(a[i].rank == b[i].rank for a, b in zip(rn, rd)
                                            for i in range(2))
     for op in ops:

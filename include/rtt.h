@@ -406,6 +406,40 @@ rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_d
                           double h, double quantile, int gram_mode, rtt_audit_record* out,
                           double* sigma_out, void* stream);
 
+/*
+ * rtt_autotune -- choose the fastest kernel variants of the FP32 applies
+ * (rtt_apply_A / rtt_apply_AT) of this operator for one batch size.  The
+ * paper has no counterpart: this is a property of the GPU implementation.
+ * Candidates: the forward with staged per-ray histories or with one hat per
+ * lane and warp shuffles (the latter only when a frame step is 1/2, 1/4 or
+ * 1/8 of a hat step), each with a few batch widths and frames per lane; the adjoint's
+ * temporal phase (general or periodic-weight) crossed with its spatial
+ * gather (scalar or 16-byte).  Each candidate runs once untimed and three
+ * times between CUDA events on `stream`, on zero-filled inputs of the arm's
+ * shape (timing does not depend on values).  The fastest is recorded in the
+ * operator for `batch` (up to 8 batch sizes per operator; later applies of
+ * that batch size use it).  Every variant sums each output in the same order
+ * with the same fused multiply-adds, so tuning never changes a result bit.
+ * Allocates temporaries (x and y of the batch, cudaMalloc/cudaFree) and
+ * synchronises the stream: call it before any graph capture, not
+ * concurrently with applies on the same operator.
+ * out: host struct (below).  Errors: RTT_EINVAL (batch outside 1..4096, bad
+ * arm), RTT_ENOMEM, RTT_ECUDA.
+ */
+typedef struct {
+    int32_t batch;
+    int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat */
+    int32_t fwd_bc;       /* batch entries per forward task */
+    int32_t fwd_frames_per_lane;
+    int32_t time_kernel;  /* adjoint phase 1: 1 general, 2 periodic weights */
+    int32_t space_kernel; /* adjoint phase 2: 1 scalar, 2 16-byte loads */
+    float fwd_ms, adj_ms;           /* chosen variants, ms per apply */
+    float fwd_ms_rule, adj_ms_rule; /* the untuned default rule, ms per apply */
+    int32_t candidates;             /* configurations timed */
+} rtt_tune_result;
+
+rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream, rtt_tune_result* out);
+
 void rtt_destroy(rtt_op op);
 
 #ifdef __cplusplus

@@ -478,8 +478,8 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
         RTT_TRY(alloc(&op->node_order, S));
         RTT_CUDA(cudaMemcpy(op->node_order, order.data(), S * 4, cudaMemcpyHostToDevice));
     }
-    // (tile, ray) visit lists for the fused adjoint
-    RTT_TRY(build_visits(op, st));
+    // (tile, ray) visit lists, only for the tile-fused adjoint variant
+    if (op->use_fused_adjoint) RTT_TRY(build_visits(op, st));
     return RTT_OK;
 }
 
@@ -548,7 +548,7 @@ static rtt_status apply_common(rtt_op op, const T* in, T* out, int batch, int ma
     if (adjoint) {
         const int bc = batch < 32 ? batch : 32;
         RTT_TRY(ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * bc * sizeof(T)));
-        const size_t pb = fused_partial_bytes(op);
+        const size_t pb = op->use_fused_adjoint ? fused_partial_bytes(op) : 0;
         if (pb > op->fpartial_bytes) {
             if (op->fpartial) {
                 cudaDeviceSynchronize();

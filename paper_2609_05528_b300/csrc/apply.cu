@@ -141,6 +141,22 @@ __device__ __forceinline__ int seg_out_row(const ArmSeg& s, int row_in) {
     return -1;
 }
 
+// Fixed-order arithmetic shared by every kernel variant, so that the variant
+// (chosen from the batch size and alignment) never changes an output bit:
+// fmac(a, b, c) = a b + c with one rounding.
+__device__ __forceinline__ float fmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmac(double a, double b, double c) { return __fma_rn(a, b, c); }
+// spatial interpolation w0 v0 + w1 v1 + w2 v2 + w3 v3
+template <typename T>
+__device__ __forceinline__ T interp4(T w0, T v0, T w1, T v1, T w2, T v2, T w3, T v3) {
+    return fmac(w3, v3, fmac(w2, v2, fmac(w1, v1, w0 * v0)));
+}
+// temporal interpolation acc + g z0 + fr z1
+template <typename T>
+__device__ __forceinline__ T hat2(T acc, T g, T z0, T fr, T z1) {
+    return fmac(fr, z1, fmac(g, z0, acc));
+}
+
 constexpr int kWarpsPerBlock = 8;
 
 constexpr int kAdjOutPerLane = 8;
@@ -201,7 +217,7 @@ adj_time_kernel(const ApplyArgs<T> a) {
                     const int k0 = (int)(U >> kFracBits);
                     const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
                     const float hw = (k0 == k) ? 1.0f - fr : fr;
-                    s += hw * yrow[(int64_t)f * a.B + b];
+                    s = fmac(hw, yrow[(int64_t)f * a.B + b], s);
                 }
             } else {
                 int64_t flo = floor_div(U0 - (int64_t)(k + 1) * kFracOne, a.D) + 1;
@@ -213,7 +229,7 @@ adj_time_kernel(const ApplyArgs<T> a) {
                     T fr;
                     hc.at(f, k0, fr);
                     const T hw = (k0 == k) ? T(1) - fr : ((k0 + 1 == k) ? fr : T(0));
-                    s += hw * yrow[(int64_t)f * a.B + b];
+                    s = fmac(hw, yrow[(int64_t)f * a.B + b], s);
                 }
             }
             a.zhat[((int64_t)e * a.K + k) * a.Bc + bb] = s;
@@ -265,13 +281,15 @@ __device__ __forceinline__ double exact_frac<double>(const ApplyArgs<double>& a,
 template <typename T>
 __device__ __forceinline__ void corner_w(const ApplyArgs<T>& a, int e, T w[4]) { load_w(a, e, w); }
 
-template <typename T, int BC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, (sizeof(T) == 8 || BC >= 32) ? 1 : 2)
+// FPL frames per lane (32 FPL per task); fewer accumulators per lane
+// (BC FPL <= 16) allow three resident CTAs per SM.
+template <typename T, int BC, int FPL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32,
+                                  (sizeof(T) == 8 || BC >= 32) ? 1 : (BC * FPL <= 16 ? 3 : 2))
 fwd3_kernel(const ApplyArgs<T> a) {
     using V = typename Vec16<T>::type;
     constexpr int VW = Vec16<T>::W;
-    constexpr int FPL = BC >= 32 ? 1 : 32 / BC;  // frames per lane
-    constexpr int FC = 32 * FPL;                 // frames per task
+    constexpr int FC = 32 * FPL;  // frames per task
     extern __shared__ __align__(16) unsigned char smem3_raw[];
     T* zs = reinterpret_cast<T*>(smem3_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
     const int lane = threadIdx.x & 31;
@@ -337,8 +355,8 @@ fwd3_kernel(const ApplyArgs<T> a) {
                             T* zc = comps<T>(z);
 #pragma unroll
                             for (int c = 0; c < VW; ++c) {
-                                zc[c] = okv[u] ? w[0] * comps<T>(v[u][0])[c] + w[1] * comps<T>(v[u][1])[c] +
-                                                     w[2] * comps<T>(v[u][2])[c] + w[3] * comps<T>(v[u][3])[c]
+                                zc[c] = okv[u] ? interp4(w[0], comps<T>(v[u][0])[c], w[1], comps<T>(v[u][1])[c],
+                                                         w[2], comps<T>(v[u][2])[c], w[3], comps<T>(v[u][3])[c])
                                                : T(0);
                             }
                             zsv[o] = z;
@@ -352,7 +370,7 @@ fwd3_kernel(const ApplyArgs<T> a) {
                     T z = T(0);
                     if (k >= 0 && k < a.K && bb < nb) {
                         const int64_t off = (int64_t)k * a.B + bb;
-                        z = w[0] * x00[off] + w[1] * x10[off] + w[2] * x01[off] + w[3] * x11[off];
+                        z = interp4(w[0], x00[off], w[1], x10[off], w[2], x01[off], w[3], x11[off]);
                     }
                     zs[o] = z;
                 }
@@ -375,11 +393,12 @@ fwd3_kernel(const ApplyArgs<T> a) {
                             const V p1 = reinterpret_cast<const V*>(z0 + BC)[q];
 #pragma unroll
                             for (int c = 0; c < VW; ++c)
-                                acc[j][VW * q + c] += g * comps<T>(p0)[c] + fr * comps<T>(p1)[c];
+                                acc[j][VW * q + c] =
+                                    hat2(acc[j][VW * q + c], g, comps<T>(p0)[c], fr, comps<T>(p1)[c]);
                         }
                     } else {
 #pragma unroll
-                        for (int b = 0; b < BC; ++b) acc[j][b] += g * z0[b] + fr * z0[BC + b];
+                        for (int b = 0; b < BC; ++b) acc[j][b] = hat2(acc[j][b], g, z0[b], fr, z0[BC + b]);
                     }
                 }
                 U -= dU;
@@ -399,6 +418,148 @@ fwd3_kernel(const ApplyArgs<T> a) {
                     for (int c = 0; c < VW; ++c) comps<T>(o)[c] = acc[j][VW * q + c];
                     reinterpret_cast<V*>(yo)[q] = o;
                 }
+            } else {
+#pragma unroll
+                for (int b = 0; b < BC; ++b)
+                    if (b < nb) yo[b] = acc[j][b];
+            }
+        }
+    }
+}
+
+// Forward when a frame step is exactly 1/P of a hat step (P an integer,
+// FP32).  Lane l owns the P consecutive frames f_c + P l + j (j < P) of the
+// task's chunk.  For every ray those frames lie between the lane's own hat
+// k_l = floor(u(f_c)) - l and its neighbours k_l +- 1, with the same
+// fractional phase on every lane, so each lane forms the spatially
+// interpolated history z of its own hat only (4 corner loads) and takes the
+// neighbours' z by warp shuffles; lanes 0 and 31 also form the two hats just
+// outside the warp.  No shared memory and no per-frame index arithmetic
+// beyond one comparison; the hat index, fraction and summation order per
+// output are those of fwd3_kernel.
+template <int BC, int P>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
+fwd4_kernel(const ApplyArgs<float> a) {
+    constexpr int Q = BC >= 4 ? BC / 4 : 1;
+    constexpr int FC = 32 * P;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const int32_t D32 = (int32_t)a.D;  // 2^24 / P
+    const int64_t KB = (int64_t)a.K * a.B;
+    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
+        const int bchunk = (int)(task % a.n_bchunk);
+        const int64_t t2 = task / a.n_bchunk;
+        const int fchunk = (int)(t2 % a.n_fchunk);
+        const int row_out = (int)(t2 / a.n_fchunk);
+        const int row = seg_in_row(a.seg, row_out);
+        const int f_c = fchunk * FC;
+        const int b0 = bchunk * BC;
+        const int nb = min(BC, a.B - b0);
+        const bool vec = (BC >= 4) && a.vec4 && nb == BC;
+        float acc[P][BC];
+#pragma unroll
+        for (int j = 0; j < P; ++j)
+#pragma unroll
+            for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+        const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
+        for (int e = e_begin; e < e_end; ++e) {
+            const int64_t Ub = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e] - (int64_t)f_c * a.D;
+            const int k_top = (int)(Ub >> kFracBits);         // own hat of lane 0
+            const int32_t phase = (int32_t)(Ub & kFracMask);  // same on every lane
+            const int k_own = k_top - lane;
+            // lanes 0 and 31 also need the hats k_top + 1 and k_top - 32
+            const int k_ext = lane == 0 ? k_top + 1 : k_top - 32;
+            const bool ext = lane == 0 || lane == 31;
+            const float4 wv = a.W[e];
+            const int n00 = a.node00[e], n01 = a.node01[e];
+            const float* x00 = a.in + (int64_t)n00 * KB + b0;
+            const float* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB + b0;
+            const float* x01 = a.in + (int64_t)n01 * KB + b0;
+            const float* x11 = a.in + (int64_t)(n01 + a.n_phi) * KB + b0;
+            float z[BC], zx[BC];
+            const bool own_ok = k_own >= 0 && k_own < a.K;
+            const bool ext_ok = ext && k_ext >= 0 && k_ext < a.K;
+            if (vec) {
+                float4 v[2][Q][4];
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const int64_t o0 = (int64_t)k_own * a.B + 4 * q, o1 = (int64_t)k_ext * a.B + 4 * q;
+                    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+                    v[0][q][0] = own_ok ? __ldg(reinterpret_cast<const float4*>(x00 + o0)) : zero;
+                    v[0][q][1] = own_ok ? __ldg(reinterpret_cast<const float4*>(x10 + o0)) : zero;
+                    v[0][q][2] = own_ok ? __ldg(reinterpret_cast<const float4*>(x01 + o0)) : zero;
+                    v[0][q][3] = own_ok ? __ldg(reinterpret_cast<const float4*>(x11 + o0)) : zero;
+                    v[1][q][0] = ext_ok ? __ldg(reinterpret_cast<const float4*>(x00 + o1)) : zero;
+                    v[1][q][1] = ext_ok ? __ldg(reinterpret_cast<const float4*>(x10 + o1)) : zero;
+                    v[1][q][2] = ext_ok ? __ldg(reinterpret_cast<const float4*>(x01 + o1)) : zero;
+                    v[1][q][3] = ext_ok ? __ldg(reinterpret_cast<const float4*>(x11 + o1)) : zero;
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const float* c0 = reinterpret_cast<const float*>(&v[h][q][0]);
+                        const float* c1 = reinterpret_cast<const float*>(&v[h][q][1]);
+                        const float* c2 = reinterpret_cast<const float*>(&v[h][q][2]);
+                        const float* c3 = reinterpret_cast<const float*>(&v[h][q][3]);
+                        float* zz = h == 0 ? z : zx;
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            zz[4 * q + c] = interp4(wv.x, c0[c], wv.y, c1[c], wv.z, c2[c], wv.w, c3[c]);
+                    }
+            } else {
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    z[b] = 0.0f;
+                    zx[b] = 0.0f;
+                    if (b < nb) {
+                        if (own_ok) {
+                            const int64_t o = (int64_t)k_own * a.B + b;
+                            z[b] = interp4(wv.x, x00[o], wv.y, x10[o], wv.z, x01[o], wv.w, x11[o]);
+                        }
+                        if (ext_ok) {
+                            const int64_t o = (int64_t)k_ext * a.B + b;
+                            zx[b] = interp4(wv.x, x00[o], wv.y, x10[o], wv.z, x01[o], wv.w, x11[o]);
+                        }
+                    }
+                }
+            }
+            // z of hat k_own + 1 (lane l - 1) and k_own - 1 (lane l + 1)
+            float zu[BC], zd[BC];
+#pragma unroll
+            for (int b = 0; b < BC; ++b) {
+                const float up = __shfl_up_sync(0xffffffffu, z[b], 1);
+                const float dn = __shfl_down_sync(0xffffffffu, z[b], 1);
+                zu[b] = lane == 0 ? zx[b] : up;
+                zd[b] = lane == 31 ? zx[b] : dn;
+            }
+#pragma unroll
+            for (int j = 0; j < P; ++j) {
+                const int32_t Uj = phase - j * D32;  // U(f) - k_own 2^24, in [-2^24, 2^24)
+                if (Uj >= 0) {  // hat base k_own
+                    const float fr = (float)Uj * (1.0f / (float)kFracOne);
+                    const float g = 1.0f - fr;
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) acc[j][b] = hat2(acc[j][b], g, z[b], fr, zu[b]);
+                } else {  // hat base k_own - 1
+                    const float fr = (float)(Uj + kFracOne) * (1.0f / (float)kFracOne);
+                    const float g = 1.0f - fr;
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) acc[j][b] = hat2(acc[j][b], g, zd[b], fr, z[b]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+            const int f = f_c + P * lane + j;
+            if (f >= a.Tn) continue;
+            float* yo = a.out + ((int64_t)row_out * a.Tn + f) * a.B + b0;
+            if (vec) {
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+                    reinterpret_cast<float4*>(yo)[q] = make_float4(acc[j][4 * q], acc[j][4 * q + 1],
+                                                                   acc[j][4 * q + 2], acc[j][4 * q + 3]);
             } else {
 #pragma unroll
                 for (int b = 0; b < BC; ++b)
@@ -504,12 +665,13 @@ adj_time3_kernel(const ApplyArgs<T> a) {
                         for (int q = 0; q < Q; ++q) {
                             const V t = ysv[swz(f - fA, q, Q, P)];
 #pragma unroll
-                            for (int c = 0; c < VW; ++c) acc[VW * q + c] += hw * comps<T>(t)[c];
+                            for (int c = 0; c < VW; ++c)
+                                acc[VW * q + c] = fmac(hw, comps<T>(t)[c], acc[VW * q + c]);
                         }
                     } else {
                         const T* yv = ys + (f - fA) * BC;
 #pragma unroll
-                        for (int b = 0; b < BC; ++b) acc[b] += hw * yv[b];
+                        for (int b = 0; b < BC; ++b) acc[b] = fmac(hw, yv[b], acc[b]);
                     }
                 }
                 T* zo = a.zhat + ((int64_t)e * a.K + k) * a.Bc;
@@ -521,6 +683,105 @@ adj_time3_kernel(const ApplyArgs<T> a) {
                         for (int c = 0; c < VW; ++c) comps<T>(o)[c] = acc[VW * q + c];
                         reinterpret_cast<V*>(zo)[q] = o;
                     }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < BC; ++b)
+                        if (b < a.Bc) zo[b] = acc[b];
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// Adjoint phase 1 when a frame step is exactly 1/P of a hat step (P an
+// integer, FP32).  With c0 = floor(U0 / D), hat k is nonzero only on the 2P
+// frames f = c0 + 1 - P (k + 1) + j, j = 0..2P-1, with weight
+// 1 - |r0 - j D| 2^-24, r0 = U0 - (c0 + 1) D + 2^24 in [2^24 - D, 2^24): the
+// same 2P weights for every hat.  The frames of a 32-hat group are staged in
+// shared memory with coalesced 16-byte loads (swizzled layout of
+// adj_time3_kernel); each lane (one hat) then runs a fixed 2P-tap loop with
+// the ray's weights, frames ascending as in the general kernel.
+template <int BC, int P>
+__global__ void __launch_bounds__(kAdj3Warps * 32)
+adj_time4_kernel(const ApplyArgs<float> a) {
+    constexpr int Q = BC >= 4 ? BC / 4 : 1;
+    extern __shared__ __align__(16) unsigned char smem_a4_raw[];
+    float* ys = reinterpret_cast<float*>(smem_a4_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kAdj3Warps + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kAdj3Warps;
+    const bool vec = (BC >= 4) && a.vec4 && (a.Bc == BC);
+    const int pshift = a.FC;  // swizzle key shift
+    const int32_t D32 = (int32_t)a.D;  // 2^24 / P
+    for (int64_t e = warp_global; e < a.n_tasks; e += n_warps) {
+        const int row_out = seg_out_row(a.seg, a.ray_row[e]);
+        if (row_out < 0) {
+            float* zo = a.zhat + (int64_t)e * a.K * a.Bc;
+            for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = 0.0f;
+            continue;
+        }
+        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
+        const int64_t c0 = (U0 * P) >> kFracBits;  // floor(U0 / D), exact
+        const int32_t r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
+        float wt[2 * P];
+#pragma unroll
+        for (int j = 0; j < 2 * P; ++j)
+            wt[j] = 1.0f - (float)abs(r0 - j * D32) * (1.0f / (float)kFracOne);
+        const int fbase = (int)(c0 + 1 - P);  // first frame of hat 0
+        const float* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
+        for (int kg0 = 0; kg0 < a.K; kg0 += 32) {
+            const int kg1 = min(kg0 + 31, a.K - 1);
+            // frames of hats kg1 .. kg0, clipped to the observation
+            const int fA = max(fbase - P * kg1, 0);
+            const int fB = min(fbase - P * kg0 + 2 * P - 1, a.Tn - 1);
+            const int nfr = fB >= fA ? fB - fA + 1 : 0;
+            if (vec) {
+                float4* ysv = reinterpret_cast<float4*>(ys);
+                for (int o = lane; o < nfr * Q; o += 32) {
+                    const int fl = o / Q, q = o - fl * Q;
+                    ysv[swz(fl, q, Q, pshift)] =
+                        __ldg(reinterpret_cast<const float4*>(yrow + (int64_t)(fA + fl) * a.B) + q);
+                }
+            } else {
+                for (int o = lane; o < nfr * BC; o += 32) {
+                    const int fl = o / BC, bb = o - fl * BC;
+                    ys[o] = bb < a.Bc ? yrow[(int64_t)(fA + fl) * a.B + bb] : 0.0f;
+                }
+            }
+            __syncwarp();
+            const int k = kg0 + lane;
+            if (k <= kg1) {
+                float acc[BC];
+#pragma unroll
+                for (int b = 0; b < BC; ++b) acc[b] = 0.0f;
+                const int f0 = fbase - P * k;
+#pragma unroll
+                for (int j = 0; j < 2 * P; ++j) {
+                    const int f = f0 + j;
+                    if (f < fA || f > fB) continue;  // outside the observation
+                    if (vec) {
+                        const float4* ysv = reinterpret_cast<const float4*>(ys);
+#pragma unroll
+                        for (int q = 0; q < Q; ++q) {
+                            const float4 t = ysv[swz(f - fA, q, Q, pshift)];
+                            acc[4 * q + 0] = fmac(wt[j], t.x, acc[4 * q + 0]);
+                            acc[4 * q + 1] = fmac(wt[j], t.y, acc[4 * q + 1]);
+                            acc[4 * q + 2] = fmac(wt[j], t.z, acc[4 * q + 2]);
+                            acc[4 * q + 3] = fmac(wt[j], t.w, acc[4 * q + 3]);
+                        }
+                    } else {
+                        const float* yv = ys + (f - fA) * BC;
+#pragma unroll
+                        for (int b = 0; b < BC; ++b) acc[b] = fmac(wt[j], yv[b], acc[b]);
+                    }
+                }
+                float* zo = a.zhat + ((int64_t)e * a.K + k) * a.Bc;
+                if (vec) {
+#pragma unroll
+                    for (int q = 0; q < Q; ++q)
+                        reinterpret_cast<float4*>(zo)[q] =
+                            make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
                 } else {
 #pragma unroll
                     for (int b = 0; b < BC; ++b)
@@ -593,10 +854,10 @@ adj_space3_kernel(const ApplyArgs<T> a) {
             for (int j = 0; j < kAdjOutPerLane; ++j) {
                 if (!live[j]) continue;
                 const T v0 = zr[0][off[j]], v1 = zr[1][off[j]], v2 = zr[2][off[j]], v3 = zr[3][off[j]];
-                acc[j] += coef[0] * v0;
-                acc[j] += coef[1] * v1;
-                acc[j] += coef[2] * v2;
-                acc[j] += coef[3] * v3;
+                acc[j] = fmac(coef[0], v0, acc[j]);
+                acc[j] = fmac(coef[1], v1, acc[j]);
+                acc[j] = fmac(coef[2], v2, acc[j]);
+                acc[j] = fmac(coef[3], v3, acc[j]);
             }
         }
         for (; ii < i_end; ++ii) {
@@ -605,7 +866,7 @@ adj_space3_kernel(const ApplyArgs<T> a) {
             const T* zr = a.zhat + (int64_t)(code >> 2) * a.K * a.Bc;
 #pragma unroll
             for (int j = 0; j < kAdjOutPerLane; ++j)
-                if (live[j]) acc[j] += coef * zr[off[j]];
+                if (live[j]) acc[j] = fmac(coef, zr[off[j]], acc[j]);
         }
 #pragma unroll
         for (int j = 0; j < kAdjOutPerLane; ++j) {
@@ -613,6 +874,86 @@ adj_space3_kernel(const ApplyArgs<T> a) {
             const int o = lane + 32 * j;
             const int kk = o / BC, bb = o - kk * BC;
             a.out[((int64_t)node * a.K + k_begin + kk) * a.B + bb] = acc[j];
+        }
+    }
+}
+
+// Adjoint phase 2 with 16-byte loads (FP32, Bc = BC a multiple of 4): each
+// lane owns 8 consecutive (hat, batch) outputs of the task's block, so one
+// incidence costs two float4 loads per lane.  Same incidence order and
+// accumulation sequence as adj_space3_kernel.
+constexpr int kSpace4Unroll = 4;
+
+template <int BC>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32)
+adj_space4_kernel(const ApplyArgs<float> a) {
+    static_assert(BC % 4 == 0, "vector path needs 4 | BC");
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const int row_len = a.K * BC;  // floats per zhat row
+    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
+        const int kchunk = (int)(task % a.n_kchunk);
+        const int node = a.node_order ? a.node_order[task / a.n_kchunk] : (int)(task / a.n_kchunk);
+        const int zoff = kchunk * a.KC * BC + 8 * lane;  // first of this lane's 8 outputs
+        const bool live0 = zoff < row_len && 8 * lane < a.KC * BC;
+        const bool live1 = zoff + 4 < row_len && 8 * lane + 4 < a.KC * BC;
+        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+        const int i_begin = a.node_ptr[node], i_end = a.node_ptr[node + 1];
+        const float* Wf = reinterpret_cast<const float*>(a.W);
+        int ii = i_begin;
+        int nxt[kSpace4Unroll];
+#pragma unroll
+        for (int u = 0; u < kSpace4Unroll; ++u) nxt[u] = (ii + u < i_end) ? a.inc[ii + u] : 0;
+        for (; ii + kSpace4Unroll <= i_end; ii += kSpace4Unroll) {
+            int code[kSpace4Unroll];
+#pragma unroll
+            for (int u = 0; u < kSpace4Unroll; ++u) code[u] = nxt[u];
+#pragma unroll
+            for (int u = 0; u < kSpace4Unroll; ++u)
+                nxt[u] = (ii + kSpace4Unroll + u < i_end) ? a.inc[ii + kSpace4Unroll + u] : 0;
+            float coef[kSpace4Unroll];
+            float4 v0[kSpace4Unroll], v1[kSpace4Unroll];
+#pragma unroll
+            for (int u = 0; u < kSpace4Unroll; ++u) {
+                coef[u] = __ldg(Wf + code[u]);
+                const float4* zr = reinterpret_cast<const float4*>(
+                    a.zhat + (int64_t)(code[u] >> 2) * row_len + zoff);
+                v0[u] = live0 ? __ldg(zr) : make_float4(0.f, 0.f, 0.f, 0.f);
+                v1[u] = live1 ? __ldg(zr + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < kSpace4Unroll; ++u) {
+                acc0.x = fmac(coef[u], v0[u].x, acc0.x); acc0.y = fmac(coef[u], v0[u].y, acc0.y);
+                acc0.z = fmac(coef[u], v0[u].z, acc0.z); acc0.w = fmac(coef[u], v0[u].w, acc0.w);
+                acc1.x = fmac(coef[u], v1[u].x, acc1.x); acc1.y = fmac(coef[u], v1[u].y, acc1.y);
+                acc1.z = fmac(coef[u], v1[u].z, acc1.z); acc1.w = fmac(coef[u], v1[u].w, acc1.w);
+            }
+        }
+        for (; ii < i_end; ++ii) {
+            const int code = a.inc[ii];
+            const float coef = __ldg(Wf + code);
+            const float4* zr =
+                reinterpret_cast<const float4*>(a.zhat + (int64_t)(code >> 2) * row_len + zoff);
+            if (live0) {
+                const float4 v = __ldg(zr);
+                acc0.x = fmac(coef, v.x, acc0.x); acc0.y = fmac(coef, v.y, acc0.y);
+                acc0.z = fmac(coef, v.z, acc0.z); acc0.w = fmac(coef, v.w, acc0.w);
+            }
+            if (live1) {
+                const float4 v = __ldg(zr + 1);
+                acc1.x = fmac(coef, v.x, acc1.x); acc1.y = fmac(coef, v.y, acc1.y);
+                acc1.z = fmac(coef, v.z, acc1.z); acc1.w = fmac(coef, v.w, acc1.w);
+            }
+        }
+        // flat zhat offset z -> hat z / BC, batch z % BC (4 | BC keeps a float4 in one hat)
+        if (live0) {
+            const int k = zoff / BC, b = zoff % BC;
+            *reinterpret_cast<float4*>(a.out + ((int64_t)node * a.K + k) * a.B + b) = acc0;
+        }
+        if (live1) {
+            const int k = (zoff + 4) / BC, b = (zoff + 4) % BC;
+            *reinterpret_cast<float4*>(a.out + ((int64_t)node * a.K + k) * a.B + b) = acc1;
         }
     }
 }
@@ -630,6 +971,28 @@ static int grid_for(int64_t n_tasks) {
     const int64_t want = (n_tasks + kWarpsPerBlock - 1) / kWarpsPerBlock;
     const int64_t cap = (int64_t)sms * 16;
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+static int sm_count() {
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+// 16-byte vector access is used only when the batch stride and both buffers
+// allow it
+template <typename T>
+static int vec_ok(const ApplyArgs<T>& a) {
+    constexpr int W = Vec16<T>::W;
+    return (a.B % W == 0) && ((uintptr_t)a.in % 16 == 0) && ((uintptr_t)a.out % 16 == 0) ? 1 : 0;
+}
+
+// frames per hat step when that is an integer the periodic kernel handles, else 0
+static int frames_per_hat(int64_t D) {
+    if (D <= 0 || kFracOne % D != 0) return 0;
+    const int P = (int)(kFracOne / D);
+    return (P == 2 || P == 4 || P == 8) ? P : 0;
 }
 
 template <typename T>
@@ -662,11 +1025,10 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     return a;
 }
 
-template <typename T, int BC>
+template <typename T, int BC, int FPL>
 static cudaError_t launch_fwd3_bc(ApplyArgs<T> a, cudaStream_t st) {
-    constexpr int FPL = BC >= 32 ? 1 : 32 / BC;
     a.FC = 32 * FPL;
-    a.vec4 = (a.B % Vec16<T>::W == 0) ? 1 : 0;
+    a.vec4 = vec_ok(a);
     a.zwin = (int)ceil((a.FC - 1) * a.delta) + 3;
     a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
     a.n_bchunk = (a.B + BC - 1) / BC;
@@ -674,38 +1036,134 @@ static cudaError_t launch_fwd3_bc(ApplyArgs<T> a, cudaStream_t st) {
     if (a.n_tasks == 0) return cudaSuccess;
     const size_t smem = (size_t)kWarpsPerBlock * a.zwin * BC * sizeof(T);
     if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(fwd3_kernel<T, BC>,
+        cudaError_t err = cudaFuncSetAttribute(fwd3_kernel<T, BC, FPL>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
     }
-    fwd3_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
+    fwd3_kernel<T, BC, FPL><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+template <int BC, int P>
+static cudaError_t launch_fwd4(ApplyArgs<float> a, cudaStream_t st) {
+    a.vec4 = vec_ok(a);
+    a.n_fchunk = (a.Tn + 32 * P - 1) / (32 * P);
+    a.n_bchunk = (a.B + BC - 1) / BC;
+    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk * a.n_bchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    fwd4_kernel<BC, P><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+ApplyVariant variant_for(const rtt_op_s* op, int batch) {
+    for (int i = 0; i < op->n_tuned; ++i)
+        if (op->tuned_batch[i] == batch) return op->tuned[i];
+    ApplyVariant v;  // default rule, from the measured kerr256 / stress1024 sweeps
+    v.fwd = 1;
+    v.fwd_bc = (int8_t)pick_bc(batch);
+    v.time = frames_per_hat(op->frame_D) > 0 ? 2 : 1;
+    v.space = 2;  // used when the chunk allows 16-byte access, else scalar
+    return v;
+}
+
+// staged forward with BC batch entries and (half = false) 32 / BC frames per
+// lane, or (half = true, FP32 only) half as many
+template <typename T, int BC>
+static cudaError_t launch_fwd3_fpl(const ApplyArgs<T>& a, bool half, cudaStream_t st) {
+    constexpr int F = BC >= 32 ? 1 : 32 / BC;
+    if constexpr (sizeof(T) == 4 && F >= 2) {
+        if (half) return launch_fwd3_bc<T, BC, F / 2>(a, st);
+    }
+    return launch_fwd3_bc<T, BC, F>(a, st);
+}
+
+template <typename T>
+static cudaError_t launch_fwd3_any(const ApplyArgs<T>& a, int bc, bool half, cudaStream_t st) {
+    switch (bc) {
+        case 1: return launch_fwd3_fpl<T, 1>(a, half, st);
+        case 2: return launch_fwd3_fpl<T, 2>(a, half, st);
+        case 4: return launch_fwd3_fpl<T, 4>(a, half, st);
+        case 8: return launch_fwd3_fpl<T, 8>(a, half, st);
+        case 16: return launch_fwd3_fpl<T, 16>(a, half, st);
+        default: return launch_fwd3_fpl<T, 32>(a, half, st);
+    }
+}
+
+template <int P>
+static cudaError_t launch_fwd4_any(const ApplyArgs<float>& a, int bc, cudaStream_t st) {
+    constexpr int BCmax = 32 / P < 8 ? 32 / P : 8;
+    if (bc <= 1) return launch_fwd4<1, P>(a, st);
+    if (bc <= 2) return launch_fwd4<2, P>(a, st);
+    if (bc <= 4 || BCmax <= 4) return launch_fwd4<(BCmax < 4 ? BCmax : 4), P>(a, st);
+    return launch_fwd4<BCmax, P>(a, st);
 }
 
 template <typename T>
 cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const ArmSeg& seg,
                            cudaStream_t st) {
     ApplyArgs<T> a = base_args<T>(op, x, y, B, seg);
-    switch (pick_bc(B)) {
-        case 1: return launch_fwd3_bc<T, 1>(a, st);
-        case 2: return launch_fwd3_bc<T, 2>(a, st);
-        case 4: return launch_fwd3_bc<T, 4>(a, st);
-        case 8: return launch_fwd3_bc<T, 8>(a, st);
-        case 16: return launch_fwd3_bc<T, 16>(a, st);
-        default: return launch_fwd3_bc<T, 32>(a, st);
+    if constexpr (sizeof(T) == 4) {
+        const ApplyVariant v = variant_for(op, B);
+        const int bc = v.fwd_bc > 0 ? v.fwd_bc : pick_bc(B);
+        if (v.fwd == 2) {
+            switch (frames_per_hat(a.D)) {
+                case 2: return launch_fwd4_any<2>(a, bc, st);
+                case 4: return launch_fwd4_any<4>(a, bc, st);
+                case 8: return launch_fwd4_any<8>(a, bc, st);
+                default: break;  // not a periodic cadence: staged kernel
+            }
+        }
+        return launch_fwd3_any<T>(a, bc, v.fwd_half != 0, st);
+    } else {
+        return launch_fwd3_any<T>(a, pick_bc(B), false, st);
     }
 }
 
 // Adjoint: fast phase 1 when the frames of a 32-hat group fit the staging
 // buffer, otherwise the general per-(hat, batch) kernel; then the gather.
+template <int BC, int P>
+static cudaError_t launch_adj4(ApplyArgs<float> t, cudaStream_t st) {
+    // staged frames per 32-hat group: 31 P + 2P = 33 P, rounded to 8 so the
+    // swizzle stays inside the buffer; swizzle key from frame bits >= log2 P
+    int ps = 0;
+    while ((2 << ps) <= P) ++ps;
+    constexpr int Qv = BC >= 4 ? BC / 4 : 1;
+    if (Qv == 1 && ps == 0) ps = 1;
+    t.FC = ps;
+    t.zwin = (33 * P + 7) & ~7;
+    t.vec4 = vec_ok(t);
+    t.n_tasks = t.n_rays_total;
+    const size_t smem = (size_t)kAdj3Warps * t.zwin * BC * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t err = cudaFuncSetAttribute(adj_time4_kernel<BC, P>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+    }
+    const int64_t want = (t.n_tasks + kAdj3Warps - 1) / kAdj3Warps;
+    const int64_t cap = (int64_t)sm_count() * 32;
+    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+    adj_time4_kernel<BC, P><<<grid, kAdj3Warps * 32, smem, st>>>(t);
+    return cudaGetLastError();
+}
+
 template <typename T, int BC>
-static cudaError_t launch_adj3_bc(ApplyArgs<T> a, cudaStream_t st) {
+static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStream_t st) {
     // staged frames per 32-hat group, rounded so the swizzle stays in bounds
     int ywin = (int)ceil(33.0 / a.delta) + 2;
     ywin = (ywin + 7) & ~7;
     const size_t smem = (size_t)kAdj3Warps * ywin * BC * sizeof(T);
     cudaError_t e = cudaSuccess;
-    if (a.seg.total > 0) {
+    bool periodic = false;
+    if constexpr (sizeof(T) == 4) {
+        const int P = v.time == 2 ? frames_per_hat(a.D) : 0;
+        if (a.seg.total > 0 && P > 0) {
+            periodic = true;
+            e = P == 2 ? launch_adj4<BC, 2>(a, st)
+                       : (P == 4 ? launch_adj4<BC, 4>(a, st) : launch_adj4<BC, 8>(a, st));
+            if (e != cudaSuccess) return e;
+        }
+    }
+    if (a.seg.total > 0 && !periodic) {
         if (smem <= 96 * 1024) {
             ApplyArgs<T> t = a;
             t.zwin = ywin;
@@ -713,9 +1171,14 @@ static cudaError_t launch_adj3_bc(ApplyArgs<T> a, cudaStream_t st) {
                 // log2 of the frames per hat step (swizzle key only)
                 int ps = 0;
                 while ((2 << ps) <= (int)floor(1.0 / a.delta + 0.5)) ++ps;
+                // the XOR key (f >> ps) & 7 must come from bits of the chunk
+                // index f * Q + q above the three it flips, or the layout is
+                // not a permutation: with Q = 1 that needs ps >= 1
+                constexpr int Qv = BC / Vec16<T>::W > 0 ? BC / Vec16<T>::W : 1;
+                if (Qv == 1 && ps == 0) ps = 1;
                 t.FC = ps;
             }
-            t.vec4 = (a.B % Vec16<T>::W == 0) ? 1 : 0;
+            t.vec4 = vec_ok(a);
             t.n_tasks = a.n_rays_total;
             if (smem > 48 * 1024) {
                 e = cudaFuncSetAttribute(adj_time3_kernel<T, BC>,
@@ -745,6 +1208,12 @@ static cudaError_t launch_adj3_bc(ApplyArgs<T> a, cudaStream_t st) {
     a.n_bchunk = 1;
     a.n_tasks = (int64_t)a.n_nodes * a.n_kchunk;
     if (a.n_tasks == 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4 && BC % 4 == 0) {
+        if (v.space == 2 && a.Bc == BC && vec_ok(a)) {
+            adj_space4_kernel<BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     adj_space3_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
     return cudaGetLastError();
 }
@@ -765,6 +1234,9 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         a.Bc = Bc;
         a.n_rays_total = op->n_rays;
         cudaError_t e;
+        ApplyVariant v;  // FP64: general kernels
+        v.time = 1;
+        v.space = 1;
         if constexpr (sizeof(T) == 4) {
             if (op->use_fused_adjoint && (op->fpartial || op->n_partial_slots == 0)) {
                 e = launch_adjoint_fused(op, y, x, B, b_first, Bc, seg, (float*)op->fpartial, st);
@@ -772,23 +1244,15 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
                 if (e != cudaErrorNotSupported) return e;
                 cudaGetLastError();  // clear the "not supported" marker
             }
-            switch (pick_bc(Bc)) {
-                case 1: e = launch_adj3_bc<T, 1>(a, st); break;
-                case 2: e = launch_adj3_bc<T, 2>(a, st); break;
-                case 4: e = launch_adj3_bc<T, 4>(a, st); break;
-                case 8: e = launch_adj3_bc<T, 8>(a, st); break;
-                case 16: e = launch_adj3_bc<T, 16>(a, st); break;
-                default: e = launch_adj3_bc<T, 32>(a, st); break;
-            }
-        } else {
-            switch (pick_bc(Bc)) {
-                case 1: e = launch_adj3_bc<T, 1>(a, st); break;
-                case 2: e = launch_adj3_bc<T, 2>(a, st); break;
-                case 4: e = launch_adj3_bc<T, 4>(a, st); break;
-                case 8: e = launch_adj3_bc<T, 8>(a, st); break;
-                case 16: e = launch_adj3_bc<T, 16>(a, st); break;
-                default: e = launch_adj3_bc<T, 32>(a, st); break;
-            }
+            v = variant_for(op, B);
+        }
+        switch (pick_bc(Bc)) {
+            case 1: e = launch_adj3_bc<T, 1>(a, v, st); break;
+            case 2: e = launch_adj3_bc<T, 2>(a, v, st); break;
+            case 4: e = launch_adj3_bc<T, 4>(a, v, st); break;
+            case 8: e = launch_adj3_bc<T, 8>(a, v, st); break;
+            case 16: e = launch_adj3_bc<T, 16>(a, v, st); break;
+            default: e = launch_adj3_bc<T, 32>(a, v, st); break;
         }
         if (e != cudaSuccess) return e;
     }

@@ -34,6 +34,22 @@ struct ArmSeg {
 
 rtt_status make_seg(const struct ::rtt_op_s* op, int mask, ArmSeg* s);
 
+// Kernel variants of one FP32 apply.  Every variant sums each output in the
+// same order with the same fused multiply-adds, so the choice changes speed
+// only, never a bit of the result.
+struct ApplyVariant {
+    int8_t fwd = 0;     // forward: 1 staged z (fwd3), 2 lane-per-hat shuffles (fwd4)
+    int8_t fwd_bc = 0;  // batch entries per forward task (power of two)
+    int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
+    int8_t time = 0;    // adjoint phase 1: 1 general (adj_time3), 2 periodic (adj_time4)
+    int8_t space = 0;   // adjoint phase 2: 1 scalar (adj_space3), 2 16-byte (adj_space4)
+};
+constexpr int kMaxTuned = 8;  // batch sizes with an autotuned variant per operator
+
+// the variant an FP32 apply of `batch` columns uses: the tuned one if
+// rtt_autotune ran for that batch size, else the default rule
+ApplyVariant variant_for(const struct ::rtt_op_s* op, int batch);
+
 }  // namespace rtt
 
 struct rtt_op_s {
@@ -80,4 +96,8 @@ struct rtt_op_s {
     void* fpartial = nullptr;
     size_t fpartial_bytes = 0;
     bool use_fused_adjoint = false;  // tile-fused adjoint (measured slower than two-phase so far)
+    // autotuned kernel variants (rtt_autotune), per batch size
+    int n_tuned = 0;
+    int tuned_batch[rtt::kMaxTuned] = {};
+    rtt::ApplyVariant tuned[rtt::kMaxTuned];
 };

@@ -1,0 +1,186 @@
+// Autotuner for the FP32 applies: for one operator and batch size, times
+// every kernel variant of the forward (staged or lane-per-hat, batch entries
+// per task) and of the two adjoint phases (general or periodic time
+// contraction, scalar or 16-byte gather) with CUDA events on the caller's
+// stream, and records the fastest in the operator.  All variants produce the
+// same bits (same per-output summation order and fused multiply-adds), so
+// tuning changes speed only.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "rtt_internal.cuh"
+
+using namespace rtt;
+
+namespace rtt {
+template <typename T>
+cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
+template <typename T>
+cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
+rtt_status ensure_zhat_bytes(rtt_op_s* op, size_t bytes);
+}  // namespace rtt
+
+namespace {
+
+constexpr int kTuneReps = 3;
+
+// installs v as the operator's variant for batch B (replacing an entry)
+void set_variant(rtt_op_s* op, int B, const ApplyVariant& v) {
+    for (int i = 0; i < op->n_tuned; ++i)
+        if (op->tuned_batch[i] == B) {
+            op->tuned[i] = v;
+            return;
+        }
+    int slot = op->n_tuned < kMaxTuned ? op->n_tuned++ : kMaxTuned - 1;
+    op->tuned_batch[slot] = B;
+    op->tuned[slot] = v;
+}
+
+void clear_variant(rtt_op_s* op, int B) {
+    for (int i = 0; i < op->n_tuned; ++i)
+        if (op->tuned_batch[i] == B) {
+            for (int j = i + 1; j < op->n_tuned; ++j) {
+                op->tuned_batch[j - 1] = op->tuned_batch[j];
+                op->tuned[j - 1] = op->tuned[j];
+            }
+            --op->n_tuned;
+            return;
+        }
+}
+
+struct Timer {
+    cudaEvent_t a = nullptr, b = nullptr;
+    Timer() {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    ~Timer() {
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+    }
+};
+
+}  // namespace
+
+extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream,
+                                   rtt_tune_result* out) {
+    if (!op || batch < 1 || batch > 4096 || !out) {
+        set_error("invalid autotune arguments (op=%p batch=%d out=%p)", (void*)op, batch,
+                  (void*)out);
+        return RTT_EINVAL;
+    }
+    ArmSeg seg;
+    rtt_status s = make_seg(op, arm_mask, &seg);
+    if (s != RTT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int B = batch;
+    const size_t nx = (size_t)op->n_nodes * op->time.n_hats * B;
+    const size_t ny = (size_t)(seg.total > 0 ? seg.total : 1) * op->time.n_frames * B;
+    s = ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * (B < 32 ? B : 32) * 4);
+    if (s != RTT_OK) return s;
+    float *x = nullptr, *y = nullptr;
+    if (cudaMalloc(&x, nx * 4) != cudaSuccess || cudaMalloc(&y, ny * 4) != cudaSuccess) {
+        cudaFree(x);
+        cudaFree(y);
+        set_error("autotune: allocation of %zu + %zu bytes failed", nx * 4, ny * 4);
+        return RTT_ENOMEM;
+    }
+    // timing inputs: x = 0 and y = 0 move the same bytes and issue the same
+    // instructions as any data (no data-dependent branches in the kernels)
+    cudaMemsetAsync(x, 0, nx * 4, st);
+    cudaMemsetAsync(y, 0, ny * 4, st);
+
+    // the rule, then candidates; a candidate is timed by installing it
+    clear_variant(op, B);
+    const ApplyVariant rule = variant_for(op, B);
+    const bool periodic = op->frame_D > 0 && (kFracOne % op->frame_D) == 0 &&
+                          (kFracOne / op->frame_D == 2 || kFracOne / op->frame_D == 4 ||
+                           kFracOne / op->frame_D == 8);
+    int bc_max = 1;
+    while (bc_max < B && bc_max < 32) bc_max <<= 1;
+
+    Timer tm;
+    int n_cand = 0;
+    cudaError_t e = cudaSuccess;
+    auto time_it = [&](const ApplyVariant& v, bool adjoint) -> float {
+        set_variant(op, B, v);
+        ++n_cand;
+        for (int w = 0; w < 1 && e == cudaSuccess; ++w)
+            e = adjoint ? launch_adjoint<float>(op, y, x, B, seg, (float*)op->zhat, st)
+                        : launch_forward<float>(op, x, y, B, seg, st);
+        if (e != cudaSuccess) return 1e30f;
+        cudaEventRecord(tm.a, st);
+        for (int r = 0; r < kTuneReps && e == cudaSuccess; ++r)
+            e = adjoint ? launch_adjoint<float>(op, y, x, B, seg, (float*)op->zhat, st)
+                        : launch_forward<float>(op, x, y, B, seg, st);
+        cudaEventRecord(tm.b, st);
+        if (e != cudaSuccess) return 1e30f;
+        if (cudaEventSynchronize(tm.b) != cudaSuccess) {
+            e = cudaGetLastError();
+            return 1e30f;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, tm.a, tm.b);
+        return ms / kTuneReps;
+    };
+
+    ApplyVariant best = rule;
+    // forward: staged kernel and (periodic cadences) lane-per-hat kernel, each
+    // with the widest batch chunk and one or two narrower ones
+    const float fwd_rule = time_it(rule, false);
+    float fwd_best = fwd_rule;
+    for (int kind = 1; kind <= (periodic ? 2 : 1); ++kind)
+        for (int bc = bc_max; bc >= 1 && bc >= bc_max / 4; bc >>= 1)
+            for (int half = 0; half <= (kind == 1 && bc < 32 ? 1 : 0); ++half) {
+                ApplyVariant v = rule;
+                v.fwd = (int8_t)kind;
+                v.fwd_bc = (int8_t)bc;
+                v.fwd_half = (int8_t)half;
+                if (kind == 2 && bc > 8) continue;  // the lane-per-hat kernel holds <= 8 per task
+                const float ms = time_it(v, false);
+                if (ms < fwd_best) {
+                    fwd_best = ms;
+                    best.fwd = v.fwd;
+                    best.fwd_bc = v.fwd_bc;
+                    best.fwd_half = v.fwd_half;
+                }
+            }
+    // adjoint: phase-1 x phase-2 variants (timed as the full adjoint)
+    const float adj_rule = time_it(rule, true);
+    float adj_best = adj_rule;
+    for (int tk = 1; tk <= (periodic ? 2 : 1); ++tk)
+        for (int sk = 1; sk <= 2; ++sk) {
+            ApplyVariant v = best;
+            v.time = (int8_t)tk;
+            v.space = (int8_t)sk;
+            const float ms = time_it(v, true);
+            if (ms < adj_best) {
+                adj_best = ms;
+                best.time = v.time;
+                best.space = v.space;
+            }
+        }
+    cudaFree(x);
+    cudaFree(y);
+    if (e != cudaSuccess) {
+        clear_variant(op, B);
+        set_error("autotune launch failed: %s", cudaGetErrorString(e));
+        return RTT_ECUDA;
+    }
+    set_variant(op, B, best);
+    out->batch = B;
+    out->fwd_kernel = best.fwd;
+    out->fwd_bc = best.fwd_bc;
+    out->fwd_frames_per_lane =
+        best.fwd == 2 ? (int32_t)(kFracOne / op->frame_D)
+                      : (best.fwd_bc >= 32 ? 1 : 32 / best.fwd_bc) / (best.fwd_half ? 2 : 1);
+    out->time_kernel = best.time;
+    out->space_kernel = best.space;
+    out->fwd_ms = fwd_best;
+    out->adj_ms = adj_best;
+    out->fwd_ms_rule = fwd_rule;
+    out->adj_ms_rule = adj_rule;
+    out->candidates = n_cand;
+    return RTT_OK;
+}

@@ -84,6 +84,15 @@ class Screen(ctypes.Structure):
                 ("n_sub", i32p), ("d_omega_pixel", ctypes.c_double)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int32), ("fwd_kernel", ctypes.c_int32),
+                ("fwd_bc", ctypes.c_int32), ("fwd_frames_per_lane", ctypes.c_int32),
+                ("time_kernel", ctypes.c_int32),
+                ("space_kernel", ctypes.c_int32), ("fwd_ms", ctypes.c_float),
+                ("adj_ms", ctypes.c_float), ("fwd_ms_rule", ctypes.c_float),
+                ("adj_ms_rule", ctypes.c_float), ("candidates", ctypes.c_int32)]
+
+
 # name -> (restype, argtypes)
 _SIGS = {
     "rtt_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -124,6 +133,8 @@ _SIGS = {
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                       ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, ctypes.POINTER(AuditRecord), dp, vp]),
+    "rtt_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp,
+                                    ctypes.POINTER(TuneResult)]),
     "rtt_destroy": (None, [vp]),
 }
 
@@ -234,6 +245,14 @@ class Operator:
         n = ctypes.c_int64(0)
         check(lib().rtt_arm_rows(self.handle, arm_mask, ctypes.byref(n)), "rtt_arm_rows")
         return int(n.value)
+
+    def autotune(self, batch: int, arm_mask: int = 7, stream=None) -> dict:
+        """rtt_autotune: time the FP32 kernel variants for `batch` columns and
+        keep the fastest for later applies of that batch size."""
+        r = TuneResult()
+        check(lib().rtt_autotune(self.handle, int(batch), int(arm_mask), _stream(stream),
+                                 ctypes.byref(r)), "rtt_autotune")
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def close(self):
         if getattr(self, "handle", None):

@@ -102,6 +102,27 @@ def test_adjoint_parity(small, B, mask):
     _cmp(x64.cpu().numpy(), ref, TOL64)
 
 
+@pytest.mark.parametrize("cadence", [0.5, 2.0, 3.0, 4.0])
+@pytest.mark.parametrize("B", [2, 4, 8])
+def test_cadence_variants(cadence, B):
+    """Frame steps of 1/8, 1/2, 3/4 and 1 hat step: the periodic-weight adjoint
+    (integer frames per hat step 8 and 2), the general kernel (3/4) and one
+    frame per hat step, against the oracle."""
+    n_frames = int(round(120 / cadence))
+    w = I.Workload(f"cad{cadence:g}", I.Geometry(0.5, 50.0, 32), I.SourceGrid(10, 20),
+                   I.TimeGrid(n_frames, cadence, 40, t_end=cadence * (n_frames - 1)),
+                   supersample=2)
+    c = Case(w)
+    x = I.uniform_batch(w, range(B))
+    _cmp(c.op.apply_A(torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64),
+         O.apply_A(w, c.tab, x, c.scale), TOL32)
+    y = I.noise((c.tab.n_rows, n_frames, B), 17)
+    ref = O.apply_AT(w, c.tab, y, c.scale)
+    got = c.op.apply_AT(torch.from_numpy(y.astype(np.float32)).cuda())
+    _cmp(got.cpu().numpy().astype(np.float64), ref, TOL32 * 3)
+    _cmp(c.op.apply_AT(torch.from_numpy(y).cuda()).cpu().numpy(), ref, TOL64)
+
+
 def test_dot_product_fp64(small):
     c = small
     x = torch.from_numpy(I.uniform_batch(c.w, [3, 4])).cuda()
@@ -120,6 +141,46 @@ def test_deterministic_bitwise(small):
     g1 = c.op.apply_AT(y1)
     g2 = c.op.apply_AT(y2)
     assert torch.equal(g1, g2)
+
+
+def test_batch_columns_independent_bitwise(small):
+    """Each batch column of A x and A^T y is the same bits whatever the batch
+    size (B = 8 takes the 16-byte vector kernels, B = 1 and B = 3 the scalar
+    ones): every kernel variant sums in the same order."""
+    c = small
+    x = torch.from_numpy(I.uniform_batch(c.w, range(8)).astype(np.float32)).cuda()
+    y = c.op.apply_A(x)
+    g = c.op.apply_AT(y)
+    for j in (0, 5):
+        yj = c.op.apply_A(x[:, :, j:j + 1].contiguous())
+        assert torch.equal(yj[:, :, 0], y[:, :, j])
+        gj = c.op.apply_AT(y[:, :, j:j + 1].contiguous())
+        assert torch.equal(gj[:, :, 0], g[:, :, j])
+    y3 = c.op.apply_A(x[:, :, 2:5].contiguous())
+    assert torch.equal(y3, y[:, :, 2:5])
+    g3 = c.op.apply_AT(y[:, :, 2:5].contiguous())
+    assert torch.equal(g3, g[:, :, 2:5])
+
+
+@pytest.mark.parametrize("B", [3, 8])
+def test_autotune_keeps_bits(B):
+    """rtt_autotune times the kernel variants and installs the fastest; the
+    outputs after tuning are the same bits as before."""
+    w = I.small_kerr(spin=0.5, incl_deg=50.0, nx=40, n_r=10, n_phi=20, n_frames=200,
+                     n_hats=60, ss=2)
+    c = Case(w)
+    x = torch.from_numpy(I.uniform_batch(w, range(B)).astype(np.float32)).cuda()
+    y0 = c.op.apply_A(x)
+    g0 = c.op.apply_AT(y0)
+    r = c.op.autotune(B)
+    assert r["batch"] == B and r["candidates"] >= 4
+    assert r["fwd_kernel"] in (1, 2) and r["time_kernel"] in (1, 2) and r["space_kernel"] in (1, 2)
+    assert 0 < r["fwd_ms"] <= r["fwd_ms_rule"] and 0 < r["adj_ms"] <= r["adj_ms_rule"]
+    y1 = c.op.apply_A(x)
+    g1 = c.op.apply_AT(y0)
+    assert torch.equal(y0, y1) and torch.equal(g0, g1)
+    _cmp(y1.cpu().numpy().astype(np.float64),
+         O.apply_A(w, c.tab, x.cpu().numpy().astype(np.float64), c.scale), TOL32)
 
 
 def test_direct_zero_columns_bit_exact(schw):
