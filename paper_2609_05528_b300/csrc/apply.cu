@@ -814,8 +814,11 @@ adj_space3_kernel(const ApplyArgs<T> a) {
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
-        const int kchunk = (int)(task % a.n_kchunk);
-        const int node = a.node_order ? a.node_order[task / a.n_kchunk] : (int)(task / a.n_kchunk);
+        // hat-chunk-major task order: while one hat chunk is gathered for all
+        // nodes, only that slice of zhat (1 / n_kchunk of it) is live in L2
+        const int kchunk = (int)(task / a.n_nodes);
+        const int ni = (int)(task - (int64_t)kchunk * a.n_nodes);
+        const int node = a.node_order ? a.node_order[ni] : ni;
         const int k_begin = kchunk * a.KC;
         T acc[kAdjOutPerLane];
 #pragma unroll
@@ -893,8 +896,11 @@ adj_space4_kernel(const ApplyArgs<float> a) {
     const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
     const int row_len = a.K * BC;  // floats per zhat row
     for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
-        const int kchunk = (int)(task % a.n_kchunk);
-        const int node = a.node_order ? a.node_order[task / a.n_kchunk] : (int)(task / a.n_kchunk);
+        // hat-chunk-major task order: while one hat chunk is gathered for all
+        // nodes, only that slice of zhat (1 / n_kchunk of it) is live in L2
+        const int kchunk = (int)(task / a.n_nodes);
+        const int ni = (int)(task - (int64_t)kchunk * a.n_nodes);
+        const int node = a.node_order ? a.node_order[ni] : ni;
         const int zoff = kchunk * a.KC * BC + 8 * lane;  // first of this lane's 8 outputs
         const bool live0 = zoff < row_len && 8 * lane < a.KC * BC;
         const bool live1 = zoff + 4 < row_len && 8 * lane + 4 < a.KC * BC;
