@@ -181,6 +181,16 @@ rtt_status rtt_op_query(rtt_op op, rtt_op_info* out);
 rtt_status rtt_arm_rows(rtt_op op, int arm_mask, int64_t* rows_out);
 
 /*
+ * rtt_op_status -- the operator's device status word, read after the work
+ * queued on `stream` (synchronises it).  Bit 0: a kernel's bounded wait on
+ * an asynchronous copy (the TMA-staged adjoint) ran out of iterations; that
+ * apply's output is incomplete.  0 after correct operation.  clear != 0
+ * resets the word.  The paper has no counterpart.  flags_out: host int32.
+ * Errors: RTT_EINVAL, RTT_ECUDA.
+ */
+rtt_status rtt_op_status(rtt_op op, int32_t* flags_out, int clear, void* stream);
+
+/*
  * rtt_apply_A -- y = scale * A x for a batch of `batch` histories (Eq. 2-3,
  * Eq. 16, Eq. 47): y[row][f][b] = scale sum_{e in row} w_e sum_c bil_c(e)
  * sum_k B_k(t_o(f) - Delta_e) x[node_c(e)][k][b].  Only the two hats whose
@@ -413,8 +423,9 @@ rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_d
  * Candidates: the forward with staged per-ray histories or with one hat per
  * lane and warp shuffles (the latter only when a frame step is 1/2, 1/4 or
  * 1/8 of a hat step), each with a few batch widths and frames per lane; the adjoint's
- * temporal phase (general or periodic-weight) crossed with its spatial
- * gather (scalar or 16-byte).  Each candidate runs once untimed and three
+ * temporal phase (general, periodic-weight, or periodic-weight with frames
+ * staged by TMA tensor copies) crossed with its spatial gather (scalar or
+ * 16-byte).  Each candidate runs once untimed and three
  * times between CUDA events on `stream`, on zero-filled inputs of the arm's
  * shape (timing does not depend on values).  The fastest is recorded in the
  * operator for `batch` (up to 8 batch sizes per operator; later applies of
@@ -431,7 +442,7 @@ typedef struct {
     int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat */
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
-    int32_t time_kernel;  /* adjoint phase 1: 1 general, 2 periodic weights */
+    int32_t time_kernel;  /* adjoint phase 1: 1 general, 2 periodic weights, 3 periodic + TMA */
     int32_t space_kernel; /* adjoint phase 2: 1 scalar, 2 16-byte loads */
     float fwd_ms, adj_ms;           /* chosen variants, ms per apply */
     float fwd_ms_rule, adj_ms_rule; /* the untuned default rule, ms per apply */
@@ -439,6 +450,27 @@ typedef struct {
 } rtt_tune_result;
 
 rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream, rtt_tune_result* out);
+
+/* A kernel variant of the FP32 applies (the same choices rtt_autotune makes). */
+typedef struct {
+    int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat (periodic cadences; else staged) */
+    int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32 */
+    int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
+    int32_t time_kernel;  /* 1 general, 2 periodic weights, 3 periodic + TMA (where
+                             the cadence or the buffers do not allow 2 or 3, the
+                             next one down runs) */
+    int32_t space_kernel; /* 1 scalar, 2 16-byte loads (where the buffers allow) */
+} rtt_variant;
+
+/*
+ * rtt_set_variant / rtt_get_variant -- pin (or, with v == NULL, reset to the
+ * default rule) the kernel variant used by FP32 applies of `batch` columns,
+ * or read the one in force.  For manual tuning and for tests that run every
+ * variant; results are the same bits for every variant.  Not thread-safe
+ * against concurrent applies on the same operator.  Errors: RTT_EINVAL.
+ */
+rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v);
+rtt_status rtt_get_variant(rtt_op op, int batch, rtt_variant* out);
 
 void rtt_destroy(rtt_op op);
 

@@ -226,7 +226,8 @@ static void free_op(rtt_op_s* op) {
     void* ps[] = {op->row_ptr, op->ray_row, op->node00, op->node01, op->W,     op->W64,
                   op->K0,      op->F0,      op->F64,    op->r,      op->delay, op->weight,
                   op->thr,     op->node_ptr, op->inc,   op->row_order, op->zhat,
-                  op->visits,  op->items,    op->split_tiles, op->fpartial, op->node_order};
+                  op->visits,  op->items,    op->split_tiles, op->fpartial, op->node_order,
+                  op->dev_status};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete op;
@@ -476,6 +477,8 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
             return (ptr[a + 1] - ptr[a]) > (ptr[b + 1] - ptr[b]);
         });
         RTT_TRY(alloc(&op->node_order, S));
+        RTT_TRY(alloc(&op->dev_status, 1));
+        RTT_CUDA(cudaMemset(op->dev_status, 0, sizeof(int)));
         RTT_CUDA(cudaMemcpy(op->node_order, order.data(), S * 4, cudaMemcpyHostToDevice));
     }
     // (tile, ray) visit lists, only for the tile-fused adjoint variant
@@ -651,6 +654,20 @@ rtt_status rtt_op_query(rtt_op op, rtt_op_info* o) {
     o->n_frames = op->time.n_frames;
     o->s_ref = op->s_ref;
     o->scale = op->scale;
+    return RTT_OK;
+}
+
+rtt_status rtt_op_status(rtt_op op, int32_t* flags_out, int clear, void* stream) {
+    if (!op || !flags_out) {
+        set_error("null argument");
+        return RTT_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int v = 0;
+    RTT_CUDA(cudaMemcpyAsync(&v, op->dev_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RTT_CUDA(cudaStreamSynchronize(st));
+    if (clear) RTT_CUDA(cudaMemsetAsync(op->dev_status, 0, sizeof(int), st));
+    *flags_out = v;
     return RTT_OK;
 }
 

@@ -10,7 +10,9 @@
 //   gather over the node's incidence list (sorted by ray), summing for each
 //   owned (k, b) the frames whose hat pair contains k, with the same integer
 //   hat arithmetic as the forward, so the two are exact transposes.
+#include <cuda.h>  // CUtensorMap and its enums (types only; no driver-library link)
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include "rtt_internal.cuh"
 
@@ -87,6 +89,7 @@ struct ApplyArgs {
     int64_t n_rays_total;
     int seg_rows_all;  // total rows of the operator (all orders)
     const int32_t* node_order;  // nodes by descending incidence count (load balance)
+    int* status;                // device status word (bit 0: a bounded wait timed out)
     int n_fchunk, n_bchunk, n_kchunk;
     int64_t n_tasks;
 };
@@ -793,6 +796,192 @@ adj_time4_kernel(const ApplyArgs<float> a) {
     }
 }
 
+// Adjoint phase 1, periodic weights, with the frames of each (ray, 32-hat
+// group) brought into shared memory by the tensor memory accelerator.  y of
+// a single batch chunk (B = BC entries per frame, frames contiguous) is
+// viewed as a 2D tensor of 128-byte rows, each holding FPR = 32 / BC
+// consecutive frames; one tiled copy per group moves the rows covering the
+// group's frames (start rounded down to a row), issued by lane 0 and tracked
+// by an mbarrier, double-buffered so the copy for the next group (of this ray
+// or the next) runs while the current one is contracted.  With the 128-byte
+// swizzle, the 16-byte chunk j of box row r lands at chunk j ^ (r mod 8) of
+// that row (buffers 1024-byte aligned), so lanes that read frames P apart
+// hit distinct banks.  Arithmetic and order are those of adj_time4_kernel.
+// Every mbarrier wait is bounded: on timeout the warp sets bit 0 of
+// *status, waits (bounded) for its other copy in flight and returns.
+constexpr int kAdj5Warps = 4;
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    for (int it = 0; it < kSpinLimit; ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(ok)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+template <int BC, int P>
+struct T5Box {
+    static constexpr int kFPR = 32 / BC;  // frames per 128-byte row
+    // rows covering up to 33 P frames that start anywhere inside a row
+    static constexpr int kRows = (33 * P + 2 * (kFPR - 1)) / kFPR;
+    static constexpr uint32_t kBytes = (uint32_t)kRows * 128;
+    static constexpr uint32_t kStride = (kBytes + 1023) & ~1023u;
+};
+
+template <int BC, int P>
+__global__ void __launch_bounds__(kAdj5Warps * 32)
+adj_time5_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float> a,
+                 int* status) {
+    static_assert(BC == 4 || BC == 8 || BC == 16 || BC == 32, "128-byte rows of whole frames");
+    constexpr int Q = BC / 4;  // 16-byte chunks per frame
+    constexpr int FPR = T5Box<BC, P>::kFPR;
+    constexpr uint32_t BOX_BYTES = T5Box<BC, P>::kBytes;
+    constexpr uint32_t BUF_STRIDE = T5Box<BC, P>::kStride;
+    extern __shared__ unsigned char smem5_raw[];
+    const uint32_t raw_u32 = smem_u32(smem5_raw);
+    const uint32_t base_u32 = (raw_u32 + 1023) & ~1023u;  // 128-byte swizzle atom alignment
+    unsigned char* base = smem5_raw + (base_u32 - raw_u32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // buffer b of this warp: shared address buf0 + b * BUF_STRIDE, mbarrier bar0 + 8 b
+    const unsigned char* bufp0 = base + (size_t)(2 * warp) * BUF_STRIDE;
+    const uint32_t buf0 = base_u32 + (2 * warp) * BUF_STRIDE;
+    const uint32_t bar0 = base_u32 + kAdj5Warps * 2 * BUF_STRIDE + 16 * warp;
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int64_t warp_global = (int64_t)blockIdx.x * kAdj5Warps + warp;
+    const int64_t n_warps = (int64_t)gridDim.x * kAdj5Warps;
+    const int n_groups = (a.K + 31) / 32;
+    const int32_t D32 = (int32_t)a.D;
+    // rays outside the arm: zero rows (no copies)
+    if (a.seg.total < a.seg_rows_all) {
+        for (int64_t e = warp_global; e < a.n_tasks; e += n_warps)
+            if (seg_out_row(a.seg, a.ray_row[e]) < 0) {
+                float* zo = a.zhat + e * a.K * a.Bc;
+                for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = 0.0f;
+            }
+    }
+    // work items (ray, group) of this warp, rays in the arm only
+    struct Item {
+        int64_t e;
+        int g, row_out, fbase, fA, fB, f4;  // f4: first frame of the first copied row
+    };
+    auto fill = [&](int64_t e, int g, Item& it) {
+        it.e = e;
+        it.g = g;
+        it.row_out = seg_out_row(a.seg, a.ray_row[e]);
+        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
+        const int64_t c0 = (U0 * P) >> kFracBits;
+        it.fbase = (int)(c0 + 1 - P);
+        const int kg0 = 32 * g, kg1 = min(kg0 + 31, a.K - 1);
+        it.fA = max(it.fbase - P * kg1, 0);
+        it.fB = min(it.fbase - P * kg0 + 2 * P - 1, a.Tn - 1);
+        it.f4 = min(it.fA, a.Tn - 1) & ~(FPR - 1);
+    };
+    // next item after (e, g): next group, else the next ray in the arm
+    auto next = [&](int64_t e, int g, Item& it) -> bool {
+        if (g + 1 < n_groups) {
+            fill(e, g + 1, it);
+            return true;
+        }
+        for (e += n_warps; e < a.n_tasks; e += n_warps)
+            if (seg_out_row(a.seg, a.ray_row[e]) >= 0) {
+                fill(e, 0, it);
+                return true;
+            }
+        return false;
+    };
+    const uint64_t tmap = reinterpret_cast<uint64_t>(&ymap);
+    auto issue = [&](const Item& it, int b) {
+        if (lane != 0) return;
+        // tensor row of (row_out, f4); frames per row divide the frame count
+        const int ycoord = (int)(((int64_t)it.row_out * a.Tn + it.f4) / FPR);
+        const uint32_t bar = bar0 + 8u * b, dst = buf0 + (uint32_t)b * BUF_STRIDE;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(BOX_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+            "l"(tmap), "r"(0), "r"(ycoord), "r"(bar)
+            : "memory");
+    };
+    Item cur;
+    bool have = false;
+    for (int64_t e = warp_global; e < a.n_tasks && !have; e += n_warps)
+        if (seg_out_row(a.seg, a.ray_row[e]) >= 0) {
+            fill(e, 0, cur);
+            have = true;
+        }
+    if (!have) return;
+    issue(cur, 0);
+    for (uint32_t t = 0; have; ++t) {
+        Item nxt;
+        const bool more = next(cur.e, cur.g, nxt);
+        if (more) issue(nxt, (t + 1) & 1);
+        if (!mbar_wait(bar0 + 8u * (t & 1), (t >> 1) & 1)) {
+            if (lane == 0) atomicOr(status, 1);
+            if (more) mbar_wait(bar0 + 8u * ((t + 1) & 1), ((t + 1) >> 1) & 1);
+            return;
+        }
+        // contraction of group cur.g of ray cur.e from buffer t & 1
+        const int64_t U0 = (int64_t)a.K0[cur.e] * kFracOne + (int64_t)a.F0[cur.e];
+        const int64_t c0 = (U0 * P) >> kFracBits;
+        const int32_t r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
+        float wt[2 * P];
+#pragma unroll
+        for (int j = 0; j < 2 * P; ++j)
+            wt[j] = 1.0f - (float)abs(r0 - j * D32) * (1.0f / (float)kFracOne);
+        const int k = 32 * cur.g + lane;
+        if (k < a.K) {
+            float acc[BC];
+#pragma unroll
+            for (int b = 0; b < BC; ++b) acc[b] = 0.0f;
+            const int f0 = cur.fbase - P * k;
+            const float4* bv = reinterpret_cast<const float4*>(bufp0 + (t & 1) * BUF_STRIDE);
+#pragma unroll
+            for (int j = 0; j < 2 * P; ++j) {
+                const int f = f0 + j;
+                if (f < cur.fA || f > cur.fB) continue;  // outside the observation
+                const int fl = f - cur.f4;                // < kRows * FPR
+                const int r = fl / FPR;
+                const int cb = (fl - r * FPR) * Q;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float4 v = bv[8 * r + ((cb + q) ^ (r & 7))];
+                    acc[4 * q + 0] = fmac(wt[j], v.x, acc[4 * q + 0]);
+                    acc[4 * q + 1] = fmac(wt[j], v.y, acc[4 * q + 1]);
+                    acc[4 * q + 2] = fmac(wt[j], v.z, acc[4 * q + 2]);
+                    acc[4 * q + 3] = fmac(wt[j], v.w, acc[4 * q + 3]);
+                }
+            }
+            float4* zo = reinterpret_cast<float4*>(a.zhat + (cur.e * a.K + k) * BC);
+#pragma unroll
+            for (int q = 0; q < Q; ++q)
+                zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+        __syncwarp();  // buffer t & 1 is free for the copy issued at step t + 1
+        cur = nxt;
+        have = more;
+    }
+}
+
 // Adjoint phase 2, fast path: lanes over (hat, batch) of one node, nodes in
 // descending-load order; the incidence loop is unrolled by 4 so that four
 // zhat rows are in flight.
@@ -1028,6 +1217,7 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     a.seg = seg;
     a.seg_rows_all = (int)op->n_rows;
     a.node_order = op->node_order;
+    a.status = op->dev_status;
     return a;
 }
 
@@ -1152,6 +1342,65 @@ static cudaError_t launch_adj4(ApplyArgs<float> t, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when unavailable
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// TMA time phase; cudaErrorNotSupported when this chunk cannot use it (its
+// frames must be contiguous 128-byte rows: one chunk holding the whole batch,
+// B = BC in {4, 8, 16, 32}, frame count a multiple of 32 / BC)
+template <int BC, int P>
+static cudaError_t launch_adj5(ApplyArgs<float> t, int* status, cudaStream_t st) {
+    if constexpr (BC < 4) {
+        return cudaErrorNotSupported;
+    } else {
+        constexpr int FPR = T5Box<BC, P>::kFPR;
+        if (!vec_ok(t) || t.Bc != BC || t.B != BC || (t.Tn % FPR) != 0 || !status)
+            return cudaErrorNotSupported;
+        const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) return cudaErrorNotSupported;
+        constexpr int ROWS = T5Box<BC, P>::kRows;
+        static_assert(ROWS <= 256, "TMA box rows");
+        const uint64_t n_rows128 = (uint64_t)t.seg.total * (uint64_t)t.Tn / FPR;
+        if (n_rows128 == 0 || n_rows128 >= (1ull << 31)) return cudaErrorNotSupported;
+        CUtensorMap m;
+        cuuint64_t dims[2] = {32, (cuuint64_t)n_rows128};  // 32 floats = 128 bytes per row
+        cuuint64_t strides[1] = {128};
+        cuuint32_t box[2] = {32, (cuuint32_t)ROWS};
+        cuuint32_t es[2] = {1, 1};
+        if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(t.in), dims, strides, box,
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+        t.n_tasks = t.n_rays_total;
+        const size_t smem =
+            1024 + (size_t)kAdj5Warps * 2 * T5Box<BC, P>::kStride + (size_t)kAdj5Warps * 16;
+        cudaError_t e = cudaFuncSetAttribute(adj_time5_kernel<BC, P>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_time5_kernel<BC, P>,
+                                                      kAdj5Warps * 32, smem);
+        if (per_sm < 1) per_sm = 1;
+        const int64_t want = (t.n_tasks + kAdj5Warps - 1) / kAdj5Warps;
+        const int64_t cap = (int64_t)sm_count() * per_sm;
+        const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+        adj_time5_kernel<BC, P><<<grid, kAdj5Warps * 32, smem, st>>>(m, t, status);
+        return cudaGetLastError();
+    }
+}
+
 template <typename T, int BC>
 static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStream_t st) {
     // staged frames per 32-hat group, rounded so the swizzle stays in bounds
@@ -1161,11 +1410,17 @@ static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStr
     cudaError_t e = cudaSuccess;
     bool periodic = false;
     if constexpr (sizeof(T) == 4) {
-        const int P = v.time == 2 ? frames_per_hat(a.D) : 0;
+        const int P = v.time >= 2 ? frames_per_hat(a.D) : 0;
         if (a.seg.total > 0 && P > 0) {
             periodic = true;
-            e = P == 2 ? launch_adj4<BC, 2>(a, st)
-                       : (P == 4 ? launch_adj4<BC, 4>(a, st) : launch_adj4<BC, 8>(a, st));
+            e = cudaErrorNotSupported;
+            if (v.time == 3 && (P == 2 || P == 4))
+                e = P == 2 ? launch_adj5<BC, 2>(a, a.status, st) : launch_adj5<BC, 4>(a, a.status, st);
+            if (e == cudaErrorNotSupported) {
+                cudaGetLastError();  // clear the "not supported" marker, if any
+                e = P == 2 ? launch_adj4<BC, 2>(a, st)
+                           : (P == 4 ? launch_adj4<BC, 4>(a, st) : launch_adj4<BC, 8>(a, st));
+            }
             if (e != cudaSuccess) return e;
         }
     }

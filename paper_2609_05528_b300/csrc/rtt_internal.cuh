@@ -41,7 +41,8 @@ struct ApplyVariant {
     int8_t fwd = 0;     // forward: 1 staged z (fwd3), 2 lane-per-hat shuffles (fwd4)
     int8_t fwd_bc = 0;  // batch entries per forward task (power of two)
     int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
-    int8_t time = 0;    // adjoint phase 1: 1 general (adj_time3), 2 periodic (adj_time4)
+    int8_t time = 0;    // adjoint phase 1: 1 general (adj_time3), 2 periodic (adj_time4),
+                        // 3 periodic with TMA-staged frames (adj_time5)
     int8_t space = 0;   // adjoint phase 2: 1 scalar (adj_space3), 2 16-byte (adj_space4)
 };
 constexpr int kMaxTuned = 8;  // batch sizes with an autotuned variant per operator
@@ -96,6 +97,7 @@ struct rtt_op_s {
     void* fpartial = nullptr;
     size_t fpartial_bytes = 0;
     bool use_fused_adjoint = false;  // tile-fused adjoint (measured slower than two-phase so far)
+    int* dev_status = nullptr;  // device status word: bit 0 = a kernel's bounded wait timed out
     // autotuned kernel variants (rtt_autotune), per batch size
     int n_tuned = 0;
     int tuned_batch[rtt::kMaxTuned] = {};

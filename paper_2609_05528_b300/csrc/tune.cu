@@ -1,7 +1,7 @@
 // Autotuner for the FP32 applies: for one operator and batch size, times
 // every kernel variant of the forward (staged or lane-per-hat, batch entries
-// per task) and of the two adjoint phases (general or periodic time
-// contraction, scalar or 16-byte gather) with CUDA events on the caller's
+// and frames per task) and of the two adjoint phases (general, periodic or
+// periodic TMA-staged time contraction; scalar or 16-byte gather) with CUDA events on the caller's
 // stream, and records the fastest in the operator.  All variants produce the
 // same bits (same per-output summation order and fused multiply-adds), so
 // tuning changes speed only.
@@ -62,6 +62,47 @@ struct Timer {
 };
 
 }  // namespace
+
+extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v) {
+    if (!op || batch < 1 || batch > 4096) {
+        set_error("invalid arguments (op=%p batch=%d)", (void*)op, batch);
+        return RTT_EINVAL;
+    }
+    if (!v) {  // back to the default rule
+        clear_variant(op, batch);
+        return RTT_OK;
+    }
+    const int bc = v->fwd_bc;
+    if (v->fwd_kernel < 1 || v->fwd_kernel > 2 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
+        v->fwd_half < 0 || v->fwd_half > 1 || v->time_kernel < 1 || v->time_kernel > 3 ||
+        v->space_kernel < 1 || v->space_kernel > 2) {
+        set_error("invalid variant (fwd %d bc %d half %d time %d space %d)", v->fwd_kernel, bc,
+                  v->fwd_half, v->time_kernel, v->space_kernel);
+        return RTT_EINVAL;
+    }
+    ApplyVariant a;
+    a.fwd = (int8_t)v->fwd_kernel;
+    a.fwd_bc = (int8_t)bc;
+    a.fwd_half = (int8_t)v->fwd_half;
+    a.time = (int8_t)v->time_kernel;
+    a.space = (int8_t)v->space_kernel;
+    set_variant(op, batch, a);
+    return RTT_OK;
+}
+
+extern "C" rtt_status rtt_get_variant(rtt_op op, int batch, rtt_variant* out) {
+    if (!op || batch < 1 || !out) {
+        set_error("invalid arguments");
+        return RTT_EINVAL;
+    }
+    const ApplyVariant a = variant_for(op, batch);
+    out->fwd_kernel = a.fwd;
+    out->fwd_bc = a.fwd_bc;
+    out->fwd_half = a.fwd_half;
+    out->time_kernel = a.time;
+    out->space_kernel = a.space;
+    return RTT_OK;
+}
 
 extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream,
                                    rtt_tune_result* out) {
@@ -149,7 +190,12 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     // adjoint: phase-1 x phase-2 variants (timed as the full adjoint)
     const float adj_rule = time_it(rule, true);
     float adj_best = adj_rule;
-    for (int tk = 1; tk <= (periodic ? 2 : 1); ++tk)
+    // the TMA-staged time phase needs the whole batch in one chunk of 16-byte
+    // multiples with whole frames per 128-byte row, and 2 or 4 frames per hat
+    const int P = periodic ? (int)(kFracOne / op->frame_D) : 0;
+    const bool tma_ok = (P == 2 || P == 4) && (B == 4 || B == 8 || B == 16 || B == 32) &&
+                        (op->time.n_frames % (32 / B)) == 0;
+    for (int tk = 1; tk <= (periodic ? (tma_ok ? 3 : 2) : 1); ++tk)
         for (int sk = 1; sk <= 2; ++sk) {
             ApplyVariant v = best;
             v.time = (int8_t)tk;

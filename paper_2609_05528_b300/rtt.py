@@ -93,6 +93,12 @@ class TuneResult(ctypes.Structure):
                 ("adj_ms_rule", ctypes.c_float), ("candidates", ctypes.c_int32)]
 
 
+class Variant(ctypes.Structure):
+    _fields_ = [("fwd_kernel", ctypes.c_int32), ("fwd_bc", ctypes.c_int32),
+                ("fwd_half", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
+                ("space_kernel", ctypes.c_int32)]
+
+
 # name -> (restype, argtypes)
 _SIGS = {
     "rtt_error_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -106,6 +112,7 @@ _SIGS = {
                                           ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]),
     "rtt_op_query": (ctypes.c_int, [vp, ctypes.POINTER(OpInfo)]),
     "rtt_arm_rows": (ctypes.c_int, [vp, ctypes.c_int, i64p]),
+    "rtt_op_status": (ctypes.c_int, [vp, i32p, ctypes.c_int, vp]),
     "rtt_apply_A": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_apply_AT": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_apply_A_f64": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
@@ -135,6 +142,8 @@ _SIGS = {
                                       ctypes.c_int, ctypes.POINTER(AuditRecord), dp, vp]),
     "rtt_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp,
                                     ctypes.POINTER(TuneResult)]),
+    "rtt_set_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(Variant)]),
+    "rtt_get_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(Variant)]),
     "rtt_destroy": (None, [vp]),
 }
 
@@ -253,6 +262,27 @@ class Operator:
         check(lib().rtt_autotune(self.handle, int(batch), int(arm_mask), _stream(stream),
                                  ctypes.byref(r)), "rtt_autotune")
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
+    def set_variant(self, batch: int, fwd_kernel=None, fwd_bc=None, fwd_half=0, time_kernel=None,
+                    space_kernel=None):
+        """rtt_set_variant; all None resets `batch` to the default rule."""
+        if fwd_kernel is None and fwd_bc is None and time_kernel is None and space_kernel is None:
+            check(lib().rtt_set_variant(self.handle, int(batch), None), "rtt_set_variant")
+            return
+        v = Variant(int(fwd_kernel), int(fwd_bc), int(fwd_half), int(time_kernel), int(space_kernel))
+        check(lib().rtt_set_variant(self.handle, int(batch), ctypes.byref(v)), "rtt_set_variant")
+
+    def get_variant(self, batch: int) -> dict:
+        v = Variant()
+        check(lib().rtt_get_variant(self.handle, int(batch), ctypes.byref(v)), "rtt_get_variant")
+        return {k: getattr(v, k) for k, _ in Variant._fields_}
+
+    def status(self, clear: bool = False, stream=None) -> int:
+        """rtt_op_status: device status word (0 = no bounded wait timed out)."""
+        v = ctypes.c_int32(0)
+        check(lib().rtt_op_status(self.handle, ctypes.byref(v), int(clear), _stream(stream)),
+              "rtt_op_status")
+        return int(v.value)
 
     def close(self):
         if getattr(self, "handle", None):
