@@ -420,8 +420,9 @@ rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_d
  * rtt_autotune -- choose the fastest kernel variants of the FP32 applies
  * (rtt_apply_A / rtt_apply_AT) of this operator for one batch size.  The
  * paper has no counterpart: this is a property of the GPU implementation.
- * Candidates: the forward with staged per-ray histories or with one hat per
- * lane and warp shuffles (the latter only when a frame step is 1/2, 1/4 or
+ * Candidates: the forward with staged per-ray histories (corner rows loaded
+ * by threads or by TMA tensor copies) or with one hat per lane and warp
+ * shuffles (the latter only when a frame step is 1/2, 1/4 or
  * 1/8 of a hat step), each with a few batch widths and frames per lane; the adjoint's
  * temporal phase (general, periodic-weight, or periodic-weight with frames
  * staged by TMA tensor copies) crossed with its spatial gather (scalar or
@@ -439,7 +440,7 @@ rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_d
  */
 typedef struct {
     int32_t batch;
-    int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat */
+    int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat, 3 staged with TMA corner copies */
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
     int32_t time_kernel;  /* adjoint phase 1: 1 general, 2 periodic weights, 3 periodic + TMA */
@@ -453,7 +454,9 @@ rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream, rtt_tu
 
 /* A kernel variant of the FP32 applies (the same choices rtt_autotune makes). */
 typedef struct {
-    int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat (periodic cadences; else staged) */
+    int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat (periodic cadences; else staged),
+                             3 staged with TMA corner copies (batch a multiple of 4;
+                             else staged) */
     int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32 */
     int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
     int32_t time_kernel;  /* 1 general, 2 periodic weights, 3 periodic + TMA (where

@@ -982,6 +982,179 @@ adj_time5_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float
     }
 }
 
+// Forward with the four corner slabs of x staged by the tensor memory
+// accelerator.  Same tasks, hat windows, interpolation and accumulation order
+// as fwd3_kernel<float, BC, FPL> (hence the same bits); what changes is how
+// x reaches shared memory: per ray, four 3D tiled copies (one per corner
+// node: BC batch entries x zwin hats starting at the window's first hat,
+// out-of-range hats zero-filled by the copy) land in a double buffer while
+// the previous ray is contracted, so the loads of ray e + 1 overlap the
+// arithmetic of ray e.  Waits are bounded as in adj_time5_kernel.
+template <int BC, int FPL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, BC * FPL <= 16 ? 3 : 2)
+fwd5_kernel(const __grid_constant__ CUtensorMap xmap, const ApplyArgs<float> a, int* status,
+            uint32_t slab_stride, uint32_t warp_bytes) {
+    static_assert(BC >= 4 && BC <= 32, "16-byte batch records");
+    constexpr int Q = BC / 4;
+    constexpr int FC = 32 * FPL;
+    extern __shared__ unsigned char smem6_raw[];
+    const uint32_t raw_u32 = smem_u32(smem6_raw);
+    const uint32_t base_u32 = (raw_u32 + 127) & ~127u;
+    unsigned char* base = smem6_raw + (base_u32 - raw_u32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // per warp: [stage 0: 4 slabs][stage 1: 4 slabs][z][2 mbarriers]
+    unsigned char* wbase = base + (size_t)warp * warp_bytes;
+    const uint32_t wbase_u32 = base_u32 + warp * warp_bytes;
+    float4* zsv = reinterpret_cast<float4*>(wbase + 8 * slab_stride);
+    const uint32_t bar0 = wbase_u32 + warp_bytes - 16;
+    const uint32_t box_bytes = (uint32_t)a.zwin * BC * 4;
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + warp;
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const uint64_t tmap = reinterpret_cast<uint64_t>(&xmap);
+    struct Item {
+        int64_t task;
+        int e, e_end, row_out, f_begin, b0, k_lo;
+    };
+    auto task_item = [&](int64_t task, Item& it) {
+        it.task = task;
+        const int bchunk = (int)(task % a.n_bchunk);
+        const int64_t t2 = task / a.n_bchunk;
+        const int fchunk = (int)(t2 % a.n_fchunk);
+        it.row_out = (int)(t2 / a.n_fchunk);
+        const int row = seg_in_row(a.seg, it.row_out);
+        it.f_begin = fchunk * FC;
+        it.b0 = bchunk * BC;
+        it.e = a.row_ptr[row];
+        it.e_end = a.row_ptr[row + 1];
+    };
+    auto set_window = [&](Item& it) {
+        const int f_end = min(a.Tn, it.f_begin + FC);
+        const int64_t U0 = (int64_t)a.K0[it.e] * kFracOne + (int64_t)a.F0[it.e];
+        it.k_lo = (int)((U0 - (int64_t)(f_end - 1) * a.D) >> kFracBits);
+    };
+    auto issue = [&](const Item& it, int b) {
+        if (lane != 0) return;
+        const uint32_t bar = bar0 + 8u * b;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(4 * box_bytes)
+                     : "memory");
+        const int n00 = a.node00[it.e], n01 = a.node01[it.e];
+        const int node[4] = {n00, n00 + a.n_phi, n01, n01 + a.n_phi};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t dst = wbase_u32 + (uint32_t)(4 * b + c) * slab_stride;
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+                "l"(tmap), "r"(it.b0), "r"(it.k_lo), "r"(node[c]), "r"(bar)
+                : "memory");
+        }
+    };
+    int64_t task = warp_global;
+    if (task >= a.n_tasks) return;
+    Item cur;
+    task_item(task, cur);
+    set_window(cur);
+    issue(cur, 0);
+    float acc[FPL][BC];
+#pragma unroll
+    for (int j = 0; j < FPL; ++j)
+#pragma unroll
+        for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+    for (uint32_t t = 0;; ++t) {
+        // the item after cur: next ray of the row, else the first ray of the next task
+        Item nxt = cur;
+        bool more = true;
+        if (cur.e + 1 < cur.e_end) {
+            ++nxt.e;
+        } else if (cur.task + n_warps < a.n_tasks) {
+            task_item(cur.task + n_warps, nxt);
+        } else {
+            more = false;
+        }
+        if (more) {
+            set_window(nxt);
+            issue(nxt, (t + 1) & 1);
+        }
+        if (!mbar_wait(bar0 + 8u * (t & 1), (t >> 1) & 1)) {
+            if (lane == 0) atomicOr(status, 1);
+            if (more) mbar_wait(bar0 + 8u * ((t + 1) & 1), ((t + 1) >> 1) & 1);
+            return;
+        }
+        // ray cur.e: z[k][.] = sum_c W_c x[node_c][k][.] from the staged slabs
+        const int f_end = min(a.Tn, cur.f_begin + FC);
+        const int64_t U0 = (int64_t)a.K0[cur.e] * kFracOne + (int64_t)a.F0[cur.e];
+        const int k_top = (int)((U0 - (int64_t)cur.f_begin * a.D) >> kFracBits);
+        const int nwin = k_top + 2 - cur.k_lo;
+        const float4 wv = a.W[cur.e];
+        const float4* slab = reinterpret_cast<const float4*>(wbase + (size_t)(4 * (t & 1)) * slab_stride);
+        const int sv = (int)(slab_stride / 16);  // float4 per slab
+        for (int o = lane; o < nwin * Q; o += 32) {
+            const float4 v0 = slab[o], v1 = slab[sv + o], v2 = slab[2 * sv + o], v3 = slab[3 * sv + o];
+            float4 z;
+            z.x = interp4(wv.x, v0.x, wv.y, v1.x, wv.z, v2.x, wv.w, v3.x);
+            z.y = interp4(wv.x, v0.y, wv.y, v1.y, wv.z, v2.y, wv.w, v3.y);
+            z.z = interp4(wv.x, v0.z, wv.y, v1.z, wv.z, v2.z, wv.w, v3.z);
+            z.w = interp4(wv.x, v0.w, wv.y, v1.w, wv.z, v2.w, wv.w, v3.w);
+            zsv[o] = z;
+        }
+        __syncwarp();
+        int64_t U = U0 - (int64_t)(cur.f_begin + lane) * a.D;
+        const int64_t dU = (int64_t)32 * a.D;
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) {
+            const int f = cur.f_begin + lane + 32 * j;
+            if (f < f_end) {
+                const int k0 = (int)(U >> kFracBits);
+                const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
+                const float g = 1.0f - fr;
+                const float4* z0 = zsv + (k0 - cur.k_lo) * Q;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float4 p0 = z0[q], p1 = z0[Q + q];
+                    acc[j][4 * q + 0] = hat2(acc[j][4 * q + 0], g, p0.x, fr, p1.x);
+                    acc[j][4 * q + 1] = hat2(acc[j][4 * q + 1], g, p0.y, fr, p1.y);
+                    acc[j][4 * q + 2] = hat2(acc[j][4 * q + 2], g, p0.z, fr, p1.z);
+                    acc[j][4 * q + 3] = hat2(acc[j][4 * q + 3], g, p0.w, fr, p1.w);
+                }
+            }
+            U -= dU;
+        }
+        __syncwarp();  // zs and stage t & 1 are free again
+        if (cur.e + 1 >= cur.e_end) {  // last ray of the task: write y
+            const int nb = min(BC, a.B - cur.b0);
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) {
+                const int f = cur.f_begin + lane + 32 * j;
+                if (f < f_end) {
+                    float* yo = a.out + ((int64_t)cur.row_out * a.Tn + f) * a.B + cur.b0;
+                    if (nb == BC) {
+#pragma unroll
+                        for (int q = 0; q < Q; ++q)
+                            reinterpret_cast<float4*>(yo)[q] = make_float4(
+                                acc[j][4 * q], acc[j][4 * q + 1], acc[j][4 * q + 2], acc[j][4 * q + 3]);
+                    } else {
+#pragma unroll
+                        for (int b = 0; b < BC; ++b)
+                            if (b < nb) yo[b] = acc[j][b];
+                    }
+                }
+#pragma unroll
+                for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+            }
+        }
+        if (!more) break;
+        cur = nxt;
+    }
+}
+
 // Adjoint phase 2, fast path: lanes over (hat, batch) of one node, nodes in
 // descending-load order; the incidence loop is unrolled by 4 so that four
 // zhat rows are in flight.
@@ -1251,6 +1424,106 @@ static cudaError_t launch_fwd4(ApplyArgs<float> a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when unavailable
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// TMA time phase; cudaErrorNotSupported when this chunk cannot use it (its
+// frames must be contiguous 128-byte rows: one chunk holding the whole batch,
+// B = BC in {4, 8, 16, 32}, frame count a multiple of 32 / BC)
+template <int BC, int P>
+static cudaError_t launch_adj5(ApplyArgs<float> t, int* status, cudaStream_t st) {
+    if constexpr (BC < 4) {
+        return cudaErrorNotSupported;
+    } else {
+        constexpr int FPR = T5Box<BC, P>::kFPR;
+        if (!vec_ok(t) || t.Bc != BC || t.B != BC || (t.Tn % FPR) != 0 || !status)
+            return cudaErrorNotSupported;
+        const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) return cudaErrorNotSupported;
+        constexpr int ROWS = T5Box<BC, P>::kRows;
+        static_assert(ROWS <= 256, "TMA box rows");
+        const uint64_t n_rows128 = (uint64_t)t.seg.total * (uint64_t)t.Tn / FPR;
+        if (n_rows128 == 0 || n_rows128 >= (1ull << 31)) return cudaErrorNotSupported;
+        CUtensorMap m;
+        cuuint64_t dims[2] = {32, (cuuint64_t)n_rows128};  // 32 floats = 128 bytes per row
+        cuuint64_t strides[1] = {128};
+        cuuint32_t box[2] = {32, (cuuint32_t)ROWS};
+        cuuint32_t es[2] = {1, 1};
+        if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(t.in), dims, strides, box,
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+        t.n_tasks = t.n_rays_total;
+        const size_t smem =
+            1024 + (size_t)kAdj5Warps * 2 * T5Box<BC, P>::kStride + (size_t)kAdj5Warps * 16;
+        cudaError_t e = cudaFuncSetAttribute(adj_time5_kernel<BC, P>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_time5_kernel<BC, P>,
+                                                      kAdj5Warps * 32, smem);
+        if (per_sm < 1) per_sm = 1;
+        const int64_t want = (t.n_tasks + kAdj5Warps - 1) / kAdj5Warps;
+        const int64_t cap = (int64_t)sm_count() * per_sm;
+        const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
+        adj_time5_kernel<BC, P><<<grid, kAdj5Warps * 32, smem, st>>>(m, t, status);
+        return cudaGetLastError();
+    }
+}
+
+// TMA forward; cudaErrorNotSupported when the batch layout cannot use it
+template <int BC, int FPL>
+static cudaError_t launch_fwd5(ApplyArgs<float> a, cudaStream_t st) {
+    if constexpr (BC < 4) {
+        return cudaErrorNotSupported;
+    } else {
+        if (!vec_ok(a) || !a.status) return cudaErrorNotSupported;
+        const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc) return cudaErrorNotSupported;
+        a.FC = 32 * FPL;
+        a.zwin = (int)ceil((a.FC - 1) * a.delta) + 3;
+        if (a.zwin > 256) return cudaErrorNotSupported;  // TMA box rows
+        a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
+        a.n_bchunk = (a.B + BC - 1) / BC;
+        a.n_tasks = (int64_t)a.seg.total * a.n_fchunk * a.n_bchunk;
+        if (a.n_tasks == 0) return cudaSuccess;
+        CUtensorMap m;
+        // x as a 3D tensor: batch (inner) x hats x nodes
+        cuuint64_t dims[3] = {(cuuint64_t)a.B, (cuuint64_t)a.K, (cuuint64_t)a.n_nodes};
+        cuuint64_t strides[2] = {(cuuint64_t)a.B * 4, (cuuint64_t)a.K * a.B * 4};
+        cuuint32_t box[3] = {(cuuint32_t)BC, (cuuint32_t)a.zwin, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(a.in), dims, strides, box,
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+        // per warp: 2 stages x 4 corner slabs (128-byte aligned), z, 2 mbarriers
+        const uint32_t slab_stride = ((uint32_t)a.zwin * BC * 4 + 127) & ~127u;
+        const uint32_t z_bytes = ((uint32_t)a.zwin * BC * 4 + 127) & ~127u;
+        const uint32_t warp_bytes = 8 * slab_stride + z_bytes + 128;  // last 16 bytes: mbarriers
+        const size_t smem = 128 + (size_t)kWarpsPerBlock * warp_bytes;
+        if (smem > 227 * 1024) return cudaErrorNotSupported;
+        cudaError_t e = cudaFuncSetAttribute(fwd5_kernel<BC, FPL>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        fwd5_kernel<BC, FPL><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(
+            m, a, a.status, slab_stride, warp_bytes);
+        return cudaGetLastError();
+    }
+}
+
 ApplyVariant variant_for(const rtt_op_s* op, int batch) {
     for (int i = 0; i < op->n_tuned; ++i)
         if (op->tuned_batch[i] == batch) return op->tuned[i];
@@ -1309,6 +1582,18 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
                 default: break;  // not a periodic cadence: staged kernel
             }
         }
+        if (v.fwd == 3 && bc >= 4) {
+            const bool half = v.fwd_half != 0;
+            cudaError_t e = cudaErrorNotSupported;
+            switch (bc) {
+                case 4: e = half ? launch_fwd5<4, 4>(a, st) : launch_fwd5<4, 8>(a, st); break;
+                case 8: e = half ? launch_fwd5<8, 2>(a, st) : launch_fwd5<8, 4>(a, st); break;
+                case 16: e = half ? launch_fwd5<16, 1>(a, st) : launch_fwd5<16, 2>(a, st); break;
+                default: e = launch_fwd5<32, 1>(a, st); break;
+            }
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();  // clear the "not supported" marker, if any
+        }
         return launch_fwd3_any<T>(a, bc, v.fwd_half != 0, st);
     } else {
         return launch_fwd3_any<T>(a, pick_bc(B), false, st);
@@ -1340,65 +1625,6 @@ static cudaError_t launch_adj4(ApplyArgs<float> t, cudaStream_t st) {
     const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
     adj_time4_kernel<BC, P><<<grid, kAdj3Warps * 32, smem, st>>>(t);
     return cudaGetLastError();
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library); null when unavailable
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            p = nullptr;
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }();
-    return fn;
-}
-
-// TMA time phase; cudaErrorNotSupported when this chunk cannot use it (its
-// frames must be contiguous 128-byte rows: one chunk holding the whole batch,
-// B = BC in {4, 8, 16, 32}, frame count a multiple of 32 / BC)
-template <int BC, int P>
-static cudaError_t launch_adj5(ApplyArgs<float> t, int* status, cudaStream_t st) {
-    if constexpr (BC < 4) {
-        return cudaErrorNotSupported;
-    } else {
-        constexpr int FPR = T5Box<BC, P>::kFPR;
-        if (!vec_ok(t) || t.Bc != BC || t.B != BC || (t.Tn % FPR) != 0 || !status)
-            return cudaErrorNotSupported;
-        const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-        if (!enc) return cudaErrorNotSupported;
-        constexpr int ROWS = T5Box<BC, P>::kRows;
-        static_assert(ROWS <= 256, "TMA box rows");
-        const uint64_t n_rows128 = (uint64_t)t.seg.total * (uint64_t)t.Tn / FPR;
-        if (n_rows128 == 0 || n_rows128 >= (1ull << 31)) return cudaErrorNotSupported;
-        CUtensorMap m;
-        cuuint64_t dims[2] = {32, (cuuint64_t)n_rows128};  // 32 floats = 128 bytes per row
-        cuuint64_t strides[1] = {128};
-        cuuint32_t box[2] = {32, (cuuint32_t)ROWS};
-        cuuint32_t es[2] = {1, 1};
-        if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(t.in), dims, strides, box,
-                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorNotSupported;
-        t.n_tasks = t.n_rays_total;
-        const size_t smem =
-            1024 + (size_t)kAdj5Warps * 2 * T5Box<BC, P>::kStride + (size_t)kAdj5Warps * 16;
-        cudaError_t e = cudaFuncSetAttribute(adj_time5_kernel<BC, P>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_time5_kernel<BC, P>,
-                                                      kAdj5Warps * 32, smem);
-        if (per_sm < 1) per_sm = 1;
-        const int64_t want = (t.n_tasks + kAdj5Warps - 1) / kAdj5Warps;
-        const int64_t cap = (int64_t)sm_count() * per_sm;
-        const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-        adj_time5_kernel<BC, P><<<grid, kAdj5Warps * 32, smem, st>>>(m, t, status);
-        return cudaGetLastError();
-    }
 }
 
 template <typename T, int BC>

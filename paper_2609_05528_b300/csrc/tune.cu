@@ -73,7 +73,7 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
         return RTT_OK;
     }
     const int bc = v->fwd_bc;
-    if (v->fwd_kernel < 1 || v->fwd_kernel > 2 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
+    if (v->fwd_kernel < 1 || v->fwd_kernel > 3 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
         v->fwd_half < 0 || v->fwd_half > 1 || v->time_kernel < 1 || v->time_kernel > 3 ||
         v->space_kernel < 1 || v->space_kernel > 2) {
         set_error("invalid variant (fwd %d bc %d half %d time %d space %d)", v->fwd_kernel, bc,
@@ -171,14 +171,16 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     // with the widest batch chunk and one or two narrower ones
     const float fwd_rule = time_it(rule, false);
     float fwd_best = fwd_rule;
-    for (int kind = 1; kind <= (periodic ? 2 : 1); ++kind)
+    const bool x_vec = (B % 4) == 0;  // 16-byte batch records: TMA forward possible
+    for (int kind = 1; kind <= 3; ++kind)
         for (int bc = bc_max; bc >= 1 && bc >= bc_max / 4; bc >>= 1)
-            for (int half = 0; half <= (kind == 1 && bc < 32 ? 1 : 0); ++half) {
+            for (int half = 0; half <= (kind != 2 && bc < 32 ? 1 : 0); ++half) {
                 ApplyVariant v = rule;
                 v.fwd = (int8_t)kind;
                 v.fwd_bc = (int8_t)bc;
                 v.fwd_half = (int8_t)half;
-                if (kind == 2 && bc > 8) continue;  // the lane-per-hat kernel holds <= 8 per task
+                if (kind == 2 && (!periodic || bc > 8)) continue;  // lane-per-hat: <= 8 per task
+                if (kind == 3 && (!x_vec || bc < 4)) continue;    // TMA: 16-byte records
                 const float ms = time_it(v, false);
                 if (ms < fwd_best) {
                     fwd_best = ms;
@@ -220,7 +222,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     out->fwd_bc = best.fwd_bc;
     out->fwd_frames_per_lane =
         best.fwd == 2 ? (int32_t)(kFracOne / op->frame_D)
-                      : (best.fwd_bc >= 32 ? 1 : 32 / best.fwd_bc) / (best.fwd_half ? 2 : 1);
+                      : (best.fwd_bc >= 32 ? 1 : (32 / best.fwd_bc) / (best.fwd_half ? 2 : 1));
     out->time_kernel = best.time;
     out->space_kernel = best.space;
     out->fwd_ms = fwd_best;

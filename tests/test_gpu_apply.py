@@ -205,7 +205,7 @@ def test_every_variant_same_bits(which, small, schw, B):
     while bc_max < min(B, 32):
         bc_max *= 2
     n = 0
-    for fk in (1, 2):
+    for fk in (1, 2, 3):
         for bc in sorted({bc_max, max(1, bc_max // 2), max(1, bc_max // 4)}):
             for half in (0, 1):
                 c.op.set_variant(B, fk, bc, half, 2, 2)
@@ -218,7 +218,7 @@ def test_every_variant_same_bits(which, small, schw, B):
             n += 1
     c.op.set_variant(B)
     assert c.op.status(clear=True) == 0
-    assert n >= 8
+    assert n >= 12
 
 
 def test_direct_zero_columns_bit_exact(schw):
