@@ -221,6 +221,27 @@ rtt_status rtt_apply_AT_f64(rtt_op op, const double* y_dev, double* x_dev, int b
                             int arm_mask, void* stream);
 
 /*
+ * rtt_apply_A_AT -- the forward and adjoint pair of the reconstruction loss
+ * L(x) = 1/2 ||scale A x - d||^2 (Eq. 2-3 and the explicit adjoint action of
+ * Sec. 5): y = scale * A x and g = scale * A^T (y - d) = grad L, in one call.
+ * x_dev: float [n_nodes][n_hats][batch]; d_dev: float [arm_rows][n_frames]
+ * [batch] or NULL (then g = scale * A^T y); y_dev: float [arm_rows][n_frames]
+ * [batch] (written; may be NULL only when the arm has no rows); g_dev: float
+ * [n_nodes][n_hats][batch] (written).  For batch 4 or 8, 16-byte aligned
+ * buffers and 2, 4 or 8 frames per hat step, a fused kernel can compute y
+ * and keep y - d in shared memory for the temporal half of the adjoint, so y
+ * is not read back from HBM; it runs when the operator's variant for this
+ * batch says so (rtt_autotune picks it where it is faster, rtt_set_variant
+ * pins it).  Otherwise the separate forward and adjoint run (y - d formed in
+ * an operator-owned scratch that grows on demand).
+ * Both paths give the bits of rtt_apply_A followed by rtt_apply_AT on
+ * (y - d) rounded to FP32.  Asynchronous on `stream`.
+ * Errors: RTT_EINVAL, RTT_ENOMEM, RTT_ECUDA.
+ */
+rtt_status rtt_apply_A_AT(rtt_op op, const float* x_dev, const float* d_dev, float* y_dev,
+                          float* g_dev, int batch, int arm_mask, void* stream);
+
+/*
  * rtt_probe_info -- age information of the scalar probe (Sec. 3.3 Eq. 10-12,
  * Sec. 4.4 Eq. 29): I(a) = || C^{-1/2} A_arm q_a ||^2 with
  * q_a = 1_[r_in, r_out](r) / N_h exp(-(t + a)^2 / (2 h^2)),
@@ -448,6 +469,8 @@ typedef struct {
     float fwd_ms, adj_ms;           /* chosen variants, ms per apply */
     float fwd_ms_rule, adj_ms_rule; /* the untuned default rule, ms per apply */
     int32_t candidates;             /* configurations timed */
+    int32_t fused_step;  /* rtt_apply_A_AT uses the fused kernel (1) or the separate pair (0) */
+    float fused_ms;      /* the fused pair, ms per call (0 where it cannot run) */
 } rtt_tune_result;
 
 rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream, rtt_tune_result* out);
@@ -463,6 +486,8 @@ typedef struct {
                              the cadence or the buffers do not allow 2 or 3, the
                              next one down runs) */
     int32_t space_kernel; /* 1 scalar, 2 16-byte loads (where the buffers allow) */
+    int32_t fused_step;   /* rtt_apply_A_AT: 1 = fused forward + temporal adjoint where the
+                             batch, cadence and buffers allow it, 0 = separate pair */
 } rtt_variant;
 
 /*

@@ -28,6 +28,9 @@ void set_error(const char* fmt, ...) {
 template <typename T>
 cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
 rtt_status build_visits(rtt_op_s* op, cudaStream_t st);
+cudaError_t launch_forward_adjoint_fused(const rtt_op_s* op, const float* x, const float* d,
+                                         float* y, float* g, int B, const ArmSeg& seg,
+                                         float* zhat, cudaStream_t st);
 size_t fused_partial_bytes(const rtt_op_s* op);
 template <typename T>
 cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
@@ -227,7 +230,7 @@ static void free_op(rtt_op_s* op) {
                   op->K0,      op->F0,      op->F64,    op->r,      op->delay, op->weight,
                   op->thr,     op->node_ptr, op->inc,   op->row_order, op->zhat,
                   op->visits,  op->items,    op->split_tiles, op->fpartial, op->node_order,
-                  op->dev_status};
+                  op->dev_status, op->rscratch};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete op;
@@ -529,6 +532,14 @@ rtt_status ensure_zhat_bytes(rtt_op_s* op, size_t bytes) {
     return RTT_OK;
 }
 
+// r = y - d, elementwise (FP32, one rounding)
+__global__ void residual_kernel(const float* __restrict__ y, const float* __restrict__ d,
+                                float* __restrict__ r, int64_t n) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        r[i] = y[i] - d[i];
+}
+
 template <typename T>
 static rtt_status apply_common(rtt_op op, const T* in, T* out, int batch, int mask, void* stream,
                                bool adjoint) {
@@ -685,6 +696,59 @@ rtt_status rtt_arm_rows(rtt_op op, int mask, int64_t* rows) {
 rtt_status rtt_apply_A(rtt_op op, const float* x, float* y, int batch, int mask, void* stream) {
     return apply_common<float>(op, x, y, batch, mask, stream, false);
 }
+rtt_status rtt_apply_A_AT(rtt_op op, const float* x, const float* d, float* y, float* g, int batch,
+                          int mask, void* stream) {
+    if (!op || batch < 1 || !x || !g) {
+        set_error("invalid argument (op=%p batch=%d x=%p g=%p)", (void*)op, batch, (const void*)x,
+                  (void*)g);
+        return RTT_EINVAL;
+    }
+    ArmSeg seg;
+    RTT_TRY(make_seg(op, mask, &seg));
+    if (seg.total > 0 && !y) {
+        set_error("null y with %d arm rows", seg.total);
+        return RTT_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int bc = batch < 32 ? batch : 32;
+    RTT_TRY(ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * bc * sizeof(float)));
+    cudaError_t e = cudaErrorNotSupported;
+    if (variant_for(op, batch).fused)
+        e = launch_forward_adjoint_fused(op, x, d, y, g, batch, seg, (float*)op->zhat, st);
+    if (e == cudaErrorNotSupported) {  // separate forward and adjoint
+        e = launch_forward<float>(op, x, y, batch, seg, st);
+        const float* r = y;
+        const int64_t n = (int64_t)seg.total * op->time.n_frames * batch;
+        if (e == cudaSuccess && d && n > 0) {
+            const size_t bytes = (size_t)n * sizeof(float);
+            if (bytes > op->rscratch_bytes) {
+                if (op->rscratch) {
+                    cudaStreamSynchronize(st);
+                    cudaFree(op->rscratch);
+                    op->rscratch = nullptr;
+                    op->rscratch_bytes = 0;
+                }
+                if (cudaMalloc(&op->rscratch, bytes) != cudaSuccess) {
+                    op->rscratch = nullptr;
+                    set_error("residual scratch of %zu bytes: allocation failed", bytes);
+                    return RTT_ENOMEM;
+                }
+                op->rscratch_bytes = bytes;
+            }
+            residual_kernel<<<blocks(n < ((int64_t)1 << 24) ? n : ((int64_t)1 << 24)), 256, 0, st>>>(
+                y, d, (float*)op->rscratch, n);
+            e = cudaGetLastError();
+            r = (const float*)op->rscratch;
+        }
+        if (e == cudaSuccess) e = launch_adjoint<float>(op, r, g, batch, seg, (float*)op->zhat, st);
+    }
+    if (e != cudaSuccess) {
+        set_error("apply launch failed: %s", cudaGetErrorString(e));
+        return RTT_ECUDA;
+    }
+    return RTT_OK;
+}
+
 rtt_status rtt_apply_AT(rtt_op op, const float* y, float* x, int batch, int mask, void* stream) {
     return apply_common<float>(op, y, x, batch, mask, stream, true);
 }

@@ -1155,6 +1155,237 @@ fwd5_kernel(const __grid_constant__ CUtensorMap xmap, const ApplyArgs<float> a, 
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused forward + adjoint phase 1 (FP32, a frame step 1/P of a hat step, the
+// whole batch of B = BC in {4, 8} entries in one chunk).  y = scale A x is
+// computed exactly as fwd3_kernel<float, BC, FPL> computes it and written;
+// r = y - d (d optional) is kept in shared memory, and the per-ray temporal
+// contraction zhat_e = H_e^T r_row is taken from there with the periodic
+// weights of adj_time4_kernel, so the adjoint never reads y back from HBM.
+// A CTA owns a group of RG rows at a time: phase 1 spreads the (row, frame
+// chunk) tasks of the group over its warps, phase 2 the (ray, 32-hat group)
+// items of the group's rays.  Outputs are the bits of the separate applies.
+// ---------------------------------------------------------------------------
+
+// one (row, frame chunk) task of the staged forward into acc (fwd3 arithmetic)
+template <int BC, int FPL>
+__device__ __forceinline__ void fwd_task_vec(const ApplyArgs<float>& a, int row, int f_begin,
+                                             int f_end, float4* zsv, int lane,
+                                             float (&acc)[FPL][BC]) {
+    constexpr int Q = BC / 4;
+#pragma unroll
+    for (int j = 0; j < FPL; ++j)
+#pragma unroll
+        for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+    const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
+    for (int e = e_begin; e < e_end; ++e) {
+        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
+        const int k_top = (int)((U0 - (int64_t)f_begin * a.D) >> kFracBits);
+        const int k_lo = (int)((U0 - (int64_t)(f_end - 1) * a.D) >> kFracBits);
+        const int nwin = k_top + 2 - k_lo;
+        const float4 wv = a.W[e];
+        const int n00 = a.node00[e], n01 = a.node01[e];
+        const int64_t KB = (int64_t)a.K * a.B;
+        const float* x00 = a.in + (int64_t)n00 * KB;
+        const float* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB;
+        const float* x01 = a.in + (int64_t)n01 * KB;
+        const float* x11 = a.in + (int64_t)(n01 + a.n_phi) * KB;
+        const int n_items = nwin * Q;
+        for (int base = 0; base < n_items; base += 64) {
+            float4 v[2][4];
+            bool okv[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int o = base + lane + 32 * u;
+                const int kk = o / Q, q = o - kk * Q;
+                const int k = k_lo + kk;
+                okv[u] = o < n_items && k >= 0 && k < a.K;
+                if (okv[u]) {
+                    const int64_t off = (int64_t)k * a.B + 4 * q;
+                    v[u][0] = __ldg(reinterpret_cast<const float4*>(x00 + off));
+                    v[u][1] = __ldg(reinterpret_cast<const float4*>(x10 + off));
+                    v[u][2] = __ldg(reinterpret_cast<const float4*>(x01 + off));
+                    v[u][3] = __ldg(reinterpret_cast<const float4*>(x11 + off));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int o = base + lane + 32 * u;
+                if (o < n_items) {
+                    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (okv[u]) {
+                        z.x = interp4(wv.x, v[u][0].x, wv.y, v[u][1].x, wv.z, v[u][2].x, wv.w, v[u][3].x);
+                        z.y = interp4(wv.x, v[u][0].y, wv.y, v[u][1].y, wv.z, v[u][2].y, wv.w, v[u][3].y);
+                        z.z = interp4(wv.x, v[u][0].z, wv.y, v[u][1].z, wv.z, v[u][2].z, wv.w, v[u][3].z);
+                        z.w = interp4(wv.x, v[u][0].w, wv.y, v[u][1].w, wv.z, v[u][2].w, wv.w, v[u][3].w);
+                    }
+                    zsv[o] = z;
+                }
+            }
+        }
+        __syncwarp();
+        int64_t U = U0 - (int64_t)(f_begin + lane) * a.D;
+        const int64_t dU = (int64_t)32 * a.D;
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) {
+            const int f = f_begin + lane + 32 * j;
+            if (f < f_end) {
+                const int k0 = (int)(U >> kFracBits);
+                const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
+                const float g = 1.0f - fr;
+                const float4* z0 = zsv + (k0 - k_lo) * Q;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float4 p0 = z0[q], p1 = z0[Q + q];
+                    acc[j][4 * q + 0] = hat2(acc[j][4 * q + 0], g, p0.x, fr, p1.x);
+                    acc[j][4 * q + 1] = hat2(acc[j][4 * q + 1], g, p0.y, fr, p1.y);
+                    acc[j][4 * q + 2] = hat2(acc[j][4 * q + 2], g, p0.z, fr, p1.z);
+                    acc[j][4 * q + 3] = hat2(acc[j][4 * q + 3], g, p0.w, fr, p1.w);
+                }
+            }
+            U -= dU;
+        }
+        __syncwarp();
+    }
+}
+
+constexpr int kFusedMaxRows = 32;  // rows per CTA group (shared r rows)
+
+template <int BC, int FPL, int P>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
+fused_kernel(const ApplyArgs<float> a, const float* __restrict__ d, int RG, int row_v4) {
+    constexpr int Q = BC / 4;
+    constexpr int FC = 32 * FPL;
+    extern __shared__ __align__(16) unsigned char smem7_raw[];
+    float4* rs = reinterpret_cast<float4*>(smem7_raw);  // [RG][row_v4] swizzled r rows
+    float4* zsv = rs + (size_t)RG * row_v4 + (size_t)(threadIdx.x >> 5) * a.zwin * Q;
+    __shared__ int ray_prefix[kFusedMaxRows + 1];  // rays of the group's rows, prefix sums
+    __shared__ int work[2];                          // next phase-1 / phase-2 item
+    const int lane = threadIdx.x & 31;
+    const int pshift = a.FC;  // swizzle key shift (log2 P, at least 1 when Q = 1)
+    const int n_groups_k = (a.K + 31) / 32;
+    const int32_t D32 = (int32_t)a.D;
+    // rays outside the arm: zero zhat rows (their data rows do not exist)
+    if (a.seg.total < a.seg_rows_all) {
+        const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+        const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = tid; i < a.n_rays_total * a.K; i += nth) {
+            const int64_t e = i / a.K;
+            if (seg_out_row(a.seg, a.ray_row[e]) < 0) {
+                float4* zo = reinterpret_cast<float4*>(a.zhat + i * BC);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) zo[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    }
+    const int n_row_groups = (a.seg.total + RG - 1) / RG;
+    for (int grp = blockIdx.x; grp < n_row_groups; grp += gridDim.x) {
+        const int first = grp * RG;
+        const int rows_here = min(RG, a.seg.total - first);
+        if (threadIdx.x == 0) {
+            int acc_rays = 0;
+            ray_prefix[0] = 0;
+            for (int i = 0; i < RG; ++i) {
+                if (i < rows_here) {
+                    const int row = seg_in_row(a.seg, first + i);
+                    acc_rays += a.row_ptr[row + 1] - a.row_ptr[row];
+                }
+                ray_prefix[i + 1] = acc_rays;
+            }
+            work[0] = 0;
+            work[1] = 0;
+        }
+        __syncthreads();
+        // phase 1: forward tasks (row of the group, frame chunk), taken by
+        // warps as they become free (rows differ in ray count)
+        const int n1 = rows_here * a.n_fchunk;
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(&work[0], 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= n1) break;
+            const int rl = it / a.n_fchunk, fchunk = it - rl * a.n_fchunk;
+            const int row_out = first + rl;
+            const int row = seg_in_row(a.seg, row_out);
+            const int f_begin = fchunk * FC, f_end = min(a.Tn, f_begin + FC);
+            float acc[FPL][BC];
+            fwd_task_vec<BC, FPL>(a, row, f_begin, f_end, zsv, lane, acc);
+            float4* rrow = rs + (size_t)rl * row_v4;
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) {
+                const int f = f_begin + lane + 32 * j;
+                if (f >= f_end) continue;
+                const int64_t yo = ((int64_t)row_out * a.Tn + f) * a.B;
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float4 yv = make_float4(acc[j][4 * q], acc[j][4 * q + 1], acc[j][4 * q + 2],
+                                                  acc[j][4 * q + 3]);
+                    reinterpret_cast<float4*>(a.out + yo)[q] = yv;
+                    float4 rv = yv;
+                    if (d) {
+                        const float4 dv = __ldg(reinterpret_cast<const float4*>(d + yo) + q);
+                        rv = make_float4(yv.x - dv.x, yv.y - dv.y, yv.z - dv.z, yv.w - dv.w);
+                    }
+                    rrow[swz(f, q, Q, pshift)] = rv;
+                }
+            }
+        }
+        __syncthreads();
+        // phase 2: zhat for every ray of the group's rows (ray, 32-hat group)
+        const int n2 = ray_prefix[RG] * n_groups_k;
+        for (;;) {
+            int it = 0;
+            if (lane == 0) it = atomicAdd(&work[1], 1);
+            it = __shfl_sync(0xffffffffu, it, 0);
+            if (it >= n2) break;
+            const int ri = it / n_groups_k, g = it - ri * n_groups_k;
+            // row of ray ri: the last rl with ray_prefix[rl] <= ri (prefix sums)
+            int lo = 0, hi = rows_here;  // ray_prefix[lo] <= ri < ray_prefix[hi]
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (ray_prefix[mid] <= ri) lo = mid; else hi = mid;
+            }
+            const int rl = lo;
+            const int row = seg_in_row(a.seg, first + rl);
+            const int64_t e = (int64_t)a.row_ptr[row] + (ri - ray_prefix[rl]);
+            const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
+            const int64_t c0 = (U0 * P) >> kFracBits;
+            const int32_t r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
+            const int fbase = (int)(c0 + 1 - P);
+            float wt[2 * P];
+#pragma unroll
+            for (int j = 0; j < 2 * P; ++j)
+                wt[j] = 1.0f - (float)abs(r0 - j * D32) * (1.0f / (float)kFracOne);
+            const int k = 32 * g + lane;
+            if (k < a.K) {
+                float accz[BC];
+#pragma unroll
+                for (int b = 0; b < BC; ++b) accz[b] = 0.0f;
+                const float4* rrow = rs + (size_t)rl * row_v4;
+                const int f0 = fbase - P * k;
+#pragma unroll
+                for (int j = 0; j < 2 * P; ++j) {
+                    const int f = f0 + j;
+                    if (f < 0 || f >= a.Tn) continue;  // outside the observation
+#pragma unroll
+                    for (int q = 0; q < Q; ++q) {
+                        const float4 v = rrow[swz(f, q, Q, pshift)];
+                        accz[4 * q + 0] = fmac(wt[j], v.x, accz[4 * q + 0]);
+                        accz[4 * q + 1] = fmac(wt[j], v.y, accz[4 * q + 1]);
+                        accz[4 * q + 2] = fmac(wt[j], v.z, accz[4 * q + 2]);
+                        accz[4 * q + 3] = fmac(wt[j], v.w, accz[4 * q + 3]);
+                    }
+                }
+                float4* zo = reinterpret_cast<float4*>(a.zhat + (e * a.K + k) * BC);
+#pragma unroll
+                for (int q = 0; q < Q; ++q)
+                    zo[q] = make_float4(accz[4 * q], accz[4 * q + 1], accz[4 * q + 2], accz[4 * q + 3]);
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Adjoint phase 2, fast path: lanes over (hat, batch) of one node, nodes in
 // descending-load order; the incidence loop is unrolled by 4 so that four
 // zhat rows are in flight.
@@ -1628,16 +1859,17 @@ static cudaError_t launch_adj4(ApplyArgs<float> t, cudaStream_t st) {
 }
 
 template <typename T, int BC>
-static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStream_t st) {
+static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStream_t st,
+                                  bool time_phase = true) {
     // staged frames per 32-hat group, rounded so the swizzle stays in bounds
     int ywin = (int)ceil(33.0 / a.delta) + 2;
     ywin = (ywin + 7) & ~7;
     const size_t smem = (size_t)kAdj3Warps * ywin * BC * sizeof(T);
     cudaError_t e = cudaSuccess;
-    bool periodic = false;
+    bool periodic = !time_phase;  // true once phase 1 is done (or not wanted)
     if constexpr (sizeof(T) == 4) {
         const int P = v.time >= 2 ? frames_per_hat(a.D) : 0;
-        if (a.seg.total > 0 && P > 0) {
+        if (!periodic && a.seg.total > 0 && P > 0) {
             periodic = true;
             e = cudaErrorNotSupported;
             if (v.time == 3 && (P == 2 || P == 4))
@@ -1709,8 +1941,20 @@ cudaError_t launch_adjoint_fused(const rtt_op_s* op, const float* y, float* x, i
                                  int Bc, const ArmSeg& seg, float* partial, cudaStream_t st);
 
 template <typename T>
+static cudaError_t launch_adjoint_impl(const rtt_op_s* op, const T* y, T* x, int B,
+                                       const ArmSeg& seg, T* zhat, cudaStream_t st,
+                                       bool time_phase);
+
+template <typename T>
 cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const ArmSeg& seg,
                            T* zhat, cudaStream_t st) {
+    return launch_adjoint_impl<T>(op, y, x, B, seg, zhat, st, true);
+}
+
+template <typename T>
+static cudaError_t launch_adjoint_impl(const rtt_op_s* op, const T* y, T* x, int B,
+                                       const ArmSeg& seg, T* zhat, cudaStream_t st,
+                                       bool time_phase) {
     if (seg.total == 0)  // no data rows in the arm: A^T y = 0
         return cudaMemsetAsync(x, 0, (size_t)op->n_nodes * op->time.n_hats * B * sizeof(T), st);
     // batch chunks of at most 32 entries share the zhat scratch [E][K][32]
@@ -1725,7 +1969,7 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         v.time = 1;
         v.space = 1;
         if constexpr (sizeof(T) == 4) {
-            if (op->use_fused_adjoint && (op->fpartial || op->n_partial_slots == 0)) {
+            if (time_phase && op->use_fused_adjoint && (op->fpartial || op->n_partial_slots == 0)) {
                 e = launch_adjoint_fused(op, y, x, B, b_first, Bc, seg, (float*)op->fpartial, st);
                 if (e == cudaSuccess) continue;
                 if (e != cudaErrorNotSupported) return e;
@@ -1734,16 +1978,72 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
             v = variant_for(op, B);
         }
         switch (pick_bc(Bc)) {
-            case 1: e = launch_adj3_bc<T, 1>(a, v, st); break;
-            case 2: e = launch_adj3_bc<T, 2>(a, v, st); break;
-            case 4: e = launch_adj3_bc<T, 4>(a, v, st); break;
-            case 8: e = launch_adj3_bc<T, 8>(a, v, st); break;
-            case 16: e = launch_adj3_bc<T, 16>(a, v, st); break;
-            default: e = launch_adj3_bc<T, 32>(a, v, st); break;
+            case 1: e = launch_adj3_bc<T, 1>(a, v, st, time_phase); break;
+            case 2: e = launch_adj3_bc<T, 2>(a, v, st, time_phase); break;
+            case 4: e = launch_adj3_bc<T, 4>(a, v, st, time_phase); break;
+            case 8: e = launch_adj3_bc<T, 8>(a, v, st, time_phase); break;
+            case 16: e = launch_adj3_bc<T, 16>(a, v, st, time_phase); break;
+            default: e = launch_adj3_bc<T, 32>(a, v, st, time_phase); break;
         }
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+template <int BC, int FPL, int P>
+static cudaError_t launch_fused(ApplyArgs<float> a, const float* d, cudaStream_t st) {
+    constexpr int Q = BC / 4;
+    int ps = 0;
+    while ((2 << ps) <= P) ++ps;  // swizzle key shift log2 P (>= 1)
+    a.FC = ps;
+    a.zwin = (int)ceil((32 * FPL - 1) * a.delta) + 3;
+    a.n_fchunk = (a.Tn + 32 * FPL - 1) / (32 * FPL);
+    const int row_v4 = (a.Tn * Q + 7) & ~7;
+    // rows per group: about 64 KB of r rows, at most kFusedMaxRows
+    int RG = (int)((64 * 1024) / ((size_t)row_v4 * 16));
+    RG = RG < 1 ? 1 : (RG > kFusedMaxRows ? kFusedMaxRows : RG);
+    const size_t smem = ((size_t)RG * row_v4 + (size_t)kWarpsPerBlock * a.zwin * Q) * 16;
+    if (smem > 200 * 1024) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(fused_kernel<BC, FPL, P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<BC, FPL, P>,
+                                                  kWarpsPerBlock * 32, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int64_t groups = (a.seg.total + RG - 1) / RG;
+    const int64_t cap = (int64_t)sm_count() * per_sm;
+    const int grid = (int)(groups < cap ? (groups > 0 ? groups : 1) : cap);
+    fused_kernel<BC, FPL, P><<<grid, kWarpsPerBlock * 32, smem, st>>>(a, d, RG, row_v4);
+    return cudaGetLastError();
+}
+
+// y = scale A x and x_out = scale A^T (y - d) in one forward pass plus the
+// gather, when the operator and buffers allow the fused kernel (FP32 batch
+// of 4 or 8, 16-byte aligned buffers, 2, 4 or 8 frames per hat step);
+// cudaErrorNotSupported otherwise (nothing launched)
+cudaError_t launch_forward_adjoint_fused(const rtt_op_s* op, const float* x, const float* d,
+                                         float* y, float* g, int B, const ArmSeg& seg,
+                                         float* zhat, cudaStream_t st) {
+    const int P = frames_per_hat(op->frame_D);
+    if ((B != 4 && B != 8) || P == 0 || seg.total == 0) return cudaErrorNotSupported;
+    if (((uintptr_t)x | (uintptr_t)y | (uintptr_t)g | (uintptr_t)(d ? d : y)) % 16 != 0)
+        return cudaErrorNotSupported;
+    ApplyArgs<float> a = base_args<float>(op, x, y, B, seg);
+    a.zhat = zhat;
+    a.Bc = B;
+    a.n_rays_total = op->n_rays;
+    a.vec4 = 1;
+    cudaError_t e;
+    if (B == 8)
+        e = P == 2 ? launch_fused<8, 4, 2>(a, d, st)
+                   : (P == 4 ? launch_fused<8, 4, 4>(a, d, st) : launch_fused<8, 4, 8>(a, d, st));
+    else
+        e = P == 2 ? launch_fused<4, 8, 2>(a, d, st)
+                   : (P == 4 ? launch_fused<4, 8, 4>(a, d, st) : launch_fused<4, 8, 8>(a, d, st));
+    if (e != cudaSuccess) return e;
+    // phase 2: the gather of zhat into g (y is only a placeholder input here)
+    return launch_adjoint_impl<float>(op, y, g, B, seg, zhat, st, false);
 }
 
 template cudaError_t launch_forward<float>(const rtt_op_s*, const float*, float*, int, const ArmSeg&,

@@ -44,6 +44,7 @@ struct ApplyVariant {
     int8_t time = 0;    // adjoint phase 1: 1 general (adj_time3), 2 periodic (adj_time4),
                         // 3 periodic with TMA-staged frames (adj_time5)
     int8_t space = 0;   // adjoint phase 2: 1 scalar (adj_space3), 2 16-byte (adj_space4)
+    int8_t fused = 0;   // rtt_apply_A_AT: 1 = fused forward + time phase where possible
 };
 constexpr int kMaxTuned = 8;  // batch sizes with an autotuned variant per operator
 
@@ -97,6 +98,8 @@ struct rtt_op_s {
     void* fpartial = nullptr;
     size_t fpartial_bytes = 0;
     bool use_fused_adjoint = false;  // tile-fused adjoint (measured slower than two-phase so far)
+    void* rscratch = nullptr;  // residual y - d of the separate-path rtt_apply_A_AT, grown on demand
+    size_t rscratch_bytes = 0;
     int* dev_status = nullptr;  // device status word: bit 0 = a kernel's bounded wait timed out
     // autotuned kernel variants (rtt_autotune), per batch size
     int n_tuned = 0;

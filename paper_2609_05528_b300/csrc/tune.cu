@@ -19,6 +19,9 @@ cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cu
 template <typename T>
 cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
 rtt_status ensure_zhat_bytes(rtt_op_s* op, size_t bytes);
+cudaError_t launch_forward_adjoint_fused(const rtt_op_s* op, const float* x, const float* d,
+                                         float* y, float* g, int B, const ArmSeg& seg,
+                                         float* zhat, cudaStream_t st);
 }  // namespace rtt
 
 namespace {
@@ -86,6 +89,7 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
     a.fwd_half = (int8_t)v->fwd_half;
     a.time = (int8_t)v->time_kernel;
     a.space = (int8_t)v->space_kernel;
+    a.fused = (int8_t)(v->fused_step != 0);
     set_variant(op, batch, a);
     return RTT_OK;
 }
@@ -101,6 +105,7 @@ extern "C" rtt_status rtt_get_variant(rtt_op op, int batch, rtt_variant* out) {
     out->fwd_half = a.fwd_half;
     out->time_kernel = a.time;
     out->space_kernel = a.space;
+    out->fused_step = a.fused;
     return RTT_OK;
 }
 
@@ -209,6 +214,36 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                 best.space = v.space;
             }
         }
+    // rtt_apply_A_AT: the fused forward + time phase against the chosen
+    // separate pair (needs a second x-sized buffer for the gradient)
+    float fused_ms = 0.f;
+    best.fused = 0;
+    if (e == cudaSuccess) {
+        float* g = nullptr;
+        if (cudaMalloc(&g, nx * 4) == cudaSuccess) {
+            set_variant(op, B, best);
+            cudaError_t f = launch_forward_adjoint_fused(op, x, nullptr, y, g, B, seg,
+                                                         (float*)op->zhat, st);
+            if (f == cudaSuccess) {
+                ++n_cand;
+                cudaEventRecord(tm.a, st);
+                for (int r = 0; r < kTuneReps && f == cudaSuccess; ++r)
+                    f = launch_forward_adjoint_fused(op, x, nullptr, y, g, B, seg,
+                                                     (float*)op->zhat, st);
+                cudaEventRecord(tm.b, st);
+                if (f == cudaSuccess && cudaEventSynchronize(tm.b) == cudaSuccess) {
+                    cudaEventElapsedTime(&fused_ms, tm.a, tm.b);
+                    fused_ms /= kTuneReps;
+                    if (fused_ms < fwd_best + adj_best) best.fused = 1;
+                } else if (f != cudaErrorNotSupported) {
+                    e = f;
+                }
+            } else if (f != cudaErrorNotSupported) {
+                e = f;
+            }
+            cudaFree(g);
+        }
+    }
     cudaFree(x);
     cudaFree(y);
     if (e != cudaSuccess) {
@@ -230,5 +265,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     out->fwd_ms_rule = fwd_rule;
     out->adj_ms_rule = adj_rule;
     out->candidates = n_cand;
+    out->fused_step = best.fused;
+    out->fused_ms = fused_ms;
     return RTT_OK;
 }

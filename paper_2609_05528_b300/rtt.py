@@ -90,13 +90,14 @@ class TuneResult(ctypes.Structure):
                 ("time_kernel", ctypes.c_int32),
                 ("space_kernel", ctypes.c_int32), ("fwd_ms", ctypes.c_float),
                 ("adj_ms", ctypes.c_float), ("fwd_ms_rule", ctypes.c_float),
-                ("adj_ms_rule", ctypes.c_float), ("candidates", ctypes.c_int32)]
+                ("adj_ms_rule", ctypes.c_float), ("candidates", ctypes.c_int32),
+                ("fused_step", ctypes.c_int32), ("fused_ms", ctypes.c_float)]
 
 
 class Variant(ctypes.Structure):
     _fields_ = [("fwd_kernel", ctypes.c_int32), ("fwd_bc", ctypes.c_int32),
                 ("fwd_half", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
-                ("space_kernel", ctypes.c_int32)]
+                ("space_kernel", ctypes.c_int32), ("fused_step", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes)
@@ -116,6 +117,7 @@ _SIGS = {
     "rtt_apply_A": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_apply_AT": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_apply_A_f64": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
+    "rtt_apply_A_AT": (ctypes.c_int, [vp, vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_apply_AT_f64": (ctypes.c_int, [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]),
     "rtt_probe_info": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp, vp]),
     "rtt_probe_info_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp,
@@ -264,12 +266,13 @@ class Operator:
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def set_variant(self, batch: int, fwd_kernel=None, fwd_bc=None, fwd_half=0, time_kernel=None,
-                    space_kernel=None):
+                    space_kernel=None, fused_step=0):
         """rtt_set_variant; all None resets `batch` to the default rule."""
         if fwd_kernel is None and fwd_bc is None and time_kernel is None and space_kernel is None:
             check(lib().rtt_set_variant(self.handle, int(batch), None), "rtt_set_variant")
             return
-        v = Variant(int(fwd_kernel), int(fwd_bc), int(fwd_half), int(time_kernel), int(space_kernel))
+        v = Variant(int(fwd_kernel), int(fwd_bc), int(fwd_half), int(time_kernel), int(space_kernel),
+                    int(fused_step))
         check(lib().rtt_set_variant(self.handle, int(batch), ctypes.byref(v)), "rtt_set_variant")
 
     def get_variant(self, batch: int) -> dict:
@@ -312,6 +315,24 @@ class Operator:
         name = "rtt_apply_A" if x.dtype == torch.float32 else "rtt_apply_A_f64"
         self._launch(name, x, y, B, arm_mask, stream)
         return y
+
+    def apply_A_AT(self, x, d=None, y=None, g=None, arm_mask: int = 7, stream=None):
+        """rtt_apply_A_AT: (y, g) = (scale A x, scale A^T (y - d)), FP32, one call."""
+        import torch
+        assert x.is_cuda and x.is_contiguous() and x.dim() == 3 and x.dtype == torch.float32
+        B = x.shape[2]
+        if y is None:
+            R = self.arm_rows(arm_mask)
+            y = torch.empty((R, self.n_frames, B), dtype=x.dtype, device=x.device)
+        if g is None:
+            g = torch.empty_like(x)
+        if d is not None:
+            assert d.is_contiguous() and d.shape == y.shape and d.dtype == torch.float32
+        dp_ = ctypes.c_void_p(d.data_ptr()) if d is not None else None
+        check(lib().rtt_apply_A_AT(self.handle, ctypes.c_void_p(x.data_ptr()), dp_,
+                                   ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(g.data_ptr()),
+                                   int(B), int(arm_mask), _stream(stream)), "rtt_apply_A_AT")
+        return y, g
 
     def apply_AT(self, y, x=None, arm_mask: int = 7, stream=None):
         """x = scale * A^T y; y: [arm_rows, n_frames, B]."""

@@ -221,6 +221,37 @@ def test_every_variant_same_bits(which, small, schw, B):
     assert n >= 12
 
 
+@pytest.mark.parametrize("which", ["small", "schw"])
+@pytest.mark.parametrize("B", [3, 4, 8])
+@pytest.mark.parametrize("mask", [7, 1])
+@pytest.mark.parametrize("with_d", [False, True])
+def test_apply_A_AT(which, small, schw, B, mask, with_d):
+    """rtt_apply_A_AT (fused for batch 4 and 8) gives the bits of rtt_apply_A
+    followed by rtt_apply_AT on y - d, and matches the oracle."""
+    c = small if which == "small" else schw
+    x = torch.from_numpy(I.uniform_batch(c.w, range(B)).astype(np.float32)).cuda()
+    y_ref = c.op.apply_A(x, arm_mask=mask)
+    d = None
+    r = y_ref
+    if with_d:
+        d = torch.from_numpy(I.noise(tuple(y_ref.shape), 23).astype(np.float32)).cuda()
+        r = (y_ref - d).contiguous()
+    g_ref = c.op.apply_AT(r, arm_mask=mask)
+    bc = 1
+    while bc < B:
+        bc *= 2
+    for fused in (0, 1):  # separate pair, then the fused kernel (where B allows it)
+        c.op.set_variant(B, 1, bc, 0, 2, 2, fused_step=fused)
+        y, g = c.op.apply_A_AT(x, d, arm_mask=mask)
+        assert torch.equal(y, y_ref), fused
+        assert torch.equal(g, g_ref), fused
+    c.op.set_variant(B)
+    sub = c.tab.select(_arm_orders(mask))
+    _cmp(g.cpu().numpy().astype(np.float64),
+         O.apply_AT(c.w, sub, r.cpu().numpy().astype(np.float64), c.scale), TOL32 * 3)
+    assert c.op.status(clear=True) == 0
+
+
 def test_direct_zero_columns_bit_exact(schw):
     """Theorem 4.1: columns the oracle finds exactly zero in the direct block
     are exactly zero on the GPU (FP32 and FP64 paths), and vice versa."""
