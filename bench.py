@@ -441,10 +441,96 @@ def run_audit(device):
     out["sigma_min_range"] = [min(min(r[0].sigma_min_pos, r[1].sigma_min_pos) for r in rn),
                               max(max(r[0].sigma_min_pos, r[1].sigma_min_pos) for r in rn)]
     out["seconds_per_record"] = [round(r[i].seconds, 4) for r in rn for i in range(2)]
+    out["seconds_split"] = {k: round(sum(getattr(r[i], "seconds_" + k) for r in rn for i in range(2)), 3)
+                            for k in ("probe", "gram", "eig")}
     out["ranks_agree_between_paths"] = all(a[i].rank == b[i].rank for a, b in zip(rn, rd)
                                            for i in range(2))
     for op in ops:
         op.close()
+    return out
+
+
+def run_recovery(device, n_test: int = 60, n_val: int = 20, max_iter: int = 400,
+                 tol: float = 1e-6):
+    """Held-out recovery (Sec. 9) on Kerr a=0.94, i=50 deg at kerr256 sizes:
+    60 test and 20 validation histories (1-4 flaring hot spots plus a
+    log-normal level), data = scale A x_true + N(0, 1) whitened noise, the
+    direct-only arm using the n=0 rows of the same draw.  Ridge by batched CG
+    on A^T A + lambda I for 8 lambdas (validation-selected), and TSVD in S224
+    at the operational rank.  Error = ||x_hat - x_true|| / ||x_true|| on the
+    grid x hat coefficients."""
+    import torch
+
+    from paper_2609_05528_b300 import inputs as I
+    from paper_2609_05528_b300 import rtt
+    lambdas = 10.0 ** np.arange(-3, 5)
+    L = len(lambdas)
+    w = I.recovery()
+    tab = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, I.screen_samples(w))
+    op = rtt.Operator(w, tab)
+    R0 = int(op.info.rows_per_order[0])
+    sets = {}
+    for name, seeds, nseed in (("test", range(1000, 1000 + n_test), 11),
+                               ("val", range(2000, 2000 + n_val), 12)):
+        xt = torch.from_numpy(I.recovery_batch(w, seeds).astype(np.float32)).to(device)
+        d = op.apply_A(xt)
+        d += torch.from_numpy(I.noise(tuple(d.shape), nseed).astype(np.float32)).to(device)
+        sets[name] = (xt, d)
+
+    def errors(xh, xt, per):
+        n = xt.shape[2]
+        xh = xh.reshape(xt.shape[0], xt.shape[1], n, per).double()
+        diff = xh - xt.double()[..., None]
+        return (diff.pow(2).sum((0, 1)).sqrt() / xt.double().pow(2).sum((0, 1)).sqrt()[:, None]).cpu().numpy()
+
+    out = {"workload": "recovery: Kerr a=0.94 i=50deg, kerr256 sizes, 60 test + 20 validation "
+                       "histories, SNR0=100 whitened noise, lambdas 1e-3..1e4",
+           "arms": {}}
+    Q = rtt.synth_class(op, rtt.CLASS_S224)
+    err = {}
+    for arm in (1, 7):
+        rec = {}
+        for name in ("val", "test"):
+            xt, d = sets[name]
+            data = (d[:R0] if arm == 1 else d).contiguous()
+            torch.cuda.synchronize(device)
+            t = time.perf_counter()
+            xh, it, rel = rtt.solve_ridge(op, data, lambdas, arm, max_iter=max_iter, tol=tol,
+                                          refresh_every=25, raise_on_stall=False)
+            torch.cuda.synchronize(device)
+            rec[name] = {"seconds": time.perf_counter() - t, "iterations": it,
+                         "max_relres": float(np.max(rel)), "columns": int(xh.shape[2]),
+                         "err": errors(xh, xt, L)}
+            del xh
+        li = int(np.argmin(np.median(rec["val"]["err"], axis=0)))
+        # TSVD in S224 at the operational rank of this arm
+        t = time.perf_counter()
+        G = rtt.gram(op, Q, arm, rtt.GRAM_NORMAL)
+        ev, V, _ = rtt.eig_sym(G)
+        sig = np.sqrt(np.maximum(ev, 0.0))
+        rank = int(np.count_nonzero(sig >= 1.0))  # rho = 1 (Eq. 31)
+        xt, d = sets["test"]
+        data64 = (d[:R0] if arm == 1 else d).double().contiguous()
+        xts = rtt.solve_tsvd(op, Q, V, ev, rank, data64, arm)
+        torch.cuda.synchronize(device)
+        t_tsvd = time.perf_counter() - t
+        e_tsvd = errors(xts, xt, 1)[:, 0]
+        err[arm] = rec["test"]["err"][:, li]
+        out["arms"]["direct" if arm == 1 else "resolved"] = {
+            "lambda": float(lambdas[li]),
+            "ridge_median_err": float(np.median(err[arm])),
+            "ridge_median_err_per_lambda": [round(float(v), 4) for v in np.median(rec["test"]["err"], axis=0)],
+            "ridge_seconds_test": round(rec["test"]["seconds"], 3),
+            "ridge_seconds_val": round(rec["val"]["seconds"], 3),
+            "ridge_iterations": rec["test"]["iterations"],
+            "ridge_max_fp64_relres": rec["test"]["max_relres"],
+            "ridge_columns": rec["test"]["columns"],
+            "tsvd_rank": rank, "tsvd_median_err": float(np.median(e_tsvd)),
+            "tsvd_seconds": round(t_tsvd, 3)}
+    red = 1.0 - err[7] / err[1]
+    out["median_paired_reduction"] = float(np.median(red))
+    out["histories_improved"] = int(np.count_nonzero(red > 0))
+    op.close()
     return out
 
 
@@ -480,6 +566,8 @@ def main():
     ap.add_argument("--no-audit", action="store_true")
     ap.add_argument("--sweep", action="store_true",
                     help="print the stress1024 batch sweep (one JSON line per geometry) and exit")
+    ap.add_argument("--recovery", action="store_true",
+                    help="print the held-out recovery leg (ridge + TSVD) as one JSON line and exit")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -521,6 +609,11 @@ def main():
             torch.cuda.set_device(device)
             for line in run_sweep(device):
                 print(json.dumps(line))
+        return
+    if args.recovery:
+        if rank == 0:
+            torch.cuda.set_device(device)
+            print(json.dumps(run_recovery(device)))
         return
     out = run_ours(args, rank, world, device)
     if rank == 0 and world == 1 and not args.no_audit:

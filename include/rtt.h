@@ -415,6 +415,9 @@ typedef struct {
     int32_t jacobi_sweeps;
     rtt_reach_result reach; /* anchor, L_anchor, T_reach, A_0,q, J_old */
     double seconds;        /* wall time of this record */
+    double seconds_probe;  /* of which: age probes and reach */
+    double seconds_gram;   /* of which: restricted Gram */
+    double seconds_eig;    /* of which: share of the batched eigensolve */
 } rtt_audit_record;
 
 #define RTT_GRAM_DATA 0   /* G = P^T P over data samples (rtt_gram) */

@@ -76,11 +76,19 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
                           nullptr);
             if (s != RTT_OK) break;
             r.reach = rr;
+            const auto t1 = std::chrono::steady_clock::now();
             double* Gi = G + ((size_t)g * n_arms + ai) * d * d;
             s = gram_mode == RTT_GRAM_NORMAL ? rtt_gram_normal(op, arm_masks[ai], Q_dev[g], d, Gi, stream)
                                              : rtt_gram(op, arm_masks[ai], Q_dev[g], d, Gi, stream);
+            if (s == RTT_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+                set_error("rank audit: Gram failed: %s", cudaGetErrorString(cudaGetLastError()));
+                s = RTT_ECUDA;
+            }
             r.s_ref = op->s_ref;
-            r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+            const auto t2 = std::chrono::steady_clock::now();
+            r.seconds_probe = std::chrono::duration<double>(t1 - t0).count();
+            r.seconds_gram = std::chrono::duration<double>(t2 - t1).count();
+            r.seconds = std::chrono::duration<double>(t2 - t0).count();
         }
     }
     // all spectra in one batched Jacobi launch (one CTA per matrix)
@@ -110,6 +118,7 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
             r.sigma_min_pos = smin_pos;
             r.jacobi_sweeps = sweeps[b];
             r.seconds += te / nb;
+            r.seconds_eig = te / nb;
             if (sigma_out)
                 for (int i = 0; i < d; ++i) sigma_out[(size_t)b * d + i] = sig[i];
         }

@@ -272,6 +272,18 @@ def history_batch(w: Workload, seeds, **kw) -> np.ndarray:
     return np.stack(xs, axis=-1)
 
 
+def recovery_history(w: Workload, seed: int) -> np.ndarray:
+    """Held-out recovery history: 1-4 hot spots (count drawn from the seed)
+    with flare envelopes and a log-normal baseline level, float64 [S, K]."""
+    n_spots = 1 + min(3, int(4.0 * uniforms(seed ^ 0xA5A5A5A5, 1)[0]))
+    return hotspot_history(w, seed, n_spots=n_spots, flare=True, level=True)
+
+
+def recovery_batch(w: Workload, seeds) -> np.ndarray:
+    """Stack of recovery histories, layout x[s][k][b] (float64)."""
+    return np.stack([recovery_history(w, int(s)) for s in seeds], axis=-1)
+
+
 def uniform_batch(w: Workload, seeds) -> np.ndarray:
     """x ~ U(0, 1) per coefficient, layout x[s][k][b] (throughput inputs)."""
     n = w.grid.n_nodes * w.time.n_hats

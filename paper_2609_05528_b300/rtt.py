@@ -76,7 +76,9 @@ class AuditRecord(ctypes.Structure):
     _fields_ = [("arm_mask", ctypes.c_int32), ("rank", ctypes.c_int32), ("margin", ctypes.c_double),
                 ("sigma_max", ctypes.c_double), ("sigma_min_pos", ctypes.c_double),
                 ("s_ref", ctypes.c_double), ("jacobi_sweeps", ctypes.c_int32),
-                ("reach", ReachResult), ("seconds", ctypes.c_double)]
+                ("reach", ReachResult), ("seconds", ctypes.c_double),
+                ("seconds_probe", ctypes.c_double), ("seconds_gram", ctypes.c_double),
+                ("seconds_eig", ctypes.c_double)]
 
 
 class Screen(ctypes.Structure):
