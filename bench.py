@@ -174,9 +174,7 @@ def run_ours(args, rank, world, device):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize(device)
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    ranks_barrier(world)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(device.index if device.index is not None else 0) as clk:
@@ -192,14 +190,10 @@ def run_ours(args, rank, world, device):
             e2.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(device)
+        ranks_barrier(world)
     t_A = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
     t_AT = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
-    ms_step = float(np.mean([a + b for a, b in zip(t_A, t_AT)]))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_step], dtype=torch.float64, device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(float(np.mean([a + b for a, b in zip(t_A, t_AT)])), world, device)
     clocks = clk.summary()
 
     # the same pair through rtt_apply_A_AT (fused forward + temporal adjoint
@@ -219,8 +213,8 @@ def run_ours(args, rank, world, device):
             a1.record(stream)
             a1.synchronize()
             f_ms.append(a0.elapsed_time(a1))
-        fused = {"ms_per_step": float(np.mean(f_ms)),
-                 "value": world * BATCH / (float(np.mean(f_ms)) * 1e-3)}
+        fm = max_over_ranks(float(np.mean(f_ms)), world, device)
+        fused = {"ms_per_step": fm, "value": job_value(world, BATCH, fm)}
     except Exception as exc:
         fused = {"error": str(exc)[:200]}
 
@@ -249,8 +243,8 @@ def run_ours(args, rank, world, device):
             a1.record(stream)
             a1.synchronize()
             g_ms.append(a0.elapsed_time(a1))
-        graph = {"ms_per_step": float(np.mean(g_ms)),
-                 "value": world * BATCH / (float(np.mean(g_ms)) * 1e-3)}
+        gm = max_over_ranks(float(np.mean(g_ms)), world, device)
+        graph = {"ms_per_step": gm, "value": job_value(world, BATCH, gm)}
     except Exception as exc:  # capture is a measurement extra; report why it failed
         graph = {"error": str(exc)[:200]}
 
@@ -278,7 +272,7 @@ def run_ours(args, rank, world, device):
         a1.record(stream)
         a1.synchronize()
         e_ms.append(a0.elapsed_time(a1))
-    e2e_ms = float(np.mean(e_ms))
+    e2e_ms = max_over_ranks(float(np.mean(e_ms)), world, device)
 
     # plain FP64 GPU path (same kernels in double) for comparison
     x64 = x.double()
@@ -298,14 +292,14 @@ def run_ours(args, rank, world, device):
         a1.record(stream)
         a1.synchronize()
         f_ms.append(a0.elapsed_time(a1))
-    fp64_ms = float(np.mean(f_ms))
+    fp64_ms = max_over_ranks(float(np.mean(f_ms)), world, device)
 
     ab = algorithmic_bytes(op, BATCH)
     mA, mAT = float(np.mean(t_A)), float(np.mean(t_AT))
     dom, dom_ms = ("A", mA) if mA >= mAT else ("AT", mAT)
     peak, peak_kind = measured_peaks()
     achieved = ab[dom] / (dom_ms * 1e-3) / 1e9
-    value = world * BATCH / (ms_step * 1e-3)
+    value = job_value(world, BATCH, ms_step)
     gbs = (ab["A"] + ab["AT"]) / (ms_step * 1e-3) / 1e9
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -324,15 +318,39 @@ def run_ours(args, rank, world, device):
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": recorded_traffic(dom), "algorithmic_bytes": ab[dom],
                      "source_hash": kernel_source_hash()},
-        "e2e": {"value": world * BATCH / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+        "e2e": {"value": job_value(world, BATCH, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4)},
-        "fp64_path": {"value": world * BATCH / (fp64_ms * 1e-3), "ms_per_step": fp64_ms},
+        "fp64_path": {"value": job_value(world, BATCH, fp64_ms), "ms_per_step": fp64_ms},
         "cuda_graph": graph,
         "fused_A_AT": fused,
         "clocks": clocks,
         "gpu_launches": launches_per_step(BATCH) * args.steps,
     }
     return out
+
+
+def ranks_barrier(world: int):
+    """Barrier across the replicas (no-op on one process)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The job's time for a timed region: the slowest replica's."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, batch: int, ms: float) -> float:
+    """Whole-job throughput: every replica applies A + A^T to its own batch
+    (weak scaling), so the job moves world * batch histories per step."""
+    return world * batch / (ms * 1e-3)
 
 
 def launches_per_step(B: int) -> int:

@@ -284,11 +284,13 @@ __device__ __forceinline__ double exact_frac<double>(const ApplyArgs<double>& a,
 template <typename T>
 __device__ __forceinline__ void corner_w(const ApplyArgs<T>& a, int e, T w[4]) { load_w(a, e, w); }
 
-// FPL frames per lane (32 FPL per task); fewer accumulators per lane
-// (BC FPL <= 16) allow three resident CTAs per SM.
-template <typename T, int BC, int FPL>
+// FPL frames per lane (32 FPL per task); SU staging items in flight per lane
+// and pass.  Fewer accumulators per lane (BC FPL <= 16) or one item in
+// flight (SU = 1) allow three resident CTAs per SM.
+template <typename T, int BC, int FPL, int SU = 2>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32,
-                                  (sizeof(T) == 8 || BC >= 32) ? 1 : (BC * FPL <= 16 ? 3 : 2))
+                                  (sizeof(T) == 8 || BC >= 32) ? 1
+                                                               : ((BC * FPL <= 16 || SU == 1) ? 3 : 2))
 fwd3_kernel(const ApplyArgs<T> a) {
     using V = typename Vec16<T>::type;
     constexpr int VW = Vec16<T>::W;
@@ -333,11 +335,11 @@ fwd3_kernel(const ApplyArgs<T> a) {
                 constexpr int Q = BC / VW > 0 ? BC / VW : 1;
                 V* zsv = reinterpret_cast<V*>(zs);
                 const int n_items = nwin * Q;
-                for (int base = 0; base < n_items; base += 64) {
-                    V v[2][4];
-                    bool okv[2];
+                for (int base = 0; base < n_items; base += 32 * SU) {
+                    V v[SU][4];
+                    bool okv[SU];
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
+                    for (int u = 0; u < SU; ++u) {
                         const int o = base + lane + 32 * u;
                         const int kk = o / Q, q = o - kk * Q;
                         const int k = k_lo + kk;
@@ -351,7 +353,7 @@ fwd3_kernel(const ApplyArgs<T> a) {
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < 2; ++u) {
+                    for (int u = 0; u < SU; ++u) {
                         const int o = base + lane + 32 * u;
                         if (o < n_items) {
                             V z;
@@ -1625,7 +1627,7 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     return a;
 }
 
-template <typename T, int BC, int FPL>
+template <typename T, int BC, int FPL, int SU = 2>
 static cudaError_t launch_fwd3_bc(ApplyArgs<T> a, cudaStream_t st) {
     a.FC = 32 * FPL;
     a.vec4 = vec_ok(a);
@@ -1636,11 +1638,11 @@ static cudaError_t launch_fwd3_bc(ApplyArgs<T> a, cudaStream_t st) {
     if (a.n_tasks == 0) return cudaSuccess;
     const size_t smem = (size_t)kWarpsPerBlock * a.zwin * BC * sizeof(T);
     if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(fwd3_kernel<T, BC, FPL>,
+        cudaError_t err = cudaFuncSetAttribute(fwd3_kernel<T, BC, FPL, SU>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
     }
-    fwd3_kernel<T, BC, FPL><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
+    fwd3_kernel<T, BC, FPL, SU><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1769,23 +1771,28 @@ ApplyVariant variant_for(const rtt_op_s* op, int batch) {
 // staged forward with BC batch entries and (half = false) 32 / BC frames per
 // lane, or (half = true, FP32 only) half as many
 template <typename T, int BC>
-static cudaError_t launch_fwd3_fpl(const ApplyArgs<T>& a, bool half, cudaStream_t st) {
+static cudaError_t launch_fwd3_fpl(const ApplyArgs<T>& a, bool half, int su, cudaStream_t st) {
     constexpr int F = BC >= 32 ? 1 : 32 / BC;
     if constexpr (sizeof(T) == 4 && F >= 2) {
         if (half) return launch_fwd3_bc<T, BC, F / 2>(a, st);
+    }
+    if constexpr (sizeof(T) == 4 && (BC == 4 || BC == 8)) {
+        if (su == 1) return launch_fwd3_bc<T, BC, F, 1>(a, st);
+        if (su == 3) return launch_fwd3_bc<T, BC, F, 3>(a, st);
     }
     return launch_fwd3_bc<T, BC, F>(a, st);
 }
 
 template <typename T>
-static cudaError_t launch_fwd3_any(const ApplyArgs<T>& a, int bc, bool half, cudaStream_t st) {
+static cudaError_t launch_fwd3_any(const ApplyArgs<T>& a, int bc, bool half, int su,
+                                   cudaStream_t st) {
     switch (bc) {
-        case 1: return launch_fwd3_fpl<T, 1>(a, half, st);
-        case 2: return launch_fwd3_fpl<T, 2>(a, half, st);
-        case 4: return launch_fwd3_fpl<T, 4>(a, half, st);
-        case 8: return launch_fwd3_fpl<T, 8>(a, half, st);
-        case 16: return launch_fwd3_fpl<T, 16>(a, half, st);
-        default: return launch_fwd3_fpl<T, 32>(a, half, st);
+        case 1: return launch_fwd3_fpl<T, 1>(a, half, su, st);
+        case 2: return launch_fwd3_fpl<T, 2>(a, half, su, st);
+        case 4: return launch_fwd3_fpl<T, 4>(a, half, su, st);
+        case 8: return launch_fwd3_fpl<T, 8>(a, half, su, st);
+        case 16: return launch_fwd3_fpl<T, 16>(a, half, su, st);
+        default: return launch_fwd3_fpl<T, 32>(a, half, su, st);
     }
 }
 
@@ -1825,9 +1832,9 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
             if (e != cudaErrorNotSupported) return e;
             cudaGetLastError();  // clear the "not supported" marker, if any
         }
-        return launch_fwd3_any<T>(a, bc, v.fwd_half != 0, st);
+        return launch_fwd3_any<T>(a, bc, v.fwd_half != 0, v.fwd_su, st);
     } else {
-        return launch_fwd3_any<T>(a, pick_bc(B), false, st);
+        return launch_fwd3_any<T>(a, pick_bc(B), false, 2, st);
     }
 }
 

@@ -41,6 +41,7 @@ struct ApplyVariant {
     int8_t fwd = 0;     // forward: 1 staged z (fwd3), 2 lane-per-hat shuffles (fwd4)
     int8_t fwd_bc = 0;  // batch entries per forward task (power of two)
     int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
+    int8_t fwd_su = 2;   // staged forward: staging items in flight per lane (1, 2 or 3)
     int8_t time = 0;    // adjoint phase 1: 1 general (adj_time3), 2 periodic (adj_time4),
                         // 3 periodic with TMA-staged frames (adj_time5)
     int8_t space = 0;   // adjoint phase 2: 1 scalar (adj_space3), 2 16-byte (adj_space4)

@@ -186,12 +186,18 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                 v.fwd_half = (int8_t)half;
                 if (kind == 2 && (!periodic || bc > 8)) continue;  // lane-per-hat: <= 8 per task
                 if (kind == 3 && (!x_vec || bc < 4)) continue;    // TMA: 16-byte records
-                const float ms = time_it(v, false);
-                if (ms < fwd_best) {
-                    fwd_best = ms;
-                    best.fwd = v.fwd;
-                    best.fwd_bc = v.fwd_bc;
-                    best.fwd_half = v.fwd_half;
+                for (int su = 1; su <= 3; ++su) {
+                    // staging depth: only the staged kernel at 4 or 8 entries, full frames
+                    if (su != 2 && (kind != 1 || half || (bc != 4 && bc != 8))) continue;
+                    v.fwd_su = (int8_t)su;
+                    const float ms = time_it(v, false);
+                    if (ms < fwd_best) {
+                        fwd_best = ms;
+                        best.fwd = v.fwd;
+                        best.fwd_bc = v.fwd_bc;
+                        best.fwd_half = v.fwd_half;
+                        best.fwd_su = v.fwd_su;
+                    }
                 }
             }
     // adjoint: phase-1 x phase-2 variants (timed as the full adjoint)
