@@ -417,8 +417,9 @@ def run_sweep(device, batches=(1, 2, 4, 8, 16, 32, 64), reps: int = 5):
 def run_audit(device):
     """The 12-geometry rank audit (Sec. 6.2-6.3): spins {0, .5, .75, .94} x
     inclinations {20, 50, 75} deg at kerr256 sizes, S224 class, direct and
-    resolved arms.  Times the audit with the FP64 Gram through the normal
-    operator against the plain FP64 path (Gram over data samples)."""
+    resolved arms.  Times the audit with the FP64 class Gram (separable S224,
+    no P) against the normal-operator Gram and the plain FP64 path (Gram over
+    data samples)."""
     import torch
 
     from paper_2609_05528_b300 import inputs as I
@@ -436,17 +437,24 @@ def run_audit(device):
                        "S224 class, arms direct/resolved, SNR0=100, rho=1",
            "trace_and_build_s": t_build}
     runs = {}
-    for name, mode in (("normal", rtt.GRAM_NORMAL), ("data", rtt.GRAM_DATA)):
+    for name, mode in (("class", rtt.GRAM_CLASS_S224), ("normal", rtt.GRAM_NORMAL),
+                       ("data", rtt.GRAM_DATA)):
         torch.cuda.synchronize(device)
         t = time.perf_counter()
         recs, sig = rtt.rank_audit(ops, Qs, (1, 7), mode=mode)
         torch.cuda.synchronize(device)
         runs[name] = (time.perf_counter() - t, recs)
-    tn, rn = runs["normal"]
+    tn, rn = runs["class"]
     td, rd = runs["data"]
     out["seconds"] = tn
+    out["normal_operator_gram_seconds"] = runs["normal"][0]
     out["fp64_data_path_seconds"] = td
     out["speedup_vs_fp64_data_path"] = td / tn
+    out["max_rel_sigma_diff_class_vs_data"] = max(
+        float(np.max(np.abs(np.array([a[i].sigma_max for i in range(2)]) -
+                            np.array([b[i].sigma_max for i in range(2)])) /
+                     np.array([b[i].sigma_max for i in range(2)])))
+        for a, b in zip(rn, rd))
     out["rank_direct"] = [r[0].rank for r in rn]
     out["rank_resolved"] = [r[1].rank for r in rn]
     out["L_anchor_direct"] = [r[0].reach.L_anchor for r in rn]
@@ -461,7 +469,8 @@ def run_audit(device):
     out["seconds_per_record"] = [round(r[i].seconds, 4) for r in rn for i in range(2)]
     out["seconds_split"] = {k: round(sum(getattr(r[i], "seconds_" + k) for r in rn for i in range(2)), 3)
                             for k in ("probe", "gram", "eig")}
-    out["ranks_agree_between_paths"] = all(a[i].rank == b[i].rank for a, b in zip(rn, rd)
+    out["ranks_agree_between_paths"] = all(a[i].rank == b[i].rank and a[i].rank == c[i].rank
+                                           for a, b, c in zip(rn, rd, runs["normal"][1])
                                            for i in range(2))
     for op in ops:
         op.close()

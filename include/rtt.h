@@ -348,6 +348,20 @@ rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q_dev, int d, double*
  * data samples.  Same arguments and result as rtt_gram up to rounding;
  * library scratch <= 32 columns of data and coefficients.  Synchronous.
  */
+/*
+ * rtt_gram_class -- the same restricted Gram G = P^T P (Eq. 7, FP64, 224 x
+ * 224 into G_dev) for the separable class `kind` (RTT_CLASS_S224 or
+ * RTT_CLASS_L224, the columns of rtt_synth_class) without forming P or Q:
+ * with s_e the class's spatial functions interpolated at ray e (times its
+ * weight) and C_row the frame sums of products of the temporal functions
+ * interpolated at each ray's hat coordinates, G = sum over rows and ray pairs
+ * of (s_e s_e'^T) kron C_row.  About 7x fewer FP64 operations than
+ * rtt_gram_normal.  Rows with more than 4 rays are not handled
+ * (RTT_ESTATE; use rtt_gram_normal).  Allocates scratch; synchronous.
+ * Errors: RTT_EINVAL, RTT_ESTATE, RTT_ENOMEM, RTT_ECUDA.
+ */
+rtt_status rtt_gram_class(rtt_op op, int arm_mask, int kind, double* G_dev, void* stream);
+
 rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q_dev, int d, double* G_dev,
                            void* stream);
 
@@ -422,6 +436,8 @@ typedef struct {
 
 #define RTT_GRAM_DATA 0   /* G = P^T P over data samples (rtt_gram) */
 #define RTT_GRAM_NORMAL 1 /* G = Q^T A^T A Q (rtt_gram_normal) */
+#define RTT_GRAM_CLASS_S224 2 /* rtt_gram_class for the S224 class (Q_dev may be NULL) */
+#define RTT_GRAM_CLASS_L224 3 /* rtt_gram_class for the L224 class (Q_dev may be NULL) */
 
 /*
  * rtt_rank_audit -- the audit of Sec. 6.2-6.3 for n_ops geometries: for each
@@ -431,7 +447,10 @@ typedef struct {
  * anchor-connected reach, the direct age boundary A_{0,quantile} (shared by
  * the arms of a geometry) and J_old (Eq. 35), then G = P^T P, P = scale A Q
  * (FP64; gram_mode RTT_GRAM_DATA uses rtt_gram, RTT_GRAM_NORMAL uses
- * rtt_gram_normal), its Jacobi spectrum and the operational rank.
+ * rtt_gram_normal, RTT_GRAM_CLASS_S224 / _L224 use rtt_gram_class for that
+ * class and d must be 224; where rtt_gram_class returns RTT_ESTATE the
+ * normal-operator Gram of Q_dev[g] is taken instead, which then must not be
+ * NULL), its Jacobi spectrum and the operational rank.
  * out: host array [n_ops][n_arms]; sigma_out (optional): host
  * [n_ops][n_arms][d], singular values descending.  Synchronous.
  */
@@ -467,6 +486,7 @@ typedef struct {
     int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat, 3 staged with TMA corner copies */
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
+    int32_t fwd_staging;  /* staged forward: x items in flight per lane */
     int32_t time_kernel;  /* adjoint phase 1: 1 general, 2 periodic weights, 3 periodic + TMA */
     int32_t space_kernel; /* adjoint phase 2: 1 scalar, 2 16-byte loads */
     float fwd_ms, adj_ms;           /* chosen variants, ms per apply */
@@ -491,6 +511,8 @@ typedef struct {
     int32_t space_kernel; /* 1 scalar, 2 16-byte loads (where the buffers allow) */
     int32_t fused_step;   /* rtt_apply_A_AT: 1 = fused forward + temporal adjoint where the
                              batch, cadence and buffers allow it, 0 = separate pair */
+    int32_t fwd_staging;  /* staged forward: x items in flight per lane, 1, 2 or 3
+                             (0 = 2; other values than 2 only at 4 or 8 entries) */
 } rtt_variant;
 
 /*

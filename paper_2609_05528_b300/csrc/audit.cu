@@ -26,6 +26,8 @@ extern "C" rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const doubl
                                 const double* info, double h, double a0q, double age_step,
                                 rtt_reach_result* out, uint8_t* pass);
 
+extern "C" rtt_status rtt_gram_class(rtt_op op, int arm_mask, int kind, double* G, void* stream);
+
 extern "C" rtt_status rtt_eig_sym_batched(int n, int batch, double* A, double* evals_host,
                                           double* V, int max_sweeps, int* sweeps_host,
                                           void* stream);
@@ -36,7 +38,8 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
                                      int gram_mode, rtt_audit_record* out, double* sigma_out,
                                      void* stream) {
     if (!ops || n_ops < 1 || !Q_dev || d < 1 || d > 4096 || !arm_masks || n_arms < 1 ||
-        (gram_mode != RTT_GRAM_DATA && gram_mode != RTT_GRAM_NORMAL) ||
+        gram_mode < RTT_GRAM_DATA || gram_mode > RTT_GRAM_CLASS_L224 ||
+        (gram_mode >= RTT_GRAM_CLASS_S224 && d != 224) ||
         n_ages < 1 || n_ages > 256 || !ages_host || !(h > 0.0) || !(quantile > 0.0) || !out) {
         set_error("invalid rank-audit arguments");
         return RTT_EINVAL;
@@ -58,7 +61,7 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
     // probes, reach and restricted Grams of every (geometry, arm)
     for (int g = 0; g < n_ops && s == RTT_OK; ++g) {
         rtt_op op = ops[g];
-        if (!op || !Q_dev[g]) {
+        if (!op || (!Q_dev[g] && gram_mode < RTT_GRAM_CLASS_S224)) {
             set_error("rank audit: operator or class %d missing", g);
             s = RTT_EINVAL;
             break;
@@ -78,8 +81,20 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
             r.reach = rr;
             const auto t1 = std::chrono::steady_clock::now();
             double* Gi = G + ((size_t)g * n_arms + ai) * d * d;
-            s = gram_mode == RTT_GRAM_NORMAL ? rtt_gram_normal(op, arm_masks[ai], Q_dev[g], d, Gi, stream)
-                                             : rtt_gram(op, arm_masks[ai], Q_dev[g], d, Gi, stream);
+            if (gram_mode >= RTT_GRAM_CLASS_S224) {
+                s = rtt_gram_class(op, arm_masks[ai],
+                                   gram_mode == RTT_GRAM_CLASS_S224 ? RTT_CLASS_S224 : RTT_CLASS_L224,
+                                   Gi, stream);
+                if (s == RTT_ESTATE) {  // rows the class path does not handle
+                    s = Q_dev[g] ? rtt_gram_normal(op, arm_masks[ai], Q_dev[g], d, Gi, stream)
+                                 : RTT_EINVAL;
+                    if (s == RTT_EINVAL) set_error("rank audit: class Gram unavailable and no Q");
+                }
+            } else {
+                s = gram_mode == RTT_GRAM_NORMAL
+                        ? rtt_gram_normal(op, arm_masks[ai], Q_dev[g], d, Gi, stream)
+                        : rtt_gram(op, arm_masks[ai], Q_dev[g], d, Gi, stream);
+            }
             if (s == RTT_OK && cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
                 set_error("rank audit: Gram failed: %s", cudaGetErrorString(cudaGetLastError()));
                 s = RTT_ECUDA;

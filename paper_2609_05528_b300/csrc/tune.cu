@@ -90,6 +90,11 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
     a.time = (int8_t)v->time_kernel;
     a.space = (int8_t)v->space_kernel;
     a.fused = (int8_t)(v->fused_step != 0);
+    if (v->fwd_staging < 0 || v->fwd_staging > 3) {
+        set_error("invalid forward staging depth %d", v->fwd_staging);
+        return RTT_EINVAL;
+    }
+    a.fwd_su = (int8_t)(v->fwd_staging == 0 ? 2 : v->fwd_staging);
     set_variant(op, batch, a);
     return RTT_OK;
 }
@@ -106,6 +111,7 @@ extern "C" rtt_status rtt_get_variant(rtt_op op, int batch, rtt_variant* out) {
     out->time_kernel = a.time;
     out->space_kernel = a.space;
     out->fused_step = a.fused;
+    out->fwd_staging = a.fwd_su;
     return RTT_OK;
 }
 
@@ -261,6 +267,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     out->batch = B;
     out->fwd_kernel = best.fwd;
     out->fwd_bc = best.fwd_bc;
+    out->fwd_staging = best.fwd_su;
     out->fwd_frames_per_lane =
         best.fwd == 2 ? (int32_t)(kFracOne / op->frame_D)
                       : (best.fwd_bc >= 32 ? 1 : (32 / best.fwd_bc) / (best.fwd_half ? 2 : 1));

@@ -89,6 +89,7 @@ class Screen(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int32), ("fwd_kernel", ctypes.c_int32),
                 ("fwd_bc", ctypes.c_int32), ("fwd_frames_per_lane", ctypes.c_int32),
+                ("fwd_staging", ctypes.c_int32),
                 ("time_kernel", ctypes.c_int32),
                 ("space_kernel", ctypes.c_int32), ("fwd_ms", ctypes.c_float),
                 ("adj_ms", ctypes.c_float), ("fwd_ms_rule", ctypes.c_float),
@@ -99,7 +100,8 @@ class TuneResult(ctypes.Structure):
 class Variant(ctypes.Structure):
     _fields_ = [("fwd_kernel", ctypes.c_int32), ("fwd_bc", ctypes.c_int32),
                 ("fwd_half", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
-                ("space_kernel", ctypes.c_int32), ("fused_step", ctypes.c_int32)]
+                ("space_kernel", ctypes.c_int32), ("fused_step", ctypes.c_int32),
+                ("fwd_staging", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes)
@@ -139,6 +141,7 @@ _SIGS = {
     "rtt_solve_tsvd": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, dp, ctypes.c_int, vp,
                                       ctypes.c_int, vp, vp]),
     "rtt_gram_normal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
+    "rtt_gram_class": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
     "rtt_synth_class": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
     "rtt_rank_audit": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
@@ -268,13 +271,13 @@ class Operator:
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def set_variant(self, batch: int, fwd_kernel=None, fwd_bc=None, fwd_half=0, time_kernel=None,
-                    space_kernel=None, fused_step=0):
+                    space_kernel=None, fused_step=0, fwd_staging=0):
         """rtt_set_variant; all None resets `batch` to the default rule."""
         if fwd_kernel is None and fwd_bc is None and time_kernel is None and space_kernel is None:
             check(lib().rtt_set_variant(self.handle, int(batch), None), "rtt_set_variant")
             return
         v = Variant(int(fwd_kernel), int(fwd_bc), int(fwd_half), int(time_kernel), int(space_kernel),
-                    int(fused_step))
+                    int(fused_step), int(fwd_staging))
         check(lib().rtt_set_variant(self.handle, int(batch), ctypes.byref(v)), "rtt_set_variant")
 
     def get_variant(self, batch: int) -> dict:
@@ -380,6 +383,8 @@ def reach(op: "Operator", info, arm_mask: int = 7, ages=AGES, h: float = 3.0, a0
 
 GRAM_DATA = 0
 GRAM_NORMAL = 1
+GRAM_CLASS_S224 = 2
+GRAM_CLASS_L224 = 3
 CLASS_S224 = 0
 CLASS_L224 = 1
 
@@ -403,6 +408,15 @@ def gram(op: "Operator", Q, arm_mask: int = 7, mode: int = GRAM_DATA, stream=Non
     name = "rtt_gram" if mode == GRAM_DATA else "rtt_gram_normal"
     check(getattr(lib(), name)(op.handle, arm_mask, ctypes.c_void_p(Q.data_ptr()), d,
                                ctypes.c_void_p(G.data_ptr()), _stream(stream)), name)
+    return G
+
+
+def gram_class(op: "Operator", kind: int = CLASS_S224, arm_mask: int = 7, stream=None):
+    """rtt_gram_class: the restricted Gram of a separable class (224 x 224 FP64)."""
+    import torch
+    G = torch.empty((224, 224), dtype=torch.float64, device="cuda")
+    check(lib().rtt_gram_class(op.handle, arm_mask, int(kind), ctypes.c_void_p(G.data_ptr()),
+                               _stream(stream)), "rtt_gram_class")
     return G
 
 
@@ -471,12 +485,15 @@ def solve_tsvd(op: "Operator", Q, V, evals, rank: int, data, arm_mask: int = 7, 
 
 def rank_audit(ops, Qs, arm_masks=(1, 7), ages=AGES, h: float = 3.0, quantile: float = 0.999,
                mode: int = GRAM_NORMAL, stream=None):
-    """rtt_rank_audit over several operators; Qs: CUDA float64 [n_nodes, n_hats, d] each.
+    """rtt_rank_audit over several operators; Qs: CUDA float64 [n_nodes, n_hats, d] each
+    (entries may be None in the GRAM_CLASS_* modes, d = 224 there).
     Returns (records [n_ops][n_arms], sigma [n_ops, n_arms, d])."""
     n = len(ops)
-    d = Qs[0].shape[2]
+    if Qs is None:
+        Qs = [None] * n
+    d = next((q.shape[2] for q in Qs if q is not None), 224)
     arr_ops = (vp * n)(*[o.handle for o in ops])
-    arr_q = (vp * n)(*[ctypes.c_void_p(q.data_ptr()) for q in Qs])
+    arr_q = (vp * n)(*[ctypes.c_void_p(q.data_ptr() if q is not None else None) for q in Qs])
     arms = (ctypes.c_int * len(arm_masks))(*arm_masks)
     ages = np.ascontiguousarray(ages, np.float64)
     recs = (AuditRecord * (n * len(arm_masks)))()

@@ -148,6 +148,23 @@ def test_gram_normal_operator_matches_oracle(case):
         assert np.array_equal(G, G.T)
 
 
+@pytest.mark.parametrize("kind", [0, 1])
+def test_gram_class_matches_normal_and_oracle(case, kind):
+    """rtt_gram_class (separable class, no P) equals the normal-operator Gram
+    and the oracle's P^T P to FP64 rounding, for both arms."""
+    w, tab, op = case
+    scl = O.scale(tab)
+    Q = O.synth_class(w, "S224" if kind == 0 else "L224")
+    Qd = torch.from_numpy(Q.reshape(w.grid.n_nodes, w.time.n_hats, -1).copy()).cuda()
+    for mask, orders in ((1, (0,)), (7, (0, 1, 2))):
+        G_ref = O.gram(O.restricted_response(w, tab.select(orders), Q, scl))
+        G = rtt.gram_class(op, kind, mask).cpu().numpy()
+        Gn = rtt.gram(op, Qd, mask, mode=rtt.GRAM_NORMAL).cpu().numpy()
+        assert np.array_equal(G, G.T)
+        assert np.max(np.abs(G - G_ref)) <= 1e-11 * np.max(np.abs(G_ref))
+        assert np.max(np.abs(G - Gn)) <= 1e-11 * np.max(np.abs(Gn))
+
+
 def test_rank_audit_driver_matches_oracle():
     """rtt_rank_audit over two geometries and two arms: rank, reach, J_old and
     A_0.999 against the oracle's audit of the same tables."""
@@ -171,8 +188,9 @@ def test_rank_audit_driver_matches_oracle():
             spec = O.operational_rank(O.gram(O.restricted_response(w, tab.select(orders), Q, scl)))
             per_arm.append((rr, O.j_old(info, a0), spec, a0))
         refs.append(per_arm)
-    for mode in (rtt.GRAM_DATA, rtt.GRAM_NORMAL):
-        recs, sig = rtt.rank_audit(ops, Qs, (1, 7), mode=mode)
+    for mode in (rtt.GRAM_DATA, rtt.GRAM_NORMAL, rtt.GRAM_CLASS_S224):
+        recs, sig = rtt.rank_audit(ops, None if mode == rtt.GRAM_CLASS_S224 else Qs, (1, 7),
+                                   mode=mode)
         for g in range(2):
             for a in range(2):
                 rr, jo, spec, a0 = refs[g][a]
