@@ -377,6 +377,18 @@ rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q_dev, int d, 
 rtt_status rtt_eig_sym(int n, double* A_dev, double* evals_host, double* V_dev, int max_sweeps,
                        int* sweeps_host, void* stream);
 
+/*
+ * rtt_eigvals_sym_batched -- eigenvalues only (ascending, evals_host: batch *
+ * n) of `batch` consecutive symmetric n x n FP64 matrices in A_dev (row-major,
+ * overwritten): Householder reduction to tridiagonal form and bisection with
+ * Sturm counts, one CTA per matrix.  Absolute error of order n eps ||A||;
+ * for eigenvalues that must be resolved relative to their own size near a
+ * threshold use rtt_eig_sym (the rank audit does so automatically).
+ * Synchronous.  Errors: RTT_EINVAL, RTT_ECUDA.
+ */
+rtt_status rtt_eigvals_sym_batched(int n, int batch, double* A_dev, double* evals_host,
+                                   void* stream);
+
 /* rtt_eig_sym on `batch` matrices at once (A_dev, V_dev: batch consecutive
    n x n blocks; evals_host: batch * n; sweeps_host: batch ints), one CTA per
    matrix. */
@@ -450,7 +462,9 @@ typedef struct {
  * rtt_gram_normal, RTT_GRAM_CLASS_S224 / _L224 use rtt_gram_class for that
  * class and d must be 224; where rtt_gram_class returns RTT_ESTATE the
  * normal-operator Gram of Q_dev[g] is taken instead, which then must not be
- * NULL), its Jacobi spectrum and the operational rank.
+ * NULL), its spectrum (rtt_eigvals_sym_batched; a matrix with an eigenvalue
+ * within 64 d eps max|lambda| of rho^2 is recomputed with the Jacobi
+ * eigensolver) and the operational rank.
  * out: host array [n_ops][n_arms]; sigma_out (optional): host
  * [n_ops][n_arms][d], singular values descending.  Synchronous.
  */

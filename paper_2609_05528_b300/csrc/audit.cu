@@ -28,6 +28,9 @@ extern "C" rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const doubl
 
 extern "C" rtt_status rtt_gram_class(rtt_op op, int arm_mask, int kind, double* G, void* stream);
 
+extern "C" rtt_status rtt_eigvals_sym_batched(int n, int batch, double* A, double* evals_host,
+                                              void* stream);
+
 extern "C" rtt_status rtt_eig_sym_batched(int n, int batch, double* A, double* evals_host,
                                           double* V, int max_sweeps, int* sweeps_host,
                                           void* stream);
@@ -106,10 +109,31 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
             r.seconds = std::chrono::duration<double>(t2 - t0).count();
         }
     }
-    // all spectra in one batched Jacobi launch (one CTA per matrix)
+    // all spectra: eigenvalues of every matrix by tridiagonal reduction and
+    // bisection (on a copy), then cyclic Jacobi for any matrix with an
+    // eigenvalue within the reduction's error bound of the threshold rho^2
     if (s == RTT_OK) {
         const auto t0 = std::chrono::steady_clock::now();
-        s = rtt_eig_sym_batched(d, nb, G, ev.data(), V, 80, sweeps.data(), stream);
+        cudaStream_t st = (cudaStream_t)stream;
+        const size_t bytes = (size_t)nb * d * d * 8;
+        if (cudaMemcpyAsync(V, G, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+            set_error("rank audit: copy failed");
+            s = RTT_ECUDA;
+        }
+        if (s == RTT_OK) s = rtt_eigvals_sym_batched(d, nb, V, ev.data(), stream);
+        for (int b = 0; s == RTT_OK && b < nb; ++b) {
+            const double rho = ops[b / n_arms]->opt.rho;
+            double amax = 0.0;
+            for (int i = 0; i < d; ++i) amax = std::fmax(amax, std::fabs(ev[(size_t)b * d + i]));
+            const double bound = 64.0 * d * 2.220446049250313e-16 * amax;
+            bool near = false;
+            for (int i = 0; i < d; ++i) near = near || std::fabs(ev[(size_t)b * d + i] - rho * rho) <= bound;
+            sweeps[b] = 0;
+            if (near) {  // decide this matrix with the Jacobi spectrum (relative accuracy)
+                s = rtt_eig_sym(d, G + (size_t)b * d * d, ev.data() + (size_t)b * d, V, 80,
+                                &sweeps[b], stream);
+            }
+        }
         const double te = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         for (int b = 0; s == RTT_OK && b < nb; ++b) {
             rtt_audit_record& r = out[b];

@@ -135,6 +135,7 @@ _SIGS = {
                                    ctypes.POINTER(ctypes.c_int), vp]),
     "rtt_eig_sym_batched": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, dp, vp, ctypes.c_int,
                                            ctypes.POINTER(ctypes.c_int), vp]),
+    "rtt_eigvals_sym_batched": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, dp, vp]),
     "rtt_solve_ridge": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, dp, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_double, ctypes.c_int, vp,
                                        ctypes.POINTER(ctypes.c_int), dp, vp]),
@@ -433,6 +434,17 @@ def eig_sym(G, max_sweeps: int = 60, stream=None):
                             _stream(stream)), "rtt_eig_sym")
     order = np.argsort(-ev, kind="stable")
     return ev[order], V[:, torch.from_numpy(order).to(V.device)], sw.value
+
+
+def eigvals_sym_batched(G, stream=None):
+    """Eigenvalues (ascending per matrix) of CUDA FP64 symmetric matrices
+    [batch, n, n] by tridiagonal reduction and bisection (input is copied)."""
+    A = G.clone().contiguous()
+    b, n = A.shape[0], A.shape[1]
+    ev = np.empty(b * n)
+    check(lib().rtt_eigvals_sym_batched(n, b, ctypes.c_void_p(A.data_ptr()), _ptr(ev, dp),
+                                        _stream(stream)), "rtt_eigvals_sym_batched")
+    return ev.reshape(b, n)
 
 
 def operational_rank(op: "Operator", Q, arm_mask: int = 7, rho: float = 1.0,

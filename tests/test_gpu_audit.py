@@ -165,6 +165,31 @@ def test_gram_class_matches_normal_and_oracle(case, kind):
         assert np.max(np.abs(G - Gn)) <= 1e-11 * np.max(np.abs(Gn))
 
 
+def test_eigvals_tridiagonal_matches_numpy():
+    """rtt_eigvals_sym_batched on graded symmetric matrices (eigenvalues from
+    1e-2 to 1e11, as the restricted Grams): every eigenvalue within
+    64 n eps max|lambda| of numpy's, the largest ones to 1e-11 relative."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    rng = np.random.default_rng(8)
+    n, b = 96, 5
+    mats = []
+    for _ in range(b):
+        Qm, _ = np.linalg.qr(rng.standard_normal((n, n)))
+        lam = 10.0 ** rng.uniform(-2, 11, n)
+        A = (Qm * lam) @ Qm.T
+        mats.append(0.5 * (A + A.T))
+    G = torch.from_numpy(np.stack(mats)).cuda()
+    ev = rtt.eigvals_sym_batched(G)
+    for i in range(b):
+        ref = np.linalg.eigvalsh(mats[i])
+        bound = 64 * n * 2.2e-16 * np.max(np.abs(ref))
+        assert np.max(np.abs(ev[i] - ref)) <= bound
+        big = ref > 1e-2 * ref.max()
+        assert np.max(np.abs(ev[i][big] / ref[big] - 1.0)) <= 1e-11
+
+
 def test_rank_audit_driver_matches_oracle():
     """rtt_rank_audit over two geometries and two arms: rank, reach, J_old and
     A_0.999 against the oracle's audit of the same tables."""
