@@ -76,18 +76,62 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(const ProbeArgs p)
         }
         const double t = p.t0 + p.cadence * (double)f;
         const int e0 = live ? p.row_ptr[row] : 0, e1 = live ? p.row_ptr[row + 1] : 0;
-        for (int ia = 0; ia < p.n_ages; ++ia) {
-            const double a = p.ages[ia];
-            T v = T(0);
-            for (int e = e0; e < e1; ++e) {
-                const T x = (T)((t - p.delay[e]) + a);
-                const T arg = x * x * (T)p.inv_2h2;
-                if (arg < T(100)) v += (T)(p.weight[e] * p.inv_Nh) * expo<T>(-arg);
-            }
-            T sq = v * v;
+        if constexpr (sizeof(T) == 4) {
+            // FP32 path: t - Delta_e split once per (frame, ray) into a head
+            // and a tail in FP32, so that x = (head + a) + tail needs only FP32
+            // adds per age (head + a is exact near the cancellation x ~ 0,
+            // and the ages are exact in FP32)
+            constexpr int kRaysReg = 8;
+            float hd[kRaysReg], tl[kRaysReg], wf[kRaysReg];
+            const int nr = e1 - e0 < kRaysReg ? e1 - e0 : kRaysReg;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-            if (lane == 0) acc[warp][ia] += (double)sq;
+            for (int q = 0; q < kRaysReg; ++q) {
+                hd[q] = 0.0f;
+                tl[q] = 0.0f;
+                wf[q] = 0.0f;
+                if (q < nr) {
+                    const double b = t - p.delay[e0 + q];
+                    hd[q] = (float)b;
+                    tl[q] = (float)(b - (double)hd[q]);
+                    wf[q] = (float)(p.weight[e0 + q] * p.inv_Nh);
+                }
+            }
+            const float i2h2 = (float)p.inv_2h2;
+            for (int ia = 0; ia < p.n_ages; ++ia) {
+                const float af = (float)p.ages[ia];
+                float v = 0.0f;
+#pragma unroll
+                for (int q = 0; q < kRaysReg; ++q) {
+                    if (q < nr) {
+                        const float x = (hd[q] + af) + tl[q];
+                        const float arg = x * x * i2h2;
+                        if (arg < 100.0f) v += wf[q] * __expf(-arg);
+                    }
+                }
+                for (int e = e0 + kRaysReg; e < e1; ++e) {  // rows with more rays
+                    const float x = (float)((t - p.delay[e]) + p.ages[ia]);
+                    const float arg = x * x * i2h2;
+                    if (arg < 100.0f) v += (float)(p.weight[e] * p.inv_Nh) * __expf(-arg);
+                }
+                float sq = v * v;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                if (lane == 0) acc[warp][ia] += (double)sq;
+            }
+        } else {
+            for (int ia = 0; ia < p.n_ages; ++ia) {
+                const double a = p.ages[ia];
+                T v = T(0);
+                for (int e = e0; e < e1; ++e) {
+                    const T x = (T)((t - p.delay[e]) + a);
+                    const T arg = x * x * (T)p.inv_2h2;
+                    if (arg < T(100)) v += (T)(p.weight[e] * p.inv_Nh) * expo<T>(-arg);
+                }
+                T sq = v * v;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+                if (lane == 0) acc[warp][ia] += (double)sq;
+            }
         }
     }
     __syncthreads();
