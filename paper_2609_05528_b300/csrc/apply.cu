@@ -284,49 +284,6 @@ __device__ __forceinline__ double exact_frac<double>(const ApplyArgs<double>& a,
 template <typename T>
 __device__ __forceinline__ void corner_w(const ApplyArgs<T>& a, int e, T w[4]) { load_w(a, e, w); }
 
-// One staging pass of the staged forward: items o = base + lane + 32 u
-// (u < U) of the ray's window, z[o] = sum_c W_c x[node_c][k_lo + o / Q][.]
-template <typename T, int BC, int U>
-__device__ __forceinline__ void stage_pass(const ApplyArgs<T>& a, const T* x00, const T* x10,
-                                           const T* x01, const T* x11, const T (&w)[4], int k_lo,
-                                           int n_items, int base, int lane,
-                                           typename Vec16<T>::type* zsv) {
-    using V = typename Vec16<T>::type;
-    constexpr int VW = Vec16<T>::W;
-    constexpr int Q = BC / VW > 0 ? BC / VW : 1;
-    V v[U][4];
-    bool okv[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int o = base + lane + 32 * u;
-        const int kk = o / Q, q = o - kk * Q;
-        const int k = k_lo + kk;
-        okv[u] = o < n_items && k >= 0 && k < a.K;
-        if (okv[u]) {
-            const int64_t off = (int64_t)k * a.B + VW * q;
-            v[u][0] = __ldg(reinterpret_cast<const V*>(x00 + off));
-            v[u][1] = __ldg(reinterpret_cast<const V*>(x10 + off));
-            v[u][2] = __ldg(reinterpret_cast<const V*>(x01 + off));
-            v[u][3] = __ldg(reinterpret_cast<const V*>(x11 + off));
-        }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const int o = base + lane + 32 * u;
-        if (o < n_items) {
-            V z;
-            T* zc = comps<T>(z);
-#pragma unroll
-            for (int c = 0; c < VW; ++c) {
-                zc[c] = okv[u] ? interp4(w[0], comps<T>(v[u][0])[c], w[1], comps<T>(v[u][1])[c],
-                                         w[2], comps<T>(v[u][2])[c], w[3], comps<T>(v[u][3])[c])
-                               : T(0);
-            }
-            zsv[o] = z;
-        }
-    }
-}
-
 // FPL frames per lane (32 FPL per task); SU staging items in flight per lane
 // and pass.  Fewer accumulators per lane (BC FPL <= 16) or one item in
 // flight (SU = 1) allow three resident CTAs per SM.
@@ -378,13 +335,39 @@ fwd3_kernel(const ApplyArgs<T> a) {
                 constexpr int Q = BC / VW > 0 ? BC / VW : 1;
                 V* zsv = reinterpret_cast<V*>(zs);
                 const int n_items = nwin * Q;
-                // full passes of SU items per lane, then single-item passes for
-                // the tail (a window of 33-34 hats is 64 items plus a few)
-                int base = 0;
-                for (; base + 32 * SU <= n_items; base += 32 * SU)
-                    stage_pass<T, BC, SU>(a, x00, x10, x01, x11, w, k_lo, n_items, base, lane, zsv);
-                for (; base < n_items; base += 32)
-                    stage_pass<T, BC, 1>(a, x00, x10, x01, x11, w, k_lo, n_items, base, lane, zsv);
+                for (int base = 0; base < n_items; base += 32 * SU) {
+                    V v[SU][4];
+                    bool okv[SU];
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const int o = base + lane + 32 * u;
+                        const int kk = o / Q, q = o - kk * Q;
+                        const int k = k_lo + kk;
+                        okv[u] = o < n_items && k >= 0 && k < a.K;
+                        if (okv[u]) {
+                            const int64_t off = (int64_t)k * a.B + VW * q;
+                            v[u][0] = __ldg(reinterpret_cast<const V*>(x00 + off));
+                            v[u][1] = __ldg(reinterpret_cast<const V*>(x10 + off));
+                            v[u][2] = __ldg(reinterpret_cast<const V*>(x01 + off));
+                            v[u][3] = __ldg(reinterpret_cast<const V*>(x11 + off));
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < SU; ++u) {
+                        const int o = base + lane + 32 * u;
+                        if (o < n_items) {
+                            V z;
+                            T* zc = comps<T>(z);
+#pragma unroll
+                            for (int c = 0; c < VW; ++c) {
+                                zc[c] = okv[u] ? interp4(w[0], comps<T>(v[u][0])[c], w[1], comps<T>(v[u][1])[c],
+                                                         w[2], comps<T>(v[u][2])[c], w[3], comps<T>(v[u][3])[c])
+                                               : T(0);
+                            }
+                            zsv[o] = z;
+                        }
+                    }
+                }
             } else {
                 for (int o = lane; o < nwin * BC; o += 32) {
                     const int kk = o / BC, bb = o - kk * BC;
