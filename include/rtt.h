@@ -502,7 +502,7 @@ typedef struct {
     int32_t fwd_frames_per_lane;
     int32_t fwd_staging;  /* staged forward: x items in flight per lane */
     int32_t time_kernel;  /* adjoint phase 1: 1 general, 2 periodic weights, 3 periodic + TMA */
-    int32_t space_kernel; /* adjoint phase 2: 1 scalar, 2 16-byte loads */
+    int32_t space_kernel; /* adjoint phase 2: 1 scalar, 2 16-byte loads, 3 same with 8 in flight */
     float fwd_ms, adj_ms;           /* chosen variants, ms per apply */
     float fwd_ms_rule, adj_ms_rule; /* the untuned default rule, ms per apply */
     int32_t candidates;             /* configurations timed */
@@ -522,7 +522,8 @@ typedef struct {
     int32_t time_kernel;  /* 1 general, 2 periodic weights, 3 periodic + TMA (where
                              the cadence or the buffers do not allow 2 or 3, the
                              next one down runs) */
-    int32_t space_kernel; /* 1 scalar, 2 16-byte loads (where the buffers allow) */
+    int32_t space_kernel; /* 1 scalar, 2 16-byte loads, 3 16-byte loads with eight
+                             incidences in flight (where the buffers allow) */
     int32_t fused_step;   /* rtt_apply_A_AT: 1 = fused forward + temporal adjoint where the
                              batch, cadence and buffers allow it, 0 = separate pair */
     int32_t fwd_staging;  /* staged forward: x items in flight per lane, 1, 2 or 3

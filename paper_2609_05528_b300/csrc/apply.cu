@@ -160,6 +160,19 @@ __device__ __forceinline__ T hat2(T acc, T g, T z0, T fr, T z1) {
     return fmac(fr, z1, fmac(g, z0, acc));
 }
 
+// a v + (c0, c1, c2, c3) per component with packed FP32 pairs (the fused
+// multiply-add of fmac on each component, two per instruction)
+__device__ __forceinline__ void fmac2x2(float a, const float4& v, float& c0, float& c1, float& c2,
+                                        float& c3) {
+    const float2 a2 = make_float2(a, a);
+    const float2 lo = __ffma2_rn(a2, make_float2(v.x, v.y), make_float2(c0, c1));
+    const float2 hi = __ffma2_rn(a2, make_float2(v.z, v.w), make_float2(c2, c3));
+    c0 = lo.x;
+    c1 = lo.y;
+    c2 = hi.x;
+    c3 = hi.y;
+}
+
 constexpr int kWarpsPerBlock = 8;
 
 constexpr int kAdjOutPerLane = 8;
@@ -358,11 +371,29 @@ fwd3_kernel(const ApplyArgs<T> a) {
                         if (o < n_items) {
                             V z;
                             T* zc = comps<T>(z);
+                            if constexpr (sizeof(T) == 4) {
+                                // packed FP32 pairs, the operations of interp4 per component
 #pragma unroll
-                            for (int c = 0; c < VW; ++c) {
-                                zc[c] = okv[u] ? interp4(w[0], comps<T>(v[u][0])[c], w[1], comps<T>(v[u][1])[c],
-                                                         w[2], comps<T>(v[u][2])[c], w[3], comps<T>(v[u][3])[c])
-                                               : T(0);
+                                for (int c = 0; c < VW; c += 2) {
+                                    float2 r = __fmul2_rn(make_float2(w[0], w[0]),
+                                                          make_float2(comps<T>(v[u][0])[c], comps<T>(v[u][0])[c + 1]));
+                                    r = __ffma2_rn(make_float2(w[1], w[1]),
+                                                   make_float2(comps<T>(v[u][1])[c], comps<T>(v[u][1])[c + 1]), r);
+                                    r = __ffma2_rn(make_float2(w[2], w[2]),
+                                                   make_float2(comps<T>(v[u][2])[c], comps<T>(v[u][2])[c + 1]), r);
+                                    r = __ffma2_rn(make_float2(w[3], w[3]),
+                                                   make_float2(comps<T>(v[u][3])[c], comps<T>(v[u][3])[c + 1]), r);
+                                    zc[c] = okv[u] ? r.x : T(0);
+                                    zc[c + 1] = okv[u] ? r.y : T(0);
+                                }
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < VW; ++c) {
+                                    zc[c] = okv[u] ? interp4(w[0], comps<T>(v[u][0])[c], w[1],
+                                                             comps<T>(v[u][1])[c], w[2], comps<T>(v[u][2])[c],
+                                                             w[3], comps<T>(v[u][3])[c])
+                                                   : T(0);
+                                }
                             }
                             zsv[o] = z;
                         }
@@ -396,10 +427,24 @@ fwd3_kernel(const ApplyArgs<T> a) {
                         for (int q = 0; q < BC / VW; ++q) {
                             const V p0 = reinterpret_cast<const V*>(z0)[q];
                             const V p1 = reinterpret_cast<const V*>(z0 + BC)[q];
+                            if constexpr (sizeof(T) == 4) {
+                                // packed FP32 pairs: per component the fused
+                                // multiply-adds of hat2, in the same order
+                                const float2 g2 = make_float2(g, g), f2 = make_float2(fr, fr);
 #pragma unroll
-                            for (int c = 0; c < VW; ++c)
-                                acc[j][VW * q + c] =
-                                    hat2(acc[j][VW * q + c], g, comps<T>(p0)[c], fr, comps<T>(p1)[c]);
+                                for (int c = 0; c < VW; c += 2) {
+                                    float2 s2 = make_float2(acc[j][VW * q + c], acc[j][VW * q + c + 1]);
+                                    s2 = __ffma2_rn(g2, make_float2(comps<T>(p0)[c], comps<T>(p0)[c + 1]), s2);
+                                    s2 = __ffma2_rn(f2, make_float2(comps<T>(p1)[c], comps<T>(p1)[c + 1]), s2);
+                                    acc[j][VW * q + c] = s2.x;
+                                    acc[j][VW * q + c + 1] = s2.y;
+                                }
+                            } else {
+#pragma unroll
+                                for (int c = 0; c < VW; ++c)
+                                    acc[j][VW * q + c] =
+                                        hat2(acc[j][VW * q + c], g, comps<T>(p0)[c], fr, comps<T>(p1)[c]);
+                            }
                         }
                     } else {
 #pragma unroll
@@ -770,10 +815,8 @@ adj_time4_kernel(const ApplyArgs<float> a) {
 #pragma unroll
                         for (int q = 0; q < Q; ++q) {
                             const float4 t = ysv[swz(f - fA, q, Q, pshift)];
-                            acc[4 * q + 0] = fmac(wt[j], t.x, acc[4 * q + 0]);
-                            acc[4 * q + 1] = fmac(wt[j], t.y, acc[4 * q + 1]);
-                            acc[4 * q + 2] = fmac(wt[j], t.z, acc[4 * q + 2]);
-                            acc[4 * q + 3] = fmac(wt[j], t.w, acc[4 * q + 3]);
+                            fmac2x2(wt[j], t, acc[4 * q + 0], acc[4 * q + 1], acc[4 * q + 2],
+                                    acc[4 * q + 3]);
                         }
                     } else {
                         const float* yv = ys + (f - fA) * BC;
@@ -967,10 +1010,7 @@ adj_time5_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float
 #pragma unroll
                 for (int q = 0; q < Q; ++q) {
                     const float4 v = bv[8 * r + ((cb + q) ^ (r & 7))];
-                    acc[4 * q + 0] = fmac(wt[j], v.x, acc[4 * q + 0]);
-                    acc[4 * q + 1] = fmac(wt[j], v.y, acc[4 * q + 1]);
-                    acc[4 * q + 2] = fmac(wt[j], v.z, acc[4 * q + 2]);
-                    acc[4 * q + 3] = fmac(wt[j], v.w, acc[4 * q + 3]);
+                    fmac2x2(wt[j], v, acc[4 * q + 0], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
                 }
             }
             float4* zo = reinterpret_cast<float4*>(a.zhat + (cur.e * a.K + k) * BC);
@@ -1372,10 +1412,8 @@ fused_kernel(const ApplyArgs<float> a, const float* __restrict__ d, int RG, int 
 #pragma unroll
                     for (int q = 0; q < Q; ++q) {
                         const float4 v = rrow[swz(f, q, Q, pshift)];
-                        accz[4 * q + 0] = fmac(wt[j], v.x, accz[4 * q + 0]);
-                        accz[4 * q + 1] = fmac(wt[j], v.y, accz[4 * q + 1]);
-                        accz[4 * q + 2] = fmac(wt[j], v.z, accz[4 * q + 2]);
-                        accz[4 * q + 3] = fmac(wt[j], v.w, accz[4 * q + 3]);
+                        fmac2x2(wt[j], v, accz[4 * q + 0], accz[4 * q + 1], accz[4 * q + 2],
+                                accz[4 * q + 3]);
                     }
                 }
                 float4* zo = reinterpret_cast<float4*>(a.zhat + (e * a.K + k) * BC);
@@ -1480,9 +1518,7 @@ adj_space3_kernel(const ApplyArgs<T> a) {
 // lane owns 8 consecutive (hat, batch) outputs of the task's block, so one
 // incidence costs two float4 loads per lane.  Same incidence order and
 // accumulation sequence as adj_space3_kernel.
-constexpr int kSpace4Unroll = 4;
-
-template <int BC>
+template <int BC, int kSpace4Unroll = 4>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 adj_space4_kernel(const ApplyArgs<float> a) {
     static_assert(BC % 4 == 0, "vector path needs 4 | BC");
@@ -1525,10 +1561,8 @@ adj_space4_kernel(const ApplyArgs<float> a) {
             }
 #pragma unroll
             for (int u = 0; u < kSpace4Unroll; ++u) {
-                acc0.x = fmac(coef[u], v0[u].x, acc0.x); acc0.y = fmac(coef[u], v0[u].y, acc0.y);
-                acc0.z = fmac(coef[u], v0[u].z, acc0.z); acc0.w = fmac(coef[u], v0[u].w, acc0.w);
-                acc1.x = fmac(coef[u], v1[u].x, acc1.x); acc1.y = fmac(coef[u], v1[u].y, acc1.y);
-                acc1.z = fmac(coef[u], v1[u].z, acc1.z); acc1.w = fmac(coef[u], v1[u].w, acc1.w);
+                fmac2x2(coef[u], v0[u], acc0.x, acc0.y, acc0.z, acc0.w);
+                fmac2x2(coef[u], v1[u], acc1.x, acc1.y, acc1.z, acc1.w);
             }
         }
         for (; ii < i_end; ++ii) {
@@ -1935,8 +1969,11 @@ static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStr
     a.n_tasks = (int64_t)a.n_nodes * a.n_kchunk;
     if (a.n_tasks == 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4 && BC % 4 == 0) {
-        if (v.space == 2 && a.Bc == BC && vec_ok(a)) {
-            adj_space4_kernel<BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+        if (v.space >= 2 && a.Bc == BC && vec_ok(a)) {
+            if (v.space == 3)  // eight incidences in flight per lane
+                adj_space4_kernel<BC, 8><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+            else
+                adj_space4_kernel<BC, 4><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
             return cudaGetLastError();
         }
     }

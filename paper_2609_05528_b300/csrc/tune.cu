@@ -78,7 +78,7 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
     const int bc = v->fwd_bc;
     if (v->fwd_kernel < 1 || v->fwd_kernel > 3 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
         v->fwd_half < 0 || v->fwd_half > 1 || v->time_kernel < 1 || v->time_kernel > 3 ||
-        v->space_kernel < 1 || v->space_kernel > 2) {
+        v->space_kernel < 1 || v->space_kernel > 3) {
         set_error("invalid variant (fwd %d bc %d half %d time %d space %d)", v->fwd_kernel, bc,
                   v->fwd_half, v->time_kernel, v->space_kernel);
         return RTT_EINVAL;
@@ -215,7 +215,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     const bool tma_ok = (P == 2 || P == 4) && (B == 4 || B == 8 || B == 16 || B == 32) &&
                         (op->time.n_frames % (32 / B)) == 0;
     for (int tk = 1; tk <= (periodic ? (tma_ok ? 3 : 2) : 1); ++tk)
-        for (int sk = 1; sk <= 2; ++sk) {
+        for (int sk = 1; sk <= 3; ++sk) {
             ApplyVariant v = best;
             v.time = (int8_t)tk;
             v.space = (int8_t)sk;

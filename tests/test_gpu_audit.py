@@ -112,6 +112,39 @@ def test_ridge_cg_matches_oracle(case):
             assert err < 1e-4, (j, lam, err)
 
 
+def test_full_space_rank_32x32():
+    """The 32x32 Schwarzschild workload audited on its full 1536-dimensional
+    grid x hat space (Q = I): the restricted Gram through both FP64 routes,
+    its eigenvalues (tridiagonal path) and the operational rank against the
+    oracle's dense A, for the direct and resolved arms."""
+    build.build()
+    w = I.schw32()
+    tab = O.build_table(w, I.screen_samples(w))
+    op = rtt.Operator(w, {"order": tab.order, "pixel": tab.pixel, "r": tab.r, "phi": tab.phi,
+                          "delay": tab.delay, "weight": tab.weight,
+                          "throughput": tab.throughput})
+    scl = O.scale(tab)
+    n = w.n_dof
+    assert n == 1536
+    Qd = torch.eye(n, dtype=torch.float64).reshape(w.grid.n_nodes, w.time.n_hats, n).cuda()
+    for mask, orders in ((1, (0,)), (7, (0, 1, 2))):
+        D = O.dense_A(w, tab.select(orders), scl)
+        lam_ref = np.linalg.eigvalsh(D.T @ D)
+        sig_ref = np.sqrt(np.maximum(lam_ref, 0.0))
+        rank_ref = int(np.count_nonzero(sig_ref >= 1.0))
+        margin = np.min(np.abs(sig_ref - 1.0))
+        for mode in (rtt.GRAM_DATA, rtt.GRAM_NORMAL):
+            G = rtt.gram(op, Qd, mask, mode=mode)
+            ev = rtt.eigvals_sym_batched(G[None])[0]
+            assert np.max(np.abs(ev - lam_ref)) <= 64 * n * 2.2e-16 * np.max(lam_ref) * 4
+            sig = np.sqrt(np.maximum(ev, 0.0))
+            if margin > 1e-6:
+                assert int(np.count_nonzero(sig >= 1.0)) == rank_ref
+        # blindness: the direct arm's rank is below the full dimension
+        if mask == 1:
+            assert rank_ref < n
+
+
 def test_tsvd_matches_oracle():
     """TSVD in the S224 class truncated at the operational rank vs the oracle."""
     build.build()
