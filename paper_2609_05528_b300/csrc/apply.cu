@@ -90,6 +90,7 @@ struct ApplyArgs {
     int seg_rows_all;  // total rows of the operator (all orders)
     const int32_t* node_order;  // nodes by descending incidence count (load balance)
     int* status;                // device status word (bit 0: a bounded wait timed out)
+    int hs32;                   // hat steps per 32 frames when a whole number, else 0
     int n_fchunk, n_bchunk, n_kchunk;
     int64_t n_tasks;
 };
@@ -412,46 +413,58 @@ fwd3_kernel(const ApplyArgs<T> a) {
                 }
             }
             __syncwarp();
-            int64_t U = U0 - (int64_t)(f_begin + lane) * a.D;
-            const int64_t dU = (int64_t)32 * a.D;
+            // (1 - fr) z[k0] + fr z[k0 + 1] for frame j of this lane
+            auto add_frame = [&](int j, int k0, T fr) {
+                const T g = T(1) - fr;
+                const T* z0 = zs + (k0 - k_lo) * BC;
+                if constexpr (BC >= VW) {
 #pragma unroll
-            for (int j = 0; j < FPL; ++j) {
-                const int f = f_begin + lane + 32 * j;
-                if (f < f_end) {
-                    const int k0 = (int)(U >> kFracBits);
-                    const T fr = frac_of<T>(U, f, a.D, F64);
-                    const T g = T(1) - fr;
-                    const T* z0 = zs + (k0 - k_lo) * BC;
-                    if constexpr (BC >= VW) {
+                    for (int q = 0; q < BC / VW; ++q) {
+                        const V p0 = reinterpret_cast<const V*>(z0)[q];
+                        const V p1 = reinterpret_cast<const V*>(z0 + BC)[q];
+                        if constexpr (sizeof(T) == 4) {
+                            // packed FP32 pairs: per component the fused
+                            // multiply-adds of hat2, in the same order
+                            const float2 g2 = make_float2(g, g), f2 = make_float2(fr, fr);
 #pragma unroll
-                        for (int q = 0; q < BC / VW; ++q) {
-                            const V p0 = reinterpret_cast<const V*>(z0)[q];
-                            const V p1 = reinterpret_cast<const V*>(z0 + BC)[q];
-                            if constexpr (sizeof(T) == 4) {
-                                // packed FP32 pairs: per component the fused
-                                // multiply-adds of hat2, in the same order
-                                const float2 g2 = make_float2(g, g), f2 = make_float2(fr, fr);
-#pragma unroll
-                                for (int c = 0; c < VW; c += 2) {
-                                    float2 s2 = make_float2(acc[j][VW * q + c], acc[j][VW * q + c + 1]);
-                                    s2 = __ffma2_rn(g2, make_float2(comps<T>(p0)[c], comps<T>(p0)[c + 1]), s2);
-                                    s2 = __ffma2_rn(f2, make_float2(comps<T>(p1)[c], comps<T>(p1)[c + 1]), s2);
-                                    acc[j][VW * q + c] = s2.x;
-                                    acc[j][VW * q + c + 1] = s2.y;
-                                }
-                            } else {
-#pragma unroll
-                                for (int c = 0; c < VW; ++c)
-                                    acc[j][VW * q + c] =
-                                        hat2(acc[j][VW * q + c], g, comps<T>(p0)[c], fr, comps<T>(p1)[c]);
+                            for (int c = 0; c < VW; c += 2) {
+                                float2 s2 = make_float2(acc[j][VW * q + c], acc[j][VW * q + c + 1]);
+                                s2 = __ffma2_rn(g2, make_float2(comps<T>(p0)[c], comps<T>(p0)[c + 1]), s2);
+                                s2 = __ffma2_rn(f2, make_float2(comps<T>(p1)[c], comps<T>(p1)[c + 1]), s2);
+                                acc[j][VW * q + c] = s2.x;
+                                acc[j][VW * q + c + 1] = s2.y;
                             }
-                        }
-                    } else {
+                        } else {
 #pragma unroll
-                        for (int b = 0; b < BC; ++b) acc[j][b] = hat2(acc[j][b], g, z0[b], fr, z0[BC + b]);
+                            for (int c = 0; c < VW; ++c)
+                                acc[j][VW * q + c] =
+                                    hat2(acc[j][VW * q + c], g, comps<T>(p0)[c], fr, comps<T>(p1)[c]);
+                        }
                     }
+                } else {
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) acc[j][b] = hat2(acc[j][b], g, z0[b], fr, z0[BC + b]);
                 }
-                U -= dU;
+            };
+            const int64_t U1 = U0 - (int64_t)(f_begin + lane) * a.D;
+            if (a.hs32 > 0) {
+                // 32 frames are hs32 whole hat steps: a lane's frames share the
+                // hat fraction and step down hs32 hats from one to the next
+                // (the same k0 and fraction as the per-frame computation)
+                const int k00 = (int)(U1 >> kFracBits);
+                const T fr0 = frac_of<T>(U1, f_begin + lane, a.D, F64);
+#pragma unroll
+                for (int j = 0; j < FPL; ++j)
+                    if (f_begin + lane + 32 * j < f_end) add_frame(j, k00 - j * a.hs32, fr0);
+            } else {
+                int64_t U = U1;
+                const int64_t dU = (int64_t)32 * a.D;
+#pragma unroll
+                for (int j = 0; j < FPL; ++j) {
+                    const int f = f_begin + lane + 32 * j;
+                    if (f < f_end) add_frame(j, (int)(U >> kFracBits), frac_of<T>(U, f, a.D, F64));
+                    U -= dU;
+                }
             }
             __syncwarp();
         }
@@ -1658,6 +1671,9 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     a.seg_rows_all = (int)op->n_rows;
     a.node_order = op->node_order;
     a.status = op->dev_status;
+    a.hs32 = (op->frame_D > 0 && ((int64_t)32 * op->frame_D) % kFracOne == 0)
+                 ? (int)((int64_t)32 * op->frame_D / kFracOne)
+                 : 0;
     return a;
 }
 
