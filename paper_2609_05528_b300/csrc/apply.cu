@@ -938,6 +938,7 @@ adj_time5_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float
     struct Item {
         int64_t e;
         int g, row_out, fbase, fA, fB, f4;  // f4: first frame of the first copied row
+        int32_t r0;                          // weight phase of the ray (see above)
     };
     auto fill = [&](int64_t e, int g, Item& it) {
         it.e = e;
@@ -946,6 +947,7 @@ adj_time5_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float
         const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
         const int64_t c0 = (U0 * P) >> kFracBits;
         it.fbase = (int)(c0 + 1 - P);
+        it.r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
         const int kg0 = 32 * g, kg1 = min(kg0 + 31, a.K - 1);
         it.fA = max(it.fbase - P * kg1, 0);
         it.fB = min(it.fbase - P * kg0 + 2 * P - 1, a.Tn - 1);
@@ -989,19 +991,21 @@ adj_time5_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float
         }
     if (!have) return;
     issue(cur, 0);
+    // item t + 1's metadata is read one iteration ahead of its copy, so the
+    // copy is issued without waiting on global loads
+    Item nxt;
+    bool have_nxt = next(cur.e, cur.g, nxt);
     for (uint32_t t = 0; have; ++t) {
-        Item nxt;
-        const bool more = next(cur.e, cur.g, nxt);
-        if (more) issue(nxt, (t + 1) & 1);
+        if (have_nxt) issue(nxt, (t + 1) & 1);
+        Item nn;
+        const bool have_nn = have_nxt && next(nxt.e, nxt.g, nn);
         if (!mbar_wait(bar0 + 8u * (t & 1), (t >> 1) & 1)) {
             if (lane == 0) atomicOr(status, 1);
-            if (more) mbar_wait(bar0 + 8u * ((t + 1) & 1), ((t + 1) >> 1) & 1);
+            if (have_nxt) mbar_wait(bar0 + 8u * ((t + 1) & 1), ((t + 1) >> 1) & 1);
             return;
         }
         // contraction of group cur.g of ray cur.e from buffer t & 1
-        const int64_t U0 = (int64_t)a.K0[cur.e] * kFracOne + (int64_t)a.F0[cur.e];
-        const int64_t c0 = (U0 * P) >> kFracBits;
-        const int32_t r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
+        const int32_t r0 = cur.r0;
         float wt[2 * P];
 #pragma unroll
         for (int j = 0; j < 2 * P; ++j)
@@ -1033,7 +1037,9 @@ adj_time5_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float
         }
         __syncwarp();  // buffer t & 1 is free for the copy issued at step t + 1
         cur = nxt;
-        have = more;
+        have = have_nxt;
+        nxt = nn;
+        have_nxt = have_nn;
     }
 }
 
