@@ -501,7 +501,8 @@ typedef struct {
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
     int32_t fwd_staging;  /* staged forward: x items in flight per lane */
-    int32_t time_kernel;  /* adjoint phase 1: 1 general, 2 periodic weights, 3 periodic + TMA */
+    int32_t time_kernel;  /* adjoint phase 1: 1 general, 2 periodic weights, 3 periodic + TMA,
+                             4 periodic + TMA, whole 64-hat items */
     int32_t space_kernel; /* adjoint phase 2: 1 scalar, 2 16-byte loads, 3 same with 8 in flight */
     float fwd_ms, adj_ms;           /* chosen variants, ms per apply */
     float fwd_ms_rule, adj_ms_rule; /* the untuned default rule, ms per apply */
@@ -519,9 +520,12 @@ typedef struct {
                              else staged) */
     int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32 */
     int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
-    int32_t time_kernel;  /* 1 general, 2 periodic weights, 3 periodic + TMA (where
-                             the cadence or the buffers do not allow 2 or 3, the
-                             next one down runs) */
+    int32_t time_kernel;  /* 1 general, 2 periodic weights, 3 periodic + TMA, 4 periodic
+                             + TMA with whole 64-hat items and zero-filled frames
+                             outside the observation (batch 4, 8, 16 or 32 whose
+                             frames per 128-byte row divide the frames per hat);
+                             where the cadence or the buffers do not allow the
+                             choice, the next one down runs */
     int32_t space_kernel; /* 1 scalar, 2 16-byte loads, 3 16-byte loads with eight
                              incidences in flight (where the buffers allow) */
     int32_t fused_step;   /* rtt_apply_A_AT: 1 = fused forward + temporal adjoint where the

@@ -176,6 +176,36 @@ __device__ __forceinline__ void fmac2x2(float a, const float4& v, float& c0, flo
 
 constexpr int kWarpsPerBlock = 8;
 
+// Grid-stride walk over (output row, frame chunk, batch chunk) tasks, batch
+// chunk fastest (task = (row nf + f) nb + b).  The first task and the stride
+// are split into those digits once; each step adds the stride's digits with
+// carries, so no task index is divided inside the loop.
+struct TaskWalk {
+    int b, f, r;     // current task
+    int db, df, dr;  // grid stride in the same digits
+    int nb, nf;
+    __device__ __forceinline__ TaskWalk(int64_t start, int64_t stride, int nb_, int nf_)
+        : nb(nb_), nf(nf_) {
+        b = (int)(start % nb);
+        int64_t q = start / nb;
+        f = (int)(q % nf);
+        r = (int)(q / nf);
+        db = (int)(stride % nb);
+        q = stride / nb;
+        df = (int)(q % nf);
+        dr = (int)(q / nf);
+    }
+    __device__ __forceinline__ void next() {
+        b += db;
+        int c = b >= nb ? 1 : 0;
+        b -= c * nb;
+        f += df + c;
+        c = f >= nf ? 1 : 0;
+        f -= c * nf;
+        r += dr + c;
+    }
+};
+
 constexpr int kAdjOutPerLane = 8;
 
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t d) {
@@ -315,11 +345,10 @@ fwd3_kernel(const ApplyArgs<T> a) {
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
     const bool vec = (BC >= VW) && a.vec4;
-    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
-        const int bchunk = (int)(task % a.n_bchunk);
-        const int64_t t2 = task / a.n_bchunk;
-        const int fchunk = (int)(t2 % a.n_fchunk);
-        const int row_out = (int)(t2 / a.n_fchunk);
+    for (TaskWalk tw(warp_global, n_warps, a.n_bchunk, a.n_fchunk); tw.r < a.seg.total; tw.next()) {
+        const int bchunk = tw.b;
+        const int fchunk = tw.f;
+        const int row_out = tw.r;
         const int row = seg_in_row(a.seg, row_out);
         const int f_begin = fchunk * FC;
         const int f_end = min(a.Tn, f_begin + FC);
@@ -1043,6 +1072,240 @@ adj_time5_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float
     }
 }
 
+// Adjoint phase 1 with whole 64-hat items: the arithmetic and order of
+// adj_time4_kernel (hence the same bits), with less work per output.
+//  * An item is (ray, group of 32 HG hats); lane l owns hats kg0 + l + 32 h.
+//    At K <= 32 HG a ray is one item: one copy, one set of 2P tap weights.
+//  * y is seen through a 3D tensor map (128-byte row, row of the frame axis,
+//    data row), so frames before 0 or after the last one arrive as zeros from
+//    the copy's out-of-bounds fill: a zero frame adds w * 0 = +0 to a sum that
+//    is never -0, leaving it unchanged, so no tap needs a bounds test.
+//  * Frames per 128-byte row F = 32 / BC divides P, so a lane's first frame
+//    fbase - P k - f4 has the same residue M mod F on every lane and hat; a
+//    switch on M makes each tap's row step and 16-byte chunk compile-time
+//    constants, and a tap's swizzled address is one OR of per-row terms.
+// Double-buffered copies per warp with item metadata one item ahead, bounded
+// mbarrier waits as in adj_time5_kernel.
+constexpr int kAdj6Warps = 4;
+
+template <int BC, int P, int HG>
+struct T6Box {
+    static constexpr int kF = 32 / BC;  // frames per 128-byte row
+    static_assert(P % kF == 0, "a row holds a whole number of frames that divides P");
+    // rows covering (32 HG + 1) P frames that start anywhere inside a row
+    static constexpr int kRows = ((32 * HG + 1) * P + 2 * (kF - 1)) / kF;
+    static constexpr uint32_t kBytes = (uint32_t)kRows * 128;
+    static constexpr uint32_t kStride = (kBytes + 1023) & ~1023u;
+};
+
+// taps of HG hats of one lane for residue M: rows rs + dj of the buffer
+template <int BC, int P, int HG, int M>
+__device__ __forceinline__ void adj6_contract(const unsigned char* buf, int rs0, const float (&wt)[2 * P],
+                                              float (&acc)[HG][BC]) {
+    constexpr int Q = BC / 4;
+    constexpr int F = 32 / BC;
+    constexpr int ND = (M + 2 * P - 1) / F + 1;  // rows one hat's taps touch
+#pragma unroll
+    for (int h = 0; h < HG; ++h) {
+        const int rs = rs0 - h * (32 * P / F);
+        uint32_t A[ND], X[ND];
+#pragma unroll
+        for (int d = 0; d < ND; ++d) {
+            A[d] = (uint32_t)(rs + d) * 128u;
+            X[d] = (uint32_t)((rs + d) & 7) << 4;
+        }
+#pragma unroll
+        for (int b = 0; b < BC; ++b) acc[h][b] = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 2 * P; ++j) {
+            const int dj = (M + j) / F, cj = (M + j) % F;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) {
+                const uint32_t off = A[dj] | ((uint32_t)(16 * (cj * Q + q)) ^ X[dj]);
+                const float4 v = *reinterpret_cast<const float4*>(buf + off);
+                fmac2x2(wt[j], v, acc[h][4 * q + 0], acc[h][4 * q + 1], acc[h][4 * q + 2],
+                        acc[h][4 * q + 3]);
+            }
+        }
+    }
+}
+
+template <int BC, int P, int HG>
+__global__ void __launch_bounds__(kAdj6Warps * 32)
+adj_time6_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float> a, int* status) {
+    static_assert(BC == 4 || BC == 8 || BC == 16 || BC == 32, "128-byte rows of whole frames");
+    constexpr int F = T6Box<BC, P, HG>::kF;
+    constexpr int LGF = F == 1 ? 0 : (F == 2 ? 1 : (F == 4 ? 2 : 3));
+    constexpr uint32_t BOX_BYTES = T6Box<BC, P, HG>::kBytes;
+    constexpr uint32_t BUF_STRIDE = T6Box<BC, P, HG>::kStride;
+    constexpr int HATS = 32 * HG;  // hats per item
+    extern __shared__ unsigned char smem6t_raw[];
+    const uint32_t raw_u32 = smem_u32(smem6t_raw);
+    const uint32_t base_u32 = (raw_u32 + 1023) & ~1023u;  // 128-byte swizzle atom alignment
+    unsigned char* base = smem6t_raw + (base_u32 - raw_u32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned char* bufp0 = base + (size_t)(2 * warp) * BUF_STRIDE;
+    const uint32_t buf0 = base_u32 + (2 * warp) * BUF_STRIDE;
+    const uint32_t bar0 = base_u32 + kAdj6Warps * 2 * BUF_STRIDE + 16 * warp;
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int64_t warp_global = (int64_t)blockIdx.x * kAdj6Warps + warp;
+    const int64_t n_warps = (int64_t)gridDim.x * kAdj6Warps;
+    const int n_groups = (a.K + HATS - 1) / HATS;
+    const int32_t D32 = (int32_t)a.D;
+    // rays outside the arm: zero rows (no copies)
+    if (a.seg.total < a.seg_rows_all) {
+        for (int64_t e = warp_global; e < a.n_tasks; e += n_warps)
+            if (seg_out_row(a.seg, a.ray_row[e]) < 0) {
+                float* zo = a.zhat + e * a.K * a.Bc;
+                for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = 0.0f;
+            }
+    }
+    // an item's raw table fields are loaded one item before the item is
+    // issued and its copy coordinates derived only then, so the loads'
+    // latency passes under the previous item's contraction
+    struct Raw {
+        int64_t e;
+        int g, ray_row, K0, F0;
+    };
+    struct Item {
+        int64_t e;
+        int g, row_out, R4, sbase;  // R4: first copied row; sbase: item frame offset in it
+        int32_t r0;                 // weight phase of the ray
+    };
+    const bool all_rows = a.seg.total == a.seg_rows_all;
+    auto load = [&](int64_t e, int g, Raw& r) {
+        r.e = e;
+        r.g = g;
+        r.ray_row = a.ray_row[e];
+        r.K0 = a.K0[e];
+        r.F0 = a.F0[e];
+    };
+    // the item after (e, g): next group, else the next ray in the arm
+    auto next = [&](int64_t e, int g, const Raw& prev, Raw& r) -> bool {
+        if (g + 1 < n_groups) {
+            r = prev;
+            r.g = g + 1;
+            return true;
+        }
+        for (e += n_warps; e < a.n_tasks; e += n_warps)
+            if (all_rows || seg_out_row(a.seg, a.ray_row[e]) >= 0) {
+                load(e, 0, r);
+                return true;
+            }
+        return false;
+    };
+    auto derive = [&](const Raw& r, Item& it) {
+        it.e = r.e;
+        it.g = r.g;
+        it.row_out = seg_out_row(a.seg, r.ray_row);
+        const int64_t U0 = (int64_t)r.K0 * kFracOne + (int64_t)r.F0;
+        const int64_t c0 = (U0 * P) >> kFracBits;
+        const int fbase = (int)(c0 + 1 - P);
+        it.r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
+        const int kg0 = HATS * r.g;
+        const int f_lo = fbase - P * (kg0 + HATS - 1);  // first frame of the item's last hat
+        it.R4 = f_lo >> LGF;                             // floor division (f_lo may be < 0)
+        it.sbase = fbase - P * kg0 - it.R4 * F;          // >= 0
+    };
+    const uint64_t tmap = reinterpret_cast<uint64_t>(&ymap);
+    auto issue = [&](const Item& it, int b) {
+        if (lane != 0) return;
+        const uint32_t bar = bar0 + 8u * b, dst = buf0 + (uint32_t)b * BUF_STRIDE;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(BOX_BYTES)
+                     : "memory");
+        // x = 0 (whole 128-byte rows); rows before 0 or past the frames are zero-filled
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+            "l"(tmap), "r"(0), "r"(it.R4), "r"(it.row_out), "r"(bar)
+            : "memory");
+    };
+    Raw rcur;
+    bool have = false;
+    for (int64_t e = warp_global; e < a.n_tasks && !have; e += n_warps)
+        if (all_rows || seg_out_row(a.seg, a.ray_row[e]) >= 0) {
+            load(e, 0, rcur);
+            have = true;
+        }
+    if (!have) return;
+    Item cur;
+    derive(rcur, cur);
+    issue(cur, 0);
+    Raw rnxt;
+    bool have_nxt = next(rcur.e, rcur.g, rcur, rnxt);
+    for (uint32_t t = 0; have; ++t) {
+        Item nxt;
+        if (have_nxt) {
+            derive(rnxt, nxt);
+            issue(nxt, (t + 1) & 1);
+        }
+        Raw rnn;
+        const bool have_nn = have_nxt && next(rnxt.e, rnxt.g, rnxt, rnn);
+        if (!mbar_wait(bar0 + 8u * (t & 1), (t >> 1) & 1)) {
+            if (lane == 0) atomicOr(status, 1);
+            if (have_nxt) mbar_wait(bar0 + 8u * ((t + 1) & 1), ((t + 1) >> 1) & 1);
+            return;
+        }
+        float wt[2 * P];
+#pragma unroll
+        for (int j = 0; j < 2 * P; ++j)
+            wt[j] = 1.0f - (float)abs(cur.r0 - j * D32) * (1.0f / (float)kFracOne);
+        // lane's first frame offset in the buffer for hat h: sbase - P (lane + 32 h)
+        const int s0 = cur.sbase - P * lane;
+        const int M = s0 & (F - 1);
+        const int rs0 = s0 >> LGF;
+        const unsigned char* buf = bufp0 + (t & 1) * BUF_STRIDE;
+        float acc[HG][BC];
+        if constexpr (F == 1) {
+            adj6_contract<BC, P, HG, 0>(buf, rs0, wt, acc);
+        } else if constexpr (F == 2) {
+            if (M == 0) adj6_contract<BC, P, HG, 0>(buf, rs0, wt, acc);
+            else adj6_contract<BC, P, HG, 1>(buf, rs0, wt, acc);
+        } else if constexpr (F == 4) {
+            switch (M) {
+                case 0: adj6_contract<BC, P, HG, 0>(buf, rs0, wt, acc); break;
+                case 1: adj6_contract<BC, P, HG, 1>(buf, rs0, wt, acc); break;
+                case 2: adj6_contract<BC, P, HG, 2>(buf, rs0, wt, acc); break;
+                default: adj6_contract<BC, P, HG, 3>(buf, rs0, wt, acc); break;
+            }
+        } else {
+            switch (M) {
+                case 0: adj6_contract<BC, P, HG, 0>(buf, rs0, wt, acc); break;
+                case 1: adj6_contract<BC, P, HG, 1>(buf, rs0, wt, acc); break;
+                case 2: adj6_contract<BC, P, HG, 2>(buf, rs0, wt, acc); break;
+                case 3: adj6_contract<BC, P, HG, 3>(buf, rs0, wt, acc); break;
+                case 4: adj6_contract<BC, P, HG, 4>(buf, rs0, wt, acc); break;
+                case 5: adj6_contract<BC, P, HG, 5>(buf, rs0, wt, acc); break;
+                case 6: adj6_contract<BC, P, HG, 6>(buf, rs0, wt, acc); break;
+                default: adj6_contract<BC, P, HG, 7>(buf, rs0, wt, acc); break;
+            }
+        }
+#pragma unroll
+        for (int h = 0; h < HG; ++h) {
+            const int k = HATS * cur.g + lane + 32 * h;
+            if (k < a.K) {
+                float4* zo = reinterpret_cast<float4*>(a.zhat + (cur.e * a.K + k) * BC);
+#pragma unroll
+                for (int q = 0; q < BC / 4; ++q)
+                    zo[q] = make_float4(acc[h][4 * q], acc[h][4 * q + 1], acc[h][4 * q + 2],
+                                        acc[h][4 * q + 3]);
+            }
+        }
+        __syncwarp();  // buffer t & 1 is free for the copy issued at step t + 1
+        cur = nxt;
+        have = have_nxt;
+        rnxt = rnn;
+        have_nxt = have_nn;
+    }
+}
+
 // Forward with the four corner slabs of x staged by the tensor memory
 // accelerator.  Same tasks, hat windows, interpolation and accumulation order
 // as fwd3_kernel<float, BC, FPL> (hence the same bits); what changes is how
@@ -1634,6 +1897,19 @@ static int sm_count() {
     return sms;
 }
 
+// one wave of resident CTAs of `kernel` for a persistent grid-stride loop
+// (fewer when the tasks need fewer)
+template <typename Kern>
+static int resident_grid(Kern kernel, int threads, size_t smem, int64_t n_tasks, int warps) {
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int64_t want = (n_tasks + warps - 1) / warps;
+    const int64_t cap = (int64_t)sm_count() * per_sm;
+    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
 // 16-byte vector access is used only when the batch stride and both buffers
 // allow it
 template <typename T>
@@ -1698,7 +1974,9 @@ static cudaError_t launch_fwd3_bc(ApplyArgs<T> a, cudaStream_t st) {
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (err != cudaSuccess) return err;
     }
-    fwd3_kernel<T, BC, FPL, SU><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, smem, st>>>(a);
+    const int grid =
+        resident_grid(fwd3_kernel<T, BC, FPL, SU>, kWarpsPerBlock * 32, smem, a.n_tasks, kWarpsPerBlock);
+    fwd3_kernel<T, BC, FPL, SU><<<grid, kWarpsPerBlock * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
@@ -1768,6 +2046,53 @@ static cudaError_t launch_adj5(ApplyArgs<float> t, int* status, cudaStream_t st)
         const int64_t cap = (int64_t)sm_count() * per_sm;
         const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
         adj_time5_kernel<BC, P><<<grid, kAdj5Warps * 32, smem, st>>>(m, t, status);
+        return cudaGetLastError();
+    }
+}
+
+// whole-item TMA time phase; cudaErrorNotSupported unless the batch is one
+// chunk of B = BC in {4, 8, 16, 32} whose 128-byte row holds F = 32 / BC
+// frames with F dividing both P and the frame count
+// (BC, P) pairs of adj_time6_kernel: whole frames per row dividing P, box <= 256 rows
+template <int BC, int P>
+constexpr bool adj6_shape_ok() {
+    if (BC < 4 || BC > 32 || P % (32 / (BC < 4 ? 4 : BC)) != 0) return false;
+    const int F = 32 / BC, HG = BC <= 8 ? 2 : 1;
+    return ((32 * HG + 1) * P + 2 * (F - 1)) / F <= 256;
+}
+
+template <int BC, int P>
+static cudaError_t launch_adj6(ApplyArgs<float> t, int* status, cudaStream_t st) {
+    if constexpr (!adj6_shape_ok<BC, P>()) {
+        return cudaErrorNotSupported;
+    } else {
+        constexpr int HG = BC <= 8 ? 2 : 1;
+        constexpr int F = T6Box<BC, P, HG>::kF;
+        constexpr int ROWS = T6Box<BC, P, HG>::kRows;
+        static_assert(ROWS <= 256, "TMA box rows");
+        if (!vec_ok(t) || t.Bc != BC || t.B != BC || (t.Tn % F) != 0 || !status)
+            return cudaErrorNotSupported;
+        const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+        if (!enc || t.seg.total <= 0) return cudaErrorNotSupported;
+        CUtensorMap m;
+        // (32 floats = one 128-byte row, rows of a data row's frames, data rows)
+        cuuint64_t dims[3] = {32, (cuuint64_t)(t.Tn / F), (cuuint64_t)t.seg.total};
+        cuuint64_t strides[2] = {128, (cuuint64_t)(t.Tn / F) * 128};
+        cuuint32_t box[3] = {32, (cuuint32_t)ROWS, 1};
+        cuuint32_t es[3] = {1, 1, 1};
+        if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(t.in), dims, strides, box,
+                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorNotSupported;
+        t.n_tasks = t.n_rays_total;
+        const size_t smem =
+            1024 + (size_t)kAdj6Warps * 2 * T6Box<BC, P, HG>::kStride + (size_t)kAdj6Warps * 16;
+        cudaError_t e = cudaFuncSetAttribute(adj_time6_kernel<BC, P, HG>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid =
+            resident_grid(adj_time6_kernel<BC, P, HG>, kAdj6Warps * 32, smem, t.n_tasks, kAdj6Warps);
+        adj_time6_kernel<BC, P, HG><<<grid, kAdj6Warps * 32, smem, st>>>(m, t, status);
         return cudaGetLastError();
     }
 }
@@ -1935,8 +2260,14 @@ static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStr
         if (!periodic && a.seg.total > 0 && P > 0) {
             periodic = true;
             e = cudaErrorNotSupported;
-            if (v.time == 3 && (P == 2 || P == 4))
+            if (v.time == 4)
+                e = P == 2 ? launch_adj6<BC, 2>(a, a.status, st)
+                           : (P == 4 ? launch_adj6<BC, 4>(a, a.status, st)
+                                     : launch_adj6<BC, 8>(a, a.status, st));
+            if (e == cudaErrorNotSupported && v.time >= 3 && (P == 2 || P == 4)) {
+                cudaGetLastError();
                 e = P == 2 ? launch_adj5<BC, 2>(a, a.status, st) : launch_adj5<BC, 4>(a, a.status, st);
+            }
             if (e == cudaErrorNotSupported) {
                 cudaGetLastError();  // clear the "not supported" marker, if any
                 e = P == 2 ? launch_adj4<BC, 2>(a, st)

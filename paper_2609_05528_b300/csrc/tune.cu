@@ -77,7 +77,7 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
     }
     const int bc = v->fwd_bc;
     if (v->fwd_kernel < 1 || v->fwd_kernel > 3 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
-        v->fwd_half < 0 || v->fwd_half > 1 || v->time_kernel < 1 || v->time_kernel > 3 ||
+        v->fwd_half < 0 || v->fwd_half > 1 || v->time_kernel < 1 || v->time_kernel > 4 ||
         v->space_kernel < 1 || v->space_kernel > 3) {
         set_error("invalid variant (fwd %d bc %d half %d time %d space %d)", v->fwd_kernel, bc,
                   v->fwd_half, v->time_kernel, v->space_kernel);
@@ -214,7 +214,11 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     const int P = periodic ? (int)(kFracOne / op->frame_D) : 0;
     const bool tma_ok = (P == 2 || P == 4) && (B == 4 || B == 8 || B == 16 || B == 32) &&
                         (op->time.n_frames % (32 / B)) == 0;
-    for (int tk = 1; tk <= (periodic ? (tma_ok ? 3 : 2) : 1); ++tk)
+    // the whole-item TMA phase also needs the frames of a 128-byte row to divide P
+    const bool tma6_ok = P > 0 && (B == 4 || B == 8 || B == 16 || B == 32) && P % (32 / B) == 0 &&
+                         (op->time.n_frames % (32 / B)) == 0 && !(B == 32 && P == 8);
+    const int tk_max = !periodic ? 1 : (tma6_ok ? 4 : (tma_ok ? 3 : 2));
+    for (int tk = 1; tk <= tk_max; ++tk)
         for (int sk = 1; sk <= 3; ++sk) {
             ApplyVariant v = best;
             v.time = (int8_t)tk;

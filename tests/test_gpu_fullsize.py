@@ -73,6 +73,14 @@ def test_kerr256_every_output(k256):
     g = op.apply_AT(torch.from_numpy(yd.astype(np.float32)).cuda()).cpu().numpy().astype(np.float64)
     assert _rel(g, gref) < 1e-5
     assert np.max(np.abs(g - gref)) <= 1e-5 * np.max(np.abs(gref))
+    # the benchmark's launch configuration: variants autotuned for batch 8,
+    # the same bits as the default rule
+    yt = torch.from_numpy(yd.astype(np.float32)).cuda()
+    xt = torch.from_numpy(x.astype(np.float32)).cuda()
+    y_rule, g_rule = op.apply_A(xt), op.apply_AT(yt)
+    op.autotune(8)
+    assert torch.equal(op.apply_A(xt), y_rule) and torch.equal(op.apply_AT(yt), g_rule)
+    assert op.status(clear=True) == 0
     # direct-only arm on the same buffers
     d = tab.select((0,))
     y1 = op.apply_A(torch.from_numpy(x.astype(np.float32)).cuda(), arm_mask=1).cpu().numpy()
