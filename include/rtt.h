@@ -497,7 +497,8 @@ rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_d
  */
 typedef struct {
     int32_t batch;
-    int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat, 3 staged with TMA corner copies */
+    int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat, 3 staged with TMA corner copies,
+                             4 staged with pipelined bulk corner copies */
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
     int32_t fwd_staging;  /* staged forward: x items in flight per lane */
@@ -517,7 +518,8 @@ rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream, rtt_tu
 typedef struct {
     int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat (periodic cadences; else staged),
                              3 staged with TMA corner copies (batch a multiple of 4;
-                             else staged) */
+                             else staged), 4 staged with bulk corner copies pipelined
+                             two rays ahead (batch 4 or 8 as one chunk; else staged) */
     int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32 */
     int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
     int32_t time_kernel;  /* 1 general, 2 periodic weights, 3 periodic + TMA, 4 periodic

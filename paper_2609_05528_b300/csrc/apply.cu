@@ -1479,6 +1479,428 @@ fwd5_kernel(const __grid_constant__ CUtensorMap xmap, const ApplyArgs<float> a, 
     }
 }
 
+// Staged forward specialised for a periodic cadence (a frame step is 1 / P of
+// a hat step, P in {2, 4, 8}) with the whole batch in one chunk (B = BC in
+// {4, 8}): the tasks, windows, values and accumulation order of
+// fwd3_kernel<float, BC, FPL> (hence the same bits), with
+//  * the hat window and each lane's hat index and fraction in exact 32-bit
+//    arithmetic: a chunk starts on a whole hat step, so U(f) = U0 - f D splits
+//    into K0 - f_begin / P and the 24-bit remainder F0 - (f - f_begin) D;
+//  * the window size fixed at compile time (FC / P + 3 hats), so every staging
+//    load, staged store and hat read is a base address plus an immediate;
+//  * range tests only where a window or a chunk reaches past the hats or the
+//    frames (a uniform branch per ray or task).
+template <int BC, int FPL, int P>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
+fwd7_kernel(const ApplyArgs<float> a) {
+    static_assert(BC == 4 || BC == 8, "16-byte batch records, one chunk");
+    constexpr int Q = BC / 4;
+    constexpr int FC = 32 * FPL;
+    static_assert(FC % P == 0, "chunks start on whole hat steps");
+    constexpr int ZW = FC / P + 3;         // hats staged per task window
+    constexpr int NU = (ZW * Q + 31) / 32;  // staging items per lane
+    constexpr int HS = 32 / P;             // hat steps per 32 frames
+    constexpr int32_t D = kFracOne / P;
+    __shared__ __align__(16) float4 zs_all[kWarpsPerBlock][ZW * Q];
+    float4* zsv = zs_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const int64_t KB = (int64_t)a.K * BC;  // floats per node row of x
+    // this lane's staging items o = lane + 32 u: hat lane / Q + (32 / Q) u, record lane % Q
+    const int kk0 = lane / Q, q0 = lane % Q;
+    const int32_t lane_off = -lane * D;  // - lane D, the lane's offset inside a hat step pattern
+    for (TaskWalk tw(warp_global, n_warps, 1, a.n_fchunk); tw.r < a.seg.total; tw.next()) {
+        const int row_out = tw.r;
+        const int row = seg_in_row(a.seg, row_out);
+        const int f_begin = tw.f * FC;
+        const bool full = f_begin + FC <= a.Tn;  // every frame of the chunk exists
+        const int hb = f_begin / P;               // whole hat steps before the chunk
+        float acc[FPL][BC];
+#pragma unroll
+        for (int j = 0; j < FPL; ++j)
+#pragma unroll
+            for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+        const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
+        for (int e = e_begin; e < e_end; ++e) {
+            const int K0 = a.K0[e], F0 = a.F0[e];
+            const float4 wv = a.W[e];
+            const int n00 = a.node00[e], n01 = a.node01[e];
+            // window [k_lo, k_lo + nwin): k_top = K0 - hb, k_lo = K0 - hb - FC / P + ((F0 + D) >> 24)
+            const int k_top = K0 - hb;
+            const int k_lo = k_top - FC / P + ((F0 + D) >> kFracBits);
+            const int nwin = k_top + 2 - k_lo;
+            const float* b00 = a.in + (int64_t)n00 * KB + (int64_t)(k_lo + kk0) * BC + 4 * q0;
+            const float* b01 = a.in + (int64_t)n01 * KB + (int64_t)(k_lo + kk0) * BC + 4 * q0;
+            const int64_t rstep = (int64_t)a.n_phi * KB;  // the radial neighbour's row
+            float4 v[NU][4];
+            if (k_lo >= 0 && k_lo + ZW <= a.K) {
+#pragma unroll
+                for (int u = 0; u < NU; ++u) {
+                    if (u < NU - 1 || lane + 32 * u < ZW * Q) {
+                        const int du = (32 / Q) * u * BC;
+                        v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
+                        v[u][1] = __ldg(reinterpret_cast<const float4*>(b00 + rstep + du));
+                        v[u][2] = __ldg(reinterpret_cast<const float4*>(b01 + du));
+                        v[u][3] = __ldg(reinterpret_cast<const float4*>(b01 + rstep + du));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < NU; ++u) {
+                    const int k = k_lo + kk0 + (32 / Q) * u;
+                    const bool ok = lane + 32 * u < ZW * Q && k >= 0 && k < a.K;
+                    const int du = (32 / Q) * u * BC;
+                    v[u][0] = v[u][1] = v[u][2] = v[u][3] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ok) {
+                        v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
+                        v[u][1] = __ldg(reinterpret_cast<const float4*>(b00 + rstep + du));
+                        v[u][2] = __ldg(reinterpret_cast<const float4*>(b01 + du));
+                        v[u][3] = __ldg(reinterpret_cast<const float4*>(b01 + rstep + du));
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                if (u < NU - 1 || lane + 32 * u < ZW * Q) {
+                    float2 r = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v[u][0].x, v[u][0].y));
+                    r = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v[u][1].x, v[u][1].y), r);
+                    r = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v[u][2].x, v[u][2].y), r);
+                    r = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v[u][3].x, v[u][3].y), r);
+                    float2 t = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v[u][0].z, v[u][0].w));
+                    t = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v[u][1].z, v[u][1].w), t);
+                    t = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v[u][2].z, v[u][2].w), t);
+                    t = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v[u][3].z, v[u][3].w), t);
+                    zsv[lane + 32 * u] = make_float4(r.x, r.y, t.x, t.y);
+                }
+            }
+            (void)nwin;
+            __syncwarp();
+            // lane's frames f_begin + lane + 32 j: remainder F0 - lane D (one value
+            // per lane: 32 frames are HS whole hat steps), hat index k_top + floor
+            const int32_t rem = F0 + lane_off;
+            const int k00 = k_top + (rem >> kFracBits);
+            const float fr = (float)(rem & kFracMask) * (1.0f / (float)kFracOne);
+            const float g = 1.0f - fr;
+            const float2 g2 = make_float2(g, g), f2 = make_float2(fr, fr);
+            const float4* z0 = zsv + (k00 - k_lo) * Q;
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) {
+                if (full || f_begin + lane + 32 * j < a.Tn) {
+#pragma unroll
+                    for (int qq = 0; qq < Q; ++qq) {
+                        const float4 p0 = z0[qq - j * HS * Q];
+                        const float4 p1 = z0[Q + qq - j * HS * Q];
+                        float2 lo = make_float2(acc[j][4 * qq], acc[j][4 * qq + 1]);
+                        float2 hi = make_float2(acc[j][4 * qq + 2], acc[j][4 * qq + 3]);
+                        lo = __ffma2_rn(g2, make_float2(p0.x, p0.y), lo);
+                        lo = __ffma2_rn(f2, make_float2(p1.x, p1.y), lo);
+                        hi = __ffma2_rn(g2, make_float2(p0.z, p0.w), hi);
+                        hi = __ffma2_rn(f2, make_float2(p1.z, p1.w), hi);
+                        acc[j][4 * qq] = lo.x;
+                        acc[j][4 * qq + 1] = lo.y;
+                        acc[j][4 * qq + 2] = hi.x;
+                        acc[j][4 * qq + 3] = hi.y;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+#pragma unroll
+        for (int j = 0; j < FPL; ++j) {
+            const int f = f_begin + lane + 32 * j;
+            if (full || f < a.Tn) {
+                float4* yo = reinterpret_cast<float4*>(a.out + ((int64_t)row_out * a.Tn + f) * BC);
+#pragma unroll
+                for (int qq = 0; qq < Q; ++qq)
+                    yo[qq] = make_float4(acc[j][4 * qq], acc[j][4 * qq + 1], acc[j][4 * qq + 2],
+                                         acc[j][4 * qq + 3]);
+            }
+        }
+    }
+}
+
+// Forward with the corner slabs of x fetched by bulk asynchronous copies,
+// pipelined over the warp's stream of (task, ray) items.  Tasks, hat windows,
+// interpolation and accumulation order are those of fwd3_kernel<float, BC,
+// FPL> (hence the same bits).  Per item, the in-range hats of the window are
+// one contiguous run of each corner node's x row (the whole batch is one
+// chunk), copied into a 3-stage ring of shared-memory slabs; hats outside
+// [0, K) are not copied and interpolate to zero.  An item's task is decided
+// four items ahead (row pointers), its table fields are loaded three ahead,
+// its copies are issued two ahead together with a stage header holding what
+// the contraction needs, so neither the table loads nor the copies wait in
+// line with the arithmetic, and only the three items not yet issued occupy
+// registers.  Waits are bounded as in adj_time5_kernel.
+constexpr int kFwd6Warps = 4;
+constexpr int kFwd6Stages = 3;
+constexpr uint32_t kFwd6Header = 64;  // stage header bytes (16-byte multiple)
+
+struct Fwd6Header {
+    int row_out, f_begin, e, e_end;  // task and ray (e == e_end: a task without rays)
+    int K0, F0, k_lo, ka;            // hat coordinate, window start, copied range [ka, kb)
+    int kb, pad0, pad1, pad2;
+    float4 w;                        // corner weights
+};
+static_assert(sizeof(Fwd6Header) == kFwd6Header, "stage header layout");
+
+template <int BC, int FPL>
+__global__ void __launch_bounds__(kFwd6Warps * 32, 4)
+fwd6_kernel(const ApplyArgs<float> a, int* status, uint32_t slab_bytes, uint32_t stage_bytes) {
+    static_assert(BC == 4 || BC == 8, "one 16-byte-aligned x row run per corner");
+    constexpr int Q = BC / 4;
+    constexpr int FC = 32 * FPL;
+    constexpr int NS = kFwd6Stages;
+    extern __shared__ __align__(16) unsigned char smem_f6[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t warp_bytes = NS * stage_bytes + 16 * ((8 * NS + 15) / 16);
+    unsigned char* wbase = smem_f6 + (size_t)warp * warp_bytes;
+    const uint32_t wbase_u32 = smem_u32(wbase);
+    const uint32_t bar0 = wbase_u32 + (uint32_t)NS * stage_bytes;  // NS mbarriers, 8 bytes each
+    if (lane == 0) {
+#pragma unroll
+        for (int st = 0; st < NS; ++st)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8 * st) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int64_t warp_global = (int64_t)blockIdx.x * kFwd6Warps + warp;
+    const int64_t n_warps = (int64_t)gridDim.x * kFwd6Warps;
+    struct It {
+        int row_out, f_begin, e, e_end;  // task and ray
+        int n00, n01, K0, F0;            // table fields of ray e
+        float4 w;
+    };
+    TaskWalk tw(warp_global, n_warps, 1, a.n_fchunk);
+    auto task_first = [&](It& it) -> bool {
+        if (tw.r >= a.seg.total) return false;
+        const int row = seg_in_row(a.seg, tw.r);
+        it.row_out = tw.r;
+        it.f_begin = tw.f * FC;
+        it.e = a.row_ptr[row];
+        it.e_end = a.row_ptr[row + 1];
+        return true;
+    };
+    auto decide = [&](const It& prev, It& it) -> bool {
+        if (prev.e + 1 < prev.e_end) {
+            it.row_out = prev.row_out;
+            it.f_begin = prev.f_begin;
+            it.e = prev.e + 1;
+            it.e_end = prev.e_end;
+            return true;
+        }
+        tw.next();
+        return task_first(it);
+    };
+    auto load = [&](It& it) {
+        if (it.e < it.e_end) {
+            it.n00 = a.node00[it.e];
+            it.n01 = a.node01[it.e];
+            it.K0 = a.K0[it.e];
+            it.F0 = a.F0[it.e];
+            it.w = a.W[it.e];
+        }
+    };
+    const int64_t KB = (int64_t)a.K * BC;  // floats per node row of x
+    // copies of item it into stage st, with the stage header: lane 0 writes the
+    // header and sets the expected bytes, then lane c < 4 copies corner c
+    // (nodes n00, n00 + n_phi, n01, n01 + n_phi)
+    auto issue = [&](const It& it, int st) {
+        const int f_end = min(a.Tn, it.f_begin + FC);
+        int bytes = 0, k_lo = 0, ka = 0, kb = 0;
+        if (it.e < it.e_end) {
+            const int64_t U0 = (int64_t)it.K0 * kFracOne + (int64_t)it.F0;
+            const int k_top = (int)((U0 - (int64_t)it.f_begin * a.D) >> kFracBits);
+            k_lo = (int)((U0 - (int64_t)(f_end - 1) * a.D) >> kFracBits);
+            ka = max(k_lo, 0);
+            kb = max(min(k_top + 2, a.K), ka);
+            bytes = (kb - ka) * BC * 4;
+        }
+        unsigned char* stage = wbase + (size_t)st * stage_bytes;
+        const uint32_t bar = bar0 + 8u * st;
+        if (lane == 0) {
+            Fwd6Header* h = reinterpret_cast<Fwd6Header*>(stage);
+            reinterpret_cast<int4*>(h)[0] = make_int4(it.row_out, it.f_begin, it.e, it.e_end);
+            reinterpret_cast<int4*>(h)[1] = make_int4(it.K0, it.F0, k_lo, ka);
+            reinterpret_cast<int4*>(h)[2] = make_int4(kb, 0, 0, 0);
+            h->w = it.w;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                         "r"(4 * bytes)
+                         : "memory");
+        }
+        __syncwarp();
+        if (lane < 4 && bytes > 0) {
+            const int node = (lane < 2 ? it.n00 : it.n01) + (lane & 1) * a.n_phi;
+            const float* src = a.in + (int64_t)node * KB + (int64_t)ka * BC;
+            const uint32_t dst = smem_u32(stage) + kFwd6Header + (uint32_t)lane * slab_bytes +
+                                 (uint32_t)((ka - k_lo) * BC * 4);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes"
+                " [%0], [%1], %2, [%3];" ::"r"(dst),
+                "l"(src), "r"(bytes), "r"(bar)
+                : "memory");
+        }
+    };
+    float acc[FPL][BC];
+#pragma unroll
+    for (int j = 0; j < FPL; ++j)
+#pragma unroll
+        for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+    // contraction of the item in stage st; false when the wait timed out
+    auto compute = [&](int st, uint32_t parity) -> bool {
+        if (!mbar_wait(bar0 + 8u * st, parity)) return false;
+        unsigned char* stage = wbase + (size_t)st * stage_bytes;
+        const Fwd6Header* hp = reinterpret_cast<const Fwd6Header*>(stage);
+        const int4 h0 = reinterpret_cast<const int4*>(hp)[0];
+        const int4 h1 = reinterpret_cast<const int4*>(hp)[1];
+        const int kb = reinterpret_cast<const int4*>(hp)[2].x;
+        const int row_out = h0.x, f_begin = h0.y, e = h0.z, e_end = h0.w;
+        const int k_lo = h1.z, ka = h1.w;
+        const int f_end = min(a.Tn, f_begin + FC);
+        if (e < e_end) {
+            // z[k][.] = sum_c W_c x[node_c][k][.] in place of slab 0 (zero outside [ka, kb))
+            float4* s0 = reinterpret_cast<float4*>(stage + kFwd6Header);
+            const int sv = (int)(slab_bytes / 16);
+            const int64_t U0 = (int64_t)h1.x * kFracOne + (int64_t)h1.y;
+            const int k_top = (int)((U0 - (int64_t)f_begin * a.D) >> kFracBits);
+            const int nwin = k_top + 2 - k_lo;
+            const int oa = (ka - k_lo) * Q, ob = (kb - k_lo) * Q;
+            const float4 wv = hp->w;
+            for (int base = 0; base < nwin * Q; base += 96) {
+                float4 zz[3];
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    const int o = base + lane + 32 * u;
+                    zz[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (o >= oa && o < ob) {
+                        const float4 v0 = s0[o], v1 = s0[sv + o], v2 = s0[2 * sv + o], v3 = s0[3 * sv + o];
+                        float2 r = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v0.x, v0.y));
+                        r = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v1.x, v1.y), r);
+                        r = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v2.x, v2.y), r);
+                        r = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v3.x, v3.y), r);
+                        float2 q = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v0.z, v0.w));
+                        q = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v1.z, v1.w), q);
+                        q = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v2.z, v2.w), q);
+                        q = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v3.z, v3.w), q);
+                        zz[u] = make_float4(r.x, r.y, q.x, q.y);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 3; ++u) {
+                    const int o = base + lane + 32 * u;
+                    if (o < nwin * Q) s0[o] = zz[u];
+                }
+            }
+            __syncwarp();
+            const float* zs = reinterpret_cast<const float*>(s0);
+            auto add_frame = [&](int j, int k0, float fr) {
+                const float g = 1.0f - fr;
+                const float* z0 = zs + (k0 - k_lo) * BC;
+                const float2 g2 = make_float2(g, g), f2 = make_float2(fr, fr);
+#pragma unroll
+                for (int q = 0; q < Q; ++q) {
+                    const float4 p0 = reinterpret_cast<const float4*>(z0)[q];
+                    const float4 p1 = reinterpret_cast<const float4*>(z0 + BC)[q];
+                    float2 lo = make_float2(acc[j][4 * q], acc[j][4 * q + 1]);
+                    float2 hi = make_float2(acc[j][4 * q + 2], acc[j][4 * q + 3]);
+                    lo = __ffma2_rn(g2, make_float2(p0.x, p0.y), lo);
+                    lo = __ffma2_rn(f2, make_float2(p1.x, p1.y), lo);
+                    hi = __ffma2_rn(g2, make_float2(p0.z, p0.w), hi);
+                    hi = __ffma2_rn(f2, make_float2(p1.z, p1.w), hi);
+                    acc[j][4 * q] = lo.x;
+                    acc[j][4 * q + 1] = lo.y;
+                    acc[j][4 * q + 2] = hi.x;
+                    acc[j][4 * q + 3] = hi.y;
+                }
+            };
+            const int64_t U1 = U0 - (int64_t)(f_begin + lane) * a.D;
+            if (a.hs32 > 0) {
+                const int k00 = (int)(U1 >> kFracBits);
+                const float fr0 = (float)(int32_t)(U1 & kFracMask) * (1.0f / (float)kFracOne);
+#pragma unroll
+                for (int j = 0; j < FPL; ++j)
+                    if (f_begin + lane + 32 * j < f_end) add_frame(j, k00 - j * a.hs32, fr0);
+            } else {
+                int64_t U = U1;
+                const int64_t dU = (int64_t)32 * a.D;
+#pragma unroll
+                for (int j = 0; j < FPL; ++j) {
+                    if (f_begin + lane + 32 * j < f_end)
+                        add_frame(j, (int)(U >> kFracBits),
+                                  (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne));
+                    U -= dU;
+                }
+            }
+        }
+        // z and the header were read or written by the generic proxy: order
+        // those accesses before the asynchronous copies that refill the stage
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();  // the stage is free for the copies issued at the next step
+        if (e + 1 >= e_end) {  // last ray of the task: write y
+#pragma unroll
+            for (int j = 0; j < FPL; ++j) {
+                const int f = f_begin + lane + 32 * j;
+                if (f < f_end) {
+                    float4* yo = reinterpret_cast<float4*>(a.out + ((int64_t)row_out * a.Tn + f) * BC);
+#pragma unroll
+                    for (int q = 0; q < Q; ++q)
+                        yo[q] = make_float4(acc[j][4 * q], acc[j][4 * q + 1], acc[j][4 * q + 2],
+                                            acc[j][4 * q + 3]);
+                }
+#pragma unroll
+                for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+            }
+        }
+        return true;
+    };
+    // prologue: items 0 and 1 issued to stages 0 and 1, item 2 loaded, item 3 decided
+    It r_[3];
+    bool h_[3];
+    bool have0, have1;
+    {
+        It i0, i1;
+        have0 = task_first(i0);
+        if (!have0) return;
+        load(i0);
+        have1 = decide(i0, i1);
+        if (have1) load(i1);
+        issue(i0, 0);
+        if (have1) issue(i1, 1);
+        h_[0] = have1 && decide(i1, r_[0]);  // item 2 (issued at step 0)
+        if (h_[0]) load(r_[0]);
+        h_[1] = h_[0] && decide(r_[0], r_[1]);  // item 3
+    }
+    // item t computes from stage t % 3; at step t the register slots hold items
+    // t + 2 (issued now into stage (t + 2) % 3), t + 3 (loaded now), t + 4
+    // (decided now); have_c / have_d: items t + 1 and t are in flight
+    bool have_d = have0, have_c = have1;
+    uint32_t ph = 0;
+    auto step = [&](const int st, It& B, bool& hB, It& A, bool& hA, It& N, bool& hN) -> bool {
+        if (!have_d) return false;
+        const int st2 = (st + 2) % NS;
+        if (hB) issue(B, st2);
+        if (hA) load(A);
+        hN = hA && decide(A, N);
+        if (!compute(st, ph)) {
+            if (lane == 0) atomicOr(status, 1);
+            const int st1 = (st + 1) % NS;
+            if (have_c) mbar_wait(bar0 + 8u * st1, st1 > st ? ph : ph ^ 1u);
+            if (hB) mbar_wait(bar0 + 8u * st2, st2 > st ? ph : ph ^ 1u);
+            return false;
+        }
+        have_d = have_c;
+        have_c = hB;
+        if (st == NS - 1) ph ^= 1u;
+        return true;
+    };
+    for (;;) {
+        if (!step(0, r_[0], h_[0], r_[1], h_[1], r_[2], h_[2])) break;
+        if (!step(1, r_[1], h_[1], r_[2], h_[2], r_[0], h_[0])) break;
+        if (!step(2, r_[2], h_[2], r_[0], h_[0], r_[1], h_[1])) break;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Fused forward + adjoint phase 1 (FP32, a frame step 1/P of a hat step, the
 // whole batch of B = BC in {4, 8} entries in one chunk).  y = scale A x is
@@ -2138,14 +2560,67 @@ static cudaError_t launch_fwd5(ApplyArgs<float> a, cudaStream_t st) {
     }
 }
 
+// pipelined bulk-copy forward; cudaErrorNotSupported unless the whole batch
+// (B = BC in {4, 8}) is one chunk of 16-byte-aligned records
+template <int BC, int FPL>
+static cudaError_t launch_fwd6(ApplyArgs<float> a, cudaStream_t st) {
+    if (!vec_ok(a) || a.B != BC || !a.status) return cudaErrorNotSupported;
+    a.FC = 32 * FPL;
+    a.zwin = (int)ceil((a.FC - 1) * a.delta) + 3;
+    a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
+    a.n_bchunk = 1;
+    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    // per warp: 3 stages (64-byte header, 4 corner slabs of zwin hats), then 3 mbarriers
+    const uint32_t slab = ((uint32_t)a.zwin * BC * 4 + 15) & ~15u;
+    const uint32_t stage = kFwd6Header + 4 * slab;
+    const uint32_t warp_bytes = (uint32_t)kFwd6Stages * stage + 16 * ((8 * kFwd6Stages + 15) / 16);
+    const size_t smem = (size_t)kFwd6Warps * warp_bytes;
+    if (smem > 227 * 1024) return cudaErrorNotSupported;
+    cudaError_t e = cudaFuncSetAttribute(fwd6_kernel<BC, FPL>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = resident_grid(fwd6_kernel<BC, FPL>, kFwd6Warps * 32, smem, a.n_tasks, kFwd6Warps);
+    fwd6_kernel<BC, FPL><<<grid, kFwd6Warps * 32, smem, st>>>(a, a.status, slab, stage);
+    return cudaGetLastError();
+}
+
+// periodic one-chunk staged forward; cudaErrorNotSupported unless the
+// cadence is P in {2, 4, 8} frames per hat and the whole batch (B = BC in
+// {4, 8}) is one chunk of 16-byte-aligned records
+template <int BC, int FPL>
+static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st) {
+    const int P = frames_per_hat(a.D);
+    if (!vec_ok(a) || a.B != BC || P == 0 || (32 * FPL) % P != 0) return cudaErrorNotSupported;
+    a.FC = 32 * FPL;
+    a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
+    a.n_bchunk = 1;
+    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    auto go = [&](auto kern) {
+        const int grid = resident_grid(kern, kWarpsPerBlock * 32, 0, a.n_tasks, kWarpsPerBlock);
+        kern<<<grid, kWarpsPerBlock * 32, 0, st>>>(a);
+        return cudaGetLastError();
+    };
+    switch (P) {
+        case 2: return go(fwd7_kernel<BC, FPL, 2>);
+        case 4: return go(fwd7_kernel<BC, FPL, 4>);
+        default: return go(fwd7_kernel<BC, FPL, 8>);
+    }
+}
+
 ApplyVariant variant_for(const rtt_op_s* op, int batch) {
     for (int i = 0; i < op->n_tuned; ++i)
         if (op->tuned_batch[i] == batch) return op->tuned[i];
-    ApplyVariant v;  // default rule, from the measured kerr256 / stress1024 sweeps
-    v.fwd = 1;
+    // default rule, from the kerr256 measurements: the periodic one-chunk
+    // forward, the whole-item TMA time phase and the gather with eight
+    // incidences in flight; each falls back to the next kernel down where
+    // the cadence, batch or buffers do not allow it
+    ApplyVariant v;
+    v.fwd = 5;
     v.fwd_bc = (int8_t)pick_bc(batch);
-    v.time = frames_per_hat(op->frame_D) > 0 ? 2 : 1;
-    v.space = 2;  // used when the chunk allows 16-byte access, else scalar
+    v.time = frames_per_hat(op->frame_D) > 0 ? 4 : 1;
+    v.space = 3;
     return v;
 }
 
@@ -2200,6 +2675,20 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
                 case 8: return launch_fwd4_any<8>(a, bc, st);
                 default: break;  // not a periodic cadence: staged kernel
             }
+        }
+        if (v.fwd == 5 && (bc == 4 || bc == 8)) {
+            const bool half = v.fwd_half != 0;
+            const cudaError_t e = bc == 4 ? (half ? launch_fwd7<4, 4>(a, st) : launch_fwd7<4, 8>(a, st))
+                                          : (half ? launch_fwd7<8, 2>(a, st) : launch_fwd7<8, 4>(a, st));
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();  // clear the "not supported" marker, if any
+        }
+        if (v.fwd == 4 && (bc == 4 || bc == 8)) {
+            const bool half = v.fwd_half != 0;
+            const cudaError_t e = bc == 4 ? (half ? launch_fwd6<4, 4>(a, st) : launch_fwd6<4, 8>(a, st))
+                                          : (half ? launch_fwd6<8, 2>(a, st) : launch_fwd6<8, 4>(a, st));
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();  // clear the "not supported" marker, if any
         }
         if (v.fwd == 3 && bc >= 4) {
             const bool half = v.fwd_half != 0;

@@ -38,13 +38,17 @@ rtt_status make_seg(const struct ::rtt_op_s* op, int mask, ArmSeg* s);
 // same order with the same fused multiply-adds, so the choice changes speed
 // only, never a bit of the result.
 struct ApplyVariant {
-    int8_t fwd = 0;     // forward: 1 staged z (fwd3), 2 lane-per-hat shuffles (fwd4)
+    int8_t fwd = 0;     // forward: 1 staged z (fwd3), 2 lane-per-hat shuffles (fwd4),
+                        // 3 TMA corner slabs (fwd5), 4 pipelined bulk corner copies
+                        // (fwd6), 5 periodic one-chunk staged (fwd7)
     int8_t fwd_bc = 0;  // batch entries per forward task (power of two)
     int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
     int8_t fwd_su = 2;   // staged forward: staging items in flight per lane (1, 2 or 3)
     int8_t time = 0;    // adjoint phase 1: 1 general (adj_time3), 2 periodic (adj_time4),
-                        // 3 periodic with TMA-staged frames (adj_time5)
-    int8_t space = 0;   // adjoint phase 2: 1 scalar (adj_space3), 2 16-byte (adj_space4)
+                        // 3 periodic with TMA-staged frames (adj_time5), 4 whole-item
+                        // TMA phase with zero-filled frames (adj_time6)
+    int8_t space = 0;   // adjoint phase 2: 1 scalar (adj_space3), 2 16-byte (adj_space4),
+                        // 3 16-byte with eight incidences in flight
     int8_t fused = 0;   // rtt_apply_A_AT: 1 = fused forward + time phase where possible
 };
 constexpr int kMaxTuned = 8;  // batch sizes with an autotuned variant per operator

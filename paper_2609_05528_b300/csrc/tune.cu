@@ -76,7 +76,7 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
         return RTT_OK;
     }
     const int bc = v->fwd_bc;
-    if (v->fwd_kernel < 1 || v->fwd_kernel > 3 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
+    if (v->fwd_kernel < 1 || v->fwd_kernel > 5 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
         v->fwd_half < 0 || v->fwd_half > 1 || v->time_kernel < 1 || v->time_kernel > 4 ||
         v->space_kernel < 1 || v->space_kernel > 3) {
         set_error("invalid variant (fwd %d bc %d half %d time %d space %d)", v->fwd_kernel, bc,
@@ -183,7 +183,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     const float fwd_rule = time_it(rule, false);
     float fwd_best = fwd_rule;
     const bool x_vec = (B % 4) == 0;  // 16-byte batch records: TMA forward possible
-    for (int kind = 1; kind <= 3; ++kind)
+    for (int kind = 1; kind <= 5; ++kind)
         for (int bc = bc_max; bc >= 1 && bc >= bc_max / 4; bc >>= 1)
             for (int half = 0; half <= (kind != 2 && bc < 32 ? 1 : 0); ++half) {
                 ApplyVariant v = rule;
@@ -192,6 +192,8 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                 v.fwd_half = (int8_t)half;
                 if (kind == 2 && (!periodic || bc > 8)) continue;  // lane-per-hat: <= 8 per task
                 if (kind == 3 && (!x_vec || bc < 4)) continue;    // TMA: 16-byte records
+                if ((kind == 4 || kind == 5) && (bc != B || (bc != 4 && bc != 8))) continue;  // one chunk
+                if (kind == 5 && !periodic) continue;  // periodic specialisation
                 for (int su = 1; su <= 3; ++su) {
                     // staging depth: only the staged kernel at 4 or 8 entries, full frames
                     if (su != 2 && (kind != 1 || half || (bc != 4 && bc != 8))) continue;

@@ -174,7 +174,7 @@ def test_autotune_keeps_bits(B):
     g0 = c.op.apply_AT(y0)
     r = c.op.autotune(B)
     assert r["batch"] == B and r["candidates"] >= 4
-    assert r["fwd_kernel"] in (1, 2) and r["time_kernel"] in (1, 2, 3, 4)
+    assert r["fwd_kernel"] in (1, 2, 3, 4, 5) and r["time_kernel"] in (1, 2, 3, 4)
     assert r["space_kernel"] in (1, 2, 3)
     if B % 4:
         assert r["time_kernel"] < 3  # the TMA phases need 16-byte frame records
@@ -187,7 +187,7 @@ def test_autotune_keeps_bits(B):
 
 
 @pytest.mark.parametrize("which", ["small", "schw"])
-@pytest.mark.parametrize("B", [1, 3, 8, 16])
+@pytest.mark.parametrize("B", [1, 3, 4, 8, 16])
 def test_every_variant_same_bits(which, small, schw, B):
     """Every kernel variant (rtt_set_variant) of the FP32 forward and adjoint
     gives the same bits as the default rule, which matches the oracle; the
@@ -205,7 +205,7 @@ def test_every_variant_same_bits(which, small, schw, B):
     while bc_max < min(B, 32):
         bc_max *= 2
     n = 0
-    for fk in (1, 2, 3):
+    for fk in (1, 2, 3, 4, 5):
         for bc in sorted({bc_max, max(1, bc_max // 2), max(1, bc_max // 4)}):
             for half in (0, 1):
                 for su in ((1, 2, 3) if (fk == 1 and half == 0 and bc in (4, 8)) else (2,)):
@@ -224,6 +224,9 @@ def test_every_variant_same_bits(which, small, schw, B):
     for tk in (1, 2, 3, 4):
         c.op.set_variant(B, 1, bc_max, 0, tk, 3)
         assert torch.equal(c.op.apply_AT(y1, arm_mask=1), g1), tk
+    for fk in (1, 3, 4, 5):
+        c.op.set_variant(B, fk, bc_max, 0, 2, 2)
+        assert torch.equal(c.op.apply_A(x, arm_mask=1), y1), fk
     c.op.set_variant(B)
     assert c.op.status(clear=True) == 0
     assert n >= 12
