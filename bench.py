@@ -171,14 +171,21 @@ def run_ours(args, rank, world, device):
         op.apply_A(x, y)
         op.apply_AT(y, g)
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize(device)
-    ranks_barrier(world)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     with ClockSampler(device.index if device.index is not None else 0) as clk:
+        # warm-up inside the sampled region, right before the timed steps, so
+        # the GPU does not idle (and drop its clocks) between the two; the last
+        # warm-up step is queued after the barrier, so the host's launches are
+        # ahead of the device when the first timed step starts
+        n_warm = max(args.warmup, 3)
+        for _ in range(n_warm - 1):
+            flush.zero_()
+            step()
         torch.cuda.synchronize(device)
+        ranks_barrier(world)
+        flush.zero_()
+        step()
         torch.cuda.nvtx.range_push("bench_timed")  # lets ncu --nvtx-include select these launches
         for i in range(args.steps):
             flush.zero_()  # L2 flush between timed iterations (outside the events)
