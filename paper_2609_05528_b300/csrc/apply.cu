@@ -2617,9 +2617,20 @@ ApplyVariant variant_for(const rtt_op_s* op, int batch) {
     // incidences in flight; each falls back to the next kernel down where
     // the cadence, batch or buffers do not allow it
     ApplyVariant v;
-    v.fwd = 5;
+    const int P = frames_per_hat(op->frame_D);
+    const bool one_chunk4 = batch == 4 || batch == 8;
+    const bool rows128 = (batch == 4 || batch == 8 || batch == 16 || batch == 32) &&
+                         op->time.n_frames % (32 / batch) == 0;
+    v.fwd = (P > 0 && one_chunk4) ? 5 : 1;
     v.fwd_bc = (int8_t)pick_bc(batch);
-    v.time = frames_per_hat(op->frame_D) > 0 ? 4 : 1;
+    if (P == 0)
+        v.time = 1;
+    else if (rows128 && P % (32 / batch) == 0 && !(batch == 32 && P == 8))
+        v.time = 4;
+    else if (rows128 && (P == 2 || P == 4))
+        v.time = 3;
+    else
+        v.time = 2;
     v.space = 3;
     return v;
 }
