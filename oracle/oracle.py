@@ -376,6 +376,54 @@ def dense_A(w, table: Table, scl: float = 1.0) -> np.ndarray:
 
 
 # ---------------------------------------------------------------------------
+# Order mixing (Sec. 3.1 Eq. 4): d_L = (L (x) I) d_R, C_L = (L (x) I) C_R (L^T (x) I)
+# ---------------------------------------------------------------------------
+MIX_UNRESOLVED = 1  # L sums the orders of each pixel (the unresolved image)
+MIX_TOTAL_FLUX = 2  # L sums every row (the total-flux readout)
+
+
+def mixer(table: Table, mode: int, orders=(0, 1, 2)):
+    """W = C_L^{-1/2} L, the whitened collapse of Eq. 4 on the rows of `orders`
+    (scipy.sparse CSR, output rows x selected rows, selected rows in the
+    table's row order).  The data rows are already whitened (C_R = I), so
+    C_L = L L^T; its noise is the propagated one, not a new level (Sec. 3.1,
+    Sec. 4.2).  Unresolved image: one output row per pixel of the selected
+    rows, in ascending pixel order, L = 1 on that pixel's rows.  Total flux:
+    one output row, L = 1 on every selected row.  Each selected row feeds one
+    output row, so C_L is diagonal (checked) and C_L^{-1/2} is taken entry by
+    entry."""
+    from scipy import sparse
+    sel = np.nonzero(np.isin(table.row_order, tuple(orders)))[0]
+    R = sel.size
+    if mode == MIX_UNRESOLVED:
+        upix, grp = np.unique(table.row_pixel[sel], return_inverse=True)
+        L = sparse.csr_matrix((np.ones(R), (grp, np.arange(R))), shape=(upix.size, R))
+    elif mode == MIX_TOTAL_FLUX:
+        L = sparse.csr_matrix((np.ones(R), (np.zeros(R, np.int64), np.arange(R))), shape=(1, R))
+    else:
+        raise ValueError(f"mix mode {mode}")
+    C = (L @ L.T).tocoo()
+    assert np.all(C.row == C.col), "C_L is diagonal: each row feeds one output row"
+    cdiag = np.zeros(L.shape[0])
+    cdiag[C.row] = C.data
+    return sparse.diags(1.0 / np.sqrt(cdiag)) @ L
+
+
+def mix_rows(table: Table, y: np.ndarray, mode: int, orders=(0, 1, 2)) -> np.ndarray:
+    """d_L = W d_R for data y [selected rows][frames][batch] (Eq. 4)."""
+    W = mixer(table, mode, orders)
+    y2 = y.reshape(y.shape[0], -1)
+    return np.asarray(W @ y2).reshape((W.shape[0],) + y.shape[1:])
+
+
+def mix_rows_T(table: Table, yl: np.ndarray, mode: int, orders=(0, 1, 2)) -> np.ndarray:
+    """W^T applied to mixed data yl [output rows][frames][batch] (the adjoint)."""
+    W = mixer(table, mode, orders)
+    y2 = yl.reshape(yl.shape[0], -1)
+    return np.asarray(W.T @ y2).reshape((W.shape[1],) + yl.shape[1:])
+
+
+# ---------------------------------------------------------------------------
 # Probes, reach and old-age innovation (Eq. 10-13, 29-30, 35)
 # ---------------------------------------------------------------------------
 AGES = np.arange(0.0, 253.0, 4.0)  # 0 ... 252 M on a 4 M grid (Sec. 6.2)

@@ -1,0 +1,110 @@
+"""Pins of the oracle's order mixing (Sec. 3.1 Eq. 4): the unresolved image
+and the total-flux readout as whitened linear collapses of the order-resolved
+data, with the noise propagated through the same map."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_05528_b300 import inputs as I
+
+
+class _Rows:
+    """The two row fields the mixer reads."""
+
+    def __init__(self, order, pixel):
+        self.row_order = np.asarray(order, np.int8)
+        self.row_pixel = np.asarray(pixel, np.int32)
+
+
+def test_hand_worked_example():
+    """Rows (order, pixel) = (0, 5), (0, 7), (1, 5), (1, 9), (2, 5) with data
+    1, 2, 3, 4, 5 (one frame, one history).  Unresolved: pixel 5 collects
+    orders 0, 1, 2 -> (1 + 3 + 5) / sqrt(3); pixel 7 -> 2 / 1; pixel 9 -> 4 / 1.
+    Total flux: (1 + 2 + 3 + 4 + 5) / sqrt(5).  Direct arm only: the two
+    direct rows unchanged."""
+    t = _Rows([0, 0, 1, 1, 2], [5, 7, 5, 9, 5])
+    y = np.array([1.0, 2.0, 3.0, 4.0, 5.0]).reshape(5, 1, 1)
+    u = O.mix_rows(t, y, O.MIX_UNRESOLVED)
+    assert u.shape == (3, 1, 1)
+    np.testing.assert_allclose(u.ravel(), [9.0 / math.sqrt(3.0), 2.0, 4.0], rtol=1e-15)
+    f = O.mix_rows(t, y, O.MIX_TOTAL_FLUX)
+    np.testing.assert_allclose(f.ravel(), [15.0 / math.sqrt(5.0)], rtol=1e-15)
+    d = O.mix_rows(t, y[:2], O.MIX_UNRESOLVED, orders=(0,))
+    np.testing.assert_allclose(d.ravel(), [1.0, 2.0], rtol=0)
+    # adjoint: each row receives its pixel's value over sqrt(its row count)
+    back = O.mix_rows_T(t, np.array([1.0, 1.0, 1.0]).reshape(3, 1, 1), O.MIX_UNRESOLVED)
+    s3 = 1.0 / math.sqrt(3.0)
+    np.testing.assert_allclose(back.ravel(), [s3, 1.0, s3, 1.0, s3], rtol=1e-15)
+
+
+@pytest.fixture(scope="module")
+def schw():
+    w = I.schw32()
+    return w, O.build_table(w, I.screen_samples(w))
+
+
+@pytest.mark.parametrize("mode", [O.MIX_UNRESOLVED, O.MIX_TOTAL_FLUX])
+@pytest.mark.parametrize("orders", [(0, 1, 2), (0, 1), (0,)])
+def test_mixed_noise_is_white(schw, mode, orders):
+    """W W^T = I: whitened rows stay unit-variance after the collapse, so no
+    arm gets an independent noise level (Sec. 4.2)."""
+    _, tab = schw
+    W = O.mixer(tab, mode, orders)
+    WW = (W @ W.T).toarray()
+    np.testing.assert_allclose(WW, np.eye(W.shape[0]), atol=1e-15)
+
+
+def test_direct_arm_unresolved_is_identity(schw):
+    """With the direct order alone every pixel has one row: no collapse."""
+    _, tab = schw
+    W = O.mixer(tab, O.MIX_UNRESOLVED, (0,)).toarray()
+    assert W.shape[0] == W.shape[1] == tab.rows_of_order(0)
+    np.testing.assert_array_equal(W, np.eye(W.shape[0]))
+
+
+def test_unresolved_brute_force(schw):
+    """Per pixel, loop over the rows of every order with that pixel, add them
+    and divide by the square root of their count; compare with W y."""
+    w, tab = schw
+    rng = np.random.default_rng(3)
+    y = rng.standard_normal((tab.n_rows, w.time.n_frames, 2))
+    got = O.mix_rows(tab, y, O.MIX_UNRESOLVED)
+    pixels = sorted(set(int(p) for p in tab.row_pixel))
+    assert got.shape[0] == len(pixels)
+    for i, p in enumerate(pixels):
+        rows = [r for r in range(tab.n_rows) if int(tab.row_pixel[r]) == p]
+        want = sum(y[r] for r in rows) / math.sqrt(len(rows))
+        np.testing.assert_allclose(got[i], want, rtol=1e-13, atol=1e-13)
+    assert any(sum(1 for r in range(tab.n_rows) if int(tab.row_pixel[r]) == p) > 1 for p in pixels)
+
+
+def test_total_flux_of_constant_rows(schw):
+    """Constant data c on R rows: the total-flux readout is c R / sqrt(R)."""
+    w, tab = schw
+    y = np.full((tab.n_rows, w.time.n_frames, 1), 2.5)
+    f = O.mix_rows(tab, y, O.MIX_TOTAL_FLUX)
+    np.testing.assert_allclose(f, 2.5 * math.sqrt(tab.n_rows), rtol=1e-14)
+
+
+@pytest.mark.parametrize("mode", [O.MIX_UNRESOLVED, O.MIX_TOTAL_FLUX])
+def test_collapse_never_adds_information(schw, mode):
+    """P = W^T W is an orthogonal projector, so the collapsed Gram
+    B^T P B is below the resolved Gram B^T B: every eigenvalue is at most the
+    resolved one (Weyl), and the total-flux Gram has rank at most T."""
+    w, tab = schw
+    scl = O.scale(tab)
+    Q = O.synth_class(w, "S224")
+    P = O.restricted_response(w, tab, Q, scl)  # [rows * T, d]
+    T = w.time.n_frames
+    d = P.shape[1]
+    W = O.mixer(tab, mode)
+    Pl = O.mix_rows(tab, P.reshape(tab.n_rows, T, d), mode).reshape(-1, d)
+    lr = np.linalg.eigvalsh(P.T @ P)
+    ll = np.linalg.eigvalsh(Pl.T @ Pl)
+    assert np.all(ll <= lr + 1e-9 * lr.max())
+    PP = (W.T @ W).toarray()
+    np.testing.assert_allclose(PP @ PP, PP, atol=1e-14)
+    if mode == O.MIX_TOTAL_FLUX:
+        assert np.sum(ll > 1e-9 * ll.max()) <= T
