@@ -366,6 +366,53 @@ rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q_dev, int d, 
                            void* stream);
 
 /*
+ * Order mixing (Sec. 3.1 Eq. 4): d_L = C_L^{-1/2} (L (x) I) d_R with
+ * C_L = (L (x) I) C_R (L^T (x) I) and C_R = I (the rows of A are whitened),
+ * so a mixed arm carries the noise propagated from the resolved rows, not a
+ * level of its own (Sec. 4.2).
+ *   RTT_MIX_UNRESOLVED: the unresolved image -- per pixel, the sum of the
+ *     arm's rows of that pixel over the orders (orders ascending) divided by
+ *     the square root of their count; one output row per pixel of the arm,
+ *     pixels ascending.
+ *   RTT_MIX_TOTAL_FLUX: the total-flux readout -- the sum of every row of the
+ *     arm (fixed row blocks, then the blocks in order) divided by the square
+ *     root of the row count; one output row.
+ * rtt_mix_rows_count: the mixed row count of (arm_mask, mode).
+ * rtt_mix_rows(_f64): y_dev [arm rows][n_frames][batch] -> yl_dev [mixed
+ *   rows][n_frames][batch] (device buffers, caller-owned, not aliased).
+ * rtt_mix_rows_T(_f64): the adjoint W^T, yl_dev -> y_dev (every arm row
+ *   written: the row's mixed row times the same 1 / sqrt(count)).
+ * Sums run in a fixed order (bitwise repeatable).  The first call for an arm
+ * mask builds that arm's pixel groups (device allocation, synchronous); the
+ * total-flux scratch grows on demand (synchronous once); otherwise
+ * asynchronous on `stream`.
+ * Errors: RTT_EINVAL (mode, arm mask, batch < 1, null pointer), RTT_ENOMEM,
+ * RTT_ECUDA.
+ */
+#define RTT_MIX_UNRESOLVED 1
+#define RTT_MIX_TOTAL_FLUX 2
+rtt_status rtt_mix_rows_count(rtt_op op, int arm_mask, int mode, int64_t* n_out);
+rtt_status rtt_mix_rows(rtt_op op, int arm_mask, int mode, const float* y_dev, float* yl_dev,
+                        int batch, void* stream);
+rtt_status rtt_mix_rows_T(rtt_op op, int arm_mask, int mode, const float* yl_dev, float* y_dev,
+                          int batch, void* stream);
+rtt_status rtt_mix_rows_f64(rtt_op op, int arm_mask, int mode, const double* y_dev,
+                            double* yl_dev, int batch, void* stream);
+rtt_status rtt_mix_rows_T_f64(rtt_op op, int arm_mask, int mode, const double* yl_dev,
+                              double* y_dev, int batch, void* stream);
+
+/*
+ * rtt_gram_normal_mix -- the restricted Gram of a mixed arm (Eq. 4, Eq. 7):
+ * G = Q^T A^T W^T W A Q with W the whitened collapse of `mode` above, by the
+ * route of rtt_gram_normal with the collapse and its adjoint between the
+ * FP64 forward and adjoint applies.  W^T W is an orthogonal projector, so no
+ * eigenvalue exceeds the resolved arm's.  Same arguments as rtt_gram_normal
+ * plus `mode`; synchronous.  Errors: RTT_EINVAL, RTT_ENOMEM, RTT_ECUDA.
+ */
+rtt_status rtt_gram_normal_mix(rtt_op op, int arm_mask, int mode, const double* Q_dev, int d,
+                               double* G_dev, void* stream);
+
+/*
  * rtt_eig_sym -- eigendecomposition of a symmetric n x n FP64 matrix on the
  * GPU (parallel cyclic Jacobi, round-robin ordering, relative off-diagonal
  * criterion), as used for the spectrum of the restricted Gram (Eq. 31).

@@ -65,7 +65,7 @@ __global__ void row_flags(int64_t n, const unsigned long long* key, int32_t* fla
 // rows[i] = inclusive scan - 1; row_ptr[row] = first ray; row order histogram
 __global__ void row_index(int64_t n, const unsigned long long* key, const int32_t* flag,
                           const int32_t* incl, int32_t* ray_row, int32_t* row_ptr,
-                          int32_t* row_order, unsigned int* order_count) {
+                          int32_t* row_order, int32_t* row_pixel, unsigned int* order_count) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int32_t row = incl[i] - 1;
@@ -74,6 +74,7 @@ __global__ void row_index(int64_t n, const unsigned long long* key, const int32_
         row_ptr[row] = (int32_t)i;
         const int ord = (int)(key[i] >> 32);
         row_order[row] = ord;
+        row_pixel[row] = (int32_t)(uint32_t)(key[i] & 0xffffffffull);
         atomicAdd(&order_count[ord], 1u);  // integer counts: order independent
     }
 }
@@ -230,7 +231,9 @@ static void free_op(rtt_op_s* op) {
                   op->K0,      op->F0,      op->F64,    op->r,      op->delay, op->weight,
                   op->thr,     op->node_ptr, op->inc,   op->row_order, op->zhat,
                   op->visits,  op->items,    op->split_tiles, op->fpartial, op->node_order,
-                  op->dev_status, op->rscratch};
+                  op->dev_status, op->rscratch, op->row_pixel, op->mix.grp_ptr,
+                  op->mix.grp_rows, op->mix.row_grp, op->mix.inv32, op->mix.inv64,
+                  op->mix.part};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete op;
@@ -375,8 +378,9 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
     RTT_TRY(alloc(&op->row_ptr, R + 1));
     RTT_TRY(alloc(&op->ray_row, E));
     RTT_TRY(alloc(&op->row_order, R));
+    RTT_TRY(alloc(&op->row_pixel, R));
     row_index<<<blocks(E), 256, 0, st>>>(E, k_out, flag, incl, op->ray_row, op->row_ptr,
-                                         op->row_order, ocount);
+                                         op->row_order, op->row_pixel, ocount);
     RTT_CUDA(cudaGetLastError());
     const int32_t E32 = (int32_t)E;
     RTT_CUDA(cudaMemcpyAsync(op->row_ptr + R, &E32, 4, cudaMemcpyHostToDevice, st));

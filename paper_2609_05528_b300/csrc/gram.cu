@@ -310,8 +310,8 @@ extern "C" rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q, int d, 
 // contraction runs over the n_nodes * n_hats source coefficients instead of
 // the rows * frames data samples (about 18x fewer at kerr256 sizes), which is
 // what makes an FP64-accurate Gram affordable on FP64-poor hardware.
-extern "C" rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q, int d, double* G,
-                                      void* stream) {
+static rtt_status gram_normal_impl(rtt_op op, int arm_mask, int mix_mode, const double* Q, int d,
+                                   double* G, void* stream) {
     if (!op || !Q || !G || d < 1 || d > 4096) {
         set_error("invalid gram arguments (d=%d)", d);
         return RTT_EINVAL;
@@ -325,15 +325,22 @@ extern "C" rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q, 
     const int64_t M = (int64_t)seg.total * op->time.n_frames;
     s = ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * W * sizeof(double));
     if (s != RTT_OK) return s;
-    double *Qc = nullptr, *Y = nullptr, *Z = nullptr;
+    double *Qc = nullptr, *Y = nullptr, *Z = nullptr, *YL = nullptr;
+    if (mix_mode) {
+        s = mix_prepare(op, seg);
+        if (s != RTT_OK) return s;
+    }
+    const int64_t ML = mix_mode ? mix_out_rows(op, seg, mix_mode) * op->time.n_frames : 0;
     cudaError_t e = cudaMalloc(&Qc, (size_t)N * W * 8);
     if (e == cudaSuccess) e = cudaMalloc(&Y, (size_t)(M > 0 ? M : 1) * W * 8);
     if (e == cudaSuccess) e = cudaMalloc(&Z, (size_t)N * W * 8);
+    if (e == cudaSuccess && mix_mode) e = cudaMalloc(&YL, (size_t)(ML > 0 ? ML : 1) * W * 8);
     cublasHandle_t h = nullptr;
     if (e == cudaSuccess && cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
         cudaFree(Qc);
         cudaFree(Y);
         cudaFree(Z);
+        if (YL) cudaFree(YL);
         set_error("cublasCreate failed");
         return RTT_ECUDA;
     }
@@ -345,6 +352,13 @@ extern "C" rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q, 
         copy_cols<<<(int)((N * w + 255) / 256), 256, 0, st>>>(Q, N, d, c0, w, Qc);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = launch_forward<double>(op, Qc, Y, w, seg, st);
+        if (e == cudaSuccess && mix_mode) {
+            // Y <- W^T W Y: the mixed arm's data and back (Eq. 4)
+            const int64_t cols = (int64_t)op->time.n_frames * w;
+            if (launch_mix<double>(op, seg, mix_mode, Y, YL, cols, false, st) != RTT_OK ||
+                launch_mix<double>(op, seg, mix_mode, YL, Y, cols, true, st) != RTT_OK)
+                e = cudaErrorUnknown;
+        }
         if (e == cudaSuccess) e = launch_adjoint<double>(op, Y, Z, w, seg, (double*)op->zhat, st);
         // rows c0 .. c0+w of G (symmetric): column-major (d x w) = Q_cm (d x N) Z_cm^T (N x w)
         if (e == cudaSuccess)
@@ -360,11 +374,26 @@ extern "C" rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q, 
     cudaFree(Qc);
     cudaFree(Y);
     cudaFree(Z);
+    if (YL) cudaFree(YL);
     if (e != cudaSuccess || cs != CUBLAS_STATUS_SUCCESS) {
         set_error("gram (normal operator): cuda %s, cublas %d", cudaGetErrorString(e), (int)cs);
         return e == cudaErrorMemoryAllocation ? RTT_ENOMEM : RTT_ECUDA;
     }
     return RTT_OK;
+}
+
+extern "C" rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q, int d, double* G,
+                                      void* stream) {
+    return gram_normal_impl(op, arm_mask, 0, Q, d, G, stream);
+}
+
+extern "C" rtt_status rtt_gram_normal_mix(rtt_op op, int arm_mask, int mode, const double* Q, int d,
+                                          double* G, void* stream) {
+    if (mode != RTT_MIX_UNRESOLVED && mode != RTT_MIX_TOTAL_FLUX) {
+        set_error("invalid mix mode %d", mode);
+        return RTT_EINVAL;
+    }
+    return gram_normal_impl(op, arm_mask, mode, Q, d, G, stream);
 }
 
 extern "C" rtt_status rtt_eig_sym_batched(int n, int batch, double* A, double* evals_host,

@@ -90,6 +90,7 @@ struct rtt_op_s {
     int32_t* node_ptr = nullptr;  // [S+1] transposed incidence CSR
     int32_t* inc = nullptr;       // [4E] e * 4 + c
     int32_t* row_order = nullptr; // [R] order of each row
+    int32_t* row_pixel = nullptr; // [R] pixel of each row
     int32_t* node_order = nullptr; // [S] nodes sorted by descending incidence count
     // adjoint scratch: per-ray temporal contraction [E][K][<=32], grown on demand
     void* zhat = nullptr;
@@ -106,8 +107,33 @@ struct rtt_op_s {
     void* rscratch = nullptr;  // residual y - d of the separate-path rtt_apply_A_AT, grown on demand
     size_t rscratch_bytes = 0;
     int* dev_status = nullptr;  // device status word: bit 0 = a kernel's bounded wait timed out
+    // order mixing (Eq. 4), built on first use for one arm mask: the arm's
+    // output rows grouped by pixel (unresolved image), and the scratch of the
+    // total-flux row reduction
+    struct MixGroups {
+        int arm_mask = -1;
+        int32_t n_groups = 0;
+        int32_t* grp_ptr = nullptr;   // [G+1] into grp_rows
+        int32_t* grp_rows = nullptr;  // arm output rows, pixel-major, orders ascending
+        int32_t* row_grp = nullptr;   // [arm rows] group of each row
+        float* inv32 = nullptr;       // [G] 1 / sqrt(rows in group), FP32
+        double* inv64 = nullptr;      // [G] the same in FP64
+        void* part = nullptr;         // total-flux partial sums, grown on demand
+        size_t part_bytes = 0;
+    } mix;
     // autotuned kernel variants (rtt_autotune), per batch size
     int n_tuned = 0;
     int tuned_batch[rtt::kMaxTuned] = {};
     rtt::ApplyVariant tuned[rtt::kMaxTuned];
 };
+
+namespace rtt {
+// order mixing (mix.cu): pixel groups of an arm, mixed row count, and the
+// collapse (adjoint = false: arm rows -> mixed rows) or its adjoint over
+// `cols` = n_frames * batch values per row
+rtt_status mix_prepare(rtt_op_s* op, const ArmSeg& seg);
+int64_t mix_out_rows(const rtt_op_s* op, const ArmSeg& seg, int mode);
+template <typename T>
+rtt_status launch_mix(rtt_op_s* op, const ArmSeg& seg, int mode, const T* in, T* out, int64_t cols,
+                      bool adjoint, cudaStream_t st);
+}  // namespace rtt

@@ -142,6 +142,13 @@ _SIGS = {
     "rtt_solve_tsvd": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, dp, ctypes.c_int, vp,
                                       ctypes.c_int, vp, vp]),
     "rtt_gram_normal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
+    "rtt_gram_normal_mix": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
+    "rtt_mix_rows_count": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "rtt_mix_rows": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
+    "rtt_mix_rows_T": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
+    "rtt_mix_rows_f64": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
+    "rtt_mix_rows_T_f64": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
     "rtt_gram_class": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
     "rtt_synth_class": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
     "rtt_rank_audit": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp),
@@ -351,6 +358,40 @@ class Operator:
         self._launch(name, y, x, B, arm_mask, stream)
         return x
 
+    def mix_rows_count(self, mode: int, arm_mask: int = 7) -> int:
+        """rtt_mix_rows_count: rows of the mixed arm (Eq. 4)."""
+        n = ctypes.c_int64()
+        check(lib().rtt_mix_rows_count(self.handle, arm_mask, mode, ctypes.byref(n)),
+              "rtt_mix_rows_count")
+        return int(n.value)
+
+    def mix_rows(self, y, mode: int, arm_mask: int = 7, out=None, stream=None):
+        """rtt_mix_rows(_f64): the whitened collapse of the arm's data y
+        [arm_rows, n_frames, B] into [mixed rows, n_frames, B] (Eq. 4)."""
+        import torch
+        assert y.is_cuda and y.is_contiguous() and y.dim() == 3
+        B = y.shape[2]
+        if out is None:
+            out = torch.empty((self.mix_rows_count(mode, arm_mask), y.shape[1], B), dtype=y.dtype,
+                              device=y.device)
+        name = "rtt_mix_rows" if y.dtype == torch.float32 else "rtt_mix_rows_f64"
+        check(getattr(lib(), name)(self.handle, arm_mask, mode, ctypes.c_void_p(y.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), B, _stream(stream)), name)
+        return out
+
+    def mix_rows_T(self, yl, mode: int, arm_mask: int = 7, out=None, stream=None):
+        """rtt_mix_rows_T(_f64): the adjoint of the collapse, [mixed rows,
+        n_frames, B] -> [arm_rows, n_frames, B]."""
+        import torch
+        assert yl.is_cuda and yl.is_contiguous() and yl.dim() == 3
+        B = yl.shape[2]
+        if out is None:
+            out = torch.empty((self.arm_rows(arm_mask), yl.shape[1], B), dtype=yl.dtype, device=yl.device)
+        name = "rtt_mix_rows_T" if yl.dtype == torch.float32 else "rtt_mix_rows_T_f64"
+        check(getattr(lib(), name)(self.handle, arm_mask, mode, ctypes.c_void_p(yl.data_ptr()),
+                                   ctypes.c_void_p(out.data_ptr()), B, _stream(stream)), name)
+        return out
+
 
 AGES = np.arange(0.0, 253.0, 4.0)
 
@@ -382,6 +423,8 @@ def reach(op: "Operator", info, arm_mask: int = 7, ages=AGES, h: float = 3.0, a0
     return res, passed.astype(bool)
 
 
+MIX_UNRESOLVED = 1  # rtt.h RTT_MIX_UNRESOLVED
+MIX_TOTAL_FLUX = 2  # rtt.h RTT_MIX_TOTAL_FLUX
 GRAM_DATA = 0
 GRAM_NORMAL = 1
 GRAM_CLASS_S224 = 2
@@ -493,6 +536,19 @@ def solve_tsvd(op: "Operator", Q, V, evals, rank: int, data, arm_mask: int = 7, 
                                ctypes.c_void_p(data.data_ptr()), n_rhs,
                                ctypes.c_void_p(xh.data_ptr()), _stream(stream)), "rtt_solve_tsvd")
     return xh
+
+
+def gram_normal_mix(op: "Operator", Q, mode: int, arm_mask: int = 7, stream=None):
+    """rtt_gram_normal_mix: G = Q^T A^T W^T W A Q for the mixed arm `mode`
+    (Eq. 4, Eq. 7); Q: CUDA float64 [n_nodes, n_hats, d]."""
+    import torch
+    assert Q.is_cuda and Q.dtype == torch.float64 and Q.is_contiguous() and Q.dim() == 3
+    d = Q.shape[2]
+    G = torch.empty((d, d), dtype=torch.float64, device=Q.device)
+    check(lib().rtt_gram_normal_mix(op.handle, arm_mask, mode, ctypes.c_void_p(Q.data_ptr()), d,
+                                    ctypes.c_void_p(G.data_ptr()), _stream(stream)),
+          "rtt_gram_normal_mix")
+    return G
 
 
 def rank_audit(ops, Qs, arm_masks=(1, 7), ages=AGES, h: float = 3.0, quantile: float = 0.999,

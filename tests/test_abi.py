@@ -75,3 +75,13 @@ def test_trace_rejects_bad_geometry(L):
         rtt.rtt_trace_rays(0.5, 95.0, w.grid, s, stream=0)
     with pytest.raises(rtt.RttError):
         rtt.rtt_trace_rays(1.2, 50.0, w.grid, s, stream=0)
+
+
+def test_mix_rejects_invalid_arguments_on_host(L):
+    """Order mixing checks its mode and pointers before any device work."""
+    n = ctypes.c_int64()
+    assert L.rtt_mix_rows_count(None, 7, 1, ctypes.byref(n)) == -1
+    assert L.rtt_mix_rows(None, 7, 1, None, None, 1, None) == -1
+    assert L.rtt_mix_rows_T_f64(None, 7, 2, None, None, 1, None) == -1
+    assert L.rtt_gram_normal_mix(None, 7, 3, None, 4, None, None) == -1
+    assert L.rtt_gram_normal_mix(None, 7, 1, None, 4, None, None) == -1

@@ -1,0 +1,118 @@
+"""Order mixing on the GPU (Sec. 3.1 Eq. 4) against the oracle: the unresolved
+image and the total-flux readout of the whitened data, their adjoints, FP32
+and FP64, every arm; the mixed arm's restricted Gram; repeatability."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_05528_b300 import build, rtt
+from paper_2609_05528_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+ARMS = {7: (0, 1, 2), 3: (0, 1), 1: (0,), 6: (1, 2)}
+MODES = [O.MIX_UNRESOLVED, O.MIX_TOTAL_FLUX]
+
+
+def _optable(tab):
+    return {"order": tab.order, "pixel": tab.pixel, "r": tab.r, "phi": tab.phi,
+            "delay": tab.delay, "weight": tab.weight, "throughput": tab.throughput}
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+
+
+@pytest.fixture(scope="module")
+def schw():
+    w = I.schw32()
+    tab = O.build_table(w, I.screen_samples(w))
+    op = rtt.Operator(w, _optable(tab))
+    yield w, tab, op
+    op.close()
+
+
+@pytest.fixture(scope="module")
+def k256():
+    w = I.kerr256()
+    tab = O.build_table(w, I.screen_samples(w))
+    op = rtt.Operator(w, _optable(tab))
+    yield w, tab, op
+    op.close()
+
+
+def test_constants_match_oracle():
+    assert rtt.MIX_UNRESOLVED == O.MIX_UNRESOLVED and rtt.MIX_TOTAL_FLUX == O.MIX_TOTAL_FLUX
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("mask", sorted(ARMS))
+@pytest.mark.parametrize("B", [1, 3, 8])
+def test_small_against_oracle(schw, mode, mask, B):
+    """Every arm, odd and vector batch widths, both directions, FP32 and FP64."""
+    w, tab, op = schw
+    orders = ARMS[mask]
+    x = I.uniform_batch(w, range(B))  # non-negative sources: data without cancellation
+    y = op.apply_A(torch.from_numpy(x).cuda(), arm_mask=mask)  # FP64 data of the arm
+    yl = op.mix_rows(y, mode, arm_mask=mask)
+    ref = O.mix_rows(tab, y.cpu().numpy(), mode, orders)
+    assert yl.shape == ref.shape == (op.mix_rows_count(mode, mask), w.time.n_frames, B)
+    assert _rel(yl.cpu().numpy(), ref) <= 1e-14
+    y32 = y.float().contiguous()
+    yl32 = op.mix_rows(y32, mode, arm_mask=mask).cpu().numpy().astype(np.float64)
+    ref32 = O.mix_rows(tab, y32.cpu().numpy().astype(np.float64), mode, orders)
+    # FP32 sums: <= 3 terms per pixel; total flux over fixed blocks of rows
+    assert _rel(yl32, ref32) <= (1e-6 if mode == O.MIX_UNRESOLVED else 2e-5)
+    # adjoint on independent data
+    z = I.noise(ref.shape, 5 + B)
+    back = op.mix_rows_T(torch.from_numpy(z).cuda(), mode, arm_mask=mask).cpu().numpy()
+    refb = O.mix_rows_T(tab, z, mode, orders)
+    assert back.shape == (op.arm_rows(mask), w.time.n_frames, B)
+    assert _rel(back, refb) <= 1e-15
+    back32 = op.mix_rows_T(torch.from_numpy(z.astype(np.float32)).cuda(), mode, arm_mask=mask)
+    assert _rel(back32.cpu().numpy().astype(np.float64), refb) <= 1e-6
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_kerr256_every_output(k256, mode):
+    """The benchmark's sizes (FP32, batch 8, resolved arm): every mixed output
+    and every row of the adjoint against the oracle on the same data."""
+    w, tab, op = k256
+    x = torch.from_numpy(I.history_batch(w, range(100, 108)).astype(np.float32)).cuda()
+    y = op.apply_A(x)
+    yl = op.mix_rows(y, mode).cpu().numpy().astype(np.float64)
+    ref = O.mix_rows(tab, y.cpu().numpy().astype(np.float64), mode)
+    assert _rel(yl, ref) <= (1e-6 if mode == O.MIX_UNRESOLVED else 2e-5)
+    z = I.noise(ref.shape, 31).astype(np.float32)
+    back = op.mix_rows_T(torch.from_numpy(z).cuda(), mode).cpu().numpy().astype(np.float64)
+    assert _rel(back, O.mix_rows_T(tab, z.astype(np.float64), mode)) <= 1e-6
+    # repeatable to the bit
+    y2 = op.mix_rows(y, mode).cpu().numpy().astype(np.float64)
+    assert np.array_equal(y2, yl)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_gram(schw, mode):
+    """rtt_gram_normal_mix = P^T W^T W P with P the oracle's scaled response on
+    S224, and no eigenvalue above the resolved arm's (W^T W is a projector)."""
+    w, tab, op = schw
+    Qn = O.synth_class(w, "S224")
+    scl = O.scale(tab)
+    P = O.restricted_response(w, tab, Qn, scl)
+    T, d = w.time.n_frames, P.shape[1]
+    Pl = O.mix_rows(tab, P.reshape(tab.n_rows, T, d), mode).reshape(-1, d)
+    Gref = Pl.T @ Pl
+    Q = torch.from_numpy(np.ascontiguousarray(Qn.reshape(w.grid.n_nodes, w.time.n_hats, d))).cuda()
+    G = rtt.gram_normal_mix(op, Q, mode).cpu().numpy()
+    assert _rel(G, Gref) <= 1e-10
+    Gr = rtt.gram(op, Q, mode=rtt.GRAM_NORMAL).cpu().numpy()
+    lr, ll = np.linalg.eigvalsh(Gr), np.linalg.eigvalsh(G)
+    assert np.all(ll <= lr + 1e-9 * lr.max())
