@@ -346,6 +346,31 @@ def run_ours(args, rank, world, device):
         f_ms.append(a0.elapsed_time(a1))
     fp64_ms = max_over_ranks(float(np.mean(f_ms)), world, device)
 
+    # order mixing (Eq. 4) of the step's y: the unresolved image and the
+    # total-flux readout, HBM bound (y read once, the mixed rows written once)
+    mix = {}
+    try:
+        from paper_2609_05528_b300 import rtt
+        peak_m, _ = measured_peaks()
+        for name, mode in (("unresolved", rtt.MIX_UNRESOLVED), ("total_flux", rtt.MIX_TOTAL_FLUX)):
+            yl = op.mix_rows(y, mode)
+            m_ms = []
+            for _ in range(args.steps):
+                flush.zero_()
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                op.mix_rows(y, mode, out=yl)
+                a1.record(stream)
+                a1.synchronize()
+                m_ms.append(a0.elapsed_time(a1))
+            mm = float(np.mean(m_ms))
+            nbytes = (y.numel() + yl.numel()) * 4
+            mix[name] = {"ms": mm, "rows_out": int(yl.shape[0]), "algorithmic_bytes": int(nbytes),
+                         "GB/s": nbytes / (mm * 1e-3) / 1e9, "frac": nbytes / (mm * 1e-3) / 1e9 / peak_m}
+    except Exception as exc:  # a measurement extra; report why it failed
+        mix = {"error": str(exc)[:200]}
+
     ab = algorithmic_bytes(op, BATCH)
     mA, mAT = float(np.mean(t_A)), float(np.mean(t_AT))
     dom, dom_ms = ("A", mA) if mA >= mAT else ("AT", mAT)
@@ -377,6 +402,7 @@ def run_ours(args, rank, world, device):
         "fp64_path": {"value": job_value(world, BATCH, fp64_ms), "ms_per_step": fp64_ms},
         "cuda_graph": graph,
         "fused_A_AT": fused,
+        "order_mix": mix,
         "clocks": clocks,
         "gpu_launches": launches_per_step(BATCH) * args.steps,
     }

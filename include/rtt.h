@@ -375,8 +375,9 @@ rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q_dev, int d, 
  *     the square root of their count; one output row per pixel of the arm,
  *     pixels ascending.
  *   RTT_MIX_TOTAL_FLUX: the total-flux readout -- the sum of every row of the
- *     arm (fixed row blocks, then the blocks in order) divided by the square
- *     root of the row count; one output row.
+ *     arm (fixed row blocks summed in order, then the blocks' sums in a fixed
+ *     lane split and shuffle tree) divided by the square root of the row
+ *     count; one output row.
  * rtt_mix_rows_count: the mixed row count of (arm_mask, mode).
  * rtt_mix_rows(_f64): y_dev [arm rows][n_frames][batch] -> yl_dev [mixed
  *   rows][n_frames][batch] (device buffers, caller-owned, not aliased).

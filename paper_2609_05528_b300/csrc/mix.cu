@@ -8,8 +8,9 @@
 //   total flux: L sums every row of the arm; C_L = R (one output row).
 // The adjoint is W^T: every row receives its output row scaled by the same
 // 1 / sqrt(count).  Sums run in a fixed order (orders ascending within a
-// pixel; fixed row blocks, then the blocks in order, for the total flux), so
-// results are bitwise repeatable.  HBM bound: the mixed data is read or
+// pixel; for the total flux, fixed row blocks summed in order, then the
+// blocks' sums by a fixed lane split and shuffle tree), so results are
+// bitwise repeatable.  HBM bound: the mixed data is read or
 // written once.
 #include <cuda_runtime.h>
 
@@ -73,6 +74,7 @@ __global__ void mix_unres_adj(int32_t R, int64_t nv, const int32_t* __restrict__
 }
 
 // total flux, pass 1: block b sums rows [b RB, min(R, (b + 1) RB)) in order
+// (eight rows' loads issued before their additions)
 template <typename V>
 __global__ void mix_flux_part(int32_t R, int32_t RB, int64_t nv, const V* __restrict__ y,
                               V* __restrict__ part) {
@@ -80,21 +82,41 @@ __global__ void mix_flux_part(int32_t R, int32_t RB, int64_t nv, const V* __rest
     const int r0 = b * RB, r1 = min(R, r0 + RB);
     for (int64_t c = threadIdx.x; c < nv; c += blockDim.x) {
         V acc = y[(int64_t)r0 * nv + c];
-        for (int r = r0 + 1; r < r1; ++r) vadd(acc, y[(int64_t)r * nv + c]);
+        int r = r0 + 1;
+        for (; r + 8 <= r1; r += 8) {
+            V v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = y[(int64_t)(r + u) * nv + c];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) vadd(acc, v[u]);
+        }
+        for (; r < r1; ++r) vadd(acc, y[(int64_t)r * nv + c]);
         part[(int64_t)b * nv + c] = acc;
     }
 }
 
-// total flux, pass 2: the blocks' sums in order, times 1 / sqrt(R)
-template <typename T, typename V>
-__global__ void mix_flux_sum(int32_t nb, int64_t nv, T inv, const V* __restrict__ part,
-                             V* __restrict__ yl) {
-    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= nv) return;
-    V acc = part[c];
-    for (int b = 1; b < nb; ++b) vadd(acc, part[(int64_t)b * nv + c]);
-    vscale(acc, inv);
-    yl[c] = acc;
+// total flux, pass 2: warp per value c; lane l sums the blocks b = l, l + 32,
+// ... in order, a fixed shuffle tree adds the lanes; times 1 / sqrt(R)
+template <typename T>
+__global__ void mix_flux_sum(int32_t nb, int64_t ncols, T inv, const T* __restrict__ part,
+                             T* __restrict__ yl) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (c >= ncols) return;
+    T acc = T(0);
+    int b = lane;
+    for (; b + 32 * 3 < nb; b += 32 * 4) {
+        const T v0 = part[(int64_t)b * ncols + c], v1 = part[(int64_t)(b + 32) * ncols + c];
+        const T v2 = part[(int64_t)(b + 64) * ncols + c], v3 = part[(int64_t)(b + 96) * ncols + c];
+        acc = acc + v0;
+        acc = acc + v1;
+        acc = acc + v2;
+        acc = acc + v3;
+    }
+    for (; b < nb; b += 32) acc = acc + part[(int64_t)b * ncols + c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc = acc + __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) yl[c] = acc * inv;
 }
 
 // total flux, adjoint: every row gets the readout times 1 / sqrt(R)
@@ -213,8 +235,9 @@ static rtt_status mix_fwd_v(rtt_op_s* op, const ArmSeg& seg, int mode, const T* 
         if (s != RTT_OK) return s;
         V* part = reinterpret_cast<V*>(op->mix.part);
         mix_flux_part<V><<<nb, 256, 0, st>>>(R, RB, nv, yv, part);
-        mix_flux_sum<T, V><<<(int)((nv + 255) / 256), 256, 0, st>>>(nb, nv, (T)(1.0 / std::sqrt((double)R)),
-                                                                    part, ylv);
+        const int64_t ncols = nv * (int64_t)(sizeof(V) / sizeof(T));
+        mix_flux_sum<T><<<(int)((ncols * 32 + 255) / 256), 256, 0, st>>>(
+            nb, ncols, (T)(1.0 / std::sqrt((double)R)), reinterpret_cast<const T*>(part), yl);
     }
     return cudaGetLastError() == cudaSuccess ? RTT_OK : RTT_ECUDA;
 }
