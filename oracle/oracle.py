@@ -443,6 +443,34 @@ def probe_info(w, table: Table, scl: float, ages=AGES, h: float = PROBE_H) -> np
     return info
 
 
+def mix_probe_info(w, table: Table, scl: float, mode: int, orders=(0, 1, 2), ages=AGES,
+                   h: float = PROBE_H) -> np.ndarray:
+    """I_L(a) = || W C^{-1/2} A q_a ||^2 for a mixed arm (Eq. 4 with Eq. 10-12,
+    29): per age, the whitened probe response of every selected (row, frame)
+    (the row's rays' w_e q_a at their source points, q_a = 1_[r_in, r_out](r)
+    / N_h exp(-(t + a)^2 / (2 h^2)), t = t_o(f) - Delta_e), collapsed by the
+    mixer W of `mode`, then its squared norm.  numpy, one age at a time."""
+    W = mixer(table, mode, orders)
+    sel = np.nonzero(np.isin(table.row_order, tuple(orders)))[0]
+    T = w.time.n_frames
+    to = w.time.frame_times()
+    Nh = probe_norm_const(w, h)
+    g = w.grid
+    # the selected rows' rays, in row order, and the start of each row among them
+    counts = table.row_ptr[sel + 1] - table.row_ptr[sel]
+    rays = np.concatenate([np.arange(table.row_ptr[i], table.row_ptr[i + 1]) for i in sel])
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    ind = ((table.r[rays] >= g.r_in) & (table.r[rays] <= g.r_out)).astype(np.float64)
+    wt = table.weight[rays] * ind / Nh
+    t = to[None, :] - table.delay[rays][:, None]  # [rays, T]
+    out = np.empty(len(ages))
+    for i, a in enumerate(np.asarray(ages, np.float64)):
+        contrib = wt[:, None] * np.exp(-(t + a) ** 2 / (2.0 * h * h))
+        Y = np.add.reduceat(contrib, starts, axis=0)  # [selected rows, T]
+        out[i] = scl * scl * float(np.sum(np.asarray(W @ Y) ** 2))
+    return out
+
+
 def probe_norm_const(w, h: float = PROBE_H) -> float:
     """N_h of Eq. 11."""
     g = w.grid

@@ -108,3 +108,27 @@ def test_collapse_never_adds_information(schw, mode):
     np.testing.assert_allclose(PP @ PP, PP, atol=1e-14)
     if mode == O.MIX_TOTAL_FLUX:
         assert np.sum(ll > 1e-9 * ll.max()) <= T
+
+
+def test_mixed_probe_identity_arm_matches_c_probe(schw):
+    """Direct arm, unresolved collapse = identity: the numpy mixed probe
+    information equals the C oracle's probe information on the direct rows."""
+    w, tab = schw
+    scl = O.scale(tab)
+    got = O.mix_probe_info(w, tab, scl, O.MIX_UNRESOLVED, (0,))
+    want = O.probe_info(w, tab.select((0,)), scl)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-300)
+    assert np.max(want) > 1.0
+
+
+@pytest.mark.parametrize("mode", [O.MIX_UNRESOLVED, O.MIX_TOTAL_FLUX])
+def test_mixed_probe_below_resolved(schw, mode):
+    """W^T W is a projector, so the collapsed probe information never exceeds
+    the resolved one (C oracle), age by age; and it is strictly below it at
+    some age (the orders do not all coincide)."""
+    w, tab = schw
+    scl = O.scale(tab)
+    got = O.mix_probe_info(w, tab, scl, mode)
+    res = O.probe_info(w, tab, scl)
+    assert np.all(got <= res * (1 + 1e-12))
+    assert np.any(got < 0.999 * res)
