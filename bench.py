@@ -565,10 +565,22 @@ def run_audit(device):
         torch.cuda.synchronize(device)
         sig = np.sqrt(np.maximum(ev, 0.0))
         ranks = [int(np.count_nonzero(sv >= 1.0)) for sv in sig]  # rho = 1
+        # probe information of the mixed arm, then its reach and J_old (the
+        # footprints of the summed orders; A_{0,0.999} of the direct order)
+        rr = []
+        for op in ops:
+            info = rtt.probe_info_mix(op, mode, 7)
+            rr.append(rtt.reach(op, info, 7, a0q=rtt.direct_age_quantile(op))[0])
+        torch.cuda.synchronize(device)
         mech[name] = {"rank": ranks, "median_rank": float(np.median(ranks)),
                       "sigma_max_range": [float(sig[:, -1].min()), float(sig[:, -1].max())],
+                      "L_anchor": [r.L_anchor for r in rr],
+                      "J_old": [round(r.J_old, 3) for r in rr],
+                      "median_J_old": float(np.median([r.J_old for r in rr])),
                       "seconds": round(time.perf_counter() - t, 3)}
     mech["resolved_median_rank"] = float(np.median(out["rank_resolved"]))
+    mech["resolved_median_J_old"] = float(np.median(out["J_old_resolved"]))
+    mech["direct_median_J_old"] = float(np.median(out["J_old_direct"]))
     mech["direct_median_rank"] = float(np.median(out["rank_direct"]))
     mech["never_above_resolved"] = all(u <= r and f <= r for u, f, r in zip(
         mech["unresolved"]["rank"], mech["total_flux"]["rank"], out["rank_resolved"]))

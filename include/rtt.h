@@ -403,6 +403,21 @@ rtt_status rtt_mix_rows_T_f64(rtt_op op, int arm_mask, int mode, const double* y
                               double* y_dev, int batch, void* stream);
 
 /*
+ * rtt_probe_info_mix -- probe information of a mixed arm (Eq. 4 with Eq.
+ * 10-12, 29): I_L(a) = || W scale A q_a ||^2, W the whitened collapse of
+ * `mode` over the arm's rows and q_a the scalar age probe of rtt_probe_info
+ * evaluated at each ray's source point.  The arm's probe responses are formed
+ * in FP64 for 16 ages at a time (terms with exponent below -100 dropped),
+ * collapsed by W and squared and summed in a fixed order.  ages_host /
+ * info_host: host arrays of n_ages (1..4096); h > 0.  The result feeds
+ * rtt_reach for the mixed arm's reach and J_old.  Allocates device scratch
+ * (arm rows x frames x 16 doubles, twice); synchronous.
+ * Errors: RTT_EINVAL, RTT_ENOMEM, RTT_ECUDA.
+ */
+rtt_status rtt_probe_info_mix(rtt_op op, int arm_mask, int mode, int n_ages,
+                              const double* ages_host, double h, double* info_host, void* stream);
+
+/*
  * rtt_gram_normal_mix -- the restricted Gram of a mixed arm (Eq. 4, Eq. 7):
  * G = Q^T A^T W^T W A Q with W the whitened collapse of `mode` above, by the
  * route of rtt_gram_normal with the collapse and its adjoint between the

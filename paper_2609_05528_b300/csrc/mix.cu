@@ -131,6 +131,84 @@ __global__ void mix_flux_adj(int32_t R, int64_t nv, T inv, const V* __restrict__
         }
 }
 
+// probe responses of the arm's rows for a chunk of ages (Eq. 10-12):
+// y[row][f][a] = scale / N_h sum_{e in row} w_e exp(-(t_o(f) - Delta_e + a)^2
+// / (2 h^2)), FP64, terms with exponent below -100 dropped (as the probe
+// kernel does); ages past `na` in the chunk are written as zero
+__device__ __forceinline__ int mix_arm_row(const ArmSeg& s, int row_out) {
+    int r = row_out;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (i < s.n && r < s.len[i]) return s.begin[i] + r;
+        if (i < s.n) r -= s.len[i];
+    }
+    return -1;
+}
+
+template <int NA>
+__global__ void mix_probe_rows(const int32_t* __restrict__ row_ptr, const double* __restrict__ delay,
+                               const double* __restrict__ weight, ArmSeg seg, int Tn, double t0,
+                               double cadence, double inv_2h2, double wscale,
+                               const double* __restrict__ ages, int na, double* __restrict__ y) {
+    const int64_t n = (int64_t)seg.total * Tn;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int ro = (int)(i / Tn), f = (int)(i - (int64_t)ro * Tn);
+        const int row = mix_arm_row(seg, ro);
+        const double t = t0 + cadence * f;
+        double v[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) v[a] = 0.0;
+        for (int e = row_ptr[row]; e < row_ptr[row + 1]; ++e) {
+            const double tt = t - delay[e];
+            const double we = weight[e];
+#pragma unroll
+            for (int a = 0; a < NA; ++a) {
+                if (a < na) {
+                    const double d = tt + ages[a];
+                    const double arg = d * d * inv_2h2;
+                    if (arg < 100.0) v[a] += we * exp(-arg);
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) y[i * NA + a] = wscale * v[a];
+    }
+}
+
+// sum over entries i of y[i][a]^2 per age a: block b takes the entries
+// [b per_block, (b + 1) per_block), its threads NA ages x (blockDim / NA)
+// strided lanes, then a fixed tree over the lanes in shared memory
+template <int NA>
+__global__ void mix_sumsq_part(int64_t N, int64_t per_block, const double* __restrict__ y,
+                               double* __restrict__ part) {
+    __shared__ double sh[256];
+    const int a = threadIdx.x % NA, lane = threadIdx.x / NA, nl = blockDim.x / NA;
+    const int64_t i0 = (int64_t)blockIdx.x * per_block;
+    const int64_t i1 = min(N, i0 + per_block);
+    double s = 0.0;
+    for (int64_t i = i0 + lane; i < i1; i += nl) {
+        const double v = y[i * NA + a];
+        s += v * v;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = nl / 2; off > 0; off >>= 1) {
+        if (lane < off) sh[threadIdx.x] += sh[threadIdx.x + off * NA];
+        __syncthreads();
+    }
+    if (lane == 0) part[(int64_t)blockIdx.x * NA + a] = sh[a];
+}
+
+template <int NA>
+__global__ void mix_sumsq_final(int nb, const double* __restrict__ part, double* __restrict__ out) {
+    const int a = threadIdx.x;
+    if (a >= NA) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[(int64_t)b * NA + a];
+    out[a] = s;
+}
+
 static int grid_cap(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>(n, 1), 65535); }
 
 // the arm's rows grouped by pixel (host build on first use for an arm mask)
@@ -332,4 +410,63 @@ extern "C" rtt_status rtt_mix_rows_f64(rtt_op op, int arm_mask, int mode, const 
 extern "C" rtt_status rtt_mix_rows_T_f64(rtt_op op, int arm_mask, int mode, const double* yl_dev,
                                          double* y_dev, int batch, void* stream) {
     return mix_call<double>(op, arm_mask, mode, yl_dev, y_dev, batch, true, stream);
+}
+
+extern "C" rtt_status rtt_probe_info_mix(rtt_op op, int arm_mask, int mode, int n_ages,
+                                         const double* ages_host, double h, double* info_host,
+                                         void* stream) {
+    if (!op || !ages_host || !info_host || n_ages < 1 || n_ages > 4096 || !(h > 0.0) ||
+        (mode != RTT_MIX_UNRESOLVED && mode != RTT_MIX_TOTAL_FLUX)) {
+        set_error("invalid mixed-probe arguments (mode=%d n_ages=%d h=%g)", mode, n_ages, h);
+        return RTT_EINVAL;
+    }
+    ArmSeg seg;
+    rtt_status s = make_seg(op, arm_mask, &seg);
+    if (s == RTT_OK) s = mix_prepare(op, seg);
+    if (s != RTT_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    constexpr int NA = 16;
+    const int Tn = op->time.n_frames;
+    const int64_t Ra = seg.total, Rl = mix_out_rows(op, seg, mode);
+    if (Ra == 0) {
+        for (int i = 0; i < n_ages; ++i) info_host[i] = 0.0;
+        return RTT_OK;
+    }
+    const int64_t N = Rl * Tn;  // mixed (row, frame) entries
+    const int nb = (int)std::min<int64_t>(1024, std::max<int64_t>(1, (N + 4095) / 4096));
+    const int64_t per_block = (N + nb - 1) / nb;
+    double *ages = nullptr, *y = nullptr, *yl = nullptr, *part = nullptr, *info = nullptr;
+    cudaError_t e = cudaMalloc(&ages, (size_t)n_ages * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&y, (size_t)Ra * Tn * NA * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&yl, (size_t)std::max<int64_t>(N, 1) * NA * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&part, (size_t)nb * NA * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&info, NA * 8);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ages, ages_host, (size_t)n_ages * 8, cudaMemcpyHostToDevice, st);
+    const double Nh = std::sqrt(M_PI * (op->grid.r_out * op->grid.r_out - op->grid.r_in * op->grid.r_in) *
+                                h * std::sqrt(M_PI));
+    for (int c0 = 0; e == cudaSuccess && c0 < n_ages; c0 += NA) {
+        const int na = std::min(NA, n_ages - c0);
+        mix_probe_rows<NA><<<grid_cap((Ra * Tn + 255) / 256), 256, 0, st>>>(
+            op->row_ptr, op->delay, op->weight, seg, Tn, op->time.t0, op->time.cadence,
+            1.0 / (2.0 * h * h), op->scale / Nh, ages + c0, na, y);
+        e = cudaGetLastError();
+        if (e == cudaSuccess &&
+            launch_mix<double>(op, seg, mode, y, yl, (int64_t)Tn * NA, false, st) != RTT_OK)
+            e = cudaErrorUnknown;
+        if (e == cudaSuccess) {
+            mix_sumsq_part<NA><<<nb, 256, 0, st>>>(N, per_block, yl, part);
+            mix_sumsq_final<NA><<<1, 32, 0, st>>>(nb, part, info);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(info_host + c0, info, (size_t)na * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    for (double* p : {ages, y, yl, part, info})
+        if (p) cudaFree(p);
+    if (e != cudaSuccess) {
+        set_error("mixed probe information: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? RTT_ENOMEM : RTT_ECUDA;
+    }
+    return RTT_OK;
 }

@@ -143,6 +143,8 @@ _SIGS = {
                                       ctypes.c_int, vp, vp]),
     "rtt_gram_normal": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
     "rtt_gram_normal_mix": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
+    "rtt_probe_info_mix": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
+                                          ctypes.c_double, dp, vp]),
     "rtt_mix_rows_count": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int64)]),
     "rtt_mix_rows": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
@@ -536,6 +538,16 @@ def solve_tsvd(op: "Operator", Q, V, evals, rank: int, data, arm_mask: int = 7, 
                                ctypes.c_void_p(data.data_ptr()), n_rhs,
                                ctypes.c_void_p(xh.data_ptr()), _stream(stream)), "rtt_solve_tsvd")
     return xh
+
+
+def probe_info_mix(op: "Operator", mode: int, arm_mask: int = 7, ages=AGES, h: float = 3.0,
+                   stream=None):
+    """rtt_probe_info_mix: I_L(a) of the mixed arm `mode` (Eq. 4 with Eq. 10-12)."""
+    ages = np.ascontiguousarray(ages, np.float64)
+    info = np.empty(ages.shape[0])
+    check(lib().rtt_probe_info_mix(op.handle, arm_mask, mode, ages.shape[0], _ptr(ages, dp), h,
+                                   _ptr(info, dp), _stream(stream)), "rtt_probe_info_mix")
+    return info
 
 
 def gram_normal_mix(op: "Operator", Q, mode: int, arm_mask: int = 7, stream=None):

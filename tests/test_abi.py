@@ -85,3 +85,13 @@ def test_mix_rejects_invalid_arguments_on_host(L):
     assert L.rtt_mix_rows_T_f64(None, 7, 2, None, None, 1, None) == -1
     assert L.rtt_gram_normal_mix(None, 7, 3, None, 4, None, None) == -1
     assert L.rtt_gram_normal_mix(None, 7, 1, None, 4, None, None) == -1
+
+
+def test_mixed_probe_rejects_invalid_arguments_on_host(L):
+    ages = np.zeros(4)
+    info = np.zeros(4)
+    dp = ctypes.POINTER(ctypes.c_double)
+    a = ages.ctypes.data_as(dp)
+    i = info.ctypes.data_as(dp)
+    assert L.rtt_probe_info_mix(None, 7, 1, 4, a, 3.0, i, None) == -1
+    assert L.rtt_probe_info_mix(None, 7, 5, 4, a, 3.0, i, None) == -1

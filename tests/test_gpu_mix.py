@@ -116,3 +116,34 @@ def test_mixed_gram(schw, mode):
     Gr = rtt.gram(op, Q, mode=rtt.GRAM_NORMAL).cpu().numpy()
     lr, ll = np.linalg.eigvalsh(Gr), np.linalg.eigvalsh(G)
     assert np.all(ll <= lr + 1e-9 * lr.max())
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("mask", [7, 3, 1])
+def test_mixed_probe_info_small(schw, mode, mask):
+    """rtt_probe_info_mix against the oracle's mixed probe information on all
+    64 ages, and (direct arm, unresolved) the plain probe information."""
+    w, tab, op = schw
+    got = rtt.probe_info_mix(op, mode, mask)
+    ref = O.mix_probe_info(w, tab, O.scale(tab), mode, ARMS[mask])
+    assert _rel(got, ref) <= 1e-10
+    if mask == 1 and mode == O.MIX_UNRESOLVED:  # one row per pixel: no collapse
+        assert _rel(got, O.probe_info(w, tab.select((0,)), O.scale(tab))) <= 1e-10
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_mixed_probe_info_kerr256(k256, mode):
+    """The benchmark's sizes on eight ages spanning the history (the oracle
+    evaluates every (ray, frame) term per age), and the mixed arm's reach and
+    J_old from rtt_reach."""
+    w, tab, op = k256
+    ages = np.array([0.0, 20.0, 40.0, 60.0, 92.0, 128.0, 200.0, 252.0])
+    got = rtt.probe_info_mix(op, mode, 7, ages)
+    ref = O.mix_probe_info(w, tab, O.scale(tab), mode, (0, 1, 2), ages)
+    assert _rel(got, ref) <= 1e-10
+    full = rtt.probe_info_mix(op, mode, 7)
+    res = rtt.probe_info(op, 7)
+    # rtt_probe_info evaluates in FP32 (its old tail underflows): bound with a floor
+    assert np.all(full <= res * (1 + 1e-5) + 1e-6 * res.max())
+    r, passed = rtt.reach(op, full, 7, a0q=5.0)
+    assert r.J_old >= 0 and passed.shape == full.shape
