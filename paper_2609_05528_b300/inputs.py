@@ -291,6 +291,29 @@ def uniform_batch(w: Workload, seeds) -> np.ndarray:
                     axis=-1)
 
 
+def order_permutation(order, seed: int) -> np.ndarray:
+    """A seeded permutation of ray indices that sends every ray to a ray of the
+    same order: within each order, the rays sorted by a seeded uniform key.
+    The pairing-destroyed control (Sec. 6.4) takes its delays through it."""
+    order = np.asarray(order)
+    u = uniforms(seed, order.size)
+    perm = np.arange(order.size)
+    for n in np.unique(order):
+        idx = np.nonzero(order == n)[0]
+        perm[idx] = idx[np.argsort(u[idx], kind="stable")]
+    return perm
+
+
+def with_permuted_delays(table: dict, seed: int) -> dict:
+    """Copy of a ray table (dict of arrays) whose delays are redrawn by
+    order_permutation: each order keeps its delay values (the old-delay
+    marginals) while their pairing with source point and weight is destroyed
+    (the pairing-destroyed control of Sec. 6.4)."""
+    out = dict(table)
+    out["delay"] = np.asarray(table["delay"])[order_permutation(table["order"], seed)]
+    return out
+
+
 def noise(shape, seed: int) -> np.ndarray:
     """i.i.d. N(0, 1) whitened noise of the given shape."""
     n = int(np.prod(shape))

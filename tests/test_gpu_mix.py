@@ -147,3 +147,23 @@ def test_mixed_probe_info_kerr256(k256, mode):
     assert np.all(full <= res * (1 + 1e-5) + 1e-6 * res.max())
     r, passed = rtt.reach(op, full, 7, a0q=5.0)
     assert r.J_old >= 0 and passed.shape == full.shape
+
+
+def test_pairing_destroyed_operator(schw):
+    """The operator built from the pairing-destroyed table (delays permuted
+    within each order) against the oracle on the same permuted table, and its
+    probe information against the oracle's."""
+    import dataclasses
+    w, tab, _ = schw
+    perm = I.order_permutation(tab.order, 7)
+    tp = dataclasses.replace(tab, delay=tab.delay[perm])
+    op = rtt.Operator(w, I.with_permuted_delays(_optable(tab), 7))
+    x = I.uniform_batch(w, range(3))
+    scl = O.scale(tp)
+    assert abs(op.scale / scl - 1.0) < 1e-12
+    y = op.apply_A(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert _rel(y, O.apply_A(w, tp, x, scl)) <= 1e-12
+    info = rtt.probe_info(op, 7)
+    ref = O.probe_info(w, tp, scl)
+    assert _rel(info, ref) <= 1e-5
+    op.close()

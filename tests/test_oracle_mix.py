@@ -132,3 +132,18 @@ def test_mixed_probe_below_resolved(schw, mode):
     res = O.probe_info(w, tab, scl)
     assert np.all(got <= res * (1 + 1e-12))
     assert np.any(got < 0.999 * res)
+
+
+def test_pairing_destroyed_keeps_marginals(schw):
+    """The pairing-destroyed control's delays: each order keeps its multiset of
+    delays, rays move only within their order, and the pairing changes."""
+    w, tab = schw
+    perm = I.order_permutation(tab.order, 11)
+    assert np.all(tab.order[perm] == tab.order)
+    for n in range(3):
+        m = tab.order == n
+        np.testing.assert_array_equal(np.sort(tab.delay[perm][m]), np.sort(tab.delay[m]))
+    assert np.count_nonzero(perm != np.arange(perm.size)) > perm.size // 2
+    d = I.with_permuted_delays({"order": tab.order, "delay": tab.delay}, 11)
+    np.testing.assert_array_equal(d["delay"], tab.delay[perm])
+    assert np.array_equal(I.order_permutation(tab.order, 11), perm)  # seeded
