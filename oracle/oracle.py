@@ -471,6 +471,78 @@ def mix_probe_info(w, table: Table, scl: float, mode: int, orders=(0, 1, 2), age
     return out
 
 
+N_LOCAL = 28  # 4 radial x 7 azimuthal localized directions (Eq. 14)
+
+
+def local_direction_norms(w, h: float = PROBE_H) -> np.ndarray:
+    """N_{h,l} of Eq. 14: each direction psi_l(r, phi) = R_i(r) Phi_m(phi)
+    (l = 7 i + m; R_i the cubic Bernstein polynomials in the log-radius
+    coordinate, Phi in {1, cos phi, sin phi, ..., cos 3 phi, sin 3 phi})
+    normalised to unit L2 norm under the equatorial area measure r dr dphi
+    times the Gaussian's h sqrt(pi) (the scalar probe's Eq. 11 convention):
+    N^2 = int R_i^2 r dr * int Phi_m^2 dphi * h sqrt(pi), by quadrature."""
+    from scipy import integrate
+    g = w.grid
+    L = math.log(g.r_out / g.r_in)
+    rad = []
+    for i in range(4):
+        def f(r, i=i):
+            s = math.log(r / g.r_in) / L
+            return (math.comb(3, i) * s ** i * (1 - s) ** (3 - i)) ** 2 * r
+        rad.append(integrate.quad(f, g.r_in, g.r_out, epsabs=0, epsrel=1e-13, limit=200)[0])
+    az = [2 * math.pi] + [math.pi] * 6
+    return np.array([math.sqrt(rad[i] * az[m] * h * math.sqrt(math.pi))
+                     for i in range(4) for m in range(7)])
+
+
+def local_direction_values(w, r: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    """psi_l at source points (r, phi), unnormalised, [points, 28]."""
+    g = w.grid
+    s = np.log(np.asarray(r) / g.r_in) / math.log(g.r_out / g.r_in)
+    R = np.stack([math.comb(3, i) * s ** i * (1 - s) ** (3 - i) for i in range(4)], axis=1)
+    ph = np.asarray(phi)
+    P = [np.ones_like(ph)]
+    for m in (1, 2, 3):
+        P += [np.cos(m * ph), np.sin(m * ph)]
+    P = np.stack(P, axis=1)
+    return (R[:, :, None] * P[:, None, :]).reshape(-1, 28)
+
+
+def local_probe_responses(w, table: Table, a: float, orders=(0, 1, 2), h: float = PROBE_H):
+    """Whitened responses (before scale) of the 28 localized probes q_{a,l} of
+    Eq. 14 on the rows of `orders`: Y[l, row, f] = sum_{e in row} w_e
+    1_[r_in, r_out](r_e) psi_l(r_e, phi_e) / N_{h,l} exp(-(t + a)^2/(2h^2)),
+    t = t_o(f) - Delta_e.  numpy."""
+    sel = np.nonzero(np.isin(table.row_order, tuple(orders)))[0]
+    counts = table.row_ptr[sel + 1] - table.row_ptr[sel]
+    rays = np.concatenate([np.arange(table.row_ptr[i], table.row_ptr[i + 1]) for i in sel])
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]])
+    g = w.grid
+    ind = ((table.r[rays] >= g.r_in) & (table.r[rays] <= g.r_out)).astype(np.float64)
+    psi = local_direction_values(w, table.r[rays], table.phi[rays]) / local_direction_norms(w, h)
+    coef = (table.weight[rays] * ind)[:, None] * psi  # [rays, 28]
+    t = w.time.frame_times()[None, :] - table.delay[rays][:, None]
+    gauss = np.exp(-(t + a) ** 2 / (2.0 * h * h))  # [rays, T]
+    contrib = coef.T[:, :, None] * gauss[None, :, :]  # [28, rays, T]
+    return np.add.reduceat(contrib, starts, axis=1)  # [28, rows, T]
+
+
+def local_probe_info(w, table: Table, scl: float, orders=(0, 1, 2), ages=AGES,
+                     h: float = PROBE_H) -> np.ndarray:
+    """I_l(a) = scl^2 || Y_l(a) ||^2 per age and direction, [ages, 28] (the
+    diagonal of the age-local Fisher matrix M(a) = P(a)^T P(a), Sec. 3.3)."""
+    return np.stack([scl * scl * np.sum(local_probe_responses(w, table, a, orders, h) ** 2,
+                                        axis=(1, 2)) for a in np.asarray(ages, np.float64)])
+
+
+def local_reach(info_local: np.ndarray, rho: float = 1.0, ages=AGES):
+    """Localized directional reach: the deepest age at which at least one
+    normalised localized direction passes, I_l(a) >= rho^2 (Sec. 3.3, the
+    table of reported quantities); None if none passes."""
+    ok = np.any(np.asarray(info_local) >= rho * rho, axis=1)
+    return float(np.asarray(ages)[np.nonzero(ok)[0][-1]]) if ok.any() else None
+
+
 def probe_norm_const(w, h: float = PROBE_H) -> float:
     """N_h of Eq. 11."""
     g = w.grid

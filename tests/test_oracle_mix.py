@@ -147,3 +147,33 @@ def test_pairing_destroyed_keeps_marginals(schw):
     d = I.with_permuted_delays({"order": tab.order, "delay": tab.delay}, 11)
     np.testing.assert_array_equal(d["delay"], tab.delay[perm])
     assert np.array_equal(I.order_permutation(tab.order, 11), perm)  # seeded
+
+
+def test_local_direction_norms_by_2d_quadrature(schw):
+    """N_{h,l}^2 / (h sqrt(pi)) equals the area integral of psi_l^2 over the
+    annulus, computed here as one 2D integral in (r, phi)."""
+    from scipy import integrate
+    w, _ = schw
+    g = w.grid
+    N = O.local_direction_norms(w)
+    for l in (0, 3, 9, 20, 27):
+        f = lambda ph, r, l=l: O.local_direction_values(w, np.array([r]), np.array([ph]))[0, l] ** 2 * r
+        area, _ = integrate.dblquad(f, g.r_in, g.r_out, 0.0, 2 * math.pi, epsabs=0, epsrel=1e-10)
+        assert abs(N[l] ** 2 / (O.PROBE_H * math.sqrt(math.pi)) / area - 1.0) < 1e-8
+
+
+def test_local_directions_rebuild_the_scalar_probe(schw):
+    """The radial Bernstein polynomials sum to one, so the four l = 0
+    directions, each times N_{h,(i,0)} / N_h, add up to the scalar probe q_a:
+    their responses rebuild the scalar probe information (C oracle)."""
+    w, tab = schw
+    scl = O.scale(tab)
+    N = O.local_direction_norms(w)
+    Nh = O.probe_norm_const(w)
+    ages = [0.0, 8.0, 24.0]
+    for a, want in zip(ages, O.probe_info(w, tab, scl, ages)):
+        Y = O.local_probe_responses(w, tab, a)
+        ys = sum(Y[7 * i] * N[7 * i] / Nh for i in range(4))
+        assert abs(scl * scl * np.sum(ys ** 2) / want - 1.0) < 1e-12
+    loc = O.local_probe_info(w, tab, scl, ages=ages)
+    assert loc.shape == (3, 28) and np.all(loc >= 0)
