@@ -602,6 +602,30 @@ def run_audit(device):
                                  "median_J_old": float(np.median([r.reach.J_old for r in pdr])),
                                  "seconds_with_build": round(time.perf_counter() - t, 3)}
     out["mechanism_arms"] = mech
+    # threshold sweep at the reconstruction geometry a = 0.5, i = 50 deg (Sec.
+    # 3.3, Table 2): detectability depends on rho / SNR_0 only, so a threshold
+    # rho at SNR_0 = 100 is rho = 1 on I(a) / rho^2; anchor-connected spans
+    sweep = []
+    for (w, _), op in zip(cells, ops):
+        if abs(w.geometry.spin - 0.5) < 1e-9 and abs(w.geometry.incl_deg - 50.0) < 1e-9:
+            inf = {m: rtt.probe_info(op, m) for m in (1, 7)}
+            for rho in (10.0 / 3.0, 1.0, 1.0 / 3.0):
+                sweep.append({"rho": round(rho, 3), "equivalent_snr0": round(100.0 / rho, 1),
+                              "direct_span": rtt.reach(op, inf[1] / rho ** 2, 1)[0].L_anchor,
+                              "resolved_span": rtt.reach(op, inf[7] / rho ** 2, 7)[0].L_anchor})
+    out["threshold_sweep_a0.5_i50"] = sweep
+    # localized directional reach (Sec. 3.3 Eq. 14) at the same geometry: the
+    # oldest age at which one of the 28 normalised directions passes (rho = 1)
+    loc = {}
+    for (w, _), op in zip(cells, ops):
+        if abs(w.geometry.spin - 0.5) < 1e-9 and abs(w.geometry.incl_deg - 50.0) < 1e-9:
+            t = time.perf_counter()
+            for name, m in (("direct", 1), ("resolved", 7)):
+                il = rtt.probe_info_local(op, m)
+                ok = np.nonzero(np.any(il >= 1.0, axis=1))[0]
+                loc[name] = float(rtt.AGES[ok[-1]]) if ok.size else None
+            loc["seconds"] = round(time.perf_counter() - t, 3)
+    out["localized_reach_a0.5_i50"] = loc
     for op in ops:
         op.close()
     return out

@@ -418,6 +418,24 @@ rtt_status rtt_probe_info_mix(rtt_op op, int arm_mask, int mode, int n_ages,
                               const double* ages_host, double h, double* info_host, void* stream);
 
 /*
+ * rtt_probe_info_local -- per-direction information of the 28-direction
+ * localized probe class (Sec. 3.3 Eq. 14): q_{a,l} = psi_l(r, phi) / N_{h,l}
+ * exp(-(t + a)^2 / (2 h^2)), psi_l = R_i(r) Phi_m(phi) (l = 7 i + m; R_i
+ * the cubic Bernstein polynomials in the log-radius coordinate, Phi_m in
+ * {1, cos phi, sin phi, cos 2 phi, sin 2 phi, cos 3 phi, sin 3 phi}), each
+ * of unit L2 norm under r dr dphi dt; I_l(a) = || scale A_arm q_{a,l} ||^2,
+ * the diagonal of the age-local Fisher matrix.  Evaluated at each ray's
+ * source point, FP64, per row through the rays' Gaussian overlap sums (rows
+ * of at most 4 rays; terms with exponent below -100 dropped), fixed-order
+ * reductions.  info_host: host [n_ages][28].  The localized directional
+ * reach is the oldest age at which some I_l(a) >= rho^2.  Allocates device
+ * scratch; synchronous.  Errors: RTT_EINVAL, RTT_ESTATE (a row with more than
+ * 4 rays), RTT_ENOMEM, RTT_ECUDA.
+ */
+rtt_status rtt_probe_info_local(rtt_op op, int arm_mask, int n_ages, const double* ages_host,
+                                double h, double* info_host, void* stream);
+
+/*
  * rtt_gram_normal_mix -- the restricted Gram of a mixed arm (Eq. 4, Eq. 7):
  * G = Q^T A^T W^T W A Q with W the whitened collapse of `mode` above, by the
  * route of rtt_gram_normal with the collapse and its adjoint between the

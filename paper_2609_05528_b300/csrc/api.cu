@@ -99,6 +99,7 @@ struct PrepArgs {
     int32_t* F0;
     double* F64;
     double* r_s;
+    double* phi_s;
     double* delay_s;
     double* weight_s;
     double* thr_s;
@@ -146,6 +147,7 @@ __global__ void prep_rays(const PrepArgs a) {
     a.F0[i] = (int32_t)fq;
     a.F64[i] = frac;
     a.r_s[i] = r;
+    a.phi_s[i] = phi;
     a.delay_s[i] = dl;
     a.weight_s[i] = w;
     a.thr_s[i] = a.thr[o];
@@ -233,7 +235,7 @@ static void free_op(rtt_op_s* op) {
                   op->visits,  op->items,    op->split_tiles, op->fpartial, op->node_order,
                   op->dev_status, op->rscratch, op->row_pixel, op->mix.grp_ptr,
                   op->mix.grp_rows, op->mix.row_grp, op->mix.inv32, op->mix.inv64,
-                  op->mix.part};
+                  op->mix.part, op->phi};
     for (void* p : ps)
         if (p) cudaFree(p);
     delete op;
@@ -392,6 +394,7 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
 
     // ---- s_ref (Eq. 17, j_ref = 1 evaluated directly) ----
     RTT_TRY(alloc(&op->r, E));
+    RTT_TRY(alloc(&op->phi, E));
     RTT_TRY(alloc(&op->delay, E));
     RTT_TRY(alloc(&op->weight, E));
     RTT_TRY(alloc(&op->thr, E));
@@ -427,6 +430,7 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
     pa.F0 = op->F0;
     pa.F64 = op->F64;
     pa.r_s = op->r;
+    pa.phi_s = op->phi;
     pa.delay_s = op->delay;
     pa.weight_s = op->weight;
     pa.thr_s = op->thr;

@@ -84,6 +84,7 @@ struct rtt_op_s {
     int32_t* F0 = nullptr;        // [E] floor(frac(u0) * 2^24)
     double* F64 = nullptr;        // [E] frac(u0) exactly
     double* r = nullptr;          // [E] FP64 copies for probes and quantiles
+    double* phi = nullptr;        // [E] source azimuth (localized probes)
     double* delay = nullptr;
     double* weight = nullptr;
     double* thr = nullptr;

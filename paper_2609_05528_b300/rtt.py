@@ -145,6 +145,8 @@ _SIGS = {
     "rtt_gram_normal_mix": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
     "rtt_probe_info_mix": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                           ctypes.c_double, dp, vp]),
+    "rtt_probe_info_local": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp,
+                                            vp]),
     "rtt_mix_rows_count": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_int64)]),
     "rtt_mix_rows": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
@@ -547,6 +549,16 @@ def probe_info_mix(op: "Operator", mode: int, arm_mask: int = 7, ages=AGES, h: f
     info = np.empty(ages.shape[0])
     check(lib().rtt_probe_info_mix(op.handle, arm_mask, mode, ages.shape[0], _ptr(ages, dp), h,
                                    _ptr(info, dp), _stream(stream)), "rtt_probe_info_mix")
+    return info
+
+
+def probe_info_local(op: "Operator", arm_mask: int = 7, ages=AGES, h: float = 3.0, stream=None):
+    """rtt_probe_info_local: I_l(a) of the 28 localized directions (Eq. 14),
+    [n_ages, 28]."""
+    ages = np.ascontiguousarray(ages, np.float64)
+    info = np.empty((ages.shape[0], 28))
+    check(lib().rtt_probe_info_local(op.handle, arm_mask, ages.shape[0], _ptr(ages, dp), h,
+                                     _ptr(info, dp), _stream(stream)), "rtt_probe_info_local")
     return info
 
 

@@ -95,3 +95,11 @@ def test_mixed_probe_rejects_invalid_arguments_on_host(L):
     i = info.ctypes.data_as(dp)
     assert L.rtt_probe_info_mix(None, 7, 1, 4, a, 3.0, i, None) == -1
     assert L.rtt_probe_info_mix(None, 7, 5, 4, a, 3.0, i, None) == -1
+
+
+def test_localized_probe_rejects_invalid_arguments_on_host(L):
+    ages = np.zeros(4)
+    info = np.zeros(4 * 28)
+    dp = ctypes.POINTER(ctypes.c_double)
+    assert L.rtt_probe_info_local(None, 7, 4, ages.ctypes.data_as(dp), 3.0,
+                                  info.ctypes.data_as(dp), None) == -1

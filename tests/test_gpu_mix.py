@@ -167,3 +167,52 @@ def test_pairing_destroyed_operator(schw):
     ref = O.probe_info(w, tp, scl)
     assert _rel(info, ref) <= 1e-5
     op.close()
+
+
+def _subtable(tab, rows):
+    rows = np.asarray(rows, np.int64)
+    counts = tab.row_ptr[rows + 1] - tab.row_ptr[rows]
+    idx = np.concatenate([np.arange(tab.row_ptr[i], tab.row_ptr[i + 1]) for i in rows])
+    rp = np.zeros(rows.size + 1, np.int64)
+    rp[1:] = np.cumsum(counts)
+    return O.Table(tab.order[idx], tab.pixel[idx], tab.r[idx], tab.phi[idx], tab.delay[idx],
+                   tab.weight[idx], tab.throughput[idx], rp, tab.row_order[rows],
+                   tab.row_pixel[rows], tab.sample[idx])
+
+
+@pytest.mark.parametrize("mask", [7, 1])
+def test_localized_probe_small(schw, mask):
+    """rtt_probe_info_local against the oracle's direct evaluation of the 28
+    directions (schw32: one ray per row; a supersampled Kerr case: rows of
+    up to four rays), all 64 ages, and the localized directional reach."""
+    w, tab, op = schw
+    got = rtt.probe_info_local(op, mask)
+    ref = O.local_probe_info(w, tab, O.scale(tab), ARMS[mask])
+    assert got.shape == (64, 28)
+    assert _rel(got, ref) <= 1e-10
+    ok = np.any(got >= 1.0, axis=1)
+    assert (O.AGES[np.nonzero(ok)[0][-1]] if ok.any() else None) == O.local_reach(ref)
+    wk = I.small_kerr(spin=0.5, incl_deg=50.0, nx=40, n_r=10, n_phi=20, n_frames=120, n_hats=30, ss=2)
+    tk = O.build_table(wk, I.screen_samples(wk))
+    assert np.max(tk.row_ptr[1:] - tk.row_ptr[:-1]) > 1
+    ok_ = rtt.Operator(wk, _optable(tk))
+    gk = rtt.probe_info_local(ok_, mask, O.AGES[:32])
+    rk = O.local_probe_info(wk, tk, O.scale(tk), ARMS[mask], O.AGES[:32])
+    assert _rel(gk, rk) <= 1e-10
+    ok_.close()
+
+
+def test_localized_probe_kerr256_rows(k256):
+    """kerr256 rays (2x2 sub-rays, rows of up to four rays): the operator of a
+    sample of 1500 rows against the oracle on the same rows, 16 ages."""
+    w, tab, _ = k256
+    rng = np.random.default_rng(9)
+    rows = np.unique(np.concatenate([rng.integers(0, tab.n_rows, 1500),
+                                     np.nonzero(tab.row_ptr[1:] - tab.row_ptr[:-1] == 4)[0][:200]]))
+    sub = _subtable(tab, rows)
+    op = rtt.Operator(w, _optable(sub))
+    ages = O.AGES[::4]
+    got = rtt.probe_info_local(op, 7, ages)
+    ref = O.local_probe_info(w, sub, O.scale(sub), (0, 1, 2), ages)
+    assert _rel(got, ref) <= 1e-10
+    op.close()
