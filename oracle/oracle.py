@@ -646,6 +646,58 @@ def _azimuthal(w):
     return np.stack(cols, axis=1)  # [n_phi, 7]
 
 
+# the nested ladder of Sec. 7-8 (Eq. 43): (radial, real azimuthal, temporal)
+# dimensions and the temporal family (DCT-II modes or degree-one B-splines)
+CLASS_SHAPES = {"S224": (4, 7, 8, "dct"), "L224": (4, 7, 8, "hat"),
+                "S448T": (4, 7, 16, "dct"), "S528S": (6, 11, 8, "dct"),
+                "S1056ST": (6, 11, 16, "dct"), "L448": (4, 7, 16, "hat"),
+                "L1056": (6, 11, 16, "hat")}
+
+
+def radial_bsplines(s: np.ndarray, n: int) -> np.ndarray:
+    """n clamped cubic B-splines on uniform knots in the normalised log radius
+    s in [0, 1] (n = 4: no interior knot, the cubic Bernstein basis), [len(s), n];
+    by scipy's B-spline evaluation."""
+    from scipy.interpolate import BSpline
+    inner = np.linspace(0.0, 1.0, n - 2)[1:-1]
+    t = np.concatenate([[0.0] * 4, inner, [1.0] * 4])
+    out = np.empty((np.size(s), n))
+    for i in range(n):
+        c = np.zeros(n)
+        c[i] = 1.0
+        out[:, i] = BSpline(t, c, 3, extrapolate=False)(np.clip(s, 0.0, 1.0))
+    return np.nan_to_num(out)
+
+
+def synth_class_ladder(w, kind: str) -> np.ndarray:
+    """Q of a class of the ladder as nodal values, rows s * K + k, columns
+    (i * NA + l) * NT + m: radial cubic B-splines x {1, cos m phi, sin m phi}
+    x NT temporal functions on the hat window [t_{K-1}, t_0] (DCT-II modes for
+    S classes, degree-one B-splines on uniform knots for L classes; Sec. 7,
+    Eq. 43).  Parents are literal prefixes in the azimuthal and temporal
+    indices; the radial refinement moves knots (containment, not prefix)."""
+    NR, NA, NT, fam = CLASS_SHAPES[kind]
+    g, t = w.grid, w.time
+    sr = (np.log(g.radii()) - np.log(g.r_in)) / (np.log(g.r_out) - np.log(g.r_in))
+    R = radial_bsplines(sr, NR)
+    ph = g.azimuths()
+    P = [np.ones_like(ph)]
+    for m in range(1, (NA - 1) // 2 + 1):
+        P += [np.cos(m * ph), np.sin(m * ph)]
+    P = np.stack(P, axis=1)
+    tk = t.hat_times()
+    ta, tb = tk.min(), tk.max()
+    if fam == "dct":
+        Tm = np.stack([np.cos(np.pi * m * (tk - ta) / (tb - ta)) for m in range(NT)], axis=1)
+    else:
+        step = (tb - ta) / (NT - 1)
+        Tm = np.stack([np.maximum(0.0, 1.0 - np.abs(tk - (ta + step * m)) / step) for m in range(NT)],
+                      axis=1)
+    spatial = (R[:, None, :, None] * P[None, :, None, :]).reshape(g.n_nodes, NR, NA)
+    Q = spatial[:, None, :, :, None] * Tm[None, :, None, None, :]
+    return Q.reshape(g.n_nodes * t.n_hats, NR * NA * NT)
+
+
 def synth_class(w, kind: str = "S224") -> np.ndarray:
     """Q_d as nodal values, rows s * K + k, columns (i_rad * 7 + l_az) * 8 + m.
     S224: 4 clamped cubic B-splines in log r (no interior knots: the cubic

@@ -1,0 +1,88 @@
+"""Pins of the oracle's class ladder (Sec. 7-8, Eq. 43): the radial cubic
+B-splines, the nesting of the classes, and Theorem 4.1's exactly-zero direct
+columns of the compact classes."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2609_05528_b300 import inputs as I
+
+
+def test_radial_bsplines():
+    """Partition of unity, non-negativity, n = 4 equals the Bernstein basis,
+    and the 6-function space contains the 4-function one (knot insertion)."""
+    s = np.linspace(0.0, 1.0, 401)
+    for n in (4, 6):
+        B = O.radial_bsplines(s, n)
+        np.testing.assert_allclose(B.sum(axis=1), 1.0, atol=1e-14)
+        assert np.all(B >= -1e-15)
+    B4 = O.radial_bsplines(s, 4)
+    bern = np.stack([[1, 3, 3, 1][j] * s ** j * (1 - s) ** (3 - j) for j in range(4)], axis=1)
+    np.testing.assert_allclose(B4, bern, atol=1e-14)
+    B6 = O.radial_bsplines(s, 6)
+    coef, *_ = np.linalg.lstsq(B6, B4, rcond=None)
+    assert np.max(np.abs(B6 @ coef - B4)) < 1e-13
+
+
+@pytest.fixture(scope="module")
+def small():
+    w = I.small_kerr(spin=0.5, incl_deg=50.0, nx=24, n_r=7, n_phi=12, n_frames=40, n_hats=18, ss=1)
+    return w, O.build_table(w, I.screen_samples(w))
+
+
+def test_ladder_matches_the_224_classes(small):
+    w, _ = small
+    np.testing.assert_allclose(O.synth_class_ladder(w, "S224"), O.synth_class(w, "S224"), atol=1e-13)
+    np.testing.assert_allclose(O.synth_class_ladder(w, "L224"), O.synth_class(w, "L224"), atol=1e-13)
+
+
+@pytest.mark.parametrize("parent,child", [("S224", "S448T"), ("S224", "S528S"),
+                                          ("S448T", "S1056ST"), ("S528S", "S1056ST")])
+def test_nesting(small, parent, child):
+    """Every parent column lies in the child's column space (Eq. 43)."""
+    w, _ = small
+    P = O.synth_class_ladder(w, parent)
+    C = O.synth_class_ladder(w, child)
+    coef, *_ = np.linalg.lstsq(C, P, rcond=None)
+    assert np.max(np.abs(C @ coef - P)) <= 1e-11 * np.max(np.abs(P))
+
+
+@pytest.fixture(scope="module")
+def schw():
+    w = I.schw32()  # the history ends at t = 0: older than the direct footprint
+    return w, O.build_table(w, I.screen_samples(w))
+
+
+@pytest.mark.parametrize("kind", ["L224", "L448", "L1056"])
+def test_exactly_zero_direct_columns(schw, kind):
+    """Theorem 4.1: a compact temporal function whose support misses the direct
+    footprint gives exactly zero direct response, in every one of its
+    (spatial functions) columns.  The condition is sufficient: richer classes
+    also have zero columns from joint spatial-temporal support (a spatial
+    factor vanishing on the stencils of the rays that reach a temporal
+    support), so the zero count is at least the theorem's."""
+    w, tab = schw
+    d = tab.select((0,))
+    Q = O.synth_class_ladder(w, kind)
+    P = O.restricted_response(w, d, Q, 1.0)
+    zero = np.all(P == 0.0, axis=0)
+    NR, NA, NT, _ = O.CLASS_SHAPES[kind]
+    tk = w.time.hat_times()
+    ta, tb = tk.min(), tk.max()
+    step = (tb - ta) / (NT - 1)
+    fp = O.footprints(w, tab, (0,))
+    lo = min(a for a, _ in fp)
+    hi = max(b for _, b in fp)
+    # hat times touched by the direct footprint (a hat reaches 4 M each side)
+    touched = tk[(tk > lo - w.time.hat_step) & (tk < hi + w.time.hat_step)]
+    miss = [m for m in range(NT)
+            if not np.any(np.abs(touched - (ta + step * m)) < step)]
+    assert len(miss) > 0
+    m_of_col = np.arange(Q.shape[1]) % NT
+    # Theorem 4.1: every column of a temporal function missing the footprint
+    # is exactly zero, NR * NA * |miss| of them
+    thm = [c for c in range(Q.shape[1]) if m_of_col[c] in miss]
+    assert len(thm) == NR * NA * len(miss) and all(zero[c] for c in thm)
+    # the sufficient condition is not the whole story for richer classes
+    assert zero.sum() >= len(thm)
+
