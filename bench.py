@@ -631,6 +631,52 @@ def run_audit(device):
     return out
 
 
+def run_ladder(device):
+    """The class ladder of Sec. 7-8 (Eq. 43, Tables 4-5): at the reconstruction
+    geometry (kerr256: a = 0.5, i = 50 deg) and on schw32 (whose history is
+    older than the direct footprint, so Theorem 4.1's zero columns appear),
+    per class: dimension, exactly-zero direct columns (zero diagonal of the
+    direct Gram), operational rank sigma >= 1 for the direct and resolved
+    arms, the spectrum's extremes; FP64 normal-operator Gram, FP64
+    eigenvalues."""
+    import torch
+
+    from paper_2609_05528_b300 import build, rtt
+    from paper_2609_05528_b300 import inputs as I
+    build.build()
+    kinds = [("S224", rtt.CLASS_S224), ("S448T", rtt.CLASS_S448T), ("S528S", rtt.CLASS_S528S),
+             ("S1056ST", rtt.CLASS_S1056ST), ("L224", rtt.CLASS_L224), ("L448", rtt.CLASS_L448),
+             ("L1056", rtt.CLASS_L1056)]
+    out = {"ladder": "Sec. 7-8 class ladder (Eq. 43)", "rho": 1.0, "snr0": 100.0, "workloads": []}
+    for w in (I.kerr256(), I.schw32()):
+        tab = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, I.screen_samples(w))
+        op = rtt.Operator(w, tab)
+        rows = []
+        for name, kind in kinds:
+            torch.cuda.synchronize(device)
+            t = time.perf_counter()
+            Q = rtt.synth_class(op, kind)
+            rec = {"class": name, "dim": int(Q.shape[2])}
+            for arm, tag in ((1, "direct"), (7, "resolved")):
+                G = rtt.gram(op, Q, arm, mode=rtt.GRAM_NORMAL)
+                diag_zero = int((torch.diagonal(G) == 0).sum())
+                ev = rtt.eigvals_sym_batched(G[None])[0]
+                sig = np.sqrt(np.maximum(ev, 0.0))
+                rec[tag + "_rank"] = int(np.count_nonzero(sig >= 1.0))
+                rec[tag + "_zero_columns"] = diag_zero
+                rec[tag + "_sigma_max"] = float(sig[-1])
+                rec[tag + "_sigma_min_at_or_above_rho"] = float(sig[sig >= 1.0].min()) if (sig >= 1.0).any() else None
+                del G
+            del Q
+            torch.cuda.synchronize(device)
+            rec["seconds"] = round(time.perf_counter() - t, 3)
+            rows.append(rec)
+        out["workloads"].append({"workload": w.name, "spin": w.geometry.spin,
+                                 "incl_deg": w.geometry.incl_deg, "classes": rows})
+        op.close()
+    return out
+
+
 def run_recovery(device, n_test: int = 60, n_val: int = 20, max_iter: int = 400,
                  tol: float = 1e-6):
     """Held-out recovery (Sec. 9) on Kerr a=0.94, i=50 deg at kerr256 sizes:
@@ -749,6 +795,8 @@ def main():
                     help="print the stress1024 batch sweep (one JSON line per geometry) and exit")
     ap.add_argument("--recovery", action="store_true",
                     help="print the held-out recovery leg (ridge + TSVD) as one JSON line and exit")
+    ap.add_argument("--ladder", action="store_true",
+                    help="print the class-ladder audit (Sec. 7-8) as one JSON line and exit")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -795,6 +843,11 @@ def main():
         if rank == 0:
             torch.cuda.set_device(device)
             print(json.dumps(run_recovery(device)))
+        return
+    if args.ladder:
+        if rank == 0:
+            torch.cuda.set_device(device)
+            print(json.dumps(run_ladder(device)))
         return
     out = run_ours(args, rank, world, device)
     if rank == 0 and world == 1 and not args.no_audit:

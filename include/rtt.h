@@ -316,15 +316,24 @@ rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const double* ages_hos
 
 #define RTT_CLASS_S224 0 /* Eq. 8: 4 radial B-splines x 7 azimuthal x 8 DCT-II */
 #define RTT_CLASS_L224 1 /* Sec. 7: the temporal DCT modes replaced by 8 hats */
+/* the nested ladder of Sec. 7-8 (Eq. 43): (radial, azimuthal, temporal) */
+#define RTT_CLASS_S448T 2   /* (4, 7, 16 DCT-II) */
+#define RTT_CLASS_S528S 3   /* (6 cubic B-splines, 11, 8 DCT-II) */
+#define RTT_CLASS_S1056ST 4 /* (6, 11, 16 DCT-II) */
+#define RTT_CLASS_L448 5    /* (4, 7, 16 degree-one B-splines) */
+#define RTT_CLASS_L1056 6   /* (6, 11, 16 degree-one B-splines) */
+/* rtt_class_dim -- the dimension d of class `kind` (0 for an unknown kind). */
+int rtt_class_dim(int kind);
 
 /*
- * rtt_synth_class -- the 224-column representation class at the operator's
- * source nodes (Sec. 3.2 Eq. 5-8; Sec. 7): Q[(s, k)][c] = R_i(r_s)
- * Phi_l(phi_s) tau_m(t_k), c = (i * 7 + l) * 8 + m, radial cubic B-splines
- * on uniform knots in log r (no interior knots), azimuthal {1, cos, sin}
- * up to m = 3, temporal DCT-II modes (S224) or degree-one B-splines (L224)
- * on the hat window [t_{K-1}, t_0]; columns unnormalised.  Q_dev: double
- * [n_nodes][n_hats][224], written asynchronously on `stream`.
+ * rtt_synth_class -- representation class `kind` at the operator's source
+ * nodes (Sec. 3.2 Eq. 5-8; Sec. 7-8 Eq. 43): Q[(s, k)][c] = R_i(r_s)
+ * Phi_l(phi_s) tau_m(t_k), c = (i * NA + l) * NT + m, with NR clamped cubic
+ * B-splines on uniform knots in log r (NR = 4: no interior knot), NA
+ * azimuthal functions {1, cos m phi, sin m phi}, NT temporal DCT-II modes (S
+ * classes) or degree-one B-splines (L classes) on the hat window [t_{K-1},
+ * t_0]; columns unnormalised.  Q_dev: double [n_nodes][n_hats][d], d =
+ * rtt_class_dim(kind), written asynchronously on `stream`.
  * Errors: RTT_EINVAL (unknown kind, fewer than 2 hats), RTT_ECUDA.
  */
 rtt_status rtt_synth_class(rtt_op op, int kind, double* Q_dev, void* stream);

@@ -145,6 +145,7 @@ _SIGS = {
     "rtt_gram_normal_mix": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp]),
     "rtt_probe_info_mix": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp,
                                           ctypes.c_double, dp, vp]),
+    "rtt_class_dim": (ctypes.c_int, [ctypes.c_int]),
     "rtt_probe_info_local": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, dp, ctypes.c_double, dp,
                                             vp]),
     "rtt_mix_rows_count": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int,
@@ -435,12 +436,25 @@ GRAM_CLASS_S224 = 2
 GRAM_CLASS_L224 = 3
 CLASS_S224 = 0
 CLASS_L224 = 1
+CLASS_S448T = 2
+CLASS_S528S = 3
+CLASS_S1056ST = 4
+CLASS_L448 = 5
+CLASS_L1056 = 6
+
+
+def class_dim(kind: int) -> int:
+    """rtt_class_dim: the dimension of class `kind` (0 if unknown)."""
+    return int(lib().rtt_class_dim(int(kind)))
 
 
 def synth_class(op: "Operator", kind: int = CLASS_S224, stream=None):
-    """Class matrix Q (CUDA float64 [n_nodes, n_hats, 224]) synthesised on the GPU."""
+    """Class matrix Q (CUDA float64 [n_nodes, n_hats, d]) synthesised on the GPU."""
     import torch
-    Q = torch.empty((op.n_nodes, op.n_hats, 224), dtype=torch.float64, device="cuda")
+    d = class_dim(kind)
+    if d == 0:
+        raise RttError(-1, "synth_class", f"unknown class kind {kind}")
+    Q = torch.empty((op.n_nodes, op.n_hats, d), dtype=torch.float64, device="cuda")
     check(lib().rtt_synth_class(op.handle, kind, ctypes.c_void_p(Q.data_ptr()), _stream(stream)),
           "rtt_synth_class")
     return Q

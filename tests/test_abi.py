@@ -103,3 +103,10 @@ def test_localized_probe_rejects_invalid_arguments_on_host(L):
     dp = ctypes.POINTER(ctypes.c_double)
     assert L.rtt_probe_info_local(None, 7, 4, ages.ctypes.data_as(dp), 3.0,
                                   info.ctypes.data_as(dp), None) == -1
+
+
+def test_class_dimensions(L):
+    """The ladder of Sec. 7-8: (4,7,8), (4,7,8), (4,7,16), (6,11,8), (6,11,16),
+    (4,7,16), (6,11,16) -> 224, 224, 448, 528, 1056, 448, 1056."""
+    assert [L.rtt_class_dim(k) for k in range(7)] == [224, 224, 448, 528, 1056, 448, 1056]
+    assert L.rtt_class_dim(7) == 0 and L.rtt_class_dim(-1) == 0
