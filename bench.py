@@ -671,8 +671,49 @@ def run_ladder(device):
             torch.cuda.synchronize(device)
             rec["seconds"] = round(time.perf_counter() - t, 3)
             rows.append(rec)
+        # old-structure subspace (Sec. 7, Eq. 41): the compact classes'
+        # temporal functions with exactly zero direct response in every
+        # spatial column, and, within each, the spatial coefficients
+        # orthogonal to the constant level (the four radial functions with
+        # the constant azimuthal mode sum to psi = 1); ranks of the direct,
+        # resolved and order-summed (unresolved image) arms on it
+        old = []
+        for name, kind in kinds:
+            if not name.startswith("L"):
+                continue
+            Q = rtt.synth_class(op, kind)
+            d = int(Q.shape[2])
+            nr, na = (4, 7) if d in (224, 448) else (6, 11)
+            nt = d // (nr * na)
+            Gd = rtt.gram(op, Q, 1, mode=rtt.GRAM_NORMAL).cpu().numpy()
+            Gr = rtt.gram(op, Q, 7, mode=rtt.GRAM_NORMAL).cpu().numpy()
+            Gu = rtt.gram_normal_mix(op, Q, rtt.MIX_UNRESOLVED, 7).cpu().numpy()
+            del Q
+            zero = np.diag(Gd) == 0.0
+            old_m = [m for m in range(nt) if all(zero[sp * nt + m] for sp in range(nr * na))]
+            if not old_m:
+                old.append({"class": name, "old_temporal_functions": 0})
+                continue
+            lev = np.zeros(nr * na)
+            lev[[i * na for i in range(nr)]] = 1.0
+            lev /= np.linalg.norm(lev)
+            B = np.linalg.svd(np.eye(nr * na) - np.outer(lev, lev))[0][:, :nr * na - 1]
+            C = np.zeros((d, len(old_m) * (nr * na - 1)))
+            for j, m in enumerate(old_m):
+                for sp in range(nr * na):
+                    C[sp * nt + m, j * (nr * na - 1):(j + 1) * (nr * na - 1)] = B[sp]
+            Gs = torch.from_numpy(np.stack([C.T @ G @ C for G in (Gd, Gr, Gu)])).to(device)
+            ev = rtt.eigvals_sym_batched(Gs)
+            sig = np.sqrt(np.maximum(ev, 0.0))
+            old.append({"class": name, "old_temporal_functions": len(old_m),
+                        "dim": int(C.shape[1]),
+                        "direct_rank": int(np.count_nonzero(sig[0] >= 1.0)),
+                        "direct_sigma_max": float(sig[0][-1]),
+                        "resolved_rank": int(np.count_nonzero(sig[1] >= 1.0)),
+                        "order_summed_rank": int(np.count_nonzero(sig[2] >= 1.0))})
         out["workloads"].append({"workload": w.name, "spin": w.geometry.spin,
-                                 "incl_deg": w.geometry.incl_deg, "classes": rows})
+                                 "incl_deg": w.geometry.incl_deg, "classes": rows,
+                                 "old_structure": old})
         op.close()
     return out
 
