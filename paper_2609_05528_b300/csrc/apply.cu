@@ -1490,8 +1490,12 @@ fwd5_kernel(const __grid_constant__ CUtensorMap xmap, const ApplyArgs<float> a, 
 //    load, staged store and hat read is a base address plus an immediate;
 //  * range tests only where a window or a chunk reaches past the hats or the
 //    frames (a uniform branch per ray or task).
+// 4-warp CTAs (4 per SM at <= 128 registers): the same occupancy as 8-warp
+// CTAs, finer blocks for the resident grid's tail (measured faster)
+constexpr int kFwd7Warps = 4;
+constexpr int kFwd7MinBlocks = 4;
 template <int BC, int FPL, int P>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
+__global__ void __launch_bounds__(kFwd7Warps * 32, kFwd7MinBlocks)
 fwd7_kernel(const ApplyArgs<float> a) {
     static_assert(BC == 4 || BC == 8, "16-byte batch records, one chunk");
     constexpr int Q = BC / 4;
@@ -1501,11 +1505,11 @@ fwd7_kernel(const ApplyArgs<float> a) {
     constexpr int NU = (ZW * Q + 31) / 32;  // staging items per lane
     constexpr int HS = 32 / P;             // hat steps per 32 frames
     constexpr int32_t D = kFracOne / P;
-    __shared__ __align__(16) float4 zs_all[kWarpsPerBlock][ZW * Q];
+    __shared__ __align__(16) float4 zs_all[kFwd7Warps][ZW * Q];
     float4* zsv = zs_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
-    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
+    const int64_t warp_global = (int64_t)blockIdx.x * kFwd7Warps + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kFwd7Warps;
     const int64_t KB = (int64_t)a.K * BC;  // floats per node row of x
     // this lane's staging items o = lane + 32 u: hat lane / Q + (32 / Q) u, record lane % Q
     const int kk0 = lane / Q, q0 = lane % Q;
@@ -2598,8 +2602,8 @@ static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st) {
     a.n_tasks = (int64_t)a.seg.total * a.n_fchunk;
     if (a.n_tasks == 0) return cudaSuccess;
     auto go = [&](auto kern) {
-        const int grid = resident_grid(kern, kWarpsPerBlock * 32, 0, a.n_tasks, kWarpsPerBlock);
-        kern<<<grid, kWarpsPerBlock * 32, 0, st>>>(a);
+        const int grid = resident_grid(kern, kFwd7Warps * 32, 0, a.n_tasks, kFwd7Warps);
+        kern<<<grid, kFwd7Warps * 32, 0, st>>>(a);
         return cudaGetLastError();
     };
     switch (P) {
