@@ -176,6 +176,29 @@ __device__ __forceinline__ void fmac2x2(float a, const float4& v, float& c0, flo
 
 constexpr int kWarpsPerBlock = 8;
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialisation may be scheduled while the previous kernel in its stream is
+// still finishing; it waits here, before touching any global memory, until
+// that kernel has completed and its writes are visible.  Without the launch
+// attribute the wait returns at once.
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Grid-stride walk over (output row, frame chunk, batch chunk) tasks, batch
 // chunk fastest (task = (row nf + f) nb + b).  The first task and the stride
 // are split into those digits once; each step adds the stride's digits with
@@ -1134,6 +1157,7 @@ template <int BC, int P, int HG>
 __global__ void __launch_bounds__(kAdj6Warps * 32)
 adj_time6_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float> a, int* status) {
     static_assert(BC == 4 || BC == 8 || BC == 16 || BC == 32, "128-byte rows of whole frames");
+    wait_prior_grid();
     constexpr int F = T6Box<BC, P, HG>::kF;
     constexpr int LGF = F == 1 ? 0 : (F == 2 ? 1 : (F == 4 ? 2 : 3));
     constexpr uint32_t BOX_BYTES = T6Box<BC, P, HG>::kBytes;
@@ -1498,6 +1522,7 @@ template <int BC, int FPL, int P>
 __global__ void __launch_bounds__(kFwd7Warps * 32, kFwd7MinBlocks)
 fwd7_kernel(const ApplyArgs<float> a) {
     static_assert(BC == 4 || BC == 8, "16-byte batch records, one chunk");
+    wait_prior_grid();
     constexpr int Q = BC / 4;
     constexpr int FC = 32 * FPL;
     static_assert(FC % P == 0, "chunks start on whole hat steps");
@@ -2230,6 +2255,7 @@ template <int BC, int kSpace4Unroll = 4>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
 adj_space4_kernel(const ApplyArgs<float> a) {
     static_assert(BC % 4 == 0, "vector path needs 4 | BC");
+    wait_prior_grid();
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
@@ -2518,8 +2544,8 @@ static cudaError_t launch_adj6(ApplyArgs<float> t, int* status, cudaStream_t st)
         if (e != cudaSuccess) return e;
         const int grid =
             resident_grid(adj_time6_kernel<BC, P, HG>, kAdj6Warps * 32, smem, t.n_tasks, kAdj6Warps);
-        adj_time6_kernel<BC, P, HG><<<grid, kAdj6Warps * 32, smem, st>>>(m, t, status);
-        return cudaGetLastError();
+        return launch_dependent(adj_time6_kernel<BC, P, HG>, dim3(grid), dim3(kAdj6Warps * 32), smem, st,
+                                m, t, status);
     }
 }
 
@@ -2603,8 +2629,7 @@ static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st) {
     if (a.n_tasks == 0) return cudaSuccess;
     auto go = [&](auto kern) {
         const int grid = resident_grid(kern, kFwd7Warps * 32, 0, a.n_tasks, kFwd7Warps);
-        kern<<<grid, kFwd7Warps * 32, 0, st>>>(a);
-        return cudaGetLastError();
+        return launch_dependent(kern, dim3(grid), dim3(kFwd7Warps * 32), 0, st, a);
     };
     switch (P) {
         case 2: return go(fwd7_kernel<BC, FPL, 2>);
@@ -2828,7 +2853,8 @@ static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStr
     if constexpr (sizeof(T) == 4 && BC % 4 == 0) {
         if (v.space >= 2 && a.Bc == BC && vec_ok(a)) {
             if (v.space == 3)  // eight incidences in flight per lane
-                adj_space4_kernel<BC, 8><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
+                return launch_dependent(adj_space4_kernel<BC, 8>, dim3(grid_for(a.n_tasks)),
+                                        dim3(kWarpsPerBlock * 32), 0, st, a);
             else
                 adj_space4_kernel<BC, 4><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
             return cudaGetLastError();
