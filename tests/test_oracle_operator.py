@@ -263,3 +263,29 @@ def test_ridge_cg_against_dense_solve(tiny_kerr):
     assert np.allclose(x.reshape(-1), ref, rtol=1e-9, atol=1e-11 * np.abs(ref).max())
     res = D.T @ (D @ x.reshape(-1)) + 0.3 * x.reshape(-1) - D.T @ data.reshape(-1)
     assert np.linalg.norm(res) <= 1e-10 * np.linalg.norm(D.T @ data.reshape(-1))
+
+
+def test_tsvd_against_svd_of_dense_response(tiny_kerr):
+    """TSVD in a class (Sec. 9): the oracle's route (eigenpairs of the Gram,
+    matrix-free A^T d) against the SVD of the dense P = A Q assembled per ray,
+    x = Q sum_{i<r} v_i (u_i . d) / s_i; the operational rank is the count of
+    singular values at or above rho."""
+    w, tab = tiny_kerr
+    scl = 0.8
+    Q = O.synth_class(w, "S224")
+    P = O.dense_A(w, tab, scl) @ Q
+    U, s, Vt = np.linalg.svd(P, full_matrices=False)
+    data = O.apply_A(w, tab, I.history_batch(w, [2, 9]), scl) \
+        + 0.05 * I.noise((tab.n_rows, w.time.n_frames, 2), 4)
+    dv = data.reshape(-1, 2)
+    rho = 0.5 * (s[5] + s[6])  # a threshold well away from every singular value
+    r_want = int(np.count_nonzero(s >= rho))
+    assert r_want == 6
+    x, r = O.tsvd_in_class(w, tab, scl, Q, data, None, rho=rho)
+    assert r == r_want
+    ref = Q @ (Vt[:r].T @ ((U[:, :r].T @ dv) / s[:r, None]))
+    np.testing.assert_allclose(x.reshape(-1, 2), ref, rtol=0, atol=1e-9 * np.abs(ref).max())
+    # data inside the retained span is recovered exactly: d = P v_0 -> Q v_0
+    d0 = (P @ Vt[0]).reshape(tab.n_rows, w.time.n_frames, 1)
+    x0, _ = O.tsvd_in_class(w, tab, scl, Q, d0, 3)
+    np.testing.assert_allclose(x0.reshape(-1), Q @ Vt[0], rtol=0, atol=1e-9 * np.abs(Q @ Vt[0]).max())
