@@ -177,3 +177,19 @@ def test_local_directions_rebuild_the_scalar_probe(schw):
         assert abs(scl * scl * np.sum(ys ** 2) / want - 1.0) < 1e-12
     loc = O.local_probe_info(w, tab, scl, ages=ages)
     assert loc.shape == (3, 28) and np.all(loc >= 0)
+
+
+def test_local_reach_hand_cases():
+    """The deepest age with any direction at or above rho^2: the passing
+    direction may change with age; an age where none passes between two that
+    do does not cut the reach (it is the last passing age, not a run)."""
+    ages = [0.0, 4.0, 8.0, 12.0]
+    info = np.array([[2.0, 0.0], [0.0, 1.0], [0.5, 0.2], [0.0, 0.0]])
+    assert O.local_reach(info, 1.0, ages) == 4.0
+    info[2, 0] = 4.0
+    assert O.local_reach(info, 2.0, ages) == 8.0
+    assert O.local_reach(info, 2.01, ages) is None  # 4 < 2.01^2: nothing passes
+    assert O.local_reach(info, 1.4, ages) == 8.0    # age 0 (2 >= 1.96) and age 8
+    assert O.local_reach(np.zeros((4, 2)), 1.0, ages) is None
+    gap = np.array([[1.0], [0.0], [1.0], [0.0]])
+    assert O.local_reach(gap, 1.0, ages) == 8.0
