@@ -198,6 +198,40 @@ def _ptr(a: np.ndarray, typ):
     return a.ctypes.data_as(typ)
 
 
+_FLOATS = ("float32", "float64")
+
+
+def _on_gpu(t) -> bool:
+    return bool(t.is_cuda)
+
+
+def _want(t, name: str, shape, dtypes=_FLOATS, like=None):
+    """Check a tensor argument before its pointer reaches the library, which
+    reads and writes exactly the sizes its header states: a torch tensor of
+    one of `dtypes` (names), of `shape` (None matches any extent), contiguous,
+    on the GPU, and on the same device and of the same dtype as `like` when
+    given.  Raises ValueError; returns t."""
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{name}: expected a torch tensor, got {type(t).__name__}")
+    dt = str(t.dtype).replace("torch.", "")
+    if dt not in dtypes:
+        raise ValueError(f"{name}: dtype {dt}, expected {' or '.join(dtypes)}")
+    if like is not None and t.dtype != like.dtype:
+        raise ValueError(f"{name}: dtype {dt} differs from the input's {like.dtype}")
+    if t.dim() != len(shape) or any(w is not None and int(n) != int(w)
+                                    for n, w in zip(t.shape, shape)):
+        want = ", ".join("*" if w is None else str(int(w)) for w in shape)
+        raise ValueError(f"{name}: shape {list(t.shape)}, expected [{want}]")
+    if not t.is_contiguous():
+        raise ValueError(f"{name}: must be contiguous")
+    if not _on_gpu(t):
+        raise ValueError(f"{name}: must be a CUDA tensor")
+    if like is not None and t.device != like.device:
+        raise ValueError(f"{name}: on {t.device}, the input is on {like.device}")
+    return t
+
+
 def _stream(stream):
     if stream is None:
         import torch
@@ -325,11 +359,13 @@ class Operator:
     def apply_A(self, x, y=None, arm_mask: int = 7, stream=None):
         """y = scale * A x; x: [n_nodes, n_hats, B] (float32 or float64, CUDA)."""
         import torch
-        assert x.is_cuda and x.is_contiguous() and x.dim() == 3
+        _want(x, "x", (self.n_nodes, self.n_hats, None))
         B = x.shape[2]
         R = self.arm_rows(arm_mask)
         if y is None:
             y = torch.empty((R, self.n_frames, B), dtype=x.dtype, device=x.device)
+        else:
+            _want(y, "y", (R, self.n_frames, B), like=x)
         name = "rtt_apply_A" if x.dtype == torch.float32 else "rtt_apply_A_f64"
         self._launch(name, x, y, B, arm_mask, stream)
         return y
@@ -337,15 +373,19 @@ class Operator:
     def apply_A_AT(self, x, d=None, y=None, g=None, arm_mask: int = 7, stream=None):
         """rtt_apply_A_AT: (y, g) = (scale A x, scale A^T (y - d)), FP32, one call."""
         import torch
-        assert x.is_cuda and x.is_contiguous() and x.dim() == 3 and x.dtype == torch.float32
+        _want(x, "x", (self.n_nodes, self.n_hats, None), ("float32",))
         B = x.shape[2]
+        R = self.arm_rows(arm_mask)
         if y is None:
-            R = self.arm_rows(arm_mask)
             y = torch.empty((R, self.n_frames, B), dtype=x.dtype, device=x.device)
+        else:
+            _want(y, "y", (R, self.n_frames, B), like=x)
         if g is None:
             g = torch.empty_like(x)
+        else:
+            _want(g, "g", tuple(x.shape), like=x)
         if d is not None:
-            assert d.is_contiguous() and d.shape == y.shape and d.dtype == torch.float32
+            _want(d, "d", (R, self.n_frames, B), like=x)
         dp_ = ctypes.c_void_p(d.data_ptr()) if d is not None else None
         check(lib().rtt_apply_A_AT(self.handle, ctypes.c_void_p(x.data_ptr()), dp_,
                                    ctypes.c_void_p(y.data_ptr()), ctypes.c_void_p(g.data_ptr()),
@@ -355,10 +395,12 @@ class Operator:
     def apply_AT(self, y, x=None, arm_mask: int = 7, stream=None):
         """x = scale * A^T y; y: [arm_rows, n_frames, B]."""
         import torch
-        assert y.is_cuda and y.is_contiguous() and y.dim() == 3
+        _want(y, "y", (self.arm_rows(arm_mask), self.n_frames, None))
         B = y.shape[2]
         if x is None:
             x = torch.empty((self.n_nodes, self.n_hats, B), dtype=y.dtype, device=y.device)
+        else:
+            _want(x, "x", (self.n_nodes, self.n_hats, B), like=y)
         name = "rtt_apply_AT" if y.dtype == torch.float32 else "rtt_apply_AT_f64"
         self._launch(name, y, x, B, arm_mask, stream)
         return x
@@ -374,11 +416,13 @@ class Operator:
         """rtt_mix_rows(_f64): the whitened collapse of the arm's data y
         [arm_rows, n_frames, B] into [mixed rows, n_frames, B] (Eq. 4)."""
         import torch
-        assert y.is_cuda and y.is_contiguous() and y.dim() == 3
+        _want(y, "y", (self.arm_rows(arm_mask), self.n_frames, None))
         B = y.shape[2]
+        n_out = self.mix_rows_count(mode, arm_mask)
         if out is None:
-            out = torch.empty((self.mix_rows_count(mode, arm_mask), y.shape[1], B), dtype=y.dtype,
-                              device=y.device)
+            out = torch.empty((n_out, self.n_frames, B), dtype=y.dtype, device=y.device)
+        else:
+            _want(out, "out", (n_out, self.n_frames, B), like=y)
         name = "rtt_mix_rows" if y.dtype == torch.float32 else "rtt_mix_rows_f64"
         check(getattr(lib(), name)(self.handle, arm_mask, mode, ctypes.c_void_p(y.data_ptr()),
                                    ctypes.c_void_p(out.data_ptr()), B, _stream(stream)), name)
@@ -388,10 +432,13 @@ class Operator:
         """rtt_mix_rows_T(_f64): the adjoint of the collapse, [mixed rows,
         n_frames, B] -> [arm_rows, n_frames, B]."""
         import torch
-        assert yl.is_cuda and yl.is_contiguous() and yl.dim() == 3
+        _want(yl, "yl", (self.mix_rows_count(mode, arm_mask), self.n_frames, None))
         B = yl.shape[2]
+        R = self.arm_rows(arm_mask)
         if out is None:
-            out = torch.empty((self.arm_rows(arm_mask), yl.shape[1], B), dtype=yl.dtype, device=yl.device)
+            out = torch.empty((R, self.n_frames, B), dtype=yl.dtype, device=yl.device)
+        else:
+            _want(out, "out", (R, self.n_frames, B), like=yl)
         name = "rtt_mix_rows_T" if yl.dtype == torch.float32 else "rtt_mix_rows_T_f64"
         check(getattr(lib(), name)(self.handle, arm_mask, mode, ctypes.c_void_p(yl.data_ptr()),
                                    ctypes.c_void_p(out.data_ptr()), B, _stream(stream)), name)
@@ -464,7 +511,7 @@ def gram(op: "Operator", Q, arm_mask: int = 7, mode: int = GRAM_DATA, stream=Non
     """G = P^T P, P = scale A_arm Q; Q: CUDA float64 [n_nodes, n_hats, d].
     mode GRAM_DATA: over data samples; GRAM_NORMAL: Q^T A^T A Q."""
     import torch
-    assert Q.is_cuda and Q.dtype == torch.float64 and Q.is_contiguous() and Q.dim() == 3
+    _want(Q, "Q", (op.n_nodes, op.n_hats, None), ("float64",))
     d = Q.shape[2]
     G = torch.empty((d, d), dtype=torch.float64, device=Q.device)
     name = "rtt_gram" if mode == GRAM_DATA else "rtt_gram_normal"
@@ -485,8 +532,8 @@ def gram_class(op: "Operator", kind: int = CLASS_S224, arm_mask: int = 7, stream
 def eig_sym(G, max_sweeps: int = 60, stream=None):
     """Eigenvalues (descending) and eigenvectors of a symmetric CUDA FP64 matrix."""
     import torch
-    n = G.shape[0]
-    A = G.clone().contiguous()
+    n = G.shape[0] if G.dim() == 2 else -1
+    A = _want(G.clone().contiguous(), "G", (n, n), ("float64",))
     V = torch.empty_like(A)
     ev = np.empty(n)
     sw = ctypes.c_int(0)
@@ -500,8 +547,8 @@ def eig_sym(G, max_sweeps: int = 60, stream=None):
 def eigvals_sym_batched(G, stream=None):
     """Eigenvalues (ascending per matrix) of CUDA FP64 symmetric matrices
     [batch, n, n] by tridiagonal reduction and bisection (input is copied)."""
-    A = G.clone().contiguous()
-    b, n = A.shape[0], A.shape[1]
+    b, n = (G.shape[0], G.shape[1]) if G.dim() == 3 else (-1, -1)
+    A = _want(G.clone().contiguous(), "G", (b, n, n), ("float64",))
     ev = np.empty(b * n)
     check(lib().rtt_eigvals_sym_batched(n, b, ctypes.c_void_p(A.data_ptr()), _ptr(ev, dp),
                                         _stream(stream)), "rtt_eigvals_sym_batched")
@@ -524,8 +571,8 @@ def solve_ridge(op: "Operator", data, lambdas, arm_mask: int = 7, max_iter: int 
     """Batched CG ridge solve; data: CUDA float32 [rows, frames, n_rhs].
     Returns (x [n_nodes, n_hats, n_rhs * n_lambda], iterations, relres)."""
     import torch
-    assert data.is_cuda and data.dtype == torch.float32 and data.is_contiguous()
-    lam = np.ascontiguousarray(lambdas, np.float64)
+    _want(data, "data", (op.arm_rows(arm_mask), op.n_frames, None), ("float32",))
+    lam = np.ascontiguousarray(lambdas, np.float64).reshape(-1)
     n_rhs = data.shape[2]
     ncol = n_rhs * lam.shape[0]
     x = torch.empty((op.n_nodes, op.n_hats, ncol), dtype=torch.float32, device=data.device)
@@ -544,10 +591,14 @@ def solve_tsvd(op: "Operator", Q, V, evals, rank: int, data, arm_mask: int = 7, 
     """TSVD in class Q (CUDA float64 [n_nodes, n_hats, d]) with eigenpairs (V, evals)
     sorted descending; data: CUDA float64 [rows, frames, n_rhs]."""
     import torch
+    _want(Q, "Q", (op.n_nodes, op.n_hats, None), ("float64",))
     d = Q.shape[2]
+    Vc = _want(V.contiguous(), "V", (d, d), ("float64",), like=Q)
+    _want(data, "data", (op.arm_rows(arm_mask), op.n_frames, None), ("float64",), like=Q)
     n_rhs = data.shape[2]
-    ev = np.ascontiguousarray(evals, np.float64)
-    Vc = V.contiguous()
+    ev = np.ascontiguousarray(evals, np.float64).reshape(-1)
+    if ev.shape[0] != d:
+        raise ValueError(f"evals: {ev.shape[0]} values, expected d = {d}")
     xh = torch.empty((op.n_nodes, op.n_hats, n_rhs), dtype=torch.float64, device=data.device)
     check(lib().rtt_solve_tsvd(op.handle, arm_mask, ctypes.c_void_p(Q.data_ptr()), d,
                                ctypes.c_void_p(Vc.data_ptr()), _ptr(ev, dp), rank,
@@ -580,7 +631,7 @@ def gram_normal_mix(op: "Operator", Q, mode: int, arm_mask: int = 7, stream=None
     """rtt_gram_normal_mix: G = Q^T A^T W^T W A Q for the mixed arm `mode`
     (Eq. 4, Eq. 7); Q: CUDA float64 [n_nodes, n_hats, d]."""
     import torch
-    assert Q.is_cuda and Q.dtype == torch.float64 and Q.is_contiguous() and Q.dim() == 3
+    _want(Q, "Q", (op.n_nodes, op.n_hats, None), ("float64",))
     d = Q.shape[2]
     G = torch.empty((d, d), dtype=torch.float64, device=Q.device)
     check(lib().rtt_gram_normal_mix(op.handle, arm_mask, mode, ctypes.c_void_p(Q.data_ptr()), d,
@@ -597,7 +648,12 @@ def rank_audit(ops, Qs, arm_masks=(1, 7), ages=AGES, h: float = 3.0, quantile: f
     n = len(ops)
     if Qs is None:
         Qs = [None] * n
-    d = next((q.shape[2] for q in Qs if q is not None), 224)
+    if len(Qs) != n:
+        raise ValueError(f"Qs: {len(Qs)} entries for {n} operators")
+    d = next((q.shape[2] for q in Qs if q is not None and q.dim() == 3), 224)
+    for o, q in zip(ops, Qs):
+        if q is not None:
+            _want(q, "Q", (o.n_nodes, o.n_hats, d), ("float64",))
     arr_ops = (vp * n)(*[o.handle for o in ops])
     arr_q = (vp * n)(*[ctypes.c_void_p(q.data_ptr() if q is not None else None) for q in Qs])
     arms = (ctypes.c_int * len(arm_masks))(*arm_masks)
