@@ -47,10 +47,33 @@ def _table(n=4):
 
 
 @pytest.mark.parametrize("bad", ["r_out_of_range", "order", "nonfinite", "no_direct",
-                                 "cadence", "grid"])
+                                 "cadence", "grid", "negative_pixel", "negative_order", "empty",
+                                 "huge_delay", "hat_offset", "no_hats", "no_frames",
+                                 "radial_range", "spin", "snr0"])
 def test_build_rejects_invalid_tables_on_host(L, bad):
     w = I.schw32()
     tab = _table()
+    kw = {}
+    if bad == "negative_pixel":
+        tab["pixel"][3] = -1
+    elif bad == "negative_order":
+        tab["order"][0] = -1
+    elif bad == "empty":
+        tab = {k: v[:0] for k, v in tab.items()}
+    elif bad == "huge_delay":
+        tab["delay"][1] = 2e6
+    elif bad == "hat_offset":  # |u0| above 2^20 hat steps of 4 M
+        w = I.Workload("h", w.geometry, w.grid, I.TimeGrid(24, 2.0, 12, t_end=4.0 * 2 ** 21))
+    elif bad == "no_hats":
+        w = I.Workload("k", w.geometry, w.grid, I.TimeGrid(24, 2.0, 0, t_end=0.0))
+    elif bad == "no_frames":
+        w = I.Workload("f", w.geometry, w.grid, I.TimeGrid(0, 2.0, 12, t_end=0.0))
+    elif bad == "radial_range":
+        w = I.Workload("r", w.geometry, I.SourceGrid(4, 16, r_in=5.0, r_out=5.0), w.time)
+    elif bad == "spin":
+        w = I.Workload("s", I.Geometry(1.0, 50.0, 32), w.grid, w.time)
+    elif bad == "snr0":
+        kw = {"snr0": 0.0}
     if bad == "r_out_of_range":
         tab["r"][1] = 11.5
     elif bad == "order":
@@ -64,7 +87,7 @@ def test_build_rejects_invalid_tables_on_host(L, bad):
     elif bad == "grid":
         w = I.Workload("g", w.geometry, I.SourceGrid(1, 16), w.time)
     with pytest.raises(rtt.RttError) as ei:
-        rtt.Operator(w, tab, stream=0)
+        rtt.Operator(w, tab, stream=0, **kw)
     assert ei.value.status == -1
 
 
