@@ -133,3 +133,18 @@ def test_class_dimensions(L):
     (4,7,16), (6,11,16) -> 224, 224, 448, 528, 1056, 448, 1056."""
     assert [L.rtt_class_dim(k) for k in range(7)] == [224, 224, 448, 528, 1056, 448, 1056]
     assert L.rtt_class_dim(7) == 0 and L.rtt_class_dim(-1) == 0
+
+
+def test_every_entry_point_rejects_null_arguments(L):
+    """Each status-returning entry point, called with null pointers and zero
+    sizes, returns RTT_EINVAL and sets the error message before it touches a
+    GPU (no crash, no CUDA call on the CPU host)."""
+    plain = {"rtt_error_string", "rtt_last_error", "rtt_abi_version", "rtt_class_dim",
+             "rtt_destroy"}
+    for name, (_, argtypes) in rtt._SIGS.items():
+        if name in plain:
+            continue
+        vals = [0 if a in (ctypes.c_int, ctypes.c_int32, ctypes.c_int64)
+                else 0.0 if a is ctypes.c_double else None for a in argtypes]
+        assert getattr(L, name)(*vals) == -1, name
+        assert L.rtt_last_error(), name
