@@ -109,7 +109,8 @@ class Trace:
 def trace(spin: float, incl: float, alpha, beta, n_orders: int = 3, r_esc: float = 11.0,
           method: str = "auto", rtol: float = 1e-13) -> Trace:
     """Per screen ray and order n = 0..n_orders-1: the (n+1)-th equatorial
-    crossing.  method "schw" (a = 0 only): exact orbit integral; "kerr":
+    crossing (the per-order ray maps of Sec. 3.1 Eq. 2; Kerr and the exact
+    Schwarzschild branch of Sec. 5).  method "schw" (a = 0 only): exact orbit integral; "kerr":
     Mino-time Carter integration; "auto": schw at a = 0, kerr otherwise."""
     alpha = _c64(alpha)
     beta = _c64(beta)
@@ -139,18 +140,21 @@ def trace(spin: float, incl: float, alpha, beta, n_orders: int = 3, r_esc: float
 
 
 def kerr_fate(spin: float, incl: float, alpha: float, beta: float):
-    """Integrate one ray until capture (-1) or escape (+1); returns (fate, r_min)."""
+    """Integrate one ray until capture (-1) or escape (+1); returns (fate, r_min)
+    (the Kerr ray maps of Sec. 5; used to pin the critical curve)."""
     rmin = ctypes.c_double(0.0)
     f = lib().orc_kerr_fate(spin, incl, alpha, beta, ctypes.byref(rmin))
     return int(f), float(rmin.value)
 
 
 def horizon(spin: float) -> float:
+    """Outer horizon r_+ = 1 + sqrt(1 - a^2) (Sec. 5, the r_+ check)."""
     return 1.0 + math.sqrt(1.0 - spin * spin)
 
 
 def isco(spin: float) -> float:
-    """Prograde ISCO radius (Bardeen, Press & Teukolsky 1972)."""
+    """Prograde ISCO radius (Bardeen, Press & Teukolsky 1972); the boundary of
+    the circular/plunging emitter branch of Sec. 5."""
     a = spin
     z1 = 1.0 + (1.0 - a * a) ** (1 / 3) * ((1.0 + a) ** (1 / 3) + (1.0 - a) ** (1 / 3))
     z2 = math.sqrt(3.0 * a * a + z1 * z1)
@@ -158,7 +162,8 @@ def isco(spin: float) -> float:
 
 
 def circular_EL(spin: float, r):
-    """Specific energy and angular momentum of prograde circular equatorial orbits."""
+    """Specific energy and angular momentum of prograde circular equatorial
+    orbits (the emitter's circular branch, Sec. 5; redshift factor of Eq. 2)."""
     a = spin
     den = r ** 0.75 * np.sqrt(r ** 1.5 - 3.0 * np.sqrt(r) + 2.0 * a)
     E = (r ** 1.5 - 2.0 * np.sqrt(r) + a) / den
@@ -320,7 +325,8 @@ def scale(table: Table, snr0: float = 100.0) -> float:
 
 def apply_A(w, table: Table, x: np.ndarray, scl: float = 1.0) -> np.ndarray:
     """y[row][f][b] = scl * sum_{e in row} w_e sum_c bil_c sum_k B_k(t_o(f) -
-    Delta_e) x[node_c][k][b].  x: [S, K, B] or [S, K]."""
+    Delta_e) x[node_c][k][b] (Sec. 3.1 Eq. 2-3; the row action of Eq. 47).
+    x: [S, K, B] or [S, K]."""
     squeeze = x.ndim == 2
     xx = _c64(x[..., None] if squeeze else x)
     B = xx.shape[-1]
@@ -348,8 +354,9 @@ def apply_AT(w, table: Table, y: np.ndarray, scl: float = 1.0) -> np.ndarray:
 
 
 def dense_A(w, table: Table, scl: float = 1.0) -> np.ndarray:
-    """Explicit per-ray assembly of the dense matrix (tiny cases only):
-    rows (row, f), columns s * K + k.  Written independently of the C loops
+    """Explicit per-ray assembly of the dense matrix of Eq. 2-3 (tiny cases
+    only; the dense/matrix-free parity check of Sec. 5): rows (row, f),
+    columns s * K + k.  Written independently of the C loops
     (numpy, evaluating every hat and the bilinear stencil by its definition)."""
     g, t = w.grid, w.time
     K, T = t.n_hats, t.n_frames
@@ -417,7 +424,8 @@ def mix_rows(table: Table, y: np.ndarray, mode: int, orders=(0, 1, 2)) -> np.nda
 
 
 def mix_rows_T(table: Table, yl: np.ndarray, mode: int, orders=(0, 1, 2)) -> np.ndarray:
-    """W^T applied to mixed data yl [output rows][frames][batch] (the adjoint)."""
+    """W^T applied to mixed data yl [output rows][frames][batch] (the adjoint
+    of the Eq. 4 collapse)."""
     W = mixer(table, mode, orders)
     y2 = yl.reshape(yl.shape[0], -1)
     return np.asarray(W.T @ y2).reshape((W.shape[1],) + yl.shape[1:])
@@ -496,7 +504,8 @@ def local_direction_norms(w, h: float = PROBE_H) -> np.ndarray:
 
 
 def local_direction_values(w, r: np.ndarray, phi: np.ndarray) -> np.ndarray:
-    """psi_l at source points (r, phi), unnormalised, [points, 28]."""
+    """psi_l at source points (r, phi), unnormalised, [points, 28]: the 28
+    spatial directions of the localized probes (Sec. 3.3 Eq. 14)."""
     g = w.grid
     s = np.log(np.asarray(r) / g.r_in) / math.log(g.r_out / g.r_in)
     R = np.stack([math.comb(3, i) * s ** i * (1 - s) ** (3 - i) for i in range(4)], axis=1)
@@ -633,12 +642,15 @@ def j_old(info: np.ndarray, A0: float, ages=AGES, da: float = 4.0) -> float:
 # Representation classes (Eq. 8; Sec. 7 compact classes)
 # ---------------------------------------------------------------------------
 def _radial_bernstein(w):
+    """The 4 clamped cubic B-splines in log r with no interior knot (cubic
+    Bernstein polynomials) at the radial nodes (Eq. 8)."""
     g = w.grid
     s = (np.log(g.radii()) - np.log(g.r_in)) / (np.log(g.r_out) - np.log(g.r_in))
     return np.stack([math.comb(3, j) * s ** j * (1 - s) ** (3 - j) for j in range(4)], axis=1)
 
 
 def _azimuthal(w):
+    """1, cos m phi, sin m phi for m = 1..3 at the azimuthal nodes (Eq. 8)."""
     ph = w.grid.azimuths()
     cols = [np.ones_like(ph)]
     for m in (1, 2, 3):
@@ -657,7 +669,8 @@ CLASS_SHAPES = {"S224": (4, 7, 8, "dct"), "L224": (4, 7, 8, "hat"),
 def radial_bsplines(s: np.ndarray, n: int) -> np.ndarray:
     """n clamped cubic B-splines on uniform knots in the normalised log radius
     s in [0, 1] (n = 4: no interior knot, the cubic Bernstein basis), [len(s), n];
-    by scipy's B-spline evaluation."""
+    by scipy's B-spline evaluation (the radial factor of the ladder, Sec. 8
+    Eq. 42-43)."""
     from scipy.interpolate import BSpline
     inner = np.linspace(0.0, 1.0, n - 2)[1:-1]
     t = np.concatenate([[0.0] * 4, inner, [1.0] * 4])
@@ -727,7 +740,8 @@ def synth_class(w, kind: str = "S224") -> np.ndarray:
 # Gram, spectrum and operational rank (Eq. 21, 31)
 # ---------------------------------------------------------------------------
 def restricted_response(w, table: Table, Q: np.ndarray, scl: float) -> np.ndarray:
-    """P = scl * A Q as an (rows*frames) x d matrix."""
+    """P = scl * A Q as an (rows*frames) x d matrix (the restricted operator
+    of Eq. 7)."""
     d = Q.shape[1]
     x = Q.reshape(w.grid.n_nodes, w.time.n_hats, d)
     return apply_A(w, table, x, scl).reshape(-1, d)
@@ -760,7 +774,7 @@ def operational_rank(G: np.ndarray, rho: float = 1.0) -> Spectrum:
 def ridge_cg(w, table: Table, scl: float, data: np.ndarray, lam: float, tol: float = 1e-12,
              max_iter: int = 5000):
     """Solve (A^T A + lam I) x = A^T d by conjugate gradients in FP64, with
-    A = scl * A_table (whitened).  data: [rows, T, B]; returns (x, iters)."""
+    A = scl * A_table (whitened): the ridge/Tikhonov estimator of Sec. 9.  data: [rows, T, B]; returns (x, iters)."""
     b = apply_AT(w, table, data, scl)
 
     def op(v):
@@ -786,8 +800,9 @@ def ridge_cg(w, table: Table, scl: float, data: np.ndarray, lam: float, tol: flo
 
 def tsvd_in_class(w, table: Table, scl: float, Q: np.ndarray, data: np.ndarray, rank: int | None,
                   rho: float = 1.0):
-    """TSVD in the class Q: x = Q V_r L_r^{-1} V_r^T Q^T A^T d with (V, L) the
-    eigenpairs of G = Q^T A^T A Q; reading: r = operational rank."""
+    """TSVD in the class Q (the truncated-SVD estimator of Sec. 9):
+    x = Q V_r L_r^{-1} V_r^T Q^T A^T d with (V, L) the eigenpairs of
+    G = Q^T A^T A Q; reading: r = operational rank (Eq. 31)."""
     P = restricted_response(w, table, Q, scl)
     G = gram(P)
     lam, V = np.linalg.eigh(G)
