@@ -601,6 +601,28 @@ def run_audit(device):
                                  "J_old": [round(r.reach.J_old, 3) for r in pdr],
                                  "median_J_old": float(np.median([r.reach.J_old for r in pdr])),
                                  "seconds_with_build": round(time.perf_counter() - t, 3)}
+    # delay-only and spatial-only arms (Sec. 6.4): the rings keep their delays
+    # with their source points moved to the direct quantile partners', or keep
+    # their source points with the partners' delays; the resolved arm's rank,
+    # reach and J_old through the class-Gram audit
+    for name, make in (("delay_only", I.delay_only), ("spatial_only", I.spatial_only)):
+        try:
+            torch.cuda.synchronize(device)
+            t = time.perf_counter()
+            arm = []
+            for w, tab in cells:
+                op_a = rtt.Operator(w, make(tab))
+                recs, _ = rtt.rank_audit([op_a], [None], (7,), mode=rtt.GRAM_CLASS_S224)
+                arm.append(recs[0][0])
+                op_a.close()
+            mech[name] = {"rank": [r.rank for r in arm],
+                          "L_anchor": [r.reach.L_anchor for r in arm],
+                          "J_old": [round(r.reach.J_old, 3) for r in arm],
+                          "median_J_old": float(np.median([r.reach.J_old for r in arm])),
+                          "median_rank": float(np.median([r.rank for r in arm])),
+                          "seconds_with_build": round(time.perf_counter() - t, 3)}
+        except Exception as exc:  # a measurement extra; report why it failed
+            mech[name] = {"error": f"{type(exc).__name__}: {exc}"}
     out["mechanism_arms"] = mech
     # threshold sweep at the reconstruction geometry a = 0.5, i = 50 deg (Sec.
     # 3.3, Table 2): detectability depends on rho / SNR_0 only, so a threshold

@@ -193,3 +193,88 @@ def test_local_reach_hand_cases():
     assert O.local_reach(np.zeros((4, 2)), 1.0, ages) is None
     gap = np.array([[1.0], [0.0], [1.0], [0.0]])
     assert O.local_reach(gap, 1.0, ages) == 8.0
+
+
+def _as_dict(tab):
+    return {"order": tab.order, "pixel": tab.pixel, "r": tab.r, "phi": tab.phi,
+            "delay": tab.delay, "weight": tab.weight, "throughput": tab.throughput}
+
+
+def test_direct_quantile_partner_hand_case():
+    """Direct ranking by delay: rays 1, 3, 0, 2.  Order 1 (two rays): ray 5
+    (k = 0) -> rank floor(0.5 * 4 / 2) = 1 -> ray 3; ray 4 (k = 1) -> rank 3
+    -> ray 2.  Order 2 (one ray): rank floor(0.5 * 4) = 2 -> ray 0.  Direct
+    rays map to themselves."""
+    order = [0, 0, 0, 0, 1, 1, 2]
+    delay = [3.0, 1.0, 4.0, 2.0, 9.0, 7.0, 20.0]
+    assert I.direct_quantile_partner(order, delay).tolist() == [0, 1, 2, 3, 2, 3, 0]
+
+
+def test_spatial_only_keeps_direct_old_epoch_blindness(schw):
+    """Spatial-only arm: the rings keep source points, weights and rows, and
+    their delays, rank for rank, become direct delays.  Every order's
+    footprint then lies inside the direct one, so Theorem 4.1's blind columns
+    of the direct image (hats whose support misses W_0) stay exactly zero in
+    the whole stack, while the true resolved stack sees some of them."""
+    import dataclasses
+    w, tab = schw
+    so = I.spatial_only(_as_dict(tab))
+    ring = tab.order > 0
+    for k in ("order", "pixel", "r", "phi", "weight", "throughput"):
+        np.testing.assert_array_equal(so[k], getattr(tab, k))
+    np.testing.assert_array_equal(so["delay"][~ring], tab.delay[~ring])
+    assert np.all(np.isin(so["delay"][ring], tab.delay[~ring]))
+    for n in (1, 2):
+        m = np.nonzero(tab.order == n)[0]
+        if m.size:
+            assert np.all(np.diff(so["delay"][m[np.argsort(tab.delay[m], kind="stable")]]) >= 0)
+    scl = O.scale(tab)
+    zero = lambda t: np.all(O.dense_A(w, t, scl) == 0.0, axis=0)  # noqa: E731
+    zs = zero(dataclasses.replace(tab, delay=so["delay"]))
+    zr = zero(tab)
+    (lo, hi), = O.footprints(w, tab, (0,))
+    tk = w.time.hat_times()
+    miss = (tk + w.time.hat_step <= lo) | (tk - w.time.hat_step >= hi)  # hat misses W_0
+    blind = np.tile(miss, w.grid.n_nodes)  # columns s * K + k
+    assert blind.sum() > 0
+    assert np.all(zs[blind]) and not np.all(zr[blind])
+
+
+@pytest.mark.parametrize("case", ["schw32", "small_kerr"])
+def test_delay_only_and_spatial_only_reach(case):
+    """The scalar probe (Eq. 10) is the same at every source point of the
+    annulus, so the delay-only arm (ring source points moved, delays kept)
+    has the resolved stack's probe information, reach and J_old exactly, as
+    the paper's Sec. 6.4 reports equal medians for the two.  The
+    spatial-only arm stays near the direct image (at most 5% more J_old,
+    never the resolved value)."""
+    import dataclasses
+    w = I.schw32() if case == "schw32" else I.small_kerr(
+        spin=0.5, incl_deg=50.0, nx=64, n_r=8, n_phi=16, n_frames=128, n_hats=32, ss=2)
+    tab = O.build_table(w, I.screen_samples(w))
+    scl = O.scale(tab)
+    a0 = O.a0999(w, tab)
+    do = I.delay_only(_as_dict(tab))
+    ring = tab.order > 0
+    for k in ("order", "pixel", "delay", "weight", "throughput"):
+        np.testing.assert_array_equal(do[k], getattr(tab, k))
+    direct_pts = set(zip(tab.r[~ring].tolist(), tab.phi[~ring].tolist()))
+    assert all(p in direct_pts for p in zip(do["r"][ring].tolist(), do["phi"][ring].tolist()))
+    td = dataclasses.replace(tab, r=do["r"], phi=do["phi"])
+    ts = dataclasses.replace(tab, delay=I.spatial_only(_as_dict(tab))["delay"])
+    assert O.scale(td) == scl and O.scale(ts) == scl  # direct rays untouched
+    info = {name: O.probe_info(w, t.select(orders), scl)
+            for name, t, orders in (("direct", tab, (0,)), ("resolved", tab, (0, 1, 2)),
+                                    ("delay_only", td, (0, 1, 2)),
+                                    ("spatial_only", ts, (0, 1, 2)))}
+    np.testing.assert_allclose(info["delay_only"], info["resolved"], rtol=1e-13, atol=0)
+    J = {k: O.j_old(v, a0) for k, v in info.items()}
+    assert J["direct"] <= J["spatial_only"] <= 1.05 * J["direct"] < J["resolved"]
+    r_res = O.reach(w, tab, info["resolved"], (0, 1, 2))
+    r_do = O.reach(w, td, info["delay_only"], (0, 1, 2))
+    assert r_do.L_anchor == r_res.L_anchor and r_res.L_anchor > 0
+    # the delay-only stack touches only nodes the direct image touches
+    nz = lambda t: np.any(O.dense_A(w, t, scl) != 0.0, axis=0).reshape(  # noqa: E731
+        w.grid.n_nodes, w.time.n_hats).any(axis=1)
+    if case == "schw32":
+        assert not np.any(nz(td) & ~nz(tab.select((0,))))
