@@ -39,6 +39,17 @@ def build(force: bool = False) -> str:
     return SO
 
 
+def set_threads(n: int) -> None:
+    """Threads of the C oracle's OpenMP loops (timing only: results do not
+    depend on the count)."""
+    lib().orc_set_threads(int(n))
+
+
+def max_threads() -> int:
+    """Threads the C oracle's OpenMP loops use."""
+    return int(lib().orc_max_threads())
+
+
 class _Grid(ctypes.Structure):
     _fields_ = [("n_r", ctypes.c_int), ("n_phi", ctypes.c_int), ("r_in", ctypes.c_double),
                 ("r_out", ctypes.c_double), ("n_frames", ctypes.c_int), ("t0", ctypes.c_double),
@@ -79,6 +90,10 @@ def lib():
         L.orc_apply_AT.restype = None
         L.orc_apply_AT.argtypes = [gp, ctypes.c_long, i64, dp, dp, dp, dp, ctypes.c_double,
                                    ctypes.c_int, dp, dp]
+        L.orc_set_threads.restype = None
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_max_threads.restype = ctypes.c_int
+        L.orc_max_threads.argtypes = []
         L.orc_probe_info.restype = None
         L.orc_probe_info.argtypes = [gp, ctypes.c_long, i64, dp, dp, dp, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_int, dp, dp]

@@ -32,6 +32,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define NSTATE 6
 #define CAPTURE_CUSHION 0.01
@@ -212,6 +215,25 @@ long orc_trace_kerr(double a, double incl, long n_rays, const double* alpha,
 
 /* Fate of one ray with no crossing limit: -1 captured (reached r_+ + 0.01),
  * +1 escaped (back to infinity); *rmin receives the smallest radius reached. */
+/* Threads of the OpenMP loops, for timing the oracle on a chosen number of
+ * host cores.  Every parallel loop writes disjoint outputs or reduces
+ * integers, so results do not depend on the count. */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
 int orc_kerr_fate(double a, double incl, double alpha, double beta, double* rmin) {
     const double si = sin(incl), ci = cos(incl);
     const double r_plus = 1.0 + sqrt(1.0 - a * a);

@@ -72,3 +72,15 @@ def test_traffic_record_only_for_its_sources(monkeypatch):
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
     assert bench.recorded_traffic("AT") is None
     assert bench.recorded_traffic("A") is None
+
+
+def test_oracle_timing_on_one_core_restores_the_thread_count():
+    from paper_2609_05528_b300 import inputs as I
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+    n_all = O.max_threads()
+    v, cores, n = bench.oracle_pairs_per_s(I.schw32(), budget_s=0.05, threads=1)
+    assert cores == 1 and n >= 1 and v > 0
+    assert O.max_threads() == n_all
+    v, cores, _ = bench.oracle_pairs_per_s(I.schw32(), budget_s=0.05)
+    assert cores == n_all

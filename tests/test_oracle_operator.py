@@ -289,3 +289,23 @@ def test_tsvd_against_svd_of_dense_response(tiny_kerr):
     d0 = (P @ Vt[0]).reshape(tab.n_rows, w.time.n_frames, 1)
     x0, _ = O.tsvd_in_class(w, tab, scl, Q, d0, 3)
     np.testing.assert_allclose(x0.reshape(-1), Q @ Vt[0], rtol=0, atol=1e-9 * np.abs(Q @ Vt[0]).max())
+
+
+def test_results_do_not_depend_on_the_thread_count(tiny_kerr):
+    """The C oracle's OpenMP loops write disjoint outputs: A, A^T and the probe
+    information are bitwise the same on one thread and on all of them."""
+    w, tab = tiny_kerr
+    x = I.history_batch(w, [3, 4])
+    y = O.apply_A(w, tab, x, 0.7)
+    runs = []
+    n_all = O.max_threads()
+    try:
+        for n in (1, n_all):
+            O.set_threads(n)
+            assert O.max_threads() == n
+            runs.append((O.apply_A(w, tab, x, 0.7), O.apply_AT(w, tab, y, 0.7),
+                         O.probe_info(w, tab, 0.7)))
+    finally:
+        O.set_threads(n_all)
+    for a, b in zip(*runs):
+        np.testing.assert_array_equal(a, b)
