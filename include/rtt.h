@@ -175,9 +175,19 @@ rtt_status rtt_build_operator(const rtt_geometry* geom, const rtt_source_grid* g
                               const rtt_time_grid* time, const rtt_ray_table* table,
                               const rtt_options* opt, void* stream, rtt_op* out);
 
+/*
+ * rtt_op_query -- the sizes, delay ranges and whitening of a built operator
+ * (s_ref of Eq. 17, scale = SNR_0 / s_ref of Eq. 18).  out: host struct.
+ * Errors: RTT_EINVAL (null op or out).
+ */
 rtt_status rtt_op_query(rtt_op op, rtt_op_info* out);
 
-/* Number of data rows selected by arm_mask. */
+/*
+ * rtt_arm_rows -- the number of data rows of the orders selected by arm_mask
+ * (the blocks of the stack of Eq. 3; bit n selects order n), i.e. the first
+ * extent of every y buffer of that arm.  rows_out: host int64.
+ * Errors: RTT_EINVAL (null op or rows_out, arm_mask not in 1..7).
+ */
 rtt_status rtt_arm_rows(rtt_op op, int arm_mask, int64_t* rows_out);
 
 /*
@@ -213,8 +223,9 @@ rtt_status rtt_apply_A(rtt_op op, const float* x_dev, float* y_dev, int batch, i
 rtt_status rtt_apply_AT(rtt_op op, const float* y_dev, float* x_dev, int batch, int arm_mask,
                         void* stream);
 
-/* FP64 storage and FP64 arithmetic versions of the two applies (the plain
-   FP64 GPU path the fast path is compared with).  Same layouts in double. */
+/* FP64 storage and FP64 arithmetic versions of the two applies (Eq. 2-3
+   and the adjoint action of Sec. 5; the plain FP64 GPU path the fast path is
+   compared with).  Same layouts in double.  Errors as rtt_apply_A. */
 rtt_status rtt_apply_A_f64(rtt_op op, const double* x_dev, double* y_dev, int batch,
                            int arm_mask, void* stream);
 rtt_status rtt_apply_AT_f64(rtt_op op, const double* y_dev, double* x_dev, int batch,
@@ -257,7 +268,8 @@ rtt_status rtt_probe_info(rtt_op op, int arm_mask, int n_ages, const double* age
                           double* info_host, void* stream);
 
 /*
- * rtt_probe_info_noalloc -- the FP32 pass of rtt_probe_info for callers that
+ * rtt_probe_info_noalloc -- the FP32 pass of rtt_probe_info (the probe
+ * information I(a) of Eq. 10-12 and Eq. 29) for callers that
  * must not allocate device memory while they run: for example an
  * application whose pool allocator has reserved all free device memory up
  * front, or a runtime that forbids allocation after initialisation.  The
@@ -287,6 +299,8 @@ rtt_status rtt_probe_info_noalloc(rtt_op op, int arm_mask, int n_ages, const dou
  * age Delta_e - t_o(f) and weight = the ray's throughput, the smallest sample
  * age whose cumulative weight (ages ascending, device radix sort, FP64
  * prefix sum) reaches q times the total.  0 < q <= 1.  Synchronous.
+ * Errors: RTT_EINVAL (null op or out_host, q outside (0, 1]), RTT_ENOMEM,
+ * RTT_ECUDA.
  */
 rtt_status rtt_direct_age_quantile(rtt_op op, double q, double* out_host, void* stream);
 
@@ -309,6 +323,8 @@ typedef struct {
  * if the anchor fails or is absent).  J_old uses the rectangle rule with
  * strict a > a0q.  ages/info: host arrays of n_ages; pass_host (optional)
  * receives n_ages bytes.  Host-only computation.
+ * Errors: RTT_EINVAL (null op, out, ages or info, n_ages < 1, h or
+ * age_step not positive, arm_mask not in 1..7).
  */
 rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const double* ages_host,
                      const double* info_host, double h, double a0q, double age_step,
@@ -322,7 +338,8 @@ rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const double* ages_hos
 #define RTT_CLASS_S1056ST 4 /* (6, 11, 16 DCT-II) */
 #define RTT_CLASS_L448 5    /* (4, 7, 16 degree-one B-splines) */
 #define RTT_CLASS_L1056 6   /* (6, 11, 16 degree-one B-splines) */
-/* rtt_class_dim -- the dimension d of class `kind` (0 for an unknown kind). */
+/* rtt_class_dim -- the dimension d of class `kind` (Eq. 8, Eq. 43; 0 for an
+   unknown kind).  Pure function, never fails. */
 int rtt_class_dim(int kind);
 
 /*
@@ -345,6 +362,8 @@ rtt_status rtt_synth_class(rtt_op op, int kind, double* Q_dev, void* stream);
  * G_dev receives double [d][d] (symmetric, row-major).  FP64 throughout: P
  * is formed chunk by chunk by the FP64 forward kernel into library scratch
  * (<= 1 GiB) and reduced in a fixed order.  1 <= d <= 4096.  Synchronous.
+ * Errors: RTT_EINVAL (null op, Q_dev or G_dev, d outside 1..4096, arm_mask
+ * not in 1..7), RTT_ENOMEM, RTT_ECUDA.
  */
 rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q_dev, int d, double* G_dev,
                     void* stream);
@@ -471,7 +490,8 @@ rtt_status rtt_eig_sym(int n, double* A_dev, double* evals_host, double* V_dev, 
  * rtt_eigvals_sym_batched -- eigenvalues only (ascending, evals_host: batch *
  * n) of `batch` consecutive symmetric n x n FP64 matrices in A_dev (row-major,
  * overwritten): Householder reduction to tridiagonal form and bisection with
- * Sturm counts, one CTA per matrix.  Absolute error of order n eps ||A||;
+ * Sturm counts, one CTA per matrix (the spectra of restricted Grams, Eq.
+ * 31).  Absolute error of order n eps ||A||;
  * for eigenvalues that must be resolved relative to their own size near a
  * threshold use rtt_eig_sym (the rank audit does so automatically).
  * Synchronous.  Errors: RTT_EINVAL, RTT_ECUDA.
@@ -481,7 +501,8 @@ rtt_status rtt_eigvals_sym_batched(int n, int batch, double* A_dev, double* eval
 
 /* rtt_eig_sym on `batch` matrices at once (A_dev, V_dev: batch consecutive
    n x n blocks; evals_host: batch * n; sweeps_host: batch ints), one CTA per
-   matrix. */
+   matrix (Eq. 31 for several Grams in one launch).  Errors as rtt_eig_sym,
+   and RTT_EINVAL for batch < 1. */
 rtt_status rtt_eig_sym_batched(int n, int batch, double* A_dev, double* evals_host, double* V_dev,
                                int max_sweeps, int* sweeps_host, void* stream);
 
@@ -631,7 +652,8 @@ typedef struct {
  * default rule) the kernel variant used by FP32 applies of `batch` columns,
  * or read the one in force.  For manual tuning and for tests that run every
  * variant; results are the same bits for every variant.  Not thread-safe
- * against concurrent applies on the same operator.  Errors: RTT_EINVAL.
+ * against concurrent applies on the same operator.  The paper has no
+ * counterpart (a property of this GPU implementation).  Errors: RTT_EINVAL.
  */
 rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v);
 rtt_status rtt_get_variant(rtt_op op, int batch, rtt_variant* out);

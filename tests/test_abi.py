@@ -148,3 +148,15 @@ def test_every_entry_point_rejects_null_arguments(L):
                 else 0.0 if a is ctypes.c_double else None for a in argtypes]
         assert getattr(L, name)(*vals) == -1, name
         assert L.rtt_last_error(), name
+
+
+def test_every_entry_point_is_documented():
+    """Each declaration block of include/rtt.h carries a comment that cites
+    the passage it implements (or says the paper has no counterpart) and
+    states its error behaviour."""
+    src = open(os.path.join(ROOT, "include", "rtt.h")).read()
+    blocks = re.findall(r"/\*(.*?)\*/\s*(?:[A-Za-z_][\w\s\*]*?)\b(rtt_\w+)\s*\(", src, re.S)
+    assert len(blocks) >= 30
+    for doc, name in blocks:
+        assert re.search(r"Sec\.|Eq\.|Theorem|counterpart", doc), name
+        assert re.search(r"Error|RTT_E|never fails", doc), name
