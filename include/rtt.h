@@ -137,6 +137,13 @@ typedef struct {
     double d_omega_pixel;  /* pixel solid angle in M^2 */
 } rtt_screen;
 
+/*
+ * rtt_error_string -- a static description of a status code;
+ * rtt_last_error -- the message of the last failing call (thread-local
+ * buffer owned by the library, overwritten by the next failure);
+ * rtt_abi_version -- the version of this interface (1).  Library plumbing:
+ * the paper has no counterpart.  Each never fails.
+ */
 const char* rtt_error_string(rtt_status s);
 const char* rtt_last_error(void);
 int rtt_abi_version(void);
@@ -390,6 +397,14 @@ rtt_status rtt_gram(rtt_op op, int arm_mask, const double* Q_dev, int d, double*
  */
 rtt_status rtt_gram_class(rtt_op op, int arm_mask, int kind, double* G_dev, void* stream);
 
+/*
+ * rtt_gram_normal -- the restricted Gram through the normal operator,
+ * G = Q^T (scale^2 A_arm^T A_arm) Q (Eq. 7, Eq. 21): Q's columns go through
+ * the FP64 forward and adjoint applies in chunks and the final contraction
+ * with Q^T is a cuBLAS DGEMM.  Arguments as rtt_gram.  Synchronous.
+ * Errors: RTT_EINVAL (null op, Q_dev or G_dev, d outside 1..4096, arm_mask
+ * not in 1..7), RTT_ENOMEM, RTT_ECUDA.
+ */
 rtt_status rtt_gram_normal(rtt_op op, int arm_mask, const double* Q_dev, int d, double* G_dev,
                            void* stream);
 
@@ -609,7 +624,8 @@ rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_d
 typedef struct {
     int32_t batch;
     int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat, 3 staged with TMA corner copies,
-                             4 staged with pipelined bulk corner copies */
+                             4 staged with pipelined bulk corner copies, 5 periodic
+                             staged with the whole batch in one chunk */
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
     int32_t fwd_staging;  /* staged forward: x items in flight per lane */
@@ -630,7 +646,10 @@ typedef struct {
     int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat (periodic cadences; else staged),
                              3 staged with TMA corner copies (batch a multiple of 4;
                              else staged), 4 staged with bulk corner copies pipelined
-                             two rays ahead (batch 4 or 8 as one chunk; else staged) */
+                             two rays ahead (batch 4 or 8 as one chunk; else staged),
+                             5 periodic staged with the whole batch in one chunk and
+                             32-bit hat arithmetic (periodic cadences, batch 4 or 8;
+                             else staged) */
     int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32 */
     int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
     int32_t time_kernel;  /* 1 general, 2 periodic weights, 3 periodic + TMA, 4 periodic
@@ -658,6 +677,12 @@ typedef struct {
 rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v);
 rtt_status rtt_get_variant(rtt_op op, int batch, rtt_variant* out);
 
+/*
+ * rtt_destroy -- free the operator and every device buffer it owns (tables,
+ * index arrays, scratch).  Work queued on a stream that uses `op` must have
+ * completed.  A null op is ignored.  Library plumbing: the paper has no
+ * counterpart.  Never fails.
+ */
 void rtt_destroy(rtt_op op);
 
 #ifdef __cplusplus
