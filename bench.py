@@ -34,6 +34,10 @@ BATCH = 8
 L2_FLUSH_BYTES = 256 << 20
 
 
+WORKLOAD = ("kerr256: Kerr a=0.5 i=50deg 256x256 (2x2 ring sub-rays), 64x128 source, 64 hats, "
+            "256 frames, resolved n=0..2")
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -382,8 +386,7 @@ def run_ours(args, rank, world, device):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "kerr256: Kerr a=0.5 i=50deg 256x256 (2x2 ring sub-rays), "
-                               "64x128 source, 64 hats, 256 frames, resolved n=0..2",
+        "config": {"workload": WORKLOAD,
                    "batch": BATCH, "rows": R, "rays": int(op.info.n_rays),
                    "nodes": op.n_nodes, "hats": op.n_hats, "frames": op.n_frames,
                    "l2": "flushed between timed steps (256 MiB write)",
@@ -897,7 +900,10 @@ def main():
                           "n_gpus": 1, "steps": len(vals), "warmup": 0,
                           "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
                           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                          "config": {"workload": "kerr256 (see ours)", "batch": 1},
+                          "config": {"workload": WORKLOAD, "batch": 1,
+                                     "sample": "one history per pass (the unit is per "
+                                               "history, so the batch does not change it)",
+                                     "parallelism": f"host cores x{cores}"},
                           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores,
                                            "kind": "oracle", "sample": sample},
                           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
