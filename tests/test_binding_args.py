@@ -133,3 +133,13 @@ def test_host_tensors_are_refused(monkeypatch):
     with pytest.raises(ValueError, match="CUDA"):
         rtt.gram(op, f64(S, K, 3), stream=0)
     assert rec.calls == []
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without librtt.so every entry point raises: there is no CPU fallback."""
+    monkeypatch.setattr(rtt, "_LIB", None)
+    monkeypatch.setattr(rtt, "LIB_PATH", "/nonexistent/librtt.so")
+    with pytest.raises(RuntimeError, match="missing"):
+        rtt.lib()
+    with pytest.raises(RuntimeError, match="missing"):
+        rtt.class_dim(rtt.CLASS_S224)
