@@ -3,7 +3,8 @@ oracle, through the C ABI (librtt.so).  The oracle's raw ray table is fed to
 both sides, so the comparison isolates the kernels.
 
 Tolerance (FP32 path): relative L2 error <= 1e-5 over the output and an
-elementwise bound |gpu - ref| <= 1e-5 * max|ref|; FP64 path: 1e-12.
+elementwise bound |gpu - ref| <= 1e-4 * max|ref| (ten times the L2 bound: a
+few outputs sum many rays); FP64 path: 1e-12 and 1e-11 * max|ref|.
 """
 import math
 
