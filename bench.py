@@ -624,6 +624,8 @@ def run_audit(device):
                           "median_J_old": float(np.median([r.reach.J_old for r in arm])),
                           "median_rank": float(np.median([r.rank for r in arm])),
                           "seconds_with_build": round(time.perf_counter() - t, 3)}
+            if name == "delay_only":  # the scalar probe ignores the source point
+                mech[name]["J_old_equals_resolved"] = mech[name]["J_old"] == out["J_old_resolved"]
         except Exception as exc:  # a measurement extra; report why it failed
             mech[name] = {"error": f"{type(exc).__name__}: {exc}"}
     out["mechanism_arms"] = mech
