@@ -1,4 +1,4 @@
-// Multi-geometry audit driver (Sec. 6.2-6.3): for each operator (geometry)
+// Multi-geometry audit (Sec. 6.2-6.3): for each operator (geometry)
 // and each observation arm, the age probes, anchor-connected reach, direct
 // age boundary and old-age innovation, and the restricted Gram spectrum with
 // its operational rank.  Host orchestration of the library's kernels.

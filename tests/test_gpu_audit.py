@@ -223,7 +223,7 @@ def test_eigvals_tridiagonal_matches_numpy():
         assert np.max(np.abs(ev[i][big] / ref[big] - 1.0)) <= 1e-11
 
 
-def test_rank_audit_driver_matches_oracle():
+def test_rank_audit_matches_oracle():
     """rtt_rank_audit over two geometries and two arms: rank, reach, J_old and
     A_0.999 against the oracle's audit of the same tables."""
     build.build()
