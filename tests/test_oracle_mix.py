@@ -278,3 +278,22 @@ def test_delay_only_and_spatial_only_reach(case):
         w.grid.n_nodes, w.time.n_hats).any(axis=1)
     if case == "schw32":
         assert not np.any(nz(td) & ~nz(tab.select((0,))))
+
+
+@pytest.mark.parametrize("mode", [O.MIX_UNRESOLVED, O.MIX_TOTAL_FLUX])
+def test_mixed_arm_reach_never_exceeds_resolved(schw, mode):
+    """The mixed arms use the resolved footprints (the union of the summed
+    orders') and the direct A_{0,0.999}; their probe information is below the
+    resolved one age by age, so their J_old is too, and their passing ages
+    are a subset of the resolved ones."""
+    w, tab = schw
+    scl = O.scale(tab)
+    res = O.probe_info(w, tab, scl)
+    mix = O.mix_probe_info(w, tab, scl, mode)
+    a0 = O.a0999(w, tab)
+    assert O.j_old(mix, a0) <= O.j_old(res, a0) * (1 + 1e-12)
+    r_res = O.reach(w, tab, res, (0, 1, 2))
+    r_mix = O.reach(w, tab, mix, (0, 1, 2))
+    assert not np.any(r_mix.passing & ~r_res.passing)
+    assert r_mix.anchor == r_res.anchor  # the anchor depends on the footprints only
+    assert r_mix.L_anchor <= r_res.L_anchor
