@@ -169,26 +169,6 @@ def test_pairing_destroyed_operator(schw):
     op.close()
 
 
-@pytest.mark.parametrize("arm", ["delay_only", "spatial_only"])
-def test_delay_only_and_spatial_only_operators(schw, arm):
-    """The operators built from the delay-only and spatial-only tables (ring
-    source points or ring delays moved to their direct quantile partners)
-    against the oracle on the same tables, and their probe information."""
-    import dataclasses
-    w, tab, _ = schw
-    t = getattr(I, arm)(_optable(tab))
-    tt = dataclasses.replace(tab, r=t["r"], phi=t["phi"], delay=t["delay"])
-    op = rtt.Operator(w, t)
-    x = I.uniform_batch(w, range(3))
-    scl = O.scale(tt)
-    assert abs(op.scale / scl - 1.0) < 1e-12
-    y = op.apply_A(torch.from_numpy(x).cuda()).cpu().numpy()
-    assert _rel(y, O.apply_A(w, tt, x, scl)) <= 1e-12
-    info = rtt.probe_info(op, 7)
-    assert _rel(info, O.probe_info(w, tt, scl)) <= 1e-5
-    op.close()
-
-
 def _subtable(tab, rows):
     rows = np.asarray(rows, np.int64)
     counts = tab.row_ptr[rows + 1] - tab.row_ptr[rows]
