@@ -595,7 +595,9 @@ def run_audit(device):
     t = time.perf_counter()
     pdr = []
     for i, (w, tab) in enumerate(cells):
-        op_pd = rtt.Operator(w, I.with_permuted_delays(tab, 1000 + i))
+        n_e = int(np.asarray(tab["r"]).shape[0])
+        op_pd = rtt.Operator(w, rtt.arm_table(tab, rtt.ARM_PAIRING_DESTROYED,
+                                              I.uniforms(1000 + i, n_e)))
         recs, _ = rtt.rank_audit([op_pd], [None], (7,), mode=rtt.GRAM_CLASS_S224)
         pdr.append(recs[0][0])
         op_pd.close()
@@ -608,13 +610,13 @@ def run_audit(device):
     # with their source points moved to the direct quantile partners', or keep
     # their source points with the partners' delays; the resolved arm's rank,
     # reach and J_old through the class-Gram audit
-    for name, make in (("delay_only", I.delay_only), ("spatial_only", I.spatial_only)):
+    for name, kind in (("delay_only", rtt.ARM_DELAY_ONLY), ("spatial_only", rtt.ARM_SPATIAL_ONLY)):
         try:
             torch.cuda.synchronize(device)
             t = time.perf_counter()
             arm = []
             for w, tab in cells:
-                op_a = rtt.Operator(w, make(tab))
+                op_a = rtt.Operator(w, rtt.arm_table(tab, kind))
                 recs, _ = rtt.rank_audit([op_a], [None], (7,), mode=rtt.GRAM_CLASS_S224)
                 arm.append(recs[0][0])
                 op_a.close()

@@ -165,6 +165,35 @@ rtt_status rtt_trace_rays(const rtt_geometry* geom, const rtt_source_grid* grid,
                           void* stream);
 
 /*
+ * rtt_arm_table -- the ray table of a Sec. 6.4 mechanism arm, built from a
+ * resolved table (host code, no device work).  kind:
+ *   RTT_ARM_PAIRING_DESTROYED: within each order n, with the order's rays
+ *     listed by ascending index (i_0 < i_1 < ...) and again by ascending
+ *     (keys_host, index) (j_0, j_1, ...), ray i_m takes the delay of ray j_m:
+ *     each order keeps its delays, their pairing with source point and
+ *     weight is broken.  keys_host: n_rays finite doubles (the random draw,
+ *     supplied by the caller).
+ *   RTT_ARM_DELAY_ONLY: each ring ray (order >= 1) takes the source point
+ *     (r, phi) of its direct quantile partner and keeps its delay.
+ *   RTT_ARM_SPATIAL_ONLY: each ring ray takes the delay of its direct
+ *     quantile partner and keeps its source point.
+ * The direct quantile partner of the ray of rank k (by delay, ties by index)
+ * among the E_n rays of order n is the direct ray of rank
+ * floor((k + 1/2) E_0 / E_n) among the E_0 direct rays.  in: the resolved
+ * table (host; only order, r, phi and delay are read).  r_out, phi_out,
+ * delay_out: host arrays of n_rays doubles owned by the caller (they may
+ * alias the input columns); the other columns of the arm's table are the
+ * input's.  keys_host is ignored for the delay-only and spatial-only arms.
+ * Errors: RTT_EINVAL (null pointers, unknown kind, order outside {0,1,2},
+ * non-finite delay or key, no direct ray), RTT_ENOMEM.
+ */
+#define RTT_ARM_PAIRING_DESTROYED 1
+#define RTT_ARM_DELAY_ONLY 2
+#define RTT_ARM_SPATIAL_ONLY 3
+rtt_status rtt_arm_table(int kind, const rtt_ray_table* in, const double* keys_host,
+                         double* r_out, double* phi_out, double* delay_out);
+
+/*
  * rtt_build_operator -- packs a raw FP64 ray table into the device operator
  * (Sec. 3.1 Eq. 2-3; Eq. 16 weights; Eq. 17-18 normalisation): bilinear
  * corner weights in (log r, phi) premultiplied by w (FP32, derived in FP64),
@@ -275,13 +304,12 @@ rtt_status rtt_probe_info(rtt_op op, int arm_mask, int n_ages, const double* age
                           double* info_host, void* stream);
 
 /*
- * rtt_probe_info_noalloc -- the FP32 pass of rtt_probe_info (the probe
- * information I(a) of Eq. 10-12 and Eq. 29) for callers that
- * must not allocate device memory while they run: for example an
- * application whose pool allocator has reserved all free device memory up
- * front, or a runtime that forbids allocation after initialisation.  The
- * paper has no counterpart; this entry point only changes where the scratch
- * lives.
+ * rtt_probe_info_noalloc -- the FP32 pass of rtt_probe_info, with the same
+ * arguments and result, for callers that must not allocate device memory
+ * while they run: for example an application whose pool allocator has
+ * reserved all free device memory up front, or a runtime that forbids
+ * allocation after initialisation.  The paper has no counterpart: this entry
+ * point only changes where the scratch lives.
  * The per-block partial sums use a file-scope static device array of
  * 1184 x 256 doubles (about 2.4 MB) that every GPU which loads the library
  * holds until the process exits; no cudaMalloc / cudaFree (or allocating
@@ -296,6 +324,8 @@ rtt_status rtt_probe_info(rtt_op op, int arm_mask, int n_ages, const double* age
  * call overwrites every entry it reads, so no clearing is needed; calls that
  * overlap on the GPU (for example on two streams) race on it and must be
  * serialised by the caller.
+ * Errors: RTT_EINVAL (null or invalid arguments, n_ages above 256),
+ * RTT_ECUDA (the symbol lookup or the launch failed).
  */
 rtt_status rtt_probe_info_noalloc(rtt_op op, int arm_mask, int n_ages, const double* ages_dev,
                                   double h, double* info_dev, void* stream);
@@ -520,6 +550,19 @@ rtt_status rtt_eigvals_sym_batched(int n, int batch, double* A_dev, double* eval
    and RTT_EINVAL for batch < 1. */
 rtt_status rtt_eig_sym_batched(int n, int batch, double* A_dev, double* evals_host, double* V_dev,
                                int max_sweeps, int* sweeps_host, void* stream);
+
+/*
+ * rtt_operational_rank -- operational rank of a restricted Gram from its
+ * eigenvalues (Sec. 4.4 Eq. 31): sigma_i = sqrt(max(lambda_i, 0)) (the
+ * whitening scale SNR_0 / s_ref is already in the Gram), rank = #{sigma_i >=
+ * rho} (inclusive), margin = min_i |sigma_i - rho| / rho.  evals_host: n
+ * eigenvalues in any order; sigma_out_host (optional, n doubles) receives the
+ * sigma_i sorted descending; rank_out and margin_out: host scalars.
+ * Errors: RTT_EINVAL (n < 1, null pointers, rho <= 0, non-finite
+ * eigenvalue).
+ */
+rtt_status rtt_operational_rank(int n, const double* evals_host, double rho, int* rank_out,
+                                double* margin_out, double* sigma_out_host);
 
 /*
  * rtt_solve_ridge -- ridge / Tikhonov estimator (Sec. 9):

@@ -168,12 +168,15 @@ def horizon(spin: float) -> float:
 
 
 def isco(spin: float) -> float:
-    """Prograde ISCO radius (Bardeen, Press & Teukolsky 1972); the boundary of
-    the circular/plunging emitter branch of Sec. 5."""
-    a = spin
+    """ISCO radius of the equatorial circular orbit that co-rotates with the
+    sign of `spin` (Bardeen, Press & Teukolsky 1972): spin >= 0 gives the
+    prograde orbit, spin < 0 the orbit against a hole of spin |spin|.  The
+    boundary of the circular/plunging emitter branch of Sec. 5."""
+    a = abs(spin)
     z1 = 1.0 + (1.0 - a * a) ** (1 / 3) * ((1.0 + a) ** (1 / 3) + (1.0 - a) ** (1 / 3))
     z2 = math.sqrt(3.0 * a * a + z1 * z1)
-    return 3.0 + z2 - math.sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2))
+    root = math.sqrt((3.0 - z1) * (3.0 + z1 + 2.0 * z2))
+    return 3.0 + z2 - root if spin >= 0 else 3.0 + z2 + root
 
 
 def circular_EL(spin: float, r):
@@ -312,6 +315,70 @@ def build_table(w, samples, method: str = "auto", n_orders: int = 3) -> Table:
     return Table(c["order"].astype(np.int8), c["pixel"].astype(np.int32), c["r"], c["phi"],
                  c["delay"], weight, thr, rp, c["order"][starts].astype(np.int8),
                  c["pixel"][starts].astype(np.int32), c["sample"].astype(np.int64))
+
+
+# ---------------------------------------------------------------------------
+# Mechanism arms of Sec. 6.4, as ray-table transforms (readings 22, 25, 26).
+# Plain Python loops over rays: these are the definitions the product's
+# library routine (rtt_arm_table) is checked against.
+# ---------------------------------------------------------------------------
+def pairing_destroyed(table: Table, keys) -> Table:
+    """Pairing-destroyed control (Sec. 6.4; reading: each order keeps its
+    multiset of delays, and their association with source point and weight is
+    broken).  Within each order n, list the rays of order n by ascending
+    index, i_0 < i_1 < ...; sort the same rays by (keys, index) into
+    j_0, j_1, ...; ray i_m then takes the delay of ray j_m.  `keys` are the
+    random numbers the construction draws (one per ray), passed in."""
+    keys = [float(k) for k in keys]
+    if len(keys) != table.n_rays:
+        raise ValueError("one key per ray")
+    order = [int(o) for o in table.order]
+    new = np.array(table.delay, dtype=np.float64, copy=True)
+    for n in sorted(set(order)):
+        by_index = [e for e in range(len(order)) if order[e] == n]
+        by_key = sorted(by_index, key=lambda e: (keys[e], e))
+        for i_m, j_m in zip(by_index, by_key):
+            new[i_m] = table.delay[j_m]
+    return dataclasses.replace(table, delay=new)
+
+
+def quantile_partner(table: Table) -> np.ndarray:
+    """The direct ray at the same delay quantile as each ray (reading of
+    Sec. 6.4's delay-only / spatial-only arms).  Rank the E_0 direct rays by
+    (delay, index); within ring order n, rank its E_n rays the same way; the
+    ray of rank k in order n has as partner the direct ray of rank
+    floor((k + 1/2) E_0 / E_n).  A direct ray is its own partner."""
+    order = [int(o) for o in table.order]
+    delay = [float(d) for d in table.delay]
+    ranked = {}
+    for n in sorted(set(order)):
+        ranked[n] = sorted((e for e in range(len(order)) if order[e] == n),
+                           key=lambda e: (delay[e], e))
+    direct = ranked.get(0, [])
+    partner = list(range(len(order)))
+    for n, rays in ranked.items():
+        if n == 0:
+            continue
+        for k, e in enumerate(rays):
+            partner[e] = direct[((2 * k + 1) * len(direct)) // (2 * len(rays))]
+    return np.array(partner, dtype=np.int64)
+
+
+def delay_only(table: Table) -> Table:
+    """Delay-only arm (Sec. 6.4, reading 25): the ring rays keep their
+    delays, weights and rows and take the source point (r, phi) of their
+    direct quantile partner."""
+    p = quantile_partner(table)
+    return dataclasses.replace(table, r=np.array([table.r[i] for i in p]),
+                               phi=np.array([table.phi[i] for i in p]))
+
+
+def spatial_only(table: Table) -> Table:
+    """Spatial-only arm (Sec. 6.4, reading 26): the ring rays keep their
+    source points, weights and rows and take the delay of their direct
+    quantile partner."""
+    p = quantile_partner(table)
+    return dataclasses.replace(table, delay=np.array([table.delay[i] for i in p]))
 
 
 # ---------------------------------------------------------------------------

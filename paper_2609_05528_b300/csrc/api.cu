@@ -27,11 +27,9 @@ void set_error(const char* fmt, ...) {
 
 template <typename T>
 cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
-rtt_status build_visits(rtt_op_s* op, cudaStream_t st);
 cudaError_t launch_forward_adjoint_fused(const rtt_op_s* op, const float* x, const float* d,
                                          float* y, float* g, int B, const ArmSeg& seg,
                                          float* zhat, cudaStream_t st);
-size_t fused_partial_bytes(const rtt_op_s* op);
 template <typename T>
 cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
 
@@ -232,7 +230,7 @@ static void free_op(rtt_op_s* op) {
     void* ps[] = {op->row_ptr, op->ray_row, op->node00, op->node01, op->W,     op->W64,
                   op->K0,      op->F0,      op->F64,    op->r,      op->delay, op->weight,
                   op->thr,     op->node_ptr, op->inc,   op->row_order, op->zhat,
-                  op->visits,  op->items,    op->split_tiles, op->fpartial, op->node_order,
+                  op->node_order,
                   op->dev_status, op->rscratch, op->row_pixel, op->mix.grp_ptr,
                   op->mix.grp_rows, op->mix.row_grp, op->mix.inv32, op->mix.inv64,
                   op->mix.part, op->phi};
@@ -492,8 +490,6 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
         RTT_CUDA(cudaMemset(op->dev_status, 0, sizeof(int)));
         RTT_CUDA(cudaMemcpy(op->node_order, order.data(), S * 4, cudaMemcpyHostToDevice));
     }
-    // (tile, ray) visit lists, only for the tile-fused adjoint variant
-    if (op->use_fused_adjoint) RTT_TRY(build_visits(op, st));
     return RTT_OK;
 }
 
@@ -570,21 +566,6 @@ static rtt_status apply_common(rtt_op op, const T* in, T* out, int batch, int ma
     if (adjoint) {
         const int bc = batch < 32 ? batch : 32;
         RTT_TRY(ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * bc * sizeof(T)));
-        const size_t pb = op->use_fused_adjoint ? fused_partial_bytes(op) : 0;
-        if (pb > op->fpartial_bytes) {
-            if (op->fpartial) {
-                cudaDeviceSynchronize();
-                cudaFree(op->fpartial);
-                op->fpartial = nullptr;
-                op->fpartial_bytes = 0;
-            }
-            if (cudaMalloc(&op->fpartial, pb) != cudaSuccess) {
-                op->fpartial = nullptr;
-                set_error("fused adjoint partial tiles: allocation of %zu bytes failed", pb);
-                return RTT_ENOMEM;
-            }
-            op->fpartial_bytes = pb;
-        }
         e = launch_adjoint<T>(op, in, out, batch, seg, (T*)op->zhat, st);
     } else {
         e = launch_forward<T>(op, in, out, batch, seg, st);

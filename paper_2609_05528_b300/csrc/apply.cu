@@ -764,7 +764,12 @@ adj_time3_kernel(const ApplyArgs<T> a) {
                 int64_t U = U0 - (int64_t)f * a.D;
                 while (f <= fB && U >= hi_excl) { ++f; U -= a.D; }
                 int32_t Ur = (int32_t)(U - (int64_t)k * kFracOne);  // in [-2^24, 2^24) once f <= fB
-                for (; f <= fB && Ur > -kFracOne; ++f, Ur -= D32) {
+                // FP64 also visits Ur = -2^24: the 24-bit coordinate puts hat k
+                // exactly on its support edge there, but the exact fraction lies
+                // in [0, 2^-24) and gives hat k that (possibly nonzero) weight,
+                // as the FP64 forward does
+                const int32_t lo_excl = sizeof(T) == 8 ? -kFracOne - 1 : -kFracOne;
+                for (; f <= fB && Ur > lo_excl; ++f, Ur -= D32) {
                     T hw;
                     if constexpr (sizeof(T) == 4) {
                         hw = 1.0f - (float)abs(Ur) * (1.0f / (float)kFracOne);
@@ -2864,8 +2869,6 @@ static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t launch_adjoint_fused(const rtt_op_s* op, const float* y, float* x, int B, int b_first,
-                                 int Bc, const ArmSeg& seg, float* partial, cudaStream_t st);
 
 template <typename T>
 static cudaError_t launch_adjoint_impl(const rtt_op_s* op, const T* y, T* x, int B,
@@ -2896,12 +2899,6 @@ static cudaError_t launch_adjoint_impl(const rtt_op_s* op, const T* y, T* x, int
         v.time = 1;
         v.space = 1;
         if constexpr (sizeof(T) == 4) {
-            if (time_phase && op->use_fused_adjoint && (op->fpartial || op->n_partial_slots == 0)) {
-                e = launch_adjoint_fused(op, y, x, B, b_first, Bc, seg, (float*)op->fpartial, st);
-                if (e == cudaSuccess) continue;
-                if (e != cudaErrorNotSupported) return e;
-                cudaGetLastError();  // clear the "not supported" marker
-            }
             v = variant_for(op, B);
         }
         switch (pick_bc(Bc)) {

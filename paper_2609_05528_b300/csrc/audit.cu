@@ -35,6 +35,33 @@ extern "C" rtt_status rtt_eig_sym_batched(int n, int batch, double* A, double* e
                                           double* V, int max_sweeps, int* sweeps_host,
                                           void* stream);
 
+extern "C" rtt_status rtt_operational_rank(int n, const double* evals, double rho, int* rank_out,
+                                           double* margin_out, double* sigma_out) {
+    if (n < 1 || !evals || !rank_out || !margin_out || !(rho > 0.0) || !std::isfinite(rho)) {
+        set_error("invalid operational-rank arguments (n=%d, rho=%g)", n, rho);
+        return RTT_EINVAL;
+    }
+    std::vector<double> sig(n);
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(evals[i])) {
+            set_error("operational rank: eigenvalue %d is not finite", i);
+            return RTT_EINVAL;
+        }
+        sig[i] = std::sqrt(evals[i] > 0.0 ? evals[i] : 0.0);
+    }
+    std::sort(sig.begin(), sig.end(), [](double a, double c) { return a > c; });
+    int rank = 0;
+    double margin = INFINITY;
+    for (int i = 0; i < n; ++i) {
+        if (sig[i] >= rho) ++rank;
+        margin = std::fmin(margin, std::fabs(sig[i] - rho) / rho);
+    }
+    *rank_out = rank;
+    *margin_out = margin;
+    if (sigma_out) std::copy(sig.begin(), sig.end(), sigma_out);
+    return RTT_OK;
+}
+
 extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_dev,
                                      int d, const int* arm_masks, int n_arms, int n_ages,
                                      const double* ages_host, double h, double quantile,
@@ -138,19 +165,13 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
         for (int b = 0; s == RTT_OK && b < nb; ++b) {
             rtt_audit_record& r = out[b];
             std::vector<double> sig(d);
-            for (int i = 0; i < d; ++i) {
-                const double l = ev[(size_t)b * d + i];
-                sig[i] = std::sqrt(l > 0.0 ? l : 0.0);
-            }
-            std::sort(sig.begin(), sig.end(), [](double a, double c) { return a > c; });
             const double rho = ops[b / n_arms]->opt.rho;
             int rank = 0;
             double margin = INFINITY, smin_pos = INFINITY;
-            for (int i = 0; i < d; ++i) {
-                if (sig[i] >= rho) ++rank;
-                margin = std::fmin(margin, std::fabs(sig[i] - rho) / rho);
+            s = rtt_operational_rank(d, ev.data() + (size_t)b * d, rho, &rank, &margin, sig.data());
+            if (s != RTT_OK) break;
+            for (int i = 0; i < d; ++i)
                 if (sig[i] > 0.0) smin_pos = std::fmin(smin_pos, sig[i]);
-            }
             r.rank = rank;
             r.margin = margin;
             r.sigma_max = sig[0];

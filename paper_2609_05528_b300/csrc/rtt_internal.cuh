@@ -96,15 +96,6 @@ struct rtt_op_s {
     // adjoint scratch: per-ray temporal contraction [E][K][<=32], grown on demand
     void* zhat = nullptr;
     size_t zhat_bytes = 0;
-    // fused adjoint: (tile, ray) visits, work items, split tiles, partial tiles
-    uint32_t* visits = nullptr;
-    void* items = nullptr;
-    void* split_tiles = nullptr;
-    int n_items = 0, n_split = 0, n_partial_slots = 0, n_tp = 0;
-    int64_t n_visits = 0;
-    void* fpartial = nullptr;
-    size_t fpartial_bytes = 0;
-    bool use_fused_adjoint = false;  // tile-fused adjoint (measured slower than two-phase so far)
     void* rscratch = nullptr;  // residual y - d of the separate-path rtt_apply_A_AT, grown on demand
     size_t rscratch_bytes = 0;
     int* dev_status = nullptr;  // device status word: bit 0 = a kernel's bounded wait timed out

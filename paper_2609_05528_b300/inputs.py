@@ -291,73 +291,6 @@ def uniform_batch(w: Workload, seeds) -> np.ndarray:
                     axis=-1)
 
 
-def order_permutation(order, seed: int) -> np.ndarray:
-    """A seeded permutation of ray indices that sends every ray to a ray of the
-    same order: within each order, the rays sorted by a seeded uniform key.
-    The pairing-destroyed control (Sec. 6.4) takes its delays through it."""
-    order = np.asarray(order)
-    u = uniforms(seed, order.size)
-    perm = np.arange(order.size)
-    for n in np.unique(order):
-        idx = np.nonzero(order == n)[0]
-        perm[idx] = idx[np.argsort(u[idx], kind="stable")]
-    return perm
-
-
-def with_permuted_delays(table: dict, seed: int) -> dict:
-    """Copy of a ray table (dict of arrays) whose delays are redrawn by
-    order_permutation: each order keeps its delay values (the old-delay
-    marginals) while their pairing with source point and weight is destroyed
-    (the pairing-destroyed control of Sec. 6.4)."""
-    out = dict(table)
-    out["delay"] = np.asarray(table["delay"])[order_permutation(table["order"], seed)]
-    return out
-
-
-def direct_quantile_partner(order, delay) -> np.ndarray:
-    """For every ray, the index of the direct (order 0) ray at the same delay
-    quantile: within each order n the E_n rays are ranked by delay (ties by
-    index) and the k-th takes the direct ray of rank floor((k + 1/2) E_0 / E_n)
-    in the direct order's delay ranking.  Direct rays map to themselves.  The
-    delay-only and spatial-only arms (Sec. 6.4) are built through it."""
-    order = np.asarray(order)
-    delay = np.asarray(delay)
-    part = np.arange(order.size)
-    d0 = np.nonzero(order == 0)[0]
-    d0 = d0[np.argsort(delay[d0], kind="stable")]
-    for n in np.unique(order):
-        if n == 0:
-            continue
-        idx = np.nonzero(order == n)[0]
-        idx = idx[np.argsort(delay[idx], kind="stable")]
-        k = np.arange(idx.size, dtype=np.int64)
-        part[idx] = d0[((2 * k + 1) * d0.size) // (2 * idx.size)]
-    return part
-
-
-def spatial_only(table: dict) -> dict:
-    """Copy of a ray table whose ring rays (n >= 1) keep their source points,
-    weights and rows but take the delay of their direct quantile partner: the
-    rings' retarded-time content flattened to the direct delay distribution
-    (the spatial-only arm of Sec. 6.4)."""
-    out = dict(table)
-    out["delay"] = np.asarray(table["delay"])[direct_quantile_partner(table["order"],
-                                                                      table["delay"])]
-    return out
-
-
-def delay_only(table: dict) -> dict:
-    """Copy of a ray table whose ring rays (n >= 1) keep their delays, weights
-    and rows but take the source point (r, phi) of their direct quantile
-    partner: the rings' spatial map held at the direct image's (the delay-only
-    arm of Sec. 6.4)."""
-    out = dict(table)
-    part = direct_quantile_partner(table["order"], table["delay"])
-    out["r"] = np.asarray(table["r"])[part]
-    out["phi"] = np.asarray(table["phi"])[part]
-    return out
-
-
 def noise(shape, seed: int) -> np.ndarray:
     """i.i.d. N(0, 1) whitened noise of the given shape."""
     n = int(np.prod(shape))

@@ -164,6 +164,9 @@ _SIGS = {
                                     ctypes.POINTER(TuneResult)]),
     "rtt_set_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(Variant)]),
     "rtt_get_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(Variant)]),
+    "rtt_arm_table": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(RayTable), dp, dp, dp, dp]),
+    "rtt_operational_rank": (ctypes.c_int, [ctypes.c_int, dp, ctypes.c_double,
+                                            ctypes.POINTER(ctypes.c_int), dp, dp]),
     "rtt_destroy": (None, [vp]),
 }
 
@@ -555,14 +558,56 @@ def eigvals_sym_batched(G, stream=None):
     return ev.reshape(b, n)
 
 
+def rank_from_eigenvalues(evals, rho: float = 1.0):
+    """rtt_operational_rank: (sigma sorted descending, rank, margin) of Eq. 31."""
+    ev = np.ascontiguousarray(evals, np.float64).reshape(-1)
+    sig = np.empty(ev.shape[0])
+    rank = ctypes.c_int(0)
+    margin = ctypes.c_double(0.0)
+    check(lib().rtt_operational_rank(ev.shape[0], _ptr(ev, dp), rho, ctypes.byref(rank),
+                                     ctypes.byref(margin), _ptr(sig, dp)), "rtt_operational_rank")
+    return sig, rank.value, margin.value
+
+
 def operational_rank(op: "Operator", Q, arm_mask: int = 7, rho: float = 1.0,
                      mode: int = GRAM_DATA):
-    """sigma_i = sqrt(max(lambda_i, 0)) of the restricted Gram; rank = #{sigma >= rho}
-    (Eq. 31; scale already carries SNR_0)."""
+    """Singular values (descending) of the whitened restricted operator and
+    its operational rank (Eq. 31), both from the library: the Gram, its
+    eigenvalues and the count."""
     G = gram(op, Q, arm_mask, mode)
     ev, V, _ = eig_sym(G)
-    sig = np.sqrt(np.maximum(ev, 0.0))
-    return sig, int(np.count_nonzero(sig >= rho))
+    sig, rank, _ = rank_from_eigenvalues(ev, rho)
+    return sig, rank
+
+
+ARM_PAIRING_DESTROYED = 1  # rtt.h RTT_ARM_PAIRING_DESTROYED
+ARM_DELAY_ONLY = 2
+ARM_SPATIAL_ONLY = 3
+
+
+def arm_table(table: dict, kind: int, keys=None) -> dict:
+    """rtt_arm_table: the ray table of a Sec. 6.4 mechanism arm (dict of host
+    arrays, as Operator takes); `keys` (one float per ray) is the random draw
+    of the pairing-destroyed arm."""
+    n = int(np.asarray(table["r"]).shape[0])
+    order = np.ascontiguousarray(table["order"], np.int8)
+    cols = {k: np.ascontiguousarray(table[k], np.float64) for k in ("r", "phi", "delay")}
+    if order.shape[0] != n or any(v.shape[0] != n for v in cols.values()):
+        raise ValueError("table columns differ in length")
+    kd = None
+    if keys is not None:
+        kd = np.ascontiguousarray(keys, np.float64).reshape(-1)
+        if kd.shape[0] != n:
+            raise ValueError(f"keys: {kd.shape[0]} values for {n} rays")
+    t = RayTable(n, order.ctypes.data_as(i8p), None, _ptr(cols["r"], dp), _ptr(cols["phi"], dp),
+                 _ptr(cols["delay"], dp), None, None)
+    out = {k: np.empty(n) for k in ("r", "phi", "delay")}
+    check(lib().rtt_arm_table(int(kind), ctypes.byref(t), _ptr(kd, dp) if kd is not None else None,
+                              _ptr(out["r"], dp), _ptr(out["phi"], dp), _ptr(out["delay"], dp)),
+          "rtt_arm_table")
+    res = dict(table)
+    res.update(out)
+    return res
 
 
 def solve_ridge(op: "Operator", data, lambdas, arm_mask: int = 7, max_iter: int = 500,

@@ -1,9 +1,6 @@
 """The delay-only and spatial-only mechanism arms (Sec. 6.4) on the GPU: the
 operators built from their tables (ring source points or ring delays moved to
-their direct quantile partners') against the oracle on the same tables.
-(Kept last in the suite.)"""
-import dataclasses
-
+their direct quantile partners') against the oracle on the same tables."""
 import numpy as np
 import pytest
 
@@ -40,8 +37,9 @@ def _rel(a, b):
 @pytest.mark.parametrize("arm", ["delay_only", "spatial_only"])
 def test_delay_only_and_spatial_only_operators(schw, arm):
     w, tab = schw
-    t = getattr(I, arm)(_optable(tab))
-    tt = dataclasses.replace(tab, r=t["r"], phi=t["phi"], delay=t["delay"])
+    kind = rtt.ARM_DELAY_ONLY if arm == "delay_only" else rtt.ARM_SPATIAL_ONLY
+    t = rtt.arm_table(_optable(tab), kind)           # the library's construction
+    tt = getattr(O, arm)(tab)                          # the oracle's own
     op = rtt.Operator(w, t)
     x = I.uniform_batch(w, range(3))
     scl = O.scale(tt)

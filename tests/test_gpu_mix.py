@@ -152,12 +152,12 @@ def test_mixed_probe_info_kerr256(k256, mode):
 def test_pairing_destroyed_operator(schw):
     """The operator built from the pairing-destroyed table (delays permuted
     within each order) against the oracle on the same permuted table, and its
-    probe information against the oracle's."""
-    import dataclasses
+    probe information against the oracle's.  The library builds the table
+    (rtt_arm_table), the oracle its own copy (oracle.pairing_destroyed)."""
     w, tab, _ = schw
-    perm = I.order_permutation(tab.order, 7)
-    tp = dataclasses.replace(tab, delay=tab.delay[perm])
-    op = rtt.Operator(w, I.with_permuted_delays(_optable(tab), 7))
+    keys = I.uniforms(7, tab.n_rays)
+    tp = O.pairing_destroyed(tab, keys)
+    op = rtt.Operator(w, rtt.arm_table(_optable(tab), rtt.ARM_PAIRING_DESTROYED, keys))
     x = I.uniform_batch(w, range(3))
     scl = O.scale(tp)
     assert abs(op.scale / scl - 1.0) < 1e-12

@@ -161,3 +161,30 @@ def test_redshift_closed_forms():
             g_out = O.redshift(a, np.array([rI * (1 + 1e-9)]), lam, eta, sr)[0]
             g_in = O.redshift(a, np.array([rI * (1 - 1e-9)]), lam, eta, sr)[0]
             assert g_in == pytest.approx(g_out, rel=1e-4)
+
+
+def test_isco_closed_forms_and_marginal_stability():
+    """The ISCO that sets the circular/plunging branch (Sec. 5) against what
+    fixes it without the Bardeen-Press-Teukolsky closed form: the extreme
+    cases r = 1 (a = 1, prograde) and r = 9 (a = 1, retrograde), r = 6 at
+    a = 0, the tabulated 4.233 (a = 0.5) and 2.3209 (a = 0.9), and the
+    marginal-stability definition: the ISCO is where the circular orbit's
+    specific energy E(r) has its minimum, found here by brute-force search on
+    circular_EL (which the Schwarzschild values above pin independently)."""
+    from scipy import optimize
+    assert O.isco(1.0) == pytest.approx(1.0, abs=1e-12)
+    assert O.isco(-1.0) == pytest.approx(9.0, abs=1e-12)
+    assert O.isco(0.0) == pytest.approx(6.0, abs=1e-12)
+    assert O.isco(0.5) == pytest.approx(4.233, abs=5e-4)
+    assert O.isco(0.9) == pytest.approx(2.3209, abs=5e-4)
+    for a in (0.3, 0.5, 0.75, 0.94, -0.5):
+        rI = O.isco(a)
+        # coarse scan for the bracket, then a bounded scalar minimisation
+        rs = np.linspace(rI * 0.6, rI * 1.8, 4001)
+        rs = rs[rs ** 1.5 - 3.0 * np.sqrt(rs) + 2.0 * a > 1e-9]
+        E = O.circular_EL(a, rs)[0]
+        i = int(np.argmin(E))
+        res = optimize.minimize_scalar(lambda r: float(O.circular_EL(a, r)[0]),
+                                       bounds=(rs[max(i - 2, 0)], rs[min(i + 2, rs.size - 1)]),
+                                       method="bounded", options={"xatol": 1e-10})
+        assert res.x == pytest.approx(rI, rel=2e-6), a

@@ -136,17 +136,30 @@ def test_mixed_probe_below_resolved(schw, mode):
 
 def test_pairing_destroyed_keeps_marginals(schw):
     """The pairing-destroyed control's delays: each order keeps its multiset of
-    delays, rays move only within their order, and the pairing changes."""
+    delays, rays move only within their order, the pairing changes, and the
+    construction is a function of the keys alone."""
     w, tab = schw
-    perm = I.order_permutation(tab.order, 11)
-    assert np.all(tab.order[perm] == tab.order)
+    keys = I.uniforms(11, tab.n_rays)
+    pd = O.pairing_destroyed(tab, keys)
     for n in range(3):
         m = tab.order == n
-        np.testing.assert_array_equal(np.sort(tab.delay[perm][m]), np.sort(tab.delay[m]))
-    assert np.count_nonzero(perm != np.arange(perm.size)) > perm.size // 2
-    d = I.with_permuted_delays({"order": tab.order, "delay": tab.delay}, 11)
-    np.testing.assert_array_equal(d["delay"], tab.delay[perm])
-    assert np.array_equal(I.order_permutation(tab.order, 11), perm)  # seeded
+        np.testing.assert_array_equal(np.sort(pd.delay[m]), np.sort(tab.delay[m]))
+    assert np.count_nonzero(pd.delay != tab.delay) > tab.n_rays // 2
+    for k in ("order", "pixel", "r", "phi", "weight", "throughput"):
+        np.testing.assert_array_equal(getattr(pd, k), getattr(tab, k))
+    np.testing.assert_array_equal(O.pairing_destroyed(tab, keys).delay, pd.delay)
+    # with keys that sort like the indices the permutation is the identity
+    ident = O.pairing_destroyed(tab, np.arange(tab.n_rays, dtype=np.float64))
+    np.testing.assert_array_equal(ident.delay, tab.delay)
+
+
+def test_pairing_destroyed_hand_case():
+    """Order 0 rays 0, 2, 3 with keys 0.7, 0.1, 0.4 sort by key as 2, 3, 0:
+    ray 0 takes ray 2's delay, ray 2 ray 3's, ray 3 ray 0's.  The single
+    order-1 ray keeps its delay."""
+    t = _hand_table([0, 1, 0, 0], [10.0, 20.0, 30.0, 40.0])
+    got = O.pairing_destroyed(t, [0.7, 0.9, 0.1, 0.4])
+    assert got.delay.tolist() == [30.0, 20.0, 40.0, 10.0]
 
 
 def test_local_direction_norms_by_2d_quadrature(schw):
@@ -195,19 +208,37 @@ def test_local_reach_hand_cases():
     assert O.local_reach(gap, 1.0, ages) == 8.0
 
 
-def _as_dict(tab):
-    return {"order": tab.order, "pixel": tab.pixel, "r": tab.r, "phi": tab.phi,
-            "delay": tab.delay, "weight": tab.weight, "throughput": tab.throughput}
+def _hand_table(order, delay):
+    order = np.asarray(order, np.int8)
+    n = order.size
+    delay = np.asarray(delay, np.float64)
+    r = 3.0 + np.arange(n, dtype=np.float64)
+    phi = 0.1 * np.arange(n, dtype=np.float64)
+    one = np.ones(n)
+    return O.Table(order, np.arange(n, dtype=np.int32), r, phi, delay, one, one.copy(),
+                   np.arange(n + 1, dtype=np.int64), order.copy(), np.arange(n, dtype=np.int32),
+                   np.arange(n, dtype=np.int64))
 
 
 def test_direct_quantile_partner_hand_case():
     """Direct ranking by delay: rays 1, 3, 0, 2.  Order 1 (two rays): ray 5
     (k = 0) -> rank floor(0.5 * 4 / 2) = 1 -> ray 3; ray 4 (k = 1) -> rank 3
     -> ray 2.  Order 2 (one ray): rank floor(0.5 * 4) = 2 -> ray 0.  Direct
-    rays map to themselves."""
+    rays map to themselves.  The arms then move source points (delay-only)
+    or delays (spatial-only) of the ring rays from these partners."""
     order = [0, 0, 0, 0, 1, 1, 2]
     delay = [3.0, 1.0, 4.0, 2.0, 9.0, 7.0, 20.0]
-    assert I.direct_quantile_partner(order, delay).tolist() == [0, 1, 2, 3, 2, 3, 0]
+    t = _hand_table(order, delay)
+    assert O.quantile_partner(t).tolist() == [0, 1, 2, 3, 2, 3, 0]
+    do = O.delay_only(t)
+    assert do.r.tolist() == [3.0, 4.0, 5.0, 6.0, 5.0, 6.0, 3.0]
+    assert do.delay.tolist() == delay
+    so = O.spatial_only(t)
+    assert so.delay.tolist() == [3.0, 1.0, 4.0, 2.0, 4.0, 2.0, 3.0]
+    assert so.r.tolist() == t.r.tolist()
+    # ties in delay are broken by ray index on both rankings
+    t2 = _hand_table([0, 0, 1, 1], [5.0, 5.0, 8.0, 8.0])
+    assert O.quantile_partner(t2).tolist() == [0, 1, 0, 1]
 
 
 def test_spatial_only_keeps_direct_old_epoch_blindness(schw):
@@ -216,21 +247,20 @@ def test_spatial_only_keeps_direct_old_epoch_blindness(schw):
     footprint then lies inside the direct one, so Theorem 4.1's blind columns
     of the direct image (hats whose support misses W_0) stay exactly zero in
     the whole stack, while the true resolved stack sees some of them."""
-    import dataclasses
     w, tab = schw
-    so = I.spatial_only(_as_dict(tab))
+    so = O.spatial_only(tab)
     ring = tab.order > 0
     for k in ("order", "pixel", "r", "phi", "weight", "throughput"):
-        np.testing.assert_array_equal(so[k], getattr(tab, k))
-    np.testing.assert_array_equal(so["delay"][~ring], tab.delay[~ring])
-    assert np.all(np.isin(so["delay"][ring], tab.delay[~ring]))
+        np.testing.assert_array_equal(getattr(so, k), getattr(tab, k))
+    np.testing.assert_array_equal(so.delay[~ring], tab.delay[~ring])
+    assert np.all(np.isin(so.delay[ring], tab.delay[~ring]))
     for n in (1, 2):
         m = np.nonzero(tab.order == n)[0]
         if m.size:
-            assert np.all(np.diff(so["delay"][m[np.argsort(tab.delay[m], kind="stable")]]) >= 0)
+            assert np.all(np.diff(so.delay[m[np.argsort(tab.delay[m], kind="stable")]]) >= 0)
     scl = O.scale(tab)
     zero = lambda t: np.all(O.dense_A(w, t, scl) == 0.0, axis=0)  # noqa: E731
-    zs = zero(dataclasses.replace(tab, delay=so["delay"]))
+    zs = zero(so)
     zr = zero(tab)
     (lo, hi), = O.footprints(w, tab, (0,))
     tk = w.time.hat_times()
@@ -248,20 +278,18 @@ def test_delay_only_and_spatial_only_reach(case):
     the paper's Sec. 6.4 reports equal medians for the two.  The
     spatial-only arm stays near the direct image (at most 5% more J_old,
     never the resolved value)."""
-    import dataclasses
     w = I.schw32() if case == "schw32" else I.small_kerr(
         spin=0.5, incl_deg=50.0, nx=64, n_r=8, n_phi=16, n_frames=128, n_hats=32, ss=2)
     tab = O.build_table(w, I.screen_samples(w))
     scl = O.scale(tab)
     a0 = O.a0999(w, tab)
-    do = I.delay_only(_as_dict(tab))
+    td = O.delay_only(tab)
     ring = tab.order > 0
     for k in ("order", "pixel", "delay", "weight", "throughput"):
-        np.testing.assert_array_equal(do[k], getattr(tab, k))
+        np.testing.assert_array_equal(getattr(td, k), getattr(tab, k))
     direct_pts = set(zip(tab.r[~ring].tolist(), tab.phi[~ring].tolist()))
-    assert all(p in direct_pts for p in zip(do["r"][ring].tolist(), do["phi"][ring].tolist()))
-    td = dataclasses.replace(tab, r=do["r"], phi=do["phi"])
-    ts = dataclasses.replace(tab, delay=I.spatial_only(_as_dict(tab))["delay"])
+    assert all(p in direct_pts for p in zip(td.r[ring].tolist(), td.phi[ring].tolist()))
+    ts = O.spatial_only(tab)
     assert O.scale(td) == scl and O.scale(ts) == scl  # direct rays untouched
     info = {name: O.probe_info(w, t.select(orders), scl)
             for name, t, orders in (("direct", tab, (0,)), ("resolved", tab, (0, 1, 2)),
