@@ -128,7 +128,7 @@ def kernel_source_hash() -> str:
     profiles/ is used only while this hash is unchanged."""
     import hashlib
     h = hashlib.sha256()
-    for name in ("apply.cu", "rtt_internal.cuh"):
+    for name in ("apply.cu", "adjoint.cu", "kern_common.cuh", "rtt_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2609_05528_b300", "csrc", name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -156,7 +156,9 @@ def algorithmic_bytes(op, B, elem=4):
     y = R * op.n_frames * B * elem
     x = S * op.n_hats * B * elem
     table_fwd = E * 32 + (R + 1) * 4
-    table_adj = E * 36 + 4 * E * 4 + (S + 1) * 4
+    # adjoint: the cell-ordered ray table (row, column, hat base and fraction,
+    # four corner weights) and the gather table (four record indices per node)
+    table_adj = E * 32 + S * 16
     return {"A": y + x + table_fwd, "AT": y + x + table_adj, "y": y, "x": x}
 
 
@@ -206,28 +208,6 @@ def run_ours(args, rank, world, device):
     t_AT = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
     ms_step = max_over_ranks(float(np.mean([a + b for a, b in zip(t_A, t_AT)])), world, device)
     clocks = clk.summary()
-
-    # the same pair through rtt_apply_A_AT (fused forward + temporal adjoint
-    # when the batch and cadence allow it: y is not read back from HBM)
-    fused = None
-    try:
-        for _ in range(3):
-            op.apply_A_AT(x, None, y, g)
-        torch.cuda.synchronize(device)
-        f_ms = []
-        for _ in range(args.steps):
-            flush.zero_()
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            op.apply_A_AT(x, None, y, g)
-            a1.record(stream)
-            a1.synchronize()
-            f_ms.append(a0.elapsed_time(a1))
-        fm = max_over_ranks(float(np.mean(f_ms)), world, device)
-        fused = {"ms_per_step": fm, "value": job_value(world, BATCH, fm)}
-    except Exception as exc:
-        fused = {"error": str(exc)[:200]}
 
     # the same A + A^T pair replayed from a captured CUDA graph (the library
     # allocates nothing once its adjoint scratch exists, so the calls capture)
@@ -404,7 +384,6 @@ def run_ours(args, rank, world, device):
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4)},
         "fp64_path": {"value": job_value(world, BATCH, fp64_ms), "ms_per_step": fp64_ms},
         "cuda_graph": graph,
-        "fused_A_AT": fused,
         "order_mix": mix,
         "clocks": clocks,
         "gpu_launches": launches_per_step(BATCH) * args.steps,
@@ -438,7 +417,7 @@ def job_value(world: int, batch: int, ms: float) -> float:
 
 def launches_per_step(B: int) -> int:
     """Kernel launches of one A + A^T pair: one forward launch; per 32-column
-    batch chunk one temporal and one spatial adjoint launch."""
+    batch pass one cell kernel and one gather launch."""
     return 1 + 2 * ((B + 31) // 32)
 
 
@@ -482,8 +461,7 @@ def run_sweep(device, batches=(1, 2, 4, 8, 16, 32, 64), reps: int = 5):
             tT = float(np.mean([b.elapsed_time(c) for _, b, c in ev]))
             ab = algorithmic_bytes(op, B)
             res.append({"batch": B, "A_ms": tA, "AT_ms": tT,
-                        "variant": [tune["fwd_kernel"], tune["fwd_bc"], tune["time_kernel"],
-                                    tune["space_kernel"]],
+                        "variant": [tune["fwd_kernel"], tune["fwd_bc"], tune["adj_kernel"]],
                         "rule_ms": [tune["fwd_ms_rule"], tune["adj_ms_rule"]],
                         "A_gbs": ab["A"] / (tA * 1e-3) / 1e9, "AT_gbs": ab["AT"] / (tT * 1e-3) / 1e9,
                         "A_frac": ab["A"] / (tA * 1e-3) / 1e9 / peak,

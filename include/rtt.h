@@ -274,14 +274,9 @@ rtt_status rtt_apply_AT_f64(rtt_op op, const double* y_dev, double* x_dev, int b
  * x_dev: float [n_nodes][n_hats][batch]; d_dev: float [arm_rows][n_frames]
  * [batch] or NULL (then g = scale * A^T y); y_dev: float [arm_rows][n_frames]
  * [batch] (written; may be NULL only when the arm has no rows); g_dev: float
- * [n_nodes][n_hats][batch] (written).  For batch 4 or 8, 16-byte aligned
- * buffers and 2, 4 or 8 frames per hat step, a fused kernel can compute y
- * and keep y - d in shared memory for the temporal half of the adjoint, so y
- * is not read back from HBM; it runs when the operator's variant for this
- * batch says so (rtt_autotune picks it where it is faster, rtt_set_variant
- * pins it).  Otherwise the separate forward and adjoint run (y - d formed in
- * an operator-owned scratch that grows on demand).
- * Both paths give the bits of rtt_apply_A followed by rtt_apply_AT on
+ * [n_nodes][n_hats][batch] (written).  The forward runs, y - d is formed in
+ * an operator-owned scratch that grows on demand (when d is given), and the
+ * adjoint runs on it: the bits of rtt_apply_A followed by rtt_apply_AT on
  * (y - d) rounded to FP32.  Asynchronous on `stream`.
  * Errors: RTT_EINVAL, RTT_ENOMEM, RTT_ECUDA.
  */
@@ -648,11 +643,10 @@ rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_d
  * paper has no counterpart: this is a property of the GPU implementation.
  * Candidates: the forward with staged per-ray histories (corner rows loaded
  * by threads or by TMA tensor copies) or with one hat per lane and warp
- * shuffles (the latter only when a frame step is 1/2, 1/4 or
- * 1/8 of a hat step), each with a few batch widths and frames per lane; the adjoint's
- * temporal phase (general, periodic-weight, or periodic-weight with frames
- * staged by TMA tensor copies) crossed with its spatial gather (scalar or
- * 16-byte).  Each candidate runs once untimed and three
+ * shuffles (the latter only when a frame step is 1/2, 1/4 or 1/8 of a hat
+ * step), each with a few batch widths and frames per lane; the adjoint's
+ * cell kernel with frames staged by per-lane copies, or by TMA tensor copies
+ * with 32-hat or 64-hat items.  Each candidate runs once untimed and three
  * times between CUDA events on `stream`, on zero-filled inputs of the arm's
  * shape (timing does not depend on values).  The fastest is recorded in the
  * operator for `batch` (up to 8 batch sizes per operator; later applies of
@@ -672,14 +666,11 @@ typedef struct {
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
     int32_t fwd_staging;  /* staged forward: x items in flight per lane */
-    int32_t time_kernel;  /* adjoint phase 1: 1 general, 2 periodic weights, 3 periodic + TMA,
-                             4 periodic + TMA, whole 64-hat items */
-    int32_t space_kernel; /* adjoint phase 2: 1 scalar, 2 16-byte loads, 3 same with 8 in flight */
+    int32_t adj_kernel;   /* adjoint: 1 per-lane staged copies, 2 TMA with 32-hat items,
+                             3 TMA with 64-hat items */
     float fwd_ms, adj_ms;           /* chosen variants, ms per apply */
     float fwd_ms_rule, adj_ms_rule; /* the untuned default rule, ms per apply */
     int32_t candidates;             /* configurations timed */
-    int32_t fused_step;  /* rtt_apply_A_AT uses the fused kernel (1) or the separate pair (0) */
-    float fused_ms;      /* the fused pair, ms per call (0 where it cannot run) */
 } rtt_tune_result;
 
 rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream, rtt_tune_result* out);
@@ -695,16 +686,13 @@ typedef struct {
                              else staged) */
     int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32 */
     int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
-    int32_t time_kernel;  /* 1 general, 2 periodic weights, 3 periodic + TMA, 4 periodic
-                             + TMA with whole 64-hat items and zero-filled frames
-                             outside the observation (batch 4, 8, 16 or 32 whose
-                             frames per 128-byte row divide the frames per hat);
-                             where the cadence or the buffers do not allow the
-                             choice, the next one down runs */
-    int32_t space_kernel; /* 1 scalar, 2 16-byte loads, 3 16-byte loads with eight
-                             incidences in flight (where the buffers allow) */
-    int32_t fused_step;   /* rtt_apply_A_AT: 1 = fused forward + temporal adjoint where the
-                             batch, cadence and buffers allow it, 0 = separate pair */
+    int32_t adj_kernel;   /* adjoint: 1 frames staged by per-lane copies (any batch,
+                             cadence and precision), 2 frames staged by TMA tensor copies
+                             with 32-hat items, 3 the same with 64-hat items (TMA: the
+                             whole batch of 4, 8 or 16 entries in one chunk, a frame
+                             step of 1/2, 1/4 or 1/8 hat step with whole frames per
+                             128-byte line; where the call does not allow the choice,
+                             the next one down runs) */
     int32_t fwd_staging;  /* staged forward: x items in flight per lane, 1, 2 or 3
                              (0 = 2; other values than 2 only at 4 or 8 entries) */
 } rtt_variant;

@@ -25,13 +25,6 @@ void set_error(const char* fmt, ...) {
     g_last_error = buf;
 }
 
-template <typename T>
-cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
-cudaError_t launch_forward_adjoint_fused(const rtt_op_s* op, const float* x, const float* d,
-                                         float* y, float* g, int B, const ArmSeg& seg,
-                                         float* zhat, cudaStream_t st);
-template <typename T>
-cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
 
 #define RTT_CUDA(call)                                                                  \
     do {                                                                                \
@@ -151,24 +144,6 @@ __global__ void prep_rays(const PrepArgs a) {
     a.thr_s[i] = a.thr[o];
 }
 
-__global__ void make_inc_keys(int64_t n, int n_phi, const int32_t* node00, const int32_t* node01,
-                              int32_t* key, int32_t* val, unsigned int* count) {
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 4 * n) return;
-    const int64_t e = t >> 2;
-    const int c = (int)(t & 3);
-    int node;
-    switch (c) {
-        case 0: node = node00[e]; break;
-        case 1: node = node00[e] + n_phi; break;
-        case 2: node = node01[e]; break;
-        default: node = node01[e] + n_phi; break;
-    }
-    key[t] = node;
-    val[t] = (int32_t)t;
-    atomicAdd(&count[node], 1u);
-}
-
 // Per direct row: sum_e w_e (FP64, sequential over the row's rays); squared.
 __global__ void row_weight_sq(int64_t n_rows, const int32_t* row_ptr, const double* w,
                               double* out) {
@@ -229,8 +204,9 @@ static void free_op(rtt_op_s* op) {
     if (!op) return;
     void* ps[] = {op->row_ptr, op->ray_row, op->node00, op->node01, op->W,     op->W64,
                   op->K0,      op->F0,      op->F64,    op->r,      op->delay, op->weight,
-                  op->thr,     op->node_ptr, op->inc,   op->row_order, op->zhat,
-                  op->node_order,
+                  op->thr,     op->row_order, op->c_row, op->c_col, op->c_K0, op->c_F0,
+                  op->c_W,     op->c_W64,   op->c_F64, op->seg_ray, op->seg_col, op->seg_ncol,
+                  op->seg_rec, op->gslot,   op->adj_ctr, op->cpart,
                   op->dev_status, op->rscratch, op->row_pixel, op->mix.grp_ptr,
                   op->mix.grp_rows, op->mix.row_grp, op->mix.inv32, op->mix.inv64,
                   op->mix.part, op->phi};
@@ -345,22 +321,6 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
     size_t tmp2 = 0;
     RTT_CUDA(cub::DeviceScan::InclusiveSum(nullptr, tmp2, flag, incl, E, st));
     tmp_bytes = tmp_bytes > tmp2 ? tmp_bytes : tmp2;
-    const int64_t S = op->n_nodes;
-    int32_t *ik_in, *ik_out, *iv_in;
-    unsigned int* ncount;
-    RTT_TRY(sc.get(&ik_in, 4 * E));
-    RTT_TRY(sc.get(&ik_out, 4 * E));
-    RTT_TRY(sc.get(&iv_in, 4 * E));
-    RTT_TRY(sc.get(&ncount, S + 1));
-    int end_bit = 1;
-    while ((1ll << end_bit) < S) ++end_bit;
-    size_t tmp3 = 0;
-    RTT_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tmp3, ik_in, ik_out, iv_in, iv_in, 4 * E, 0,
-                                             end_bit, st));
-    tmp_bytes = tmp_bytes > tmp3 ? tmp_bytes : tmp3;
-    size_t tmp4 = 0;
-    RTT_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp4, ncount, ncount, S + 1, st));
-    tmp_bytes = tmp_bytes > tmp4 ? tmp_bytes : tmp4;
     void* d_tmp;
     RTT_TRY(sc.get((unsigned char**)&d_tmp, tmp_bytes));
 
@@ -462,34 +422,10 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
     prep_rays<<<blocks(E), 256, 0, st>>>(pa);
     RTT_CUDA(cudaGetLastError());
 
-    // ---- transposed incidence CSR: stable sort of (node, ray*4+corner) ----
-    RTT_CUDA(cudaMemsetAsync(ncount, 0, (S + 1) * 4, st));
-    make_inc_keys<<<blocks(4 * E), 256, 0, st>>>(E, grid->n_phi, op->node00, op->node01, ik_in,
-                                                  iv_in, ncount);
-    RTT_CUDA(cudaGetLastError());
-    RTT_TRY(alloc(&op->inc, 4 * E));
-    RTT_TRY(alloc(&op->node_ptr, S + 1));
-    tb = tmp_bytes;
-    RTT_CUDA(cub::DeviceRadixSort::SortPairs(d_tmp, tb, ik_in, ik_out, iv_in, op->inc, 4 * E, 0,
-                                             end_bit, st));
-    tb = tmp_bytes;
-    RTT_CUDA(cub::DeviceScan::ExclusiveSum(d_tmp, tb, ncount, (unsigned int*)op->node_ptr, S + 1,
-                                           st));
-    RTT_CUDA(cudaStreamSynchronize(st));
-    // node order by descending incidence count (deterministic: ties by node index)
-    {
-        std::vector<int32_t> ptr(S + 1);
-        RTT_CUDA(cudaMemcpy(ptr.data(), op->node_ptr, (S + 1) * 4, cudaMemcpyDeviceToHost));
-        std::vector<int32_t> order(S);
-        for (int64_t i = 0; i < S; ++i) order[i] = (int32_t)i;
-        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-            return (ptr[a + 1] - ptr[a]) > (ptr[b + 1] - ptr[b]);
-        });
-        RTT_TRY(alloc(&op->node_order, S));
-        RTT_TRY(alloc(&op->dev_status, 1));
-        RTT_CUDA(cudaMemset(op->dev_status, 0, sizeof(int)));
-        RTT_CUDA(cudaMemcpy(op->node_order, order.data(), S * 4, cudaMemcpyHostToDevice));
-    }
+    RTT_TRY(alloc(&op->dev_status, 1));
+    RTT_CUDA(cudaMemsetAsync(op->dev_status, 0, sizeof(int), st));
+    // ---- the adjoint's cell structures (rays by source cell, strip segments) ----
+    RTT_TRY(build_cells(op, st));
     return RTT_OK;
 }
 
@@ -518,23 +454,6 @@ rtt_status make_seg(const rtt_op_s* op, int mask, ArmSeg* s) {
 // Grow-only adjoint scratch owned by the operator.  Growing frees the old
 // buffer after synchronising the device, so calls that need more scratch
 // than any earlier call are synchronous once.
-rtt_status ensure_zhat_bytes(rtt_op_s* op, size_t bytes) {
-    if (op->zhat_bytes >= bytes) return RTT_OK;
-    if (op->zhat) {
-        cudaDeviceSynchronize();
-        cudaFree(op->zhat);
-        op->zhat = nullptr;
-        op->zhat_bytes = 0;
-    }
-    cudaError_t e = cudaMalloc(&op->zhat, bytes);
-    if (e != cudaSuccess) {
-        op->zhat = nullptr;
-        set_error("adjoint scratch of %zu bytes: %s", bytes, cudaGetErrorString(e));
-        return RTT_ENOMEM;
-    }
-    op->zhat_bytes = bytes;
-    return RTT_OK;
-}
 
 // r = y - d, elementwise (FP32, one rounding)
 __global__ void residual_kernel(const float* __restrict__ y, const float* __restrict__ d,
@@ -564,9 +483,8 @@ static rtt_status apply_common(rtt_op op, const T* in, T* out, int batch, int ma
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e;
     if (adjoint) {
-        const int bc = batch < 32 ? batch : 32;
-        RTT_TRY(ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * bc * sizeof(T)));
-        e = launch_adjoint<T>(op, in, out, batch, seg, (T*)op->zhat, st);
+        RTT_TRY(ensure_adjoint_scratch(op, batch, (int)sizeof(T)));
+        e = launch_adjoint<T>(op, in, out, batch, seg, st);
     } else {
         e = launch_forward<T>(op, in, out, batch, seg, st);
     }
@@ -699,38 +617,32 @@ rtt_status rtt_apply_A_AT(rtt_op op, const float* x, const float* d, float* y, f
         return RTT_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    const int bc = batch < 32 ? batch : 32;
-    RTT_TRY(ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * bc * sizeof(float)));
-    cudaError_t e = cudaErrorNotSupported;
-    if (variant_for(op, batch).fused)
-        e = launch_forward_adjoint_fused(op, x, d, y, g, batch, seg, (float*)op->zhat, st);
-    if (e == cudaErrorNotSupported) {  // separate forward and adjoint
-        e = launch_forward<float>(op, x, y, batch, seg, st);
-        const float* r = y;
-        const int64_t n = (int64_t)seg.total * op->time.n_frames * batch;
-        if (e == cudaSuccess && d && n > 0) {
-            const size_t bytes = (size_t)n * sizeof(float);
-            if (bytes > op->rscratch_bytes) {
-                if (op->rscratch) {
-                    cudaStreamSynchronize(st);
-                    cudaFree(op->rscratch);
-                    op->rscratch = nullptr;
-                    op->rscratch_bytes = 0;
-                }
-                if (cudaMalloc(&op->rscratch, bytes) != cudaSuccess) {
-                    op->rscratch = nullptr;
-                    set_error("residual scratch of %zu bytes: allocation failed", bytes);
-                    return RTT_ENOMEM;
-                }
-                op->rscratch_bytes = bytes;
+    RTT_TRY(ensure_adjoint_scratch(op, batch, (int)sizeof(float)));
+    cudaError_t e = launch_forward<float>(op, x, y, batch, seg, st);
+    const float* r = y;
+    const int64_t n = (int64_t)seg.total * op->time.n_frames * batch;
+    if (e == cudaSuccess && d && n > 0) {
+        const size_t bytes = (size_t)n * sizeof(float);
+        if (bytes > op->rscratch_bytes) {
+            if (op->rscratch) {
+                cudaStreamSynchronize(st);
+                cudaFree(op->rscratch);
+                op->rscratch = nullptr;
+                op->rscratch_bytes = 0;
             }
-            residual_kernel<<<blocks(n < ((int64_t)1 << 24) ? n : ((int64_t)1 << 24)), 256, 0, st>>>(
-                y, d, (float*)op->rscratch, n);
-            e = cudaGetLastError();
-            r = (const float*)op->rscratch;
+            if (cudaMalloc(&op->rscratch, bytes) != cudaSuccess) {
+                op->rscratch = nullptr;
+                set_error("residual scratch of %zu bytes: allocation failed", bytes);
+                return RTT_ENOMEM;
+            }
+            op->rscratch_bytes = bytes;
         }
-        if (e == cudaSuccess) e = launch_adjoint<float>(op, r, g, batch, seg, (float*)op->zhat, st);
+        residual_kernel<<<blocks(n < ((int64_t)1 << 24) ? n : ((int64_t)1 << 24)), 256, 0, st>>>(
+            y, d, (float*)op->rscratch, n);
+        e = cudaGetLastError();
+        r = (const float*)op->rscratch;
     }
+    if (e == cudaSuccess) e = launch_adjoint<float>(op, r, g, batch, seg, st);
     if (e != cudaSuccess) {
         set_error("apply launch failed: %s", cudaGetErrorString(e));
         return RTT_ECUDA;

@@ -1,20 +1,17 @@
-// Forward operator A and its adjoint A^T (Sec. 3.1 Eq. 2-3, Eq. 16, Eq. 47).
+// Forward operator A (Sec. 3.1 Eq. 2-3, Eq. 16, Eq. 47); the adjoint is in
+// adjoint.cu.
 //
-// Forward (one warp per (row, frame chunk, batch chunk)):
-//   for each ray e of the row, the spatially interpolated history
-//   z_e[k][b] = sum_c W_{e,c} x[node_c][k][b] is staged in shared memory for
-//   the hats the frame chunk can touch, then every output sample adds
-//   (1 - fr) z_e[k0] + fr z_e[k0 + 1] with the exact integer hat index k0 and
-//   24-bit fraction fr of that (ray, frame).  y is written once, coalesced.
-// Adjoint (one warp per (node, hat chunk, batch chunk)): a deterministic
-//   gather over the node's incidence list (sorted by ray), summing for each
-//   owned (k, b) the frames whose hat pair contains k, with the same integer
-//   hat arithmetic as the forward, so the two are exact transposes.
+// One warp per (row, frame chunk, batch chunk): for each ray e of the row,
+// the spatially interpolated history z_e[k][b] = sum_c W_{e,c} x[node_c][k][b]
+// is staged in shared memory for the hats the frame chunk can touch, then
+// every output sample adds (1 - fr) z_e[k0] + fr z_e[k0 + 1] with the exact
+// integer hat index k0 and 24-bit fraction fr of that (ray, frame).  y is
+// written once, coalesced.
 #include <cuda.h>  // CUtensorMap and its enums (types only; no driver-library link)
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
 
-#include "rtt_internal.cuh"
+#include "kern_common.cuh"
 
 namespace rtt {
 
@@ -72,8 +69,6 @@ struct ApplyArgs {
     const int32_t* K0;
     const int32_t* F0;
     const double* F64;
-    const int32_t* node_ptr;
-    const int32_t* inc;
     const T* in;
     T* out;
     int B, K, Tn, n_phi, n_nodes;
@@ -84,11 +79,8 @@ struct ApplyArgs {
     int zwin;     // hats staged per chunk (forward)
     int KC;       // hats per chunk (adjoint)
     int vec4;     // batch stride and chunk allow 16-byte loads
-    T* zhat;      // adjoint scratch [E][K][Bc]
-    int Bc;       // batch entries held per ray in zhat
     int64_t n_rays_total;
     int seg_rows_all;  // total rows of the operator (all orders)
-    const int32_t* node_order;  // nodes by descending incidence count (load balance)
     int* status;                // device status word (bit 0: a bounded wait timed out)
     int hs32;                   // hat steps per 32 frames when a whole number, else 0
     int n_fchunk, n_bchunk, n_kchunk;
@@ -125,31 +117,6 @@ __device__ __forceinline__ HatCoef<double> load_hat<double>(const ApplyArgs<doub
     return h;
 }
 
-__device__ __forceinline__ int seg_in_row(const ArmSeg& s, int row_out) {
-    int r = row_out;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (i < s.n && r < s.len[i]) return s.begin[i] + r;
-        if (i < s.n) r -= s.len[i];
-    }
-    return -1;
-}
-
-// output row of an input row under the arm mask, -1 if not selected
-__device__ __forceinline__ int seg_out_row(const ArmSeg& s, int row_in) {
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        if (i < s.n && row_in >= s.begin[i] && row_in < s.begin[i] + s.len[i])
-            return s.out_off[i] + (row_in - s.begin[i]);
-    }
-    return -1;
-}
-
-// Fixed-order arithmetic shared by every kernel variant, so that the variant
-// (chosen from the batch size and alignment) never changes an output bit:
-// fmac(a, b, c) = a b + c with one rounding.
-__device__ __forceinline__ float fmac(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fmac(double a, double b, double c) { return __fma_rn(a, b, c); }
 // spatial interpolation w0 v0 + w1 v1 + w2 v2 + w3 v3
 template <typename T>
 __device__ __forceinline__ T interp4(T w0, T v0, T w1, T v1, T w2, T v2, T w3, T v3) {
@@ -161,43 +128,7 @@ __device__ __forceinline__ T hat2(T acc, T g, T z0, T fr, T z1) {
     return fmac(fr, z1, fmac(g, z0, acc));
 }
 
-// a v + (c0, c1, c2, c3) per component with packed FP32 pairs (the fused
-// multiply-add of fmac on each component, two per instruction)
-__device__ __forceinline__ void fmac2x2(float a, const float4& v, float& c0, float& c1, float& c2,
-                                        float& c3) {
-    const float2 a2 = make_float2(a, a);
-    const float2 lo = __ffma2_rn(a2, make_float2(v.x, v.y), make_float2(c0, c1));
-    const float2 hi = __ffma2_rn(a2, make_float2(v.z, v.w), make_float2(c2, c3));
-    c0 = lo.x;
-    c1 = lo.y;
-    c2 = hi.x;
-    c3 = hi.y;
-}
-
 constexpr int kWarpsPerBlock = 8;
-
-// Programmatic dependent launch: a kernel launched with programmatic stream
-// serialisation may be scheduled while the previous kernel in its stream is
-// still finishing; it waits here, before touching any global memory, until
-// that kernel has completed and its writes are visible.  Without the launch
-// attribute the wait returns at once.
-__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-
-template <typename... KArgs, typename... Args>
-static cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
-                                    cudaStream_t st, Args... args) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kernel, args...);
-}
 
 // Grid-stride walk over (output row, frame chunk, batch chunk) tasks, batch
 // chunk fastest (task = (row nf + f) nb + b).  The first task and the stride
@@ -228,84 +159,6 @@ struct TaskWalk {
         r += dr + c;
     }
 };
-
-constexpr int kAdjOutPerLane = 8;
-
-__device__ __forceinline__ int64_t floor_div(int64_t a, int64_t d) {
-    return a >= 0 ? a / d : -((-a + d - 1) / d);
-}
-
-// Phase 1 of the adjoint: temporal contraction per ray,
-//   zhat_e[k][b] = sum_f h_{e,f,k} y[row_e][f][b0 + b],
-// one warp per (ray, hat chunk, batch chunk).  The frames feeding hat k are
-// the contiguous range where the exact hat index is k or k - 1, found by
-// integer division on the 24-bit fixed-point hat coordinate.
-template <typename T, int BC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-adj_time_kernel(const ApplyArgs<T> a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
-        const int bchunk = (int)(task % a.n_bchunk);
-        const int64_t t2 = task / a.n_bchunk;
-        const int kchunk = (int)(t2 % a.n_kchunk);
-        const int e = (int)(t2 / a.n_kchunk);
-        const int row_out = seg_out_row(a.seg, a.ray_row[e]);
-        if (row_out < 0) {
-            // rays outside the arm contribute nothing: their zhat rows are zero
-            const int k_begin = kchunk * a.KC;
-            for (int o = lane; o < a.KC * a.Bc; o += 32) {
-                const int kk = o / a.Bc, bb = o - kk * a.Bc;
-                if (k_begin + kk < a.K) a.zhat[((int64_t)e * a.K + k_begin + kk) * a.Bc + bb] = T(0);
-            }
-            continue;
-        }
-        const HatCoef<T> hc = load_hat(a, e);
-        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
-        const T* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
-        const int b0 = bchunk * BC;
-        const int k_begin = kchunk * a.KC;
-#pragma unroll
-        for (int j = 0; j < kAdjOutPerLane; ++j) {
-            const int o = lane + 32 * j;
-            const int kk = o / BC, bb = o - kk * BC;
-            const int k = k_begin + kk;
-            const int b = b0 + bb;
-            if (kk >= a.KC || k >= a.K || bb >= a.Bc) continue;
-            T s = T(0);
-            if constexpr (sizeof(T) == 4) {
-                // frames with (k-1) 2^24 <= U(f) < (k+1) 2^24, U(f) = U0 - f D:
-                // start from a float estimate and test each frame exactly
-                const int64_t hi_excl = (int64_t)(k + 1) * kFracOne;
-                const int64_t lo_incl = (int64_t)(k - 1) * kFracOne;
-                const float est = (float)(U0 - hi_excl) * (1.0f / (float)a.D);
-                int f = (int)fminf(fmaxf(floorf(est) - 1.0f, 0.0f), (float)a.Tn);
-                int64_t U = U0 - (int64_t)f * a.D;
-                while (f < a.Tn && U >= hi_excl) { ++f; U -= a.D; }
-                for (; f < a.Tn && U >= lo_incl; ++f, U -= a.D) {
-                    const int k0 = (int)(U >> kFracBits);
-                    const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
-                    const float hw = (k0 == k) ? 1.0f - fr : fr;
-                    s = fmac(hw, yrow[(int64_t)f * a.B + b], s);
-                }
-            } else {
-                int64_t flo = floor_div(U0 - (int64_t)(k + 1) * kFracOne, a.D) + 1;
-                int64_t fhi = floor_div(U0 - (int64_t)(k - 1) * kFracOne, a.D);
-                if (flo < 0) flo = 0;
-                if (fhi > a.Tn - 1) fhi = a.Tn - 1;
-                for (int f = (int)flo; f <= (int)fhi; ++f) {
-                    int k0;
-                    T fr;
-                    hc.at(f, k0, fr);
-                    const T hw = (k0 == k) ? T(1) - fr : ((k0 + 1 == k) ? fr : T(0));
-                    s = fmac(hw, yrow[(int64_t)f * a.B + b], s);
-                }
-            }
-            a.zhat[((int64_t)e * a.K + k) * a.Bc + bb] = s;
-        }
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Fast paths (FP32 and FP64 storage).  Forward: lane per frame, each lane
@@ -681,657 +534,6 @@ fwd4_kernel(const ApplyArgs<float> a) {
                     if (b < nb) yo[b] = acc[j][b];
             }
         }
-    }
-}
-
-// Adjoint phase 1, fast path: lane per hat within a group of 32 hats; the
-// frames feeding the group are staged once in shared memory and each lane
-// accumulates all BC batch entries of its hat.
-constexpr int kAdj3Warps = 4;
-
-// Swizzled staging layout: the 16-byte chunk index of (frame f, chunk q) has
-// its low three bits XORed with (f / P) mod 8, P = frames per hat step, so
-// the lanes of a warp (one hat each, hats P frames apart) read eight distinct
-// bank groups.
-__device__ __forceinline__ int swz(int f, int q, int Q, int pshift) {
-    const int idx = f * Q + q;
-    return idx ^ ((f >> pshift) & 7);
-}
-
-template <typename T, int BC>
-__global__ void __launch_bounds__(kAdj3Warps * 32)
-adj_time3_kernel(const ApplyArgs<T> a) {
-    using V = typename Vec16<T>::type;
-    constexpr int VW = Vec16<T>::W;
-    extern __shared__ __align__(16) unsigned char smem_a3_raw[];
-    T* ys = reinterpret_cast<T*>(smem_a3_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_global = (int64_t)blockIdx.x * kAdj3Warps + (threadIdx.x >> 5);
-    const int64_t n_warps = (int64_t)gridDim.x * kAdj3Warps;
-    const bool vec = (BC >= VW) && a.vec4 && (a.Bc == BC);
-    constexpr int Q = BC / VW > 0 ? BC / VW : 1;
-    const int P = a.FC;  // log2 of frames per hat step, used only for the swizzle
-    const float invD = 1.0f / (float)a.D;
-    const int32_t D32 = (int32_t)a.D;  // D <= 2^24
-    for (int64_t e = warp_global; e < a.n_tasks; e += n_warps) {
-        const int row_out = seg_out_row(a.seg, a.ray_row[e]);
-        if (row_out < 0) {
-            // rays outside the arm contribute nothing: their zhat rows are zero
-            T* zo = a.zhat + (int64_t)e * a.K * a.Bc;
-            for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = T(0);
-            continue;
-        }
-        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
-        const double F64 = exact_frac(a, (int)e);
-        const T* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
-        for (int kg0 = 0; kg0 < a.K; kg0 += 32) {
-            const int kg1 = min(kg0 + 31, a.K - 1);
-            // frames with (kg0 - 1) 2^24 <= U(f) < (kg1 + 1) 2^24, found from a float
-            // estimate corrected by exact integer tests
-            const int64_t hiX = (int64_t)(kg1 + 1) * kFracOne;
-            const int64_t loX = (int64_t)(kg0 - 1) * kFracOne;
-            int fA = (int)fminf(fmaxf(floorf((float)(U0 - hiX) * invD) - 1.0f, 0.0f), (float)a.Tn);
-            while (fA < a.Tn && U0 - (int64_t)fA * a.D >= hiX) ++fA;
-            int fB = (int)fminf(fmaxf(floorf((float)(U0 - loX) * invD) + 1.0f, -1.0f),
-                                (float)(a.Tn - 1));
-            while (fB >= 0 && U0 - (int64_t)fB * a.D < loX) --fB;
-            const int nfr = fB >= fA ? fB - fA + 1 : 0;
-            if (vec) {
-                V* ysv = reinterpret_cast<V*>(ys);
-                for (int o = lane; o < nfr * Q; o += 32) {
-                    const int fl = o / Q, q = o - fl * Q;
-                    ysv[swz(fl, q, Q, P)] =
-                        __ldg(reinterpret_cast<const V*>(yrow + (int64_t)(fA + fl) * a.B) + q);
-                }
-            } else {
-                for (int o = lane; o < nfr * BC; o += 32) {
-                    const int fl = o / BC, bb = o - fl * BC;
-                    ys[o] = bb < a.Bc ? yrow[(int64_t)(fA + fl) * a.B + bb] : T(0);
-                }
-            }
-            __syncwarp();
-            const int k = kg0 + lane;
-            if (k <= kg1) {
-                T acc[BC];
-#pragma unroll
-                for (int b = 0; b < BC; ++b) acc[b] = T(0);
-                // frames with |U(f) - k 2^24| < 2^24 (hat k's support); in that
-                // window Ur = U(f) - k 2^24 fits 32 bits and the hat weight is
-                // 1 - |Ur| 2^-24 exactly (FP32); FP64 uses the exact fraction
-                const int64_t hi_excl = (int64_t)(k + 1) * kFracOne;
-                const float est = (float)(U0 - hi_excl) * invD;
-                int f = (int)fminf(fmaxf(floorf(est) - 1.0f, (float)fA), (float)(fB + 1));
-                int64_t U = U0 - (int64_t)f * a.D;
-                while (f <= fB && U >= hi_excl) { ++f; U -= a.D; }
-                int32_t Ur = (int32_t)(U - (int64_t)k * kFracOne);  // in [-2^24, 2^24) once f <= fB
-                // FP64 also visits Ur = -2^24: the 24-bit coordinate puts hat k
-                // exactly on its support edge there, but the exact fraction lies
-                // in [0, 2^-24) and gives hat k that (possibly nonzero) weight,
-                // as the FP64 forward does
-                const int32_t lo_excl = sizeof(T) == 8 ? -kFracOne - 1 : -kFracOne;
-                for (; f <= fB && Ur > lo_excl; ++f, Ur -= D32) {
-                    T hw;
-                    if constexpr (sizeof(T) == 4) {
-                        hw = 1.0f - (float)abs(Ur) * (1.0f / (float)kFracOne);
-                    } else {
-                        const int64_t Uf = (int64_t)k * kFracOne + Ur;
-                        const int k0 = (int)(Uf >> kFracBits);
-                        const T fr = frac_of<T>(Uf, f, a.D, F64);
-                        hw = (k0 == k) ? T(1) - fr : fr;
-                    }
-                    if (vec) {
-                        const V* ysv = reinterpret_cast<const V*>(ys);
-#pragma unroll
-                        for (int q = 0; q < Q; ++q) {
-                            const V t = ysv[swz(f - fA, q, Q, P)];
-#pragma unroll
-                            for (int c = 0; c < VW; ++c)
-                                acc[VW * q + c] = fmac(hw, comps<T>(t)[c], acc[VW * q + c]);
-                        }
-                    } else {
-                        const T* yv = ys + (f - fA) * BC;
-#pragma unroll
-                        for (int b = 0; b < BC; ++b) acc[b] = fmac(hw, yv[b], acc[b]);
-                    }
-                }
-                T* zo = a.zhat + ((int64_t)e * a.K + k) * a.Bc;
-                if (vec) {
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        V o;
-#pragma unroll
-                        for (int c = 0; c < VW; ++c) comps<T>(o)[c] = acc[VW * q + c];
-                        reinterpret_cast<V*>(zo)[q] = o;
-                    }
-                } else {
-#pragma unroll
-                    for (int b = 0; b < BC; ++b)
-                        if (b < a.Bc) zo[b] = acc[b];
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
-// Adjoint phase 1 when a frame step is exactly 1/P of a hat step (P an
-// integer, FP32).  With c0 = floor(U0 / D), hat k is nonzero only on the 2P
-// frames f = c0 + 1 - P (k + 1) + j, j = 0..2P-1, with weight
-// 1 - |r0 - j D| 2^-24, r0 = U0 - (c0 + 1) D + 2^24 in [2^24 - D, 2^24): the
-// same 2P weights for every hat.  The frames of a 32-hat group are staged in
-// shared memory with coalesced 16-byte loads (swizzled layout of
-// adj_time3_kernel); each lane (one hat) then runs a fixed 2P-tap loop with
-// the ray's weights, frames ascending as in the general kernel.
-template <int BC, int P>
-__global__ void __launch_bounds__(kAdj3Warps * 32)
-adj_time4_kernel(const ApplyArgs<float> a) {
-    constexpr int Q = BC >= 4 ? BC / 4 : 1;
-    extern __shared__ __align__(16) unsigned char smem_a4_raw[];
-    float* ys = reinterpret_cast<float*>(smem_a4_raw) + (threadIdx.x >> 5) * (a.zwin * BC);
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_global = (int64_t)blockIdx.x * kAdj3Warps + (threadIdx.x >> 5);
-    const int64_t n_warps = (int64_t)gridDim.x * kAdj3Warps;
-    const bool vec = (BC >= 4) && a.vec4 && (a.Bc == BC);
-    const int pshift = a.FC;  // swizzle key shift
-    const int32_t D32 = (int32_t)a.D;  // 2^24 / P
-    for (int64_t e = warp_global; e < a.n_tasks; e += n_warps) {
-        const int row_out = seg_out_row(a.seg, a.ray_row[e]);
-        if (row_out < 0) {
-            float* zo = a.zhat + (int64_t)e * a.K * a.Bc;
-            for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = 0.0f;
-            continue;
-        }
-        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
-        const int64_t c0 = (U0 * P) >> kFracBits;  // floor(U0 / D), exact
-        const int32_t r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
-        float wt[2 * P];
-#pragma unroll
-        for (int j = 0; j < 2 * P; ++j)
-            wt[j] = 1.0f - (float)abs(r0 - j * D32) * (1.0f / (float)kFracOne);
-        const int fbase = (int)(c0 + 1 - P);  // first frame of hat 0
-        const float* yrow = a.in + (int64_t)row_out * a.Tn * a.B;
-        for (int kg0 = 0; kg0 < a.K; kg0 += 32) {
-            const int kg1 = min(kg0 + 31, a.K - 1);
-            // frames of hats kg1 .. kg0, clipped to the observation
-            const int fA = max(fbase - P * kg1, 0);
-            const int fB = min(fbase - P * kg0 + 2 * P - 1, a.Tn - 1);
-            const int nfr = fB >= fA ? fB - fA + 1 : 0;
-            if (vec) {
-                float4* ysv = reinterpret_cast<float4*>(ys);
-                for (int o = lane; o < nfr * Q; o += 32) {
-                    const int fl = o / Q, q = o - fl * Q;
-                    ysv[swz(fl, q, Q, pshift)] =
-                        __ldg(reinterpret_cast<const float4*>(yrow + (int64_t)(fA + fl) * a.B) + q);
-                }
-            } else {
-                for (int o = lane; o < nfr * BC; o += 32) {
-                    const int fl = o / BC, bb = o - fl * BC;
-                    ys[o] = bb < a.Bc ? yrow[(int64_t)(fA + fl) * a.B + bb] : 0.0f;
-                }
-            }
-            __syncwarp();
-            const int k = kg0 + lane;
-            if (k <= kg1) {
-                float acc[BC];
-#pragma unroll
-                for (int b = 0; b < BC; ++b) acc[b] = 0.0f;
-                const int f0 = fbase - P * k;
-#pragma unroll
-                for (int j = 0; j < 2 * P; ++j) {
-                    const int f = f0 + j;
-                    if (f < fA || f > fB) continue;  // outside the observation
-                    if (vec) {
-                        const float4* ysv = reinterpret_cast<const float4*>(ys);
-#pragma unroll
-                        for (int q = 0; q < Q; ++q) {
-                            const float4 t = ysv[swz(f - fA, q, Q, pshift)];
-                            fmac2x2(wt[j], t, acc[4 * q + 0], acc[4 * q + 1], acc[4 * q + 2],
-                                    acc[4 * q + 3]);
-                        }
-                    } else {
-                        const float* yv = ys + (f - fA) * BC;
-#pragma unroll
-                        for (int b = 0; b < BC; ++b) acc[b] = fmac(wt[j], yv[b], acc[b]);
-                    }
-                }
-                float* zo = a.zhat + ((int64_t)e * a.K + k) * a.Bc;
-                if (vec) {
-#pragma unroll
-                    for (int q = 0; q < Q; ++q)
-                        reinterpret_cast<float4*>(zo)[q] =
-                            make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-                } else {
-#pragma unroll
-                    for (int b = 0; b < BC; ++b)
-                        if (b < a.Bc) zo[b] = acc[b];
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
-// Adjoint phase 1, periodic weights, with the frames of each (ray, 32-hat
-// group) brought into shared memory by the tensor memory accelerator.  y of
-// a single batch chunk (B = BC entries per frame, frames contiguous) is
-// viewed as a 2D tensor of 128-byte rows, each holding FPR = 32 / BC
-// consecutive frames; one tiled copy per group moves the rows covering the
-// group's frames (start rounded down to a row), issued by lane 0 and tracked
-// by an mbarrier, double-buffered so the copy for the next group (of this ray
-// or the next) runs while the current one is contracted.  With the 128-byte
-// swizzle, the 16-byte chunk j of box row r lands at chunk j ^ (r mod 8) of
-// that row (buffers 1024-byte aligned), so lanes that read frames P apart
-// hit distinct banks.  Arithmetic and order are those of adj_time4_kernel.
-// Every mbarrier wait is bounded: on timeout the warp sets bit 0 of
-// *status, waits (bounded) for its other copy in flight and returns.
-constexpr int kAdj5Warps = 4;
-constexpr int kSpinLimit = 1 << 22;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (int it = 0; it < kSpinLimit; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}\n"
-            : "=r"(ok)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
-template <int BC, int P>
-struct T5Box {
-    static constexpr int kFPR = 32 / BC;  // frames per 128-byte row
-    // rows covering up to 33 P frames that start anywhere inside a row
-    static constexpr int kRows = (33 * P + 2 * (kFPR - 1)) / kFPR;
-    static constexpr uint32_t kBytes = (uint32_t)kRows * 128;
-    static constexpr uint32_t kStride = (kBytes + 1023) & ~1023u;
-};
-
-template <int BC, int P>
-__global__ void __launch_bounds__(kAdj5Warps * 32)
-adj_time5_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float> a,
-                 int* status) {
-    static_assert(BC == 4 || BC == 8 || BC == 16 || BC == 32, "128-byte rows of whole frames");
-    constexpr int Q = BC / 4;  // 16-byte chunks per frame
-    constexpr int FPR = T5Box<BC, P>::kFPR;
-    constexpr uint32_t BOX_BYTES = T5Box<BC, P>::kBytes;
-    constexpr uint32_t BUF_STRIDE = T5Box<BC, P>::kStride;
-    extern __shared__ unsigned char smem5_raw[];
-    const uint32_t raw_u32 = smem_u32(smem5_raw);
-    const uint32_t base_u32 = (raw_u32 + 1023) & ~1023u;  // 128-byte swizzle atom alignment
-    unsigned char* base = smem5_raw + (base_u32 - raw_u32);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // buffer b of this warp: shared address buf0 + b * BUF_STRIDE, mbarrier bar0 + 8 b
-    const unsigned char* bufp0 = base + (size_t)(2 * warp) * BUF_STRIDE;
-    const uint32_t buf0 = base_u32 + (2 * warp) * BUF_STRIDE;
-    const uint32_t bar0 = base_u32 + kAdj5Warps * 2 * BUF_STRIDE + 16 * warp;
-    if (lane == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    const int64_t warp_global = (int64_t)blockIdx.x * kAdj5Warps + warp;
-    const int64_t n_warps = (int64_t)gridDim.x * kAdj5Warps;
-    const int n_groups = (a.K + 31) / 32;
-    const int32_t D32 = (int32_t)a.D;
-    // rays outside the arm: zero rows (no copies)
-    if (a.seg.total < a.seg_rows_all) {
-        for (int64_t e = warp_global; e < a.n_tasks; e += n_warps)
-            if (seg_out_row(a.seg, a.ray_row[e]) < 0) {
-                float* zo = a.zhat + e * a.K * a.Bc;
-                for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = 0.0f;
-            }
-    }
-    // work items (ray, group) of this warp, rays in the arm only
-    struct Item {
-        int64_t e;
-        int g, row_out, fbase, fA, fB, f4;  // f4: first frame of the first copied row
-        int32_t r0;                          // weight phase of the ray (see above)
-    };
-    auto fill = [&](int64_t e, int g, Item& it) {
-        it.e = e;
-        it.g = g;
-        it.row_out = seg_out_row(a.seg, a.ray_row[e]);
-        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
-        const int64_t c0 = (U0 * P) >> kFracBits;
-        it.fbase = (int)(c0 + 1 - P);
-        it.r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
-        const int kg0 = 32 * g, kg1 = min(kg0 + 31, a.K - 1);
-        it.fA = max(it.fbase - P * kg1, 0);
-        it.fB = min(it.fbase - P * kg0 + 2 * P - 1, a.Tn - 1);
-        it.f4 = min(it.fA, a.Tn - 1) & ~(FPR - 1);
-    };
-    // next item after (e, g): next group, else the next ray in the arm
-    auto next = [&](int64_t e, int g, Item& it) -> bool {
-        if (g + 1 < n_groups) {
-            fill(e, g + 1, it);
-            return true;
-        }
-        for (e += n_warps; e < a.n_tasks; e += n_warps)
-            if (seg_out_row(a.seg, a.ray_row[e]) >= 0) {
-                fill(e, 0, it);
-                return true;
-            }
-        return false;
-    };
-    const uint64_t tmap = reinterpret_cast<uint64_t>(&ymap);
-    auto issue = [&](const Item& it, int b) {
-        if (lane != 0) return;
-        // tensor row of (row_out, f4); frames per row divide the frame count
-        const int ycoord = (int)(((int64_t)it.row_out * a.Tn + it.f4) / FPR);
-        const uint32_t bar = bar0 + 8u * b, dst = buf0 + (uint32_t)b * BUF_STRIDE;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"(BOX_BYTES)
-                     : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-            "l"(tmap), "r"(0), "r"(ycoord), "r"(bar)
-            : "memory");
-    };
-    Item cur;
-    bool have = false;
-    for (int64_t e = warp_global; e < a.n_tasks && !have; e += n_warps)
-        if (seg_out_row(a.seg, a.ray_row[e]) >= 0) {
-            fill(e, 0, cur);
-            have = true;
-        }
-    if (!have) return;
-    issue(cur, 0);
-    // item t + 1's metadata is read one iteration ahead of its copy, so the
-    // copy is issued without waiting on global loads
-    Item nxt;
-    bool have_nxt = next(cur.e, cur.g, nxt);
-    for (uint32_t t = 0; have; ++t) {
-        if (have_nxt) issue(nxt, (t + 1) & 1);
-        Item nn;
-        const bool have_nn = have_nxt && next(nxt.e, nxt.g, nn);
-        if (!mbar_wait(bar0 + 8u * (t & 1), (t >> 1) & 1)) {
-            if (lane == 0) atomicOr(status, 1);
-            if (have_nxt) mbar_wait(bar0 + 8u * ((t + 1) & 1), ((t + 1) >> 1) & 1);
-            return;
-        }
-        // contraction of group cur.g of ray cur.e from buffer t & 1
-        const int32_t r0 = cur.r0;
-        float wt[2 * P];
-#pragma unroll
-        for (int j = 0; j < 2 * P; ++j)
-            wt[j] = 1.0f - (float)abs(r0 - j * D32) * (1.0f / (float)kFracOne);
-        const int k = 32 * cur.g + lane;
-        if (k < a.K) {
-            float acc[BC];
-#pragma unroll
-            for (int b = 0; b < BC; ++b) acc[b] = 0.0f;
-            const int f0 = cur.fbase - P * k;
-            const float4* bv = reinterpret_cast<const float4*>(bufp0 + (t & 1) * BUF_STRIDE);
-#pragma unroll
-            for (int j = 0; j < 2 * P; ++j) {
-                const int f = f0 + j;
-                if (f < cur.fA || f > cur.fB) continue;  // outside the observation
-                const int fl = f - cur.f4;                // < kRows * FPR
-                const int r = fl / FPR;
-                const int cb = (fl - r * FPR) * Q;
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const float4 v = bv[8 * r + ((cb + q) ^ (r & 7))];
-                    fmac2x2(wt[j], v, acc[4 * q + 0], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-                }
-            }
-            float4* zo = reinterpret_cast<float4*>(a.zhat + (cur.e * a.K + k) * BC);
-#pragma unroll
-            for (int q = 0; q < Q; ++q)
-                zo[q] = make_float4(acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-        }
-        __syncwarp();  // buffer t & 1 is free for the copy issued at step t + 1
-        cur = nxt;
-        have = have_nxt;
-        nxt = nn;
-        have_nxt = have_nn;
-    }
-}
-
-// Adjoint phase 1 with whole 64-hat items: the arithmetic and order of
-// adj_time4_kernel (hence the same bits), with less work per output.
-//  * An item is (ray, group of 32 HG hats); lane l owns hats kg0 + l + 32 h.
-//    At K <= 32 HG a ray is one item: one copy, one set of 2P tap weights.
-//  * y is seen through a 3D tensor map (128-byte row, row of the frame axis,
-//    data row), so frames before 0 or after the last one arrive as zeros from
-//    the copy's out-of-bounds fill: a zero frame adds w * 0 = +0 to a sum that
-//    is never -0, leaving it unchanged, so no tap needs a bounds test.
-//  * Frames per 128-byte row F = 32 / BC divides P, so a lane's first frame
-//    fbase - P k - f4 has the same residue M mod F on every lane and hat; a
-//    switch on M makes each tap's row step and 16-byte chunk compile-time
-//    constants, and a tap's swizzled address is one OR of per-row terms.
-// Double-buffered copies per warp with item metadata one item ahead, bounded
-// mbarrier waits as in adj_time5_kernel.
-constexpr int kAdj6Warps = 4;
-
-template <int BC, int P, int HG>
-struct T6Box {
-    static constexpr int kF = 32 / BC;  // frames per 128-byte row
-    static_assert(P % kF == 0, "a row holds a whole number of frames that divides P");
-    // rows covering (32 HG + 1) P frames that start anywhere inside a row
-    static constexpr int kRows = ((32 * HG + 1) * P + 2 * (kF - 1)) / kF;
-    static constexpr uint32_t kBytes = (uint32_t)kRows * 128;
-    static constexpr uint32_t kStride = (kBytes + 1023) & ~1023u;
-};
-
-// taps of HG hats of one lane for residue M: rows rs + dj of the buffer
-template <int BC, int P, int HG, int M>
-__device__ __forceinline__ void adj6_contract(const unsigned char* buf, int rs0, const float (&wt)[2 * P],
-                                              float (&acc)[HG][BC]) {
-    constexpr int Q = BC / 4;
-    constexpr int F = 32 / BC;
-    constexpr int ND = (M + 2 * P - 1) / F + 1;  // rows one hat's taps touch
-#pragma unroll
-    for (int h = 0; h < HG; ++h) {
-        const int rs = rs0 - h * (32 * P / F);
-        uint32_t A[ND], X[ND];
-#pragma unroll
-        for (int d = 0; d < ND; ++d) {
-            A[d] = (uint32_t)(rs + d) * 128u;
-            X[d] = (uint32_t)((rs + d) & 7) << 4;
-        }
-#pragma unroll
-        for (int b = 0; b < BC; ++b) acc[h][b] = 0.0f;
-#pragma unroll
-        for (int j = 0; j < 2 * P; ++j) {
-            const int dj = (M + j) / F, cj = (M + j) % F;
-#pragma unroll
-            for (int q = 0; q < Q; ++q) {
-                const uint32_t off = A[dj] | ((uint32_t)(16 * (cj * Q + q)) ^ X[dj]);
-                const float4 v = *reinterpret_cast<const float4*>(buf + off);
-                fmac2x2(wt[j], v, acc[h][4 * q + 0], acc[h][4 * q + 1], acc[h][4 * q + 2],
-                        acc[h][4 * q + 3]);
-            }
-        }
-    }
-}
-
-template <int BC, int P, int HG>
-__global__ void __launch_bounds__(kAdj6Warps * 32)
-adj_time6_kernel(const __grid_constant__ CUtensorMap ymap, const ApplyArgs<float> a, int* status) {
-    static_assert(BC == 4 || BC == 8 || BC == 16 || BC == 32, "128-byte rows of whole frames");
-    wait_prior_grid();
-    constexpr int F = T6Box<BC, P, HG>::kF;
-    constexpr int LGF = F == 1 ? 0 : (F == 2 ? 1 : (F == 4 ? 2 : 3));
-    constexpr uint32_t BOX_BYTES = T6Box<BC, P, HG>::kBytes;
-    constexpr uint32_t BUF_STRIDE = T6Box<BC, P, HG>::kStride;
-    constexpr int HATS = 32 * HG;  // hats per item
-    extern __shared__ unsigned char smem6t_raw[];
-    const uint32_t raw_u32 = smem_u32(smem6t_raw);
-    const uint32_t base_u32 = (raw_u32 + 1023) & ~1023u;  // 128-byte swizzle atom alignment
-    unsigned char* base = smem6t_raw + (base_u32 - raw_u32);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const unsigned char* bufp0 = base + (size_t)(2 * warp) * BUF_STRIDE;
-    const uint32_t buf0 = base_u32 + (2 * warp) * BUF_STRIDE;
-    const uint32_t bar0 = base_u32 + kAdj6Warps * 2 * BUF_STRIDE + 16 * warp;
-    if (lane == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncwarp();
-    const int64_t warp_global = (int64_t)blockIdx.x * kAdj6Warps + warp;
-    const int64_t n_warps = (int64_t)gridDim.x * kAdj6Warps;
-    const int n_groups = (a.K + HATS - 1) / HATS;
-    const int32_t D32 = (int32_t)a.D;
-    // rays outside the arm: zero rows (no copies)
-    if (a.seg.total < a.seg_rows_all) {
-        for (int64_t e = warp_global; e < a.n_tasks; e += n_warps)
-            if (seg_out_row(a.seg, a.ray_row[e]) < 0) {
-                float* zo = a.zhat + e * a.K * a.Bc;
-                for (int o = lane; o < a.K * a.Bc; o += 32) zo[o] = 0.0f;
-            }
-    }
-    // an item's raw table fields are loaded one item before the item is
-    // issued and its copy coordinates derived only then, so the loads'
-    // latency passes under the previous item's contraction
-    struct Raw {
-        int64_t e;
-        int g, ray_row, K0, F0;
-    };
-    struct Item {
-        int64_t e;
-        int g, row_out, R4, sbase;  // R4: first copied row; sbase: item frame offset in it
-        int32_t r0;                 // weight phase of the ray
-    };
-    const bool all_rows = a.seg.total == a.seg_rows_all;
-    auto load = [&](int64_t e, int g, Raw& r) {
-        r.e = e;
-        r.g = g;
-        r.ray_row = a.ray_row[e];
-        r.K0 = a.K0[e];
-        r.F0 = a.F0[e];
-    };
-    // the item after (e, g): next group, else the next ray in the arm
-    auto next = [&](int64_t e, int g, const Raw& prev, Raw& r) -> bool {
-        if (g + 1 < n_groups) {
-            r = prev;
-            r.g = g + 1;
-            return true;
-        }
-        for (e += n_warps; e < a.n_tasks; e += n_warps)
-            if (all_rows || seg_out_row(a.seg, a.ray_row[e]) >= 0) {
-                load(e, 0, r);
-                return true;
-            }
-        return false;
-    };
-    auto derive = [&](const Raw& r, Item& it) {
-        it.e = r.e;
-        it.g = r.g;
-        it.row_out = seg_out_row(a.seg, r.ray_row);
-        const int64_t U0 = (int64_t)r.K0 * kFracOne + (int64_t)r.F0;
-        const int64_t c0 = (U0 * P) >> kFracBits;
-        const int fbase = (int)(c0 + 1 - P);
-        it.r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
-        const int kg0 = HATS * r.g;
-        const int f_lo = fbase - P * (kg0 + HATS - 1);  // first frame of the item's last hat
-        it.R4 = f_lo >> LGF;                             // floor division (f_lo may be < 0)
-        it.sbase = fbase - P * kg0 - it.R4 * F;          // >= 0
-    };
-    const uint64_t tmap = reinterpret_cast<uint64_t>(&ymap);
-    auto issue = [&](const Item& it, int b) {
-        if (lane != 0) return;
-        const uint32_t bar = bar0 + 8u * b, dst = buf0 + (uint32_t)b * BUF_STRIDE;
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                     "r"(BOX_BYTES)
-                     : "memory");
-        // x = 0 (whole 128-byte rows); rows before 0 or past the frames are zero-filled
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-            "l"(tmap), "r"(0), "r"(it.R4), "r"(it.row_out), "r"(bar)
-            : "memory");
-    };
-    Raw rcur;
-    bool have = false;
-    for (int64_t e = warp_global; e < a.n_tasks && !have; e += n_warps)
-        if (all_rows || seg_out_row(a.seg, a.ray_row[e]) >= 0) {
-            load(e, 0, rcur);
-            have = true;
-        }
-    if (!have) return;
-    Item cur;
-    derive(rcur, cur);
-    issue(cur, 0);
-    Raw rnxt;
-    bool have_nxt = next(rcur.e, rcur.g, rcur, rnxt);
-    for (uint32_t t = 0; have; ++t) {
-        Item nxt;
-        if (have_nxt) {
-            derive(rnxt, nxt);
-            issue(nxt, (t + 1) & 1);
-        }
-        Raw rnn;
-        const bool have_nn = have_nxt && next(rnxt.e, rnxt.g, rnxt, rnn);
-        if (!mbar_wait(bar0 + 8u * (t & 1), (t >> 1) & 1)) {
-            if (lane == 0) atomicOr(status, 1);
-            if (have_nxt) mbar_wait(bar0 + 8u * ((t + 1) & 1), ((t + 1) >> 1) & 1);
-            return;
-        }
-        float wt[2 * P];
-#pragma unroll
-        for (int j = 0; j < 2 * P; ++j)
-            wt[j] = 1.0f - (float)abs(cur.r0 - j * D32) * (1.0f / (float)kFracOne);
-        // lane's first frame offset in the buffer for hat h: sbase - P (lane + 32 h)
-        const int s0 = cur.sbase - P * lane;
-        const int M = s0 & (F - 1);
-        const int rs0 = s0 >> LGF;
-        const unsigned char* buf = bufp0 + (t & 1) * BUF_STRIDE;
-        float acc[HG][BC];
-        if constexpr (F == 1) {
-            adj6_contract<BC, P, HG, 0>(buf, rs0, wt, acc);
-        } else if constexpr (F == 2) {
-            if (M == 0) adj6_contract<BC, P, HG, 0>(buf, rs0, wt, acc);
-            else adj6_contract<BC, P, HG, 1>(buf, rs0, wt, acc);
-        } else if constexpr (F == 4) {
-            switch (M) {
-                case 0: adj6_contract<BC, P, HG, 0>(buf, rs0, wt, acc); break;
-                case 1: adj6_contract<BC, P, HG, 1>(buf, rs0, wt, acc); break;
-                case 2: adj6_contract<BC, P, HG, 2>(buf, rs0, wt, acc); break;
-                default: adj6_contract<BC, P, HG, 3>(buf, rs0, wt, acc); break;
-            }
-        } else {
-            switch (M) {
-                case 0: adj6_contract<BC, P, HG, 0>(buf, rs0, wt, acc); break;
-                case 1: adj6_contract<BC, P, HG, 1>(buf, rs0, wt, acc); break;
-                case 2: adj6_contract<BC, P, HG, 2>(buf, rs0, wt, acc); break;
-                case 3: adj6_contract<BC, P, HG, 3>(buf, rs0, wt, acc); break;
-                case 4: adj6_contract<BC, P, HG, 4>(buf, rs0, wt, acc); break;
-                case 5: adj6_contract<BC, P, HG, 5>(buf, rs0, wt, acc); break;
-                case 6: adj6_contract<BC, P, HG, 6>(buf, rs0, wt, acc); break;
-                default: adj6_contract<BC, P, HG, 7>(buf, rs0, wt, acc); break;
-            }
-        }
-#pragma unroll
-        for (int h = 0; h < HG; ++h) {
-            const int k = HATS * cur.g + lane + 32 * h;
-            if (k < a.K) {
-                float4* zo = reinterpret_cast<float4*>(a.zhat + (cur.e * a.K + k) * BC);
-#pragma unroll
-                for (int q = 0; q < BC / 4; ++q)
-                    zo[q] = make_float4(acc[h][4 * q], acc[h][4 * q + 1], acc[h][4 * q + 2],
-                                        acc[h][4 * q + 3]);
-            }
-        }
-        __syncwarp();  // buffer t & 1 is free for the copy issued at step t + 1
-        cur = nxt;
-        have = have_nxt;
-        rnxt = rnn;
-        have_nxt = have_nn;
     }
 }
 
@@ -1935,403 +1137,6 @@ fwd6_kernel(const ApplyArgs<float> a, int* status, uint32_t slab_bytes, uint32_t
     }
 }
 
-// ---------------------------------------------------------------------------
-// Fused forward + adjoint phase 1 (FP32, a frame step 1/P of a hat step, the
-// whole batch of B = BC in {4, 8} entries in one chunk).  y = scale A x is
-// computed exactly as fwd3_kernel<float, BC, FPL> computes it and written;
-// r = y - d (d optional) is kept in shared memory, and the per-ray temporal
-// contraction zhat_e = H_e^T r_row is taken from there with the periodic
-// weights of adj_time4_kernel, so the adjoint never reads y back from HBM.
-// A CTA owns a group of RG rows at a time: phase 1 spreads the (row, frame
-// chunk) tasks of the group over its warps, phase 2 the (ray, 32-hat group)
-// items of the group's rays.  Outputs are the bits of the separate applies.
-// ---------------------------------------------------------------------------
-
-// one (row, frame chunk) task of the staged forward into acc (fwd3 arithmetic)
-template <int BC, int FPL>
-__device__ __forceinline__ void fwd_task_vec(const ApplyArgs<float>& a, int row, int f_begin,
-                                             int f_end, float4* zsv, int lane,
-                                             float (&acc)[FPL][BC]) {
-    constexpr int Q = BC / 4;
-#pragma unroll
-    for (int j = 0; j < FPL; ++j)
-#pragma unroll
-        for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
-    const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
-    for (int e = e_begin; e < e_end; ++e) {
-        const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
-        const int k_top = (int)((U0 - (int64_t)f_begin * a.D) >> kFracBits);
-        const int k_lo = (int)((U0 - (int64_t)(f_end - 1) * a.D) >> kFracBits);
-        const int nwin = k_top + 2 - k_lo;
-        const float4 wv = a.W[e];
-        const int n00 = a.node00[e], n01 = a.node01[e];
-        const int64_t KB = (int64_t)a.K * a.B;
-        const float* x00 = a.in + (int64_t)n00 * KB;
-        const float* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB;
-        const float* x01 = a.in + (int64_t)n01 * KB;
-        const float* x11 = a.in + (int64_t)(n01 + a.n_phi) * KB;
-        const int n_items = nwin * Q;
-        for (int base = 0; base < n_items; base += 64) {
-            float4 v[2][4];
-            bool okv[2];
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int o = base + lane + 32 * u;
-                const int kk = o / Q, q = o - kk * Q;
-                const int k = k_lo + kk;
-                okv[u] = o < n_items && k >= 0 && k < a.K;
-                if (okv[u]) {
-                    const int64_t off = (int64_t)k * a.B + 4 * q;
-                    v[u][0] = __ldg(reinterpret_cast<const float4*>(x00 + off));
-                    v[u][1] = __ldg(reinterpret_cast<const float4*>(x10 + off));
-                    v[u][2] = __ldg(reinterpret_cast<const float4*>(x01 + off));
-                    v[u][3] = __ldg(reinterpret_cast<const float4*>(x11 + off));
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-                const int o = base + lane + 32 * u;
-                if (o < n_items) {
-                    float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (okv[u]) {
-                        z.x = interp4(wv.x, v[u][0].x, wv.y, v[u][1].x, wv.z, v[u][2].x, wv.w, v[u][3].x);
-                        z.y = interp4(wv.x, v[u][0].y, wv.y, v[u][1].y, wv.z, v[u][2].y, wv.w, v[u][3].y);
-                        z.z = interp4(wv.x, v[u][0].z, wv.y, v[u][1].z, wv.z, v[u][2].z, wv.w, v[u][3].z);
-                        z.w = interp4(wv.x, v[u][0].w, wv.y, v[u][1].w, wv.z, v[u][2].w, wv.w, v[u][3].w);
-                    }
-                    zsv[o] = z;
-                }
-            }
-        }
-        __syncwarp();
-        int64_t U = U0 - (int64_t)(f_begin + lane) * a.D;
-        const int64_t dU = (int64_t)32 * a.D;
-#pragma unroll
-        for (int j = 0; j < FPL; ++j) {
-            const int f = f_begin + lane + 32 * j;
-            if (f < f_end) {
-                const int k0 = (int)(U >> kFracBits);
-                const float fr = (float)(int32_t)(U & kFracMask) * (1.0f / (float)kFracOne);
-                const float g = 1.0f - fr;
-                const float4* z0 = zsv + (k0 - k_lo) * Q;
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const float4 p0 = z0[q], p1 = z0[Q + q];
-                    acc[j][4 * q + 0] = hat2(acc[j][4 * q + 0], g, p0.x, fr, p1.x);
-                    acc[j][4 * q + 1] = hat2(acc[j][4 * q + 1], g, p0.y, fr, p1.y);
-                    acc[j][4 * q + 2] = hat2(acc[j][4 * q + 2], g, p0.z, fr, p1.z);
-                    acc[j][4 * q + 3] = hat2(acc[j][4 * q + 3], g, p0.w, fr, p1.w);
-                }
-            }
-            U -= dU;
-        }
-        __syncwarp();
-    }
-}
-
-constexpr int kFusedMaxRows = 32;  // rows per CTA group (shared r rows)
-
-template <int BC, int FPL, int P>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32, 2)
-fused_kernel(const ApplyArgs<float> a, const float* __restrict__ d, int RG, int row_v4) {
-    constexpr int Q = BC / 4;
-    constexpr int FC = 32 * FPL;
-    extern __shared__ __align__(16) unsigned char smem7_raw[];
-    float4* rs = reinterpret_cast<float4*>(smem7_raw);  // [RG][row_v4] swizzled r rows
-    float4* zsv = rs + (size_t)RG * row_v4 + (size_t)(threadIdx.x >> 5) * a.zwin * Q;
-    __shared__ int ray_prefix[kFusedMaxRows + 1];  // rays of the group's rows, prefix sums
-    __shared__ int work[2];                          // next phase-1 / phase-2 item
-    const int lane = threadIdx.x & 31;
-    const int pshift = a.FC;  // swizzle key shift (log2 P, at least 1 when Q = 1)
-    const int n_groups_k = (a.K + 31) / 32;
-    const int32_t D32 = (int32_t)a.D;
-    // rays outside the arm: zero zhat rows (their data rows do not exist)
-    if (a.seg.total < a.seg_rows_all) {
-        const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-        const int64_t nth = (int64_t)gridDim.x * blockDim.x;
-        for (int64_t i = tid; i < a.n_rays_total * a.K; i += nth) {
-            const int64_t e = i / a.K;
-            if (seg_out_row(a.seg, a.ray_row[e]) < 0) {
-                float4* zo = reinterpret_cast<float4*>(a.zhat + i * BC);
-#pragma unroll
-                for (int q = 0; q < Q; ++q) zo[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-    }
-    const int n_row_groups = (a.seg.total + RG - 1) / RG;
-    for (int grp = blockIdx.x; grp < n_row_groups; grp += gridDim.x) {
-        const int first = grp * RG;
-        const int rows_here = min(RG, a.seg.total - first);
-        if (threadIdx.x == 0) {
-            int acc_rays = 0;
-            ray_prefix[0] = 0;
-            for (int i = 0; i < RG; ++i) {
-                if (i < rows_here) {
-                    const int row = seg_in_row(a.seg, first + i);
-                    acc_rays += a.row_ptr[row + 1] - a.row_ptr[row];
-                }
-                ray_prefix[i + 1] = acc_rays;
-            }
-            work[0] = 0;
-            work[1] = 0;
-        }
-        __syncthreads();
-        // phase 1: forward tasks (row of the group, frame chunk), taken by
-        // warps as they become free (rows differ in ray count)
-        const int n1 = rows_here * a.n_fchunk;
-        for (;;) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(&work[0], 1);
-            it = __shfl_sync(0xffffffffu, it, 0);
-            if (it >= n1) break;
-            const int rl = it / a.n_fchunk, fchunk = it - rl * a.n_fchunk;
-            const int row_out = first + rl;
-            const int row = seg_in_row(a.seg, row_out);
-            const int f_begin = fchunk * FC, f_end = min(a.Tn, f_begin + FC);
-            float acc[FPL][BC];
-            fwd_task_vec<BC, FPL>(a, row, f_begin, f_end, zsv, lane, acc);
-            float4* rrow = rs + (size_t)rl * row_v4;
-#pragma unroll
-            for (int j = 0; j < FPL; ++j) {
-                const int f = f_begin + lane + 32 * j;
-                if (f >= f_end) continue;
-                const int64_t yo = ((int64_t)row_out * a.Tn + f) * a.B;
-#pragma unroll
-                for (int q = 0; q < Q; ++q) {
-                    const float4 yv = make_float4(acc[j][4 * q], acc[j][4 * q + 1], acc[j][4 * q + 2],
-                                                  acc[j][4 * q + 3]);
-                    reinterpret_cast<float4*>(a.out + yo)[q] = yv;
-                    float4 rv = yv;
-                    if (d) {
-                        const float4 dv = __ldg(reinterpret_cast<const float4*>(d + yo) + q);
-                        rv = make_float4(yv.x - dv.x, yv.y - dv.y, yv.z - dv.z, yv.w - dv.w);
-                    }
-                    rrow[swz(f, q, Q, pshift)] = rv;
-                }
-            }
-        }
-        __syncthreads();
-        // phase 2: zhat for every ray of the group's rows (ray, 32-hat group)
-        const int n2 = ray_prefix[RG] * n_groups_k;
-        for (;;) {
-            int it = 0;
-            if (lane == 0) it = atomicAdd(&work[1], 1);
-            it = __shfl_sync(0xffffffffu, it, 0);
-            if (it >= n2) break;
-            const int ri = it / n_groups_k, g = it - ri * n_groups_k;
-            // row of ray ri: the last rl with ray_prefix[rl] <= ri (prefix sums)
-            int lo = 0, hi = rows_here;  // ray_prefix[lo] <= ri < ray_prefix[hi]
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) >> 1;
-                if (ray_prefix[mid] <= ri) lo = mid; else hi = mid;
-            }
-            const int rl = lo;
-            const int row = seg_in_row(a.seg, first + rl);
-            const int64_t e = (int64_t)a.row_ptr[row] + (ri - ray_prefix[rl]);
-            const int64_t U0 = (int64_t)a.K0[e] * kFracOne + (int64_t)a.F0[e];
-            const int64_t c0 = (U0 * P) >> kFracBits;
-            const int32_t r0 = (int32_t)(U0 - (c0 + 1) * a.D) + kFracOne;
-            const int fbase = (int)(c0 + 1 - P);
-            float wt[2 * P];
-#pragma unroll
-            for (int j = 0; j < 2 * P; ++j)
-                wt[j] = 1.0f - (float)abs(r0 - j * D32) * (1.0f / (float)kFracOne);
-            const int k = 32 * g + lane;
-            if (k < a.K) {
-                float accz[BC];
-#pragma unroll
-                for (int b = 0; b < BC; ++b) accz[b] = 0.0f;
-                const float4* rrow = rs + (size_t)rl * row_v4;
-                const int f0 = fbase - P * k;
-#pragma unroll
-                for (int j = 0; j < 2 * P; ++j) {
-                    const int f = f0 + j;
-                    if (f < 0 || f >= a.Tn) continue;  // outside the observation
-#pragma unroll
-                    for (int q = 0; q < Q; ++q) {
-                        const float4 v = rrow[swz(f, q, Q, pshift)];
-                        fmac2x2(wt[j], v, accz[4 * q + 0], accz[4 * q + 1], accz[4 * q + 2],
-                                accz[4 * q + 3]);
-                    }
-                }
-                float4* zo = reinterpret_cast<float4*>(a.zhat + (e * a.K + k) * BC);
-#pragma unroll
-                for (int q = 0; q < Q; ++q)
-                    zo[q] = make_float4(accz[4 * q], accz[4 * q + 1], accz[4 * q + 2], accz[4 * q + 3]);
-            }
-        }
-        __syncthreads();
-    }
-}
-
-// Adjoint phase 2, fast path: lanes over (hat, batch) of one node, nodes in
-// descending-load order; the incidence loop is unrolled by 4 so that four
-// zhat rows are in flight.
-template <typename T>
-__device__ __forceinline__ T corner_coef(const ApplyArgs<T>& a, int code);
-template <>
-__device__ __forceinline__ float corner_coef<float>(const ApplyArgs<float>& a, int code) {
-    return reinterpret_cast<const float*>(a.W)[code];  // W[e] component c = element 4e + c
-}
-template <>
-__device__ __forceinline__ double corner_coef<double>(const ApplyArgs<double>& a, int code) {
-    return a.W64[code];
-}
-
-template <typename T, int BC>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-adj_space3_kernel(const ApplyArgs<T> a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
-        // hat-chunk-major task order: while one hat chunk is gathered for all
-        // nodes, only that slice of zhat (1 / n_kchunk of it) is live in L2
-        const int kchunk = (int)(task / a.n_nodes);
-        const int ni = (int)(task - (int64_t)kchunk * a.n_nodes);
-        const int node = a.node_order ? a.node_order[ni] : ni;
-        const int k_begin = kchunk * a.KC;
-        T acc[kAdjOutPerLane];
-#pragma unroll
-        for (int j = 0; j < kAdjOutPerLane; ++j) acc[j] = T(0);
-        int off[kAdjOutPerLane];
-        bool live[kAdjOutPerLane];
-#pragma unroll
-        for (int j = 0; j < kAdjOutPerLane; ++j) {
-            const int o = lane + 32 * j;
-            const int kk = o / BC, bb = o - kk * BC;
-            const int k = k_begin + kk;
-            live[j] = kk < a.KC && k < a.K && bb < a.Bc;
-            off[j] = k * a.Bc + bb;
-        }
-        const int i_begin = a.node_ptr[node], i_end = a.node_ptr[node + 1];
-        int ii = i_begin;
-        // incidence codes of the next group of 4 are loaded before the current
-        // group's zhat rows are consumed (two loads levels in flight)
-        int nxt[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) nxt[u] = (ii + u < i_end) ? a.inc[ii + u] : 0;
-        for (; ii + 4 <= i_end; ii += 4) {
-            int code[4];
-            T coef[4];
-            const T* zr[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) code[u] = nxt[u];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) nxt[u] = (ii + 4 + u < i_end) ? a.inc[ii + 4 + u] : 0;
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                coef[u] = corner_coef(a, code[u]);
-                zr[u] = a.zhat + (int64_t)(code[u] >> 2) * a.K * a.Bc;
-            }
-#pragma unroll
-            for (int j = 0; j < kAdjOutPerLane; ++j) {
-                if (!live[j]) continue;
-                const T v0 = zr[0][off[j]], v1 = zr[1][off[j]], v2 = zr[2][off[j]], v3 = zr[3][off[j]];
-                acc[j] = fmac(coef[0], v0, acc[j]);
-                acc[j] = fmac(coef[1], v1, acc[j]);
-                acc[j] = fmac(coef[2], v2, acc[j]);
-                acc[j] = fmac(coef[3], v3, acc[j]);
-            }
-        }
-        for (; ii < i_end; ++ii) {
-            const int code = a.inc[ii];
-            const T coef = corner_coef(a, code);
-            const T* zr = a.zhat + (int64_t)(code >> 2) * a.K * a.Bc;
-#pragma unroll
-            for (int j = 0; j < kAdjOutPerLane; ++j)
-                if (live[j]) acc[j] = fmac(coef, zr[off[j]], acc[j]);
-        }
-#pragma unroll
-        for (int j = 0; j < kAdjOutPerLane; ++j) {
-            if (!live[j]) continue;
-            const int o = lane + 32 * j;
-            const int kk = o / BC, bb = o - kk * BC;
-            a.out[((int64_t)node * a.K + k_begin + kk) * a.B + bb] = acc[j];
-        }
-    }
-}
-
-// Adjoint phase 2 with 16-byte loads (FP32, Bc = BC a multiple of 4): each
-// lane owns 8 consecutive (hat, batch) outputs of the task's block, so one
-// incidence costs two float4 loads per lane.  Same incidence order and
-// accumulation sequence as adj_space3_kernel.
-template <int BC, int kSpace4Unroll = 4>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-adj_space4_kernel(const ApplyArgs<float> a) {
-    static_assert(BC % 4 == 0, "vector path needs 4 | BC");
-    wait_prior_grid();
-    const int lane = threadIdx.x & 31;
-    const int64_t warp_global = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
-    const int64_t n_warps = (int64_t)gridDim.x * kWarpsPerBlock;
-    const int row_len = a.K * BC;  // floats per zhat row
-    for (int64_t task = warp_global; task < a.n_tasks; task += n_warps) {
-        // hat-chunk-major task order: while one hat chunk is gathered for all
-        // nodes, only that slice of zhat (1 / n_kchunk of it) is live in L2
-        const int kchunk = (int)(task / a.n_nodes);
-        const int ni = (int)(task - (int64_t)kchunk * a.n_nodes);
-        const int node = a.node_order ? a.node_order[ni] : ni;
-        const int zoff = kchunk * a.KC * BC + 8 * lane;  // first of this lane's 8 outputs
-        const bool live0 = zoff < row_len && 8 * lane < a.KC * BC;
-        const bool live1 = zoff + 4 < row_len && 8 * lane + 4 < a.KC * BC;
-        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
-        const int i_begin = a.node_ptr[node], i_end = a.node_ptr[node + 1];
-        const float* Wf = reinterpret_cast<const float*>(a.W);
-        int ii = i_begin;
-        int nxt[kSpace4Unroll];
-#pragma unroll
-        for (int u = 0; u < kSpace4Unroll; ++u) nxt[u] = (ii + u < i_end) ? a.inc[ii + u] : 0;
-        for (; ii + kSpace4Unroll <= i_end; ii += kSpace4Unroll) {
-            int code[kSpace4Unroll];
-#pragma unroll
-            for (int u = 0; u < kSpace4Unroll; ++u) code[u] = nxt[u];
-#pragma unroll
-            for (int u = 0; u < kSpace4Unroll; ++u)
-                nxt[u] = (ii + kSpace4Unroll + u < i_end) ? a.inc[ii + kSpace4Unroll + u] : 0;
-            float coef[kSpace4Unroll];
-            float4 v0[kSpace4Unroll], v1[kSpace4Unroll];
-#pragma unroll
-            for (int u = 0; u < kSpace4Unroll; ++u) {
-                coef[u] = __ldg(Wf + code[u]);
-                const float4* zr = reinterpret_cast<const float4*>(
-                    a.zhat + (int64_t)(code[u] >> 2) * row_len + zoff);
-                v0[u] = live0 ? __ldg(zr) : make_float4(0.f, 0.f, 0.f, 0.f);
-                v1[u] = live1 ? __ldg(zr + 1) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-#pragma unroll
-            for (int u = 0; u < kSpace4Unroll; ++u) {
-                fmac2x2(coef[u], v0[u], acc0.x, acc0.y, acc0.z, acc0.w);
-                fmac2x2(coef[u], v1[u], acc1.x, acc1.y, acc1.z, acc1.w);
-            }
-        }
-        for (; ii < i_end; ++ii) {
-            const int code = a.inc[ii];
-            const float coef = __ldg(Wf + code);
-            const float4* zr =
-                reinterpret_cast<const float4*>(a.zhat + (int64_t)(code >> 2) * row_len + zoff);
-            if (live0) {
-                const float4 v = __ldg(zr);
-                acc0.x = fmac(coef, v.x, acc0.x); acc0.y = fmac(coef, v.y, acc0.y);
-                acc0.z = fmac(coef, v.z, acc0.z); acc0.w = fmac(coef, v.w, acc0.w);
-            }
-            if (live1) {
-                const float4 v = __ldg(zr + 1);
-                acc1.x = fmac(coef, v.x, acc1.x); acc1.y = fmac(coef, v.y, acc1.y);
-                acc1.z = fmac(coef, v.z, acc1.z); acc1.w = fmac(coef, v.w, acc1.w);
-            }
-        }
-        // flat zhat offset z -> hat z / BC, batch z % BC (4 | BC keeps a float4 in one hat)
-        if (live0) {
-            const int k = zoff / BC, b = zoff % BC;
-            *reinterpret_cast<float4*>(a.out + ((int64_t)node * a.K + k) * a.B + b) = acc0;
-        }
-        if (live1) {
-            const int k = (zoff + 4) / BC, b = (zoff + 4) % BC;
-            *reinterpret_cast<float4*>(a.out + ((int64_t)node * a.K + k) * a.B + b) = acc1;
-        }
-    }
-}
-
 static int pick_bc(int B) {
     int bc = 1;
     while (bc < B && bc < 32) bc <<= 1;
@@ -2347,39 +1152,12 @@ static int grid_for(int64_t n_tasks) {
     return (int)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
-static int sm_count() {
-    int dev = 0, sms = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;
-}
-
-// one wave of resident CTAs of `kernel` for a persistent grid-stride loop
-// (fewer when the tasks need fewer)
-template <typename Kern>
-static int resident_grid(Kern kernel, int threads, size_t smem, int64_t n_tasks, int warps) {
-    int per_sm = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
-    const int64_t want = (n_tasks + warps - 1) / warps;
-    const int64_t cap = (int64_t)sm_count() * per_sm;
-    return (int)(want < cap ? (want > 0 ? want : 1) : cap);
-}
-
 // 16-byte vector access is used only when the batch stride and both buffers
 // allow it
 template <typename T>
 static int vec_ok(const ApplyArgs<T>& a) {
     constexpr int W = Vec16<T>::W;
     return (a.B % W == 0) && ((uintptr_t)a.in % 16 == 0) && ((uintptr_t)a.out % 16 == 0) ? 1 : 0;
-}
-
-// frames per hat step when that is an integer the periodic kernel handles, else 0
-static int frames_per_hat(int64_t D) {
-    if (D <= 0 || kFracOne % D != 0) return 0;
-    const int P = (int)(kFracOne / D);
-    return (P == 2 || P == 4 || P == 8) ? P : 0;
 }
 
 template <typename T>
@@ -2395,8 +1173,6 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     a.K0 = op->K0;
     a.F0 = op->F0;
     a.F64 = op->F64;
-    a.node_ptr = op->node_ptr;
-    a.inc = op->inc;
     a.in = in;
     a.out = out;
     a.B = B;
@@ -2408,7 +1184,6 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     a.delta = op->delta;
     a.seg = seg;
     a.seg_rows_all = (int)op->n_rows;
-    a.node_order = op->node_order;
     a.status = op->dev_status;
     a.hs32 = (op->frame_D > 0 && ((int64_t)32 * op->frame_D) % kFracOne == 0)
                  ? (int)((int64_t)32 * op->frame_D / kFracOne)
@@ -2446,112 +1221,6 @@ static cudaError_t launch_fwd4(ApplyArgs<float> a, cudaStream_t st) {
     if (a.n_tasks == 0) return cudaSuccess;
     fwd4_kernel<BC, P><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
     return cudaGetLastError();
-}
-
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library); null when unavailable
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) != cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            p = nullptr;
-        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }();
-    return fn;
-}
-
-// TMA time phase; cudaErrorNotSupported when this chunk cannot use it (its
-// frames must be contiguous 128-byte rows: one chunk holding the whole batch,
-// B = BC in {4, 8, 16, 32}, frame count a multiple of 32 / BC)
-template <int BC, int P>
-static cudaError_t launch_adj5(ApplyArgs<float> t, int* status, cudaStream_t st) {
-    if constexpr (BC < 4) {
-        return cudaErrorNotSupported;
-    } else {
-        constexpr int FPR = T5Box<BC, P>::kFPR;
-        if (!vec_ok(t) || t.Bc != BC || t.B != BC || (t.Tn % FPR) != 0 || !status)
-            return cudaErrorNotSupported;
-        const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-        if (!enc) return cudaErrorNotSupported;
-        constexpr int ROWS = T5Box<BC, P>::kRows;
-        static_assert(ROWS <= 256, "TMA box rows");
-        const uint64_t n_rows128 = (uint64_t)t.seg.total * (uint64_t)t.Tn / FPR;
-        if (n_rows128 == 0 || n_rows128 >= (1ull << 31)) return cudaErrorNotSupported;
-        CUtensorMap m;
-        cuuint64_t dims[2] = {32, (cuuint64_t)n_rows128};  // 32 floats = 128 bytes per row
-        cuuint64_t strides[1] = {128};
-        cuuint32_t box[2] = {32, (cuuint32_t)ROWS};
-        cuuint32_t es[2] = {1, 1};
-        if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(t.in), dims, strides, box,
-                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorNotSupported;
-        t.n_tasks = t.n_rays_total;
-        const size_t smem =
-            1024 + (size_t)kAdj5Warps * 2 * T5Box<BC, P>::kStride + (size_t)kAdj5Warps * 16;
-        cudaError_t e = cudaFuncSetAttribute(adj_time5_kernel<BC, P>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        int per_sm = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_time5_kernel<BC, P>,
-                                                      kAdj5Warps * 32, smem);
-        if (per_sm < 1) per_sm = 1;
-        const int64_t want = (t.n_tasks + kAdj5Warps - 1) / kAdj5Warps;
-        const int64_t cap = (int64_t)sm_count() * per_sm;
-        const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-        adj_time5_kernel<BC, P><<<grid, kAdj5Warps * 32, smem, st>>>(m, t, status);
-        return cudaGetLastError();
-    }
-}
-
-// whole-item TMA time phase; cudaErrorNotSupported unless the batch is one
-// chunk of B = BC in {4, 8, 16, 32} whose 128-byte row holds F = 32 / BC
-// frames with F dividing both P and the frame count
-// (BC, P) pairs of adj_time6_kernel: whole frames per row dividing P, box <= 256 rows
-template <int BC, int P>
-constexpr bool adj6_shape_ok() {
-    if (BC < 4 || BC > 32 || P % (32 / (BC < 4 ? 4 : BC)) != 0) return false;
-    const int F = 32 / BC, HG = BC <= 8 ? 2 : 1;
-    return ((32 * HG + 1) * P + 2 * (F - 1)) / F <= 256;
-}
-
-template <int BC, int P>
-static cudaError_t launch_adj6(ApplyArgs<float> t, int* status, cudaStream_t st) {
-    if constexpr (!adj6_shape_ok<BC, P>()) {
-        return cudaErrorNotSupported;
-    } else {
-        constexpr int HG = BC <= 8 ? 2 : 1;
-        constexpr int F = T6Box<BC, P, HG>::kF;
-        constexpr int ROWS = T6Box<BC, P, HG>::kRows;
-        static_assert(ROWS <= 256, "TMA box rows");
-        if (!vec_ok(t) || t.Bc != BC || t.B != BC || (t.Tn % F) != 0 || !status)
-            return cudaErrorNotSupported;
-        const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-        if (!enc || t.seg.total <= 0) return cudaErrorNotSupported;
-        CUtensorMap m;
-        // (32 floats = one 128-byte row, rows of a data row's frames, data rows)
-        cuuint64_t dims[3] = {32, (cuuint64_t)(t.Tn / F), (cuuint64_t)t.seg.total};
-        cuuint64_t strides[2] = {128, (cuuint64_t)(t.Tn / F) * 128};
-        cuuint32_t box[3] = {32, (cuuint32_t)ROWS, 1};
-        cuuint32_t es[3] = {1, 1, 1};
-        if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(t.in), dims, strides, box,
-                es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorNotSupported;
-        t.n_tasks = t.n_rays_total;
-        const size_t smem =
-            1024 + (size_t)kAdj6Warps * 2 * T6Box<BC, P, HG>::kStride + (size_t)kAdj6Warps * 16;
-        cudaError_t e = cudaFuncSetAttribute(adj_time6_kernel<BC, P, HG>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        const int grid =
-            resident_grid(adj_time6_kernel<BC, P, HG>, kAdj6Warps * 32, smem, t.n_tasks, kAdj6Warps);
-        return launch_dependent(adj_time6_kernel<BC, P, HG>, dim3(grid), dim3(kAdj6Warps * 32), smem, st,
-                                m, t, status);
-    }
 }
 
 // TMA forward; cudaErrorNotSupported when the batch layout cannot use it
@@ -2643,29 +1312,20 @@ static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st) {
     }
 }
 
+int adjoint_best_kind(const rtt_op_s* op, int batch);
+
 ApplyVariant variant_for(const rtt_op_s* op, int batch) {
     for (int i = 0; i < op->n_tuned; ++i)
         if (op->tuned_batch[i] == batch) return op->tuned[i];
     // default rule, from the kerr256 measurements: the periodic one-chunk
-    // forward, the whole-item TMA time phase and the gather with eight
-    // incidences in flight; each falls back to the next kernel down where
-    // the cadence, batch or buffers do not allow it
+    // forward and the widest TMA adjoint items; each falls back to the next
+    // kernel down where the cadence, batch or buffers do not allow it
     ApplyVariant v;
     const int P = frames_per_hat(op->frame_D);
     const bool one_chunk4 = batch == 4 || batch == 8;
-    const bool rows128 = (batch == 4 || batch == 8 || batch == 16 || batch == 32) &&
-                         op->time.n_frames % (32 / batch) == 0;
     v.fwd = (P > 0 && one_chunk4) ? 5 : 1;
     v.fwd_bc = (int8_t)pick_bc(batch);
-    if (P == 0)
-        v.time = 1;
-    else if (rows128 && P % (32 / batch) == 0 && !(batch == 32 && P == 8))
-        v.time = 4;
-    else if (rows128 && (P == 2 || P == 4))
-        v.time = 3;
-    else
-        v.time = 2;
-    v.space = 3;
+    v.adj = (int8_t)adjoint_best_kind(op, batch);
     return v;
 }
 
@@ -2753,230 +1413,9 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
     }
 }
 
-// Adjoint: fast phase 1 when the frames of a 32-hat group fit the staging
-// buffer, otherwise the general per-(hat, batch) kernel; then the gather.
-template <int BC, int P>
-static cudaError_t launch_adj4(ApplyArgs<float> t, cudaStream_t st) {
-    // staged frames per 32-hat group: 31 P + 2P = 33 P, rounded to 8 so the
-    // swizzle stays inside the buffer; swizzle key from frame bits >= log2 P
-    int ps = 0;
-    while ((2 << ps) <= P) ++ps;
-    constexpr int Qv = BC >= 4 ? BC / 4 : 1;
-    if (Qv == 1 && ps == 0) ps = 1;
-    t.FC = ps;
-    t.zwin = (33 * P + 7) & ~7;
-    t.vec4 = vec_ok(t);
-    t.n_tasks = t.n_rays_total;
-    const size_t smem = (size_t)kAdj3Warps * t.zwin * BC * sizeof(float);
-    if (smem > 48 * 1024) {
-        cudaError_t err = cudaFuncSetAttribute(adj_time4_kernel<BC, P>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-    }
-    const int64_t want = (t.n_tasks + kAdj3Warps - 1) / kAdj3Warps;
-    const int64_t cap = (int64_t)sm_count() * 32;
-    const int grid = (int)(want < cap ? (want > 0 ? want : 1) : cap);
-    adj_time4_kernel<BC, P><<<grid, kAdj3Warps * 32, smem, st>>>(t);
-    return cudaGetLastError();
-}
-
-template <typename T, int BC>
-static cudaError_t launch_adj3_bc(ApplyArgs<T> a, const ApplyVariant& v, cudaStream_t st,
-                                  bool time_phase = true) {
-    // staged frames per 32-hat group, rounded so the swizzle stays in bounds
-    int ywin = (int)ceil(33.0 / a.delta) + 2;
-    ywin = (ywin + 7) & ~7;
-    const size_t smem = (size_t)kAdj3Warps * ywin * BC * sizeof(T);
-    cudaError_t e = cudaSuccess;
-    bool periodic = !time_phase;  // true once phase 1 is done (or not wanted)
-    if constexpr (sizeof(T) == 4) {
-        const int P = v.time >= 2 ? frames_per_hat(a.D) : 0;
-        if (!periodic && a.seg.total > 0 && P > 0) {
-            periodic = true;
-            e = cudaErrorNotSupported;
-            if (v.time == 4)
-                e = P == 2 ? launch_adj6<BC, 2>(a, a.status, st)
-                           : (P == 4 ? launch_adj6<BC, 4>(a, a.status, st)
-                                     : launch_adj6<BC, 8>(a, a.status, st));
-            if (e == cudaErrorNotSupported && v.time >= 3 && (P == 2 || P == 4)) {
-                cudaGetLastError();
-                e = P == 2 ? launch_adj5<BC, 2>(a, a.status, st) : launch_adj5<BC, 4>(a, a.status, st);
-            }
-            if (e == cudaErrorNotSupported) {
-                cudaGetLastError();  // clear the "not supported" marker, if any
-                e = P == 2 ? launch_adj4<BC, 2>(a, st)
-                           : (P == 4 ? launch_adj4<BC, 4>(a, st) : launch_adj4<BC, 8>(a, st));
-            }
-            if (e != cudaSuccess) return e;
-        }
-    }
-    if (a.seg.total > 0 && !periodic) {
-        if (smem <= 96 * 1024) {
-            ApplyArgs<T> t = a;
-            t.zwin = ywin;
-            {
-                // log2 of the frames per hat step (swizzle key only)
-                int ps = 0;
-                while ((2 << ps) <= (int)floor(1.0 / a.delta + 0.5)) ++ps;
-                // the XOR key (f >> ps) & 7 must come from bits of the chunk
-                // index f * Q + q above the three it flips, or the layout is
-                // not a permutation: with Q = 1 that needs ps >= 1
-                constexpr int Qv = BC / Vec16<T>::W > 0 ? BC / Vec16<T>::W : 1;
-                if (Qv == 1 && ps == 0) ps = 1;
-                t.FC = ps;
-            }
-            t.vec4 = vec_ok(a);
-            t.n_tasks = a.n_rays_total;
-            if (smem > 48 * 1024) {
-                e = cudaFuncSetAttribute(adj_time3_kernel<T, BC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (e != cudaSuccess) return e;
-            }
-            const int64_t want = (t.n_tasks + kAdj3Warps - 1) / kAdj3Warps;
-            int dev = 0, sms = 148;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int grid = (int)(want < (int64_t)sms * 32 ? (want > 0 ? want : 1) : (int64_t)sms * 32);
-            adj_time3_kernel<T, BC><<<grid, kAdj3Warps * 32, smem, st>>>(t);
-            e = cudaGetLastError();
-        } else {
-            ApplyArgs<T> t = a;
-            t.KC = kAdjOutPerLane * 32 / BC;
-            t.n_kchunk = (a.K + t.KC - 1) / t.KC;
-            t.n_bchunk = 1;
-            t.n_tasks = a.n_rays_total * t.n_kchunk;
-            adj_time_kernel<T, BC><<<grid_for(t.n_tasks), kWarpsPerBlock * 32, 0, st>>>(t);
-            e = cudaGetLastError();
-        }
-        if (e != cudaSuccess) return e;
-    }
-    a.KC = kAdjOutPerLane * 32 / BC;
-    a.n_kchunk = (a.K + a.KC - 1) / a.KC;
-    a.n_bchunk = 1;
-    a.n_tasks = (int64_t)a.n_nodes * a.n_kchunk;
-    if (a.n_tasks == 0) return cudaSuccess;
-    if constexpr (sizeof(T) == 4 && BC % 4 == 0) {
-        if (v.space >= 2 && a.Bc == BC && vec_ok(a)) {
-            if (v.space == 3)  // eight incidences in flight per lane
-                return launch_dependent(adj_space4_kernel<BC, 8>, dim3(grid_for(a.n_tasks)),
-                                        dim3(kWarpsPerBlock * 32), 0, st, a);
-            else
-                adj_space4_kernel<BC, 4><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
-            return cudaGetLastError();
-        }
-    }
-    adj_space3_kernel<T, BC><<<grid_for(a.n_tasks), kWarpsPerBlock * 32, 0, st>>>(a);
-    return cudaGetLastError();
-}
-
-
-template <typename T>
-static cudaError_t launch_adjoint_impl(const rtt_op_s* op, const T* y, T* x, int B,
-                                       const ArmSeg& seg, T* zhat, cudaStream_t st,
-                                       bool time_phase);
-
-template <typename T>
-cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const ArmSeg& seg,
-                           T* zhat, cudaStream_t st) {
-    return launch_adjoint_impl<T>(op, y, x, B, seg, zhat, st, true);
-}
-
-template <typename T>
-static cudaError_t launch_adjoint_impl(const rtt_op_s* op, const T* y, T* x, int B,
-                                       const ArmSeg& seg, T* zhat, cudaStream_t st,
-                                       bool time_phase) {
-    if (seg.total == 0)  // no data rows in the arm: A^T y = 0
-        return cudaMemsetAsync(x, 0, (size_t)op->n_nodes * op->time.n_hats * B * sizeof(T), st);
-    // batch chunks of at most 32 entries share the zhat scratch [E][K][32]
-    for (int b_first = 0; b_first < B; b_first += 32) {
-        const int Bc = B - b_first < 32 ? B - b_first : 32;
-        ApplyArgs<T> a = base_args<T>(op, y + b_first, x + b_first, B, seg);
-        a.zhat = zhat;
-        a.Bc = Bc;
-        a.n_rays_total = op->n_rays;
-        cudaError_t e;
-        ApplyVariant v;  // FP64: general kernels
-        v.time = 1;
-        v.space = 1;
-        if constexpr (sizeof(T) == 4) {
-            v = variant_for(op, B);
-        }
-        switch (pick_bc(Bc)) {
-            case 1: e = launch_adj3_bc<T, 1>(a, v, st, time_phase); break;
-            case 2: e = launch_adj3_bc<T, 2>(a, v, st, time_phase); break;
-            case 4: e = launch_adj3_bc<T, 4>(a, v, st, time_phase); break;
-            case 8: e = launch_adj3_bc<T, 8>(a, v, st, time_phase); break;
-            case 16: e = launch_adj3_bc<T, 16>(a, v, st, time_phase); break;
-            default: e = launch_adj3_bc<T, 32>(a, v, st, time_phase); break;
-        }
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
-}
-
-template <int BC, int FPL, int P>
-static cudaError_t launch_fused(ApplyArgs<float> a, const float* d, cudaStream_t st) {
-    constexpr int Q = BC / 4;
-    int ps = 0;
-    while ((2 << ps) <= P) ++ps;  // swizzle key shift log2 P (>= 1)
-    a.FC = ps;
-    a.zwin = (int)ceil((32 * FPL - 1) * a.delta) + 3;
-    a.n_fchunk = (a.Tn + 32 * FPL - 1) / (32 * FPL);
-    const int row_v4 = (a.Tn * Q + 7) & ~7;
-    // rows per group: about 64 KB of r rows, at most kFusedMaxRows
-    int RG = (int)((64 * 1024) / ((size_t)row_v4 * 16));
-    RG = RG < 1 ? 1 : (RG > kFusedMaxRows ? kFusedMaxRows : RG);
-    const size_t smem = ((size_t)RG * row_v4 + (size_t)kWarpsPerBlock * a.zwin * Q) * 16;
-    if (smem > 200 * 1024) return cudaErrorNotSupported;
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<BC, FPL, P>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_kernel<BC, FPL, P>,
-                                                  kWarpsPerBlock * 32, smem);
-    if (per_sm < 1) per_sm = 1;
-    const int64_t groups = (a.seg.total + RG - 1) / RG;
-    const int64_t cap = (int64_t)sm_count() * per_sm;
-    const int grid = (int)(groups < cap ? (groups > 0 ? groups : 1) : cap);
-    fused_kernel<BC, FPL, P><<<grid, kWarpsPerBlock * 32, smem, st>>>(a, d, RG, row_v4);
-    return cudaGetLastError();
-}
-
-// y = scale A x and x_out = scale A^T (y - d) in one forward pass plus the
-// gather, when the operator and buffers allow the fused kernel (FP32 batch
-// of 4 or 8, 16-byte aligned buffers, 2, 4 or 8 frames per hat step);
-// cudaErrorNotSupported otherwise (nothing launched)
-cudaError_t launch_forward_adjoint_fused(const rtt_op_s* op, const float* x, const float* d,
-                                         float* y, float* g, int B, const ArmSeg& seg,
-                                         float* zhat, cudaStream_t st) {
-    const int P = frames_per_hat(op->frame_D);
-    if ((B != 4 && B != 8) || P == 0 || seg.total == 0) return cudaErrorNotSupported;
-    if (((uintptr_t)x | (uintptr_t)y | (uintptr_t)g | (uintptr_t)(d ? d : y)) % 16 != 0)
-        return cudaErrorNotSupported;
-    ApplyArgs<float> a = base_args<float>(op, x, y, B, seg);
-    a.zhat = zhat;
-    a.Bc = B;
-    a.n_rays_total = op->n_rays;
-    a.vec4 = 1;
-    cudaError_t e;
-    if (B == 8)
-        e = P == 2 ? launch_fused<8, 4, 2>(a, d, st)
-                   : (P == 4 ? launch_fused<8, 4, 4>(a, d, st) : launch_fused<8, 4, 8>(a, d, st));
-    else
-        e = P == 2 ? launch_fused<4, 8, 2>(a, d, st)
-                   : (P == 4 ? launch_fused<4, 8, 4>(a, d, st) : launch_fused<4, 8, 8>(a, d, st));
-    if (e != cudaSuccess) return e;
-    // phase 2: the gather of zhat into g (y is only a placeholder input here)
-    return launch_adjoint_impl<float>(op, y, g, B, seg, zhat, st, false);
-}
-
 template cudaError_t launch_forward<float>(const rtt_op_s*, const float*, float*, int, const ArmSeg&,
                                            cudaStream_t);
 template cudaError_t launch_forward<double>(const rtt_op_s*, const double*, double*, int,
                                             const ArmSeg&, cudaStream_t);
-template cudaError_t launch_adjoint<float>(const rtt_op_s*, const float*, float*, int, const ArmSeg&,
-                                           float*, cudaStream_t);
-template cudaError_t launch_adjoint<double>(const rtt_op_s*, const double*, double*, int,
-                                            const ArmSeg&, double*, cudaStream_t);
 
 }  // namespace rtt

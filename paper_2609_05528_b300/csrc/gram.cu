@@ -20,11 +20,6 @@
 
 namespace rtt {
 
-template <typename T>
-cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
-template <typename T>
-cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
-rtt_status ensure_zhat_bytes(rtt_op_s* op, size_t bytes);
 
 // dst[n][j] = Q[n][c0 + j], j < w
 __global__ void copy_cols(const double* Q, int64_t n, int d, int c0, int w, double* dst) {
@@ -323,7 +318,7 @@ static rtt_status gram_normal_impl(rtt_op op, int arm_mask, int mix_mode, const 
     const int W = 32;  // columns per pass
     const int64_t N = (int64_t)op->n_nodes * op->time.n_hats;
     const int64_t M = (int64_t)seg.total * op->time.n_frames;
-    s = ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * W * sizeof(double));
+    s = ensure_adjoint_scratch(op, W, (int)sizeof(double));
     if (s != RTT_OK) return s;
     double *Qc = nullptr, *Y = nullptr, *Z = nullptr, *YL = nullptr;
     if (mix_mode) {
@@ -359,7 +354,7 @@ static rtt_status gram_normal_impl(rtt_op op, int arm_mask, int mix_mode, const 
                 launch_mix<double>(op, seg, mix_mode, YL, Y, cols, true, st) != RTT_OK)
                 e = cudaErrorUnknown;
         }
-        if (e == cudaSuccess) e = launch_adjoint<double>(op, Y, Z, w, seg, (double*)op->zhat, st);
+        if (e == cudaSuccess) e = launch_adjoint<double>(op, Y, Z, w, seg, st);
         // rows c0 .. c0+w of G (symmetric): column-major (d x w) = Q_cm (d x N) Z_cm^T (N x w)
         if (e == cudaSuccess)
             cs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, d, w, (int)N, &one, Q, d, Z, w, &zero,

@@ -44,12 +44,8 @@ struct ApplyVariant {
     int8_t fwd_bc = 0;  // batch entries per forward task (power of two)
     int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
     int8_t fwd_su = 2;   // staged forward: staging items in flight per lane (1, 2 or 3)
-    int8_t time = 0;    // adjoint phase 1: 1 general (adj_time3), 2 periodic (adj_time4),
-                        // 3 periodic with TMA-staged frames (adj_time5), 4 whole-item
-                        // TMA phase with zero-filled frames (adj_time6)
-    int8_t space = 0;   // adjoint phase 2: 1 scalar (adj_space3), 2 16-byte (adj_space4),
-                        // 3 16-byte with eight incidences in flight
-    int8_t fused = 0;   // rtt_apply_A_AT: 1 = fused forward + time phase where possible
+    int8_t adj = 0;     // adjoint: 1 general (staged by per-lane copies), 2 TMA with 32-hat
+                        // items, 3 TMA with 64-hat items (the widest the call allows is used)
 };
 constexpr int kMaxTuned = 8;  // batch sizes with an autotuned variant per operator
 
@@ -88,14 +84,27 @@ struct rtt_op_s {
     double* delay = nullptr;
     double* weight = nullptr;
     double* thr = nullptr;
-    int32_t* node_ptr = nullptr;  // [S+1] transposed incidence CSR
-    int32_t* inc = nullptr;       // [4E] e * 4 + c
     int32_t* row_order = nullptr; // [R] order of each row
     int32_t* row_pixel = nullptr; // [R] pixel of each row
-    int32_t* node_order = nullptr; // [S] nodes sorted by descending incidence count
-    // adjoint scratch: per-ray temporal contraction [E][K][<=32], grown on demand
-    void* zhat = nullptr;
-    size_t zhat_bytes = 0;
+    // adjoint by source cells (adjoint.cu): ray tables in cell order, strip
+    // segments of cells, their partial records and the gather table
+    int32_t* c_row = nullptr;    // [E] input data row
+    int32_t* c_col = nullptr;    // [E] cell column
+    int32_t* c_K0 = nullptr;     // [E]
+    int32_t* c_F0 = nullptr;     // [E]
+    float4* c_W = nullptr;       // [E]
+    double* c_W64 = nullptr;     // [4E]
+    double* c_F64 = nullptr;     // [E]
+    int32_t* seg_ray = nullptr;  // [n_seg + 1]
+    int32_t* seg_col = nullptr;  // [n_seg]
+    int32_t* seg_ncol = nullptr; // [n_seg]
+    int32_t* seg_rec = nullptr;  // [n_seg]
+    int32_t* gslot = nullptr;    // [S][4] records of each node, -1 for none
+    int32_t n_seg = 0;
+    int64_t n_rec = 0;
+    int* adj_ctr = nullptr;      // work ticket counter of the adjoint (reset by its gather)
+    void* cpart = nullptr;       // partial records [n_rec][K][<= 32 columns], grown on demand
+    size_t cpart_bytes = 0;
     void* rscratch = nullptr;  // residual y - d of the separate-path rtt_apply_A_AT, grown on demand
     size_t rscratch_bytes = 0;
     int* dev_status = nullptr;  // device status word: bit 0 = a kernel's bounded wait timed out
@@ -128,4 +137,15 @@ int64_t mix_out_rows(const rtt_op_s* op, const ArmSeg& seg, int mode);
 template <typename T>
 rtt_status launch_mix(rtt_op_s* op, const ArmSeg& seg, int mode, const T* in, T* out, int64_t cols,
                       bool adjoint, cudaStream_t st);
+// the adjoint's partial-record scratch for `batch` columns of `elem`-byte
+// values (grown on demand; synchronises the device when it grows)
+rtt_status ensure_adjoint_scratch(rtt_op_s* op, int batch, int elem);
+size_t adjoint_scratch_bytes(const rtt_op_s* op, int batch, int elem);
+rtt_status build_cells(rtt_op_s* op, cudaStream_t st);
+template <typename T>
+cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const ArmSeg& seg,
+                           cudaStream_t st);
+template <typename T>
+cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const ArmSeg& seg,
+                           cudaStream_t st);
 }  // namespace rtt

@@ -19,11 +19,6 @@
 
 namespace rtt {
 
-template <typename T>
-cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
-template <typename T>
-cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
-rtt_status ensure_zhat_bytes(rtt_op_s* op, size_t bytes);
 
 constexpr int kDotBlocks = 296;  // fixed grid: deterministic partial order
 constexpr int kDotThreads = 256;
@@ -184,10 +179,9 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
     const int ncol = n_rhs * n_lambda;
     const int64_t N = (int64_t)op->n_nodes * op->time.n_hats;
     const int64_t M = (int64_t)seg.total * op->time.n_frames;
-    s = ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * (ncol < 32 ? ncol : 32) * 8);
+    s = ensure_adjoint_scratch(op, ncol, 8);  // the larger of the FP32 and FP64 needs
+    if (s == RTT_OK) s = ensure_adjoint_scratch(op, ncol, 4);
     if (s != RTT_OK) return s;
-    float* zf = (float*)op->zhat;
-    double* zd = (double*)op->zhat;
     DevBuf buf;
     float *b1, *r, *p, *Ap, *y;
     double *lam, *partial, *dots, *coef, *x64, *y64, *g64, *b64, *r64, *b1_64;
@@ -209,7 +203,7 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
     // right-hand side A^T d in FP64 (exact transpose of the FP64 forward)
     convert<float, double><<<nb(M * n_rhs), 256, 0, st>>>(data, y64, M * n_rhs);
     SOLVE_CUDA(cudaGetLastError());
-    SOLVE_CUDA(launch_adjoint<double>(op, y64, b1_64, n_rhs, seg, zd, st));
+    SOLVE_CUDA(launch_adjoint<double>(op, y64, b1_64, n_rhs, seg, st));
     replicate_cols<double><<<nb(N * ncol), 256, 0, st>>>(b1_64, N, n_rhs, n_lambda, b64);
     SOLVE_CUDA(cudaGetLastError());
     SOLVE_CUDA(coldots(b64, b64, N, ncol, partial, dots, st));
@@ -237,7 +231,7 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
         ++it;
         // Ap = A^T A p + lambda p
         SOLVE_CUDA(launch_forward<float>(op, p, y, ncol, seg, st));
-        SOLVE_CUDA(launch_adjoint<float>(op, y, Ap, ncol, seg, zf, st));
+        SOLVE_CUDA(launch_adjoint<float>(op, y, Ap, ncol, seg, st));
         add_shift<<<nb(N * ncol), 256, 0, st>>>(Ap, p, lam, N, ncol);
         SOLVE_CUDA(cudaGetLastError());
         SOLVE_CUDA(coldots(p, Ap, N, ncol, partial, dots, st));
@@ -252,7 +246,7 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
             convert<float, double><<<nb(N * ncol), 256, 0, st>>>(x, x64, N * ncol);
             SOLVE_CUDA(cudaGetLastError());
             SOLVE_CUDA(launch_forward<double>(op, x64, y64, ncol, seg, st));
-            SOLVE_CUDA(launch_adjoint<double>(op, y64, g64, ncol, seg, zd, st));
+            SOLVE_CUDA(launch_adjoint<double>(op, y64, g64, ncol, seg, st));
             refresh_residual<<<nb(N * ncol), 256, 0, st>>>(b64, g64, x64, lam, N, ncol, r64, r);
             SOLVE_CUDA(cudaGetLastError());
         }
@@ -276,7 +270,7 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
     convert<float, double><<<nb(N * ncol), 256, 0, st>>>(x, x64, N * ncol);
     SOLVE_CUDA(cudaGetLastError());
     SOLVE_CUDA(launch_forward<double>(op, x64, y64, ncol, seg, st));
-    SOLVE_CUDA(launch_adjoint<double>(op, y64, g64, ncol, seg, zd, st));
+    SOLVE_CUDA(launch_adjoint<double>(op, y64, g64, ncol, seg, st));
     refresh_residual<<<nb(N * ncol), 256, 0, st>>>(b64, g64, x64, lam, N, ncol, r64, r);
     SOLVE_CUDA(cudaGetLastError());
     SOLVE_CUDA(coldots(r64, r64, N, ncol, partial, dots, st));
@@ -314,7 +308,7 @@ extern "C" rtt_status rtt_solve_tsvd(rtt_op op, int arm_mask, const double* Q, i
     if (s != RTT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t N = (int64_t)op->n_nodes * op->time.n_hats;
-    s = ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * (n_rhs < 32 ? n_rhs : 32) * 8);
+    s = ensure_adjoint_scratch(op, n_rhs, 8);
     if (s != RTT_OK) return s;
     DevBuf buf;
     double *g, *c, *Mx, *coefm, *lam;
@@ -324,7 +318,7 @@ extern "C" rtt_status rtt_solve_tsvd(rtt_op op, int arm_mask, const double* Q, i
         return RTT_ENOMEM;
     }
     SOLVE_CUDA(cudaMemcpyAsync(lam, evals_host, d * 8, cudaMemcpyHostToDevice, st));
-    SOLVE_CUDA(launch_adjoint<double>(op, data, g, n_rhs, seg, (double*)op->zhat, st));
+    SOLVE_CUDA(launch_adjoint<double>(op, data, g, n_rhs, seg, st));
     tsvd_kernel_matrix<<<nb((int64_t)d * d), 256, 0, st>>>(V, lam, d, rank, Mx);
     SOLVE_CUDA(cudaGetLastError());
     cublasHandle_t h;

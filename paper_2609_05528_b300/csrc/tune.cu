@@ -1,10 +1,10 @@
 // Autotuner for the FP32 applies: for one operator and batch size, times
 // every kernel variant of the forward (staged or lane-per-hat, batch entries
-// and frames per task) and of the two adjoint phases (general, periodic or
-// periodic TMA-staged time contraction; scalar or 16-byte gather) with CUDA events on the caller's
-// stream, and records the fastest in the operator.  All variants produce the
-// same bits (same per-output summation order and fused multiply-adds), so
-// tuning changes speed only.
+// and frames per task) and of the adjoint (frames staged by per-lane copies
+// or by TMA tensor copies, 32- or 64-hat items) with CUDA events on the
+// caller's stream, and records the fastest in the operator.  All variants
+// produce the same bits (same per-output summation order and fused
+// multiply-adds), so tuning changes speed only.
 #include <cuda_runtime.h>
 
 #include <vector>
@@ -14,14 +14,7 @@
 using namespace rtt;
 
 namespace rtt {
-template <typename T>
-cudaError_t launch_forward(const rtt_op_s*, const T*, T*, int, const ArmSeg&, cudaStream_t);
-template <typename T>
-cudaError_t launch_adjoint(const rtt_op_s*, const T*, T*, int, const ArmSeg&, T*, cudaStream_t);
-rtt_status ensure_zhat_bytes(rtt_op_s* op, size_t bytes);
-cudaError_t launch_forward_adjoint_fused(const rtt_op_s* op, const float* x, const float* d,
-                                         float* y, float* g, int B, const ArmSeg& seg,
-                                         float* zhat, cudaStream_t st);
+int adjoint_best_kind(const rtt_op_s* op, int batch);
 }  // namespace rtt
 
 namespace {
@@ -77,19 +70,16 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
     }
     const int bc = v->fwd_bc;
     if (v->fwd_kernel < 1 || v->fwd_kernel > 5 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
-        v->fwd_half < 0 || v->fwd_half > 1 || v->time_kernel < 1 || v->time_kernel > 4 ||
-        v->space_kernel < 1 || v->space_kernel > 3) {
-        set_error("invalid variant (fwd %d bc %d half %d time %d space %d)", v->fwd_kernel, bc,
-                  v->fwd_half, v->time_kernel, v->space_kernel);
+        v->fwd_half < 0 || v->fwd_half > 1 || v->adj_kernel < 1 || v->adj_kernel > 3) {
+        set_error("invalid variant (fwd %d bc %d half %d adj %d)", v->fwd_kernel, bc, v->fwd_half,
+                  v->adj_kernel);
         return RTT_EINVAL;
     }
     ApplyVariant a;
     a.fwd = (int8_t)v->fwd_kernel;
     a.fwd_bc = (int8_t)bc;
     a.fwd_half = (int8_t)v->fwd_half;
-    a.time = (int8_t)v->time_kernel;
-    a.space = (int8_t)v->space_kernel;
-    a.fused = (int8_t)(v->fused_step != 0);
+    a.adj = (int8_t)v->adj_kernel;
     if (v->fwd_staging < 0 || v->fwd_staging > 3) {
         set_error("invalid forward staging depth %d", v->fwd_staging);
         return RTT_EINVAL;
@@ -108,9 +98,7 @@ extern "C" rtt_status rtt_get_variant(rtt_op op, int batch, rtt_variant* out) {
     out->fwd_kernel = a.fwd;
     out->fwd_bc = a.fwd_bc;
     out->fwd_half = a.fwd_half;
-    out->time_kernel = a.time;
-    out->space_kernel = a.space;
-    out->fused_step = a.fused;
+    out->adj_kernel = a.adj;
     out->fwd_staging = a.fwd_su;
     return RTT_OK;
 }
@@ -129,7 +117,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     const int B = batch;
     const size_t nx = (size_t)op->n_nodes * op->time.n_hats * B;
     const size_t ny = (size_t)(seg.total > 0 ? seg.total : 1) * op->time.n_frames * B;
-    s = ensure_zhat_bytes(op, (size_t)op->n_rays * op->time.n_hats * (B < 32 ? B : 32) * 4);
+    s = ensure_adjoint_scratch(op, B, 4);
     if (s != RTT_OK) return s;
     float *x = nullptr, *y = nullptr;
     if (cudaMalloc(&x, nx * 4) != cudaSuccess || cudaMalloc(&y, ny * 4) != cudaSuccess) {
@@ -159,12 +147,12 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
         set_variant(op, B, v);
         ++n_cand;
         for (int w = 0; w < 1 && e == cudaSuccess; ++w)
-            e = adjoint ? launch_adjoint<float>(op, y, x, B, seg, (float*)op->zhat, st)
+            e = adjoint ? launch_adjoint<float>(op, y, x, B, seg, st)
                         : launch_forward<float>(op, x, y, B, seg, st);
         if (e != cudaSuccess) return 1e30f;
         cudaEventRecord(tm.a, st);
         for (int r = 0; r < kTuneReps && e == cudaSuccess; ++r)
-            e = adjoint ? launch_adjoint<float>(op, y, x, B, seg, (float*)op->zhat, st)
+            e = adjoint ? launch_adjoint<float>(op, y, x, B, seg, st)
                         : launch_forward<float>(op, x, y, B, seg, st);
         cudaEventRecord(tm.b, st);
         if (e != cudaSuccess) return 1e30f;
@@ -208,58 +196,17 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                     }
                 }
             }
-    // adjoint: phase-1 x phase-2 variants (timed as the full adjoint)
+    // adjoint: the per-lane staged kernel and the TMA kernels the call allows
     const float adj_rule = time_it(rule, true);
     float adj_best = adj_rule;
-    // the TMA-staged time phase needs the whole batch in one chunk of 16-byte
-    // multiples with whole frames per 128-byte row, and 2 or 4 frames per hat
-    const int P = periodic ? (int)(kFracOne / op->frame_D) : 0;
-    const bool tma_ok = (P == 2 || P == 4) && (B == 4 || B == 8 || B == 16 || B == 32) &&
-                        (op->time.n_frames % (32 / B)) == 0;
-    // the whole-item TMA phase also needs the frames of a 128-byte row to divide P
-    const bool tma6_ok = P > 0 && (B == 4 || B == 8 || B == 16 || B == 32) && P % (32 / B) == 0 &&
-                         (op->time.n_frames % (32 / B)) == 0 && !(B == 32 && P == 8);
-    const int tk_max = !periodic ? 1 : (tma6_ok ? 4 : (tma_ok ? 3 : 2));
-    for (int tk = 1; tk <= tk_max; ++tk)
-        for (int sk = 1; sk <= 3; ++sk) {
-            ApplyVariant v = best;
-            v.time = (int8_t)tk;
-            v.space = (int8_t)sk;
-            const float ms = time_it(v, true);
-            if (ms < adj_best) {
-                adj_best = ms;
-                best.time = v.time;
-                best.space = v.space;
-            }
-        }
-    // rtt_apply_A_AT: the fused forward + time phase against the chosen
-    // separate pair (needs a second x-sized buffer for the gradient)
-    float fused_ms = 0.f;
-    best.fused = 0;
-    if (e == cudaSuccess) {
-        float* g = nullptr;
-        if (cudaMalloc(&g, nx * 4) == cudaSuccess) {
-            set_variant(op, B, best);
-            cudaError_t f = launch_forward_adjoint_fused(op, x, nullptr, y, g, B, seg,
-                                                         (float*)op->zhat, st);
-            if (f == cudaSuccess) {
-                ++n_cand;
-                cudaEventRecord(tm.a, st);
-                for (int r = 0; r < kTuneReps && f == cudaSuccess; ++r)
-                    f = launch_forward_adjoint_fused(op, x, nullptr, y, g, B, seg,
-                                                     (float*)op->zhat, st);
-                cudaEventRecord(tm.b, st);
-                if (f == cudaSuccess && cudaEventSynchronize(tm.b) == cudaSuccess) {
-                    cudaEventElapsedTime(&fused_ms, tm.a, tm.b);
-                    fused_ms /= kTuneReps;
-                    if (fused_ms < fwd_best + adj_best) best.fused = 1;
-                } else if (f != cudaErrorNotSupported) {
-                    e = f;
-                }
-            } else if (f != cudaErrorNotSupported) {
-                e = f;
-            }
-            cudaFree(g);
+    const int adj_max = adjoint_best_kind(op, B);
+    for (int k = 1; k <= adj_max; ++k) {
+        ApplyVariant v = best;
+        v.adj = (int8_t)k;
+        const float ms = time_it(v, true);
+        if (ms < adj_best) {
+            adj_best = ms;
+            best.adj = v.adj;
         }
     }
     cudaFree(x);
@@ -277,14 +224,11 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     out->fwd_frames_per_lane =
         best.fwd == 2 ? (int32_t)(kFracOne / op->frame_D)
                       : (best.fwd_bc >= 32 ? 1 : (32 / best.fwd_bc) / (best.fwd_half ? 2 : 1));
-    out->time_kernel = best.time;
-    out->space_kernel = best.space;
+    out->adj_kernel = best.adj;
     out->fwd_ms = fwd_best;
     out->adj_ms = adj_best;
     out->fwd_ms_rule = fwd_rule;
     out->adj_ms_rule = adj_rule;
     out->candidates = n_cand;
-    out->fused_step = best.fused;
-    out->fused_ms = fused_ms;
     return RTT_OK;
 }

@@ -89,18 +89,15 @@ class Screen(ctypes.Structure):
 class TuneResult(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int32), ("fwd_kernel", ctypes.c_int32),
                 ("fwd_bc", ctypes.c_int32), ("fwd_frames_per_lane", ctypes.c_int32),
-                ("fwd_staging", ctypes.c_int32),
-                ("time_kernel", ctypes.c_int32),
-                ("space_kernel", ctypes.c_int32), ("fwd_ms", ctypes.c_float),
-                ("adj_ms", ctypes.c_float), ("fwd_ms_rule", ctypes.c_float),
-                ("adj_ms_rule", ctypes.c_float), ("candidates", ctypes.c_int32),
-                ("fused_step", ctypes.c_int32), ("fused_ms", ctypes.c_float)]
+                ("fwd_staging", ctypes.c_int32), ("adj_kernel", ctypes.c_int32),
+                ("fwd_ms", ctypes.c_float), ("adj_ms", ctypes.c_float),
+                ("fwd_ms_rule", ctypes.c_float), ("adj_ms_rule", ctypes.c_float),
+                ("candidates", ctypes.c_int32)]
 
 
 class Variant(ctypes.Structure):
     _fields_ = [("fwd_kernel", ctypes.c_int32), ("fwd_bc", ctypes.c_int32),
-                ("fwd_half", ctypes.c_int32), ("time_kernel", ctypes.c_int32),
-                ("space_kernel", ctypes.c_int32), ("fused_step", ctypes.c_int32),
+                ("fwd_half", ctypes.c_int32), ("adj_kernel", ctypes.c_int32),
                 ("fwd_staging", ctypes.c_int32)]
 
 
@@ -320,14 +317,13 @@ class Operator:
                                  ctypes.byref(r)), "rtt_autotune")
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
-    def set_variant(self, batch: int, fwd_kernel=None, fwd_bc=None, fwd_half=0, time_kernel=None,
-                    space_kernel=None, fused_step=0, fwd_staging=0):
+    def set_variant(self, batch: int, fwd_kernel=None, fwd_bc=None, fwd_half=0, adj_kernel=None,
+                    fwd_staging=0):
         """rtt_set_variant; all None resets `batch` to the default rule."""
-        if fwd_kernel is None and fwd_bc is None and time_kernel is None and space_kernel is None:
+        if fwd_kernel is None and fwd_bc is None and adj_kernel is None:
             check(lib().rtt_set_variant(self.handle, int(batch), None), "rtt_set_variant")
             return
-        v = Variant(int(fwd_kernel), int(fwd_bc), int(fwd_half), int(time_kernel), int(space_kernel),
-                    int(fused_step), int(fwd_staging))
+        v = Variant(int(fwd_kernel), int(fwd_bc), int(fwd_half), int(adj_kernel), int(fwd_staging))
         check(lib().rtt_set_variant(self.handle, int(batch), ctypes.byref(v)), "rtt_set_variant")
 
     def get_variant(self, batch: int) -> dict:

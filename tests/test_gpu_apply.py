@@ -175,10 +175,9 @@ def test_autotune_keeps_bits(B):
     g0 = c.op.apply_AT(y0)
     r = c.op.autotune(B)
     assert r["batch"] == B and r["candidates"] >= 4
-    assert r["fwd_kernel"] in (1, 2, 3, 4, 5) and r["time_kernel"] in (1, 2, 3, 4)
-    assert r["space_kernel"] in (1, 2, 3)
+    assert r["fwd_kernel"] in (1, 2, 3, 4, 5) and r["adj_kernel"] in (1, 2, 3)
     if B % 4:
-        assert r["time_kernel"] < 3  # the TMA phases need 16-byte frame records
+        assert r["adj_kernel"] == 1  # the TMA adjoint needs 16-byte frame records
     assert 0 < r["fwd_ms"] <= r["fwd_ms_rule"] and 0 < r["adj_ms"] <= r["adj_ms_rule"]
     y1 = c.op.apply_A(x)
     g1 = c.op.apply_AT(y0)
@@ -210,23 +209,22 @@ def test_every_variant_same_bits(which, small, schw, B):
         for bc in sorted({bc_max, max(1, bc_max // 2), max(1, bc_max // 4)}):
             for half in (0, 1):
                 for su in ((1, 2, 3) if (fk == 1 and half == 0 and bc in (4, 8)) else (2,)):
-                    c.op.set_variant(B, fk, bc, half, 2, 2, fwd_staging=su)
+                    c.op.set_variant(B, fk, bc, half, 1, fwd_staging=su)
                     assert torch.equal(c.op.apply_A(x), y0), (fk, bc, half, su)
                     n += 1
-    for tk in (1, 2, 3, 4):
-        for sk in (1, 2, 3):
-            c.op.set_variant(B, 1, bc_max, 0, tk, sk)
-            assert torch.equal(c.op.apply_AT(y0), g0), (tk, sk)
-            n += 1
-    # direct arm only: rays of the other orders get zero rows in every time phase
+    for ak in (1, 2, 3):
+        c.op.set_variant(B, 1, bc_max, 0, ak)
+        assert torch.equal(c.op.apply_AT(y0), g0), ak
+        n += 1
+    # direct arm only: rays of the other orders are skipped by every adjoint kernel
     c.op.set_variant(B)
     y1 = c.op.apply_A(x, arm_mask=1)
     g1 = c.op.apply_AT(y1, arm_mask=1)
-    for tk in (1, 2, 3, 4):
-        c.op.set_variant(B, 1, bc_max, 0, tk, 3)
-        assert torch.equal(c.op.apply_AT(y1, arm_mask=1), g1), tk
+    for ak in (1, 2, 3):
+        c.op.set_variant(B, 1, bc_max, 0, ak)
+        assert torch.equal(c.op.apply_AT(y1, arm_mask=1), g1), ak
     for fk in (1, 3, 4, 5):
-        c.op.set_variant(B, fk, bc_max, 0, 2, 2)
+        c.op.set_variant(B, fk, bc_max, 0, 1)
         assert torch.equal(c.op.apply_A(x, arm_mask=1), y1), fk
     c.op.set_variant(B)
     assert c.op.status(clear=True) == 0
@@ -238,8 +236,8 @@ def test_every_variant_same_bits(which, small, schw, B):
 @pytest.mark.parametrize("mask", [7, 1])
 @pytest.mark.parametrize("with_d", [False, True])
 def test_apply_A_AT(which, small, schw, B, mask, with_d):
-    """rtt_apply_A_AT (fused for batch 4 and 8) gives the bits of rtt_apply_A
-    followed by rtt_apply_AT on y - d, and matches the oracle."""
+    """rtt_apply_A_AT gives the bits of rtt_apply_A followed by rtt_apply_AT
+    on y - d, with every adjoint kernel, and matches the oracle."""
     c = small if which == "small" else schw
     x = torch.from_numpy(I.uniform_batch(c.w, range(B)).astype(np.float32)).cuda()
     y_ref = c.op.apply_A(x, arm_mask=mask)
@@ -252,11 +250,11 @@ def test_apply_A_AT(which, small, schw, B, mask, with_d):
     bc = 1
     while bc < B:
         bc *= 2
-    for fused in (0, 1):  # separate pair, then the fused kernel (where B allows it)
-        c.op.set_variant(B, 1, bc, 0, 2, 2, fused_step=fused)
+    for ak in (1, 2, 3):
+        c.op.set_variant(B, 1, bc, 0, ak)
         y, g = c.op.apply_A_AT(x, d, arm_mask=mask)
-        assert torch.equal(y, y_ref), fused
-        assert torch.equal(g, g_ref), fused
+        assert torch.equal(y, y_ref), ak
+        assert torch.equal(g, g_ref), ak
     c.op.set_variant(B)
     sub = c.tab.select(_arm_orders(mask))
     _cmp(g.cpu().numpy().astype(np.float64),
