@@ -671,6 +671,7 @@ typedef struct {
     float fwd_ms, adj_ms;           /* chosen variants, ms per apply */
     float fwd_ms_rule, adj_ms_rule; /* the untuned default rule, ms per apply */
     int32_t candidates;             /* configurations timed */
+    int32_t fwd_order;    /* forward task rows: 0 (order, pixel), 1 source-cell order */
 } rtt_tune_result;
 
 rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream, rtt_tune_result* out);
@@ -695,6 +696,10 @@ typedef struct {
                              the next one down runs) */
     int32_t fwd_staging;  /* staged forward: x items in flight per lane, 1, 2 or 3
                              (0 = 2; other values than 2 only at 4 or 8 entries) */
+    int32_t fwd_order;    /* forward task rows: 0 in (order, pixel) order, 1 in source-cell
+                             order (within each order, by the Morton index of the row's
+                             first ray's cell: rows that read the same x nodes run
+                             close together) */
 } rtt_variant;
 
 /*

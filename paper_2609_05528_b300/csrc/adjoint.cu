@@ -47,8 +47,8 @@ struct CellArgs {
     // rays in cell order (cell = the stencil's (i0, j0) node, then ray index)
     const int32_t* c_row;    // input data row
     const int32_t* c_col;    // column j0 of the cell
-    const int32_t* c_K0;     // hat base
-    const int32_t* c_F0;     // 24-bit hat fraction
+    const int32_t* c_h0;     // general kernel: hat base K0; TMA kernel: fbase (below)
+    const int32_t* c_h1;     // general kernel: 24-bit fraction F0; TMA kernel: phase r0
     const float4* c_W;       // corner weights (whitening scale included)
     const double* c_W64;     // [4 per ray] the same in FP64
     const double* c_F64;     // exact hat fraction
@@ -82,7 +82,8 @@ struct Step {
     int pos;         // ray: position in the cell order
     int row_out;     // ray: output row
     int col;         // ray: column relative to the segment's first column
-    int K0, F0;      // ray: hat coordinate
+    int h0, h1;      // ray: hat coordinate (general kernel: K0, F0; TMA kernel: first
+                     // frame of the ray's hat-0 taps and its weight phase r0)
     int rec0, ncol;  // item: first record, columns
     int g, bc;       // item: hat group and batch chunk
 };
@@ -132,8 +133,8 @@ __device__ __forceinline__ Step walk_next(const CellArgs& a, Walk& w, int lane) 
         s.pos = p;
         s.row_out = row_out;
         s.col = a.c_col[p] - w.col0;
-        s.K0 = a.c_K0[p];
-        s.F0 = a.c_F0[p];
+        s.h0 = a.c_h0[p];
+        s.h1 = a.c_h1[p];
         return s;
     }
     w.open = false;
@@ -141,8 +142,11 @@ __device__ __forceinline__ Step walk_next(const CellArgs& a, Walk& w, int lane) 
     return s;
 }
 
-// Register accumulators of an item: lower / upper node rows of the current
-// column (c) and of the next column (n), NH hats x BC columns per lane.
+// Register accumulators of an item: lower / upper node-row sums of the
+// current column (lc, uc) and of the next column (ln, un), NH hats x BC
+// columns per lane.  A ray adds its corners (i,j), (i+1,j) to the current
+// column and (i,j+1), (i+1,j+1) to the next; passing a column writes the
+// current sums and moves the next column's into their place.
 template <typename T, int NH, int BC>
 struct ColAcc {
     T lc[NH][BC], uc[NH][BC], ln[NH][BC], un[NH][BC];
@@ -163,7 +167,6 @@ struct ColAcc {
                 un[h][b] = T(0);
             }
     }
-    // the ray's corner contributions, corners (i,j), (i+1,j), (i,j+1), (i+1,j+1)
     __device__ __forceinline__ void add(const T (&z)[NH][BC], T w0, T w1, T w2, T w3) {
 #pragma unroll
         for (int h = 0; h < NH; ++h)
@@ -212,10 +215,11 @@ struct EmitAt {
     bool vec;
 };
 
-// write the current column's two records (hats k_h = kbase + lane + 32 h)
+// write one slot's two records (hats k_h = kbase + lane + 32 h)
 template <typename T, int NH, int BC>
-__device__ __forceinline__ void emit(const CellArgs& a, const ColAcc<T, NH, BC>& A, int rec,
-                                     const EmitAt& at, int lane) {
+__device__ __forceinline__ void emit_slot(const CellArgs& a, const T (&lo)[NH][BC],
+                                          const T (&up)[NH][BC], int rec, const EmitAt& at,
+                                          int lane) {
     if (lane >= at.nlanes) return;
     T* part = reinterpret_cast<T*>(a.part);
 #pragma unroll
@@ -225,7 +229,7 @@ __device__ __forceinline__ void emit(const CellArgs& a, const ColAcc<T, NH, BC>&
 #pragma unroll
         for (int half = 0; half < 2; ++half) {
             T* o = part + ((int64_t)(rec + half) * a.K + k) * a.Bp + at.boff;
-            const T(&v)[BC] = half ? A.uc[h] : A.lc[h];
+            const T(&v)[BC] = half ? up[h] : lo[h];
             if constexpr (sizeof(T) == 4 && BC % 4 == 0) {
                 if (at.vec) {
 #pragma unroll
@@ -250,15 +254,20 @@ __device__ __forceinline__ void emit(const CellArgs& a, const ColAcc<T, NH, BC>&
     }
 }
 
+// pass the current column: write its records, move the next column's sums in
+template <typename T, int NH, int BC>
+__device__ __forceinline__ void next_column(const CellArgs& a, ColAcc<T, NH, BC>& A, int rec,
+                                            const EmitAt& at, int lane) {
+    emit_slot(a, A.lc, A.uc, rec, at, lane);
+    A.shift();
+}
+
 // close an item: write every column not yet written and the successor column
 template <typename T, int NH, int BC>
 __device__ __forceinline__ void finish_item(const CellArgs& a, ColAcc<T, NH, BC>& A, int& jc,
                                             const Step& s, const EmitAt& at, int lane) {
-    for (; jc < s.ncol; ++jc) {
-        emit(a, A, s.rec0 + 2 * jc, at, lane);
-        A.shift();
-    }
-    emit(a, A, s.rec0 + 2 * s.ncol, at, lane);
+    for (; jc < s.ncol; ++jc) next_column(a, A, s.rec0 + 2 * jc, at, lane);
+    emit_slot(a, A.lc, A.uc, s.rec0 + 2 * s.ncol, at, lane);
     A.zero_all();
     jc = 0;
 }
@@ -346,7 +355,7 @@ __device__ __forceinline__ void cell_contract_any(int M, const unsigned char* bu
 }
 
 template <int BC, int P, int HG>
-__global__ void __launch_bounds__(kCellWarps * 32)
+__global__ void __launch_bounds__(kCellWarps * 32, 3)
 adj_cell_tma_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) {
     static_assert(BC == 4 || BC == 8 || BC == 16, "128-byte lines of whole frames");
     wait_prior_grid();
@@ -378,10 +387,8 @@ adj_cell_tma_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) 
         float4 w;
     };
     auto derive = [&](const Step& s, Cp& c) {
-        const int64_t U0 = (int64_t)s.K0 * kFracOne + (int64_t)s.F0;
-        const int64_t c0 = (U0 * P) >> kFracBits;
-        const int fbase = (int)(c0 + 1 - P);
-        c.r0 = (int32_t)(U0 - (c0 + 1) * (int64_t)D32) + kFracOne;
+        const int fbase = s.h0;  // first frame of hat 0's taps
+        c.r0 = s.h1;             // weight phase: tap j of every hat weighs 1 - |r0 - j D| 2^-24
         const int kg0 = HATS * s.g;
         const int f_lo = fbase - P * (kg0 + HATS - 1);  // first frame of the item's last hat
         c.R4 = f_lo >> LGF;                              // floor division (f_lo may be < 0)
@@ -439,10 +446,7 @@ adj_cell_tma_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) 
             cell_contract_any<BC, P, HG>(s0f & (F - 1), bufp0 + b * BUF_STRIDE, s0f >> LGF, wt, z);
             __syncwarp();  // buffer b is free for the next copy issued into it
             ++n_done;
-            for (; jc < s0.col; ++jc) {
-                emit(a, A, s0.rec0 + 2 * jc, at, lane);
-                A.shift();
-            }
+            for (; jc < s0.col; ++jc) next_column(a, A, s0.rec0 + 2 * jc, at, lane);
             acc_add2(A, z, c0.w);
         } else {
             finish_item(a, A, jc, s0, at, lane);
@@ -501,7 +505,7 @@ adj_cell_gen_kernel(const CellArgs a, uint32_t buf_bytes, int vec_stage) {
         T w[4];
     };
     auto derive = [&](const Step& s, Cp& c) {
-        c.U0 = (int64_t)s.K0 * kFracOne + (int64_t)s.F0;
+        c.U0 = (int64_t)s.h0 * kFracOne + (int64_t)s.h1;
         const int kg0 = a.hw * s.g;
         // frames with (kg0 - 1) 2^24 <= U(f) < (kg0 + hw) 2^24
         int64_t fa = floor_div(c.U0 - (int64_t)(kg0 + a.hw) * kFracOne, D) + 1;
@@ -602,10 +606,7 @@ adj_cell_gen_kernel(const CellArgs a, uint32_t buf_bytes, int vec_stage) {
             }
             __syncwarp();  // buffer free for the copy issued into it next
             ++n_done;
-            for (; jc < s0.col; ++jc) {
-                emit(a, A, s0.rec0 + 2 * jc, at, lane);
-                A.shift();
-            }
+            for (; jc < s0.col; ++jc) next_column(a, A, s0.rec0 + 2 * jc, at, lane);
             A.add(z, c0.w[0], c0.w[1], c0.w[2], c0.w[3]);
         } else {
             finish_item(a, A, jc, s0, at, lane);
@@ -720,10 +721,17 @@ rtt_status ensure_adjoint_scratch(rtt_op_s* op, int batch, int elem) {
 }
 
 // ray tables in cell order
-__global__ void cell_tables(int64_t E, int n_phi, const int32_t* cray, const int32_t* ray_row,
-                            const int32_t* node00, const int32_t* K0, const int32_t* F0,
-                            const float4* W, const double* W64, const double* F64, int32_t* c_row,
-                            int32_t* c_col, int32_t* c_K0, int32_t* c_F0, float4* c_W, double* c_W64,
+// ray tables in cell order; with a periodic cadence (P frames per hat step,
+// D = 2^24 / P) also each ray's first tap frame of hat 0, c0 + 1 - P with
+// c0 = floor(U0 / D), and its weight phase r0 = U0 - (c0 + 1) D + 2^24 in
+// [2^24 - D, 2^24): hat k's taps are the frames fbase - P k + j, j < 2P, with
+// weights 1 - |r0 - j D| 2^-24 (U0 = K0 2^24 + F0, the fixed-point hat
+// coordinate of frame 0)
+__global__ void cell_tables(int64_t E, int n_phi, int P, int64_t D, const int32_t* cray,
+                            const int32_t* ray_row, const int32_t* node00, const int32_t* K0,
+                            const int32_t* F0, const float4* W, const double* W64, const double* F64,
+                            int32_t* c_row, int32_t* c_col, int32_t* c_K0, int32_t* c_F0,
+                            int32_t* c_fb, int32_t* c_r0, float4* c_W, double* c_W64,
                             double* c_F64) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= E) return;
@@ -732,6 +740,12 @@ __global__ void cell_tables(int64_t E, int n_phi, const int32_t* cray, const int
     c_col[p] = node00[e] % n_phi;
     c_K0[p] = K0[e];
     c_F0[p] = F0[e];
+    if (P > 0) {
+        const int64_t U0 = (int64_t)K0[e] * kFracOne + (int64_t)F0[e];
+        const int64_t c0 = floor_div(U0, D);
+        c_fb[p] = (int32_t)(c0 + 1 - P);
+        c_r0[p] = (int32_t)(U0 - (c0 + 1) * D) + kFracOne;
+    }
     c_W[p] = W[e];
     for (int c = 0; c < 4; ++c) c_W64[4 * p + c] = W64[4 * (int64_t)e + c];
     c_F64[p] = F64[e];
@@ -787,13 +801,16 @@ rtt_status build_cells(rtt_op_s* op, cudaStream_t st) {
     dev(&op->c_col, E);
     dev(&op->c_K0, E);
     dev(&op->c_F0, E);
+    dev(&op->c_fb, E);
+    dev(&op->c_r0, E);
     dev(&op->c_W, E);
     dev(&op->c_W64, 4 * E);
     dev(&op->c_F64, E);
     if (e2 != cudaSuccess) return fail("allocation of the cell-ordered tables");
     cell_tables<<<(unsigned)((E + 255) / 256), 256, 0, st>>>(
-        E, n_phi, cray, op->ray_row, op->node00, op->K0, op->F0, op->W, op->W64, op->F64, op->c_row,
-        op->c_col, op->c_K0, op->c_F0, op->c_W, op->c_W64, op->c_F64);
+        E, n_phi, frames_per_hat(op->frame_D), op->frame_D, cray, op->ray_row, op->node00, op->K0,
+        op->F0, op->W, op->W64, op->F64, op->c_row, op->c_col, op->c_K0, op->c_F0, op->c_fb,
+        op->c_r0, op->c_W, op->c_W64, op->c_F64);
     if (cudaGetLastError() != cudaSuccess) return fail("table kernel");
     std::vector<int32_t> cell(E);
     if (cudaMemcpyAsync(cell.data(), keys_out, E * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -879,8 +896,8 @@ static CellArgs cell_args(const rtt_op_s* op, const void* y, int B, const ArmSeg
     CellArgs a{};
     a.c_row = op->c_row;
     a.c_col = op->c_col;
-    a.c_K0 = op->c_K0;
-    a.c_F0 = op->c_F0;
+    a.c_h0 = op->c_K0;
+    a.c_h1 = op->c_F0;
     a.c_W = op->c_W;
     a.c_W64 = op->c_W64;
     a.c_F64 = op->c_F64;
@@ -912,7 +929,8 @@ static bool tma_shape(const rtt_op_s* op, int B, int P, int* hg) {
 }
 
 template <int BC, int P, int HG>
-static cudaError_t launch_cell_tma(CellArgs a, const float* y, cudaStream_t st) {
+static cudaError_t launch_cell_tma(CellArgs a, const float* y, const int32_t* op_fb,
+                                   const int32_t* op_r0, cudaStream_t st) {
     constexpr int F = CellBox<BC, P, HG>::kF;
     constexpr int ROWS = CellBox<BC, P, HG>::kRows;
     static_assert(ROWS <= 256, "TMA box rows");
@@ -932,6 +950,8 @@ static cudaError_t launch_cell_tma(CellArgs a, const float* y, cudaStream_t st) 
     a.n_hg = (a.K + 32 * HG - 1) / (32 * HG);
     a.n_bc = 1;
     a.hw = 32 * HG;
+    a.c_h0 = op_fb;  // the periodic tap tables (cell_tables)
+    a.c_h1 = op_r0;
     a.n_items = (int64_t)a.n_hg * a.n_items;  // n_items holds the segment count on entry
     const size_t smem = 1024 + (size_t)kCellWarps * 2 * CellBox<BC, P, HG>::kStride + kCellWarps * 16;
     cudaError_t e = cudaFuncSetAttribute(adj_cell_tma_kernel<BC, P, HG>,
@@ -943,14 +963,18 @@ static cudaError_t launch_cell_tma(CellArgs a, const float* y, cudaStream_t st) 
                             m, a);
 }
 
-static cudaError_t dispatch_tma(const CellArgs& a, const float* y, int B, int P, int hg,
-                                cudaStream_t st) {
-    if (B == 4 && P == 8) return hg == 2 ? launch_cell_tma<4, 8, 2>(a, y, st) : launch_cell_tma<4, 8, 1>(a, y, st);
-    if (B == 8 && P == 4) return hg == 2 ? launch_cell_tma<8, 4, 2>(a, y, st) : launch_cell_tma<8, 4, 1>(a, y, st);
-    if (B == 8 && P == 8) return hg == 2 ? launch_cell_tma<8, 8, 2>(a, y, st) : launch_cell_tma<8, 8, 1>(a, y, st);
-    if (B == 16 && P == 2) return launch_cell_tma<16, 2, 1>(a, y, st);
-    if (B == 16 && P == 4) return launch_cell_tma<16, 4, 1>(a, y, st);
-    if (B == 16 && P == 8) return launch_cell_tma<16, 8, 1>(a, y, st);
+static cudaError_t dispatch_tma(const rtt_op_s* op, const CellArgs& a, const float* y, int B, int P,
+                                int hg, cudaStream_t st) {
+    const int32_t *fb = op->c_fb, *r0 = op->c_r0;
+    if (B == 4 && P == 8)
+        return hg == 2 ? launch_cell_tma<4, 8, 2>(a, y, fb, r0, st) : launch_cell_tma<4, 8, 1>(a, y, fb, r0, st);
+    if (B == 8 && P == 4)
+        return hg == 2 ? launch_cell_tma<8, 4, 2>(a, y, fb, r0, st) : launch_cell_tma<8, 4, 1>(a, y, fb, r0, st);
+    if (B == 8 && P == 8)
+        return hg == 2 ? launch_cell_tma<8, 8, 2>(a, y, fb, r0, st) : launch_cell_tma<8, 8, 1>(a, y, fb, r0, st);
+    if (B == 16 && P == 2) return launch_cell_tma<16, 2, 1>(a, y, fb, r0, st);
+    if (B == 16 && P == 4) return launch_cell_tma<16, 4, 1>(a, y, fb, r0, st);
+    if (B == 16 && P == 8) return launch_cell_tma<16, 8, 1>(a, y, fb, r0, st);
     return cudaErrorNotSupported;
 }
 
@@ -1059,7 +1083,8 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         cudaError_t e = cudaErrorNotSupported;
         if constexpr (sizeof(T) == 4) {
             if (kind >= 2 && Bp == B)
-                e = dispatch_tma(a, (const float*)y, B, frames_per_hat(op->frame_D), kind == 3 ? 2 : 1, st);
+                e = dispatch_tma(op, a, (const float*)y, B, frames_per_hat(op->frame_D), kind == 3 ? 2 : 1,
+                                 st);
         }
         if (e == cudaErrorNotSupported) {
             cudaGetLastError();  // clear the "not supported" marker, if any

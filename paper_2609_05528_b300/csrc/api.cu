@@ -204,9 +204,9 @@ static void free_op(rtt_op_s* op) {
     if (!op) return;
     void* ps[] = {op->row_ptr, op->ray_row, op->node00, op->node01, op->W,     op->W64,
                   op->K0,      op->F0,      op->F64,    op->r,      op->delay, op->weight,
-                  op->thr,     op->row_order, op->c_row, op->c_col, op->c_K0, op->c_F0,
+                  op->thr,     op->row_order, op->c_row, op->c_col, op->c_K0, op->c_F0, op->c_fb, op->c_r0,
                   op->c_W,     op->c_W64,   op->c_F64, op->seg_ray, op->seg_col, op->seg_ncol,
-                  op->seg_rec, op->gslot,   op->adj_ctr, op->cpart,
+                  op->seg_rec, op->gslot,   op->adj_ctr, op->cpart, op->row_sched,
                   op->dev_status, op->rscratch, op->row_pixel, op->mix.grp_ptr,
                   op->mix.grp_rows, op->mix.row_grp, op->mix.inv32, op->mix.inv64,
                   op->mix.part, op->phi};
@@ -422,6 +422,32 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
     prep_rays<<<blocks(E), 256, 0, st>>>(pa);
     RTT_CUDA(cudaGetLastError());
 
+    // ---- the forward's source-cell row order: within each order, rows by the
+    // Morton index of their first ray's cell (i0, j0) (ties by row) ----
+    {
+        std::vector<int32_t> rp(R + 1), n00(E);
+        RTT_CUDA(cudaMemcpyAsync(rp.data(), op->row_ptr, (R + 1) * 4, cudaMemcpyDeviceToHost, st));
+        RTT_CUDA(cudaMemcpyAsync(n00.data(), op->node00, E * 4, cudaMemcpyDeviceToHost, st));
+        RTT_CUDA(cudaStreamSynchronize(st));
+        auto morton = [](uint32_t i, uint32_t j) {
+            uint64_t m = 0;
+            for (int b = 0; b < 16; ++b)
+                m |= (uint64_t)((i >> b) & 1u) << (2 * b + 1) | (uint64_t)((j >> b) & 1u) << (2 * b);
+            return m;
+        };
+        std::vector<uint64_t> key(R);
+        for (int64_t r = 0; r < R; ++r) {
+            const int32_t c = n00[rp[r]];
+            key[r] = morton((uint32_t)(c / grid->n_phi), (uint32_t)(c % grid->n_phi));
+        }
+        std::vector<int32_t> sched(R);
+        for (int64_t r = 0; r < R; ++r) sched[r] = (int32_t)r;
+        for (int n = 0; n < 3; ++n)
+            std::stable_sort(sched.begin() + op->row_begin[n], sched.begin() + op->row_begin[n + 1],
+                             [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+        RTT_TRY(alloc(&op->row_sched, R));
+        RTT_CUDA(cudaMemcpy(op->row_sched, sched.data(), R * 4, cudaMemcpyHostToDevice));
+    }
     RTT_TRY(alloc(&op->dev_status, 1));
     RTT_CUDA(cudaMemsetAsync(op->dev_status, 0, sizeof(int), st));
     // ---- the adjoint's cell structures (rays by source cell, strip segments) ----

@@ -82,6 +82,7 @@ struct ApplyArgs {
     int64_t n_rays_total;
     int seg_rows_all;  // total rows of the operator (all orders)
     int* status;                // device status word (bit 0: a bounded wait timed out)
+    const int32_t* row_sched;   // rows in source-cell order within each order, or null
     int hs32;                   // hat steps per 32 frames when a whole number, else 0
     int n_fchunk, n_bchunk, n_kchunk;
     int64_t n_tasks;
@@ -115,6 +116,21 @@ __device__ __forceinline__ HatCoef<double> load_hat<double>(const ApplyArgs<doub
     HatCoef<double> h;
     h.K0 = a.K0[e]; h.F = a.F64[e]; h.D = a.D;
     return h;
+}
+
+// output row and input row of the t-th task row of the arm: the natural
+// (order, pixel) order, or the source-cell order of the operator's row
+// schedule (a permutation within each order, so the arm's rows stay a union
+// of whole order blocks)
+template <typename T>
+__device__ __forceinline__ void task_row(const ApplyArgs<T>& a, int t, int& row_out, int& row) {
+    if (a.row_sched) {
+        row = a.row_sched[seg_in_row(a.seg, t)];
+        row_out = seg_out_row(a.seg, row);
+    } else {
+        row_out = t;
+        row = seg_in_row(a.seg, t);
+    }
 }
 
 // spatial interpolation w0 v0 + w1 v1 + w2 v2 + w3 v3
@@ -224,8 +240,8 @@ fwd3_kernel(const ApplyArgs<T> a) {
     for (TaskWalk tw(warp_global, n_warps, a.n_bchunk, a.n_fchunk); tw.r < a.seg.total; tw.next()) {
         const int bchunk = tw.b;
         const int fchunk = tw.f;
-        const int row_out = tw.r;
-        const int row = seg_in_row(a.seg, row_out);
+        int row_out, row;
+        task_row(a, tw.r, row_out, row);
         const int f_begin = fchunk * FC;
         const int f_end = min(a.Tn, f_begin + FC);
         const int b0 = bchunk * BC;
@@ -419,8 +435,8 @@ fwd4_kernel(const ApplyArgs<float> a) {
         const int bchunk = (int)(task % a.n_bchunk);
         const int64_t t2 = task / a.n_bchunk;
         const int fchunk = (int)(t2 % a.n_fchunk);
-        const int row_out = (int)(t2 / a.n_fchunk);
-        const int row = seg_in_row(a.seg, row_out);
+        int row_out, row;
+        task_row(a, (int)(t2 / a.n_fchunk), row_out, row);
         const int f_c = fchunk * FC;
         const int b0 = bchunk * BC;
         const int nb = min(BC, a.B - b0);
@@ -581,8 +597,8 @@ fwd5_kernel(const __grid_constant__ CUtensorMap xmap, const ApplyArgs<float> a, 
         const int bchunk = (int)(task % a.n_bchunk);
         const int64_t t2 = task / a.n_bchunk;
         const int fchunk = (int)(t2 % a.n_fchunk);
-        it.row_out = (int)(t2 / a.n_fchunk);
-        const int row = seg_in_row(a.seg, it.row_out);
+        int row;
+        task_row(a, (int)(t2 / a.n_fchunk), it.row_out, row);
         it.f_begin = fchunk * FC;
         it.b0 = bchunk * BC;
         it.e = a.row_ptr[row];
@@ -747,8 +763,8 @@ fwd7_kernel(const ApplyArgs<float> a) {
     const int kk0 = lane / Q, q0 = lane % Q;
     const int32_t lane_off = -lane * D;  // - lane D, the lane's offset inside a hat step pattern
     for (TaskWalk tw(warp_global, n_warps, 1, a.n_fchunk); tw.r < a.seg.total; tw.next()) {
-        const int row_out = tw.r;
-        const int row = seg_in_row(a.seg, row_out);
+        int row_out, row;
+        task_row(a, tw.r, row_out, row);
         const int f_begin = tw.f * FC;
         const bool full = f_begin + FC <= a.Tn;  // every frame of the chunk exists
         const int hb = f_begin / P;               // whole hat steps before the chunk
@@ -910,8 +926,8 @@ fwd6_kernel(const ApplyArgs<float> a, int* status, uint32_t slab_bytes, uint32_t
     TaskWalk tw(warp_global, n_warps, 1, a.n_fchunk);
     auto task_first = [&](It& it) -> bool {
         if (tw.r >= a.seg.total) return false;
-        const int row = seg_in_row(a.seg, tw.r);
-        it.row_out = tw.r;
+        int row;
+        task_row(a, tw.r, it.row_out, row);
         it.f_begin = tw.f * FC;
         it.e = a.row_ptr[row];
         it.e_end = a.row_ptr[row + 1];
@@ -1372,6 +1388,7 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
     ApplyArgs<T> a = base_args<T>(op, x, y, B, seg);
     if constexpr (sizeof(T) == 4) {
         const ApplyVariant v = variant_for(op, B);
+        a.row_sched = v.fwd_order ? op->row_sched : nullptr;
         const int bc = v.fwd_bc > 0 ? v.fwd_bc : pick_bc(B);
         if (v.fwd == 2) {
             switch (frames_per_hat(a.D)) {

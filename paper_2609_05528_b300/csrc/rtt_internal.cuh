@@ -44,6 +44,7 @@ struct ApplyVariant {
     int8_t fwd_bc = 0;  // batch entries per forward task (power of two)
     int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
     int8_t fwd_su = 2;   // staged forward: staging items in flight per lane (1, 2 or 3)
+    int8_t fwd_order = 0; // forward task rows: 0 (order, pixel), 1 source-cell order
     int8_t adj = 0;     // adjoint: 1 general (staged by per-lane copies), 2 TMA with 32-hat
                         // items, 3 TMA with 64-hat items (the widest the call allows is used)
 };
@@ -86,12 +87,16 @@ struct rtt_op_s {
     double* thr = nullptr;
     int32_t* row_order = nullptr; // [R] order of each row
     int32_t* row_pixel = nullptr; // [R] pixel of each row
+    int32_t* row_sched = nullptr; // [R] rows by source cell (Morton order of the first ray's
+                                  // cell) within each order: the forward's alternative task order
     // adjoint by source cells (adjoint.cu): ray tables in cell order, strip
     // segments of cells, their partial records and the gather table
     int32_t* c_row = nullptr;    // [E] input data row
     int32_t* c_col = nullptr;    // [E] cell column
     int32_t* c_K0 = nullptr;     // [E]
     int32_t* c_F0 = nullptr;     // [E]
+    int32_t* c_fb = nullptr;     // [E] periodic cadences: first tap frame of hat 0
+    int32_t* c_r0 = nullptr;     // [E] periodic cadences: tap weight phase
     float4* c_W = nullptr;       // [E]
     double* c_W64 = nullptr;     // [4E]
     double* c_F64 = nullptr;     // [E]

@@ -80,6 +80,11 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
     a.fwd_bc = (int8_t)bc;
     a.fwd_half = (int8_t)v->fwd_half;
     a.adj = (int8_t)v->adj_kernel;
+    if (v->fwd_order < 0 || v->fwd_order > 1) {
+        set_error("invalid forward row order %d", v->fwd_order);
+        return RTT_EINVAL;
+    }
+    a.fwd_order = (int8_t)v->fwd_order;
     if (v->fwd_staging < 0 || v->fwd_staging > 3) {
         set_error("invalid forward staging depth %d", v->fwd_staging);
         return RTT_EINVAL;
@@ -100,6 +105,7 @@ extern "C" rtt_status rtt_get_variant(rtt_op op, int batch, rtt_variant* out) {
     out->fwd_half = a.fwd_half;
     out->adj_kernel = a.adj;
     out->fwd_staging = a.fwd_su;
+    out->fwd_order = a.fwd_order;
     return RTT_OK;
 }
 
@@ -196,6 +202,16 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                     }
                 }
             }
+    // forward task rows in source-cell order, for the chosen kernel
+    {
+        ApplyVariant v = best;
+        v.fwd_order = 1;
+        const float ms = time_it(v, false);
+        if (ms < fwd_best) {
+            fwd_best = ms;
+            best.fwd_order = 1;
+        }
+    }
     // adjoint: the per-lane staged kernel and the TMA kernels the call allows
     const float adj_rule = time_it(rule, true);
     float adj_best = adj_rule;
@@ -225,6 +241,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
         best.fwd == 2 ? (int32_t)(kFracOne / op->frame_D)
                       : (best.fwd_bc >= 32 ? 1 : (32 / best.fwd_bc) / (best.fwd_half ? 2 : 1));
     out->adj_kernel = best.adj;
+    out->fwd_order = best.fwd_order;
     out->fwd_ms = fwd_best;
     out->adj_ms = adj_best;
     out->fwd_ms_rule = fwd_rule;

@@ -209,9 +209,10 @@ def test_every_variant_same_bits(which, small, schw, B):
         for bc in sorted({bc_max, max(1, bc_max // 2), max(1, bc_max // 4)}):
             for half in (0, 1):
                 for su in ((1, 2, 3) if (fk == 1 and half == 0 and bc in (4, 8)) else (2,)):
-                    c.op.set_variant(B, fk, bc, half, 1, fwd_staging=su)
-                    assert torch.equal(c.op.apply_A(x), y0), (fk, bc, half, su)
-                    n += 1
+                    for order in (0, 1):  # task rows in (order, pixel) or source-cell order
+                        c.op.set_variant(B, fk, bc, half, 1, fwd_staging=su, fwd_order=order)
+                        assert torch.equal(c.op.apply_A(x), y0), (fk, bc, half, su, order)
+                        n += 1
     for ak in (1, 2, 3):
         c.op.set_variant(B, 1, bc_max, 0, ak)
         assert torch.equal(c.op.apply_AT(y0), g0), ak
@@ -224,8 +225,15 @@ def test_every_variant_same_bits(which, small, schw, B):
         c.op.set_variant(B, 1, bc_max, 0, ak)
         assert torch.equal(c.op.apply_AT(y1, arm_mask=1), g1), ak
     for fk in (1, 3, 4, 5):
-        c.op.set_variant(B, fk, bc_max, 0, 1)
-        assert torch.equal(c.op.apply_A(x, arm_mask=1), y1), fk
+        for order in (0, 1):
+            c.op.set_variant(B, fk, bc_max, 0, 1, fwd_order=order)
+            assert torch.equal(c.op.apply_A(x, arm_mask=1), y1), (fk, order)
+    # rings only (an arm that starts after the direct block)
+    c.op.set_variant(B)
+    y6 = c.op.apply_A(x, arm_mask=6)
+    for order in (0, 1):
+        c.op.set_variant(B, 1, bc_max, 0, 1, fwd_order=order)
+        assert torch.equal(c.op.apply_A(x, arm_mask=6), y6), order
     c.op.set_variant(B)
     assert c.op.status(clear=True) == 0
     assert n >= 12
