@@ -666,8 +666,8 @@ typedef struct {
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
     int32_t fwd_staging;  /* staged forward: x items in flight per lane */
-    int32_t adj_kernel;   /* adjoint: 1 per-lane staged copies, 2 TMA with 32-hat items,
-                             3 TMA with 64-hat items */
+    int32_t adj_kernel;   /* adjoint: 1 general, 2 periodic staged by per-lane copies,
+                             3 TMA with 32-hat items, 4 TMA with 64-hat items */
     float fwd_ms, adj_ms;           /* chosen variants, ms per apply */
     float fwd_ms_rule, adj_ms_rule; /* the untuned default rule, ms per apply */
     int32_t candidates;             /* configurations timed */
@@ -687,13 +687,14 @@ typedef struct {
                              else staged) */
     int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32 */
     int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
-    int32_t adj_kernel;   /* adjoint: 1 frames staged by per-lane copies (any batch,
-                             cadence and precision), 2 frames staged by TMA tensor copies
-                             with 32-hat items, 3 the same with 64-hat items (TMA: the
-                             whole batch of 4, 8 or 16 entries in one chunk, a frame
-                             step of 1/2, 1/4 or 1/8 hat step with whole frames per
-                             128-byte line; where the call does not allow the choice,
-                             the next one down runs) */
+    int32_t adj_kernel;   /* adjoint: 1 general (any cadence, batch and precision; frames
+                             staged by per-lane copies), 2 periodic (a frame step of 1/2,
+                             1/4 or 1/8 hat step; any batch, in 8- or 4-column chunks;
+                             frames staged by per-lane copies), 3 frames staged by TMA
+                             tensor copies with 32-hat items, 4 the same with 64-hat items
+                             (TMA: the whole batch of 4, 8 or 16 entries in one chunk with
+                             whole frames per 128-byte line); where the call does not
+                             allow the choice, the next one down runs */
     int32_t fwd_staging;  /* staged forward: x items in flight per lane, 1, 2 or 3
                              (0 = 2; other values than 2 only at 4 or 8 entries) */
     int32_t fwd_order;    /* forward task rows: 0 in (order, pixel) order, 1 in source-cell

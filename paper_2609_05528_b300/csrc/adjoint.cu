@@ -624,6 +624,175 @@ adj_cell_gen_kernel(const CellArgs a, uint32_t buf_bytes, int vec_stage) {
 }
 
 // ---------------------------------------------------------------------------
+// Periodic staged kernel (FP32 or FP64; a frame step of 1/P hat step, P in
+// {2, 4, 8}; any batch, in chunks of BC columns).  An item covers 32 NH hats
+// (lane l: hats l + 32 h).  Per ray step the item's (32 NH + 1) P frames of
+// the chunk are staged by per-lane asynchronous copies into the padded
+// buffer of the general kernel, double-buffered over the warp's steps.  Hat
+// k sums its 2P taps, frames fbase - P k + j in ascending order, with the
+// TMA kernel's FP32 weights 1 - |r0 - j D| 2^-24 (hence its bits) or, in
+// FP64, the exact weights of the ray's FP64 hat fraction (taps j < P carry
+// 1 - frac, taps j >= P carry frac).  Frames outside the observation are
+// skipped.
+// ---------------------------------------------------------------------------
+template <typename T, int BC, int P, int NH>
+__global__ void __launch_bounds__(kGenWarps * 32, 3)
+adj_cell_per_kernel(const CellArgs a, uint32_t buf_bytes, int vec_stage) {
+    wait_prior_grid();
+    extern __shared__ __align__(16) unsigned char smem_per_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* bufp0 = smem_per_raw + (size_t)(2 * warp) * buf_bytes;
+    const uint32_t buf0 = smem_u32(bufp0);
+    constexpr int E = BC * (int)sizeof(T);  // staged bytes per frame
+    constexpr int HATS = 32 * NH;
+    const T* y = reinterpret_cast<const T*>(a.y);
+    const int32_t D32 = a.D;
+    struct Cp {
+        int fa, nf;   // staged frames [fa, fa + nf)
+        int fbase;    // first tap frame of hat 0
+        int32_t r0;   // FP32 weight phase
+        T w[4];
+    };
+    auto derive = [&](const Step& s, Cp& c) {
+        c.fbase = s.h0;
+        c.r0 = s.h1;
+        const int kg0 = HATS * s.g;
+        int fa = c.fbase - P * (kg0 + HATS - 1);
+        int fb = c.fbase - P * kg0 + 2 * P - 1;
+        if (fa < 0) fa = 0;
+        if (fb > a.Tn - 1) fb = a.Tn - 1;
+        c.fa = fa;
+        c.nf = fb >= fa ? fb - fa + 1 : 0;  // <= (HATS + 1) P = fwin
+        if constexpr (sizeof(T) == 8) {
+            const double2* p = reinterpret_cast<const double2*>(a.c_W64 + 4 * (int64_t)s.pos);
+            const double2 v0 = p[0], v1 = p[1];
+            c.w[0] = v0.x; c.w[1] = v0.y; c.w[2] = v1.x; c.w[3] = v1.y;
+        } else {
+            const float4 v = a.c_W[s.pos];
+            c.w[0] = v.x; c.w[1] = v.y; c.w[2] = v.z; c.w[3] = v.w;
+        }
+    };
+    auto issue = [&](const Step& s, const Cp& c, uint32_t b) {
+        const uint32_t dst = buf0 + b * buf_bytes;
+        const int bcol = s.bc * BC;
+        const int nb = a.Bp - bcol < BC ? a.Bp - bcol : BC;
+        const T* src = y + ((int64_t)s.row_out * a.Tn + c.fa) * a.B + a.b0 + bcol;
+        if (vec_stage) {
+            constexpr int QE = E / 16 > 0 ? E / 16 : 1;
+            for (int o = lane; o < c.nf * QE; o += 32) {
+                const int fl = o / QE, q = o - fl * QE;
+                cp_async<T>(dst + stage_off(fl, E) + 16 * q,
+                            reinterpret_cast<const unsigned char*>(src + (int64_t)fl * a.B) + 16 * q, 16);
+            }
+        } else {
+            for (int o = lane; o < c.nf * BC; o += 32) {
+                const int fl = o / BC, bb = o - fl * BC;
+                if (bb < nb)
+                    cp_async<T>(dst + stage_off(fl, E) + bb * (int)sizeof(T), src + (int64_t)fl * a.B + bb,
+                                (int)sizeof(T));
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    Walk wk;
+    ColAcc<T, NH, BC> A;
+    A.zero_all();
+    int jc = 0;
+    uint32_t n_issued = 0, n_done = 0;
+    Step s0 = walk_next(a, wk, lane);
+    Step s1 = s0.kind ? walk_next(a, wk, lane) : s0;
+    Step s2 = s1.kind ? walk_next(a, wk, lane) : s1;
+    Cp c0{}, c1{};
+    if (s0.kind == 1) {
+        derive(s0, c0);
+        issue(s0, c0, n_issued++ & 1);
+    }
+    if (s1.kind == 1) {
+        derive(s1, c1);
+        issue(s1, c1, n_issued++ & 1);
+    }
+    EmitAt at{0, 0, BC, 32, false};
+    while (s0.kind) {
+        at.kbase = HATS * s0.g;
+        at.boff = s0.bc * BC;
+        at.nb = a.Bp - at.boff < BC ? a.Bp - at.boff : BC;
+        if (s0.kind == 1) {
+            if (n_issued > n_done + 1)
+                asm volatile("cp.async.wait_group 1;" ::: "memory");
+            else
+                asm volatile("cp.async.wait_group 0;" ::: "memory");
+            __syncwarp();
+            const unsigned char* buf = bufp0 + (n_done & 1) * buf_bytes;
+            T wt[2 * P];
+            if constexpr (sizeof(T) == 4) {
+#pragma unroll
+                for (int j = 0; j < 2 * P; ++j)
+                    wt[j] = 1.0f - (float)abs(c0.r0 - j * D32) * (1.0f / (float)kFracOne);
+            } else {
+                // exact fraction of u(f) at the taps' frames: F64 - (f D mod 2^24) 2^-24, mod 1
+                const double F64 = a.c_F64[s0.pos];
+#pragma unroll
+                for (int j = 0; j < 2 * P; ++j) {
+                    const int64_t f = (int64_t)c0.fbase + j;  // any hat: P k D is a whole step
+                    const int64_t fd = f * (int64_t)D32;
+                    const double R = (double)(((fd % kFracOne) + kFracOne) & kFracMask) *
+                                     (1.0 / (double)kFracOne);
+                    double v = F64 - R;
+                    if (v < 0.0) v += 1.0;
+                    wt[j] = j < P ? 1.0 - v : v;
+                }
+            }
+            T z[NH][BC];
+#pragma unroll
+            for (int h = 0; h < NH; ++h) {
+#pragma unroll
+                for (int b = 0; b < BC; ++b) z[h][b] = T(0);
+                const int k = at.kbase + lane + 32 * h;
+                const int f0 = c0.fbase - P * k;  // first tap frame
+                if (k < a.K) {
+#pragma unroll
+                    for (int j = 0; j < 2 * P; ++j) {
+                        const int fl = f0 + j - c0.fa;
+                        if (fl >= 0 && fl < c0.nf) {
+                            const T* vv = reinterpret_cast<const T*>(buf + stage_off(fl, E));
+                            if constexpr (sizeof(T) == 4 && BC % 4 == 0) {
+#pragma unroll
+                                for (int q = 0; q < BC / 4; ++q) {
+                                    const float4 v = reinterpret_cast<const float4*>(vv)[q];
+                                    fmac2x2(wt[j], v, z[h][4 * q], z[h][4 * q + 1], z[h][4 * q + 2],
+                                            z[h][4 * q + 3]);
+                                }
+                            } else {
+#pragma unroll
+                                for (int b = 0; b < BC; ++b) z[h][b] = fmac(wt[j], vv[b], z[h][b]);
+                            }
+                        }
+                    }
+                }
+            }
+            __syncwarp();  // buffer free for the copy issued into it next
+            ++n_done;
+            for (; jc < s0.col; ++jc) next_column(a, A, s0.rec0 + 2 * jc, at, lane);
+            if constexpr (sizeof(T) == 4 && BC % 2 == 0)
+                acc_add2(A, z, make_float4(c0.w[0], c0.w[1], c0.w[2], c0.w[3]));
+            else
+                A.add(z, c0.w[0], c0.w[1], c0.w[2], c0.w[3]);
+        } else {
+            finish_item(a, A, jc, s0, at, lane);
+        }
+        s0 = s1;
+        c0 = c1;
+        s1 = s2;
+        s2 = s1.kind ? walk_next(a, wk, lane) : s1;
+        if (s1.kind == 1) {
+            derive(s1, c1);
+            issue(s1, c1, n_issued++ & 1);
+        }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
 // Gather: x[node][k][b0 + b] = sum of the node's records in the fixed order
 // (strip i - 1 upper row: segment before, own; strip i lower row: segment
 // before, own).  Also resets the work ticket counter for the next adjoint.
@@ -1011,6 +1180,55 @@ static cudaError_t launch_cell_gen_bc(CellArgs a, cudaStream_t st) {
                             buf, vec);
 }
 
+template <typename T, int BC, int P, int NH>
+static cudaError_t launch_cell_per(CellArgs a, const int32_t* fb, const int32_t* r0, cudaStream_t st) {
+    constexpr int E = BC * (int)sizeof(T);
+    a.hw = 32 * NH;
+    a.fwin = (32 * NH + 1) * P;
+    const uint32_t buf = (uint32_t)(((size_t)stage_off(a.fwin, E) + 16 + 15) & ~(size_t)15);
+    const size_t smem = (size_t)kGenWarps * 2 * buf;
+    if (smem > 200 * 1024) return cudaErrorNotSupported;
+    a.n_hg = (a.K + 32 * NH - 1) / (32 * NH);
+    a.n_bc = (a.Bp + BC - 1) / BC;
+    a.n_items = a.n_items * a.n_hg * a.n_bc;  // n_items holds the segment count on entry
+    a.c_h0 = fb;
+    a.c_h1 = r0;
+    const int vec = (E % 16 == 0) && ((a.B * (int)sizeof(T)) % 16 == 0) &&
+                    ((a.b0 * (int)sizeof(T)) % 16 == 0) && (a.Bp % BC == 0) &&
+                    ((uintptr_t)a.y % 16 == 0);
+    auto kern = adj_cell_per_kernel<T, BC, P, NH>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const int grid = resident_grid(kern, kGenWarps * 32, smem, a.n_items, kGenWarps);
+    return launch_dependent(kern, dim3(grid), dim3(kGenWarps * 32), smem, st, a, buf, vec);
+}
+
+// the periodic staged kernel: 8-column chunks (FP32) or 4-column chunks (FP64),
+// two hats per lane; cudaErrorNotSupported for other cadences
+template <typename T>
+static cudaError_t launch_cell_per_any(const rtt_op_s* op, const CellArgs& a, cudaStream_t st) {
+    const int P = frames_per_hat(op->frame_D);
+    const int32_t *fb = op->c_fb, *r0 = op->c_r0;
+    if constexpr (sizeof(T) == 4) {
+        if (a.Bp % 8 == 0) {
+            if (P == 2) return launch_cell_per<T, 8, 2, 2>(a, fb, r0, st);
+            if (P == 4) return launch_cell_per<T, 8, 4, 2>(a, fb, r0, st);
+            if (P == 8) return launch_cell_per<T, 8, 8, 2>(a, fb, r0, st);
+        } else {
+            if (P == 2) return launch_cell_per<T, 4, 2, 2>(a, fb, r0, st);
+            if (P == 4) return launch_cell_per<T, 4, 4, 2>(a, fb, r0, st);
+            if (P == 8) return launch_cell_per<T, 4, 8, 2>(a, fb, r0, st);
+        }
+    } else {
+        if (P == 2) return launch_cell_per<T, 4, 2, 1>(a, fb, r0, st);
+        if (P == 4) return launch_cell_per<T, 4, 4, 1>(a, fb, r0, st);
+        if (P == 8) return launch_cell_per<T, 4, 8, 1>(a, fb, r0, st);
+    }
+    return cudaErrorNotSupported;
+}
+
 template <typename T>
 static cudaError_t launch_cell_gen(const CellArgs& a, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
@@ -1049,11 +1267,13 @@ static cudaError_t launch_gather(const rtt_op_s* op, T* x, int B, int b0, int Bp
 }
 
 // the adjoint kernel an FP32 call of `batch` columns can use at most:
-// 3 (TMA, 64-hat items), 2 (TMA, 32-hat items) or 1 (general)
+// 4 (TMA, 64-hat items), 3 (TMA, 32-hat items), 2 (periodic, staged by
+// per-lane copies) or 1 (general)
 int adjoint_best_kind(const rtt_op_s* op, int batch) {
+    const int P = frames_per_hat(op->frame_D);
     int hg = 0;
-    if (!tma_shape(op, batch, frames_per_hat(op->frame_D), &hg)) return 1;
-    return hg == 2 ? 3 : 2;
+    if (tma_shape(op, batch, P, &hg)) return hg == 2 ? 4 : 3;
+    return P > 0 ? 2 : 1;
 }
 
 template <typename T>
@@ -1067,7 +1287,7 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         return cudaErrorInvalidValue;
     }
     const int PC = pass_cols((int)sizeof(T));
-    int kind = 1;
+    int kind = frames_per_hat(op->frame_D) > 0 ? 2 : 1;  // FP64: periodic when the cadence allows
     if constexpr (sizeof(T) == 4) {
         const ApplyVariant v = variant_for(op, B);
         kind = v.adj;
@@ -1082,12 +1302,16 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         a.n_items = op->n_seg;
         cudaError_t e = cudaErrorNotSupported;
         if constexpr (sizeof(T) == 4) {
-            if (kind >= 2 && Bp == B)
-                e = dispatch_tma(op, a, (const float*)y, B, frames_per_hat(op->frame_D), kind == 3 ? 2 : 1,
+            if (kind >= 3 && Bp == B)
+                e = dispatch_tma(op, a, (const float*)y, B, frames_per_hat(op->frame_D), kind == 4 ? 2 : 1,
                                  st);
         }
-        if (e == cudaErrorNotSupported) {
+        if (e == cudaErrorNotSupported && kind >= 2) {
             cudaGetLastError();  // clear the "not supported" marker, if any
+            e = launch_cell_per_any<T>(op, a, st);
+        }
+        if (e == cudaErrorNotSupported) {
+            cudaGetLastError();
             e = launch_cell_gen<T>(a, st);
         }
         if (e != cudaSuccess) return e;

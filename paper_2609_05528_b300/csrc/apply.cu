@@ -744,7 +744,7 @@ constexpr int kFwd7MinBlocks = 4;
 template <int BC, int FPL, int P>
 __global__ void __launch_bounds__(kFwd7Warps * 32, kFwd7MinBlocks)
 fwd7_kernel(const ApplyArgs<float> a) {
-    static_assert(BC == 4 || BC == 8, "16-byte batch records, one chunk");
+    static_assert(BC == 4 || BC == 8, "16-byte batch records");
     wait_prior_grid();
     constexpr int Q = BC / 4;
     constexpr int FC = 32 * FPL;
@@ -758,11 +758,13 @@ fwd7_kernel(const ApplyArgs<float> a) {
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = (int64_t)blockIdx.x * kFwd7Warps + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kFwd7Warps;
-    const int64_t KB = (int64_t)a.K * BC;  // floats per node row of x
+    const int64_t KB = (int64_t)a.K * a.B;  // floats per node row of x
+    const int B = a.B;                       // hat stride of x, frame stride of y
     // this lane's staging items o = lane + 32 u: hat lane / Q + (32 / Q) u, record lane % Q
     const int kk0 = lane / Q, q0 = lane % Q;
     const int32_t lane_off = -lane * D;  // - lane D, the lane's offset inside a hat step pattern
-    for (TaskWalk tw(warp_global, n_warps, 1, a.n_fchunk); tw.r < a.seg.total; tw.next()) {
+    for (TaskWalk tw(warp_global, n_warps, a.n_bchunk, a.n_fchunk); tw.r < a.seg.total; tw.next()) {
+        const int b0 = tw.b * BC;
         int row_out, row;
         task_row(a, tw.r, row_out, row);
         const int f_begin = tw.f * FC;
@@ -782,15 +784,15 @@ fwd7_kernel(const ApplyArgs<float> a) {
             const int k_top = K0 - hb;
             const int k_lo = k_top - FC / P + ((F0 + D) >> kFracBits);
             const int nwin = k_top + 2 - k_lo;
-            const float* b00 = a.in + (int64_t)n00 * KB + (int64_t)(k_lo + kk0) * BC + 4 * q0;
-            const float* b01 = a.in + (int64_t)n01 * KB + (int64_t)(k_lo + kk0) * BC + 4 * q0;
+            const float* b00 = a.in + (int64_t)n00 * KB + (int64_t)(k_lo + kk0) * B + b0 + 4 * q0;
+            const float* b01 = a.in + (int64_t)n01 * KB + (int64_t)(k_lo + kk0) * B + b0 + 4 * q0;
             const int64_t rstep = (int64_t)a.n_phi * KB;  // the radial neighbour's row
             float4 v[NU][4];
             if (k_lo >= 0 && k_lo + ZW <= a.K) {
 #pragma unroll
                 for (int u = 0; u < NU; ++u) {
                     if (u < NU - 1 || lane + 32 * u < ZW * Q) {
-                        const int du = (32 / Q) * u * BC;
+                        const int du = (32 / Q) * u * B;
                         v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
                         v[u][1] = __ldg(reinterpret_cast<const float4*>(b00 + rstep + du));
                         v[u][2] = __ldg(reinterpret_cast<const float4*>(b01 + du));
@@ -802,7 +804,7 @@ fwd7_kernel(const ApplyArgs<float> a) {
                 for (int u = 0; u < NU; ++u) {
                     const int k = k_lo + kk0 + (32 / Q) * u;
                     const bool ok = lane + 32 * u < ZW * Q && k >= 0 && k < a.K;
-                    const int du = (32 / Q) * u * BC;
+                    const int du = (32 / Q) * u * B;
                     v[u][0] = v[u][1] = v[u][2] = v[u][3] = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (ok) {
                         v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
@@ -862,7 +864,7 @@ fwd7_kernel(const ApplyArgs<float> a) {
         for (int j = 0; j < FPL; ++j) {
             const int f = f_begin + lane + 32 * j;
             if (full || f < a.Tn) {
-                float4* yo = reinterpret_cast<float4*>(a.out + ((int64_t)row_out * a.Tn + f) * BC);
+                float4* yo = reinterpret_cast<float4*>(a.out + ((int64_t)row_out * a.Tn + f) * B + b0);
 #pragma unroll
                 for (int qq = 0; qq < Q; ++qq)
                     yo[qq] = make_float4(acc[j][4 * qq], acc[j][4 * qq + 1], acc[j][4 * qq + 2],
@@ -1311,11 +1313,11 @@ static cudaError_t launch_fwd6(ApplyArgs<float> a, cudaStream_t st) {
 template <int BC, int FPL>
 static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st) {
     const int P = frames_per_hat(a.D);
-    if (!vec_ok(a) || a.B != BC || P == 0 || (32 * FPL) % P != 0) return cudaErrorNotSupported;
+    if (!vec_ok(a) || a.B % BC != 0 || P == 0 || (32 * FPL) % P != 0) return cudaErrorNotSupported;
     a.FC = 32 * FPL;
     a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
-    a.n_bchunk = 1;
-    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk;
+    a.n_bchunk = a.B / BC;
+    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk * a.n_bchunk;
     if (a.n_tasks == 0) return cudaSuccess;
     auto go = [&](auto kern) {
         const int grid = resident_grid(kern, kFwd7Warps * 32, 0, a.n_tasks, kFwd7Warps);
@@ -1338,9 +1340,15 @@ ApplyVariant variant_for(const rtt_op_s* op, int batch) {
     // kernel down where the cadence, batch or buffers do not allow it
     ApplyVariant v;
     const int P = frames_per_hat(op->frame_D);
-    const bool one_chunk4 = batch == 4 || batch == 8;
-    v.fwd = (P > 0 && one_chunk4) ? 5 : 1;
-    v.fwd_bc = (int8_t)pick_bc(batch);
+    // the periodic staged forward takes any batch of whole 16-byte records,
+    // in chunks of 8 (or 4) columns
+    if (P > 0 && batch % 4 == 0) {
+        v.fwd = 5;
+        v.fwd_bc = (int8_t)(batch % 8 == 0 ? 8 : 4);
+    } else {
+        v.fwd = 1;
+        v.fwd_bc = (int8_t)pick_bc(batch);
+    }
     v.adj = (int8_t)adjoint_best_kind(op, batch);
     return v;
 }

@@ -70,7 +70,7 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
     }
     const int bc = v->fwd_bc;
     if (v->fwd_kernel < 1 || v->fwd_kernel > 5 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
-        v->fwd_half < 0 || v->fwd_half > 1 || v->adj_kernel < 1 || v->adj_kernel > 3) {
+        v->fwd_half < 0 || v->fwd_half > 1 || v->adj_kernel < 1 || v->adj_kernel > 4) {
         set_error("invalid variant (fwd %d bc %d half %d adj %d)", v->fwd_kernel, bc, v->fwd_half,
                   v->adj_kernel);
         return RTT_EINVAL;
@@ -186,7 +186,8 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                 v.fwd_half = (int8_t)half;
                 if (kind == 2 && (!periodic || bc > 8)) continue;  // lane-per-hat: <= 8 per task
                 if (kind == 3 && (!x_vec || bc < 4)) continue;    // TMA: 16-byte records
-                if ((kind == 4 || kind == 5) && (bc != B || (bc != 4 && bc != 8))) continue;  // one chunk
+                if (kind == 4 && (bc != B || (bc != 4 && bc != 8))) continue;  // one chunk
+                if (kind == 5 && (B % bc != 0 || (bc != 4 && bc != 8))) continue;  // 8- or 4-column chunks
                 if (kind == 5 && !periodic) continue;  // periodic specialisation
                 for (int su = 1; su <= 3; ++su) {
                     // staging depth: only the staged kernel at 4 or 8 entries, full frames

@@ -12,7 +12,9 @@ Workloads (the paper's configurations restated as sizes):
   * ``kerr256``  Kerr a=0.5, i=50 deg, 256x256 image with 2x2 sub-rays in the
                  photon-ring annulus, 64x128 grid, 64 hats, 256 frames at 1 M.
   * ``audit12``  12 geometries, spins {0, .5, .75, .94} x incl {20, 50, 75} at
-                 the kerr256 sizes (rank audit, Sec. 6.2).
+                 the kerr256 sizes (rank audit, Sec. 6.2); ``audit12_paper_sampling``
+                 the same geometries with eight frames 2.5 M apart (the paper's
+                 audit sampling).
   * ``recovery`` Kerr a=0.94, i=50 deg at kerr256 sizes, 60 held-out histories.
   * ``stress1024`` a in {0, .94}, i=75 deg, 1024x1024, 256x512 grid, 256 hats,
                  1024 frames.
@@ -143,6 +145,18 @@ def audit12() -> list[Workload]:
     for a in (0.0, 0.5, 0.75, 0.94):
         for i in (20.0, 50.0, 75.0):
             out.append(kerr256(a, i, name=f"audit_a{a:g}_i{i:g}"))
+    return out
+
+
+def audit12_paper_sampling() -> list[Workload]:
+    """The 12 geometries at kerr256 sizes with the paper's audit sampling
+    (Sec. 6.2): eight observer times uniformly spanning 20 M, read as
+    t_o = 2.5 f, f = 0..7, the youngest hat at the last frame."""
+    out = []
+    for a in (0.0, 0.5, 0.75, 0.94):
+        for i in (20.0, 50.0, 75.0):
+            out.append(Workload(f"audit8_a{a:g}_i{i:g}", Geometry(a, i, 256), SourceGrid(64, 128),
+                                TimeGrid(8, 2.5, 64, t_end=17.5), supersample=2))
     return out
 
 

@@ -175,9 +175,9 @@ def test_autotune_keeps_bits(B):
     g0 = c.op.apply_AT(y0)
     r = c.op.autotune(B)
     assert r["batch"] == B and r["candidates"] >= 4
-    assert r["fwd_kernel"] in (1, 2, 3, 4, 5) and r["adj_kernel"] in (1, 2, 3)
+    assert r["fwd_kernel"] in (1, 2, 3, 4, 5) and r["adj_kernel"] in (1, 2, 3, 4)
     if B % 4:
-        assert r["adj_kernel"] == 1  # the TMA adjoint needs 16-byte frame records
+        assert r["adj_kernel"] <= 2  # the TMA adjoint needs 16-byte frame records
     assert 0 < r["fwd_ms"] <= r["fwd_ms_rule"] and 0 < r["adj_ms"] <= r["adj_ms_rule"]
     y1 = c.op.apply_A(x)
     g1 = c.op.apply_AT(y0)
@@ -213,7 +213,7 @@ def test_every_variant_same_bits(which, small, schw, B):
                         c.op.set_variant(B, fk, bc, half, 1, fwd_staging=su, fwd_order=order)
                         assert torch.equal(c.op.apply_A(x), y0), (fk, bc, half, su, order)
                         n += 1
-    for ak in (1, 2, 3):
+    for ak in (1, 2, 3, 4):
         c.op.set_variant(B, 1, bc_max, 0, ak)
         assert torch.equal(c.op.apply_AT(y0), g0), ak
         n += 1
@@ -221,7 +221,7 @@ def test_every_variant_same_bits(which, small, schw, B):
     c.op.set_variant(B)
     y1 = c.op.apply_A(x, arm_mask=1)
     g1 = c.op.apply_AT(y1, arm_mask=1)
-    for ak in (1, 2, 3):
+    for ak in (1, 2, 3, 4):
         c.op.set_variant(B, 1, bc_max, 0, ak)
         assert torch.equal(c.op.apply_AT(y1, arm_mask=1), g1), ak
     for fk in (1, 3, 4, 5):
@@ -258,7 +258,7 @@ def test_apply_A_AT(which, small, schw, B, mask, with_d):
     bc = 1
     while bc < B:
         bc *= 2
-    for ak in (1, 2, 3):
+    for ak in (1, 2, 3, 4):
         c.op.set_variant(B, 1, bc, 0, ak)
         y, g = c.op.apply_A_AT(x, d, arm_mask=mask)
         assert torch.equal(y, y_ref), ak
