@@ -1,11 +1,15 @@
-"""Benchmark of the operator hot path on the kerr256 workload.
+"""Benchmark of the operator hot path on the throughput workload stress1024.
 
 One step = one pass of the A / A^T pair behind the reconstruction-loss
 gradient for a batch of 8 histories: y = A x (forward) followed by
-g = A^T y (adjoint), on the Kerr a = 0.5, i = 50 deg geometry with a
-256 x 256 image (2 x 2 sub-rays in the photon-ring annulus), a 64 x 128
-source grid, 64 hats and 256 frames.  Ray tables come from the library's
-own GPU tracer (rtt_trace_rays), the operator from rtt_build_operator.
+g = A^T y (adjoint), on the Kerr a = 0.94, i = 75 deg geometry with a
+1024 x 1024 image, a 256 x 512 source grid, 256 hats and 1024 frames (FP32
+tables and accumulation), x ~ U(0, 1) per coefficient.  Ray tables come from
+the library's own GPU tracer (rtt_trace_rays), the operator from
+rtt_build_operator.  The same JSON line carries the batch sweep 1-64 of that
+workload, the kerr256 step (a = 0.5, i = 50 deg, 256 x 256 with 2 x 2 ring
+sub-rays, 64 x 128 nodes, 64 hats, 256 frames), the 12-geometry rank audit
+against the plain FP64 path, and the FP64 CPU oracle timed on the host.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).  Under torchrun each rank runs an
@@ -31,11 +35,14 @@ sys.path.insert(0, ROOT)
 METRIC = "A+A^T applies/s"
 UNIT = "history-applies/s"
 BATCH = 8
+SWEEP_BATCHES = (1, 2, 4, 8, 16, 32, 64)
 L2_FLUSH_BYTES = 256 << 20
 
 
-WORKLOAD = ("kerr256: Kerr a=0.5 i=50deg 256x256 (2x2 ring sub-rays), 64x128 source, 64 hats, "
-            "256 frames, resolved n=0..2")
+WORKLOAD = ("stress1024: Kerr a=0.94 i=75deg 1024x1024, 256x512 source, 256 hats, 1024 frames, "
+            "resolved n=0..2, FP32")
+WORKLOAD_KERR256 = ("kerr256: Kerr a=0.5 i=50deg 256x256 (2x2 ring sub-rays), 64x128 source, "
+                    "64 hats, 256 frames, resolved n=0..2")
 
 
 def measured_peaks():
@@ -107,20 +114,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_workload(device):
+def build_workload(device, w, batch, seed0: int = 1, tune: bool = True):
+    """Trace, build and (optionally) autotune an operator; x ~ U(0, 1) per
+    coefficient from the seeded generator (seeds seed0 .. seed0 + batch - 1)."""
     import torch
 
     from paper_2609_05528_b300 import build, rtt
     from paper_2609_05528_b300 import inputs as I
     build.build()
-    w = I.kerr256()
     s = I.screen_samples(w)
     torch.cuda.synchronize(device)
     tab = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, s)
     op = rtt.Operator(w, tab)
-    x = torch.from_numpy(I.history_batch(w, range(100, 100 + BATCH)).astype(np.float32)).to(device)
-    op.tune = op.autotune(BATCH)  # kernel variants for this batch size (setup, untimed)
-    return w, tab, op, x
+    x = torch.from_numpy(I.uniform_batch(w, range(seed0, seed0 + batch)).astype(np.float32)).to(device)
+    op.tune = op.autotune(batch) if tune else None  # kernel variants (setup, untimed)
+    return tab, op, x
 
 
 def kernel_source_hash() -> str:
@@ -162,55 +170,80 @@ def algorithmic_bytes(op, B, elem=4):
     return {"A": y + x + table_fwd, "AT": y + x + table_adj, "y": y, "x": x}
 
 
+def time_loop(stream, fn, n, flush=None):
+    """Per-call device times (ms) of fn on `stream`, CUDA events around each
+    call, optional L2 flush before each (outside the events)."""
+    import torch
+    out = []
+    for _ in range(n):
+        if flush is not None:
+            flush.zero_()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        fn()
+        a1.record(stream)
+        a1.synchronize()
+        out.append(a0.elapsed_time(a1))
+    return out
+
+
+def roofline_of(op, B, mA, mAT, traffic_key=None):
+    ab = algorithmic_bytes(op, B)
+    dom, dom_ms = ("A", mA) if mA >= mAT else ("AT", mAT)
+    peak, peak_kind = measured_peaks()
+    achieved = ab[dom] / (dom_ms * 1e-3) / 1e9
+    return ab, {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": recorded_traffic(dom) if traffic_key else None,
+                "algorithmic_bytes": ab[dom], "source_hash": kernel_source_hash(),
+                "A_frac": ab["A"] / (mA * 1e-3) / 1e9 / peak,
+                "AT_frac": ab["AT"] / (mAT * 1e-3) / 1e9 / peak}
+
+
 def run_ours(args, rank, world, device):
     import torch
 
+    from paper_2609_05528_b300 import inputs as I
     torch.cuda.set_device(device)
-    w, tab, op, x = build_workload(device)
+    w = I.stress1024(0.94)
+    tab, op, x = build_workload(device, w, BATCH)
     stream = torch.cuda.current_stream(device)
     R = op.arm_rows(7)
     y = torch.empty((R, op.n_frames, BATCH), dtype=torch.float32, device=device)
     g = torch.empty_like(x)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
 
     def step():
         op.apply_A(x, y)
         op.apply_AT(y, g)
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    # y (12.4 GB) and x (1.07 GB) are far larger than L2: no flush needed
     with ClockSampler(device.index if device.index is not None else 0) as clk:
-        # warm-up inside the sampled region, right before the timed steps, so
-        # the GPU does not idle (and drop its clocks) between the two; the last
-        # warm-up step is queued after the barrier, so the host's launches are
-        # ahead of the device when the first timed step starts
         n_warm = max(args.warmup, 3)
         for _ in range(n_warm - 1):
-            flush.zero_()
             step()
         torch.cuda.synchronize(device)
         ranks_barrier(world)
-        flush.zero_()
         step()
-        torch.cuda.nvtx.range_push("bench_timed")  # lets ncu --nvtx-include select these launches
-        for i in range(args.steps):
-            flush.zero_()  # L2 flush between timed iterations (outside the events)
-            e0, e1, e2 = ev[i]
-            e0.record(stream)
-            op.apply_A(x, y)
-            e1.record(stream)
-            op.apply_AT(y, g)
-            e2.record(stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("bench_timed")
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize(device)
         ranks_barrier(world)
-    t_A = [ev[i][0].elapsed_time(ev[i][1]) for i in range(args.steps)]
-    t_AT = [ev[i][1].elapsed_time(ev[i][2]) for i in range(args.steps)]
-    ms_step = max_over_ranks(float(np.mean([a + b for a, b in zip(t_A, t_AT)])), world, device)
+    ms_step = max_over_ranks(e0.elapsed_time(e1) / args.steps, world, device)
     clocks = clk.summary()
+    # the split between the two applies, each timed alone (events around one call)
+    t_A = time_loop(stream, lambda: op.apply_A(x, y), args.steps)
+    t_AT = time_loop(stream, lambda: op.apply_AT(y, g), args.steps)
+    mA, mAT = float(np.median(t_A)), float(np.median(t_AT))
+    ab, roof = roofline_of(op, BATCH, mA, mAT)
 
-    # the same A + A^T pair replayed from a captured CUDA graph (the library
-    # allocates nothing once its adjoint scratch exists, so the calls capture)
+    # the same step replayed from a captured CUDA graph
     graph = None
     try:
         graph_obj = torch.cuda.CUDAGraph()
@@ -224,52 +257,33 @@ def run_ours(args, rank, world, device):
         torch.cuda.synchronize(device)
         for _ in range(3):
             graph_obj.replay()
-        g_ms = []
-        for _ in range(args.steps):
-            flush.zero_()
-            a0 = torch.cuda.Event(enable_timing=True)
-            a1 = torch.cuda.Event(enable_timing=True)
-            a0.record(stream)
-            graph_obj.replay()
-            a1.record(stream)
-            a1.synchronize()
-            g_ms.append(a0.elapsed_time(a1))
-        gm = max_over_ranks(float(np.mean(g_ms)), world, device)
+        gm = max_over_ranks(float(np.mean(time_loop(stream, graph_obj.replay, args.steps))), world,
+                            device)
         graph = {"ms_per_step": gm, "value": job_value(world, BATCH, gm)}
     except Exception as exc:  # capture is a measurement extra; report why it failed
         graph = {"error": str(exc)[:200]}
 
     # end-to-end through the C ABI with host buffers: x from pinned host
-    # memory to the device, A, A^T, gradient back to pinned host memory
+    # memory to the device, A, A^T, the gradient back to pinned host memory
     xh = x.cpu().pin_memory()
     gh = torch.empty(g.shape, dtype=g.dtype).pin_memory()
     xd = torch.empty_like(x)
-    for _ in range(3):
-        xd.copy_(xh, non_blocking=True)
-        op.apply_A(xd, y)
-        op.apply_AT(y, g)
-        gh.copy_(g, non_blocking=True)
-    torch.cuda.synchronize(device)
-    e_ms = []
-    for _ in range(args.steps):
-        flush.zero_()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        xd.copy_(xh, non_blocking=True)
-        op.apply_A(xd, y)
-        op.apply_AT(y, g)
-        gh.copy_(g, non_blocking=True)
-        a1.record(stream)
-        a1.synchronize()
-        e_ms.append(a0.elapsed_time(a1))
-    e2e_serial_ms = max_over_ranks(float(np.mean(e_ms)), world, device)
 
-    # the same, pipelined over steps as a user streaming histories would run
-    # it: each step still copies its x in and its gradient out, but the copies
-    # of one step overlap the kernels of its neighbours (copy-in, compute and
-    # copy-out streams, two buffer sets, event dependencies).  No L2 flush
-    # between steps here: y (299 MB) alone exceeds the L2.
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        op.apply_A(xd, y)
+        op.apply_AT(y, g)
+        gh.copy_(g, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(device)
+    e2e_serial_ms = max_over_ranks(float(np.mean(time_loop(stream, e2e_step, max(3, args.steps // 4)))),
+                                   world, device)
+    # pipelined over steps as a user streaming histories would run it: each
+    # step still copies its x in and its gradient out, overlapping the
+    # kernels of its neighbours (copy-in, compute, copy-out streams, two
+    # buffer sets, event dependencies)
     s_in, s_cmp, s_out = (torch.cuda.Stream(device) for _ in range(3))
     xds = [torch.empty_like(x) for _ in range(2)]
     gds = [torch.empty_like(x) for _ in range(2)]
@@ -297,97 +311,143 @@ def run_ours(args, rank, world, device):
                 ghs[b].copy_(gds[b], non_blocking=True)
             ev_out[b].record(s_out)
 
-    pipeline(4)
+    pipeline(3)
     torch.cuda.synchronize(device)
+    n_pipe = max(4, args.steps // 2)
     p0 = torch.cuda.Event(enable_timing=True)
     p1 = torch.cuda.Event(enable_timing=True)
     p0.record(s_in)
     s_cmp.wait_event(p0)
     s_out.wait_event(p0)
-    pipeline(args.steps)
+    pipeline(n_pipe)
     p1.record(s_out)
     p1.synchronize()
     torch.cuda.synchronize(device)
-    e2e_ms = max_over_ranks(p0.elapsed_time(p1) / args.steps, world, device)
+    e2e_ms = max_over_ranks(p0.elapsed_time(p1) / n_pipe, world, device)
+    del xds, gds, ghs, xd
 
-    # plain FP64 GPU path (same kernels in double) for comparison
-    x64 = x.double()
-    y64 = torch.empty((R, op.n_frames, BATCH), dtype=torch.float64, device=device)
-    g64 = torch.empty_like(x64)
-    op.apply_A(x64, y64)
-    op.apply_AT(y64, g64)
-    torch.cuda.synchronize(device)
-    f_ms = []
-    for _ in range(max(3, args.steps // 4)):
-        flush.zero_()
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
+    # plain FP64 GPU path (the same kernels in double) for comparison
+    fp64 = None
+    try:
+        x64 = x.double()
+        y64 = torch.empty((R, op.n_frames, BATCH), dtype=torch.float64, device=device)
+        g64 = torch.empty_like(x64)
         op.apply_A(x64, y64)
         op.apply_AT(y64, g64)
-        a1.record(stream)
-        a1.synchronize()
-        f_ms.append(a0.elapsed_time(a1))
-    fp64_ms = max_over_ranks(float(np.mean(f_ms)), world, device)
+        torch.cuda.synchronize(device)
+        f_ms = time_loop(stream, lambda: (op.apply_A(x64, y64), op.apply_AT(y64, g64)), 3)
+        fp64_ms = max_over_ranks(float(np.mean(f_ms)), world, device)
+        fp64 = {"value": job_value(world, BATCH, fp64_ms), "ms_per_step": fp64_ms}
+        del x64, y64, g64
+    except Exception as exc:  # a measurement extra; report why it failed
+        fp64 = {"error": str(exc)[:200]}
+    del y, g
+    torch.cuda.empty_cache()
 
-    # order mixing (Eq. 4) of the step's y: the unresolved image and the
-    # total-flux readout, HBM bound (y read once, the mixed rows written once)
+    # batch sweep of the same workload (config 5: A and A^T GB/s against HBM),
+    # each batch size autotuned first; y >= 1.5 GB per history, far above L2
+    sweep = []
+    peak, _ = measured_peaks()
+    for B in SWEEP_BATCHES:
+        try:
+            tune = op.autotune(B)
+            xb = torch.from_numpy(I.uniform_batch(w, range(1, 1 + B)).astype(np.float32)).to(device)
+            yb = torch.empty((R, op.n_frames, B), dtype=torch.float32, device=device)
+            gb = torch.empty_like(xb)
+            op.apply_A(xb, yb)
+            op.apply_AT(yb, gb)
+            reps = 5 if B <= 16 else 3
+            tA = float(np.median(time_loop(stream, lambda: op.apply_A(xb, yb), reps)))
+            tT = float(np.median(time_loop(stream, lambda: op.apply_AT(yb, gb), reps)))
+            abb = algorithmic_bytes(op, B)
+            sweep.append({"batch": B, "A_ms": tA, "AT_ms": tT,
+                          "A_gbs": abb["A"] / (tA * 1e-3) / 1e9, "AT_gbs": abb["AT"] / (tT * 1e-3) / 1e9,
+                          "A_frac": abb["A"] / (tA * 1e-3) / 1e9 / peak,
+                          "AT_frac": abb["AT"] / (tT * 1e-3) / 1e9 / peak,
+                          "history_applies_per_s": B / ((tA + tT) * 1e-3),
+                          "variant": {k: tune[k] for k in ("fwd_kernel", "fwd_bc", "fwd_order",
+                                                           "adj_kernel")}})
+            del xb, yb, gb
+            torch.cuda.empty_cache()
+        except Exception as exc:
+            sweep.append({"batch": B, "error": str(exc)[:200]})
+    n_rays, n_nodes = int(op.info.n_rays), op.n_nodes
+    op.close()
+
+    # kerr256, batch 8 (the autograd reconstruction step's workload)
+    k256 = run_kerr256(args, world, device)
+
+    value = job_value(world, BATCH, ms_step)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch": BATCH, "rows": R, "rays": n_rays,
+                   "nodes": n_nodes, "hats": w.time.n_hats, "frames": w.time.n_frames,
+                   "x": "U(0,1) per coefficient, seeds 1..8",
+                   "l2": "inputs larger than L2 (y 12.4 GB per step), no flush",
+                   "parallelism": f"replicas x{world}", "autotune": op.tune},
+        "hbm_gbs": (ab["A"] + ab["AT"]) / (ms_step * 1e-3) / 1e9,
+        "kernels_ms": {"A": mA, "AT": mAT},
+        "roofline": roof,
+        "e2e": {"value": job_value(world, BATCH, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
+                "pipelined": "copy-in / compute / copy-out streams over steps",
+                "serial_ms_per_step": e2e_serial_ms,
+                "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4)},
+        "fp64_path": fp64,
+        "cuda_graph": graph,
+        "sweep": sweep,
+        "kerr256": k256,
+        "clocks": clocks,
+        "gpu_launches": launches_per_step(BATCH) * args.steps,
+    }
+    return out
+
+
+def run_kerr256(args, world, device):
+    """kerr256 at batch 8: the A + A^T step (L2 flushed between steps), its
+    split, the order mixing of its y (Eq. 4) and a CUDA-graph replay."""
+    import torch
+
+    from paper_2609_05528_b300 import inputs as I
+    from paper_2609_05528_b300 import rtt
+    w = I.kerr256()
+    _, op, x = build_workload(device, w, BATCH, seed0=100)
+    stream = torch.cuda.current_stream(device)
+    R = op.arm_rows(7)
+    y = torch.empty((R, op.n_frames, BATCH), dtype=torch.float32, device=device)
+    g = torch.empty_like(x)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def step():
+        op.apply_A(x, y)
+        op.apply_AT(y, g)
+
+    for _ in range(3):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(device)
+    ms = float(np.mean(time_loop(stream, step, args.steps, flush)))
+    mA = float(np.median(time_loop(stream, lambda: op.apply_A(x, y), args.steps, flush)))
+    mAT = float(np.median(time_loop(stream, lambda: op.apply_AT(y, g), args.steps, flush)))
+    _, roof = roofline_of(op, BATCH, mA, mAT, traffic_key=True)
     mix = {}
     try:
-        from paper_2609_05528_b300 import rtt
         peak_m, _ = measured_peaks()
         for name, mode in (("unresolved", rtt.MIX_UNRESOLVED), ("total_flux", rtt.MIX_TOTAL_FLUX)):
             yl = op.mix_rows(y, mode)
-            m_ms = []
-            for _ in range(args.steps):
-                flush.zero_()
-                a0 = torch.cuda.Event(enable_timing=True)
-                a1 = torch.cuda.Event(enable_timing=True)
-                a0.record(stream)
-                op.mix_rows(y, mode, out=yl)
-                a1.record(stream)
-                a1.synchronize()
-                m_ms.append(a0.elapsed_time(a1))
-            mm = float(np.mean(m_ms))
+            mm = float(np.mean(time_loop(stream, lambda: op.mix_rows(y, mode, out=yl), args.steps,
+                                         flush)))
             nbytes = (y.numel() + yl.numel()) * 4
             mix[name] = {"ms": mm, "rows_out": int(yl.shape[0]), "algorithmic_bytes": int(nbytes),
                          "GB/s": nbytes / (mm * 1e-3) / 1e9, "frac": nbytes / (mm * 1e-3) / 1e9 / peak_m}
     except Exception as exc:  # a measurement extra; report why it failed
         mix = {"error": str(exc)[:200]}
-
-    ab = algorithmic_bytes(op, BATCH)
-    mA, mAT = float(np.mean(t_A)), float(np.mean(t_AT))
-    dom, dom_ms = ("A", mA) if mA >= mAT else ("AT", mAT)
-    peak, peak_kind = measured_peaks()
-    achieved = ab[dom] / (dom_ms * 1e-3) / 1e9
-    value = job_value(world, BATCH, ms_step)
-    gbs = (ab["A"] + ab["AT"]) / (ms_step * 1e-3) / 1e9
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD,
-                   "batch": BATCH, "rows": R, "rays": int(op.info.n_rays),
-                   "nodes": op.n_nodes, "hats": op.n_hats, "frames": op.n_frames,
-                   "l2": "flushed between timed steps (256 MiB write)",
-                   "parallelism": f"replicas x{world}",
-                   "autotune": op.tune},
-        "hbm_gbs": gbs,
-        "kernels_ms": {"A": mA, "AT": mAT},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(dom), "algorithmic_bytes": ab[dom],
-                     "source_hash": kernel_source_hash()},
-        "e2e": {"value": job_value(world, BATCH, e2e_ms), "unit": UNIT, "ms_per_step": e2e_ms,
-                "pipelined": "copy-in / compute / copy-out streams over steps; inputs larger than L2",
-                "serial_ms_per_step": e2e_serial_ms,
-                "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4)},
-        "fp64_path": {"value": job_value(world, BATCH, fp64_ms), "ms_per_step": fp64_ms},
-        "cuda_graph": graph,
-        "order_mix": mix,
-        "clocks": clocks,
-        "gpu_launches": launches_per_step(BATCH) * args.steps,
-    }
+    out = {"workload": WORKLOAD_KERR256, "batch": BATCH, "ms_per_step": ms,
+           "value": job_value(world, BATCH, ms), "kernels_ms": {"A": mA, "AT": mAT},
+           "roofline": roof, "order_mix": mix, "autotune": op.tune,
+           "l2": "flushed between timed steps (256 MiB write)"}
+    op.close()
     return out
 
 
@@ -812,19 +872,36 @@ def run_recovery(device, n_test: int = 60, n_val: int = 20, max_iter: int = 400,
 _ORACLE_TABLES = {}
 
 
-def oracle_pairs_per_s(w, budget_s: float = 12.0, B: int = 1, threads: int | None = None):
-    """Time the FP64 CPU oracle (as it stands) on A + A^T for one history, on
-    all host cores or on `threads` of them.  Returns (pairs/s, threads used,
-    pairs timed); the oracle's table is built once per workload, untimed."""
+def oracle_sample(w, row_block: int = 4, every: int = 8):
+    """The oracle's ray table on a bounded, stratified sample of the screen:
+    every `every`-th block of `row_block` pixel rows (1 / every of the
+    screen).  Built once per workload (untimed)."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
 
     from paper_2609_05528_b300 import inputs as I
-    if w.name not in _ORACLE_TABLES:
-        _ORACLE_TABLES[w.name] = O.build_table(w, I.screen_samples(w))
-    tab = _ORACLE_TABLES[w.name]
+    key = (w.name, row_block, every)
+    if key not in _ORACLE_TABLES:
+        s = I.screen_samples(w)
+        iy = s.pixel // w.geometry.nx
+        m = (iy // row_block) % every == 0
+        sub = I.ScreenSamples(s.alpha[m], s.beta[m], s.pixel[m], s.n_sub[m], s.d_omega_pixel)
+        _ORACLE_TABLES[key] = O.build_table(w, sub)
+    return _ORACLE_TABLES[key], every
+
+
+def oracle_pairs_per_s(w, budget_s: float = 12.0, threads: int | None = None):
+    """Time the FP64 CPU oracle (as it stands) on A + A^T for one history on
+    the stratified screen sample of `oracle_sample`, on all host cores or on
+    `threads` of them.  Returns (history-applies/s scaled to the whole
+    screen, threads used, pairs timed, sample description)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    from paper_2609_05528_b300 import inputs as I
+    tab, every = oracle_sample(w)
     scl = O.scale(tab)
-    x = I.history_batch(w, [100])
+    x = I.uniform_batch(w, [1])
     all_cores = O.max_threads()
     if threads:
         O.set_threads(threads)
@@ -833,15 +910,17 @@ def oracle_pairs_per_s(w, budget_s: float = 12.0, B: int = 1, threads: int | Non
         n = 0
         t0 = time.perf_counter()
         while True:
-            y = O.apply_A(w, tab, x, scl)
-            O.apply_AT(w, tab, y, scl)
+            yv = O.apply_A(w, tab, x, scl)
+            O.apply_AT(w, tab, yv, scl)
             n += 1
             if time.perf_counter() - t0 > budget_s:
                 break
         dt = time.perf_counter() - t0
     finally:
         O.set_threads(all_cores)
-    return n * B / dt, cores, n
+    sample = (f"{n} x (A + A^T) on 1 history, FP64 oracle, on every {every}th block of 4 pixel "
+              f"rows ({tab.n_rows} data rows, 1/{every} of the screen); value scaled by 1/{every}")
+    return n / dt / every, cores, n, sample
 
 
 def main():
@@ -868,23 +947,22 @@ def main():
         # the reference arm is the FP64 CPU oracle, timed on the host cores
         if rank != 0:
             return
-        w = I.kerr256()
-        per_step_budget = 10.0
+        w = I.stress1024(0.94)
         vals = []
         for _ in range(max(1, args.steps)):
-            v, cores, n = oracle_pairs_per_s(w, budget_s=per_step_budget)
+            v, cores, n, sample = oracle_pairs_per_s(w, budget_s=10.0)
             vals.append(v)
             if len(vals) >= 2:
                 break
         v = float(np.mean(vals))
-        sample = f"{n} x (A + A^T) on 1 history of kerr256 per timed pass, FP64 oracle"
         print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
                           "n_gpus": 1, "steps": len(vals), "warmup": 0,
                           "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
                           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                           "config": {"workload": WORKLOAD, "batch": 1,
-                                     "sample": "one history per pass (the unit is per "
-                                               "history, so the batch does not change it)",
+                                     "sample": "one history per pass on a stratified 1/8 of the "
+                                               "screen (the unit is per history, so the batch does "
+                                               "not change it)",
                                      "parallelism": f"host cores x{cores}"},
                           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores,
                                            "kind": "oracle", "sample": sample},
@@ -918,14 +996,13 @@ def main():
         out["audit"] = run_audit(device)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            v, cores, n = oracle_pairs_per_s(I.kerr256())
-            v1, _, n1 = oracle_pairs_per_s(I.kerr256(), budget_s=6.0, threads=1)
+            w5 = I.stress1024(0.94)
+            v, cores, n, sample = oracle_pairs_per_s(w5)
+            v1, _, n1, sample1 = oracle_pairs_per_s(w5, budget_s=6.0, threads=1)
             out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                   "sample": f"{n} x (A + A^T) on 1 history of kerr256, "
-                                             "FP64 oracle, ~12 s",
+                                   "sample": sample + ", ~12 s",
                                    "single_core": {"value": v1, "unit": UNIT, "cores": 1,
-                                                   "sample": f"{n1} x (A + A^T), same history, "
-                                                             "~6 s"}}
+                                                   "sample": sample1 + ", ~6 s"}}
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

@@ -672,6 +672,8 @@ typedef struct {
     float fwd_ms_rule, adj_ms_rule; /* the untuned default rule, ms per apply */
     int32_t candidates;             /* configurations timed */
     int32_t fwd_order;    /* forward task rows: 0 (order, pixel), 1 source-cell order */
+    int32_t fwd_cols;     /* forward column passes (0: all columns at once) */
+    int32_t adj_cols;     /* adjoint columns per pass (0: 32 in FP32) */
 } rtt_tune_result;
 
 rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream, rtt_tune_result* out);
@@ -701,6 +703,12 @@ typedef struct {
                              order (within each order, by the Morton index of the row's
                              first ray's cell: rows that read the same x nodes run
                              close together) */
+    int32_t fwd_cols;     /* periodic forward (fwd_kernel 5): 0 = all columns in one
+                             launch, or a multiple of 4 dividing the batch = the whole
+                             operator for that many columns at a time (bounds x's and
+                             y's working set for large batches); 0..64 */
+    int32_t adj_cols;     /* adjoint columns per pass (0 = 32; else 4..32, a multiple of
+                             4): the partial records hold one pass */
 } rtt_variant;
 
 /*

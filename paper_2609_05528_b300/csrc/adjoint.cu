@@ -1286,13 +1286,14 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         set_error("adjoint scratch not prepared for batch %d", B);
         return cudaErrorInvalidValue;
     }
-    const int PC = pass_cols((int)sizeof(T));
+    int PC = pass_cols((int)sizeof(T));
     int kind = frames_per_hat(op->frame_D) > 0 ? 2 : 1;  // FP64: periodic when the cadence allows
     if constexpr (sizeof(T) == 4) {
         const ApplyVariant v = variant_for(op, B);
         kind = v.adj;
         const int best = adjoint_best_kind(op, B);
         if (kind > best) kind = best;
+        if (v.adj_cols > 0 && v.adj_cols < PC) PC = v.adj_cols;
     }
     for (int b0 = 0; b0 < B; b0 += PC) {
         const int Bp = B - b0 < PC ? B - b0 : PC;

@@ -83,6 +83,7 @@ struct ApplyArgs {
     int seg_rows_all;  // total rows of the operator (all orders)
     int* status;                // device status word (bit 0: a bounded wait timed out)
     const int32_t* row_sched;   // rows in source-cell order within each order, or null
+    int Bcols;                  // columns of this launch (0: all B), the periodic forward
     int hs32;                   // hat steps per 32 frames when a whole number, else 0
     int n_fchunk, n_bchunk, n_kchunk;
     int64_t n_tasks;
@@ -1316,7 +1317,7 @@ static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st) {
     if (!vec_ok(a) || a.B % BC != 0 || P == 0 || (32 * FPL) % P != 0) return cudaErrorNotSupported;
     a.FC = 32 * FPL;
     a.n_fchunk = (a.Tn + a.FC - 1) / a.FC;
-    a.n_bchunk = a.B / BC;
+    a.n_bchunk = (a.Bcols > 0 ? a.Bcols : a.B) / BC;
     a.n_tasks = (int64_t)a.seg.total * a.n_fchunk * a.n_bchunk;
     if (a.n_tasks == 0) return cudaSuccess;
     auto go = [&](auto kern) {
@@ -1408,8 +1409,26 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
         }
         if (v.fwd == 5 && (bc == 4 || bc == 8)) {
             const bool half = v.fwd_half != 0;
-            const cudaError_t e = bc == 4 ? (half ? launch_fwd7<4, 4>(a, st) : launch_fwd7<4, 8>(a, st))
-                                          : (half ? launch_fwd7<8, 2>(a, st) : launch_fwd7<8, 4>(a, st));
+            auto go = [&](const ApplyArgs<float>& aa) {
+                return bc == 4 ? (half ? launch_fwd7<4, 4>(aa, st) : launch_fwd7<4, 8>(aa, st))
+                               : (half ? launch_fwd7<8, 2>(aa, st) : launch_fwd7<8, 4>(aa, st));
+            };
+            cudaError_t e;
+            const int pc = v.fwd_cols;
+            if (pc > 0 && pc < B && B % pc == 0 && pc % bc == 0) {
+                // column passes: the whole operator for pc columns at a time
+                // (x's and y's working set per pass is that of a pc-column batch)
+                e = cudaSuccess;
+                for (int b0 = 0; b0 < B && e == cudaSuccess; b0 += pc) {
+                    ApplyArgs<float> ap = a;
+                    ap.in = x + b0;
+                    ap.out = y + b0;
+                    ap.Bcols = pc;
+                    e = go(ap);
+                }
+            } else {
+                e = go(a);
+            }
             if (e != cudaErrorNotSupported) return e;
             cudaGetLastError();  // clear the "not supported" marker, if any
         }

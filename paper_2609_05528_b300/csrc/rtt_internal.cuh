@@ -45,6 +45,8 @@ struct ApplyVariant {
     int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
     int8_t fwd_su = 2;   // staged forward: staging items in flight per lane (1, 2 or 3)
     int8_t fwd_order = 0; // forward task rows: 0 (order, pixel), 1 source-cell order
+    int8_t fwd_cols = 0;  // periodic forward: 0 all columns at once, else passes of this many
+    int8_t adj_cols = 0;  // adjoint: columns per pass (0: 32 in FP32, 16 in FP64)
     int8_t adj = 0;     // adjoint: 1 general, 2 periodic staged by per-lane copies, 3 TMA
                         // with 32-hat items, 4 TMA with 64-hat items (the most the call allows)
 };

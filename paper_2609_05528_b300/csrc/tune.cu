@@ -85,6 +85,13 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
         return RTT_EINVAL;
     }
     a.fwd_order = (int8_t)v->fwd_order;
+    if (v->fwd_cols < 0 || v->fwd_cols > 64 || v->adj_cols < 0 || v->adj_cols > 32 ||
+        (v->fwd_cols & 3) || (v->adj_cols & 3)) {
+        set_error("invalid column passes (forward %d, adjoint %d)", v->fwd_cols, v->adj_cols);
+        return RTT_EINVAL;
+    }
+    a.fwd_cols = (int8_t)v->fwd_cols;
+    a.adj_cols = (int8_t)v->adj_cols;
     if (v->fwd_staging < 0 || v->fwd_staging > 3) {
         set_error("invalid forward staging depth %d", v->fwd_staging);
         return RTT_EINVAL;
@@ -106,6 +113,8 @@ extern "C" rtt_status rtt_get_variant(rtt_op op, int batch, rtt_variant* out) {
     out->adj_kernel = a.adj;
     out->fwd_staging = a.fwd_su;
     out->fwd_order = a.fwd_order;
+    out->fwd_cols = a.fwd_cols;
+    out->adj_cols = a.adj_cols;
     return RTT_OK;
 }
 
@@ -213,6 +222,16 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
             best.fwd_order = 1;
         }
     }
+    // forward column passes of 8 columns (large batches of the periodic forward)
+    if (best.fwd == 5 && B > 8 && B % 8 == 0) {
+        ApplyVariant v = best;
+        v.fwd_cols = 8;
+        const float ms = time_it(v, false);
+        if (ms < fwd_best) {
+            fwd_best = ms;
+            best.fwd_cols = 8;
+        }
+    }
     // adjoint: the per-lane staged kernel and the TMA kernels the call allows
     const float adj_rule = time_it(rule, true);
     float adj_best = adj_rule;
@@ -224,6 +243,16 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
         if (ms < adj_best) {
             adj_best = ms;
             best.adj = v.adj;
+        }
+    }
+    // adjoint passes of 8 or 16 columns (large batches)
+    for (int pc = 8; pc <= 16 && B > pc; pc *= 2) {
+        ApplyVariant v = best;
+        v.adj_cols = (int8_t)pc;
+        const float ms = time_it(v, true);
+        if (ms < adj_best) {
+            adj_best = ms;
+            best.adj_cols = (int8_t)pc;
         }
     }
     cudaFree(x);
@@ -243,6 +272,8 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                       : (best.fwd_bc >= 32 ? 1 : (32 / best.fwd_bc) / (best.fwd_half ? 2 : 1));
     out->adj_kernel = best.adj;
     out->fwd_order = best.fwd_order;
+    out->fwd_cols = best.fwd_cols;
+    out->adj_cols = best.adj_cols;
     out->fwd_ms = fwd_best;
     out->adj_ms = adj_best;
     out->fwd_ms_rule = fwd_rule;

@@ -242,6 +242,14 @@ def screen_samples(w: Workload) -> ScreenSamples:
                          counts[idx].astype(np.int32), d * d)
 
 
+def screen_band(s: ScreenSamples, nx: int, row_lo: int, row_hi: int) -> ScreenSamples:
+    """The samples of the pixel rows iy in [row_lo, row_hi) (a bounded sample
+    of a large screen, for timing the CPU oracle)."""
+    iy = s.pixel // nx
+    m = (iy >= row_lo) & (iy < row_hi)
+    return ScreenSamples(s.alpha[m], s.beta[m], s.pixel[m], s.n_sub[m], s.d_omega_pixel)
+
+
 # ---------------------------------------------------------------------------
 # Source histories (nodal coefficients x[s][k], s = i_r * n_phi + j_phi)
 # ---------------------------------------------------------------------------

@@ -92,13 +92,15 @@ class TuneResult(ctypes.Structure):
                 ("fwd_staging", ctypes.c_int32), ("adj_kernel", ctypes.c_int32),
                 ("fwd_ms", ctypes.c_float), ("adj_ms", ctypes.c_float),
                 ("fwd_ms_rule", ctypes.c_float), ("adj_ms_rule", ctypes.c_float),
-                ("candidates", ctypes.c_int32), ("fwd_order", ctypes.c_int32)]
+                ("candidates", ctypes.c_int32), ("fwd_order", ctypes.c_int32),
+                ("fwd_cols", ctypes.c_int32), ("adj_cols", ctypes.c_int32)]
 
 
 class Variant(ctypes.Structure):
     _fields_ = [("fwd_kernel", ctypes.c_int32), ("fwd_bc", ctypes.c_int32),
                 ("fwd_half", ctypes.c_int32), ("adj_kernel", ctypes.c_int32),
-                ("fwd_staging", ctypes.c_int32), ("fwd_order", ctypes.c_int32)]
+                ("fwd_staging", ctypes.c_int32), ("fwd_order", ctypes.c_int32),
+                ("fwd_cols", ctypes.c_int32), ("adj_cols", ctypes.c_int32)]
 
 
 # name -> (restype, argtypes)
@@ -318,13 +320,13 @@ class Operator:
         return {k: getattr(r, k) for k, _ in TuneResult._fields_}
 
     def set_variant(self, batch: int, fwd_kernel=None, fwd_bc=None, fwd_half=0, adj_kernel=None,
-                    fwd_staging=0, fwd_order=0):
+                    fwd_staging=0, fwd_order=0, fwd_cols=0, adj_cols=0):
         """rtt_set_variant; all None resets `batch` to the default rule."""
         if fwd_kernel is None and fwd_bc is None and adj_kernel is None:
             check(lib().rtt_set_variant(self.handle, int(batch), None), "rtt_set_variant")
             return
         v = Variant(int(fwd_kernel), int(fwd_bc), int(fwd_half), int(adj_kernel), int(fwd_staging),
-                    int(fwd_order))
+                    int(fwd_order), int(fwd_cols), int(adj_cols))
         check(lib().rtt_set_variant(self.handle, int(batch), ctypes.byref(v)), "rtt_set_variant")
 
     def get_variant(self, batch: int) -> dict:

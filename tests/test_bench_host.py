@@ -5,6 +5,7 @@ import os
 import sys
 import types
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -81,8 +82,18 @@ def test_oracle_timing_on_one_core_restores_the_thread_count():
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
     n_all = O.max_threads()
-    v, cores, n = bench.oracle_pairs_per_s(I.schw32(), budget_s=0.05, threads=1)
-    assert cores == 1 and n >= 1 and v > 0
+    v, cores, n, sample = bench.oracle_pairs_per_s(I.schw32(), budget_s=0.05, threads=1)
+    assert cores == 1 and n >= 1 and v > 0 and "1/8 of the screen" in sample
     assert O.max_threads() == n_all
-    v, cores, _ = bench.oracle_pairs_per_s(I.schw32(), budget_s=0.05)
+    v, cores, _, _ = bench.oracle_pairs_per_s(I.schw32(), budget_s=0.05)
     assert cores == n_all
+
+
+def test_oracle_sample_is_a_stratified_eighth_of_the_screen():
+    """Every eighth block of four pixel rows: the sample's pixels are exactly
+    those rows, about an eighth of the screen."""
+    from paper_2609_05528_b300 import inputs as I
+    w = I.schw32()
+    tab, every = bench.oracle_sample(w)
+    iy = tab.pixel // w.geometry.nx
+    assert every == 8 and np.all((iy // 4) % 8 == 0) and tab.n_rays > 0

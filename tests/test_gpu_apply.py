@@ -228,6 +228,14 @@ def test_every_variant_same_bits(which, small, schw, B):
         for order in (0, 1):
             c.op.set_variant(B, fk, bc_max, 0, 1, fwd_order=order)
             assert torch.equal(c.op.apply_A(x, arm_mask=1), y1), (fk, order)
+    # column passes: the periodic forward and the adjoint over a few columns at a time
+    if B % 8 == 0 and B > 8:
+        c.op.set_variant(B, 5, 8, 0, 2, fwd_cols=8)
+        assert torch.equal(c.op.apply_A(x), y0)
+        for ak in (1, 2):
+            for pc in (4, 8):
+                c.op.set_variant(B, 5, 8, 0, ak, adj_cols=pc)
+                assert torch.equal(c.op.apply_AT(y0), g0), (ak, pc)
     # rings only (an arm that starts after the direct block)
     c.op.set_variant(B)
     y6 = c.op.apply_A(x, arm_mask=6)
