@@ -1212,7 +1212,11 @@ static cudaError_t launch_cell_per_any(const rtt_op_s* op, const CellArgs& a, cu
     const int P = frames_per_hat(op->frame_D);
     const int32_t *fb = op->c_fb, *r0 = op->c_r0;
     if constexpr (sizeof(T) == 4) {
-        if (a.Bp % 8 == 0) {
+        if (a.Bp % 16 == 0) {  // 64-byte pieces of each frame record
+            if (P == 2) return launch_cell_per<T, 16, 2, 1>(a, fb, r0, st);
+            if (P == 4) return launch_cell_per<T, 16, 4, 1>(a, fb, r0, st);
+            if (P == 8) return launch_cell_per<T, 16, 8, 1>(a, fb, r0, st);
+        } else if (a.Bp % 8 == 0) {
             if (P == 2) return launch_cell_per<T, 8, 2, 2>(a, fb, r0, st);
             if (P == 4) return launch_cell_per<T, 8, 4, 2>(a, fb, r0, st);
             if (P == 8) return launch_cell_per<T, 8, 8, 2>(a, fb, r0, st);

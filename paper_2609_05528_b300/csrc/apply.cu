@@ -745,7 +745,7 @@ constexpr int kFwd7MinBlocks = 4;
 template <int BC, int FPL, int P>
 __global__ void __launch_bounds__(kFwd7Warps * 32, kFwd7MinBlocks)
 fwd7_kernel(const ApplyArgs<float> a) {
-    static_assert(BC == 4 || BC == 8, "16-byte batch records");
+    static_assert(BC == 4 || BC == 8 || BC == 16, "16-byte batch records");
     wait_prior_grid();
     constexpr int Q = BC / 4;
     constexpr int FC = 32 * FPL;
@@ -1345,7 +1345,7 @@ ApplyVariant variant_for(const rtt_op_s* op, int batch) {
     // in chunks of 8 (or 4) columns
     if (P > 0 && batch % 4 == 0) {
         v.fwd = 5;
-        v.fwd_bc = (int8_t)(batch % 8 == 0 ? 8 : 4);
+        v.fwd_bc = (int8_t)(batch % 16 == 0 ? 16 : (batch % 8 == 0 ? 8 : 4));
     } else {
         v.fwd = 1;
         v.fwd_bc = (int8_t)pick_bc(batch);
@@ -1407,9 +1407,10 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
                 default: break;  // not a periodic cadence: staged kernel
             }
         }
-        if (v.fwd == 5 && (bc == 4 || bc == 8)) {
+        if (v.fwd == 5 && (bc == 4 || bc == 8 || bc == 16)) {
             const bool half = v.fwd_half != 0;
             auto go = [&](const ApplyArgs<float>& aa) {
+                if (bc == 16) return half ? launch_fwd7<16, 1>(aa, st) : launch_fwd7<16, 2>(aa, st);
                 return bc == 4 ? (half ? launch_fwd7<4, 4>(aa, st) : launch_fwd7<4, 8>(aa, st))
                                : (half ? launch_fwd7<8, 2>(aa, st) : launch_fwd7<8, 4>(aa, st));
             };

@@ -196,7 +196,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                 if (kind == 2 && (!periodic || bc > 8)) continue;  // lane-per-hat: <= 8 per task
                 if (kind == 3 && (!x_vec || bc < 4)) continue;    // TMA: 16-byte records
                 if (kind == 4 && (bc != B || (bc != 4 && bc != 8))) continue;  // one chunk
-                if (kind == 5 && (B % bc != 0 || (bc != 4 && bc != 8))) continue;  // 8- or 4-column chunks
+                if (kind == 5 && (B % bc != 0 || (bc != 4 && bc != 8 && bc != 16))) continue;
                 if (kind == 5 && !periodic) continue;  // periodic specialisation
                 for (int su = 1; su <= 3; ++su) {
                     // staging depth: only the staged kernel at 4 or 8 entries, full frames
