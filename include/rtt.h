@@ -547,6 +547,27 @@ rtt_status rtt_eig_sym_batched(int n, int batch, double* A_dev, double* evals_ho
                                int max_sweeps, int* sweeps_host, void* stream);
 
 /*
+ * rtt_gemm_tn_f64 -- C = A^T B in FP64 accuracy on the tensor cores: the
+ * contraction of the restricted Gram, G = Q^T (A^T A Q) (Eq. 21), and of the
+ * TSVD projections (Sec. 9).  A: k x m, B: k x n, C: m x n, FP64 device
+ * memory, row-major with row strides lda >= m, ldb >= n, ldc >= n.  Every
+ * column of A and of B is scaled by a power of two and split exactly into
+ * seven signed 7-bit integer digits (BF16); the 28 digit pairs whose weights
+ * reach 2^-56 are multiplied by tcgen05.mma with FP32 accumulation over
+ * windows of 128 k (exact: the sums stay below 2^22), and the windows are
+ * added in 64-bit integers, so the result is deterministic and its error is
+ * that of truncating each operand column to 49 bits below its largest entry
+ * (about 2^-46 of sum_k |A_ki| |B_kj| scaled by the column maxima).
+ * 1 <= k < 2^27.  Allocates its workspace (digit slices, 14 (m + n) k bytes)
+ * and synchronises `stream`.
+ * Errors: RTT_EINVAL, RTT_ENOMEM, RTT_ECUDA, RTT_ETIMEOUT (a bounded wait of
+ * the kernel gave up).
+ */
+rtt_status rtt_gemm_tn_f64(int64_t k, int m, int n, const double* A_dev, int64_t lda,
+                           const double* B_dev, int64_t ldb, double* C_dev, int64_t ldc,
+                           void* stream);
+
+/*
  * rtt_operational_rank -- operational rank of a restricted Gram from its
  * eigenvalues (Sec. 4.4 Eq. 31): sigma_i = sqrt(max(lambda_i, 0)) (the
  * whitening scale SNR_0 / s_ref is already in the Gram), rank = #{sigma_i >=

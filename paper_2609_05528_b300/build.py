@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if verbose and out:
             sys.stderr.write(out.decode())
     if force or _stale(LIB, objs):
-        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lcublas"]
+        cmd = [nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"]
         subprocess.check_call(cmd)
     return LIB
 

@@ -10,7 +10,6 @@
 // adds P_chunk^T P_chunk.  Partial sums over fixed row splits are reduced in
 // a fixed order (deterministic).  The eigendecomposition is a parallel
 // cyclic two-sided Jacobi method (round-robin pair ordering) in one CTA.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -19,6 +18,8 @@
 #include "rtt_internal.cuh"
 
 namespace rtt {
+rtt_status gemm_tn_f64(int64_t k, int m, int n, const double* A, int64_t lda, const double* B,
+                       int64_t ldb, double* C, int64_t ldc, int* status, cudaStream_t st);
 
 
 // dst[n][j] = Q[n][c0 + j], j < w
@@ -28,6 +29,15 @@ __global__ void copy_cols(const double* Q, int64_t n, int d, int c0, int w, doub
     const int64_t row = t / w;
     const int j = (int)(t - row * w);
     dst[t] = Q[row * d + c0 + j];
+}
+
+// dst[row][c0 + j] = src[row][j], j < w (a column block into a d-wide matrix)
+__global__ void put_cols(const double* src, int64_t n, int d, int c0, int w, double* dst) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n * w) return;
+    const int64_t row = t / w;
+    const int j = (int)(t - row * w);
+    dst[row * d + c0 + j] = src[t];
 }
 
 // G <- (G + G^T) / 2
@@ -330,19 +340,10 @@ static rtt_status gram_normal_impl(rtt_op op, int arm_mask, int mix_mode, const 
     if (e == cudaSuccess) e = cudaMalloc(&Y, (size_t)(M > 0 ? M : 1) * W * 8);
     if (e == cudaSuccess) e = cudaMalloc(&Z, (size_t)N * W * 8);
     if (e == cudaSuccess && mix_mode) e = cudaMalloc(&YL, (size_t)(ML > 0 ? ML : 1) * W * 8);
-    cublasHandle_t h = nullptr;
-    if (e == cudaSuccess && cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
-        cudaFree(Qc);
-        cudaFree(Y);
-        cudaFree(Z);
-        if (YL) cudaFree(YL);
-        set_error("cublasCreate failed");
-        return RTT_ECUDA;
-    }
-    if (h) cublasSetStream(h, st);
-    cublasStatus_t cs = CUBLAS_STATUS_SUCCESS;
-    const double one = 1.0, zero = 0.0;
-    for (int c0 = 0; e == cudaSuccess && cs == CUBLAS_STATUS_SUCCESS && c0 < d; c0 += W) {
+    // Z = A^T A Q, column block by column block, gathered into one N x d matrix
+    double* Zf = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&Zf, (size_t)N * d * 8);
+    for (int c0 = 0; e == cudaSuccess && c0 < d; c0 += W) {
         const int w = d - c0 < W ? d - c0 : W;
         copy_cols<<<(int)((N * w + 255) / 256), 256, 0, st>>>(Q, N, d, c0, w, Qc);
         e = cudaGetLastError();
@@ -355,23 +356,27 @@ static rtt_status gram_normal_impl(rtt_op op, int arm_mask, int mix_mode, const 
                 e = cudaErrorUnknown;
         }
         if (e == cudaSuccess) e = launch_adjoint<double>(op, Y, Z, w, seg, st);
-        // rows c0 .. c0+w of G (symmetric): column-major (d x w) = Q_cm (d x N) Z_cm^T (N x w)
-        if (e == cudaSuccess)
-            cs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, d, w, (int)N, &one, Q, d, Z, w, &zero,
-                             G + (int64_t)c0 * d, d);
+        if (e == cudaSuccess) {
+            put_cols<<<(int)((N * w + 255) / 256), 256, 0, st>>>(Z, N, d, c0, w, Zf);
+            e = cudaGetLastError();
+        }
     }
-    if (e == cudaSuccess && cs == CUBLAS_STATUS_SUCCESS) {
-        symmetrize<<<(int)(((int64_t)d * d + 255) / 256), 256, 0, st>>>(G, d);
-        e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    if (h) cublasDestroy(h);
     cudaFree(Qc);
     cudaFree(Y);
     cudaFree(Z);
     if (YL) cudaFree(YL);
-    if (e != cudaSuccess || cs != CUBLAS_STATUS_SUCCESS) {
-        set_error("gram (normal operator): cuda %s, cublas %d", cudaGetErrorString(e), (int)cs);
+    // G = Q^T Z on the tensor cores in FP64 accuracy (digit splitting)
+    rtt_status gs = RTT_OK;
+    if (e == cudaSuccess) gs = gemm_tn_f64(N, d, d, Q, d, Zf, d, G, d, op->dev_status, st);
+    if (e == cudaSuccess && gs == RTT_OK) {
+        symmetrize<<<(int)(((int64_t)d * d + 255) / 256), 256, 0, st>>>(G, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && gs == RTT_OK) e = cudaStreamSynchronize(st);
+    cudaFree(Zf);
+    if (gs != RTT_OK) return gs;
+    if (e != cudaSuccess) {
+        set_error("gram (normal operator): %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? RTT_ENOMEM : RTT_ECUDA;
     }
     return RTT_OK;

@@ -9,7 +9,6 @@
 // keeps the FP32 recurrence from drifting and gives the reported residual.
 // TSVD: x = Q V_r L_r^{-1} V_r^T Q^T A^T d with (V, L) the eigenpairs of the
 // restricted Gram (Eq. 31), FP64, plain GEMMs through cuBLAS.
-#include <cublas_v2.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -18,6 +17,26 @@
 #include "rtt_internal.cuh"
 
 namespace rtt {
+rtt_status gemm_tn_f64(int64_t k, int m, int n, const double* A, int64_t lda, const double* B,
+                       int64_t ldb, double* C, int64_t ldc, int* status, cudaStream_t st);
+
+// out (cols x rows) = in^T, in: rows x cols row-major
+__global__ void transpose_kernel(const double* __restrict__ in, int64_t rows, int cols, double* out) {
+    __shared__ double t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int c0 = blockIdx.y * 32;
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int64_t r = r0 + j;
+        const int c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[j][threadIdx.x] = in[r * cols + c];
+    }
+    __syncthreads();
+    for (int j = threadIdx.y; j < 32; j += 8) {
+        const int c = c0 + j;
+        const int64_t r = r0 + threadIdx.x;
+        if (r < rows && c < cols) out[(int64_t)c * rows + r] = t[threadIdx.x][j];
+    }
+}
 
 
 constexpr int kDotBlocks = 296;  // fixed grid: deterministic partial order
@@ -321,29 +340,26 @@ extern "C" rtt_status rtt_solve_tsvd(rtt_op op, int arm_mask, const double* Q, i
     SOLVE_CUDA(launch_adjoint<double>(op, data, g, n_rhs, seg, st));
     tsvd_kernel_matrix<<<nb((int64_t)d * d), 256, 0, st>>>(V, lam, d, rank, Mx);
     SOLVE_CUDA(cudaGetLastError());
-    cublasHandle_t h;
-    if (cublasCreate(&h) != CUBLAS_STATUS_SUCCESS) {
-        set_error("cublasCreate failed");
-        return RTT_ECUDA;
+    // the three contractions on the tensor cores in FP64 accuracy:
+    // c = Q^T g (d x n_rhs), coef = M^T c = M c (M symmetric), xhat = Q coef
+    // (as (Q^T)^T coef, with Q^T formed once)
+    double* Qt = nullptr;
+    if (!buf.get(&Qt, (size_t)d * N)) {
+        set_error("tsvd: device allocation failed");
+        return RTT_ENOMEM;
     }
-    cublasSetStream(h, st);
-    const double one = 1.0, zero = 0.0;
-    // row-major c (d x n_rhs) = Q^T g  <=>  column-major (n_rhs x d) = g_cm Q_cm^T
-    cublasStatus_t cs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_T, n_rhs, d, (int)N, &one, g, n_rhs,
-                                    Q, d, &zero, c, n_rhs);
-    // row-major coef (d x n_rhs) = M c  <=>  column-major (n_rhs x d) = c_cm M (M symmetric)
-    if (cs == CUBLAS_STATUS_SUCCESS)
-        cs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, n_rhs, d, d, &one, c, n_rhs, Mx, d, &zero,
-                         coefm, n_rhs);
-    // row-major xhat (N x n_rhs) = Q coef  <=>  column-major (n_rhs x N) = coef_cm Q_cm
-    if (cs == CUBLAS_STATUS_SUCCESS)
-        cs = cublasDgemm(h, CUBLAS_OP_N, CUBLAS_OP_N, n_rhs, (int)N, d, &one, coefm, n_rhs, Q, d,
-                         &zero, xhat, n_rhs);
-    cudaError_t e = cudaStreamSynchronize(st);
-    cublasDestroy(h);
-    if (cs != CUBLAS_STATUS_SUCCESS || e != cudaSuccess) {
-        set_error("tsvd GEMMs failed (cublas %d, cuda %s)", (int)cs, cudaGetErrorString(e));
-        return RTT_ECUDA;
+    s = gemm_tn_f64(N, d, n_rhs, Q, d, g, n_rhs, c, n_rhs, op->dev_status, st);
+    if (s == RTT_OK) s = gemm_tn_f64(d, d, n_rhs, Mx, d, c, n_rhs, coefm, n_rhs, op->dev_status, st);
+    if (s == RTT_OK) {
+        transpose_kernel<<<dim3((unsigned)((N + 31) / 32), (unsigned)((d + 31) / 32)), dim3(32, 8), 0, st>>>(
+            Q, N, d, Qt);
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("tsvd: transpose launch failed");
+            return RTT_ECUDA;
+        }
+        s = gemm_tn_f64(d, (int)N, n_rhs, Qt, N, coefm, n_rhs, xhat, n_rhs, op->dev_status, st);
     }
+    if (s != RTT_OK) return s;
+    SOLVE_CUDA(cudaStreamSynchronize(st));
     return RTT_OK;
 }

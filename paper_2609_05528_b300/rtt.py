@@ -166,6 +166,8 @@ _SIGS = {
     "rtt_arm_table": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(RayTable), dp, dp, dp, dp]),
     "rtt_operational_rank": (ctypes.c_int, [ctypes.c_int, dp, ctypes.c_double,
                                             ctypes.POINTER(ctypes.c_int), dp, dp]),
+    "rtt_gemm_tn_f64": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int64,
+                                       vp, ctypes.c_int64, vp, ctypes.c_int64, vp]),
     "rtt_destroy": (None, [vp]),
 }
 
@@ -555,6 +557,21 @@ def eigvals_sym_batched(G, stream=None):
     check(lib().rtt_eigvals_sym_batched(n, b, ctypes.c_void_p(A.data_ptr()), _ptr(ev, dp),
                                         _stream(stream)), "rtt_eigvals_sym_batched")
     return ev.reshape(b, n)
+
+
+def gemm_tn(A, B, stream=None):
+    """rtt_gemm_tn_f64: C = A^T B (CUDA float64 2D tensors, k x m and k x n) in
+    FP64 accuracy on the tensor cores."""
+    import torch
+    k, m = (A.shape[0], A.shape[1]) if A.dim() == 2 else (-1, -1)
+    _want(A, "A", (k, m), ("float64",))
+    _want(B, "B", (k, None), ("float64",), like=A)
+    n = B.shape[1]
+    C = torch.empty((m, n), dtype=torch.float64, device=A.device)
+    check(lib().rtt_gemm_tn_f64(k, m, n, ctypes.c_void_p(A.data_ptr()), m,
+                                ctypes.c_void_p(B.data_ptr()), n, ctypes.c_void_p(C.data_ptr()), n,
+                                _stream(stream)), "rtt_gemm_tn_f64")
+    return C
 
 
 def rank_from_eigenvalues(evals, rho: float = 1.0):
