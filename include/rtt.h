@@ -33,7 +33,7 @@
 extern "C" {
 #endif
 
-#define RTT_ABI_VERSION 1
+#define RTT_ABI_VERSION 2
 
 typedef enum rtt_status {
     RTT_OK = 0,
@@ -122,9 +122,21 @@ typedef struct {
     int32_t n_frames;
     double s_ref;          /* Eq. 17 */
     double scale;          /* snr0 / s_ref: whitening factor applied by A */
-    double delay_min[3];   /* per order, over its rays (NaN if no rays) */
+    double delay_min[3];   /* per order, over its rays (NaN if no rays); of the
+                              whole table for a row shard */
     double delay_max[3];
+    int64_t total_rows;      /* rows of the whole table (= n_rows unless sharded) */
+    int64_t total_rows_per_order[3];
+    int64_t shard_row_begin; /* first row of this operator in the whole table */
+    int32_t shard_index;     /* 0 and 1 unless built by rtt_build_operator_shard */
+    int32_t shard_count;
 } rtt_op_info;
+
+/* Row shard: block `index` of `count` of the (order, pixel)-sorted rows. */
+typedef struct {
+    int32_t index;  /* 0 <= index < count */
+    int32_t count;  /* >= 1 */
+} rtt_shard;
 
 /* Screen samples for the tracer: pixel centres or sub-rays (alpha, beta) in
    M, the pixel each belongs to and the number of sub-rays of that pixel. */
@@ -199,9 +211,9 @@ rtt_status rtt_arm_table(int kind, const rtt_ray_table* in, const double* keys_h
  * corner weights in (log r, phi) premultiplied by w (FP32, derived in FP64),
  * integer hat base and 24-bit hat fraction per ray (derived in FP64, so that
  * the set of hats touched equals the exact one), the row CSR over rays
- * sorted by (order, pixel) and the transposed node -> (ray, corner) CSR,
- * both sorted on the device.  Computes s_ref with j_ref = 1 evaluated
- * directly and scale = snr0 / s_ref.
+ * sorted by (order, pixel) on the device, and the adjoint's tables of rays
+ * by source cell.  Computes s_ref with j_ref = 1 evaluated directly and
+ * scale = snr0 / s_ref.
  * table: host FP64 SoA (not retained).  *out receives the handle.
  * Errors: RTT_EINVAL (bad grid, non-dyadic cadence/hat_step, order outside
  * {0,1,2}, negative pixel, r outside [r_in, r_out], non-finite values, no
@@ -210,6 +222,40 @@ rtt_status rtt_arm_table(int kind, const rtt_ray_table* in, const double* keys_h
 rtt_status rtt_build_operator(const rtt_geometry* geom, const rtt_source_grid* grid,
                               const rtt_time_grid* time, const rtt_ray_table* table,
                               const rtt_options* opt, void* stream, rtt_op* out);
+
+/*
+ * rtt_build_operator_shard -- the operator restricted to one block of rows
+ * (Sec. 3.1: each row of the stack of Eq. 3 is the response of one (order,
+ * pixel) to the whole source, so a block of rows is an operator of its own).
+ * shard == NULL or count == 1: the whole operator (rtt_build_operator).
+ * Otherwise every rank passes the WHOLE raw table; shard `index` of `count`
+ * keeps rows [R index / count, R (index + 1) / count) of the R sorted rows
+ * (rtt_shard_rows) and their rays, with s_ref and scale of the whole table,
+ * so the shards' A x are the whole operator's rows, bit for bit, and the
+ * whole A^T y is the sum over shards of each shard's A^T of its rows.
+ * On a shard, the applies, rtt_probe_info, rtt_gram, rtt_gram_class and
+ * rtt_gram_normal sum over the shard's rows only (the whole operator's value
+ * is the sum over shards); entry points that need every row (order mixing,
+ * the direct age quantile, reach, the rank audit, the solvers) return
+ * RTT_ESTATE.  arm_mask still selects orders: a shard's y holds its own rows
+ * of the selected orders, in order.
+ * Errors: those of rtt_build_operator; RTT_EINVAL for an invalid shard or a
+ * shard with no rows (count > R).
+ */
+rtt_status rtt_build_operator_shard(const rtt_geometry* geom, const rtt_source_grid* grid,
+                                    const rtt_time_grid* time, const rtt_ray_table* table,
+                                    const rtt_options* opt, const rtt_shard* shard, void* stream,
+                                    rtt_op* out);
+
+/*
+ * rtt_shard_rows -- rows [*begin_out, *end_out) that shard `index` of `count`
+ * holds out of n_rows sorted rows (the rows of the stack of Eq. 3):
+ * floor(n_rows index / count) to floor(n_rows (index + 1) / count).  Host
+ * only.
+ * Errors: RTT_EINVAL (null pointer, n_rows < 0, invalid shard).
+ */
+rtt_status rtt_shard_rows(int64_t n_rows, const rtt_shard* shard, int64_t* begin_out,
+                          int64_t* end_out);
 
 /*
  * rtt_op_query -- the sizes, delay ranges and whitening of a built operator

@@ -70,6 +70,12 @@ __global__ void row_index(int64_t n, const unsigned long long* key, const int32_
     }
 }
 
+// out[i] = in[i] - base (row pointers and row indices of a row shard)
+__global__ void rebase_rows(int64_t n, const int32_t* in, int32_t base, int32_t* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[i] - base;
+}
+
 struct PrepArgs {
     int64_t n;
     const int32_t* perm;
@@ -194,12 +200,6 @@ static rtt_status alloc(T** p, size_t n) {
     return RTT_OK;
 }
 
-#define RTT_TRY(x)                  \
-    do {                            \
-        rtt_status _s = (x);        \
-        if (_s != RTT_OK) return _s; \
-    } while (0)
-
 static void free_op(rtt_op_s* op) {
     if (!op) return;
     void* ps[] = {op->row_ptr, op->ray_row, op->node00, op->node01, op->W,     op->W64,
@@ -231,9 +231,17 @@ struct Scratch {
     }
 };
 
+// Rows [lo, hi) of shard `index` of `count` over R rows: contiguous blocks of
+// the (order, pixel)-sorted rows, sizes differing by at most one.
+static void shard_rows(int64_t R, int index, int count, int64_t* lo, int64_t* hi) {
+    *lo = R * (int64_t)index / count;
+    *hi = R * (int64_t)(index + 1) / count;
+}
+
 static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* grid,
                              const rtt_time_grid* time, const rtt_ray_table* tab,
-                             const rtt_options* opt, cudaStream_t st, rtt_op_s* op) {
+                             const rtt_options* opt, const rtt_shard* shard, cudaStream_t st,
+                             rtt_op_s* op) {
     const int64_t E = tab->n_rays;
     // ---- host validation pass (also yields per-order delay ranges) ----
     for (int n = 0; n < 3; ++n) {
@@ -417,14 +425,96 @@ static rtt_status build_impl(const rtt_geometry* geom, const rtt_source_grid* gr
         return RTT_EINVAL;
     }
     op->scale = opt->snr0 / op->s_ref;
+    op->total_rows = R;
+    for (int n = 0; n < 4; ++n) op->total_row_begin[n] = op->row_begin[n];
+    op->shard_index = 0;
+    op->shard_count = 1;
+    op->shard_row_begin = 0;
+    // ---- row shard: keep rows [lo, hi) of the sorted row list and their rays,
+    // which are the sorted rays [row_ptr[lo], row_ptr[hi]); s_ref and the
+    // scale above are those of the whole table ----
+    if (shard && shard->count > 1) {
+        int64_t lo = 0, hi = 0;
+        shard_rows(R, shard->index, shard->count, &lo, &hi);
+        if (hi <= lo) {
+            set_error("shard %d of %d has no rows (%lld rows in the table)", shard->index,
+                      shard->count, (long long)R);
+            return RTT_EINVAL;
+        }
+        int32_t eb[2];
+        RTT_CUDA(cudaMemcpyAsync(&eb[0], op->row_ptr + lo, 4, cudaMemcpyDeviceToHost, st));
+        RTT_CUDA(cudaMemcpyAsync(&eb[1], op->row_ptr + hi, 4, cudaMemcpyDeviceToHost, st));
+        RTT_CUDA(cudaStreamSynchronize(st));
+        const int64_t Rs = hi - lo, e_lo = eb[0], Es = (int64_t)eb[1] - eb[0];
+        int32_t *rp, *rr, *ro, *rpx;
+        RTT_TRY(alloc(&rp, Rs + 1));
+        RTT_TRY(alloc(&rr, Es));
+        RTT_TRY(alloc(&ro, Rs));
+        RTT_TRY(alloc(&rpx, Rs));
+        rebase_rows<<<blocks(Rs + 1), 256, 0, st>>>(Rs + 1, op->row_ptr + lo, (int32_t)e_lo, rp);
+        rebase_rows<<<blocks(Es), 256, 0, st>>>(Es, op->ray_row + e_lo, (int32_t)lo, rr);
+        RTT_CUDA(cudaGetLastError());
+        RTT_CUDA(cudaMemcpyAsync(ro, op->row_order + lo, Rs * 4, cudaMemcpyDeviceToDevice, st));
+        RTT_CUDA(cudaMemcpyAsync(rpx, op->row_pixel + lo, Rs * 4, cudaMemcpyDeviceToDevice, st));
+        RTT_CUDA(cudaStreamSynchronize(st));
+        void* old_arrays[] = {op->row_ptr, op->ray_row, op->row_order, op->row_pixel, op->node00,
+                              op->node01,  op->W,       op->W64,       op->K0,         op->F0,
+                              op->F64,     op->r,       op->phi,       op->delay,      op->weight,
+                              op->thr};
+        for (void* q : old_arrays) cudaFree(q);
+        op->row_ptr = rp;
+        op->ray_row = rr;
+        op->row_order = ro;
+        op->row_pixel = rpx;
+        op->node00 = op->node01 = op->K0 = op->F0 = nullptr;
+        op->W = nullptr;
+        op->W64 = op->F64 = op->r = op->phi = op->delay = op->weight = op->thr = nullptr;
+        RTT_TRY(alloc(&op->r, Es));
+        RTT_TRY(alloc(&op->phi, Es));
+        RTT_TRY(alloc(&op->delay, Es));
+        RTT_TRY(alloc(&op->weight, Es));
+        RTT_TRY(alloc(&op->thr, Es));
+        RTT_TRY(alloc(&op->node00, Es));
+        RTT_TRY(alloc(&op->node01, Es));
+        RTT_TRY(alloc(&op->W, Es));
+        RTT_TRY(alloc(&op->W64, 4 * Es));
+        RTT_TRY(alloc(&op->K0, Es));
+        RTT_TRY(alloc(&op->F0, Es));
+        RTT_TRY(alloc(&op->F64, Es));
+        // order blocks of the shard: the global blocks clipped to [lo, hi)
+        for (int n = 0; n < 4; ++n) {
+            const int64_t b = op->row_begin[n] - lo;
+            op->row_begin[n] = b < 0 ? 0 : (b > Rs ? Rs : b);
+        }
+        op->n_rows = Rs;
+        op->n_rays = Es;
+        op->shard_index = shard->index;
+        op->shard_count = shard->count;
+        op->shard_row_begin = lo;
+        pa.n = Es;
+        pa.perm = perm + e_lo;
+        pa.node00 = op->node00;
+        pa.node01 = op->node01;
+        pa.W = op->W;
+        pa.W64 = op->W64;
+        pa.K0 = op->K0;
+        pa.F0 = op->F0;
+        pa.F64 = op->F64;
+        pa.r_s = op->r;
+        pa.phi_s = op->phi;
+        pa.delay_s = op->delay;
+        pa.weight_s = op->weight;
+        pa.thr_s = op->thr;
+    }
     // second pass with the whitening scale folded into the corner weights
     pa.scale = op->scale;
-    prep_rays<<<blocks(E), 256, 0, st>>>(pa);
+    prep_rays<<<blocks(pa.n), 256, 0, st>>>(pa);
     RTT_CUDA(cudaGetLastError());
 
     // ---- the forward's source-cell row order: within each order, rows by the
     // Morton index of their first ray's cell (i0, j0) (ties by row) ----
     {
+        const int64_t R = op->n_rows, E = op->n_rays;
         std::vector<int32_t> rp(R + 1), n00(E);
         RTT_CUDA(cudaMemcpyAsync(rp.data(), op->row_ptr, (R + 1) * 4, cudaMemcpyDeviceToHost, st));
         RTT_CUDA(cudaMemcpyAsync(n00.data(), op->node00, E * 4, cudaMemcpyDeviceToHost, st));
@@ -545,14 +635,19 @@ const char* rtt_last_error(void) { return g_last_error.c_str(); }
 
 int rtt_abi_version(void) { return RTT_ABI_VERSION; }
 
-rtt_status rtt_build_operator(const rtt_geometry* geom, const rtt_source_grid* grid,
-                              const rtt_time_grid* time, const rtt_ray_table* table,
-                              const rtt_options* opt, void* stream, rtt_op* out) {
+rtt_status rtt_build_operator_shard(const rtt_geometry* geom, const rtt_source_grid* grid,
+                                    const rtt_time_grid* time, const rtt_ray_table* table,
+                                    const rtt_options* opt, const rtt_shard* shard, void* stream,
+                                    rtt_op* out) {
     if (!geom || !grid || !time || !table || !opt || !out) {
         set_error("null argument");
         return RTT_EINVAL;
     }
     *out = nullptr;
+    if (shard && (shard->count < 1 || shard->index < 0 || shard->index >= shard->count)) {
+        set_error("shard index %d of %d invalid", shard->index, shard->count);
+        return RTT_EINVAL;
+    }
     if (table->n_rays < 1 || table->n_rays > (1ll << 29) || !table->order || !table->pixel ||
         !table->r || !table->phi || !table->delay || !table->weight || !table->throughput) {
         set_error("invalid ray table (n_rays=%lld)", (long long)table->n_rays);
@@ -572,12 +667,29 @@ rtt_status rtt_build_operator(const rtt_geometry* geom, const rtt_source_grid* g
         set_error("host allocation failed");
         return RTT_ENOMEM;
     }
-    rtt_status s = build_impl(geom, grid, time, table, opt, (cudaStream_t)stream, op);
+    rtt_status s = build_impl(geom, grid, time, table, opt, shard, (cudaStream_t)stream, op);
     if (s != RTT_OK) {
         free_op(op);
         return s;
     }
     *out = op;
+    return RTT_OK;
+}
+
+rtt_status rtt_build_operator(const rtt_geometry* geom, const rtt_source_grid* grid,
+                              const rtt_time_grid* time, const rtt_ray_table* table,
+                              const rtt_options* opt, void* stream, rtt_op* out) {
+    return rtt_build_operator_shard(geom, grid, time, table, opt, nullptr, stream, out);
+}
+
+rtt_status rtt_shard_rows(int64_t n_rows, const rtt_shard* shard, int64_t* begin_out,
+                          int64_t* end_out) {
+    if (!shard || !begin_out || !end_out || n_rows < 0 || shard->count < 1 ||
+        shard->index < 0 || shard->index >= shard->count) {
+        set_error("invalid shard (n_rows=%lld)", (long long)n_rows);
+        return RTT_EINVAL;
+    }
+    shard_rows(n_rows, shard->index, shard->count, begin_out, end_out);
     return RTT_OK;
 }
 
@@ -598,6 +710,12 @@ rtt_status rtt_op_query(rtt_op op, rtt_op_info* o) {
     o->n_frames = op->time.n_frames;
     o->s_ref = op->s_ref;
     o->scale = op->scale;
+    o->total_rows = op->total_rows;
+    for (int n = 0; n < 3; ++n)
+        o->total_rows_per_order[n] = op->total_row_begin[n + 1] - op->total_row_begin[n];
+    o->shard_row_begin = op->shard_row_begin;
+    o->shard_index = op->shard_index;
+    o->shard_count = op->shard_count;
     return RTT_OK;
 }
 

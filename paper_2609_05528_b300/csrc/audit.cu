@@ -74,6 +74,7 @@ extern "C" rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double*
         set_error("invalid rank-audit arguments");
         return RTT_EINVAL;
     }
+    for (int g = 0; g < n_ops; ++g) RTT_TRY(whole_only(ops[g], "the rank audit"));
     const int nb = n_ops * n_arms;
     double *G = nullptr, *V = nullptr;
     cudaError_t e = cudaMalloc(&G, (size_t)nb * d * d * 8);

@@ -321,6 +321,7 @@ static rtt_status gram_normal_impl(rtt_op op, int arm_mask, int mix_mode, const 
         set_error("invalid gram arguments (d=%d)", d);
         return RTT_EINVAL;
     }
+    if (mix_mode) RTT_TRY(whole_only(op, "order mixing"));
     ArmSeg seg;
     rtt_status s = make_seg(op, arm_mask, &seg);
     if (s != RTT_OK) return s;

@@ -213,6 +213,9 @@ static int grid_cap(int64_t n) { return (int)std::min<int64_t>(std::max<int64_t>
 
 // the arm's rows grouped by pixel (host build on first use for an arm mask)
 rtt_status mix_prepare(rtt_op_s* op, const ArmSeg& seg) {
+    // a pixel's rows of different orders lie in different order blocks, so a
+    // row shard does not hold whole pixel groups
+    RTT_TRY(whole_only(op, "order mixing"));
     auto& m = op->mix;
     if (m.arm_mask == seg.mask && m.grp_ptr) return RTT_OK;
     const int64_t R = op->n_rows, Ra = seg.total;
@@ -368,6 +371,7 @@ static rtt_status mix_args(rtt_op op, int arm_mask, int mode, const void* a, con
         set_error("invalid mix arguments (mode=%d batch=%d)", mode, batch);
         return RTT_EINVAL;
     }
+    RTT_TRY(whole_only(op, "order mixing"));
     return make_seg(op, arm_mask, seg);
 }
 

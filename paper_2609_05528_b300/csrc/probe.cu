@@ -354,6 +354,7 @@ extern "C" rtt_status rtt_direct_age_quantile(rtt_op op, double q, double* out, 
         set_error("invalid quantile arguments");
         return RTT_EINVAL;
     }
+    RTT_TRY(whole_only(op, "the direct age quantile"));
     cudaStream_t st = (cudaStream_t)stream;
     // direct rays are the rays of rows [0, row_begin[1]): rays [0, row_ptr[row_begin[1]])
     int32_t n0 = 0;
@@ -430,6 +431,7 @@ extern "C" rtt_status rtt_reach(rtt_op op, int arm_mask, int n_ages, const doubl
         set_error("invalid reach arguments");
         return RTT_EINVAL;
     }
+    RTT_TRY(whole_only(op, "reach"));
     const double thr = op->opt.rho * op->opt.rho;
     const double to_min = op->time.t0;
     const double to_max = op->time.t0 + op->time.cadence * (op->time.n_frames - 1);

@@ -8,6 +8,13 @@
 
 #include "rtt.h"
 
+// return the status of x from the calling function unless it is RTT_OK
+#define RTT_TRY(x)                   \
+    do {                             \
+        rtt_status _s = (x);         \
+        if (_s != RTT_OK) return _s; \
+    } while (0)
+
 namespace rtt {
 
 // 24 fractional bits for the per-ray hat offset: the fraction of every
@@ -65,6 +72,13 @@ struct rtt_op_s {
     rtt_options opt;
     int64_t n_rays = 0;
     int64_t n_rows = 0;
+    // row shard (rtt_build_operator_shard): this operator holds rows
+    // [shard_row_begin, shard_row_begin + n_rows) of the whole table's total_rows
+    int64_t total_rows = 0;
+    int64_t total_row_begin[4] = {0, 0, 0, 0};  // row_begin of the whole table
+    int64_t shard_row_begin = 0;
+    int32_t shard_index = 0;
+    int32_t shard_count = 1;
     int64_t row_begin[4] = {0, 0, 0, 0};  // rows of order n: [row_begin[n], row_begin[n+1])
     int32_t n_nodes = 0;
     int64_t frame_D = 0;  // (cadence / hat_step) * 2^24, exact integer
@@ -136,6 +150,17 @@ struct rtt_op_s {
 };
 
 namespace rtt {
+// RTT_ESTATE for a row shard at entry points that need every row of the
+// operator (order mixing, quantiles, reach, audit, solvers)
+inline rtt_status whole_only(const rtt_op_s* op, const char* what) {
+    if (op && op->shard_count > 1) {
+        set_error("%s needs the whole operator (this is row shard %d of %d)", what,
+                  op->shard_index, op->shard_count);
+        return RTT_ESTATE;
+    }
+    return RTT_OK;
+}
+
 // order mixing (mix.cu): pixel groups of an arm, mixed row count, and the
 // collapse (adjoint = false: arm rows -> mixed rows) or its adjoint over
 // `cols` = n_frames * batch values per row

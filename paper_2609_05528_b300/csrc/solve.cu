@@ -186,6 +186,7 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
         set_error("invalid ridge arguments");
         return RTT_EINVAL;
     }
+    RTT_TRY(whole_only(op, "the ridge solver"));
     for (int l = 0; l < n_lambda; ++l)
         if (!(lambdas[l] >= 0.0) || !std::isfinite(lambdas[l])) {
             set_error("lambda[%d] = %g must be finite and >= 0", l, lambdas[l]);
@@ -317,6 +318,7 @@ extern "C" rtt_status rtt_solve_tsvd(rtt_op op, int arm_mask, const double* Q, i
         set_error("invalid tsvd arguments (d=%d rank=%d n_rhs=%d)", d, rank, n_rhs);
         return RTT_EINVAL;
     }
+    RTT_TRY(whole_only(op, "the TSVD solver"));
     for (int k = 0; k < rank; ++k)
         if (!(evals_host[k] > 0.0)) {
             set_error("tsvd: eigenvalue %d = %g is not positive", k, evals_host[k]);

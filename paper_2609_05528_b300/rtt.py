@@ -15,6 +15,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "librtt.so")
 _LIB = None
+ABI_VERSION = 2  # RTT_ABI_VERSION of include/rtt.h
 
 i8p = ctypes.POINTER(ctypes.c_int8)
 i32p = ctypes.POINTER(ctypes.c_int32)
@@ -63,7 +64,14 @@ class OpInfo(ctypes.Structure):
                 ("rows_per_order", ctypes.c_int64 * 3), ("n_nodes", ctypes.c_int64),
                 ("n_hats", ctypes.c_int32), ("n_frames", ctypes.c_int32),
                 ("s_ref", ctypes.c_double), ("scale", ctypes.c_double),
-                ("delay_min", ctypes.c_double * 3), ("delay_max", ctypes.c_double * 3)]
+                ("delay_min", ctypes.c_double * 3), ("delay_max", ctypes.c_double * 3),
+                ("total_rows", ctypes.c_int64), ("total_rows_per_order", ctypes.c_int64 * 3),
+                ("shard_row_begin", ctypes.c_int64),
+                ("shard_index", ctypes.c_int32), ("shard_count", ctypes.c_int32)]
+
+
+class Shard(ctypes.Structure):
+    _fields_ = [("index", ctypes.c_int32), ("count", ctypes.c_int32)]
 
 
 class ReachResult(ctypes.Structure):
@@ -114,6 +122,12 @@ _SIGS = {
     "rtt_build_operator": (ctypes.c_int, [ctypes.POINTER(Geometry), ctypes.POINTER(SourceGrid),
                                           ctypes.POINTER(TimeGrid), ctypes.POINTER(RayTable),
                                           ctypes.POINTER(Options), vp, ctypes.POINTER(vp)]),
+    "rtt_build_operator_shard": (ctypes.c_int, [ctypes.POINTER(Geometry), ctypes.POINTER(SourceGrid),
+                                                ctypes.POINTER(TimeGrid), ctypes.POINTER(RayTable),
+                                                ctypes.POINTER(Options), ctypes.POINTER(Shard), vp,
+                                                ctypes.POINTER(vp)]),
+    "rtt_shard_rows": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(Shard),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "rtt_op_query": (ctypes.c_int, [vp, ctypes.POINTER(OpInfo)]),
     "rtt_arm_rows": (ctypes.c_int, [vp, ctypes.c_int, i64p]),
     "rtt_op_status": (ctypes.c_int, [vp, i32p, ctypes.c_int, vp]),
@@ -184,6 +198,11 @@ def lib():
             fn = getattr(L, name)
             fn.restype = res
             fn.argtypes = args
+        # the structs below mirror rtt.h of this ABI version; a library of
+        # another version would write past them
+        if L.rtt_abi_version() != ABI_VERSION:
+            raise RuntimeError(f"{LIB_PATH} has ABI version {L.rtt_abi_version()}, the binding "
+                               f"expects {ABI_VERSION}: rebuild it")
         _LIB = L
     return _LIB
 
@@ -275,7 +294,11 @@ def rtt_trace_rays(spin, incl_deg, grid, samples, stream=None):
 class Operator:
     """Owns an rtt_op handle (rtt_build_operator / rtt_destroy)."""
 
-    def __init__(self, workload, table, snr0: float = 100.0, rho: float = 1.0, stream=None):
+    def __init__(self, workload, table, snr0: float = 100.0, rho: float = 1.0, stream=None,
+                 shard=None):
+        """shard = (index, count): rtt_build_operator_shard, the block of rows
+        `index` of `count` with the whole table's whitening (the whole table is
+        passed on every rank)."""
         L = lib()
         self.workload = workload
         g, t = workload.grid, workload.time
@@ -294,9 +317,12 @@ class Operator:
         tg = TimeGrid(t.n_frames, t.t0, t.cadence, t.n_hats, t.hat_step, t.t_end)
         opt = Options(snr0, rho)
         h = ctypes.c_void_p()
-        check(L.rtt_build_operator(ctypes.byref(geo), ctypes.byref(sg), ctypes.byref(tg),
-                                   ctypes.byref(rt), ctypes.byref(opt), _stream(stream),
-                                   ctypes.byref(h)), "rtt_build_operator")
+        sh = Shard(int(shard[0]), int(shard[1])) if shard is not None else None
+        check(L.rtt_build_operator_shard(ctypes.byref(geo), ctypes.byref(sg), ctypes.byref(tg),
+                                         ctypes.byref(rt), ctypes.byref(opt),
+                                         ctypes.byref(sh) if sh is not None else None,
+                                         _stream(stream), ctypes.byref(h)),
+              "rtt_build_operator_shard")
         self.handle = h
         self._keep = None
         info = OpInfo()
@@ -307,6 +333,9 @@ class Operator:
         self.n_frames = int(info.n_frames)
         self.scale = float(info.scale)
         self.s_ref = float(info.s_ref)
+        self.shard_index, self.shard_count = int(info.shard_index), int(info.shard_count)
+        self.shard_row_begin, self.total_rows = int(info.shard_row_begin), int(info.total_rows)
+        self.total_rows_per_order = tuple(int(v) for v in info.total_rows_per_order)
 
     def arm_rows(self, arm_mask: int = 7) -> int:
         n = ctypes.c_int64(0)
@@ -572,6 +601,15 @@ def gemm_tn(A, B, stream=None):
                                 ctypes.c_void_p(B.data_ptr()), n, ctypes.c_void_p(C.data_ptr()), n,
                                 _stream(stream)), "rtt_gemm_tn_f64")
     return C
+
+
+def shard_rows(n_rows: int, index: int, count: int):
+    """rtt_shard_rows: rows [begin, end) of row shard `index` of `count`."""
+    b, e = ctypes.c_int64(0), ctypes.c_int64(0)
+    sh = Shard(int(index), int(count))
+    check(lib().rtt_shard_rows(int(n_rows), ctypes.byref(sh), ctypes.byref(b), ctypes.byref(e)),
+          "rtt_shard_rows")
+    return int(b.value), int(e.value)
 
 
 def rank_from_eigenvalues(evals, rho: float = 1.0):

@@ -35,7 +35,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_status_strings(L):
-    assert L.rtt_abi_version() == 1
+    assert L.rtt_abi_version() == rtt.ABI_VERSION == 2
     assert L.rtt_error_string(0) == b"ok"
     assert L.rtt_error_string(-1) == b"invalid argument"
 
