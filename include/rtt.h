@@ -130,6 +130,8 @@ typedef struct {
     int64_t shard_row_begin; /* first row of this operator in the whole table */
     int32_t shard_index;     /* 0 and 1 unless built by rtt_build_operator_shard */
     int32_t shard_count;
+    int32_t weight_precision; /* RTT_WEIGHTS_FP32 or RTT_WEIGHTS_BF16 */
+    int32_t reserved;
 } rtt_op_info;
 
 /* Row shard: block `index` of `count` of the (order, pixel)-sorted rows. */
@@ -246,6 +248,22 @@ rtt_status rtt_build_operator_shard(const rtt_geometry* geom, const rtt_source_g
                                     const rtt_time_grid* time, const rtt_ray_table* table,
                                     const rtt_options* opt, const rtt_shard* shard, void* stream,
                                     rtt_op* out);
+
+/*
+ * rtt_set_weight_precision -- precision of the corner weights the FP32
+ * applies use (Eq. 2 bilinear weights times the whitened ray weight of
+ * Eq. 16 and the scale of Eq. 18; no counterpart in the paper, which works in
+ * FP64).  RTT_WEIGHTS_FP32 (the default): each weight is its FP64 value
+ * rounded to FP32.  RTT_WEIGHTS_BF16: that FP32 value rounded on to BF16
+ * (nearest even); the fast kernels then read an 8-byte BF16 copy per ray
+ * instead of 16 bytes, and every kernel variant computes the same operator
+ * bit for bit.  The FP64 applies always use the FP64 weights.  Synchronises
+ * `stream`.
+ * Errors: RTT_EINVAL (null op, unknown precision), RTT_ENOMEM, RTT_ECUDA.
+ */
+#define RTT_WEIGHTS_FP32 0
+#define RTT_WEIGHTS_BF16 1
+rtt_status rtt_set_weight_precision(rtt_op op, int precision, void* stream);
 
 /*
  * rtt_shard_rows -- rows [*begin_out, *end_out) that shard `index` of `count`

@@ -86,10 +86,12 @@ def lib():
                                     ctypes.c_double, dp]
         L.orc_apply_A.restype = None
         L.orc_apply_A.argtypes = [gp, ctypes.c_long, i64, dp, dp, dp, dp, ctypes.c_double,
-                                  ctypes.c_int, dp, dp]
+                                  ctypes.c_int, ctypes.c_int, dp, dp]
         L.orc_apply_AT.restype = None
         L.orc_apply_AT.argtypes = [gp, ctypes.c_long, i64, dp, dp, dp, dp, ctypes.c_double,
-                                   ctypes.c_int, dp, dp]
+                                   ctypes.c_int, ctypes.c_int, dp, dp]
+        L.orc_round_bf16.restype = ctypes.c_double
+        L.orc_round_bf16.argtypes = [ctypes.c_double]
         L.orc_set_threads.restype = None
         L.orc_set_threads.argtypes = [ctypes.c_int]
         L.orc_max_threads.restype = ctypes.c_int
@@ -405,10 +407,17 @@ def scale(table: Table, snr0: float = 100.0) -> float:
     return snr0 / s_ref(table)
 
 
-def apply_A(w, table: Table, x: np.ndarray, scl: float = 1.0) -> np.ndarray:
+def round_bf16(v: float) -> float:
+    """The oracle's BF16 rounding of a weight: to the nearest float, then to
+    the nearest BF16 (ties to even)."""
+    return float(lib().orc_round_bf16(float(v)))
+
+
+def apply_A(w, table: Table, x: np.ndarray, scl: float = 1.0, bf16: bool = False) -> np.ndarray:
     """y[row][f][b] = scl * sum_{e in row} w_e sum_c bil_c sum_k B_k(t_o(f) -
     Delta_e) x[node_c][k][b] (Sec. 3.1 Eq. 2-3; the row action of Eq. 47).
-    x: [S, K, B] or [S, K]."""
+    x: [S, K, B] or [S, K].  bf16: each corner weight scl w_e bil_c rounded
+    to BF16 (the GPU tables' BF16-weight option)."""
     squeeze = x.ndim == 2
     xx = _c64(x[..., None] if squeeze else x)
     B = xx.shape[-1]
@@ -417,12 +426,13 @@ def apply_A(w, table: Table, x: np.ndarray, scl: float = 1.0) -> np.ndarray:
                       np.ascontiguousarray(table.row_ptr, np.int64).ctypes.data_as(
                           ctypes.POINTER(ctypes.c_int64)),
                       _dp(_c64(table.r)), _dp(_c64(table.phi)), _dp(_c64(table.delay)),
-                      _dp(_c64(table.weight)), scl, B, _dp(xx), _dp(y))
+                      _dp(_c64(table.weight)), scl, int(bool(bf16)), B, _dp(xx), _dp(y))
     return y[..., 0] if squeeze else y
 
 
-def apply_AT(w, table: Table, y: np.ndarray, scl: float = 1.0) -> np.ndarray:
-    """Exact transpose of apply_A (Sec. 5: explicit adjoint action)."""
+def apply_AT(w, table: Table, y: np.ndarray, scl: float = 1.0, bf16: bool = False) -> np.ndarray:
+    """Exact transpose of apply_A (Sec. 5: explicit adjoint action), with
+    the same weights (bf16 as in apply_A)."""
     squeeze = y.ndim == 2
     yy = _c64(y[..., None] if squeeze else y)
     B = yy.shape[-1]
@@ -431,7 +441,7 @@ def apply_AT(w, table: Table, y: np.ndarray, scl: float = 1.0) -> np.ndarray:
                        np.ascontiguousarray(table.row_ptr, np.int64).ctypes.data_as(
                            ctypes.POINTER(ctypes.c_int64)),
                        _dp(_c64(table.r)), _dp(_c64(table.phi)), _dp(_c64(table.delay)),
-                       _dp(_c64(table.weight)), scl, B, _dp(yy), _dp(x))
+                       _dp(_c64(table.weight)), scl, int(bool(bf16)), B, _dp(yy), _dp(x))
     return x[..., 0] if squeeze else x
 
 

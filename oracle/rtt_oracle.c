@@ -570,6 +570,47 @@ static void bilinear(const orc_grid* g, double r, double phi, long node[4], doub
     node[3] = (long)(i0 + 1) * g->n_phi + j1; wt[3] = fr * fp;
 }
 
+/* BF16-weight tables (a precision option of the GPU tables, not of the
+   paper): each corner weight W_c = (scale w) times its two bilinear factors,
+   multiplied in the order (scale w) * a_c * b_c, is rounded to the nearest
+   float and then to the nearest BF16 (8 significant bits, ties to even).   */
+double orc_round_bf16(double v) {
+    float f = (float)v;
+    uint32_t u;
+    memcpy(&u, &f, sizeof u);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    memcpy(&f, &u, sizeof f);
+    return (double)f;
+}
+
+/* corner weights of one ray: wt[c] = scale w bil_c (FP64), or the BF16 weights */
+static void corner_weights(const orc_grid* g, double r, double phi, double sw, int bf16,
+                           long node[4], double wt[4]) {
+    double bw[4];
+    bilinear(g, r, phi, node, bw);
+    if (!bf16) {
+        for (int c = 0; c < 4; ++c) wt[c] = sw * bw[c];
+        return;
+    }
+    /* the two factors of each corner, recovered from the stencil */
+    double rho = (log(r) - log(g->r_in)) / (log(g->r_out) - log(g->r_in)) * (g->n_r - 1);
+    int i0 = (int)floor(rho);
+    if (i0 < 0) i0 = 0;
+    if (i0 > g->n_r - 2) i0 = g->n_r - 2;
+    const double fr = rho - i0;
+    double ph = phi / (2.0 * M_PI) * g->n_phi;
+    ph = fmod(ph, (double)g->n_phi);
+    if (ph < 0.0) ph += g->n_phi;
+    int j0 = (int)floor(ph);
+    if (j0 >= g->n_phi) j0 = g->n_phi - 1;
+    const double fp = ph - j0;
+    wt[0] = orc_round_bf16(sw * (1.0 - fr) * (1.0 - fp));
+    wt[1] = orc_round_bf16(sw * fr * (1.0 - fp));
+    wt[2] = orc_round_bf16(sw * (1.0 - fr) * fp);
+    wt[3] = orc_round_bf16(sw * fr * fp);
+}
+
 static double hat(const orc_grid* g, int k, double t) {
     const double tk = g->t_end - g->hat_step * k;
     const double v = 1.0 - fabs(t - tk) / g->hat_step;
@@ -589,15 +630,15 @@ static void hat_range(const orc_grid* g, double t, int* klo, int* khi) {
    of one pixel of one order) that form the pixel-average datum of that row. */
 void orc_apply_A(const orc_grid* g, long n_rows, const int64_t* row_ptr, const double* r,
                      const double* phi, const double* delay, const double* w, double scale,
-                     int B, const double* x, double* y) {
+                     int bf16, int B, const double* x, double* y) {
     const int T = g->n_frames, K = g->n_hats;
     memset(y, 0, sizeof(double) * (size_t)n_rows * T * B);
 #pragma omp parallel for schedule(dynamic, 32)
     for (long row = 0; row < n_rows; ++row) {
         for (long e = row_ptr[row]; e < row_ptr[row + 1]; ++e) {
             long node[4];
-            double bw[4];
-            bilinear(g, r[e], phi[e], node, bw);
+            double wt[4];
+            corner_weights(g, r[e], phi[e], scale * w[e], bf16, node, wt);
             for (int f = 0; f < T; ++f) {
                 const double t = g->t0 + g->cadence * f - delay[e];
                 int klo, khi;
@@ -607,7 +648,7 @@ void orc_apply_A(const orc_grid* g, long n_rows, const int64_t* row_ptr, const d
                     for (int k = klo; k <= khi; ++k) {
                         const double hv = hat(g, k, t);
                         if (hv == 0.0) continue;
-                        const double coef = scale * w[e] * bw[c] * hv;
+                        const double coef = wt[c] * hv;
                         const double* xx = x + ((size_t)node[c] * K + k) * B;
                         for (int b = 0; b < B; ++b) yy[b] += coef * xx[b];
                     }
@@ -622,7 +663,7 @@ void orc_apply_A(const orc_grid* g, long n_rows, const int64_t* row_ptr, const d
    is accumulated by one thread in one fixed sequential order. */
 void orc_apply_AT(const orc_grid* g, long n_rows, const int64_t* row_ptr, const double* r,
                   const double* phi, const double* delay, const double* w, double scale,
-                  int B, const double* y, double* x) {
+                  int bf16, int B, const double* y, double* x) {
     const int T = g->n_frames, K = g->n_hats;
     const long S = (long)g->n_r * g->n_phi;
     memset(x, 0, sizeof(double) * (size_t)S * K * B);
@@ -632,15 +673,15 @@ void orc_apply_AT(const orc_grid* g, long n_rows, const int64_t* row_ptr, const 
         for (long row = 0; row < n_rows; ++row) {
             for (long e = row_ptr[row]; e < row_ptr[row + 1]; ++e) {
                 long node[4];
-                double bw[4];
-                bilinear(g, r[e], phi[e], node, bw);
+                double wt[4];
+                corner_weights(g, r[e], phi[e], scale * w[e], bf16, node, wt);
                 for (int f = 0; f < T; ++f) {
                     const double t = g->t0 + g->cadence * f - delay[e];
                     const double hv = hat(g, kk, t);
                     if (hv == 0.0) continue;
                     const double yv = y[((size_t)row * T + f) * B + b];
                     for (int c = 0; c < 4; ++c)
-                        x[((size_t)node[c] * K + kk) * B + b] += scale * w[e] * bw[c] * hv * yv;
+                        x[((size_t)node[c] * K + kk) * B + b] += wt[c] * hv * yv;
                 }
             }
         }

@@ -50,6 +50,7 @@ struct CellArgs {
     const int32_t* c_h0;     // general kernel: hat base K0; TMA kernel: fbase (below)
     const int32_t* c_h1;     // general kernel: 24-bit fraction F0; TMA kernel: phase r0
     const float4* c_W;       // corner weights (whitening scale included)
+    const uint2* c_W16;      // their BF16 copy (weights of BF16 precision), or null
     const double* c_W64;     // [4 per ray] the same in FP64
     const double* c_F64;     // exact hat fraction
     const int32_t* seg_ray;  // [n_seg + 1] segment -> positions in the cell order
@@ -393,7 +394,7 @@ adj_cell_tma_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) 
         const int f_lo = fbase - P * (kg0 + HATS - 1);  // first frame of the item's last hat
         c.R4 = f_lo >> LGF;                              // floor division (f_lo may be < 0)
         c.sbase = fbase - P * kg0 - c.R4 * F;            // >= 0
-        c.w = a.c_W[s.pos];
+        c.w = corner_weights(a.c_W, a.c_W16, s.pos);
     };
     auto issue = [&](const Step& s, const Cp& c, uint32_t b) {
         if (lane != 0) return;
@@ -520,7 +521,7 @@ adj_cell_gen_kernel(const CellArgs a, uint32_t buf_bytes, int vec_stage) {
             const double2 v0 = p[0], v1 = p[1];
             c.w[0] = v0.x; c.w[1] = v0.y; c.w[2] = v1.x; c.w[3] = v1.y;
         } else {
-            const float4 v = a.c_W[s.pos];
+            const float4 v = corner_weights(a.c_W, a.c_W16, s.pos);
             c.w[0] = v.x; c.w[1] = v.y; c.w[2] = v.z; c.w[3] = v.w;
             c.F64 = 0.0;
         }
@@ -668,7 +669,7 @@ adj_cell_per_kernel(const CellArgs a, uint32_t buf_bytes, int vec_stage) {
             const double2 v0 = p[0], v1 = p[1];
             c.w[0] = v0.x; c.w[1] = v0.y; c.w[2] = v1.x; c.w[3] = v1.y;
         } else {
-            const float4 v = a.c_W[s.pos];
+            const float4 v = corner_weights(a.c_W, a.c_W16, s.pos);
             c.w[0] = v.x; c.w[1] = v.y; c.w[2] = v.z; c.w[3] = v.w;
         }
     };
@@ -1068,6 +1069,7 @@ static CellArgs cell_args(const rtt_op_s* op, const void* y, int B, const ArmSeg
     a.c_h0 = op->c_K0;
     a.c_h1 = op->c_F0;
     a.c_W = op->c_W;
+    a.c_W16 = op->c_W16;
     a.c_W64 = op->c_W64;
     a.c_F64 = op->c_F64;
     a.seg_ray = op->seg_ray;

@@ -1,5 +1,6 @@
 // C ABI entry points: operator construction (table preparation on the
 // device), queries, and the forward / adjoint applies.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -68,6 +69,22 @@ __global__ void row_index(int64_t n, const unsigned long long* key, const int32_
         row_pixel[row] = (int32_t)(uint32_t)(key[i] & 0xffffffffull);
         atomicAdd(&order_count[ord], 1u);  // integer counts: order independent
     }
+}
+
+// FP32 corner weights from the FP64 ones (rounded to nearest), optionally
+// rounded on to BF16 (nearest even) with the packed BF16 copy
+__global__ void set_weights(int64_t n, const double* __restrict__ W64, int bf16, float4* W, uint2* W16) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float c[4];
+    for (int q = 0; q < 4; ++q) {
+        c[q] = (float)W64[4 * i + q];
+        if (bf16) c[q] = __bfloat162float(__float2bfloat16_rn(c[q]));
+    }
+    W[i] = make_float4(c[0], c[1], c[2], c[3]);
+    if (bf16)
+        W16[i] = make_uint2((__float_as_uint(c[1]) & 0xffff0000u) | (__float_as_uint(c[0]) >> 16),
+                            (__float_as_uint(c[3]) & 0xffff0000u) | (__float_as_uint(c[2]) >> 16));
 }
 
 // out[i] = in[i] - base (row pointers and row indices of a row shard)
@@ -207,6 +224,7 @@ static void free_op(rtt_op_s* op) {
                   op->thr,     op->row_order, op->c_row, op->c_col, op->c_K0, op->c_F0, op->c_fb, op->c_r0,
                   op->c_W,     op->c_W64,   op->c_F64, op->seg_ray, op->seg_col, op->seg_ncol,
                   op->seg_rec, op->gslot,   op->adj_ctr, op->cpart, op->row_sched,
+                  op->W16,     op->c_W16,
                   op->dev_status, op->rscratch, op->row_pixel, op->mix.grp_ptr,
                   op->mix.grp_rows, op->mix.row_grp, op->mix.inv32, op->mix.inv64,
                   op->mix.part, op->phi};
@@ -682,6 +700,32 @@ rtt_status rtt_build_operator(const rtt_geometry* geom, const rtt_source_grid* g
     return rtt_build_operator_shard(geom, grid, time, table, opt, nullptr, stream, out);
 }
 
+rtt_status rtt_set_weight_precision(rtt_op op, int precision, void* stream) {
+    if (!op || (precision != RTT_WEIGHTS_FP32 && precision != RTT_WEIGHTS_BF16)) {
+        set_error("invalid weight precision %d", precision);
+        return RTT_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t E = op->n_rays;
+    const bool bf16 = precision == RTT_WEIGHTS_BF16;
+    if (bf16 && !op->W16) {
+        RTT_TRY(alloc(&op->W16, E));
+        RTT_TRY(alloc(&op->c_W16, E));
+    }
+    const int nb = (int)((E + 255) / 256);
+    set_weights<<<nb, 256, 0, st>>>(E, op->W64, bf16, op->W, op->W16);
+    set_weights<<<nb, 256, 0, st>>>(E, op->c_W64, bf16, op->c_W, op->c_W16);
+    RTT_CUDA(cudaGetLastError());
+    RTT_CUDA(cudaStreamSynchronize(st));
+    if (!bf16 && op->W16) {
+        cudaFree(op->W16);
+        cudaFree(op->c_W16);
+        op->W16 = op->c_W16 = nullptr;
+    }
+    op->weight_precision = precision;
+    return RTT_OK;
+}
+
 rtt_status rtt_shard_rows(int64_t n_rows, const rtt_shard* shard, int64_t* begin_out,
                           int64_t* end_out) {
     if (!shard || !begin_out || !end_out || n_rows < 0 || shard->count < 1 ||
@@ -711,6 +755,7 @@ rtt_status rtt_op_query(rtt_op op, rtt_op_info* o) {
     o->s_ref = op->s_ref;
     o->scale = op->scale;
     o->total_rows = op->total_rows;
+    o->weight_precision = op->weight_precision;
     for (int n = 0; n < 3; ++n)
         o->total_rows_per_order[n] = op->total_row_begin[n + 1] - op->total_row_begin[n];
     o->shard_row_begin = op->shard_row_begin;

@@ -65,6 +65,7 @@ struct ApplyArgs {
     const int32_t* node00;
     const int32_t* node01;
     const float4* W;
+    const uint2* W16;  // BF16 copy of W (weights of BF16 precision), or null
     const double* W64;
     const int32_t* K0;
     const int32_t* F0;
@@ -94,7 +95,7 @@ __device__ __forceinline__ void load_w(const ApplyArgs<T>& a, int e, T w[4]);
 
 template <>
 __device__ __forceinline__ void load_w<float>(const ApplyArgs<float>& a, int e, float w[4]) {
-    const float4 v = a.W[e];
+    const float4 v = corner_weights(a.W, a.W16, e);
     w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
 }
 template <>
@@ -456,7 +457,7 @@ fwd4_kernel(const ApplyArgs<float> a) {
             // lanes 0 and 31 also need the hats k_top + 1 and k_top - 32
             const int k_ext = lane == 0 ? k_top + 1 : k_top - 32;
             const bool ext = lane == 0 || lane == 31;
-            const float4 wv = a.W[e];
+            const float4 wv = corner_weights(a.W, a.W16, e);
             const int n00 = a.node00[e], n01 = a.node01[e];
             const float* x00 = a.in + (int64_t)n00 * KB + b0;
             const float* x10 = a.in + (int64_t)(n00 + a.n_phi) * KB + b0;
@@ -665,7 +666,7 @@ fwd5_kernel(const __grid_constant__ CUtensorMap xmap, const ApplyArgs<float> a, 
         const int64_t U0 = (int64_t)a.K0[cur.e] * kFracOne + (int64_t)a.F0[cur.e];
         const int k_top = (int)((U0 - (int64_t)cur.f_begin * a.D) >> kFracBits);
         const int nwin = k_top + 2 - cur.k_lo;
-        const float4 wv = a.W[cur.e];
+        const float4 wv = corner_weights(a.W, a.W16, cur.e);
         const float4* slab = reinterpret_cast<const float4*>(wbase + (size_t)(4 * (t & 1)) * slab_stride);
         const int sv = (int)(slab_stride / 16);  // float4 per slab
         for (int o = lane; o < nwin * Q; o += 32) {
@@ -779,7 +780,7 @@ fwd7_kernel(const ApplyArgs<float> a) {
         const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
         for (int e = e_begin; e < e_end; ++e) {
             const int K0 = a.K0[e], F0 = a.F0[e];
-            const float4 wv = a.W[e];
+            const float4 wv = corner_weights(a.W, a.W16, e);
             const int n00 = a.node00[e], n01 = a.node01[e];
             // window [k_lo, k_lo + nwin): k_top = K0 - hb, k_lo = K0 - hb - FC / P + ((F0 + D) >> 24)
             const int k_top = K0 - hb;
@@ -953,7 +954,7 @@ fwd6_kernel(const ApplyArgs<float> a, int* status, uint32_t slab_bytes, uint32_t
             it.n01 = a.node01[it.e];
             it.K0 = a.K0[it.e];
             it.F0 = a.F0[it.e];
-            it.w = a.W[it.e];
+            it.w = corner_weights(a.W, a.W16, it.e);
         }
     };
     const int64_t KB = (int64_t)a.K * BC;  // floats per node row of x
@@ -1188,6 +1189,7 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     a.node00 = op->node00;
     a.node01 = op->node01;
     a.W = op->W;
+    a.W16 = op->W16;
     a.W64 = op->W64;
     a.K0 = op->K0;
     a.F0 = op->F0;

@@ -74,6 +74,19 @@ static cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 bl
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
+// corner weights of one ray: the FP32 table, or its BF16 copy (4 x 16 bits,
+// corners 0 and 1 in .x, 2 and 3 in .y, low half first) widened exactly; the
+// FP32 table then holds the same BF16-rounded values, so either read gives
+// the same operand
+__device__ __forceinline__ float4 corner_weights(const float4* W, const uint2* W16, int64_t e) {
+    if (W16) {
+        const uint2 v = W16[e];
+        return make_float4(__uint_as_float(v.x << 16), __uint_as_float(v.x & 0xffff0000u),
+                           __uint_as_float(v.y << 16), __uint_as_float(v.y & 0xffff0000u));
+    }
+    return W[e];
+}
+
 __device__ __forceinline__ int64_t floor_div(int64_t a, int64_t d) {
     return a >= 0 ? a / d : -((-a + d - 1) / d);
 }

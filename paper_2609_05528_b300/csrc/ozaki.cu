@@ -4,16 +4,17 @@
 // Ozaki, Ogita, Oishi & Rump 2012, in its integer-digit form):
 //
 //  * every column c of an operand is scaled by a power of two 2^e_c so its
-//    entries lie in (-1, 1), then split exactly into 7 signed digits of 7
-//    bits, x 2^-e_c = sum_{s<7} q_s 2^-7(s+1) + r, |q_0| <= 128,
-//    |q_{s>=1}| <= 64, |r| <= 2^-50 (q_s = round(128 t), t <- 128 t - q_s);
+//    entries lie in (-1, 1), rounded to 49 fractional bits and split exactly
+//    into 7 signed digits of 7 bits, x 2^-e_c = sum_{s<7} q_s 2^-7(s+1) + r,
+//    |q_0| <= 128, q_{s>=1} in [-64, 63] (balanced base 128), |r| <= 2^-50;
 //    every digit is an integer, exact in BF16;
 //  * C_ij = 2^(e_i+f_j) sum_{s,t} 2^-7(s+t+2) sum_k q^A_s[k,i] q^B_t[k,j]:
 //    the digit products are integers of at most 14 bits, so a BF16 tensor-
 //    core product with FP32 accumulation is exact as long as a sum stays
-//    below 2^24: the pairs of one level L = s + t (at most 7 pairs) are
-//    accumulated over windows of 128 k in one FP32 TMEM accumulator per
-//    level (|sum| < 2^21.7);
+//    below 2^24: the pairs of one level L = s + t (at most 7 pairs, at most
+//    two of them with the 8-bit leading digit) are accumulated over windows
+//    of 256 k in one FP32 TMEM accumulator per level (per k at most
+//    2 * 128 * 64 + 5 * 64 * 64 = 36864, so |sum| <= 256 * 36864 < 2^23.2);
 //  * after each window the 7 level sums (exact integers) are read out of
 //    TMEM and added into two 64-bit integer accumulators per output,
 //    hi = sum_{L<=3} v_L 2^7(3-L) and lo = sum_{4<=L<=6} v_L 2^7(6-L) (no
@@ -22,12 +23,14 @@
 //    order: the result is deterministic.  Levels L >= 7 (below 2^-49 of
 //    2^(e_i+f_j) per product) and the digit remainders are dropped.
 //
-// tcgen05 pipeline per CTA (one 128 x 64 output tile, one K range): a TMA
-// producer warp streams 32-wide K chunks of the 7 A and 7 B digit slices
-// (BF16, K-major, 64-byte swizzle) through two shared-memory stages; one
-// thread issues tcgen05.mma (M = 128, N = 64, K = 16) for the 28 digit pairs
-// into the 7 level accumulators (448 TMEM columns) and commits to mbarriers;
-// eight epilogue warps drain TMEM every window.  Every wait is bounded.
+// tcgen05 pipeline: a persistent CTA per SM walks work units (one 128 x 64
+// output tile and one K range each; the K split is chosen so the units fill
+// the SMs evenly).  A TMA producer warp streams 32-wide K chunks of the 7 A
+// and 7 B digit slices (BF16, K-major, 64-byte swizzle) through two shared-
+// memory stages; one thread issues tcgen05.mma (M = 128, N = 64, K = 16) for
+// the 28 digit pairs into the 7 level accumulators (448 TMEM columns) and
+// commits to mbarriers; sixteen epilogue warps (16 columns each) drain TMEM
+// every window.  Every wait is bounded.
 #include <cuda_bf16.h>
 
 #include <climits>
@@ -41,9 +44,10 @@ constexpr int kOzDigits = 7;
 constexpr int kOzMT = 128;      // output rows per CTA (TMEM lanes)
 constexpr int kOzNT = 64;       // output columns per CTA
 constexpr int kOzKC = 32;       // K elements per stage (64 bytes of BF16: one swizzle atom)
-constexpr int kOzWindow = 128;  // K elements per exact FP32 accumulation window
+constexpr int kOzWindow = 256;  // K elements per exact FP32 accumulation window
 constexpr int kOzStages = 2;
-constexpr int kOzEpiWarps = 8;
+constexpr int kOzEpiWarps = 16;
+constexpr int kOzEpiCols = kOzNT * 4 / kOzEpiWarps;  // output columns per epilogue thread (16)
 constexpr int kOzThreads = (2 + kOzEpiWarps) * 32;
 constexpr uint32_t kOzATile = kOzMT * kOzKC * 2;  // 8 KB
 constexpr uint32_t kOzBTile = kOzNT * kOzKC * 2;  // 4 KB
@@ -51,6 +55,16 @@ constexpr uint32_t kOzStageBytes = kOzDigits * (kOzATile + kOzBTile);  // 84 KB
 constexpr int kOzTmemCols = 512;  // 7 levels x 64 columns = 448, allocated as 512
 
 // ---- column exponents: expo[c] = max over rows of frexp's exponent of X[r][c]
+// (read from the exponent field; subnormal entries through frexp)
+__device__ __forceinline__ int oz_frexp_exponent(double v) {
+    const long long b = __double_as_longlong(v);
+    const int field = (int)((b >> 52) & 0x7FF);
+    if (field != 0) return field - 1022;
+    int ex;
+    frexp(v, &ex);
+    return ex;
+}
+
 __global__ void oz_colmax(int64_t rows, int cols, const double* __restrict__ X, int64_t ldx,
                           int* expo) {
     const int c = blockIdx.y * blockDim.x + threadIdx.x;
@@ -58,20 +72,32 @@ __global__ void oz_colmax(int64_t rows, int cols, const double* __restrict__ X, 
     int e = INT_MIN;
     for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
         const double v = X[r * ldx + c];
-        if (v != 0.0) {
-            int ex;
-            frexp(v, &ex);
-            e = max(e, ex);
-        }
+        if (v != 0.0) e = max(e, oz_frexp_exponent(v));
     }
     if (e != INT_MIN) atomicMax(expo + c, e);
 }
 
-// ---- digit slices, transposed to K-major: S[s][c][k] = q_s of X[k][c] 2^-e_c
-// (zero in the padding: c >= cols or k >= rows)
+// ---- packed digit slices.  The operand's columns form tiles of R (128 for
+// A, 64 for B); for tile t and K chunk ch (32 k) the 7 digit slices are one
+// contiguous block of 7 x R rows of 64 bytes, exactly the shared-memory image
+// the MMA descriptors read: slice s at s R 64 bytes, row r at r 64 bytes,
+// its 16-byte piece j (k = 8 j ... 8 j + 7) at position j ^ ((r >> 1) & 3)
+// (the 64-byte swizzle of 512-byte aligned 8-row atoms).  A stage is then two
+// contiguous bulk copies.
+__host__ __device__ __forceinline__ int64_t oz_packed_index(int s, int c, int64_t k, int R,
+                                                            int64_t n_chunks) {
+    const int t = c / R, r = c - t * R;
+    const int64_t ch = k >> 5;
+    const int kk = (int)(k & 31), j = kk >> 3, e = kk & 7;
+    const int64_t block = ((int64_t)t * n_chunks + ch) * kOzDigits + s;  // in units of R rows
+    return (block * R + r) * 32 + ((j ^ ((r >> 1) & 3)) << 3) + e;     // BF16 elements
+}
+
+// q_s of X[k][c] 2^-e_c into the packed slices (zero in the padding:
+// c >= cols or k >= rows)
 __global__ void __launch_bounds__(256) oz_split(int64_t rows, int cols, const double* __restrict__ X,
                                                 int64_t ldx, const int* __restrict__ expo,
-                                                int cols_pad, int64_t k_pad, __nv_bfloat16* S) {
+                                                int cols_pad, int64_t k_pad, int R, __nv_bfloat16* S) {
     __shared__ float tile[kOzDigits][32][33];
     const int64_t k0 = (int64_t)blockIdx.x * 32;
     const int c0 = blockIdx.y * 32;
@@ -84,29 +110,34 @@ __global__ void __launch_bounds__(256) oz_split(int64_t rows, int cols, const do
         for (int s = 0; s < kOzDigits; ++s) q[s] = 0.0f;
         if (k < rows && c < cols) {
             const int e = expo[c];
-            double a = X[k * ldx + c];
+            const double a = X[k * ldx + c];
             if (e != INT_MIN && a != 0.0) {
-                a = ldexp(a, -e);  // exact: |a| < 1
+                // N = a 2^(49 - e) rounded to the nearest integer (|a 2^-e| < 1,
+                // so |N| <= 2^49; the part dropped is at most 2^-50 of 2^e),
+                // then its balanced base-128 digits: q_6 ... q_1 in [-64, 63],
+                // q_0 = what remains, |q_0| <= 128; all integer arithmetic
+                long long N = __double2ll_rn(ldexp(a, 49 - e));
 #pragma unroll
-                for (int s = 0; s < kOzDigits; ++s) {
-                    const double t = a * 128.0;  // exact
-                    const double d = rint(t);    // |d| <= 128, then <= 64
-                    a = t - d;                   // exact, |a| <= 1/2
+                for (int s = kOzDigits - 1; s >= 1; --s) {
+                    const long long d = ((N + 64) & 127) - 64;
                     q[s] = (float)d;
+                    N = (N - d) >> 7;  // exact: N - d is a multiple of 128
                 }
+                q[0] = (float)N;
             }
         }
 #pragma unroll
         for (int s = 0; s < kOzDigits; ++s) tile[s][j][tx] = q[s];
     }
     __syncthreads();
+    const int64_t n_chunks = k_pad >> 5;
     for (int j = ty; j < 32; j += 8) {
         const int c = c0 + j;
         const int64_t k = k0 + tx;
         if (c < cols_pad && k < k_pad) {
 #pragma unroll
             for (int s = 0; s < kOzDigits; ++s)
-                S[((int64_t)s * cols_pad + c) * k_pad + k] = __float2bfloat16_rn(tile[s][tx][j]);
+                S[oz_packed_index(s, c, k, R, n_chunks)] = __float2bfloat16_rn(tile[s][tx][j]);
         }
     }
 }
@@ -159,22 +190,43 @@ __device__ __forceinline__ void oz_commit(uint32_t bar) {
                  : "memory");
 }
 
-// exact integer value of an FP32 that holds an integer of magnitude below 2^22
-__device__ __forceinline__ int oz_int(float v) {
-    return __float_as_int(v + 12582912.0f) - 0x4B400000;
-}
+// exact integer value of an FP32 that holds an integer (|v| < 2^24)
+__device__ __forceinline__ int oz_int(float v) { return __float2int_rn(v); }
 
 struct OzArgs {
+    const __nv_bfloat16* sa;  // packed A slices
+    const __nv_bfloat16* sb;  // packed B slices
     int m_pad, n_pad;
     int64_t k_pad;
-    int64_t k_per_cta;  // multiple of kOzWindow
-    long long* acc;     // [m_pad][n_pad][2]
+    int64_t k_per_unit;  // multiple of kOzWindow
+    int m_tiles, splits;
+    int units;           // m_tiles * (n_pad / kOzNT) * splits
+    long long* acc;      // [m_pad][n_pad][2]
     int* status;
 };
 
-__global__ void __launch_bounds__(kOzThreads, 1)
-oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__ CUtensorMap bmap,
-               const OzArgs a) {
+// tile and K range of work unit u (tiles fastest, so concurrent CTAs share
+// K ranges of the digit slices in L2)
+struct OzUnit {
+    int mt, nt;
+    int64_t k_begin;
+    int n_chunks;
+};
+
+__device__ __forceinline__ OzUnit oz_unit(const OzArgs& a, int u) {
+    const int tiles = a.m_tiles * (a.n_pad / kOzNT);
+    const int tile = u % tiles, sp = u / tiles;
+    OzUnit r;
+    r.mt = tile % a.m_tiles;
+    r.nt = tile / a.m_tiles;
+    r.k_begin = (int64_t)sp * a.k_per_unit;
+    int64_t k_end = r.k_begin + a.k_per_unit;
+    if (k_end > a.k_pad) k_end = a.k_pad;
+    r.n_chunks = k_end > r.k_begin ? (int)((k_end - r.k_begin) / kOzKC) : 0;
+    return r;
+}
+
+__global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzArgs a) {
     extern __shared__ unsigned char oz_smem_raw[];
     const uint32_t raw = smem_u32(oz_smem_raw);
     const uint32_t base = (raw + 1023) & ~1023u;
@@ -187,11 +239,6 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     unsigned char* slot_ptr = oz_smem_raw + (tmem_slot - raw);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(oz_smem_raw + (tmem_slot + 8 - raw));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mt = blockIdx.x, nt = blockIdx.y;
-    const int64_t k_begin = (int64_t)blockIdx.z * a.k_per_cta;
-    int64_t k_end = k_begin + a.k_per_cta;
-    if (k_end > a.k_pad) k_end = a.k_pad;
-    const int n_chunks = k_end > k_begin ? (int)((k_end - k_begin) / kOzKC) : 0;
     constexpr int kChunksPerWindow = kOzWindow / kOzKC;
 
     if (threadIdx.x == 0) {
@@ -218,35 +265,36 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     const uint32_t tmem = *reinterpret_cast<volatile uint32_t*>(slot_ptr);
 
     if (warp == 0) {
-        // ---- TMA producer
+        // ---- TMA producer: the chunks of this CTA's units, one ring of stages
         if (lane == 0) {
-            const uint64_t am = reinterpret_cast<uint64_t>(&amap), bm = reinterpret_cast<uint64_t>(&bmap);
-            for (int c = 0; c < n_chunks; ++c) {
-                const int st = c % kOzStages;
-                const uint32_t ph = (uint32_t)((c / kOzStages) & 1);
-                if (c >= kOzStages && !mbar_wait(bar_empty + 8 * st, ph ^ 1)) {
-                    *abort_flag = 1;
-                    atomicOr(a.status, 1);
-                    break;
-                }
-                if (*abort_flag) break;
-                const uint32_t sb = base + st * kOzStageBytes;
-                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_full + 8 * st),
-                             "r"(kOzStageBytes)
-                             : "memory");
-                const int kx = (int)(k_begin + (int64_t)c * kOzKC);
-                for (int s = 0; s < kOzDigits; ++s) {
-                    const int ra = s * a.m_pad + mt * kOzMT;
+            const int64_t n_chunks_k = a.k_pad / kOzKC;
+            int c = 0;  // chunks issued by this CTA
+            for (int u = blockIdx.x; u < a.units && !*abort_flag; u += gridDim.x) {
+                const OzUnit un = oz_unit(a, u);
+                for (int cu = 0; cu < un.n_chunks; ++cu, ++c) {
+                    const int st = c % kOzStages;
+                    const uint32_t ph = (uint32_t)((c / kOzStages) & 1);
+                    if (c >= kOzStages && !mbar_wait(bar_empty + 8 * st, ph ^ 1)) {
+                        *abort_flag = 1;
+                        atomicOr(a.status, 1);
+                        break;
+                    }
+                    if (*abort_flag) break;
+                    const uint32_t sb = base + st * kOzStageBytes;
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_full + 8 * st),
+                                 "r"(kOzStageBytes)
+                                 : "memory");
+                    const int64_t ch = un.k_begin / kOzKC + cu;
+                    const __nv_bfloat16* ga = a.sa + (((int64_t)un.mt * n_chunks_k + ch) * kOzDigits) * kOzMT * kOzKC;
+                    const __nv_bfloat16* gb = a.sb + (((int64_t)un.nt * n_chunks_k + ch) * kOzDigits) * kOzNT * kOzKC;
                     asm volatile(
-                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(sb + s * kOzATile),
-                        "l"(am), "r"(kx), "r"(ra), "r"(bar_full + 8 * st)
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                        ::"r"(sb), "l"(ga), "r"(kOzDigits * kOzATile), "r"(bar_full + 8 * st)
                         : "memory");
-                    const int rb = s * a.n_pad + nt * kOzNT;
                     asm volatile(
-                        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-                        " [%0], [%1, {%2, %3}], [%4];" ::"r"(sb + kOzDigits * kOzATile + s * kOzBTile),
-                        "l"(bm), "r"(kx), "r"(rb), "r"(bar_full + 8 * st)
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                        ::"r"(sb + kOzDigits * kOzATile), "l"(gb), "r"(kOzDigits * kOzBTile),
+                        "r"(bar_full + 8 * st)
                         : "memory");
                 }
             }
@@ -254,99 +302,122 @@ oz_gemm_kernel(const __grid_constant__ CUtensorMap amap, const __grid_constant__
     } else if (warp == 1) {
         // ---- MMA issuer
         if (lane == 0) {
-            for (int c = 0; c < n_chunks; ++c) {
-                const int st = c % kOzStages;
-                const uint32_t ph = (uint32_t)((c / kOzStages) & 1);
-                const int w = c / kChunksPerWindow, cw = c - w * kChunksPerWindow;
-                if (cw == 0 && w > 0 && !mbar_wait(bar_tempty, (uint32_t)((w - 1) & 1))) {
-                    *abort_flag = 1;
-                    atomicOr(a.status, 1);
-                    break;
-                }
-                if (!mbar_wait(bar_full + 8 * st, ph)) {
-                    *abort_flag = 1;
-                    atomicOr(a.status, 1);
-                    break;
-                }
-                if (*abort_flag) break;
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t sb = base + st * kOzStageBytes;
-#pragma unroll 1
-                for (int s = 0; s < kOzDigits; ++s) {
-                    const uint32_t sa = sb + s * kOzATile;
-#pragma unroll 1
-                    for (int t = 0; s + t < kOzDigits; ++t) {
-                        const uint32_t sbb = sb + kOzDigits * kOzATile + t * kOzBTile;
-                        const uint32_t d = tmem + (uint32_t)((s + t) * kOzNT);
+            int c = 0, gw = 0;  // chunks and windows consumed by this CTA
+            bool live = true;
+            for (int u = blockIdx.x; u < a.units && live; u += gridDim.x) {
+                const OzUnit un = oz_unit(a, u);
+                for (int cu = 0; cu < un.n_chunks; ++cu, ++c) {
+                    const int st = c % kOzStages;
+                    const uint32_t ph = (uint32_t)((c / kOzStages) & 1);
+                    const int cw = cu % kChunksPerWindow;
+                    // a new window overwrites the level accumulators: wait
+                    // until the epilogue has read the previous window
+                    if (cw == 0 && gw > 0 && !mbar_wait(bar_tempty, (uint32_t)((gw - 1) & 1))) {
+                        *abort_flag = 1;
+                        atomicOr(a.status, 1);
+                        live = false;
+                        break;
+                    }
+                    if (!mbar_wait(bar_full + 8 * st, ph)) {
+                        *abort_flag = 1;
+                        atomicOr(a.status, 1);
+                        live = false;
+                        break;
+                    }
+                    if (*abort_flag) {
+                        live = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t sb = base + st * kOzStageBytes;
+                    // descriptors of the stage's first A and B rows; every
+                    // operand of the chunk is a constant byte offset from them
+                    // (the address field counts 16-byte units)
+                    const uint64_t da0 = oz_desc(sb), db0 = oz_desc(sb + kOzDigits * kOzATile);
+                    const uint32_t first = cw == 0 ? 0u : 1u;
 #pragma unroll
-                        for (int kk = 0; kk < kOzKC / 16; ++kk) {
-                            // the first product into a level in a window overwrites it
-                            const uint32_t accum = (cw == 0 && kk == 0 && s == 0) ? 0u : 1u;
-                            oz_mma(d, oz_desc(sa + 32 * kk), oz_desc(sbb + 32 * kk), accum);
+                    for (int s = 0; s < kOzDigits; ++s) {
+#pragma unroll
+                        for (int t = 0; s + t < kOzDigits; ++t) {
+                            const uint32_t d = tmem + (uint32_t)((s + t) * kOzNT);
+#pragma unroll
+                            for (int kk = 0; kk < kOzKC / 16; ++kk) {
+                                // the first product into a level in a window overwrites it
+                                const uint32_t accum = (kk == 0 && s == 0) ? first : 1u;
+                                oz_mma(d, da0 + (uint64_t)((s * kOzATile + 32 * kk) >> 4),
+                                       db0 + (uint64_t)((t * kOzBTile + 32 * kk) >> 4), accum);
+                            }
                         }
                     }
+                    oz_commit(bar_empty + 8 * st);  // the stage is free once these MMAs complete
+                    if (cw == kChunksPerWindow - 1) {
+                        oz_commit(bar_tfull);
+                        ++gw;
+                    }
                 }
-                oz_commit(bar_empty + 8 * st);  // the stage is free once these MMAs complete
-                if (cw == kChunksPerWindow - 1) oz_commit(bar_tfull);
             }
             // every MMA issued has completed before the TMEM is released
             oz_commit(bar_final);
             if (!mbar_wait(bar_final, 0)) atomicOr(a.status, 1);
         }
     } else {
-        // ---- epilogue: rows 32 (warp % 4) + lane, columns 32 h ... 32 h + 31
-        const int q = warp & 3, h = (warp - 2) >> 2;
-        long long hi[32], lo[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) hi[j] = lo[j] = 0;
-        const int n_windows = n_chunks / kChunksPerWindow;
+        // ---- epilogue: rows 32 (warp % 4) + lane, columns kOzEpiCols g ... of
+        // the 64 (g = (warp - 2) / 4; a warp reads the TMEM lanes of its
+        // quadrant warp % 4)
+        const int q = warp & 3, g = (warp - 2) >> 2;
+        int gw = 0;  // windows drained by this CTA
         bool ok = true;
-        for (int w = 0; w < n_windows && ok; ++w) {
-            if (!mbar_wait(bar_tfull, (uint32_t)(w & 1))) {
-                ok = false;
-                if (lane == 0) atomicOr(a.status, 1);
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll 1
-            for (int L = 0; L < kOzDigits; ++L) {
-                uint32_t v[32];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L * kOzNT + 32 * h);
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-                    "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-                    "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                      "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-                      "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-                      "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-                      "=r"(v[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                // level L weighs 2^-7(L+2): hi holds L <= 3 at 2^7(3-L), lo holds L >= 4 at 2^7(6-L)
-                const long long sc = L <= 3 ? (1ll << (7 * (3 - L))) : (1ll << (7 * (6 - L)));
+        for (int u = blockIdx.x; u < a.units && ok; u += gridDim.x) {
+            const OzUnit un = oz_unit(a, u);
+            const int n_windows = un.n_chunks / kChunksPerWindow;
+            long long hi[kOzEpiCols], lo[kOzEpiCols];
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const long long iv = (long long)oz_int(__uint_as_float(v[j])) * sc;
-                    if (L <= 3)
-                        hi[j] += iv;
-                    else
-                        lo[j] += iv;
+            for (int j = 0; j < kOzEpiCols; ++j) hi[j] = lo[j] = 0;
+            for (int w = 0; w < n_windows; ++w, ++gw) {
+                if (!mbar_wait(bar_tfull, (uint32_t)(gw & 1))) {
+                    ok = false;
+                    if (lane == 0) atomicOr(a.status, 1);
+                    break;
                 }
-            }
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_tempty) : "memory");
-        }
-        if (ok && n_windows > 0) {
-            const int i = mt * kOzMT + 32 * q + lane;
-            unsigned long long* out = reinterpret_cast<unsigned long long*>(a.acc) +
-                                      ((int64_t)i * a.n_pad + nt * kOzNT + 32 * h) * 2;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+                for (int L = 0; L < kOzDigits; ++L) {
+                    uint32_t v[kOzEpiCols];
+                    const uint32_t taddr =
+                        tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(L * kOzNT + kOzEpiCols * g);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                          "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                          "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                        : "r"(taddr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    // level L weighs 2^-7(L+2): hi holds L <= 3 at 2^7(3-L), lo
+                    // holds L >= 4 at 2^7(6-L)
+                    const int sh = L <= 3 ? 7 * (3 - L) : 7 * (6 - L);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {  // integer sums: order-independent
-                atomicAdd(out + 2 * j, (unsigned long long)hi[j]);
-                atomicAdd(out + 2 * j + 1, (unsigned long long)lo[j]);
+                    for (int j = 0; j < kOzEpiCols; ++j) {
+                        const long long iv = (long long)oz_int(__uint_as_float(v[j])) << sh;
+                        if (L <= 3)
+                            hi[j] += iv;
+                        else
+                            lo[j] += iv;
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar_tempty) : "memory");
+            }
+            if (ok && n_windows > 0) {
+                const int i = un.mt * kOzMT + 32 * q + lane;
+                unsigned long long* out = reinterpret_cast<unsigned long long*>(a.acc) +
+                                          ((int64_t)i * a.n_pad + un.nt * kOzNT + kOzEpiCols * g) * 2;
+#pragma unroll
+                for (int j = 0; j < kOzEpiCols; ++j) {  // integer sums: order-independent
+                    atomicAdd(out + 2 * j, (unsigned long long)hi[j]);
+                    atomicAdd(out + 2 * j + 1, (unsigned long long)lo[j]);
+                }
             }
         }
     }
@@ -370,20 +441,35 @@ rtt_status gemm_tn_f64(int64_t k, int m, int n, const double* A, int64_t lda, co
         set_error("gemm: invalid arguments (k=%lld m=%d n=%d)", (long long)k, m, n);
         return RTT_EINVAL;
     }
-    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-    if (!enc) {
-        set_error("gemm: tensor-map encoder unavailable");
-        return RTT_ECUDA;
-    }
     const int m_pad = (int)round_up(m, kOzMT), n_pad = (int)round_up(n, kOzNT);
     const int64_t k_pad = round_up(k, kOzWindow);
     const int tiles = (m_pad / kOzMT) * (n_pad / kOzNT);
     const int sms = sm_count();
-    int splits = (sms + tiles - 1) / tiles;
+    // K split: the number of units (tiles x splits, whole windows each) whose
+    // rounds over the persistent CTAs waste the least, the smallest such
+    // count once the waste is below 4%
     const int64_t windows = k_pad / kOzWindow;
-    if (splits > windows) splits = (int)windows;
-    const int64_t k_per = round_up((k_pad + splits - 1) / splits, kOzWindow);
+    int splits = 1;
+    double best = -1.0;
+    for (int sp = 1; sp <= 64 && sp <= windows; ++sp) {
+        const int64_t per = (windows + sp - 1) / sp;          // windows per unit
+        const int64_t used = (windows + per - 1) / per;       // splits actually needed
+        const int64_t units = (int64_t)tiles * used;
+        const int64_t grid = units < sms ? units : sms;
+        const int64_t rounds = (units + grid - 1) / grid;
+        // work of the busiest CTA against the even share
+        const double eff = (double)windows * tiles / ((double)rounds * per * grid) *
+                           ((double)grid / sms);
+        if (eff > best + 1e-9) {
+            best = eff;
+            splits = (int)used;
+        }
+        if (best >= 0.96) break;
+    }
+    const int64_t k_per = ((windows + splits - 1) / splits) * kOzWindow;
     splits = (int)((k_pad + k_per - 1) / k_per);
+    const int units = tiles * splits;
+    const int grid = units < sms ? units : sms;
     __nv_bfloat16 *sa = nullptr, *sb = nullptr;
     int* ex = nullptr;
     long long* acc = nullptr;
@@ -410,45 +496,31 @@ rtt_status gemm_tn_f64(int64_t k, int m, int n, const double* A, int64_t lda, co
         const int gx = (int)(k < 512 ? k : 512);
         oz_colmax<<<dim3(gx, (m + 127) / 128), 128, 0, st>>>(k, m, A, lda, ex);
         oz_colmax<<<dim3(gx, (n + 127) / 128), 128, 0, st>>>(k, n, B, ldb, ex + m);
-        oz_split<<<dim3((unsigned)(k_pad / 32), m_pad / 32), 256, 0, st>>>(k, m, A, lda, ex, m_pad, k_pad, sa);
-        oz_split<<<dim3((unsigned)(k_pad / 32), n_pad / 32), 256, 0, st>>>(k, n, B, ldb, ex + m, n_pad, k_pad, sb);
+        oz_split<<<dim3((unsigned)(k_pad / 32), m_pad / 32), 256, 0, st>>>(k, m, A, lda, ex, m_pad, k_pad,
+                                                                          kOzMT, sa);
+        oz_split<<<dim3((unsigned)(k_pad / 32), n_pad / 32), 256, 0, st>>>(k, n, B, ldb, ex + m, n_pad, k_pad,
+                                                                          kOzNT, sb);
         if ((e = cudaGetLastError()) != cudaSuccess) {
             set_error("gemm: split kernels: %s", cudaGetErrorString(e));
             return done(RTT_ECUDA);
         }
     }
-    CUtensorMap am, bm;
-    {
-        cuuint64_t dims[2] = {(cuuint64_t)k_pad, (cuuint64_t)kOzDigits * m_pad};
-        cuuint64_t strides[1] = {(cuuint64_t)k_pad * 2};
-        cuuint32_t box[2] = {kOzKC, kOzMT};
-        cuuint32_t es[2] = {1, 1};
-        if (enc(&am, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sa, dims, strides, box, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
-            set_error("gemm: tensor map (A) rejected");
-            return done(RTT_ECUDA);
-        }
-        cuuint64_t dimsb[2] = {(cuuint64_t)k_pad, (cuuint64_t)kOzDigits * n_pad};
-        cuuint32_t boxb[2] = {kOzKC, kOzNT};
-        if (enc(&bm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, sb, dimsb, strides, boxb, es,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
-            set_error("gemm: tensor map (B) rejected");
-            return done(RTT_ECUDA);
-        }
-    }
     OzArgs oa;
+    oa.sa = sa;
+    oa.sb = sb;
     oa.m_pad = m_pad;
     oa.n_pad = n_pad;
     oa.k_pad = k_pad;
-    oa.k_per_cta = k_per;
+    oa.k_per_unit = k_per;
+    oa.m_tiles = m_pad / kOzMT;
+    oa.splits = splits;
+    oa.units = units;
     oa.acc = acc;
     oa.status = status;
     const size_t smem = 1024 + (size_t)kOzStages * kOzStageBytes + 8 * (2 * kOzStages + 3) + 16;
     e = cudaFuncSetAttribute(oz_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) {
-        oz_gemm_kernel<<<dim3(m_pad / kOzMT, n_pad / kOzNT, splits), kOzThreads, smem, st>>>(am, bm, oa);
+        oz_gemm_kernel<<<grid, kOzThreads, smem, st>>>(oa);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

@@ -93,6 +93,8 @@ struct rtt_op_s {
     int32_t* node01 = nullptr;    // [E] node (i0, j1), j1 = (j0 + 1) mod n_phi
     float4* W = nullptr;          // [E] scale * w * bilinear, corners (i0j0, i1j0, i0j1, i1j1)
     double* W64 = nullptr;        // [4E] same in FP64
+    uint2* W16 = nullptr;         // [E] BF16 copy of W when the weights are BF16 (else null)
+    int weight_precision = 0;     // RTT_WEIGHTS_FP32 or RTT_WEIGHTS_BF16
     int32_t* K0 = nullptr;        // [E] floor(u0)
     int32_t* F0 = nullptr;        // [E] floor(frac(u0) * 2^24)
     double* F64 = nullptr;        // [E] frac(u0) exactly
@@ -114,6 +116,7 @@ struct rtt_op_s {
     int32_t* c_fb = nullptr;     // [E] periodic cadences: first tap frame of hat 0
     int32_t* c_r0 = nullptr;     // [E] periodic cadences: tap weight phase
     float4* c_W = nullptr;       // [E]
+    uint2* c_W16 = nullptr;      // [E] BF16 copy of c_W, or null
     double* c_W64 = nullptr;     // [4E]
     double* c_F64 = nullptr;     // [E]
     int32_t* seg_ray = nullptr;  // [n_seg + 1]

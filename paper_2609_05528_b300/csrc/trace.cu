@@ -6,8 +6,9 @@
 //   (ds/dl)^2 = s^4 R(1/s),  (du/dl)^2 = eta - (eta + lam^2 - a^2) u^2 - a^2 u^4,
 // written in second-order form (no sign flips at turning points), starting
 // exactly at the observer (s = 0).  Classic RK4 with adaptive steps chosen by
-// step doubling (Richardson error estimate); each sign change of u is
-// refined by Newton iterations on a partial step.  The travel time is carried with the
+// step doubling (Richardson error estimate, the extrapolated fifth-order
+// state accepted); each sign change of u is refined by Newton iterations on
+// the length of an extrapolated partial step.  The travel time is carried with the
 // divergent r + 2 ln r part removed analytically.
 #include <cuda_runtime.h>
 
@@ -58,6 +59,29 @@ __device__ __forceinline__ void deriv(const RayConst& c, const St& y, St& d) {
 __device__ __forceinline__ St axpy(const St& y, double h, const St& k) {
     return St{y.s + h * k.s, y.vs + h * k.vs, y.u + h * k.u, y.vu + h * k.vu, y.ph + h * k.ph,
               y.Y + h * k.Y};
+}
+
+// one step of h as two half steps, Richardson-extrapolated against the full
+// step (fifth order); err receives the largest scaled local error estimate
+__device__ __forceinline__ St rk4(const RayConst& c, const St& y, double h);
+
+__device__ __forceinline__ St richardson_step(const RayConst& c, const St& y, double h, double tol,
+                                              double* err) {
+    const St full = rk4(c, y, h);
+    const St half = rk4(c, rk4(c, y, 0.5 * h), 0.5 * h);
+    const double e[6] = {half.s - full.s, half.vs - full.vs, half.u - full.u,
+                         half.vu - full.vu, half.ph - full.ph, half.Y - full.Y};
+    // error scales: every component relative to 1 + |value| except phi, which
+    // is held absolutely (it grows by about 2 pi per order, its required
+    // accuracy does not)
+    const double m[6] = {1.0 + fmax(fabs(y.s), fabs(half.s)), 1.0 + fmax(fabs(y.vs), fabs(half.vs)),
+                         1.0 + fmax(fabs(y.u), fabs(half.u)), 1.0 + fmax(fabs(y.vu), fabs(half.vu)),
+                         1.0, 1.0 + fmax(fabs(y.Y), fabs(half.Y))};
+    double er = 0.0;
+    for (int q = 0; q < 6; ++q) er = fmax(er, fabs(e[q]) / (15.0 * tol * m[q]));
+    *err = er;
+    return St{half.s + e[0] / 15.0, half.vs + e[1] / 15.0, half.u + e[2] / 15.0,
+              half.vu + e[3] / 15.0, half.ph + e[4] / 15.0, half.Y + e[5] / 15.0};
 }
 
 __device__ __forceinline__ St rk4(const RayConst& c, const St& y, double h) {
@@ -141,36 +165,30 @@ __global__ void trace_kernel(const TraceArgs A) {
     A.status[i] = 0;
     const double inv_nsub = 1.0 / (double)A.n_sub[i];
     // adaptive RK4 with step doubling: local error = (two half steps - one
-    // full step) / 15, relative to tol * (1 + |y|); the accepted state is the
-    // Richardson-extrapolated one
+    // full step) / 15 against tol (scaled as in richardson_step); the
+    // accepted state is the Richardson-extrapolated one
     const double tol = A.tol;
     for (int step = 0; n_cross < 3; ++step) {
         if (step > 200000) {
             A.status[i] = 1;
             break;
         }
-        const St full = rk4(c, y, h);
-        const St half = rk4(c, rk4(c, y, 0.5 * h), 0.5 * h);
-        const double e[6] = {half.s - full.s, half.vs - full.vs, half.u - full.u,
-                             half.vu - full.vu, half.ph - full.ph, half.Y - full.Y};
-        const double m[6] = {fmax(fabs(y.s), fabs(half.s)),   fmax(fabs(y.vs), fabs(half.vs)),
-                             fmax(fabs(y.u), fabs(half.u)),   fmax(fabs(y.vu), fabs(half.vu)),
-                             fmax(fabs(y.ph), fabs(half.ph)), fmax(fabs(y.Y), fabs(half.Y))};
         double err = 0.0;
-        for (int q = 0; q < 6; ++q) err = fmax(err, fabs(e[q]) / (15.0 * tol * (1.0 + m[q])));
+        const St yn = richardson_step(c, y, h, tol, &err);
         if (err > 1.0) {
             h *= fmax(0.1, 0.9 * pow(err, -0.2));
             continue;
         }
-        const St yn{half.s + e[0] / 15.0, half.vs + e[1] / 15.0, half.u + e[2] / 15.0,
-                    half.vu + e[3] / 15.0, half.ph + e[4] / 15.0, half.Y + e[5] / 15.0};
         if ((y.u > 0.0 && yn.u <= 0.0) || (y.u < 0.0 && yn.u >= 0.0)) {
-            double hc = h * y.u / (y.u - yn.u);
-            St yc = rk4(c, rk4(c, y, 0.5 * hc), 0.5 * hc);
+            // the crossing u = 0 inside this step: Newton on the length of a
+            // partial step from y, each partial step taken like an accepted
+            // one (extrapolated, so of the same order)
+            double hc = h * y.u / (y.u - yn.u), ec = 0.0;
+            St yc = richardson_step(c, y, hc, tol, &ec);
             for (int it = 0; it < 8; ++it) {
                 const double dh = -yc.u / yc.vu;
                 hc += dh;
-                yc = rk4(c, rk4(c, y, 0.5 * hc), 0.5 * hc);
+                yc = richardson_step(c, y, hc, tol, &ec);
                 if (fabs(dh) < 1e-15 * h) break;
             }
             if (!(yc.s > 0.0 && yc.s < A.s_cap)) break;
@@ -313,7 +331,7 @@ extern "C" rtt_status rtt_trace_rays(const rtt_geometry* geom, const rtt_source_
     A.domega = scr->d_omega_pixel;
     A.sqrt_domega = std::sqrt(scr->d_omega_pixel);
     A.step_scale = 0.01;
-    A.tol = 1e-12;
+    A.tol = 1e-14;
     A.valid = d_valid;
     A.r = d_r;
     A.phi = d_phi;

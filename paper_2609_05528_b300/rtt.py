@@ -67,7 +67,8 @@ class OpInfo(ctypes.Structure):
                 ("delay_min", ctypes.c_double * 3), ("delay_max", ctypes.c_double * 3),
                 ("total_rows", ctypes.c_int64), ("total_rows_per_order", ctypes.c_int64 * 3),
                 ("shard_row_begin", ctypes.c_int64),
-                ("shard_index", ctypes.c_int32), ("shard_count", ctypes.c_int32)]
+                ("shard_index", ctypes.c_int32), ("shard_count", ctypes.c_int32),
+                ("weight_precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Shard(ctypes.Structure):
@@ -126,6 +127,7 @@ _SIGS = {
                                                 ctypes.POINTER(TimeGrid), ctypes.POINTER(RayTable),
                                                 ctypes.POINTER(Options), ctypes.POINTER(Shard), vp,
                                                 ctypes.POINTER(vp)]),
+    "rtt_set_weight_precision": (ctypes.c_int, [vp, ctypes.c_int, vp]),
     "rtt_shard_rows": (ctypes.c_int, [ctypes.c_int64, ctypes.POINTER(Shard),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "rtt_op_query": (ctypes.c_int, [vp, ctypes.POINTER(OpInfo)]),
@@ -337,6 +339,15 @@ class Operator:
         self.shard_row_begin, self.total_rows = int(info.shard_row_begin), int(info.total_rows)
         self.total_rows_per_order = tuple(int(v) for v in info.total_rows_per_order)
 
+    def set_weight_precision(self, precision: int, stream=None):
+        """rtt_set_weight_precision: WEIGHTS_FP32 or WEIGHTS_BF16 corner
+        weights for the FP32 applies."""
+        check(lib().rtt_set_weight_precision(self.handle, int(precision), _stream(stream)),
+              "rtt_set_weight_precision")
+        info = OpInfo()
+        check(lib().rtt_op_query(self.handle, ctypes.byref(info)), "rtt_op_query")
+        self.info = info
+
     def arm_rows(self, arm_mask: int = 7) -> int:
         n = ctypes.c_int64(0)
         check(lib().rtt_arm_rows(self.handle, arm_mask, ctypes.byref(n)), "rtt_arm_rows")
@@ -508,6 +519,8 @@ def reach(op: "Operator", info, arm_mask: int = 7, ages=AGES, h: float = 3.0, a0
     return res, passed.astype(bool)
 
 
+WEIGHTS_FP32 = 0  # rtt.h RTT_WEIGHTS_FP32
+WEIGHTS_BF16 = 1  # rtt.h RTT_WEIGHTS_BF16
 MIX_UNRESOLVED = 1  # rtt.h RTT_MIX_UNRESOLVED
 MIX_TOTAL_FLUX = 2  # rtt.h RTT_MIX_TOTAL_FLUX
 GRAM_DATA = 0
