@@ -142,10 +142,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu record, or None
-    when the record is missing or was taken on other kernel sources."""
-    p = os.path.join(ROOT, "profiles", "traffic_kerr256_b8.json")
+def recorded_traffic(kernel: str, workload: str = "kerr256"):
+    """DRAM bytes per launch of `kernel` (the apply A or AT) from the committed
+    ncu record of `workload` at batch 8, or None when the record is missing or
+    was taken on other kernel sources."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload}_b8.json")
     try:
         with open(p) as fh:
             rec = json.load(fh)
@@ -189,13 +190,16 @@ def time_loop(stream, fn, n, flush=None):
 
 
 def roofline_of(op, B, mA, mAT, traffic_key=None):
+    """traffic_key: the workload name of the committed ncu traffic record."""
     ab = algorithmic_bytes(op, B)
     dom, dom_ms = ("A", mA) if mA >= mAT else ("AT", mAT)
     peak, peak_kind = measured_peaks()
     achieved = ab[dom] / (dom_ms * 1e-3) / 1e9
     return ab, {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(dom) if traffic_key else None,
+                "traffic": recorded_traffic(dom, traffic_key) if traffic_key else None,
+                "traffic_other": recorded_traffic("AT" if dom == "A" else "A", traffic_key)
+                if traffic_key else None,
                 "algorithmic_bytes": ab[dom], "source_hash": kernel_source_hash(),
                 "A_frac": ab["A"] / (mA * 1e-3) / 1e9 / peak,
                 "AT_frac": ab["AT"] / (mAT * 1e-3) / 1e9 / peak}
@@ -241,7 +245,7 @@ def run_ours(args, rank, world, device):
     t_A = time_loop(stream, lambda: op.apply_A(x, y), args.steps)
     t_AT = time_loop(stream, lambda: op.apply_AT(y, g), args.steps)
     mA, mAT = float(np.median(t_A)), float(np.median(t_AT))
-    ab, roof = roofline_of(op, BATCH, mA, mAT)
+    ab, roof = roofline_of(op, BATCH, mA, mAT, traffic_key="stress1024")
 
     # the same step replayed from a captured CUDA graph
     graph = None
@@ -348,7 +352,7 @@ def run_ours(args, rank, world, device):
     # each batch size autotuned first; y >= 1.5 GB per history, far above L2
     sweep = []
     peak, _ = measured_peaks()
-    for B in SWEEP_BATCHES:
+    for B in (() if args.no_sweep else SWEEP_BATCHES):
         try:
             tune = op.autotune(B)
             xb = torch.from_numpy(I.uniform_batch(w, range(1, 1 + B)).astype(np.float32)).to(device)
@@ -430,7 +434,7 @@ def run_kerr256(args, world, device):
     ms = float(np.mean(time_loop(stream, step, args.steps, flush)))
     mA = float(np.median(time_loop(stream, lambda: op.apply_A(x, y), args.steps, flush)))
     mAT = float(np.median(time_loop(stream, lambda: op.apply_AT(y, g), args.steps, flush)))
-    _, roof = roofline_of(op, BATCH, mA, mAT, traffic_key=True)
+    _, roof = roofline_of(op, BATCH, mA, mAT, traffic_key="kerr256")
     mix = {}
     try:
         peak_m, _ = measured_peaks()
@@ -447,6 +451,34 @@ def run_kerr256(args, world, device):
            "value": job_value(world, BATCH, ms), "kernels_ms": {"A": mA, "AT": mAT},
            "roofline": roof, "order_mix": mix, "autotune": op.tune,
            "l2": "flushed between timed steps (256 MiB write)"}
+    op.close()
+    return out
+
+
+def run_profile_case(args, device):
+    """The step alone, for profiling: the workload at batch 8 with its
+    autotuned variants, max(warmup, 3) untimed steps, then args.steps steps
+    inside the NVTX range bench_timed (ncu --nvtx-include "bench_timed/")."""
+    import torch
+
+    from paper_2609_05528_b300 import inputs as I
+    w = I.stress1024(0.94) if args.profile == "stress1024" else I.kerr256()
+    _, op, x = build_workload(device, w, BATCH, seed0=100)
+    y = torch.empty((op.arm_rows(7), op.n_frames, BATCH), dtype=torch.float32, device=device)
+    g = torch.empty_like(x)
+    for _ in range(max(args.warmup, 3)):
+        op.apply_A(x, y)
+        op.apply_AT(y, g)
+    torch.cuda.synchronize(device)
+    torch.cuda.nvtx.range_push("bench_timed")
+    for _ in range(args.steps):
+        op.apply_A(x, y)
+        op.apply_AT(y, g)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize(device)
+    out = {"workload": w.name, "batch": BATCH, "steps": args.steps, "variant": op.get_variant(BATCH),
+           "algorithmic_bytes": algorithmic_bytes(op, BATCH), "source_hash": kernel_source_hash(),
+           "status": op.status()}
     op.close()
     return out
 
@@ -568,6 +600,44 @@ def run_audit(device):
         runs[name] = (time.perf_counter() - t, recs)
     tn, rn = runs["class"]
     td, rd = runs["data"]
+    # the class audit is one batched plan over the 24 (geometry, arm) jobs:
+    # create (tables, A_{0,0.999}, buffers), a run (one launch per stage, no
+    # host synchronisation) and the results; a second run and a run replayed
+    # from a captured CUDA graph reuse the plan
+    torch.cuda.synchronize(device)
+    t = time.perf_counter()
+    plan = rtt.AuditPlan(ops, (1, 7))
+    torch.cuda.synchronize(device)
+    t_create = time.perf_counter() - t
+    runs_s = []
+    for _ in range(2):
+        t = time.perf_counter()
+        plan.run()
+        recs_p, _ = plan.results()
+        runs_s.append(time.perf_counter() - t)
+    s = torch.cuda.Stream(device)
+    graph = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize(device)
+    with torch.cuda.stream(s):
+        graph.capture_begin()
+        plan.run(stream=s)
+        graph.capture_end()
+    torch.cuda.synchronize(device)
+    t = time.perf_counter()
+    with torch.cuda.stream(s):
+        graph.replay()
+    recs_g, _ = plan.results(stream=s)
+    t_graph = time.perf_counter() - t
+    out["plan"] = {"jobs": len(ops) * 2, "create_s": round(t_create, 4),
+                   "run_and_results_s": [round(v, 4) for v in runs_s],
+                   "graph_replay_and_results_s": round(t_graph, 4),
+                   "stage_s": {k: round(sum(getattr(r[i], "seconds_" + k) for r in recs_p for i in range(2)), 4)
+                               for k in ("probe", "gram", "eig")},
+                   "graph_records_identical": all(
+                       a[i].rank == b[i].rank and a[i].reach.J_old == b[i].reach.J_old
+                       and a[i].sigma_max == b[i].sigma_max
+                       for a, b in zip(recs_p, recs_g) for i in range(2))}
+    plan.close()
     out["seconds"] = tn
     out["normal_operator_gram_seconds"] = runs["normal"][0]
     out["fp64_data_path_seconds"] = td
@@ -931,12 +1001,18 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-audit", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the batch sweep leg")
     ap.add_argument("--sweep", action="store_true",
                     help="print the stress1024 batch sweep (one JSON line per geometry) and exit")
     ap.add_argument("--recovery", action="store_true",
                     help="print the held-out recovery leg (ridge + TSVD) as one JSON line and exit")
     ap.add_argument("--ladder", action="store_true",
                     help="print the class-ladder audit (Sec. 7-8) as one JSON line and exit")
+    ap.add_argument("--audit", action="store_true",
+                    help="print the 12-geometry audit leg as one JSON line and exit")
+    ap.add_argument("--profile", choices=["stress1024", "kerr256"],
+                    help="for ncu: build the workload at batch 8, autotune, warm up, run --steps "
+                         "A + A^T steps inside the NVTX range bench_timed, and exit")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -990,6 +1066,16 @@ def main():
         if rank == 0:
             torch.cuda.set_device(device)
             print(json.dumps(run_ladder(device)))
+        return
+    if args.audit:
+        if rank == 0:
+            torch.cuda.set_device(device)
+            print(json.dumps(run_audit(device)))
+        return
+    if args.profile:
+        if rank == 0:
+            torch.cuda.set_device(device)
+            print(json.dumps(run_profile_case(args, device)))
         return
     out = run_ours(args, rank, world, device)
     if rank == 0 and world == 1 and not args.no_audit:

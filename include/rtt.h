@@ -713,7 +713,9 @@ typedef struct {
  * normal-operator Gram of Q_dev[g] is taken instead, which then must not be
  * NULL), its spectrum (rtt_eigvals_sym_batched; a matrix with an eigenvalue
  * within 64 d eps max|lambda| of rho^2 is recomputed with the Jacobi
- * eigensolver) and the operational rank.
+ * eigensolver) and the operational rank.  The class modes run as one batched
+ * plan (rtt_audit_plan_*) unless a geometry has rows the class path does not
+ * handle.
  * out: host array [n_ops][n_arms]; sigma_out (optional): host
  * [n_ops][n_arms][d], singular values descending.  Synchronous.
  */
@@ -721,6 +723,39 @@ rtt_status rtt_rank_audit(const rtt_op* ops, int n_ops, const double* const* Q_d
                           const int* arm_masks, int n_arms, int n_ages, const double* ages_host,
                           double h, double quantile, int gram_mode, rtt_audit_record* out,
                           double* sigma_out, void* stream);
+
+/*
+ * Batched audit plan (Sec. 6.2-6.3, the audit of rtt_rank_audit for the
+ * separable classes, one launch per stage over every (geometry, arm) job).
+ * rtt_audit_plan_create: validates, computes each geometry's A_{0,quantile}
+ * (Sec. 4.5), builds every geometry's class tables (factor tables, ray-space
+ * values, per-row temporal blocks of Eq. 21's separable form) and allocates
+ * every buffer of the run; synchronises `stream`.  class_kind:
+ * RTT_CLASS_S224 or RTT_CLASS_L224 (d = 224).  Jobs are geometry-major:
+ * record j = g n_arms + a.
+ * rtt_audit_plan_run: enqueues the run on `stream` with no host
+ * synchronisation and no allocation (capturable in a CUDA graph): the probes
+ * of Eq. 10-12 and 29 of all jobs (FP32 pass; FP64 re-evaluation of the ages
+ * within 1e-3 of rho^2, decided on the device), the class Grams of all jobs,
+ * and their eigenvalues (tridiagonal reduction and bisection).
+ * rtt_audit_plan_results: synchronises `stream` and fills out[n_ops * n_arms]
+ * (and sigma_out [n_ops][n_arms][224], descending, if not NULL) with the
+ * reach and J_old (Eq. 13, 30, 33-35) and the operational rank (Eq. 31); a
+ * spectrum with an eigenvalue within 64 d eps max|lambda| of rho^2 is
+ * recomputed by the Jacobi eigensolver first.  The stage times of the run
+ * (CUDA events) are shared evenly by the records.
+ * Errors: RTT_EINVAL (arguments, null operator), RTT_ESTATE (a row shard; a
+ * geometry with rows the class path does not handle, create; results before
+ * a run), RTT_ENOMEM, RTT_ECUDA.
+ */
+typedef struct rtt_audit_plan_s* rtt_audit_plan;
+rtt_status rtt_audit_plan_create(const rtt_op* ops, int n_ops, const int* arm_masks, int n_arms,
+                                 int n_ages, const double* ages_host, double h, double quantile,
+                                 int class_kind, void* stream, rtt_audit_plan* out);
+rtt_status rtt_audit_plan_run(rtt_audit_plan plan, void* stream);
+rtt_status rtt_audit_plan_results(rtt_audit_plan plan, rtt_audit_record* out, double* sigma_out,
+                                  void* stream);
+rtt_status rtt_audit_plan_destroy(rtt_audit_plan plan);
 
 /*
  * rtt_autotune -- choose the fastest kernel variants of the FP32 applies

@@ -1054,6 +1054,11 @@ rtt_status build_cells(rtt_op_s* op, cudaStream_t st) {
     up(&op->seg_ncol, s_ncol);
     up(&op->seg_rec, s_rec);
     up(&op->gslot, gs);
+    {
+        std::vector<int32_t> cp(cstart.size());
+        for (size_t c = 0; c < cstart.size(); ++c) cp[c] = (int32_t)cstart[c];
+        up(&op->cell_ptr, cp);
+    }
     if (e2 == cudaSuccess) e2 = cudaMalloc(&op->adj_ctr, 16);
     if (e2 == cudaSuccess) e2 = cudaMemset(op->adj_ctr, 0, 16);
     if (e2 != cudaSuccess) return fail("upload");

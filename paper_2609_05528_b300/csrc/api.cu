@@ -224,7 +224,7 @@ static void free_op(rtt_op_s* op) {
                   op->thr,     op->row_order, op->c_row, op->c_col, op->c_K0, op->c_F0, op->c_fb, op->c_r0,
                   op->c_W,     op->c_W64,   op->c_F64, op->seg_ray, op->seg_col, op->seg_ncol,
                   op->seg_rec, op->gslot,   op->adj_ctr, op->cpart, op->row_sched,
-                  op->W16,     op->c_W16,
+                  op->W16,     op->c_W16,   op->cell_ptr,
                   op->dev_status, op->rscratch, op->row_pixel, op->mix.grp_ptr,
                   op->mix.grp_rows, op->mix.row_grp, op->mix.inv32, op->mix.inv64,
                   op->mix.part, op->phi};

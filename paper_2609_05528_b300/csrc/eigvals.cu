@@ -150,6 +150,18 @@ bisect_kernel(const double* d_all, const double* e_all, int n, double* ev_all) {
 
 using namespace rtt;
 
+namespace rtt {
+// eigenvalues of `batch` symmetric n x n matrices (destroying A) into ev,
+// enqueued on st with caller-owned scratch d, e (n batch each) and work
+// (2 n batch)
+cudaError_t launch_eigvals_batched(int n, int batch, double* A, double* d, double* e, double* work,
+                                   double* ev, cudaStream_t st) {
+    tridiag_kernel<<<batch, kEvThreads, 0, st>>>(A, n, d, e, work);
+    bisect_kernel<<<batch, kEvThreads, 0, st>>>(d, e, n, ev);
+    return cudaGetLastError();
+}
+}  // namespace rtt
+
 extern "C" rtt_status rtt_eigvals_sym_batched(int n, int batch, double* A, double* evals_host,
                                               void* stream) {
     if (n < 1 || n > 4096 || batch < 1 || !A || !evals_host) {

@@ -18,6 +18,7 @@
 #include <cub/cub.cuh>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -186,25 +187,19 @@ __device__ __forceinline__ void tile_pair(int t, int& ti, int& tj) {
     ti = tj = 0;
 }
 
-__global__ void __launch_bounds__(kTileThreads)
-class_gram_tiles(const int32_t* row_ptr, ArmSeg seg, const double* S, const int64_t* off,
-                 const double* C, double* partial) {
-    constexpr int NT = kTilesPerDim * (kTilesPerDim + 1) / 2;  // 10
-    __shared__ double Cs[kMaxRayRow * 8][kMaxRayRow * 8 + 1];
-    __shared__ double Ys[kMaxRayRow * 8][kTile + 1];
-    __shared__ double sI[kMaxRayRow][7], sJ[kMaxRayRow][7];
-    const int tile = blockIdx.x % NT, chunk = blockIdx.x / NT;
-    int ti, tj;
-    tile_pair(tile, ti, tj);
-    const int rows_per = (seg.total + kRowChunks - 1) / kRowChunks;
-    const int r_begin = chunk * rows_per, r_end = min(seg.total, r_begin + rows_per);
-    double acc[kTileRegs];
-#pragma unroll
-    for (int j = 0; j < kTileRegs; ++j) acc[j] = 0.0;
+// acc += the (ti, tj) tile of sum over arm rows [r_begin, r_end) of
+// (s_e s_e'^T) (x) C_row; the row's C block starts at C + off[arm row] (the
+// C of the arm's rows) or C + off[operator row] (the C of all rows)
+__device__ __forceinline__ void class_tile_rows(const int32_t* row_ptr, const ArmSeg& seg, const double* S,
+                                                const int64_t* off, bool off_by_row, const double* C,
+                                                int r_begin, int r_end, int ti, int tj, double* acc,
+                                                double (*Cs)[kMaxRayRow * 8 + 1], double (*Ys)[kTile + 1],
+                                                double (*sI)[7], double (*sJ)[7]) {
     for (int i = r_begin; i < r_end; ++i) {
         const int row = arm_row_of(seg, i);
         const int e0 = row_ptr[row], n = row_ptr[row + 1] - e0;
         const int m = 8 * n;
+        const int64_t o = off[off_by_row ? row : i];
         for (int t = threadIdx.x; t < n * 7; t += blockDim.x) {
             const int e = t / 7, l = t % 7;
             sI[e][l] = S[(int64_t)(e0 + e) * 28 + ti * 7 + l];
@@ -212,7 +207,7 @@ class_gram_tiles(const int32_t* row_ptr, ArmSeg seg, const double* S, const int6
         }
         for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
             const int p = t / m, q = t - p * m;
-            Cs[p][q] = C[off[i] + t];
+            Cs[p][q] = C[o + t];
         }
         __syncthreads();
         // Y[(e, c)][(l', c')] = sum_e' sJ[e'][l'] C[(e, c)][(e', c')]
@@ -238,12 +233,101 @@ class_gram_tiles(const int32_t* row_ptr, ArmSeg seg, const double* S, const int6
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kTileThreads)
+class_gram_tiles(const int32_t* row_ptr, ArmSeg seg, const double* S, const int64_t* off,
+                 const double* C, double* partial) {
+    constexpr int NT = kTilesPerDim * (kTilesPerDim + 1) / 2;  // 10
+    __shared__ double Cs[kMaxRayRow * 8][kMaxRayRow * 8 + 1];
+    __shared__ double Ys[kMaxRayRow * 8][kTile + 1];
+    __shared__ double sI[kMaxRayRow][7], sJ[kMaxRayRow][7];
+    const int tile = blockIdx.x % NT, chunk = blockIdx.x / NT;
+    int ti, tj;
+    tile_pair(tile, ti, tj);
+    const int rows_per = (seg.total + kRowChunks - 1) / kRowChunks;
+    const int r_begin = chunk * rows_per, r_end = min(seg.total, r_begin + rows_per);
+    double acc[kTileRegs];
+#pragma unroll
+    for (int j = 0; j < kTileRegs; ++j) acc[j] = 0.0;
+    class_tile_rows(row_ptr, seg, S, off, false, C, r_begin, r_end, ti, tj, acc, Cs, Ys, sI, sJ);
 #pragma unroll
     for (int j = 0; j < kTileRegs; ++j) {
         const int idx = threadIdx.x + kTileThreads * j;
         if (idx < kTile * kTile)
             partial[((int64_t)chunk * NT + tile) * kTile * kTile + idx] = acc[j];
     }
+}
+
+// ---- the class Grams of many (operator, arm) jobs: one launch over the
+// flattened (job, row chunk, tile) items, one reduce over (job, entry)
+struct ClassJob {
+    const int32_t* row_ptr;
+    ArmSeg seg;
+    const double* S;      // the operator's ray space values
+    const int64_t* off;   // C block offset of every operator row
+    const double* C;      // C blocks of all operator rows
+    int item0, n_chunks, rows_per_chunk;
+    double* G;            // 224 x 224 output
+};
+
+__global__ void __launch_bounds__(kTileThreads)
+class_gram_tiles_multi(const ClassJob* __restrict__ jobs, int n_jobs, double* partial) {
+    constexpr int NT = kTilesPerDim * (kTilesPerDim + 1) / 2;
+    __shared__ double Cs[kMaxRayRow * 8][kMaxRayRow * 8 + 1];
+    __shared__ double Ys[kMaxRayRow * 8][kTile + 1];
+    __shared__ double sI[kMaxRayRow][7], sJ[kMaxRayRow][7];
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].item0 <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const ClassJob& J = jobs[lo];
+    const int local = (int)blockIdx.x - J.item0;
+    const int chunk = local / NT, tile = local - chunk * NT;
+    int ti, tj;
+    tile_pair(tile, ti, tj);
+    const int r_begin = chunk * J.rows_per_chunk;
+    const int r_end = min(J.seg.total, r_begin + J.rows_per_chunk);
+    double acc[kTileRegs];
+#pragma unroll
+    for (int j = 0; j < kTileRegs; ++j) acc[j] = 0.0;
+    class_tile_rows(J.row_ptr, J.seg, J.S, J.off, true, J.C, r_begin, r_end, ti, tj, acc, Cs, Ys, sI, sJ);
+#pragma unroll
+    for (int j = 0; j < kTileRegs; ++j) {
+        const int idx = threadIdx.x + kTileThreads * j;
+        if (idx < kTile * kTile) partial[(int64_t)blockIdx.x * kTile * kTile + idx] = acc[j];
+    }
+}
+
+// G_j from its chunks' tiles, chunks in order; lower tiles mirrored, diagonal
+// tiles symmetrised (as class_gram_reduce)
+__global__ void class_gram_reduce_multi(const ClassJob* __restrict__ jobs, const double* partial) {
+    constexpr int NT = kTilesPerDim * (kTilesPerDim + 1) / 2;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= kCD * kCD) return;
+    const ClassJob& J = jobs[blockIdx.y];
+    const int gi = t / kCD, gj = t - gi * kCD;
+    auto sum_at = [&](int a, int b) {
+        const int ti = a / kTile, tj = b / kTile;  // requires ti <= tj
+        int tile = 0;
+        for (int x = 0; x < ti; ++x) tile += kTilesPerDim - x;
+        tile += tj - ti;
+        const int idx = (a - ti * kTile) * kTile + (b - tj * kTile);
+        double v = 0.0;
+        for (int ch = 0; ch < J.n_chunks; ++ch)
+            v += partial[((int64_t)J.item0 + (int64_t)ch * NT + tile) * kTile * kTile + idx];
+        return v;
+    };
+    const int ti = gi / kTile, tj = gj / kTile;
+    double v;
+    if (ti < tj) v = sum_at(gi, gj);
+    else if (ti > tj) v = sum_at(gj, gi);
+    else v = 0.5 * (sum_at(gi, gj) + sum_at(gj, gi));
+    J.G[t] = v;
 }
 
 // G from the partial tiles: chunks summed in order; lower tiles mirrored,
@@ -269,6 +353,151 @@ __global__ void class_gram_reduce(const double* partial, double* G) {
     else if (ti > tj) v = sum_at(gj, gi);
     else v = 0.5 * (sum_at(gi, gj) + sum_at(gj, gi));
     G[t] = v;
+}
+
+// ---- batched class Grams: per operator the factor tables, the ray-space
+// values and the C blocks of all its rows are built once (create); a run is
+// two launches for every (operator, arm) job together
+struct ClassOpTables {
+    double *Rt = nullptr, *Pt = nullptr, *Tt = nullptr, *S = nullptr, *C = nullptr;
+    int64_t* off = nullptr;  // [rows + 1]
+};
+
+struct ClassPlan {
+    std::vector<ClassOpTables> tables;
+    ClassJob* jobs = nullptr;
+    double* partial = nullptr;
+    int n_jobs = 0, n_items = 0;
+};
+
+void class_plan_destroy(ClassPlan* cp) {
+    if (!cp) return;
+    for (auto& t : cp->tables) {
+        void* ps[] = {t.Rt, t.Pt, t.Tt, t.S, t.C, t.off};
+        for (void* q : ps) cudaFree(q);
+    }
+    cudaFree(cp->jobs);
+    cudaFree(cp->partial);
+    delete cp;
+}
+
+// tables of one operator for class `kind` over all its rows (synchronises
+// `st`); RTT_ESTATE if a row has more rays than the class path handles
+static rtt_status class_op_tables(const rtt_op_s* op, int kind, ClassOpTables* t, cudaStream_t st) {
+    ArmSeg all;
+    RTT_TRY(make_seg(op, 7, &all));
+    const int n_r = op->grid.n_r, n_phi = op->grid.n_phi, K = op->time.n_hats;
+    const int64_t R = all.total;
+    int* flag = nullptr;
+    int64_t* sizes = nullptr;
+    void* tmp = nullptr;
+    auto fail = [&](rtt_status s, const char* what) {
+        cudaFree(flag);
+        cudaFree(sizes);
+        cudaFree(tmp);
+        set_error("class plan: %s", what);
+        return s;
+    };
+    if (cudaMalloc(&t->Rt, sizeof(double) * n_r * 4) != cudaSuccess ||
+        cudaMalloc(&t->Pt, sizeof(double) * n_phi * 7) != cudaSuccess ||
+        cudaMalloc(&t->Tt, sizeof(double) * K * 8) != cudaSuccess ||
+        cudaMalloc(&t->S, sizeof(double) * (op->n_rays > 0 ? op->n_rays : 1) * 28) != cudaSuccess ||
+        cudaMalloc(&t->off, sizeof(int64_t) * (R + 1)) != cudaSuccess ||
+        cudaMalloc(&sizes, sizeof(int64_t) * (R + 1)) != cudaSuccess || cudaMalloc(&flag, sizeof(int)) != cudaSuccess)
+        return fail(RTT_ENOMEM, "table allocation failed");
+    const int nf = std::max(std::max(n_r * 4, n_phi * 7), K * 8);
+    class_factor_kernel<<<(nf + 255) / 256, 256, 0, st>>>(n_r, n_phi, K, op->time.t_end, op->time.hat_step,
+                                                          kind, t->Rt, t->Pt, t->Tt);
+    cudaMemsetAsync(flag, 0, sizeof(int), st);
+    cudaMemsetAsync(sizes, 0, sizeof(int64_t) * (R + 1), st);
+    if (R > 0) class_row_sizes<<<(int)((R + 255) / 256), 256, 0, st>>>(op->row_ptr, all, sizes, flag);
+    size_t tb = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tb, sizes, t->off, R + 1, st);
+    if (cudaMalloc(&tmp, tb + 16) != cudaSuccess) return fail(RTT_ENOMEM, "scan scratch allocation failed");
+    cub::DeviceScan::ExclusiveSum(tmp, tb, sizes, t->off, R + 1, st);
+    int flag_h = 0;
+    int64_t total = 0;
+    cudaMemcpyAsync(&flag_h, flag, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(&total, t->off + R, sizeof(int64_t), cudaMemcpyDeviceToHost, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(RTT_ECUDA, "table kernels failed");
+    if (flag_h) return fail(RTT_ESTATE, "a data row has more rays than the class path handles");
+    if (cudaMalloc(&t->C, sizeof(double) * (total > 0 ? total : 1)) != cudaSuccess)
+        return fail(RTT_ENOMEM, "C allocation failed");
+    if (R > 0) {
+        class_ray_space<<<(unsigned)R, 32, 0, st>>>(op->row_ptr, all, op->node00, op->node01, op->W64, n_phi,
+                                                     t->Rt, t->Pt, t->S);
+        class_row_C<<<(unsigned)R, 256, 0, st>>>(op->row_ptr, all, op->K0, op->F0, op->F64, op->frame_D,
+                                                op->time.n_frames, K, t->Tt, t->off, t->C);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return fail(RTT_ECUDA, "class tables failed");
+    cudaFree(flag);
+    cudaFree(sizes);
+    cudaFree(tmp);
+    return RTT_OK;
+}
+
+rtt_status class_plan_create(const rtt_op_s* const* ops, int n_ops, const int* job_op, const ArmSeg* segs,
+                             int n_jobs, int kind, double* G, cudaStream_t st, ClassPlan** out) {
+    *out = nullptr;
+    ClassPlan* cp = new (std::nothrow) ClassPlan();
+    if (!cp) {
+        set_error("class plan: host allocation failed");
+        return RTT_ENOMEM;
+    }
+    cp->tables.resize(n_ops);
+    for (int g = 0; g < n_ops; ++g) {
+        if (ops[g]->time.n_hats < 2) {
+            class_plan_destroy(cp);
+            set_error("class plan: the class Gram needs at least 2 hats");
+            return RTT_EINVAL;
+        }
+        const rtt_status s = class_op_tables(ops[g], kind, &cp->tables[g], st);
+        if (s != RTT_OK) {
+            class_plan_destroy(cp);
+            return s;
+        }
+    }
+    // rows per chunk: the whole list in about 8 waves of 148 chunk-tiles
+    int64_t total_rows = 0;
+    for (int j = 0; j < n_jobs; ++j) total_rows += segs[j].total;
+    int rpc = (int)((total_rows + 1183) / 1184);
+    if (rpc < 64) rpc = 64;
+    constexpr int NT = kTilesPerDim * (kTilesPerDim + 1) / 2;
+    std::vector<ClassJob> jobs(n_jobs);
+    int items = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const rtt_op_s* op = ops[job_op[j]];
+        const ClassOpTables& t = cp->tables[job_op[j]];
+        ClassJob& J = jobs[j];
+        J.row_ptr = op->row_ptr;
+        J.seg = segs[j];
+        J.S = t.S;
+        J.off = t.off;
+        J.C = t.C;
+        J.rows_per_chunk = rpc;
+        J.n_chunks = segs[j].total > 0 ? (segs[j].total + rpc - 1) / rpc : 0;
+        J.item0 = items;
+        J.G = G + (size_t)j * kCD * kCD;
+        items += J.n_chunks * NT;
+    }
+    cp->n_jobs = n_jobs;
+    cp->n_items = items;
+    if (cudaMalloc(&cp->jobs, sizeof(ClassJob) * n_jobs) != cudaSuccess ||
+        cudaMalloc(&cp->partial, sizeof(double) * ((size_t)(items > 0 ? items : 1)) * kTile * kTile) != cudaSuccess ||
+        cudaMemcpy(cp->jobs, jobs.data(), sizeof(ClassJob) * n_jobs, cudaMemcpyHostToDevice) != cudaSuccess) {
+        class_plan_destroy(cp);
+        set_error("class plan: device allocation failed");
+        return RTT_ENOMEM;
+    }
+    *out = cp;
+    return RTT_OK;
+}
+
+cudaError_t class_plan_run(ClassPlan* cp, cudaStream_t st) {
+    if (cp->n_items > 0) class_gram_tiles_multi<<<cp->n_items, kTileThreads, 0, st>>>(cp->jobs, cp->n_jobs, cp->partial);
+    class_gram_reduce_multi<<<dim3((kCD * kCD + 255) / 256, cp->n_jobs), 256, 0, st>>>(cp->jobs, cp->partial);
+    return cudaGetLastError();
 }
 
 }  // namespace rtt

@@ -40,12 +40,105 @@ struct ProbeArgs {
     double* partial;     // [blocks][n_ages]
 };
 
+// one (operator, arm) job of the batched probe passes
+struct ProbeJob {
+    ProbeArgs p;      // p.partial: the partials of all jobs, block-major
+    double scale2;    // scale^2 of the operator
+    double thr;       // rho^2
+    int blk0, nblk;   // the job's blocks in the flattened grid
+};
+constexpr int kProbeItemsPerBlock = 4096;  // (row, frame) items per block of the batched pass
+
 template <typename T>
 __device__ __forceinline__ T expo(T x);
 template <>
 __device__ __forceinline__ float expo<float>(float x) { return __expf(x); }
 template <>
 __device__ __forceinline__ double expo<double>(double x) { return exp(x); }
+
+// The squared responses of the 32 (row, frame) items base + lane (those
+// below n_items) for every age, or only the ages flagged in `mask`, summed
+// over the warp; lane 0 adds each sum to acc[age].
+template <typename T>
+__device__ __forceinline__ void probe_warp(const ProbeArgs& p, int64_t base, int64_t n_items, int lane,
+                                           double* acc, const uint8_t* mask) {
+    const int64_t item = base + lane;
+    const bool live = item < n_items;
+    int row = 0, f = 0;
+    if (live) {
+        const int row_out = (int)(item / p.Tn);
+        f = (int)(item - (int64_t)row_out * p.Tn);
+        int r = row_out;
+        for (int i = 0; i < p.seg.n; ++i) {
+            if (r < p.seg.len[i]) {
+                row = p.seg.begin[i] + r;
+                break;
+            }
+            r -= p.seg.len[i];
+        }
+    }
+    const double t = p.t0 + p.cadence * (double)f;
+    const int e0 = live ? p.row_ptr[row] : 0, e1 = live ? p.row_ptr[row + 1] : 0;
+    if constexpr (sizeof(T) == 4) {
+        // FP32 path: t - Delta_e split once per (frame, ray) into a head
+        // and a tail in FP32, so that x = (head + a) + tail needs only FP32
+        // adds per age (head + a is exact near the cancellation x ~ 0,
+        // and the ages are exact in FP32)
+        constexpr int kRaysReg = 8;
+        float hd[kRaysReg], tl[kRaysReg], wf[kRaysReg];
+        const int nr = e1 - e0 < kRaysReg ? e1 - e0 : kRaysReg;
+#pragma unroll
+        for (int q = 0; q < kRaysReg; ++q) {
+            hd[q] = 0.0f;
+            tl[q] = 0.0f;
+            wf[q] = 0.0f;
+            if (q < nr) {
+                const double b = t - p.delay[e0 + q];
+                hd[q] = (float)b;
+                tl[q] = (float)(b - (double)hd[q]);
+                wf[q] = (float)(p.weight[e0 + q] * p.inv_Nh);
+            }
+        }
+        const float i2h2 = (float)p.inv_2h2;
+        for (int ia = 0; ia < p.n_ages; ++ia) {
+            if (mask && !mask[ia]) continue;
+            const float af = (float)p.ages[ia];
+            float v = 0.0f;
+#pragma unroll
+            for (int q = 0; q < kRaysReg; ++q) {
+                if (q < nr) {
+                    const float x = (hd[q] + af) + tl[q];
+                    const float arg = x * x * i2h2;
+                    if (arg < 100.0f) v += wf[q] * __expf(-arg);
+                }
+            }
+            for (int e = e0 + kRaysReg; e < e1; ++e) {  // rows with more rays
+                const float x = (float)((t - p.delay[e]) + p.ages[ia]);
+                const float arg = x * x * i2h2;
+                if (arg < 100.0f) v += (float)(p.weight[e] * p.inv_Nh) * __expf(-arg);
+            }
+            float sq = v * v;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0) acc[ia] += (double)sq;
+        }
+    } else {
+        for (int ia = 0; ia < p.n_ages; ++ia) {
+            if (mask && !mask[ia]) continue;
+            const double a = p.ages[ia];
+            T v = T(0);
+            for (int e = e0; e < e1; ++e) {
+                const T x = (T)((t - p.delay[e]) + a);
+                const T arg = x * x * (T)p.inv_2h2;
+                if (arg < T(100)) v += (T)(p.weight[e] * p.inv_Nh) * expo<T>(-arg);
+            }
+            T sq = v * v;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+            if (lane == 0) acc[ia] += (double)sq;
+        }
+    }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kProbeThreads) probe_kernel(const ProbeArgs p) {
@@ -58,88 +151,71 @@ __global__ void __launch_bounds__(kProbeThreads) probe_kernel(const ProbeArgs p)
     // same fixed sequence so the partial sums do not depend on timing
     const int64_t warps_total = (int64_t)gridDim.x * (kProbeThreads / 32);
     const int64_t gw = (int64_t)blockIdx.x * (kProbeThreads / 32) + warp;
-    for (int64_t base = gw * 32; base < n_items; base += warps_total * 32) {
-        const int64_t item = base + lane;
-        const bool live = item < n_items;
-        int row = 0, f = 0;
-        if (live) {
-            const int row_out = (int)(item / p.Tn);
-            f = (int)(item - (int64_t)row_out * p.Tn);
-            int r = row_out;
-            for (int i = 0; i < p.seg.n; ++i) {
-                if (r < p.seg.len[i]) {
-                    row = p.seg.begin[i] + r;
-                    break;
-                }
-                r -= p.seg.len[i];
-            }
-        }
-        const double t = p.t0 + p.cadence * (double)f;
-        const int e0 = live ? p.row_ptr[row] : 0, e1 = live ? p.row_ptr[row + 1] : 0;
-        if constexpr (sizeof(T) == 4) {
-            // FP32 path: t - Delta_e split once per (frame, ray) into a head
-            // and a tail in FP32, so that x = (head + a) + tail needs only FP32
-            // adds per age (head + a is exact near the cancellation x ~ 0,
-            // and the ages are exact in FP32)
-            constexpr int kRaysReg = 8;
-            float hd[kRaysReg], tl[kRaysReg], wf[kRaysReg];
-            const int nr = e1 - e0 < kRaysReg ? e1 - e0 : kRaysReg;
-#pragma unroll
-            for (int q = 0; q < kRaysReg; ++q) {
-                hd[q] = 0.0f;
-                tl[q] = 0.0f;
-                wf[q] = 0.0f;
-                if (q < nr) {
-                    const double b = t - p.delay[e0 + q];
-                    hd[q] = (float)b;
-                    tl[q] = (float)(b - (double)hd[q]);
-                    wf[q] = (float)(p.weight[e0 + q] * p.inv_Nh);
-                }
-            }
-            const float i2h2 = (float)p.inv_2h2;
-            for (int ia = 0; ia < p.n_ages; ++ia) {
-                const float af = (float)p.ages[ia];
-                float v = 0.0f;
-#pragma unroll
-                for (int q = 0; q < kRaysReg; ++q) {
-                    if (q < nr) {
-                        const float x = (hd[q] + af) + tl[q];
-                        const float arg = x * x * i2h2;
-                        if (arg < 100.0f) v += wf[q] * __expf(-arg);
-                    }
-                }
-                for (int e = e0 + kRaysReg; e < e1; ++e) {  // rows with more rays
-                    const float x = (float)((t - p.delay[e]) + p.ages[ia]);
-                    const float arg = x * x * i2h2;
-                    if (arg < 100.0f) v += (float)(p.weight[e] * p.inv_Nh) * __expf(-arg);
-                }
-                float sq = v * v;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-                if (lane == 0) acc[warp][ia] += (double)sq;
-            }
-        } else {
-            for (int ia = 0; ia < p.n_ages; ++ia) {
-                const double a = p.ages[ia];
-                T v = T(0);
-                for (int e = e0; e < e1; ++e) {
-                    const T x = (T)((t - p.delay[e]) + a);
-                    const T arg = x * x * (T)p.inv_2h2;
-                    if (arg < T(100)) v += (T)(p.weight[e] * p.inv_Nh) * expo<T>(-arg);
-                }
-                T sq = v * v;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-                if (lane == 0) acc[warp][ia] += (double)sq;
-            }
-        }
-    }
+    for (int64_t base = gw * 32; base < n_items; base += warps_total * 32)
+        probe_warp<T>(p, base, n_items, lane, acc[warp], nullptr);
     __syncthreads();
     for (int a = threadIdx.x; a < p.n_ages; a += kProbeThreads) {
         double s = 0.0;
         for (int w = 0; w < kProbeThreads / 32; ++w) s += acc[w][a];
         p.partial[(int64_t)blockIdx.x * p.n_ages + a] = s;
     }
+}
+
+// ---- the probes of many (operator, arm) jobs in one launch per pass: the
+// jobs' (row, frame) items cut into blocks of kProbeItemsPerBlock, all blocks
+// in one grid (a block finds its job by binary search on the first blocks)
+template <typename T>
+__global__ void __launch_bounds__(kProbeThreads) probe_multi_kernel(const ProbeJob* __restrict__ jobs,
+                                                                    int n_jobs,
+                                                                    const uint8_t* __restrict__ flags) {
+    __shared__ double acc[kProbeThreads / 32][kMaxAges];
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].blk0 <= (int)blockIdx.x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const ProbeArgs p = jobs[lo].p;
+    const int lb = (int)blockIdx.x - jobs[lo].blk0;
+    const uint8_t* mask = flags ? flags + (int64_t)lo * p.n_ages : nullptr;
+    if (mask) {  // the FP64 pass: only jobs with an age near the threshold
+        bool any = false;
+        for (int a = 0; a < p.n_ages; ++a) any = any || mask[a];
+        if (!any) return;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int a = lane; a < p.n_ages; a += 32) acc[warp][a] = 0.0;
+    __syncwarp();
+    const int64_t n_items = (int64_t)p.seg.total * p.Tn;
+    const int64_t i0 = (int64_t)lb * kProbeItemsPerBlock;
+    const int64_t i1 = i0 + kProbeItemsPerBlock < n_items ? i0 + kProbeItemsPerBlock : n_items;
+    for (int64_t base = i0 + warp * 32; base < i1; base += kProbeThreads)
+        probe_warp<T>(p, base, i1, lane, acc[warp], mask);
+    __syncthreads();
+    for (int a = threadIdx.x; a < p.n_ages; a += kProbeThreads) {
+        double s = 0.0;
+        for (int w = 0; w < kProbeThreads / 32; ++w) s += acc[w][a];
+        p.partial[(int64_t)blockIdx.x * p.n_ages + a] = s;
+    }
+}
+
+// info[j][a] = scale^2 x the job's block partials summed in order.  Pass 0
+// (FP32 values) also sets flags[j][a] where the value is within 1e-3 of
+// rho^2; pass 1 (FP64 values) replaces just the flagged entries.
+__global__ void probe_multi_reduce(const ProbeJob* __restrict__ jobs, int n_jobs, int n_ages,
+                                   const double* __restrict__ partial, double* info, uint8_t* flags,
+                                   int pass) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_jobs * n_ages) return;
+    const int j = t / n_ages, a = t - j * n_ages;
+    if (pass == 1 && !flags[t]) return;
+    double s = 0.0;
+    for (int b = 0; b < jobs[j].nblk; ++b) s += partial[(int64_t)(jobs[j].blk0 + b) * n_ages + a];
+    const double v = jobs[j].scale2 * s;
+    info[t] = v;
+    if (pass == 0) flags[t] = fabs(v - jobs[j].thr) <= 1e-3 * jobs[j].thr ? 1 : 0;
 }
 
 __global__ void probe_reduce(const double* partial, int n_blocks, int n_ages, double scale2,
@@ -169,6 +245,111 @@ __global__ void first_reaching(int64_t n, const double* cum, double target, int6
 }
 
 
+// the probe arguments of one operator and arm (Eq. 10-12: N_h from the
+// source annulus area and the probe width h)
+static ProbeArgs probe_args(const rtt_op_s* op, const ArmSeg& seg, int n_ages, const double* ages_dev,
+                            double h, double* partial) {
+    ProbeArgs p{};
+    p.row_ptr = op->row_ptr;
+    p.delay = op->delay;
+    p.weight = op->weight;
+    p.seg = seg;
+    p.Tn = op->time.n_frames;
+    p.t0 = op->time.t0;
+    p.cadence = op->time.cadence;
+    p.inv_2h2 = 1.0 / (2.0 * h * h);
+    const double Nh = std::sqrt(M_PI * (op->grid.r_out * op->grid.r_out -
+                                        op->grid.r_in * op->grid.r_in) * h * std::sqrt(M_PI));
+    p.inv_Nh = 1.0 / Nh;
+    p.n_ages = n_ages;
+    p.ages = ages_dev;
+    p.partial = partial;
+    return p;
+}
+
+// ---- batched probes of many (operator, arm) jobs: all buffers allocated
+// once here; a run is four launches on one stream, no host synchronisation
+struct ProbePlan {
+    int n_jobs = 0, n_ages = 0, blocks = 0;
+    double* ages = nullptr;
+    double* partial = nullptr;
+    double* info = nullptr;
+    uint8_t* flags = nullptr;
+    ProbeJob* jobs = nullptr;
+};
+
+void probe_plan_destroy(ProbePlan* pp) {
+    if (!pp) return;
+    cudaFree(pp->ages);
+    cudaFree(pp->partial);
+    cudaFree(pp->info);
+    cudaFree(pp->flags);
+    cudaFree(pp->jobs);
+    delete pp;
+}
+
+rtt_status probe_plan_create(const rtt_op_s* const* job_ops, const ArmSeg* segs, int n_jobs, int n_ages,
+                             const double* ages_host, double h, ProbePlan** out) {
+    *out = nullptr;
+    if (n_jobs < 1 || n_ages < 1 || n_ages > kMaxAges) {
+        set_error("probe plan: %d jobs, %d ages (1..%d)", n_jobs, n_ages, kMaxAges);
+        return RTT_EINVAL;
+    }
+    ProbePlan* pp = new (std::nothrow) ProbePlan();
+    if (!pp) {
+        set_error("probe plan: host allocation failed");
+        return RTT_ENOMEM;
+    }
+    pp->n_jobs = n_jobs;
+    pp->n_ages = n_ages;
+    std::vector<ProbeJob> jobs(n_jobs);
+    int blocks = 0;
+    for (int j = 0; j < n_jobs; ++j) {
+        const rtt_op_s* op = job_ops[j];
+        const int64_t items = (int64_t)segs[j].total * op->time.n_frames;
+        jobs[j].nblk = (int)((items + kProbeItemsPerBlock - 1) / kProbeItemsPerBlock);
+        if (jobs[j].nblk < 1) jobs[j].nblk = 1;
+        jobs[j].blk0 = blocks;
+        blocks += jobs[j].nblk;
+        jobs[j].scale2 = op->scale * op->scale;
+        jobs[j].thr = op->opt.rho * op->opt.rho;
+    }
+    pp->blocks = blocks;
+    cudaError_t e = cudaMalloc(&pp->ages, (size_t)n_ages * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->partial, (size_t)blocks * n_ages * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->info, (size_t)n_jobs * n_ages * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->flags, (size_t)n_jobs * n_ages);
+    if (e == cudaSuccess) e = cudaMalloc(&pp->jobs, sizeof(ProbeJob) * n_jobs);
+    if (e != cudaSuccess) {
+        probe_plan_destroy(pp);
+        set_error("probe plan: device allocation failed");
+        return RTT_ENOMEM;
+    }
+    for (int j = 0; j < n_jobs; ++j) jobs[j].p = probe_args(job_ops[j], segs[j], n_ages, pp->ages, h, pp->partial);
+    e = cudaMemcpy(pp->ages, ages_host, (size_t)n_ages * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(pp->jobs, jobs.data(), sizeof(ProbeJob) * n_jobs, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        probe_plan_destroy(pp);
+        set_error("probe plan: copy failed");
+        return RTT_ECUDA;
+    }
+    *out = pp;
+    return RTT_OK;
+}
+
+cudaError_t probe_plan_run(ProbePlan* pp, cudaStream_t st) {
+    const int n = pp->n_jobs * pp->n_ages;
+    probe_multi_kernel<float><<<pp->blocks, kProbeThreads, 0, st>>>(pp->jobs, pp->n_jobs, nullptr);
+    probe_multi_reduce<<<(n + 127) / 128, 128, 0, st>>>(pp->jobs, pp->n_jobs, pp->n_ages, pp->partial,
+                                                        pp->info, pp->flags, 0);
+    probe_multi_kernel<double><<<pp->blocks, kProbeThreads, 0, st>>>(pp->jobs, pp->n_jobs, pp->flags);
+    probe_multi_reduce<<<(n + 127) / 128, 128, 0, st>>>(pp->jobs, pp->n_jobs, pp->n_ages, pp->partial,
+                                                        pp->info, pp->flags, 1);
+    return cudaGetLastError();
+}
+
+const double* probe_plan_info(const ProbePlan* pp) { return pp->info; }
+
 static rtt_status run_probe(const rtt_op_s* op, const ArmSeg& seg, int n_ages,
                             const double* ages_h, double h, bool fp64, double* info_h,
                             cudaStream_t st) {
@@ -184,21 +365,7 @@ static rtt_status run_probe(const rtt_op_s* op, const ArmSeg& seg, int n_ages,
         set_error("probe scratch allocation failed: %s", cudaGetErrorString(e));
         return RTT_ENOMEM;
     }
-    ProbeArgs p{};
-    p.row_ptr = op->row_ptr;
-    p.delay = op->delay;
-    p.weight = op->weight;
-    p.seg = seg;
-    p.Tn = op->time.n_frames;
-    p.t0 = op->time.t0;
-    p.cadence = op->time.cadence;
-    p.inv_2h2 = 1.0 / (2.0 * h * h);
-    const double Nh = std::sqrt(M_PI * (op->grid.r_out * op->grid.r_out -
-                                        op->grid.r_in * op->grid.r_in) * h * std::sqrt(M_PI));
-    p.inv_Nh = 1.0 / Nh;
-    p.n_ages = n_ages;
-    p.ages = d_ages;
-    p.partial = d_part;
+    const ProbeArgs p = probe_args(op, seg, n_ages, d_ages, h, d_part);
     e = cudaMemcpyAsync(d_ages, ages_h, n_ages * 8, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) {
         if (fp64)
@@ -289,21 +456,7 @@ extern "C" rtt_status rtt_probe_info_noalloc(rtt_op op, int arm_mask, int n_ages
     s = static_partial_address(&partial);
     if (s != RTT_OK) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    ProbeArgs p{};
-    p.row_ptr = op->row_ptr;
-    p.delay = op->delay;
-    p.weight = op->weight;
-    p.seg = seg;
-    p.Tn = op->time.n_frames;
-    p.t0 = op->time.t0;
-    p.cadence = op->time.cadence;
-    p.inv_2h2 = 1.0 / (2.0 * h * h);
-    const double Nh = std::sqrt(M_PI * (op->grid.r_out * op->grid.r_out -
-                                        op->grid.r_in * op->grid.r_in) * h * std::sqrt(M_PI));
-    p.inv_Nh = 1.0 / Nh;
-    p.n_ages = n_ages;
-    p.ages = ages_dev;
-    p.partial = partial;
+    const ProbeArgs p = probe_args(op, seg, n_ages, ages_dev, h, partial);
     probe_kernel<float><<<kProbeBlocks, kProbeThreads, 0, st>>>(p);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) {

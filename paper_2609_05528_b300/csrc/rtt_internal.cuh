@@ -124,6 +124,7 @@ struct rtt_op_s {
     int32_t* seg_ncol = nullptr; // [n_seg]
     int32_t* seg_rec = nullptr;  // [n_seg]
     int32_t* gslot = nullptr;    // [S][4] records of each node, -1 for none
+    int32_t* cell_ptr = nullptr; // [cells + 1] first cell-ordered ray of each cell (i0 n_phi + j0)
     int32_t n_seg = 0;
     int64_t n_rec = 0;
     int* adj_ctr = nullptr;      // work ticket counter of the adjoint (reset by its gather)
@@ -183,4 +184,20 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
 template <typename T>
 cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const ArmSeg& seg,
                            cudaStream_t st);
+
+// batched audit stages (one launch per stage over all (operator, arm) jobs;
+// buffers allocated at create, no host synchronisation in a run)
+struct ProbePlan;
+rtt_status probe_plan_create(const rtt_op_s* const* job_ops, const ArmSeg* segs, int n_jobs, int n_ages,
+                             const double* ages_host, double h, ProbePlan** out);
+cudaError_t probe_plan_run(ProbePlan* pp, cudaStream_t st);
+const double* probe_plan_info(const ProbePlan* pp);  // device [jobs][ages]
+void probe_plan_destroy(ProbePlan* pp);
+struct ClassPlan;
+rtt_status class_plan_create(const rtt_op_s* const* ops, int n_ops, const int* job_op, const ArmSeg* segs,
+                             int n_jobs, int kind, double* G, cudaStream_t st, ClassPlan** out);
+cudaError_t class_plan_run(ClassPlan* cp, cudaStream_t st);
+void class_plan_destroy(ClassPlan* cp);
+cudaError_t launch_eigvals_batched(int n, int batch, double* A, double* d, double* e, double* work,
+                                   double* ev, cudaStream_t st);
 }  // namespace rtt

@@ -2,11 +2,13 @@
 // gradients and truncated SVD in a representation class.
 //
 // Ridge: (A^T A + lambda I) x = A^T d for n_rhs data columns times n_lambda
-// regularisation values, all in one batch (column c = rhs * n_lambda + l).
-// Vectors and applies are FP32; per-column dot products accumulate in FP64
-// in a fixed order; every `refresh_every` iterations, and at the end, the
-// residual is recomputed in FP64 (FP64 applies on an FP64 copy of x), which
-// keeps the FP32 recurrence from drifting and gives the reported residual.
+// regularisation values, all in one batch (column c = rhs * n_lambda + l),
+// by conjugate gradients preconditioned with M = diag(D) + lambda, D the
+// ray-level diagonal of A^T A (below).  Vectors and applies are FP32;
+// per-column dot products accumulate in FP64 in a fixed order; every
+// `refresh_every` iterations, and at the end, the residual is recomputed in
+// FP64 (FP64 applies on an FP64 copy of x), which keeps the FP32 recurrence
+// from drifting and gives the reported residual.
 // TSVD: x = Q V_r L_r^{-1} V_r^T Q^T A^T d with (V, L) the eigenpairs of the
 // restricted Gram (Eq. 31), FP64, plain GEMMs through cuBLAS.
 #include <cuda_runtime.h>
@@ -14,7 +16,7 @@
 #include <cmath>
 #include <vector>
 
-#include "rtt_internal.cuh"
+#include "kern_common.cuh"
 
 namespace rtt {
 rtt_status gemm_tn_f64(int64_t k, int m, int n, const double* A, int64_t lda, const double* B,
@@ -38,6 +40,59 @@ __global__ void transpose_kernel(const double* __restrict__ in, int64_t rows, in
     }
 }
 
+
+// Ray-level diagonal of A^T A for the preconditioner: for coefficient
+// (node s, hat k), the sum over the rays of the arm whose stencil touches s of
+// W_{e,c}^2 sum_f h_e(f, k)^2, c the corner of e at s and h_e(f, k) the hat
+// weight of frame f (the cross terms between rays of one data row are left
+// out; the preconditioner only sets the convergence rate, never the
+// solution).  One thread per (s, k) walks the rays of the (at most four)
+// cells around s in the cell-ordered table: a fixed order, deterministic.
+__global__ void ridge_diag_kernel(const int32_t* __restrict__ cell_ptr, const int32_t* __restrict__ c_row,
+                                  const int32_t* __restrict__ c_K0, const double* __restrict__ c_F64,
+                                  const double* __restrict__ c_W64, ArmSeg seg, int n_r, int n_phi, int K,
+                                  int Tn, double delta, double* __restrict__ D) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_r * n_phi * K) return;
+    const int s = (int)(t / K), k = (int)(t - (int64_t)s * K);
+    const int i = s / n_phi, j = s - i * n_phi;
+    const int jm = (j + n_phi - 1) % n_phi;
+    // (cell i0, j0; corner of s in that cell): corners ordered (i0 j0),
+    // (i0+1 j0), (i0 j1), (i0+1 j1)
+    const int ci[4] = {i, i - 1, i, i - 1}, cj[4] = {j, j, jm, jm}, corner[4] = {0, 1, 2, 3};
+    double acc = 0.0;
+    for (int q = 0; q < 4; ++q) {
+        if (ci[q] < 0 || ci[q] > n_r - 2) continue;
+        const int cell = ci[q] * n_phi + cj[q];
+        for (int p = cell_ptr[cell]; p < cell_ptr[cell + 1]; ++p) {
+            if (seg_out_row(seg, c_row[p]) < 0) continue;
+            const double w = c_W64[4 * (int64_t)p + corner[q]];
+            // frames with |u0 - f delta - k| < 1, u0 = K0 + F
+            const double u0 = (double)c_K0[p] + c_F64[p];
+            const double fl = floor((u0 - k - 1.0) / delta);
+            if (fl >= (double)Tn) continue;
+            const int f0 = fl < 0.0 ? 0 : (int)fl;
+            double h2 = 0.0;
+            for (int f = f0; f < Tn; ++f) {
+                const double x = u0 - f * delta - k;
+                if (x <= -1.0) break;
+                const double hw = 1.0 - fabs(x);
+                if (hw > 0.0) h2 += hw * hw;
+            }
+            acc += w * w * h2;
+        }
+    }
+    D[t] = acc;
+}
+
+// z = r / (D + lambda) per column (z = r where D + lambda is 0)
+__global__ void ridge_precond(const float* __restrict__ r, const double* __restrict__ D,
+                              const double* __restrict__ lam, int64_t n, int ncol, float* __restrict__ z) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * ncol) return;
+    const double m = D[i / ncol] + lam[i % ncol];
+    z[i] = m > 0.0 ? (float)((double)r[i] / m) : r[i];
+}
 
 constexpr int kDotBlocks = 296;  // fixed grid: deterministic partial order
 constexpr int kDotThreads = 256;
@@ -203,10 +258,11 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
     if (s == RTT_OK) s = ensure_adjoint_scratch(op, ncol, 4);
     if (s != RTT_OK) return s;
     DevBuf buf;
-    float *b1, *r, *p, *Ap, *y;
-    double *lam, *partial, *dots, *coef, *x64, *y64, *g64, *b64, *r64, *b1_64;
+    float *b1, *r, *p, *Ap, *y, *z;
+    double *lam, *partial, *dots, *coef, *x64, *y64, *g64, *b64, *r64, *b1_64, *Dg;
     const int64_t Mm = M > 0 ? M : 1;
     bool ok = buf.get(&b1, N * n_rhs) && buf.get(&r, N * ncol) && buf.get(&p, N * ncol) &&
+              buf.get(&z, N * ncol) && buf.get(&Dg, N) &&
               buf.get(&Ap, N * ncol) && buf.get(&y, Mm * ncol) && buf.get(&lam, ncol) &&
               buf.get(&partial, (size_t)kDotBlocks * ncol) && buf.get(&dots, ncol) &&
               buf.get(&coef, 2 * ncol) && buf.get(&x64, N * ncol) && buf.get(&y64, Mm * ncol) &&
@@ -228,13 +284,23 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
     SOLVE_CUDA(cudaGetLastError());
     SOLVE_CUDA(coldots(b64, b64, N, ncol, partial, dots, st));
     SOLVE_CUDA(cudaMemcpyAsync(bnorm.data(), dots, ncol * 8, cudaMemcpyDeviceToHost, st));
-    // x = 0, r = b, p = r
+    // the preconditioner's diagonal (ray level, this arm's rays)
+    ridge_diag_kernel<<<nb(N), 256, 0, st>>>(op->cell_ptr, op->c_row, op->c_K0, op->c_F64, op->c_W64, seg,
+                                             op->grid.n_r, op->grid.n_phi, op->time.n_hats, op->time.n_frames,
+                                             op->delta, Dg);
+    SOLVE_CUDA(cudaGetLastError());
+    // x = 0, r = b, z = M^-1 r, p = z
     SOLVE_CUDA(cudaMemsetAsync(x, 0, (size_t)N * ncol * 4, st));
     convert<double, float><<<nb(N * ncol), 256, 0, st>>>(b64, r, N * ncol);
     SOLVE_CUDA(cudaGetLastError());
-    SOLVE_CUDA(cudaMemcpyAsync(p, r, (size_t)N * ncol * 4, cudaMemcpyDeviceToDevice, st));
+    ridge_precond<<<nb(N * ncol), 256, 0, st>>>(r, Dg, lam, N, ncol, z);
+    SOLVE_CUDA(cudaGetLastError());
+    SOLVE_CUDA(cudaMemcpyAsync(p, z, (size_t)N * ncol * 4, cudaMemcpyDeviceToDevice, st));
+    std::vector<double> rz(ncol), rz_new(ncol);
     SOLVE_CUDA(coldots(r, r, N, ncol, partial, dots, st));
     SOLVE_CUDA(cudaMemcpyAsync(rr.data(), dots, ncol * 8, cudaMemcpyDeviceToHost, st));
+    SOLVE_CUDA(coldots(r, z, N, ncol, partial, dots, st));
+    SOLVE_CUDA(cudaMemcpyAsync(rz.data(), dots, ncol * 8, cudaMemcpyDeviceToHost, st));
     SOLVE_CUDA(cudaStreamSynchronize(st));
     for (int c = 0; c < ncol; ++c) bnorm[c] = std::sqrt(bnorm[c]);
     std::vector<char> done(ncol, 0);
@@ -258,7 +324,7 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
         SOLVE_CUDA(cudaMemcpyAsync(pap.data(), dots, ncol * 8, cudaMemcpyDeviceToHost, st));
         SOLVE_CUDA(cudaStreamSynchronize(st));
         for (int c = 0; c < ncol; ++c)
-            alpha[c] = (done[c] || !(pap[c] > 0.0)) ? 0.0 : rr[c] / pap[c];
+            alpha[c] = (done[c] || !(pap[c] > 0.0)) ? 0.0 : rz[c] / pap[c];
         SOLVE_CUDA(cudaMemcpyAsync(coef, alpha.data(), ncol * 8, cudaMemcpyHostToDevice, st));
         cg_update_xr<<<nb(N * ncol), 256, 0, st>>>(x, r, p, Ap, coef, N, ncol);
         SOLVE_CUDA(cudaGetLastError());
@@ -270,20 +336,63 @@ extern "C" rtt_status rtt_solve_ridge(rtt_op op, int arm_mask, const float* data
             refresh_residual<<<nb(N * ncol), 256, 0, st>>>(b64, g64, x64, lam, N, ncol, r64, r);
             SOLVE_CUDA(cudaGetLastError());
         }
+        ridge_precond<<<nb(N * ncol), 256, 0, st>>>(r, Dg, lam, N, ncol, z);
+        SOLVE_CUDA(cudaGetLastError());
         SOLVE_CUDA(coldots(r, r, N, ncol, partial, dots, st));
         SOLVE_CUDA(cudaMemcpyAsync(rr_new.data(), dots, ncol * 8, cudaMemcpyDeviceToHost, st));
+        SOLVE_CUDA(coldots(r, z, N, ncol, partial, dots, st));
+        SOLVE_CUDA(cudaMemcpyAsync(rz_new.data(), dots, ncol * 8, cudaMemcpyDeviceToHost, st));
         SOLVE_CUDA(cudaStreamSynchronize(st));
+        // a column stops only on an FP64 residual: right after a refresh (r
+        // was recomputed in FP64 from x), or at the next refresh once the
+        // FP32 recurrence says it has converged
+        const bool refreshed = it % refresh_every == 0;
+        bool want_refresh = false;
+        const std::vector<double> rz_prev = rz;
         all_done = true;
         for (int c = 0; c < ncol; ++c) {
-            beta[c] = done[c] || rr[c] == 0.0 ? 0.0 : rr_new[c] / rr[c];
+            beta[c] = done[c] || rz[c] == 0.0 ? 0.0 : rz_new[c] / rz[c];
             if (!done[c]) {
                 rr[c] = rr_new[c];
-                done[c] = converged(c, rr[c]);
+                rz[c] = rz_new[c];
+                if (converged(c, rr[c])) {
+                    if (refreshed)
+                        done[c] = 1;
+                    else
+                        want_refresh = true;
+                }
             }
             all_done = all_done && done[c];
         }
+        if (want_refresh && !all_done) {
+            // confirm in FP64 now rather than at the next scheduled refresh
+            convert<float, double><<<nb(N * ncol), 256, 0, st>>>(x, x64, N * ncol);
+            SOLVE_CUDA(cudaGetLastError());
+            SOLVE_CUDA(launch_forward<double>(op, x64, y64, ncol, seg, st));
+            SOLVE_CUDA(launch_adjoint<double>(op, y64, g64, ncol, seg, st));
+            refresh_residual<<<nb(N * ncol), 256, 0, st>>>(b64, g64, x64, lam, N, ncol, r64, r);
+            SOLVE_CUDA(cudaGetLastError());
+            ridge_precond<<<nb(N * ncol), 256, 0, st>>>(r, Dg, lam, N, ncol, z);
+            SOLVE_CUDA(cudaGetLastError());
+            SOLVE_CUDA(coldots(r, r, N, ncol, partial, dots, st));
+            SOLVE_CUDA(cudaMemcpyAsync(rr_new.data(), dots, ncol * 8, cudaMemcpyDeviceToHost, st));
+            SOLVE_CUDA(coldots(r, z, N, ncol, partial, dots, st));
+            SOLVE_CUDA(cudaMemcpyAsync(rz_new.data(), dots, ncol * 8, cudaMemcpyDeviceToHost, st));
+            SOLVE_CUDA(cudaStreamSynchronize(st));
+            all_done = true;
+            for (int c = 0; c < ncol; ++c) {
+                if (!done[c]) {
+                    // beta from the refreshed residual, as at a scheduled refresh
+                    beta[c] = rz_prev[c] == 0.0 ? 0.0 : rz_new[c] / rz_prev[c];
+                    rr[c] = rr_new[c];
+                    rz[c] = rz_new[c];
+                    done[c] = converged(c, rr[c]);
+                }
+                all_done = all_done && done[c];
+            }
+        }
         SOLVE_CUDA(cudaMemcpyAsync(coef + ncol, beta.data(), ncol * 8, cudaMemcpyHostToDevice, st));
-        cg_update_p<<<nb(N * ncol), 256, 0, st>>>(p, r, coef + ncol, N, ncol);
+        cg_update_p<<<nb(N * ncol), 256, 0, st>>>(p, z, coef + ncol, N, ncol);
         SOLVE_CUDA(cudaGetLastError());
     }
     // final FP64 residual ||b - (A^T A + lambda) x|| / ||b|| per column

@@ -175,6 +175,12 @@ _SIGS = {
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                       ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, ctypes.POINTER(AuditRecord), dp, vp]),
+    "rtt_audit_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                             ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
+                                             ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(vp)]),
+    "rtt_audit_plan_run": (ctypes.c_int, [vp, vp]),
+    "rtt_audit_plan_results": (ctypes.c_int, [vp, ctypes.POINTER(AuditRecord), dp, vp]),
+    "rtt_audit_plan_destroy": (ctypes.c_int, [vp]),
     "rtt_autotune": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp,
                                     ctypes.POINTER(TuneResult)]),
     "rtt_set_variant": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(Variant)]),
@@ -778,6 +784,49 @@ def rank_audit(ops, Qs, arm_masks=(1, 7), ages=AGES, h: float = 3.0, quantile: f
           "rtt_rank_audit")
     out = [[recs[g * len(arm_masks) + a] for a in range(len(arm_masks))] for g in range(n)]
     return out, sig
+
+
+class AuditPlan:
+    """rtt_audit_plan_*: the class-Gram audit of several geometries as one
+    batched plan (create builds every table; run enqueues the device work
+    only, so it can be replayed or captured in a CUDA graph; results
+    synchronises and returns (records [n_ops][n_arms], sigma [n_ops, n_arms,
+    224]))."""
+
+    def __init__(self, ops, arm_masks=(1, 7), ages=AGES, h: float = 3.0, quantile: float = 0.999,
+                 kind: int = CLASS_S224, stream=None):
+        self._ops = list(ops)  # keeps the operators alive as long as the plan
+        self.n_ops, self.arms = len(self._ops), tuple(int(a) for a in arm_masks)
+        arr_ops = (vp * self.n_ops)(*[o.handle for o in self._ops])
+        arms = (ctypes.c_int * len(self.arms))(*self.arms)
+        ages = np.ascontiguousarray(ages, np.float64)
+        h_out = vp()
+        check(lib().rtt_audit_plan_create(arr_ops, self.n_ops, arms, len(self.arms), ages.shape[0],
+                                          _ptr(ages, dp), h, quantile, int(kind), _stream(stream),
+                                          ctypes.byref(h_out)), "rtt_audit_plan_create")
+        self.handle = h_out
+
+    def run(self, stream=None):
+        check(lib().rtt_audit_plan_run(self.handle, _stream(stream)), "rtt_audit_plan_run")
+
+    def results(self, stream=None):
+        n, na = self.n_ops, len(self.arms)
+        recs = (AuditRecord * (n * na))()
+        sig = np.empty((n, na, 224))
+        check(lib().rtt_audit_plan_results(self.handle, recs, _ptr(sig, dp), _stream(stream)),
+              "rtt_audit_plan_results")
+        return [[recs[g * na + a] for a in range(na)] for g in range(n)], sig
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rtt_audit_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _autograd():

@@ -140,7 +140,7 @@ def test_every_entry_point_rejects_null_arguments(L):
     sizes, returns RTT_EINVAL and sets the error message before it touches a
     GPU (no crash, no CUDA call on the CPU host)."""
     plain = {"rtt_error_string", "rtt_last_error", "rtt_abi_version", "rtt_class_dim",
-             "rtt_destroy"}
+             "rtt_destroy", "rtt_audit_plan_destroy"}
     for name, (_, argtypes) in rtt._SIGS.items():
         if name in plain:
             continue

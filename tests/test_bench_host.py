@@ -67,14 +67,15 @@ def test_job_value_and_launch_count():
     assert [bench.launches_per_step(b) for b in (1, 8, 32, 33, 64)] == [3, 3, 3, 5, 5]
 
 
-def test_traffic_record_only_for_its_sources(monkeypatch):
-    rec = bench.recorded_traffic("AT")
+@pytest.mark.parametrize("workload", ["stress1024", "kerr256"])
+def test_traffic_record_only_for_its_sources(monkeypatch, workload):
+    rec = bench.recorded_traffic("AT", workload)
     if rec is None:
-        pytest.skip("no traffic record for the current apply sources")
+        pytest.skip(f"no {workload} traffic record for the current apply sources")
     assert rec > 0
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
-    assert bench.recorded_traffic("AT") is None
-    assert bench.recorded_traffic("A") is None
+    assert bench.recorded_traffic("AT", workload) is None
+    assert bench.recorded_traffic("A", workload) is None
 
 
 def test_oracle_timing_on_one_core_restores_the_thread_count():
