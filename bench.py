@@ -45,13 +45,15 @@ WORKLOAD_KERR256 = ("kerr256: Kerr a=0.5 i=50deg 256x256 (2x2 ring sub-rays), 64
                     "64 hats, 256 frames, resolved n=0..2")
 
 
-def measured_peaks():
+def measured_peaks(kind: str = "hbm"):
+    """(peak, "measured" | "fallback"): HBM copy GB/s, or (kind="tensor") the
+    burst dense BF16 TFLOP/s."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as fh:
             d = json.load(fh)
-        return float(d["hbm_gbs"]), "measured"
-    return 6400.0, "fallback"
+        return float(d["bf16_tflops" if kind == "tensor" else "hbm_gbs"]), "measured"
+    return (1800.0 if kind == "tensor" else 6400.0), "fallback"
 
 
 class ClockSampler:
@@ -453,6 +455,32 @@ def run_kerr256(args, world, device):
            "l2": "flushed between timed steps (256 MiB write)"}
     op.close()
     return out
+
+
+def run_gemm(args, device):
+    """The tensor-core FP64 contraction C = A^T B on N(0, 1) inputs: CUDA-event
+    time per call (after --warmup calls; --steps timed calls), its FP64 and
+    digit-product rates, cuBLAS DGEMM on the same operands, and the largest
+    error relative to sum_k |A_ki| |B_kj|."""
+    import torch
+
+    from paper_2609_05528_b300 import rtt
+    k, m, n = args.gemm
+    g = torch.Generator(device=device).manual_seed(1)
+    A = torch.randn((k, m), dtype=torch.float64, device=device, generator=g)
+    B = torch.randn((k, n), dtype=torch.float64, device=device, generator=g)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(max(args.warmup, 1)):
+        C = rtt.gemm_tn(A, B)
+    torch.cuda.synchronize(device)
+    t = float(np.median(time_loop(stream, lambda: rtt.gemm_tn(A, B), max(args.steps, 1))))
+    td = float(np.median(time_loop(stream, lambda: A.T @ B, 2)))
+    ref = A.T @ B
+    err = float(((C - ref).abs() / (A.abs().T @ B.abs())).max())
+    peak = measured_peaks(kind="tensor")[0]
+    return {"k": k, "m": m, "n": n, "ms": t, "dgemm_ms": td, "fp64_tflops": 2 * k * m * n / t / 1e9,
+            "digit_product_tflops": 56 * k * m * n / t / 1e9,
+            "frac_of_bf16_peak": 56 * k * m * n / t / 1e9 / peak, "max_err_over_abs_bound": err}
 
 
 def run_profile_case(args, device):
@@ -1010,6 +1038,9 @@ def main():
                     help="print the class-ladder audit (Sec. 7-8) as one JSON line and exit")
     ap.add_argument("--audit", action="store_true",
                     help="print the 12-geometry audit leg as one JSON line and exit")
+    ap.add_argument("--gemm", type=int, nargs=3, metavar=("K", "M", "N"),
+                    help="time rtt_gemm_tn_f64 (C = A^T B, A: K x M, B: K x N, N(0,1) FP64) against "
+                         "cuBLAS DGEMM, print one JSON line and exit")
     ap.add_argument("--profile", choices=["stress1024", "kerr256"],
                     help="for ncu: build the workload at batch 8, autotune, warm up, run --steps "
                          "A + A^T steps inside the NVTX range bench_timed, and exit")
@@ -1071,6 +1102,11 @@ def main():
         if rank == 0:
             torch.cuda.set_device(device)
             print(json.dumps(run_audit(device)))
+        return
+    if args.gemm:
+        if rank == 0:
+            torch.cuda.set_device(device)
+            print(json.dumps(run_gemm(args, device)))
         return
     if args.profile:
         if rank == 0:

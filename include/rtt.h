@@ -782,7 +782,8 @@ typedef struct {
     int32_t batch;
     int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat, 3 staged with TMA corner copies,
                              4 staged with pipelined bulk corner copies, 5 periodic
-                             staged with the whole batch in one chunk */
+                             staged with the whole batch in one chunk, 6 the same with
+                             its table loads one task ahead */
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
     int32_t fwd_staging;  /* staged forward: x items in flight per lane */
@@ -806,7 +807,8 @@ typedef struct {
                              two rays ahead (batch 4 or 8 as one chunk; else staged),
                              5 periodic staged with the whole batch in one chunk and
                              32-bit hat arithmetic (periodic cadences, batch 4 or 8;
-                             else staged) */
+                             else staged), 6 kernel 5 with each task's table loads
+                             issued during the task before it */
     int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32 */
     int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
     int32_t adj_kernel;   /* adjoint: 1 general (any cadence, batch and precision; frames
@@ -823,7 +825,7 @@ typedef struct {
                              order (within each order, by the Morton index of the row's
                              first ray's cell: rows that read the same x nodes run
                              close together) */
-    int32_t fwd_cols;     /* periodic forward (fwd_kernel 5): 0 = all columns in one
+    int32_t fwd_cols;     /* periodic forward (fwd_kernel 5, 6): 0 = all columns in one
                              launch, or a multiple of 4 dividing the batch = the whole
                              operator for that many columns at a time (bounds x's and
                              y's working set for large batches); 0..64 */

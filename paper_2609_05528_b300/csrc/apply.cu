@@ -728,9 +728,144 @@ fwd5_kernel(const __grid_constant__ CUtensorMap xmap, const ApplyArgs<float> a, 
     }
 }
 
+constexpr int kFwd7Warps = 4;
+constexpr int kFwd7MinBlocks = 4;
+
+// one ray's table fields (the forward's per-ray inputs)
+struct Fwd7Ray {
+    int K0, F0, n00, n01;
+    float4 w;
+};
+
+__device__ __forceinline__ Fwd7Ray fwd7_load_ray(const ApplyArgs<float>& a, int e) {
+    Fwd7Ray r;
+    r.K0 = a.K0[e];
+    r.F0 = a.F0[e];
+    r.w = corner_weights(a.W, a.W16, e);
+    r.n00 = a.node00[e];
+    r.n01 = a.node01[e];
+    return r;
+}
+
+// One ray of a periodic forward task: stage the interpolated history of the
+// hats the chunk touches in shared memory, then add each lane's frames.
+template <int BC, int FPL, int P>
+__device__ __forceinline__ void fwd7_ray(const ApplyArgs<float>& a, const Fwd7Ray& rf, int hb, int b0,
+                                         int f_begin, bool full, int lane, float4* zsv,
+                                         float (&acc)[FPL][BC]) {
+    constexpr int Q = BC / 4;
+    constexpr int FC = 32 * FPL;
+    constexpr int ZW = FC / P + 3;         // hats staged per task window
+    constexpr int NU = (ZW * Q + 31) / 32;  // staging items per lane
+    constexpr int HS = 32 / P;             // hat steps per 32 frames
+    constexpr int32_t D = kFracOne / P;
+    const int64_t KB = (int64_t)a.K * a.B;  // floats per node row of x
+    const int B = a.B;                       // hat stride of x
+    // this lane's staging items o = lane + 32 u: hat lane / Q + (32 / Q) u, record lane % Q
+    const int kk0 = lane / Q, q0 = lane % Q;
+    const int32_t lane_off = -lane * D;  // - lane D, the lane's offset inside a hat step pattern
+    const int K0 = rf.K0, F0 = rf.F0;
+    const float4 wv = rf.w;
+    // window [k_lo, k_lo + nwin): k_top = K0 - hb, k_lo = K0 - hb - FC / P + ((F0 + D) >> 24)
+    const int k_top = K0 - hb;
+    const int k_lo = k_top - FC / P + ((F0 + D) >> kFracBits);
+    const float* b00 = a.in + (int64_t)rf.n00 * KB + (int64_t)(k_lo + kk0) * B + b0 + 4 * q0;
+    const float* b01 = a.in + (int64_t)rf.n01 * KB + (int64_t)(k_lo + kk0) * B + b0 + 4 * q0;
+    const int64_t rstep = (int64_t)a.n_phi * KB;  // the radial neighbour's row
+    float4 v[NU][4];
+    if (k_lo >= 0 && k_lo + ZW <= a.K) {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            if (u < NU - 1 || lane + 32 * u < ZW * Q) {
+                const int du = (32 / Q) * u * B;
+                v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
+                v[u][1] = __ldg(reinterpret_cast<const float4*>(b00 + rstep + du));
+                v[u][2] = __ldg(reinterpret_cast<const float4*>(b01 + du));
+                v[u][3] = __ldg(reinterpret_cast<const float4*>(b01 + rstep + du));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int k = k_lo + kk0 + (32 / Q) * u;
+            const bool ok = lane + 32 * u < ZW * Q && k >= 0 && k < a.K;
+            const int du = (32 / Q) * u * B;
+            v[u][0] = v[u][1] = v[u][2] = v[u][3] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok) {
+                v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
+                v[u][1] = __ldg(reinterpret_cast<const float4*>(b00 + rstep + du));
+                v[u][2] = __ldg(reinterpret_cast<const float4*>(b01 + du));
+                v[u][3] = __ldg(reinterpret_cast<const float4*>(b01 + rstep + du));
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        if (u < NU - 1 || lane + 32 * u < ZW * Q) {
+            float2 r = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v[u][0].x, v[u][0].y));
+            r = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v[u][1].x, v[u][1].y), r);
+            r = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v[u][2].x, v[u][2].y), r);
+            r = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v[u][3].x, v[u][3].y), r);
+            float2 t = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v[u][0].z, v[u][0].w));
+            t = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v[u][1].z, v[u][1].w), t);
+            t = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v[u][2].z, v[u][2].w), t);
+            t = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v[u][3].z, v[u][3].w), t);
+            zsv[lane + 32 * u] = make_float4(r.x, r.y, t.x, t.y);
+        }
+    }
+    __syncwarp();
+    // lane's frames f_begin + lane + 32 j: remainder F0 - lane D (one value
+    // per lane: 32 frames are HS whole hat steps), hat index k_top + floor
+    const int32_t rem = F0 + lane_off;
+    const int k00 = k_top + (rem >> kFracBits);
+    const float fr = (float)(rem & kFracMask) * (1.0f / (float)kFracOne);
+    const float g = 1.0f - fr;
+    const float2 g2 = make_float2(g, g), f2 = make_float2(fr, fr);
+    const float4* z0 = zsv + (k00 - k_lo) * Q;
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) {
+        if (full || f_begin + lane + 32 * j < a.Tn) {
+#pragma unroll
+            for (int qq = 0; qq < Q; ++qq) {
+                const float4 p0 = z0[qq - j * HS * Q];
+                const float4 p1 = z0[Q + qq - j * HS * Q];
+                float2 lo = make_float2(acc[j][4 * qq], acc[j][4 * qq + 1]);
+                float2 hi = make_float2(acc[j][4 * qq + 2], acc[j][4 * qq + 3]);
+                lo = __ffma2_rn(g2, make_float2(p0.x, p0.y), lo);
+                lo = __ffma2_rn(f2, make_float2(p1.x, p1.y), lo);
+                hi = __ffma2_rn(g2, make_float2(p0.z, p0.w), hi);
+                hi = __ffma2_rn(f2, make_float2(p1.z, p1.w), hi);
+                acc[j][4 * qq] = lo.x;
+                acc[j][4 * qq + 1] = lo.y;
+                acc[j][4 * qq + 2] = hi.x;
+                acc[j][4 * qq + 3] = hi.y;
+            }
+        }
+    }
+    __syncwarp();
+}
+
+// a periodic forward task's outputs: y written once, 16-byte records
+template <int BC, int FPL>
+__device__ __forceinline__ void fwd7_store(const ApplyArgs<float>& a, int row_out, int b0, int f_begin,
+                                           bool full, int lane, const float (&acc)[FPL][BC]) {
+    constexpr int Q = BC / 4;
+#pragma unroll
+    for (int j = 0; j < FPL; ++j) {
+        const int f = f_begin + lane + 32 * j;
+        if (full || f < a.Tn) {
+            float4* yo = reinterpret_cast<float4*>(a.out + ((int64_t)row_out * a.Tn + f) * a.B + b0);
+#pragma unroll
+            for (int qq = 0; qq < Q; ++qq)
+                yo[qq] = make_float4(acc[j][4 * qq], acc[j][4 * qq + 1], acc[j][4 * qq + 2],
+                                     acc[j][4 * qq + 3]);
+        }
+    }
+}
+
 // Staged forward specialised for a periodic cadence (a frame step is 1 / P of
 // a hat step, P in {2, 4, 8}) with the whole batch in one chunk (B = BC in
-// {4, 8}): the tasks, windows, values and accumulation order of
+// {4, 8, 16}): the tasks, windows, values and accumulation order of
 // fwd3_kernel<float, BC, FPL> (hence the same bits), with
 //  * the hat window and each lane's hat index and fraction in exact 32-bit
 //    arithmetic: a chunk starts on a whole hat step, so U(f) = U0 - f D splits
@@ -741,8 +876,6 @@ fwd5_kernel(const __grid_constant__ CUtensorMap xmap, const ApplyArgs<float> a, 
 //    frames (a uniform branch per ray or task).
 // 4-warp CTAs (4 per SM at <= 128 registers): the same occupancy as 8-warp
 // CTAs, finer blocks for the resident grid's tail (measured faster)
-constexpr int kFwd7Warps = 4;
-constexpr int kFwd7MinBlocks = 4;
 template <int BC, int FPL, int P>
 __global__ void __launch_bounds__(kFwd7Warps * 32, kFwd7MinBlocks)
 fwd7_kernel(const ApplyArgs<float> a) {
@@ -751,20 +884,12 @@ fwd7_kernel(const ApplyArgs<float> a) {
     constexpr int Q = BC / 4;
     constexpr int FC = 32 * FPL;
     static_assert(FC % P == 0, "chunks start on whole hat steps");
-    constexpr int ZW = FC / P + 3;         // hats staged per task window
-    constexpr int NU = (ZW * Q + 31) / 32;  // staging items per lane
-    constexpr int HS = 32 / P;             // hat steps per 32 frames
-    constexpr int32_t D = kFracOne / P;
+    constexpr int ZW = FC / P + 3;
     __shared__ __align__(16) float4 zs_all[kFwd7Warps][ZW * Q];
     float4* zsv = zs_all[threadIdx.x >> 5];
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = (int64_t)blockIdx.x * kFwd7Warps + (threadIdx.x >> 5);
     const int64_t n_warps = (int64_t)gridDim.x * kFwd7Warps;
-    const int64_t KB = (int64_t)a.K * a.B;  // floats per node row of x
-    const int B = a.B;                       // hat stride of x, frame stride of y
-    // this lane's staging items o = lane + 32 u: hat lane / Q + (32 / Q) u, record lane % Q
-    const int kk0 = lane / Q, q0 = lane % Q;
-    const int32_t lane_off = -lane * D;  // - lane D, the lane's offset inside a hat step pattern
     for (TaskWalk tw(warp_global, n_warps, a.n_bchunk, a.n_fchunk); tw.r < a.seg.total; tw.next()) {
         const int b0 = tw.b * BC;
         int row_out, row;
@@ -778,101 +903,87 @@ fwd7_kernel(const ApplyArgs<float> a) {
 #pragma unroll
             for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
         const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
-        for (int e = e_begin; e < e_end; ++e) {
-            const int K0 = a.K0[e], F0 = a.F0[e];
-            const float4 wv = corner_weights(a.W, a.W16, e);
-            const int n00 = a.node00[e], n01 = a.node01[e];
-            // window [k_lo, k_lo + nwin): k_top = K0 - hb, k_lo = K0 - hb - FC / P + ((F0 + D) >> 24)
-            const int k_top = K0 - hb;
-            const int k_lo = k_top - FC / P + ((F0 + D) >> kFracBits);
-            const int nwin = k_top + 2 - k_lo;
-            const float* b00 = a.in + (int64_t)n00 * KB + (int64_t)(k_lo + kk0) * B + b0 + 4 * q0;
-            const float* b01 = a.in + (int64_t)n01 * KB + (int64_t)(k_lo + kk0) * B + b0 + 4 * q0;
-            const int64_t rstep = (int64_t)a.n_phi * KB;  // the radial neighbour's row
-            float4 v[NU][4];
-            if (k_lo >= 0 && k_lo + ZW <= a.K) {
-#pragma unroll
-                for (int u = 0; u < NU; ++u) {
-                    if (u < NU - 1 || lane + 32 * u < ZW * Q) {
-                        const int du = (32 / Q) * u * B;
-                        v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
-                        v[u][1] = __ldg(reinterpret_cast<const float4*>(b00 + rstep + du));
-                        v[u][2] = __ldg(reinterpret_cast<const float4*>(b01 + du));
-                        v[u][3] = __ldg(reinterpret_cast<const float4*>(b01 + rstep + du));
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < NU; ++u) {
-                    const int k = k_lo + kk0 + (32 / Q) * u;
-                    const bool ok = lane + 32 * u < ZW * Q && k >= 0 && k < a.K;
-                    const int du = (32 / Q) * u * B;
-                    v[u][0] = v[u][1] = v[u][2] = v[u][3] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (ok) {
-                        v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
-                        v[u][1] = __ldg(reinterpret_cast<const float4*>(b00 + rstep + du));
-                        v[u][2] = __ldg(reinterpret_cast<const float4*>(b01 + du));
-                        v[u][3] = __ldg(reinterpret_cast<const float4*>(b01 + rstep + du));
-                    }
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < NU; ++u) {
-                if (u < NU - 1 || lane + 32 * u < ZW * Q) {
-                    float2 r = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v[u][0].x, v[u][0].y));
-                    r = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v[u][1].x, v[u][1].y), r);
-                    r = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v[u][2].x, v[u][2].y), r);
-                    r = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v[u][3].x, v[u][3].y), r);
-                    float2 t = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v[u][0].z, v[u][0].w));
-                    t = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v[u][1].z, v[u][1].w), t);
-                    t = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v[u][2].z, v[u][2].w), t);
-                    t = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v[u][3].z, v[u][3].w), t);
-                    zsv[lane + 32 * u] = make_float4(r.x, r.y, t.x, t.y);
-                }
-            }
-            (void)nwin;
-            __syncwarp();
-            // lane's frames f_begin + lane + 32 j: remainder F0 - lane D (one value
-            // per lane: 32 frames are HS whole hat steps), hat index k_top + floor
-            const int32_t rem = F0 + lane_off;
-            const int k00 = k_top + (rem >> kFracBits);
-            const float fr = (float)(rem & kFracMask) * (1.0f / (float)kFracOne);
-            const float g = 1.0f - fr;
-            const float2 g2 = make_float2(g, g), f2 = make_float2(fr, fr);
-            const float4* z0 = zsv + (k00 - k_lo) * Q;
-#pragma unroll
-            for (int j = 0; j < FPL; ++j) {
-                if (full || f_begin + lane + 32 * j < a.Tn) {
-#pragma unroll
-                    for (int qq = 0; qq < Q; ++qq) {
-                        const float4 p0 = z0[qq - j * HS * Q];
-                        const float4 p1 = z0[Q + qq - j * HS * Q];
-                        float2 lo = make_float2(acc[j][4 * qq], acc[j][4 * qq + 1]);
-                        float2 hi = make_float2(acc[j][4 * qq + 2], acc[j][4 * qq + 3]);
-                        lo = __ffma2_rn(g2, make_float2(p0.x, p0.y), lo);
-                        lo = __ffma2_rn(f2, make_float2(p1.x, p1.y), lo);
-                        hi = __ffma2_rn(g2, make_float2(p0.z, p0.w), hi);
-                        hi = __ffma2_rn(f2, make_float2(p1.z, p1.w), hi);
-                        acc[j][4 * qq] = lo.x;
-                        acc[j][4 * qq + 1] = lo.y;
-                        acc[j][4 * qq + 2] = hi.x;
-                        acc[j][4 * qq + 3] = hi.y;
-                    }
-                }
-            }
-            __syncwarp();
+        for (int e = e_begin; e < e_end; ++e)
+            fwd7_ray<BC, FPL, P>(a, fwd7_load_ray(a, e), hb, b0, f_begin, full, lane, zsv, acc);
+        fwd7_store<BC, FPL>(a, row_out, b0, f_begin, full, lane, acc);
+    }
+}
+
+// fwd7 with the table loads moved ahead of the work that needs them: while a
+// task is processed, the next task's first ray and the row range of the task
+// after it are already on their way, and inside a task the next ray's fields
+// load during the current ray.  Same tasks, arithmetic and order as fwd7 (the
+// same bits); 3 CTAs per SM for the extra registers.
+constexpr int kFwd8MinBlocks = 3;
+template <int BC, int FPL, int P>
+__global__ void __launch_bounds__(kFwd7Warps * 32, kFwd8MinBlocks)
+fwd8_kernel(const ApplyArgs<float> a) {
+    static_assert(BC == 4 || BC == 8 || BC == 16, "16-byte batch records");
+    wait_prior_grid();
+    constexpr int Q = BC / 4;
+    constexpr int FC = 32 * FPL;
+    static_assert(FC % P == 0, "chunks start on whole hat steps");
+    constexpr int ZW = FC / P + 3;
+    __shared__ __align__(16) float4 zs_all[kFwd7Warps][ZW * Q];
+    float4* zsv = zs_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kFwd7Warps + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kFwd7Warps;
+    const int n_rows = a.seg.total;
+    TaskWalk tw(warp_global, n_warps, a.n_bchunk, a.n_fchunk);
+    if (tw.r >= n_rows) return;
+    int row_out, row;
+    task_row(a, tw.r, row_out, row);
+    int eb = a.row_ptr[row], ee = a.row_ptr[row + 1];
+    TaskWalk tn = tw;
+    tn.next();
+    int row_out_n = 0, eb_n = 0, ee_n = 0;
+    if (tn.r < n_rows) {
+        int rn;
+        task_row(a, tn.r, row_out_n, rn);
+        eb_n = a.row_ptr[rn];
+        ee_n = a.row_ptr[rn + 1];
+    }
+    Fwd7Ray cur{};
+    if (eb < ee) cur = fwd7_load_ray(a, eb);
+    while (true) {
+        // ahead: the next task's first ray, the row range of the task after it
+        Fwd7Ray nxt{};
+        if (tn.r < n_rows && eb_n < ee_n) nxt = fwd7_load_ray(a, eb_n);
+        TaskWalk tnn = tn;
+        tnn.next();
+        int row_out_nn = 0, eb_nn = 0, ee_nn = 0;
+        if (tnn.r < n_rows) {
+            int r2;
+            task_row(a, tnn.r, row_out_nn, r2);
+            eb_nn = a.row_ptr[r2];
+            ee_nn = a.row_ptr[r2 + 1];
         }
+        const int b0 = tw.b * BC;
+        const int f_begin = tw.f * FC;
+        const bool full = f_begin + FC <= a.Tn;
+        const int hb = f_begin / P;
+        float acc[FPL][BC];
 #pragma unroll
-        for (int j = 0; j < FPL; ++j) {
-            const int f = f_begin + lane + 32 * j;
-            if (full || f < a.Tn) {
-                float4* yo = reinterpret_cast<float4*>(a.out + ((int64_t)row_out * a.Tn + f) * B + b0);
+        for (int j = 0; j < FPL; ++j)
 #pragma unroll
-                for (int qq = 0; qq < Q; ++qq)
-                    yo[qq] = make_float4(acc[j][4 * qq], acc[j][4 * qq + 1], acc[j][4 * qq + 2],
-                                         acc[j][4 * qq + 3]);
-            }
+            for (int b = 0; b < BC; ++b) acc[j][b] = 0.0f;
+        for (int e = eb; e < ee; ++e) {
+            const Fwd7Ray rf = cur;
+            if (e + 1 < ee) cur = fwd7_load_ray(a, e + 1);
+            fwd7_ray<BC, FPL, P>(a, rf, hb, b0, f_begin, full, lane, zsv, acc);
         }
+        fwd7_store<BC, FPL>(a, row_out, b0, f_begin, full, lane, acc);
+        if (tn.r >= n_rows) break;
+        tw = tn;
+        row_out = row_out_n;
+        eb = eb_n;
+        ee = ee_n;
+        cur = nxt;
+        tn = tnn;
+        row_out_n = row_out_nn;
+        eb_n = eb_nn;
+        ee_n = ee_nn;
     }
 }
 
@@ -1314,7 +1425,7 @@ static cudaError_t launch_fwd6(ApplyArgs<float> a, cudaStream_t st) {
 // cadence is P in {2, 4, 8} frames per hat and the whole batch (B = BC in
 // {4, 8}) is one chunk of 16-byte-aligned records
 template <int BC, int FPL>
-static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st) {
+static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st, bool prefetch) {
     const int P = frames_per_hat(a.D);
     if (!vec_ok(a) || a.B % BC != 0 || P == 0 || (32 * FPL) % P != 0) return cudaErrorNotSupported;
     a.FC = 32 * FPL;
@@ -1326,6 +1437,13 @@ static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st) {
         const int grid = resident_grid(kern, kFwd7Warps * 32, 0, a.n_tasks, kFwd7Warps);
         return launch_dependent(kern, dim3(grid), dim3(kFwd7Warps * 32), 0, st, a);
     };
+    if (prefetch) {
+        switch (P) {
+            case 2: return go(fwd8_kernel<BC, FPL, 2>);
+            case 4: return go(fwd8_kernel<BC, FPL, 4>);
+            default: return go(fwd8_kernel<BC, FPL, 8>);
+        }
+    }
     switch (P) {
         case 2: return go(fwd7_kernel<BC, FPL, 2>);
         case 4: return go(fwd7_kernel<BC, FPL, 4>);
@@ -1409,12 +1527,12 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
                 default: break;  // not a periodic cadence: staged kernel
             }
         }
-        if (v.fwd == 5 && (bc == 4 || bc == 8 || bc == 16)) {
-            const bool half = v.fwd_half != 0;
+        if ((v.fwd == 5 || v.fwd == 6) && (bc == 4 || bc == 8 || bc == 16)) {
+            const bool half = v.fwd_half != 0, pf = v.fwd == 6;
             auto go = [&](const ApplyArgs<float>& aa) {
-                if (bc == 16) return half ? launch_fwd7<16, 1>(aa, st) : launch_fwd7<16, 2>(aa, st);
-                return bc == 4 ? (half ? launch_fwd7<4, 4>(aa, st) : launch_fwd7<4, 8>(aa, st))
-                               : (half ? launch_fwd7<8, 2>(aa, st) : launch_fwd7<8, 4>(aa, st));
+                if (bc == 16) return half ? launch_fwd7<16, 1>(aa, st, pf) : launch_fwd7<16, 2>(aa, st, pf);
+                return bc == 4 ? (half ? launch_fwd7<4, 4>(aa, st, pf) : launch_fwd7<4, 8>(aa, st, pf))
+                               : (half ? launch_fwd7<8, 2>(aa, st, pf) : launch_fwd7<8, 4>(aa, st, pf));
             };
             cudaError_t e;
             const int pc = v.fwd_cols;

@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 
 #include <climits>
+#include <mutex>
 #include <vector>
 
 #include "kern_common.cuh"
@@ -433,6 +434,15 @@ __global__ void __launch_bounds__(kOzThreads, 1) oz_gemm_kernel(const OzArgs a) 
 // ---- host ---------------------------------------------------------------------
 static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// grow-only workspace per device (kept for the life of the process)
+struct OzWorkspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+constexpr int kOzMaxDevices = 64;
+static OzWorkspace g_oz_ws[kOzMaxDevices];
+static std::mutex g_oz_ws_mu[kOzMaxDevices];
+
 // C (m x n, row stride ldc) = A^T B with A: k x m (row stride lda), B: k x n
 // (row stride ldb), all FP64 device memory.  Workspace is allocated here.
 rtt_status gemm_tn_f64(int64_t k, int m, int n, const double* A, int64_t lda, const double* B,
@@ -470,25 +480,40 @@ rtt_status gemm_tn_f64(int64_t k, int m, int n, const double* A, int64_t lda, co
     splits = (int)((k_pad + k_per - 1) / k_per);
     const int units = tiles * splits;
     const int grid = units < sms ? units : sms;
-    __nv_bfloat16 *sa = nullptr, *sb = nullptr;
-    int* ex = nullptr;
-    long long* acc = nullptr;
+    // the workspace: digit slices of A and B, column exponents, integer
+    // accumulators, from one grow-only per-device buffer held while the call
+    // runs (the call synchronises its stream before it returns)
     const size_t bytes_a = (size_t)kOzDigits * m_pad * k_pad * 2, bytes_b = (size_t)kOzDigits * n_pad * k_pad * 2;
-    cudaError_t e = cudaMalloc(&sa, bytes_a);
-    if (e == cudaSuccess) e = cudaMalloc(&sb, bytes_b);
-    if (e == cudaSuccess) e = cudaMalloc(&ex, (size_t)(m + n) * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&acc, (size_t)m_pad * n_pad * 16);
-    auto done = [&](rtt_status s) {
-        cudaFree(sa);
-        cudaFree(sb);
-        cudaFree(ex);
-        cudaFree(acc);
-        return s;
-    };
-    if (e != cudaSuccess) {
-        set_error("gemm: workspace allocation failed");
-        return done(RTT_ENOMEM);
+    const size_t off_b = (bytes_a + 255) / 256 * 256, off_x = off_b + (bytes_b + 255) / 256 * 256;
+    const size_t off_acc = off_x + ((size_t)(m + n) * 4 + 255) / 256 * 256;
+    const size_t total = off_acc + (size_t)m_pad * n_pad * 16;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kOzMaxDevices) {
+        set_error("gemm: device %d beyond the workspace table", dev);
+        return RTT_EINVAL;
     }
+    std::lock_guard<std::mutex> lock(g_oz_ws_mu[dev]);
+    OzWorkspace& ws = g_oz_ws[dev];
+    cudaError_t e = cudaSuccess;
+    if (ws.bytes < total) {
+        cudaFree(ws.ptr);
+        ws.ptr = nullptr;
+        ws.bytes = 0;
+        e = cudaMalloc(&ws.ptr, total);
+        if (e != cudaSuccess) {
+            ws.ptr = nullptr;
+            set_error("gemm: workspace allocation of %zu bytes failed", total);
+            return RTT_ENOMEM;
+        }
+        ws.bytes = total;
+    }
+    unsigned char* base = static_cast<unsigned char*>(ws.ptr);
+    __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(base);
+    __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(base + off_b);
+    int* ex = reinterpret_cast<int*>(base + off_x);
+    long long* acc = reinterpret_cast<long long*>(base + off_acc);
+    auto done = [&](rtt_status s) { return s; };
     std::vector<int> init(m + n, INT_MIN);
     cudaMemcpyAsync(ex, init.data(), (size_t)(m + n) * 4, cudaMemcpyHostToDevice, st);
     cudaMemsetAsync(acc, 0, (size_t)m_pad * n_pad * 16, st);
@@ -527,7 +552,7 @@ rtt_status gemm_tn_f64(int64_t k, int m, int n, const double* A, int64_t lda, co
         oz_finish<<<(unsigned)(((int64_t)m * n + 255) / 256), 256, 0, st>>>(m, n, acc, ex, ex + m, n_pad, C, ldc);
         e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // before the workspace is freed
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // before the workspace is reused
     if (e != cudaSuccess) {
         set_error("gemm: %s", cudaGetErrorString(e));
         return done(RTT_ECUDA);

@@ -47,7 +47,8 @@ rtt_status make_seg(const struct ::rtt_op_s* op, int mask, ArmSeg* s);
 struct ApplyVariant {
     int8_t fwd = 0;     // forward: 1 staged z (fwd3), 2 lane-per-hat shuffles (fwd4),
                         // 3 TMA corner slabs (fwd5), 4 pipelined bulk corner copies
-                        // (fwd6), 5 periodic one-chunk staged (fwd7)
+                        // (fwd6), 5 periodic one-chunk staged (fwd7), 6 the same with its
+                        // table loads one task ahead (fwd8)
     int8_t fwd_bc = 0;  // batch entries per forward task (power of two)
     int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
     int8_t fwd_su = 2;   // staged forward: staging items in flight per lane (1, 2 or 3)

@@ -69,7 +69,7 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
         return RTT_OK;
     }
     const int bc = v->fwd_bc;
-    if (v->fwd_kernel < 1 || v->fwd_kernel > 5 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
+    if (v->fwd_kernel < 1 || v->fwd_kernel > 6 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
         v->fwd_half < 0 || v->fwd_half > 1 || v->adj_kernel < 1 || v->adj_kernel > 4) {
         set_error("invalid variant (fwd %d bc %d half %d adj %d)", v->fwd_kernel, bc, v->fwd_half,
                   v->adj_kernel);
@@ -186,7 +186,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     const float fwd_rule = time_it(rule, false);
     float fwd_best = fwd_rule;
     const bool x_vec = (B % 4) == 0;  // 16-byte batch records: TMA forward possible
-    for (int kind = 1; kind <= 5; ++kind)
+    for (int kind = 1; kind <= 6; ++kind)
         for (int bc = bc_max; bc >= 1 && bc >= bc_max / 4; bc >>= 1)
             for (int half = 0; half <= (kind != 2 && bc < 32 ? 1 : 0); ++half) {
                 ApplyVariant v = rule;
@@ -196,8 +196,8 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                 if (kind == 2 && (!periodic || bc > 8)) continue;  // lane-per-hat: <= 8 per task
                 if (kind == 3 && (!x_vec || bc < 4)) continue;    // TMA: 16-byte records
                 if (kind == 4 && (bc != B || (bc != 4 && bc != 8))) continue;  // one chunk
-                if (kind == 5 && (B % bc != 0 || (bc != 4 && bc != 8 && bc != 16))) continue;
-                if (kind == 5 && !periodic) continue;  // periodic specialisation
+                if (kind >= 5 && (B % bc != 0 || (bc != 4 && bc != 8 && bc != 16))) continue;
+                if (kind >= 5 && !periodic) continue;  // periodic specialisation
                 for (int su = 1; su <= 3; ++su) {
                     // staging depth: only the staged kernel at 4 or 8 entries, full frames
                     if (su != 2 && (kind != 1 || half || (bc != 4 && bc != 8))) continue;
@@ -223,7 +223,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
         }
     }
     // forward column passes of 8 columns (large batches of the periodic forward)
-    if (best.fwd == 5 && B > 8 && B % 8 == 0) {
+    if ((best.fwd == 5 || best.fwd == 6) && B > 8 && B % 8 == 0) {
         ApplyVariant v = best;
         v.fwd_cols = 8;
         const float ms = time_it(v, false);

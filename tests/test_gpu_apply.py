@@ -175,7 +175,7 @@ def test_autotune_keeps_bits(B):
     g0 = c.op.apply_AT(y0)
     r = c.op.autotune(B)
     assert r["batch"] == B and r["candidates"] >= 4
-    assert r["fwd_kernel"] in (1, 2, 3, 4, 5) and r["adj_kernel"] in (1, 2, 3, 4)
+    assert r["fwd_kernel"] in (1, 2, 3, 4, 5, 6) and r["adj_kernel"] in (1, 2, 3, 4)
     if B % 4:
         assert r["adj_kernel"] <= 2  # the TMA adjoint needs 16-byte frame records
     assert 0 < r["fwd_ms"] <= r["fwd_ms_rule"] and 0 < r["adj_ms"] <= r["adj_ms_rule"]
@@ -205,7 +205,7 @@ def test_every_variant_same_bits(which, small, schw, B):
     while bc_max < min(B, 32):
         bc_max *= 2
     n = 0
-    for fk in (1, 2, 3, 4, 5):
+    for fk in (1, 2, 3, 4, 5, 6):
         for bc in sorted({bc_max, max(1, bc_max // 2), max(1, bc_max // 4)}):
             for half in (0, 1):
                 for su in ((1, 2, 3) if (fk == 1 and half == 0 and bc in (4, 8)) else (2,)):
