@@ -823,15 +823,28 @@ def run_ladder(device):
             Q = rtt.synth_class(op, kind)
             rec = {"class": name, "dim": int(Q.shape[2])}
             for arm, tag in ((1, "direct"), (7, "resolved")):
+                torch.cuda.synchronize(device)
+                tg = time.perf_counter()
                 G = rtt.gram(op, Q, arm, mode=rtt.GRAM_NORMAL)
                 diag_zero = int((torch.diagonal(G) == 0).sum())
                 ev = rtt.eigvals_sym_batched(G[None])[0]
                 sig = np.sqrt(np.maximum(ev, 0.0))
+                rec[tag + "_gram_and_eig_s"] = round(time.perf_counter() - tg, 3)
                 rec[tag + "_rank"] = int(np.count_nonzero(sig >= 1.0))
                 rec[tag + "_zero_columns"] = diag_zero
                 rec[tag + "_sigma_max"] = float(sig[-1])
                 rec[tag + "_sigma_min_at_or_above_rho"] = float(sig[sig >= 1.0].min()) if (sig >= 1.0).any() else None
                 del G
+            # the adaptive randomized range finder (blocks of 256 seeded
+            # Gaussian vectors, FP64 Ritz values) on the resolved arm
+            d = int(Q.shape[2])
+            nbk = (d + 255) // 256 + 1
+            omega = I.normals(7000 + d, d * 256 * nbk).reshape(d, 256 * nbk)
+            torch.cuda.synchronize(device)
+            tr = time.perf_counter()
+            sig_rf, rank_rf, blocks = rtt.range_finder(op, Q, omega, 7, 256, 1.0)
+            rec["range_finder_resolved"] = {"rank": rank_rf, "blocks": blocks, "basis": int(sig_rf.shape[0]),
+                                            "seconds": round(time.perf_counter() - tr, 3)}
             del Q
             torch.cuda.synchronize(device)
             rec["seconds"] = round(time.perf_counter() - t, 3)

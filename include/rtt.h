@@ -632,6 +632,33 @@ rtt_status rtt_gemm_tn_f64(int64_t k, int m, int n, const double* A_dev, int64_t
                            void* stream);
 
 /*
+ * rtt_range_finder -- adaptive randomized range finder with an FP64
+ * projected eigensolve for the spectrum of the restricted normal operator
+ * H = Q^T A^T A Q of a class (Sec. 7-8, the spectra of the larger classes;
+ * Eq. 31).  Q_dev: double [n_nodes][n_hats][d] (device); omega_host: the
+ * caller's Gaussian draws, double [d][block * max_blocks] row-major (block
+ * i = columns i*block .. i*block + block - 1).  Per block: Y = H Omega_i
+ * (FP64 applies of A and A^T, contractions with Q by rtt_gemm_tn_f64), Y
+ * made orthogonal to the basis found so far (twice) and orthonormal by
+ * Householder QR with column pivoting (FP64, host; columns whose pivot is
+ * below 1e-12 of Y's largest column norm dropped), then the Ritz values of H
+ * on the whole basis (its Gram with H applied, Jacobi eigensolver).  Stops after a block that adds no Ritz value at or
+ * above rho^2, once the basis has d vectors, or after max_blocks.  Ritz
+ * values never exceed H's eigenvalues, so *rank_out (sigma >= rho, sigma =
+ * sqrt of a Ritz value) never exceeds the operational rank, and equals it
+ * once the basis spans the class.  sigma_out: host, capacity d, the
+ * *n_sigma_out singular values descending; blocks_out (optional): blocks
+ * used.  Synchronous.
+ * Errors: RTT_EINVAL, RTT_ESTATE (row shard), RTT_ENOMEM, RTT_ECUDA,
+ * RTT_ETIMEOUT (a bounded device wait of the contraction timed out),
+ * RTT_ENOTCONVERGED (the eigensolver).
+ */
+rtt_status rtt_range_finder(rtt_op op, int arm_mask, const double* Q_dev, int d, int block,
+                            int max_blocks, const double* omega_host, double rho,
+                            double* sigma_out, int* n_sigma_out, int* rank_out, int* blocks_out,
+                            void* stream);
+
+/*
  * rtt_operational_rank -- operational rank of a restricted Gram from its
  * eigenvalues (Sec. 4.4 Eq. 31): sigma_i = sqrt(max(lambda_i, 0)) (the
  * whitening scale SNR_0 / s_ref is already in the Gram), rank = #{sigma_i >=

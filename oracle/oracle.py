@@ -844,6 +844,50 @@ def gram(P: np.ndarray) -> np.ndarray:
     return P.T @ P
 
 
+def range_finder(G: np.ndarray, omega: np.ndarray, block: int, rho: float = 1.0):
+    """Adaptive randomized range finder for the spectrum of the symmetric
+    PSD G (the restricted normal operator of Eq. 21) from the Gaussian draws
+    omega [d, block * n_blocks] (Sec. 7-8: the spectra of the large classes).
+    Per block: Y = G Omega_i, made orthogonal to the basis V so far (two
+    passes), then orthonormal columns by QR with column pivoting, keeping the
+    columns whose pivot exceeds 1e-12 of Y's largest column norm before the
+    projection; the Ritz values are the eigenvalues of V^T G V.  Stops after
+    a block that adds no Ritz value >= rho^2, when V has d columns, or after
+    the last block.  Returns (Ritz values descending, basis size, blocks)."""
+    import scipy.linalg
+    d = G.shape[0]
+    n_blocks = omega.shape[1] // block
+    V = np.zeros((d, 0))
+    ritz = np.zeros(0)
+    prev = -1
+    used = 0
+    for i in range(n_blocks):
+        if V.shape[1] >= d:
+            break
+        Y = G @ omega[:, i * block:(i + 1) * block]
+        used += 1
+        ymax = float(np.max(np.linalg.norm(Y, axis=0)))
+        for _ in range(2):
+            if V.shape[1]:
+                Y = Y - V @ (V.T @ Y)
+        Qy, R, _ = scipy.linalg.qr(Y, mode="economic", pivoting=True)
+        piv = np.abs(np.diag(R))
+        r = 0
+        while r < piv.size and piv[r] > 1e-12 * ymax:
+            r += 1
+        nk = min(r, d - V.shape[1])
+        if nk == 0:
+            break
+        V = np.hstack([V, Qy[:, :nk]])
+        T = V.T @ G @ V
+        ritz = np.sort(np.linalg.eigvalsh(0.5 * (T + T.T)))[::-1]
+        count = int(np.count_nonzero(ritz >= rho * rho))
+        if count == prev:
+            break
+        prev = count
+    return ritz, V.shape[1], used
+
+
 @dataclasses.dataclass
 class Spectrum:
     sigma: np.ndarray  # descending

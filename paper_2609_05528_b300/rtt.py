@@ -175,6 +175,9 @@ _SIGS = {
                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                                       ctypes.c_int, dp, ctypes.c_double, ctypes.c_double,
                                       ctypes.c_int, ctypes.POINTER(AuditRecord), dp, vp]),
+    "rtt_range_finder": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        dp, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), vp]),
     "rtt_audit_plan_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                              ctypes.c_int, ctypes.c_int, dp, ctypes.c_double,
                                              ctypes.c_double, ctypes.c_int, vp, ctypes.POINTER(vp)]),
@@ -629,6 +632,25 @@ def shard_rows(n_rows: int, index: int, count: int):
     check(lib().rtt_shard_rows(int(n_rows), ctypes.byref(sh), ctypes.byref(b), ctypes.byref(e)),
           "rtt_shard_rows")
     return int(b.value), int(e.value)
+
+
+def range_finder(op: "Operator", Q, omega, arm_mask: int = 7, block: int = 256, rho: float = 1.0,
+                 stream=None):
+    """rtt_range_finder: (sigma descending, rank, blocks used) of the
+    restricted normal operator Q^T A^T A Q from the Gaussian draws omega
+    (host float64 [d, block * max_blocks])."""
+    _want(Q, "Q", (op.n_nodes, op.n_hats, None), ("float64",))
+    d = Q.shape[2]
+    om = np.ascontiguousarray(omega, np.float64)
+    if om.ndim != 2 or om.shape[0] != d or om.shape[1] % block:
+        raise ValueError(f"omega: want [{d}, a multiple of {block}], got {om.shape}")
+    sig = np.empty(d)
+    n, rank, blocks = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+    check(lib().rtt_range_finder(op.handle, arm_mask, ctypes.c_void_p(Q.data_ptr()), d, block,
+                                 om.shape[1] // block, _ptr(om, dp), rho, _ptr(sig, dp),
+                                 ctypes.byref(n), ctypes.byref(rank), ctypes.byref(blocks),
+                                 _stream(stream)), "rtt_range_finder")
+    return sig[:n.value].copy(), rank.value, blocks.value
 
 
 def rank_from_eigenvalues(evals, rho: float = 1.0):
