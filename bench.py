@@ -484,15 +484,17 @@ def run_gemm(args, device):
 
 
 def run_profile_case(args, device):
-    """The step alone, for profiling: the workload at batch 8 with its
-    autotuned variants, max(warmup, 3) untimed steps, then args.steps steps
-    inside the NVTX range bench_timed (ncu --nvtx-include "bench_timed/")."""
+    """The step alone, for profiling: the workload at batch args.batch
+    (default 8) with its autotuned variants, max(warmup, 3) untimed steps,
+    then args.steps steps inside the NVTX range bench_timed
+    (ncu --nvtx-include "bench_timed/")."""
     import torch
 
     from paper_2609_05528_b300 import inputs as I
     w = I.stress1024(0.94) if args.profile == "stress1024" else I.kerr256()
-    _, op, x = build_workload(device, w, BATCH, seed0=100)
-    y = torch.empty((op.arm_rows(7), op.n_frames, BATCH), dtype=torch.float32, device=device)
+    B = args.batch
+    _, op, x = build_workload(device, w, B, seed0=100)
+    y = torch.empty((op.arm_rows(7), op.n_frames, B), dtype=torch.float32, device=device)
     g = torch.empty_like(x)
     for _ in range(max(args.warmup, 3)):
         op.apply_A(x, y)
@@ -504,8 +506,8 @@ def run_profile_case(args, device):
         op.apply_AT(y, g)
     torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(device)
-    out = {"workload": w.name, "batch": BATCH, "steps": args.steps, "variant": op.get_variant(BATCH),
-           "algorithmic_bytes": algorithmic_bytes(op, BATCH), "source_hash": kernel_source_hash(),
+    out = {"workload": w.name, "batch": B, "steps": args.steps, "variant": op.get_variant(B),
+           "algorithmic_bytes": algorithmic_bytes(op, B), "source_hash": kernel_source_hash(),
            "status": op.status()}
     op.close()
     return out
@@ -1054,6 +1056,7 @@ def main():
     ap.add_argument("--gemm", type=int, nargs=3, metavar=("K", "M", "N"),
                     help="time rtt_gemm_tn_f64 (C = A^T B, A: K x M, B: K x N, N(0,1) FP64) against "
                          "cuBLAS DGEMM, print one JSON line and exit")
+    ap.add_argument("--batch", type=int, default=8, help="history batch of the --profile step")
     ap.add_argument("--profile", choices=["stress1024", "kerr256"],
                     help="for ncu: build the workload at batch 8, autotune, warm up, run --steps "
                          "A + A^T steps inside the NVTX range bench_timed, and exit")

@@ -810,7 +810,8 @@ typedef struct {
     int32_t fwd_kernel;   /* 1 staged, 2 lane-per-hat, 3 staged with TMA corner copies,
                              4 staged with pipelined bulk corner copies, 5 periodic
                              staged with the whole batch in one chunk, 6 the same with
-                             its table loads one task ahead */
+                             its table loads one task ahead, 7 periodic quad-lane, 8 the
+                             same with its table loads one task ahead */
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
     int32_t fwd_staging;  /* staged forward: x items in flight per lane */
@@ -835,8 +836,14 @@ typedef struct {
                              5 periodic staged with the whole batch in one chunk and
                              32-bit hat arithmetic (periodic cadences, batch 4 or 8;
                              else staged), 6 kernel 5 with each task's table loads
-                             issued during the task before it */
-    int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32 */
+                             issued during the task before it, 7 periodic quad-lane:
+                             fwd_bc / 4 lanes share a frame, each holding 4 of its
+                             columns, so every store instruction writes 512 contiguous
+                             bytes (periodic cadences, chunks of 4..64 columns dividing
+                             the batch; else staged), 8 kernel 7 with each task's table
+                             loads issued during the task before it */
+    int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32; 64 for
+                             fwd_kernel 7 and 8 */
     int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
     int32_t adj_kernel;   /* adjoint: 1 general (any cadence, batch and precision; frames
                              staged by per-lane copies), 2 periodic (a frame step of 1/2,

@@ -987,6 +987,228 @@ fwd8_kernel(const ApplyArgs<float> a) {
     }
 }
 
+// Periodic forward with the batch spread over the lanes: Q = BC / 4 lanes
+// share a frame, each holding one 16-byte quad of its columns, so a warp's
+// store instruction writes 512 contiguous bytes of y (whole sectors and lines)
+// at every batch size, where the lane-per-frame kernels (fwd7/fwd8) write
+// 16-byte pieces at a BC * 4-byte stride (8 lines per instruction at BC = 8,
+// 16 at BC = 16) and their stores and shared-memory reads of whole frame
+// records saturate the load/store pipe as BC grows.  Lane (s, c) = (lane / Q,
+// lane % Q) adds the frames f_begin + s + (32 / Q) j, j < NF, of the quad c;
+// the chunk is FC = 32 NF / Q frames.  The hat window, its staging in shared
+// memory (the interpolated history z of fwd7_ray, the same values), the ray
+// order and each output's fused multiply-add chain are fwd7's: the same bits.
+// BC in {4, 8, 16, 32, 64}; B = BC or whole chunks of BC columns.
+template <int BC, int NF>
+struct Fwd9Shape {
+    static constexpr int Q = BC / 4;
+    static constexpr int R = 32 / Q;  // frames per lane row
+    static constexpr int FC = R * NF;
+};
+
+template <int BC, int NF, int P>
+__device__ __forceinline__ void fwd9_ray(const ApplyArgs<float>& a, const Fwd7Ray& rf, int hb, int b0,
+                                         int f_begin, bool full, int lane, float4* zsv,
+                                         float4 (&acc)[NF]) {
+    constexpr int Q = Fwd9Shape<BC, NF>::Q;
+    constexpr int R = Fwd9Shape<BC, NF>::R;
+    constexpr int FC = Fwd9Shape<BC, NF>::FC;
+    constexpr int ZW = FC / P + 3;          // hats staged per task window
+    constexpr int NU = (ZW * Q + 31) / 32;  // staging items per lane
+    constexpr int32_t D = kFracOne / P;
+    const int64_t KB = (int64_t)a.K * a.B;  // floats per node row of x
+    const int B = a.B;                       // hat stride of x
+    const int s = lane / Q, c = lane % Q;    // staging: hat s + (32 / Q) u, quad c
+    const int K0 = rf.K0, F0 = rf.F0;
+    const float4 wv = rf.w;
+    const int k_top = K0 - hb;
+    const int k_lo = k_top - FC / P + ((F0 + D) >> kFracBits);
+    const float* b00 = a.in + (int64_t)rf.n00 * KB + (int64_t)(k_lo + s) * B + b0 + 4 * c;
+    const float* b01 = a.in + (int64_t)rf.n01 * KB + (int64_t)(k_lo + s) * B + b0 + 4 * c;
+    const int64_t rstep = (int64_t)a.n_phi * KB;  // the radial neighbour's row
+    float4 v[NU][4];
+    if (k_lo >= 0 && k_lo + ZW <= a.K) {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            if (u < NU - 1 || lane + 32 * u < ZW * Q) {
+                const int du = R * u * B;
+                v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
+                v[u][1] = __ldg(reinterpret_cast<const float4*>(b00 + rstep + du));
+                v[u][2] = __ldg(reinterpret_cast<const float4*>(b01 + du));
+                v[u][3] = __ldg(reinterpret_cast<const float4*>(b01 + rstep + du));
+            }
+        }
+    } else {
+#pragma unroll
+        for (int u = 0; u < NU; ++u) {
+            const int k = k_lo + s + R * u;
+            const bool ok = lane + 32 * u < ZW * Q && k >= 0 && k < a.K;
+            const int du = R * u * B;
+            v[u][0] = v[u][1] = v[u][2] = v[u][3] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (ok) {
+                v[u][0] = __ldg(reinterpret_cast<const float4*>(b00 + du));
+                v[u][1] = __ldg(reinterpret_cast<const float4*>(b00 + rstep + du));
+                v[u][2] = __ldg(reinterpret_cast<const float4*>(b01 + du));
+                v[u][3] = __ldg(reinterpret_cast<const float4*>(b01 + rstep + du));
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        if (u < NU - 1 || lane + 32 * u < ZW * Q) {
+            float2 r = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v[u][0].x, v[u][0].y));
+            r = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v[u][1].x, v[u][1].y), r);
+            r = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v[u][2].x, v[u][2].y), r);
+            r = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v[u][3].x, v[u][3].y), r);
+            float2 t = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v[u][0].z, v[u][0].w));
+            t = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v[u][1].z, v[u][1].w), t);
+            t = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v[u][2].z, v[u][2].w), t);
+            t = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v[u][3].z, v[u][3].w), t);
+            zsv[lane + 32 * u] = make_float4(r.x, r.y, t.x, t.y);
+        }
+    }
+    __syncwarp();
+    // frame f_begin + s + R j: remainder F0 - (s + R j) D (above -2^31: (FC - 1) D
+    // < 128 hat steps), hat k_top + floor(remainder / 2^24), fraction its low 24 bits
+    const float4* zc = zsv + c;
+    const int32_t rem_s = F0 - s * D;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+        if (full || f_begin + s + R * j < a.Tn) {
+            int k;
+            float fr;
+            if constexpr (R % P == 0) {  // every row of lanes a whole number of hat steps on
+                k = k_top + (rem_s >> kFracBits) - j * (R / P);
+                fr = (float)(rem_s & kFracMask) * (1.0f / (float)kFracOne);
+            } else {
+                const int32_t rem = rem_s - R * j * D;
+                k = k_top + (rem >> kFracBits);
+                fr = (float)(rem & kFracMask) * (1.0f / (float)kFracOne);
+            }
+            const float g = 1.0f - fr;
+            const float2 g2 = make_float2(g, g), f2 = make_float2(fr, fr);
+            const float4 p0 = zc[(k - k_lo) * Q];
+            const float4 p1 = zc[(k + 1 - k_lo) * Q];
+            float2 lo = make_float2(acc[j].x, acc[j].y);
+            float2 hi = make_float2(acc[j].z, acc[j].w);
+            lo = __ffma2_rn(g2, make_float2(p0.x, p0.y), lo);
+            lo = __ffma2_rn(f2, make_float2(p1.x, p1.y), lo);
+            hi = __ffma2_rn(g2, make_float2(p0.z, p0.w), hi);
+            hi = __ffma2_rn(f2, make_float2(p1.z, p1.w), hi);
+            acc[j] = make_float4(lo.x, lo.y, hi.x, hi.y);
+        }
+    }
+    __syncwarp();
+}
+
+template <int BC, int NF>
+__device__ __forceinline__ void fwd9_store(const ApplyArgs<float>& a, int row_out, int b0, int f_begin,
+                                           bool full, int lane, const float4 (&acc)[NF]) {
+    constexpr int Q = Fwd9Shape<BC, NF>::Q;
+    constexpr int R = Fwd9Shape<BC, NF>::R;
+    const int s = lane / Q, c = lane % Q;
+    float* base = a.out + ((int64_t)row_out * a.Tn + f_begin + s) * a.B + b0 + 4 * c;
+#pragma unroll
+    for (int j = 0; j < NF; ++j)
+        if (full || f_begin + s + R * j < a.Tn)
+            *reinterpret_cast<float4*>(base + (int64_t)R * j * a.B) = acc[j];
+}
+
+constexpr int kFwd9Warps = 4;
+template <int BC>
+struct Fwd9Occ {  // CTAs per SM the register budget is set for
+    static constexpr int kMinBlocks = BC >= 32 ? 3 : 4;
+};
+
+// PF: the table loads one task (and, inside a task, one ray) ahead, as fwd8
+template <int BC, int NF, int P, bool PF>
+__global__ void __launch_bounds__(kFwd9Warps * 32, Fwd9Occ<BC>::kMinBlocks)
+fwd9_kernel(const ApplyArgs<float> a) {
+    static_assert(BC == 4 || BC == 8 || BC == 16 || BC == 32 || BC == 64, "16-byte quads");
+    wait_prior_grid();
+    constexpr int Q = Fwd9Shape<BC, NF>::Q;
+    constexpr int FC = Fwd9Shape<BC, NF>::FC;
+    static_assert(FC % P == 0, "chunks start on whole hat steps");
+    static_assert(FC / P <= 128, "remainders stay above -2^31");
+    constexpr int ZW = FC / P + 3;
+    __shared__ __align__(16) float4 zs_all[kFwd9Warps][ZW * Q];
+    float4* zsv = zs_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kFwd9Warps + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kFwd9Warps;
+    const int n_rows = a.seg.total;
+    if constexpr (!PF) {
+        for (TaskWalk tw(warp_global, n_warps, a.n_bchunk, a.n_fchunk); tw.r < n_rows; tw.next()) {
+            const int b0 = tw.b * BC;
+            int row_out, row;
+            task_row(a, tw.r, row_out, row);
+            const int f_begin = tw.f * FC;
+            const bool full = f_begin + FC <= a.Tn;
+            const int hb = f_begin / P;
+            float4 acc[NF];
+#pragma unroll
+            for (int j = 0; j < NF; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
+            for (int e = e_begin; e < e_end; ++e)
+                fwd9_ray<BC, NF, P>(a, fwd7_load_ray(a, e), hb, b0, f_begin, full, lane, zsv, acc);
+            fwd9_store<BC, NF>(a, row_out, b0, f_begin, full, lane, acc);
+        }
+    } else {
+        TaskWalk tw(warp_global, n_warps, a.n_bchunk, a.n_fchunk);
+        if (tw.r >= n_rows) return;
+        int row_out, row;
+        task_row(a, tw.r, row_out, row);
+        int eb = a.row_ptr[row], ee = a.row_ptr[row + 1];
+        TaskWalk tn = tw;
+        tn.next();
+        int row_out_n = 0, eb_n = 0, ee_n = 0;
+        if (tn.r < n_rows) {
+            int rn;
+            task_row(a, tn.r, row_out_n, rn);
+            eb_n = a.row_ptr[rn];
+            ee_n = a.row_ptr[rn + 1];
+        }
+        Fwd7Ray cur{};
+        if (eb < ee) cur = fwd7_load_ray(a, eb);
+        while (true) {
+            Fwd7Ray nxt{};
+            if (tn.r < n_rows && eb_n < ee_n) nxt = fwd7_load_ray(a, eb_n);
+            TaskWalk tnn = tn;
+            tnn.next();
+            int row_out_nn = 0, eb_nn = 0, ee_nn = 0;
+            if (tnn.r < n_rows) {
+                int r2;
+                task_row(a, tnn.r, row_out_nn, r2);
+                eb_nn = a.row_ptr[r2];
+                ee_nn = a.row_ptr[r2 + 1];
+            }
+            const int b0 = tw.b * BC;
+            const int f_begin = tw.f * FC;
+            const bool full = f_begin + FC <= a.Tn;
+            const int hb = f_begin / P;
+            float4 acc[NF];
+#pragma unroll
+            for (int j = 0; j < NF; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int e = eb; e < ee; ++e) {
+                const Fwd7Ray rf = cur;
+                if (e + 1 < ee) cur = fwd7_load_ray(a, e + 1);
+                fwd9_ray<BC, NF, P>(a, rf, hb, b0, f_begin, full, lane, zsv, acc);
+            }
+            fwd9_store<BC, NF>(a, row_out, b0, f_begin, full, lane, acc);
+            if (tn.r >= n_rows) break;
+            tw = tn;
+            row_out = row_out_n;
+            eb = eb_n;
+            ee = ee_n;
+            cur = nxt;
+            tn = tnn;
+            row_out_n = row_out_nn;
+            eb_n = eb_nn;
+            ee_n = ee_nn;
+        }
+    }
+}
+
 // Forward with the corner slabs of x fetched by bulk asynchronous copies,
 // pipelined over the warp's stream of (task, ray) items.  Tasks, hat windows,
 // interpolation and accumulation order are those of fwd3_kernel<float, BC,
@@ -1451,6 +1673,45 @@ static cudaError_t launch_fwd7(ApplyArgs<float> a, cudaStream_t st, bool prefetc
     }
 }
 
+// periodic quad-lane forward (fwd9); cudaErrorNotSupported unless the cadence
+// is P in {2, 4, 8} frames per hat and the batch is whole chunks of BC columns
+template <int BC, int NF>
+static cudaError_t launch_fwd9(ApplyArgs<float> a, cudaStream_t st, bool prefetch) {
+    const int P = frames_per_hat(a.D);
+    constexpr int FC = Fwd9Shape<BC, NF>::FC;
+    const int cols = a.Bcols > 0 ? a.Bcols : a.B;
+    if (!vec_ok(a) || cols % BC != 0 || P == 0 || FC % P != 0) return cudaErrorNotSupported;
+    a.FC = FC;
+    a.n_fchunk = (a.Tn + FC - 1) / FC;
+    a.n_bchunk = cols / BC;
+    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk * a.n_bchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    auto go = [&](auto kern) {
+        const int grid = resident_grid(kern, kFwd9Warps * 32, 0, a.n_tasks, kFwd9Warps);
+        return launch_dependent(kern, dim3(grid), dim3(kFwd9Warps * 32), 0, st, a);
+    };
+    if (prefetch) {
+        switch (P) {
+            case 2: return go(fwd9_kernel<BC, NF, 2, true>);
+            case 4: return go(fwd9_kernel<BC, NF, 4, true>);
+            default: return go(fwd9_kernel<BC, NF, 8, true>);
+        }
+    }
+    switch (P) {
+        case 2: return go(fwd9_kernel<BC, NF, 2, false>);
+        case 4: return go(fwd9_kernel<BC, NF, 4, false>);
+        default: return go(fwd9_kernel<BC, NF, 8, false>);
+    }
+}
+
+// the widest quad-lane chunk for a batch: the largest of 64, 32, 16, 8, 4 that
+// divides it (0 when the batch is not whole 16-byte records)
+static int quad_bc(int B) {
+    for (int bc = 64; bc >= 4; bc >>= 1)
+        if (B % bc == 0) return bc;
+    return 0;
+}
+
 int adjoint_best_kind(const rtt_op_s* op, int batch);
 
 ApplyVariant variant_for(const rtt_op_s* op, int batch) {
@@ -1461,11 +1722,11 @@ ApplyVariant variant_for(const rtt_op_s* op, int batch) {
     // kernel down where the cadence, batch or buffers do not allow it
     ApplyVariant v;
     const int P = frames_per_hat(op->frame_D);
-    // the periodic staged forward takes any batch of whole 16-byte records,
-    // in chunks of 8 (or 4) columns
+    // the periodic quad-lane forward takes any batch of whole 16-byte records,
+    // in chunks of up to 64 columns
     if (P > 0 && batch % 4 == 0) {
-        v.fwd = 5;
-        v.fwd_bc = (int8_t)(batch % 16 == 0 ? 16 : (batch % 8 == 0 ? 8 : 4));
+        v.fwd = 7;
+        v.fwd_bc = (int8_t)quad_bc(batch);
     } else {
         v.fwd = 1;
         v.fwd_bc = (int8_t)pick_bc(batch);
@@ -1526,6 +1787,20 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
                 case 8: return launch_fwd4_any<8>(a, bc, st);
                 default: break;  // not a periodic cadence: staged kernel
             }
+        }
+        if ((v.fwd == 7 || v.fwd == 8) && (bc == 4 || bc == 8 || bc == 16 || bc == 32 || bc == 64)) {
+            const bool half = v.fwd_half != 0, pf = v.fwd == 8;
+            // NF = 8 frames per lane (half: 4), FC = 32 NF / (BC / 4) frames per task
+            cudaError_t e;
+            switch (bc) {
+                case 4: e = half ? launch_fwd9<4, 4>(a, st, pf) : launch_fwd9<4, 8>(a, st, pf); break;
+                case 8: e = half ? launch_fwd9<8, 4>(a, st, pf) : launch_fwd9<8, 8>(a, st, pf); break;
+                case 16: e = half ? launch_fwd9<16, 4>(a, st, pf) : launch_fwd9<16, 8>(a, st, pf); break;
+                case 32: e = half ? launch_fwd9<32, 4>(a, st, pf) : launch_fwd9<32, 8>(a, st, pf); break;
+                default: e = half ? launch_fwd9<64, 4>(a, st, pf) : launch_fwd9<64, 8>(a, st, pf); break;
+            }
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();  // clear the "not supported" marker, if any
         }
         if ((v.fwd == 5 || v.fwd == 6) && (bc == 4 || bc == 8 || bc == 16)) {
             const bool half = v.fwd_half != 0, pf = v.fwd == 6;

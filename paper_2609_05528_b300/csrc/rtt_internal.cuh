@@ -48,7 +48,8 @@ struct ApplyVariant {
     int8_t fwd = 0;     // forward: 1 staged z (fwd3), 2 lane-per-hat shuffles (fwd4),
                         // 3 TMA corner slabs (fwd5), 4 pipelined bulk corner copies
                         // (fwd6), 5 periodic one-chunk staged (fwd7), 6 the same with its
-                        // table loads one task ahead (fwd8)
+                        // table loads one task ahead (fwd8), 7 periodic quad-lane (fwd9),
+                        // 8 the same with its table loads one task ahead
     int8_t fwd_bc = 0;  // batch entries per forward task (power of two)
     int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
     int8_t fwd_su = 2;   // staged forward: staging items in flight per lane (1, 2 or 3)

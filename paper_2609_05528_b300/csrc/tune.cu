@@ -1,6 +1,6 @@
 // Autotuner for the FP32 applies: for one operator and batch size, times
-// every kernel variant of the forward (staged or lane-per-hat, batch entries
-// and frames per task) and of the adjoint (frames staged by per-lane copies
+// every kernel variant of the forward (staged, lane-per-hat or quad-lane,
+// batch entries and frames per task) and of the adjoint (frames staged by per-lane copies
 // or by TMA tensor copies, 32- or 64-hat items) with CUDA events on the
 // caller's stream, and records the fastest in the operator.  All variants
 // produce the same bits (same per-output summation order and fused
@@ -69,7 +69,8 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
         return RTT_OK;
     }
     const int bc = v->fwd_bc;
-    if (v->fwd_kernel < 1 || v->fwd_kernel > 6 || bc < 1 || bc > 32 || (bc & (bc - 1)) != 0 ||
+    if (v->fwd_kernel < 1 || v->fwd_kernel > 8 || bc < 1 || bc > 64 || (bc & (bc - 1)) != 0 ||
+        (bc > 32 && v->fwd_kernel < 7) ||
         v->fwd_half < 0 || v->fwd_half > 1 || v->adj_kernel < 1 || v->adj_kernel > 4) {
         set_error("invalid variant (fwd %d bc %d half %d adj %d)", v->fwd_kernel, bc, v->fwd_half,
                   v->adj_kernel);
@@ -212,6 +213,29 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                     }
                 }
             }
+    // the quad-lane forward (periodic cadences, whole 16-byte records): the
+    // widest chunk of up to 64 columns dividing the batch and two narrower ones
+    if (periodic && x_vec) {
+        int qbc = 64;
+        while (B % qbc != 0) qbc >>= 1;
+        for (int kind = 7; kind <= 8; ++kind)
+            for (int bc = qbc; bc >= 4 && bc >= qbc / 4; bc >>= 1)
+                for (int half = 0; half <= 1; ++half) {
+                    ApplyVariant v = rule;
+                    v.fwd = (int8_t)kind;
+                    v.fwd_bc = (int8_t)bc;
+                    v.fwd_half = (int8_t)half;
+                    v.fwd_su = 2;
+                    const float ms = time_it(v, false);
+                    if (ms < fwd_best) {
+                        fwd_best = ms;
+                        best.fwd = v.fwd;
+                        best.fwd_bc = v.fwd_bc;
+                        best.fwd_half = v.fwd_half;
+                        best.fwd_su = v.fwd_su;
+                    }
+                }
+    }
     // forward task rows in source-cell order, for the chosen kernel
     {
         ApplyVariant v = best;

@@ -175,7 +175,7 @@ def test_autotune_keeps_bits(B):
     g0 = c.op.apply_AT(y0)
     r = c.op.autotune(B)
     assert r["batch"] == B and r["candidates"] >= 4
-    assert r["fwd_kernel"] in (1, 2, 3, 4, 5, 6) and r["adj_kernel"] in (1, 2, 3, 4)
+    assert r["fwd_kernel"] in range(1, 9) and r["adj_kernel"] in (1, 2, 3, 4)
     if B % 4:
         assert r["adj_kernel"] <= 2  # the TMA adjoint needs 16-byte frame records
     assert 0 < r["fwd_ms"] <= r["fwd_ms_rule"] and 0 < r["adj_ms"] <= r["adj_ms_rule"]
@@ -205,7 +205,7 @@ def test_every_variant_same_bits(which, small, schw, B):
     while bc_max < min(B, 32):
         bc_max *= 2
     n = 0
-    for fk in (1, 2, 3, 4, 5, 6):
+    for fk in (1, 2, 3, 4, 5, 6, 7, 8):
         for bc in sorted({bc_max, max(1, bc_max // 2), max(1, bc_max // 4)}):
             for half in (0, 1):
                 for su in ((1, 2, 3) if (fk == 1 and half == 0 and bc in (4, 8)) else (2,)):
@@ -224,7 +224,7 @@ def test_every_variant_same_bits(which, small, schw, B):
     for ak in (1, 2, 3, 4):
         c.op.set_variant(B, 1, bc_max, 0, ak)
         assert torch.equal(c.op.apply_AT(y1, arm_mask=1), g1), ak
-    for fk in (1, 3, 4, 5):
+    for fk in (1, 3, 4, 5, 7):
         for order in (0, 1):
             c.op.set_variant(B, fk, bc_max, 0, 1, fwd_order=order)
             assert torch.equal(c.op.apply_A(x, arm_mask=1), y1), (fk, order)
@@ -245,6 +245,40 @@ def test_every_variant_same_bits(which, small, schw, B):
     c.op.set_variant(B)
     assert c.op.status(clear=True) == 0
     assert n >= 12
+
+
+@pytest.mark.parametrize("which", ["small", "schw"])
+@pytest.mark.parametrize("B", [4, 8, 16, 32, 64])
+def test_quad_lane_forward_same_bits(which, small, schw, B):
+    """The quad-lane forward (kernels 7 and 8: B/4 lanes share a frame, each
+    holding 4 of its columns) at every chunk width from 4 to 64 columns and
+    both frame counts per lane gives the bits of the staged kernel, which
+    matches the oracle: ragged frame chunks (300 frames), hat windows past
+    either end of the hats, cadences of 1/4 (small) and 1/2 (schw) hat step,
+    every arm."""
+    c = small if which == "small" else schw
+    x = torch.from_numpy(I.uniform_batch(c.w, range(B)).astype(np.float32)).cuda()
+    qbc = 64
+    while B % qbc:
+        qbc //= 2
+    for mask in (7, 1, 6):
+        c.op.set_variant(B, 1, min(B, 32), 0, 1)
+        y0 = c.op.apply_A(x, arm_mask=mask)
+        if B in (8, 64):
+            sub = c.tab.select(_arm_orders(mask))
+            _cmp(y0.cpu().numpy().astype(np.float64),
+                 O.apply_A(c.w, sub, x.cpu().numpy().astype(np.float64), c.scale), TOL32)
+        for fk in (7, 8):
+            for bc in (qbc, qbc // 2, qbc // 4):
+                if bc < 4:
+                    continue
+                for half in (0, 1):
+                    for order in (0, 1):
+                        c.op.set_variant(B, fk, bc, half, 1, fwd_order=order)
+                        assert torch.equal(c.op.apply_A(x, arm_mask=mask), y0), (mask, fk, bc, half, order)
+    c.op.set_variant(B)
+    assert c.op.get_variant(B)["fwd_kernel"] == 7 and c.op.get_variant(B)["fwd_bc"] == qbc
+    assert c.op.status(clear=True) == 0
 
 
 @pytest.mark.parametrize("which", ["small", "schw"])
