@@ -211,9 +211,13 @@ __device__ __forceinline__ void acc_add2(ColAcc<float, NH, BC>& A, const float (
 // Where an item writes: record row (rec, hat k) of the pass holds Bp
 // columns; the item's batch chunk starts at column boff and has nb of them.
 // Lanes at or beyond `nlanes` hold no hat of the item and write nothing.
+// A lane whose registers hold its column quads in the order q ^ qx (qx = 0
+// or 1: the TMA kernel's bank-spreading order, whose records are always
+// whole 16-byte quads) writes register quad q to column quad q ^ qx.
 struct EmitAt {
     int kbase, boff, nb, nlanes;
     bool vec;
+    int qx = 0;
 };
 
 // write one slot's two records (hats k_h = kbase + lane + 32 h)
@@ -235,7 +239,7 @@ __device__ __forceinline__ void emit_slot(const CellArgs& a, const T (&lo)[NH][B
                 if (at.vec) {
 #pragma unroll
                     for (int q = 0; q < BC / 4; ++q)
-                        reinterpret_cast<float4*>(o)[q] =
+                        reinterpret_cast<float4*>(o)[q ^ at.qx] =
                             make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
                     continue;
                 }
@@ -294,9 +298,14 @@ struct CellBox {
     static constexpr uint32_t kStride = (kBytes + 1023) & ~1023u;
 };
 
-// taps of HG hats of one lane for the frame residue M: lines rs + d
+// taps of HG hats of one lane for the frame residue M: lines rs + d.  The
+// lane's register quad q holds column quad q ^ qx: at BC = 16 consecutive
+// lanes' taps lie two 128-byte lines apart, so under the 128-byte swizzle a
+// warp's reads of one quad would meet only four bank groups; with the
+// neighbouring quad read by half of the lanes they meet all eight (each
+// output's chain of taps is unchanged).
 template <int BC, int P, int HG, int M>
-__device__ __forceinline__ void cell_contract(const unsigned char* buf, int rs0,
+__device__ __forceinline__ void cell_contract(const unsigned char* buf, int rs0, int qx,
                                               const float (&wt)[2 * P], float (&z)[HG][BC]) {
     constexpr int Q = BC / 4;
     constexpr int F = 32 / BC;
@@ -317,7 +326,7 @@ __device__ __forceinline__ void cell_contract(const unsigned char* buf, int rs0,
             const int dj = (M + j) / F, cj = (M + j) % F;
 #pragma unroll
             for (int q = 0; q < Q; ++q) {
-                const uint32_t off = A[dj] | ((uint32_t)(16 * (cj * Q + q)) ^ X[dj]);
+                const uint32_t off = A[dj] | ((uint32_t)(16 * (cj * Q + (q ^ qx))) ^ X[dj]);
                 const float4 v = *reinterpret_cast<const float4*>(buf + off);
                 fmac2x2(wt[j], v, z[h][4 * q + 0], z[h][4 * q + 1], z[h][4 * q + 2], z[h][4 * q + 3]);
             }
@@ -326,37 +335,45 @@ __device__ __forceinline__ void cell_contract(const unsigned char* buf, int rs0,
 }
 
 template <int BC, int P, int HG>
-__device__ __forceinline__ void cell_contract_any(int M, const unsigned char* buf, int rs0,
+__device__ __forceinline__ void cell_contract_any(int M, const unsigned char* buf, int rs0, int qx,
                                                   const float (&wt)[2 * P], float (&z)[HG][BC]) {
     constexpr int F = 32 / BC;
     if constexpr (F == 1) {
-        cell_contract<BC, P, HG, 0>(buf, rs0, wt, z);
+        cell_contract<BC, P, HG, 0>(buf, rs0, qx, wt, z);
     } else if constexpr (F == 2) {
-        if (M == 0) cell_contract<BC, P, HG, 0>(buf, rs0, wt, z);
-        else cell_contract<BC, P, HG, 1>(buf, rs0, wt, z);
+        if (M == 0) cell_contract<BC, P, HG, 0>(buf, rs0, qx, wt, z);
+        else cell_contract<BC, P, HG, 1>(buf, rs0, qx, wt, z);
     } else if constexpr (F == 4) {
         switch (M) {
-            case 0: cell_contract<BC, P, HG, 0>(buf, rs0, wt, z); break;
-            case 1: cell_contract<BC, P, HG, 1>(buf, rs0, wt, z); break;
-            case 2: cell_contract<BC, P, HG, 2>(buf, rs0, wt, z); break;
-            default: cell_contract<BC, P, HG, 3>(buf, rs0, wt, z); break;
+            case 0: cell_contract<BC, P, HG, 0>(buf, rs0, qx, wt, z); break;
+            case 1: cell_contract<BC, P, HG, 1>(buf, rs0, qx, wt, z); break;
+            case 2: cell_contract<BC, P, HG, 2>(buf, rs0, qx, wt, z); break;
+            default: cell_contract<BC, P, HG, 3>(buf, rs0, qx, wt, z); break;
         }
     } else {
         switch (M) {
-            case 0: cell_contract<BC, P, HG, 0>(buf, rs0, wt, z); break;
-            case 1: cell_contract<BC, P, HG, 1>(buf, rs0, wt, z); break;
-            case 2: cell_contract<BC, P, HG, 2>(buf, rs0, wt, z); break;
-            case 3: cell_contract<BC, P, HG, 3>(buf, rs0, wt, z); break;
-            case 4: cell_contract<BC, P, HG, 4>(buf, rs0, wt, z); break;
-            case 5: cell_contract<BC, P, HG, 5>(buf, rs0, wt, z); break;
-            case 6: cell_contract<BC, P, HG, 6>(buf, rs0, wt, z); break;
-            default: cell_contract<BC, P, HG, 7>(buf, rs0, wt, z); break;
+            case 0: cell_contract<BC, P, HG, 0>(buf, rs0, qx, wt, z); break;
+            case 1: cell_contract<BC, P, HG, 1>(buf, rs0, qx, wt, z); break;
+            case 2: cell_contract<BC, P, HG, 2>(buf, rs0, qx, wt, z); break;
+            case 3: cell_contract<BC, P, HG, 3>(buf, rs0, qx, wt, z); break;
+            case 4: cell_contract<BC, P, HG, 4>(buf, rs0, qx, wt, z); break;
+            case 5: cell_contract<BC, P, HG, 5>(buf, rs0, qx, wt, z); break;
+            case 6: cell_contract<BC, P, HG, 6>(buf, rs0, qx, wt, z); break;
+            default: cell_contract<BC, P, HG, 7>(buf, rs0, qx, wt, z); break;
         }
     }
 }
 
+// CTAs per SM the TMA kernel's registers are set for: three (the shared
+// memory's limit), two at BC = 16, whose four 16-column accumulators do not
+// fit in a third of the register file without spilling in the tap loop
+template <int BC>
+struct CellTmaOcc {
+    static constexpr int kMinBlocks = BC == 16 ? 2 : 3;
+};
+
 template <int BC, int P, int HG>
-__global__ void __launch_bounds__(kCellWarps * 32, 3)
+__global__ void __launch_bounds__(kCellWarps * 32, CellTmaOcc<BC>::kMinBlocks)
 adj_cell_tma_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) {
     static_assert(BC == 4 || BC == 8 || BC == 16, "128-byte lines of whole frames");
     wait_prior_grid();
@@ -428,6 +445,11 @@ adj_cell_tma_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) 
         issue(s1, c1, n_issued++ & 1);
     }
     EmitAt at{0, 0, BC, 32, true};
+    // register quad q holds column quad q ^ qx: at BC = 16 the swizzle phase of
+    // a lane's taps repeats every four lanes, so lanes 4-7 of each eight take
+    // the neighbouring quad (eight bank groups per read instead of four)
+    const int qx = BC == 16 ? ((lane >> 2) & 1) : 0;
+    at.qx = qx;
     while (s0.kind) {
         at.kbase = HATS * s0.g;
         if (s0.kind == 1) {
@@ -444,7 +466,7 @@ adj_cell_tma_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) 
                 wt[j] = 1.0f - (float)abs(c0.r0 - j * D32) * (1.0f / (float)kFracOne);
             const int s0f = c0.sbase - P * lane;
             float z[HG][BC];
-            cell_contract_any<BC, P, HG>(s0f & (F - 1), bufp0 + b * BUF_STRIDE, s0f >> LGF, wt, z);
+            cell_contract_any<BC, P, HG>(s0f & (F - 1), bufp0 + b * BUF_STRIDE, s0f >> LGF, qx, wt, z);
             __syncwarp();  // buffer b is free for the next copy issued into it
             ++n_done;
             for (; jc < s0.col; ++jc) next_column(a, A, s0.rec0 + 2 * jc, at, lane);
