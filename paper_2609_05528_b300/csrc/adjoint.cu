@@ -486,6 +486,165 @@ adj_cell_tma_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) 
 }
 
 // ---------------------------------------------------------------------------
+// TMA kernel for 32-column passes (FP32; any batch of whole 32-column passes,
+// a periodic cadence of P in {2, 4, 8} frames per hat step).  A pass's frame
+// record is one 128-byte line, so a ray step's frames arrive by one 3D tensor
+// copy of the pass's columns (the tensor map's line stride is the batch's
+// frame stride) under the 128-byte swizzle, as in adj_cell_tma_kernel.  Two
+// lanes share a hat: lane (h, c) = (lane / 2, lane % 2) holds the 16 columns
+// 16 c .. 16 c + 15 of hat h of the item's 16, so its accumulators are those
+// of the 16-column kernel.  Its register quad q holds column quad q ^ (h & 3)
+// of its half: consecutive hats' taps lie P lines apart, and with the quads
+// spread this way a warp's reads of a quad meet all eight bank groups.  Each
+// output's tap chain, the walk and the records are the other kernels' (the
+// same bits).
+// ---------------------------------------------------------------------------
+template <int P>
+struct CellBox32 {
+    static constexpr int kW = 16;               // hats per item
+    static constexpr int kRows = (kW + 1) * P;  // frames (128-byte lines) per ray step
+    static constexpr uint32_t kBytes = (uint32_t)kRows * 128;
+    static constexpr uint32_t kStride = (kBytes + 1023) & ~1023u;
+};
+
+template <int P>
+__global__ void __launch_bounds__(kCellWarps * 32, 2)
+adj_cell_tma32_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) {
+    wait_prior_grid();
+    constexpr int W = CellBox32<P>::kW;
+    constexpr uint32_t BOX_BYTES = CellBox32<P>::kBytes;
+    constexpr uint32_t BUF_STRIDE = CellBox32<P>::kStride;
+    extern __shared__ unsigned char smem_cell32_raw[];
+    const uint32_t raw_u32 = smem_u32(smem_cell32_raw);
+    const uint32_t base_u32 = (raw_u32 + 1023) & ~1023u;  // swizzle atom alignment
+    unsigned char* base = smem_cell32_raw + (base_u32 - raw_u32);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int h = lane >> 1, c = lane & 1;  // the lane's hat in the item and its 16-column half
+    const int qx = h & 3;                    // register quad q holds column quad q ^ qx of the half
+    const unsigned char* bufp0 = base + (size_t)(2 * warp) * BUF_STRIDE;
+    const uint32_t buf0 = base_u32 + (2 * warp) * BUF_STRIDE;
+    const uint32_t bar0 = base_u32 + kCellWarps * 2 * BUF_STRIDE + 16 * warp;
+    if (lane == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0 + 8) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int32_t D32 = a.D;
+    const uint64_t tmap = reinterpret_cast<uint64_t>(&ymap);
+    struct Cp {
+        int R;  // first frame of the box: the item's last hat's first tap
+        int32_t r0;
+        float4 w;
+    };
+    auto derive = [&](const Step& s, Cp& cp) {
+        cp.r0 = s.h1;  // weight phase: tap j of every hat weighs 1 - |r0 - j D| 2^-24
+        cp.R = s.h0 - P * (W * s.g + W - 1);
+        cp.w = corner_weights(a.c_W, a.c_W16, s.pos);
+    };
+    auto issue = [&](const Step& s, const Cp& cp, uint32_t b) {
+        if (lane != 0) return;
+        const uint32_t bar = bar0 + 8u * b, dst = buf0 + b * BUF_STRIDE;
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                     "r"(BOX_BYTES)
+                     : "memory");
+        asm volatile(
+            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+            "l"(tmap), "r"(0), "r"(cp.R), "r"(s.row_out), "r"(bar)
+            : "memory");
+    };
+    // records of the current column: hat kbase + h, columns 16 c .. of the pass
+    auto emit = [&](const float (&lo)[1][16], const float (&up)[1][16], int rec, int kbase) {
+        const int k = kbase + h;
+        if (k >= a.K) return;
+        float* part = reinterpret_cast<float*>(a.part);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            float4* o = reinterpret_cast<float4*>(part + ((int64_t)(rec + half) * a.K + k) * a.Bp + 16 * c);
+            const float(&v)[16] = half ? up[0] : lo[0];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                o[q ^ qx] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+        }
+    };
+    Walk wk;
+    ColAcc<float, 1, 16> A;
+    A.zero_all();
+    int jc = 0;
+    uint32_t n_issued = 0, n_done = 0;  // ray copies issued / consumed
+    // steps s0 (consumed now), s1 (copy in flight), s2 (fields loading)
+    Step s0 = walk_next(a, wk, lane);
+    Step s1 = s0.kind ? walk_next(a, wk, lane) : s0;
+    Step s2 = s1.kind ? walk_next(a, wk, lane) : s1;
+    Cp c0{}, c1{};
+    if (s0.kind == 1) {
+        derive(s0, c0);
+        issue(s0, c0, n_issued++ & 1);
+    }
+    if (s1.kind == 1) {
+        derive(s1, c1);
+        issue(s1, c1, n_issued++ & 1);
+    }
+    while (s0.kind) {
+        const int kbase = W * s0.g;
+        if (s0.kind == 1) {
+            const uint32_t b = n_done & 1;
+            if (!mbar_wait(bar0 + 8u * b, (n_done >> 1) & 1)) {
+                if (lane == 0) atomicOr(a.status, 1);
+                if (n_issued > n_done + 1)
+                    mbar_wait(bar0 + 8u * ((n_done + 1) & 1), ((n_done + 1) >> 1) & 1);
+                return;
+            }
+            float wt[2 * P];
+#pragma unroll
+            for (int j = 0; j < 2 * P; ++j)
+                wt[j] = 1.0f - (float)abs(c0.r0 - j * D32) * (1.0f / (float)kFracOne);
+            const unsigned char* buf = bufp0 + b * BUF_STRIDE;
+            const int fb0 = P * (W - 1 - h);  // box line of the lane's first tap
+            float z[1][16];
+#pragma unroll
+            for (int k = 0; k < 16; ++k) z[0][k] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 2 * P; ++j) {
+                const uint32_t line = (uint32_t)(fb0 + j);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t chunk = (uint32_t)(4 * c + (q ^ qx)) ^ (line & 7u);
+                    const float4 v = *reinterpret_cast<const float4*>(buf + line * 128u + chunk * 16u);
+                    fmac2x2(wt[j], v, z[0][4 * q + 0], z[0][4 * q + 1], z[0][4 * q + 2], z[0][4 * q + 3]);
+                }
+            }
+            __syncwarp();  // buffer b is free for the next copy issued into it
+            ++n_done;
+            for (; jc < s0.col; ++jc) {
+                emit(A.lc, A.uc, s0.rec0 + 2 * jc, kbase);
+                A.shift();
+            }
+            acc_add2(A, z, c0.w);
+        } else {
+            // close the item: every column not yet written, then the successor column
+            for (; jc < s0.ncol; ++jc) {
+                emit(A.lc, A.uc, s0.rec0 + 2 * jc, kbase);
+                A.shift();
+            }
+            emit(A.lc, A.uc, s0.rec0 + 2 * s0.ncol, kbase);
+            A.zero_all();
+            jc = 0;
+        }
+        s0 = s1;
+        c0 = c1;
+        s1 = s2;
+        s2 = s1.kind ? walk_next(a, wk, lane) : s1;
+        if (s1.kind == 1) {
+            derive(s1, c1);
+            issue(s1, c1, n_issued++ & 1);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // General kernel (FP32 or FP64; any cadence, batch chunk and alignment).  An
 // item covers hw <= 32 hats (lane = hat).  Per ray step the frames those hats
 // touch are staged by per-lane asynchronous copies into a padded
@@ -1176,6 +1335,54 @@ static cudaError_t dispatch_tma(const rtt_op_s* op, const CellArgs& a, const flo
     return cudaErrorNotSupported;
 }
 
+// one 32-column pass through adj_cell_tma32_kernel; cudaErrorNotSupported
+// unless the pass has 32 columns of a batch of whole passes and the periodic
+// cadence P in {2, 4, 8}
+template <int P>
+static cudaError_t launch_cell_tma32(CellArgs a, const float* y, const int32_t* op_fb,
+                                     const int32_t* op_r0, cudaStream_t st) {
+    constexpr int ROWS = CellBox32<P>::kRows;
+    static_assert(ROWS <= 256, "TMA box rows");
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    const float* yp = y + a.b0;
+    if (!enc || a.seg.total <= 0 || a.Bp != 32 || a.B % 32 != 0 || ((uintptr_t)yp % 16) != 0)
+        return cudaErrorNotSupported;
+    CUtensorMap m;
+    // (the pass's 32 floats = one 128-byte line, frames of a data row, data rows)
+    cuuint64_t dims[3] = {32, (cuuint64_t)a.Tn, (cuuint64_t)a.seg.total};
+    cuuint64_t strides[2] = {(cuuint64_t)a.B * 4, (cuuint64_t)a.Tn * a.B * 4};
+    cuuint32_t box[3] = {32, (cuuint32_t)ROWS, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(yp), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaErrorNotSupported;
+    constexpr int W = CellBox32<P>::kW;
+    a.n_hg = (a.K + W - 1) / W;
+    a.n_bc = 1;
+    a.hw = W;
+    a.c_h0 = op_fb;  // the periodic tap tables (cell_tables)
+    a.c_h1 = op_r0;
+    a.n_items = (int64_t)a.n_hg * a.n_items;  // n_items holds the segment count on entry
+    const size_t smem = 1024 + (size_t)kCellWarps * 2 * CellBox32<P>::kStride + kCellWarps * 16;
+    cudaError_t e = cudaFuncSetAttribute(adj_cell_tma32_kernel<P>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int grid = resident_grid(adj_cell_tma32_kernel<P>, kCellWarps * 32, smem, a.n_items, kCellWarps);
+    return launch_dependent(adj_cell_tma32_kernel<P>, dim3(grid), dim3(kCellWarps * 32), smem, st, m, a);
+}
+
+static cudaError_t dispatch_tma32(const rtt_op_s* op, const CellArgs& a, const float* y, int P,
+                                  cudaStream_t st) {
+    const int32_t *fb = op->c_fb, *r0 = op->c_r0;
+    switch (P) {
+        case 2: return launch_cell_tma32<2>(a, y, fb, r0, st);
+        case 4: return launch_cell_tma32<4>(a, y, fb, r0, st);
+        case 8: return launch_cell_tma32<8>(a, y, fb, r0, st);
+        default: return cudaErrorNotSupported;
+    }
+}
+
 // staged-frame capacity of the general kernel's buffers
 constexpr int kGenFrameCap = 192;
 
@@ -1306,6 +1513,7 @@ int adjoint_best_kind(const rtt_op_s* op, int batch) {
     const int P = frames_per_hat(op->frame_D);
     int hg = 0;
     if (tma_shape(op, batch, P, &hg)) return hg == 2 ? 4 : 3;
+    if (P > 0 && batch % 32 == 0) return 4;  // 32-column passes by the TMA kernel
     return P > 0 ? 2 : 1;
 }
 
@@ -1336,9 +1544,11 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         a.n_items = op->n_seg;
         cudaError_t e = cudaErrorNotSupported;
         if constexpr (sizeof(T) == 4) {
-            if (kind >= 3 && Bp == B)
+            if (kind >= 3 && Bp == B && B <= 16)
                 e = dispatch_tma(op, a, (const float*)y, B, frames_per_hat(op->frame_D), kind == 4 ? 2 : 1,
                                  st);
+            else if (kind >= 3 && Bp == 32 && B % 32 == 0)
+                e = dispatch_tma32(op, a, (const float*)y, frames_per_hat(op->frame_D), st);
         }
         if (e == cudaErrorNotSupported && kind >= 2) {
             cudaGetLastError();  // clear the "not supported" marker, if any

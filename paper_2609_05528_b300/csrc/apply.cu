@@ -1704,10 +1704,12 @@ static cudaError_t launch_fwd9(ApplyArgs<float> a, cudaStream_t st, bool prefetc
     }
 }
 
-// the widest quad-lane chunk for a batch: the largest of 64, 32, 16, 8, 4 that
-// divides it (0 when the batch is not whole 16-byte records)
+// the default quad-lane chunk for a batch: the largest of 32, 16, 8, 4 that
+// divides it (0 when the batch is not whole 16-byte records); 64-column chunks
+// (16-frame tasks) measured slower than 32 (stress1024, batch 64: 33.6 vs
+// 25.9 ms) and are left to the tuner
 static int quad_bc(int B) {
-    for (int bc = 64; bc >= 4; bc >>= 1)
+    for (int bc = 32; bc >= 4; bc >>= 1)
         if (B % bc == 0) return bc;
     return 0;
 }
@@ -1723,7 +1725,7 @@ ApplyVariant variant_for(const rtt_op_s* op, int batch) {
     ApplyVariant v;
     const int P = frames_per_hat(op->frame_D);
     // the periodic quad-lane forward takes any batch of whole 16-byte records,
-    // in chunks of up to 64 columns
+    // in chunks of up to 32 columns
     if (P > 0 && batch % 4 == 0) {
         v.fwd = 7;
         v.fwd_bc = (int8_t)quad_bc(batch);

@@ -277,7 +277,34 @@ def test_quad_lane_forward_same_bits(which, small, schw, B):
                         c.op.set_variant(B, fk, bc, half, 1, fwd_order=order)
                         assert torch.equal(c.op.apply_A(x, arm_mask=mask), y0), (mask, fk, bc, half, order)
     c.op.set_variant(B)
-    assert c.op.get_variant(B)["fwd_kernel"] == 7 and c.op.get_variant(B)["fwd_bc"] == qbc
+    assert c.op.get_variant(B)["fwd_kernel"] == 7 and c.op.get_variant(B)["fwd_bc"] == min(qbc, 32)
+    assert c.op.status(clear=True) == 0
+
+
+@pytest.mark.parametrize("which", ["small", "schw"])
+@pytest.mark.parametrize("B", [32, 64])
+def test_adjoint_32_column_passes_same_bits(which, small, schw, B):
+    """The adjoint at batches of whole 32-column passes: the TMA kernel of
+    32-column passes (adjoint kernels 3 and 4; two lanes per hat) gives the
+    bits of the general and periodic kernels, which match the oracle, on
+    every arm, with 1/4 (small) and 1/2 (schw) hat-step cadences and the
+    records of narrower passes."""
+    c = small if which == "small" else schw
+    for mask in (7, 1, 6):
+        d = torch.from_numpy(I.noise((c.op.arm_rows(mask), c.w.time.n_frames, B), 31 + B).astype(np.float32)).cuda()
+        c.op.set_variant(B, 1, 32, 0, 1)
+        g0 = c.op.apply_AT(d, arm_mask=mask)
+        if B == 32:
+            sub = c.tab.select(_arm_orders(mask))
+            _cmp(g0.cpu().numpy().astype(np.float64),
+                 O.apply_AT(c.w, sub, d.cpu().numpy().astype(np.float64), c.scale), TOL32)
+        for ak in (2, 3, 4):
+            c.op.set_variant(B, 1, 32, 0, ak)
+            assert torch.equal(c.op.apply_AT(d, arm_mask=mask), g0), (mask, ak)
+        c.op.set_variant(B, 1, 32, 0, 4, adj_cols=16)
+        assert torch.equal(c.op.apply_AT(d, arm_mask=mask), g0), (mask, "16-column passes")
+    c.op.set_variant(B)
+    assert c.op.get_variant(B)["adj_kernel"] == 4
     assert c.op.status(clear=True) == 0
 
 
