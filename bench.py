@@ -74,7 +74,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -159,17 +159,18 @@ def recorded_traffic(kernel: str, workload: str = "kerr256"):
     return rec.get("traffic_bytes", {}).get(kernel)
 
 
-def algorithmic_bytes(op, B, elem=4):
-    """Bytes the method must move per launch: y once, x once, plus tables."""
+def algorithmic_bytes(op, B, elem=4, weight_bytes=16):
+    """Bytes the method must move per launch: y once, x once, plus tables
+    (weight_bytes: the four corner weights of a ray, 16 in FP32, 8 in BF16)."""
     E = int(op.info.n_rays)
     R = int(op.info.n_rows)
     S = int(op.info.n_nodes)
     y = R * op.n_frames * B * elem
     x = S * op.n_hats * B * elem
-    table_fwd = E * 32 + (R + 1) * 4
+    table_fwd = E * (16 + weight_bytes) + (R + 1) * 4
     # adjoint: the cell-ordered ray table (row, column, hat base and fraction,
     # four corner weights) and the gather table (four record indices per node)
-    table_adj = E * 32 + S * 16
+    table_adj = E * (16 + weight_bytes) + S * 16
     return {"A": y + x + table_fwd, "AT": y + x + table_adj, "y": y, "x": x}
 
 
@@ -211,6 +212,7 @@ def run_ours(args, rank, world, device):
     import torch
 
     from paper_2609_05528_b300 import inputs as I
+    from paper_2609_05528_b300 import rtt
     torch.cuda.set_device(device)
     w = I.stress1024(0.94)
     tab, op, x = build_workload(device, w, BATCH)
@@ -248,6 +250,30 @@ def run_ours(args, rank, world, device):
     t_AT = time_loop(stream, lambda: op.apply_AT(y, g), args.steps)
     mA, mAT = float(np.median(t_A)), float(np.median(t_AT))
     ab, roof = roofline_of(op, BATCH, mA, mAT, traffic_key="stress1024")
+
+    # the BF16-weight table variant of the same step (rtt_set_weight_precision):
+    # the applies read 8-byte corner weights; y's change against the FP32
+    # weights on every 101st row
+    try:
+        y_ref = y[::101].clone()  # y of the last FP32-weight forward above
+        op.set_weight_precision(rtt.WEIGHTS_BF16)
+        op.apply_A(x, y)
+        op.apply_AT(y, g)
+        mA16 = float(np.median(time_loop(stream, lambda: op.apply_A(x, y), args.steps)))
+        mAT16 = float(np.median(time_loop(stream, lambda: op.apply_AT(y, g), args.steps)))
+        op.apply_A(x, y)
+        rel = float(torch.linalg.vector_norm(y[::101] - y_ref) / torch.linalg.vector_norm(y_ref))
+        op.set_weight_precision(rtt.WEIGHTS_FP32)
+        ab16 = algorithmic_bytes(op, BATCH, weight_bytes=8)
+        peak16, _ = measured_peaks()
+        bf16 = {"ms_per_step": mA16 + mAT16, "value": job_value(world, BATCH, mA16 + mAT16),
+                "A_ms": mA16, "AT_ms": mAT16,
+                "A_frac": ab16["A"] / (mA16 * 1e-3) / 1e9 / peak16,
+                "AT_frac": ab16["AT"] / (mAT16 * 1e-3) / 1e9 / peak16,
+                "y_rel_l2_vs_fp32_weights": rel, "rows_compared": int(y_ref.shape[0])}
+        del y_ref
+    except Exception as exc:  # a measurement extra; report why it failed
+        bf16 = {"error": str(exc)[:200]}
 
     # the same step replayed from a captured CUDA graph
     graph = None
@@ -350,8 +376,9 @@ def run_ours(args, rank, world, device):
     del y, g
     torch.cuda.empty_cache()
 
-    # batch sweep of the same workload (config 5: A and A^T GB/s against HBM),
-    # each batch size autotuned first; y >= 1.5 GB per history, far above L2
+    # batch sweep of the same workload (A and A^T GB/s against HBM, FP32 and
+    # BF16-weight tables), each batch size autotuned first; y >= 1.5 GB per
+    # history, far above L2
     sweep = []
     peak, _ = measured_peaks()
     for B in (() if args.no_sweep else SWEEP_BATCHES):
@@ -366,13 +393,25 @@ def run_ours(args, rank, world, device):
             tA = float(np.median(time_loop(stream, lambda: op.apply_A(xb, yb), reps)))
             tT = float(np.median(time_loop(stream, lambda: op.apply_AT(yb, gb), reps)))
             abb = algorithmic_bytes(op, B)
-            sweep.append({"batch": B, "A_ms": tA, "AT_ms": tT,
-                          "A_gbs": abb["A"] / (tA * 1e-3) / 1e9, "AT_gbs": abb["AT"] / (tT * 1e-3) / 1e9,
-                          "A_frac": abb["A"] / (tA * 1e-3) / 1e9 / peak,
-                          "AT_frac": abb["AT"] / (tT * 1e-3) / 1e9 / peak,
-                          "history_applies_per_s": B / ((tA + tT) * 1e-3),
-                          "variant": {k: tune[k] for k in ("fwd_kernel", "fwd_bc", "fwd_order",
-                                                           "adj_kernel")}})
+            row = {"batch": B, "A_ms": tA, "AT_ms": tT,
+                   "A_gbs": abb["A"] / (tA * 1e-3) / 1e9, "AT_gbs": abb["AT"] / (tT * 1e-3) / 1e9,
+                   "A_frac": abb["A"] / (tA * 1e-3) / 1e9 / peak,
+                   "AT_frac": abb["AT"] / (tT * 1e-3) / 1e9 / peak,
+                   "history_applies_per_s": B / ((tA + tT) * 1e-3),
+                   "variant": {k: tune[k] for k in ("fwd_kernel", "fwd_bc", "fwd_order", "adj_kernel")}}
+            # the BF16-weight table variant beside the FP32 one
+            op.set_weight_precision(rtt.WEIGHTS_BF16)
+            op.apply_A(xb, yb)
+            op.apply_AT(yb, gb)
+            tA16 = float(np.median(time_loop(stream, lambda: op.apply_A(xb, yb), reps)))
+            tT16 = float(np.median(time_loop(stream, lambda: op.apply_AT(yb, gb), reps)))
+            op.set_weight_precision(rtt.WEIGHTS_FP32)
+            ab16 = algorithmic_bytes(op, B, weight_bytes=8)
+            row["bf16_weights"] = {"A_ms": tA16, "AT_ms": tT16,
+                                   "A_frac": ab16["A"] / (tA16 * 1e-3) / 1e9 / peak,
+                                   "AT_frac": ab16["AT"] / (tT16 * 1e-3) / 1e9 / peak,
+                                   "history_applies_per_s": B / ((tA16 + tT16) * 1e-3)}
+            sweep.append(row)
             del xb, yb, gb
             torch.cuda.empty_cache()
         except Exception as exc:
@@ -401,6 +440,7 @@ def run_ours(args, rank, world, device):
                 "serial_ms_per_step": e2e_serial_ms,
                 "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(gh.numel() * 4)},
         "fp64_path": fp64,
+        "bf16_weights": bf16,
         "cuda_graph": graph,
         "sweep": sweep,
         "kerr256": k256,
@@ -546,7 +586,8 @@ def launches_per_step(B: int) -> int:
 def run_sweep(device, batches=(1, 2, 4, 8, 16, 32, 64), reps: int = 5):
     """Throughput sweep on the stress1024 workloads (i=75 deg, 1024x1024,
     256x512 nodes, 256 hats, 1024 frames; Schwarzschild and Kerr a=0.94):
-    A and A^T achieved GB/s (algorithmic bytes / event time) per batch size.
+    A and A^T achieved GB/s (algorithmic bytes / event time) per batch size,
+    and on the Kerr workload the BF16-weight table variant beside it.
     y is >= 1.5 GB per history, far above L2, so no flush is needed."""
     import torch
 
@@ -556,6 +597,7 @@ def run_sweep(device, batches=(1, 2, 4, 8, 16, 32, 64), reps: int = 5):
     stream = torch.cuda.current_stream(device)
     lines = []
     for spin in (0.94, 0.0):
+        bf16 = spin == 0.94
         w = I.stress1024(spin)
         tab = rtt.rtt_trace_rays(w.geometry.spin, w.geometry.incl_deg, w.grid, I.screen_samples(w))
         op = rtt.Operator(w, tab)
@@ -582,12 +624,24 @@ def run_sweep(device, batches=(1, 2, 4, 8, 16, 32, 64), reps: int = 5):
             tA = float(np.mean([a.elapsed_time(b) for a, b, _ in ev]))
             tT = float(np.mean([b.elapsed_time(c) for _, b, c in ev]))
             ab = algorithmic_bytes(op, B)
-            res.append({"batch": B, "A_ms": tA, "AT_ms": tT,
-                        "variant": [tune["fwd_kernel"], tune["fwd_bc"], tune["adj_kernel"]],
-                        "rule_ms": [tune["fwd_ms_rule"], tune["adj_ms_rule"]],
-                        "A_gbs": ab["A"] / (tA * 1e-3) / 1e9, "AT_gbs": ab["AT"] / (tT * 1e-3) / 1e9,
-                        "A_frac": ab["A"] / (tA * 1e-3) / 1e9 / peak,
-                        "AT_frac": ab["AT"] / (tT * 1e-3) / 1e9 / peak})
+            row = {"batch": B, "A_ms": tA, "AT_ms": tT,
+                   "variant": [tune["fwd_kernel"], tune["fwd_bc"], tune["adj_kernel"]],
+                   "rule_ms": [tune["fwd_ms_rule"], tune["adj_ms_rule"]],
+                   "A_gbs": ab["A"] / (tA * 1e-3) / 1e9, "AT_gbs": ab["AT"] / (tT * 1e-3) / 1e9,
+                   "A_frac": ab["A"] / (tA * 1e-3) / 1e9 / peak,
+                   "AT_frac": ab["AT"] / (tT * 1e-3) / 1e9 / peak}
+            if bf16:  # the BF16-weight table variant beside the FP32 one
+                op.set_weight_precision(rtt.WEIGHTS_BF16)
+                op.apply_A(x, y)
+                op.apply_AT(y, g)
+                tA16 = float(np.median(time_loop(stream, lambda: op.apply_A(x, y), reps)))
+                tT16 = float(np.median(time_loop(stream, lambda: op.apply_AT(y, g), reps)))
+                op.set_weight_precision(rtt.WEIGHTS_FP32)
+                ab16 = algorithmic_bytes(op, B, weight_bytes=8)
+                row["bf16_weights"] = {"A_ms": tA16, "AT_ms": tT16,
+                                       "A_frac": ab16["A"] / (tA16 * 1e-3) / 1e9 / peak,
+                                       "AT_frac": ab16["AT"] / (tT16 * 1e-3) / 1e9 / peak}
+            res.append(row)
             del x, y, g
             torch.cuda.empty_cache()
         lines.append({"sweep": f"stress1024 a={spin:g} i=75deg", "rows": R,

@@ -1115,14 +1115,17 @@ __device__ __forceinline__ void fwd9_store(const ApplyArgs<float>& a, int row_ou
 }
 
 constexpr int kFwd9Warps = 4;
-template <int BC>
-struct Fwd9Occ {  // CTAs per SM the register budget is set for
-    static constexpr int kMinBlocks = BC >= 32 ? 3 : 4;
+// CTAs per SM the register budget is set for: four, three for 32 and more
+// columns and for the prefetching form (whose next-task fields and row range
+// spilled in the four-CTA budget)
+template <int BC, bool PF>
+struct Fwd9Occ {
+    static constexpr int kMinBlocks = (BC >= 32 || PF) ? 3 : 4;
 };
 
 // PF: the table loads one task (and, inside a task, one ray) ahead, as fwd8
 template <int BC, int NF, int P, bool PF>
-__global__ void __launch_bounds__(kFwd9Warps * 32, Fwd9Occ<BC>::kMinBlocks)
+__global__ void __launch_bounds__(kFwd9Warps * 32, Fwd9Occ<BC, PF>::kMinBlocks)
 fwd9_kernel(const ApplyArgs<float> a) {
     static_assert(BC == 4 || BC == 8 || BC == 16 || BC == 32 || BC == 64, "16-byte quads");
     wait_prior_grid();
