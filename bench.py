@@ -61,7 +61,7 @@ class ClockSampler:
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,clocks.mem")
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
@@ -90,7 +90,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, smax, reasons = [], [], set()
+        sm, smax, reasons, power, mem = [], [], set(), [], []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         try:
             for line in open(self.path):
@@ -102,6 +102,11 @@ class ClockSampler:
                     smax.append(float(f[2]))
                 except ValueError:
                     continue
+                for v, dst in ((f[3], power), (f[9] if len(f) > 9 else "", mem)):
+                    try:
+                        dst.append(float(v))
+                    except ValueError:
+                        pass
                 for nm, v in zip(names, f[5:9]):
                     if v.lower() == "active":
                         reasons.add(nm)
@@ -112,8 +117,14 @@ class ClockSampler:
                 os.unlink(self.path)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
-                "reasons": sorted(reasons), "samples": len(sm)}
+        out = {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "sm_min_mhz": min(sm),
+               "reasons": sorted(reasons), "samples": len(sm)}
+        if power:
+            out["power_w_max"] = max(power)
+        if mem:
+            out["mem_mhz"] = statistics.median(mem)
+            out["mem_min_mhz"] = min(mem)
+        return out
 
 
 def build_workload(device, w, batch, seed0: int = 1, tune: bool = True):
@@ -376,11 +387,19 @@ def run_ours(args, rank, world, device):
     del y, g
     torch.cuda.empty_cache()
 
+    # kerr256, batch 8 (the autograd reconstruction step's workload), before
+    # the long sweep, with its own clock record
+    with ClockSampler(device.index if device.index is not None else 0) as clk_k:
+        k256 = run_kerr256(args, world, device)
+    k256["clocks"] = clk_k.summary()
+
     # batch sweep of the same workload (A and A^T GB/s against HBM, FP32 and
     # BF16-weight tables), each batch size autotuned first; y >= 1.5 GB per
     # history, far above L2
     sweep = []
     peak, _ = measured_peaks()
+    clk_s = ClockSampler(device.index if device.index is not None else 0)
+    clk_s.__enter__()
     for B in (() if args.no_sweep else SWEEP_BATCHES):
         try:
             tune = op.autotune(B)
@@ -416,11 +435,10 @@ def run_ours(args, rank, world, device):
             torch.cuda.empty_cache()
         except Exception as exc:
             sweep.append({"batch": B, "error": str(exc)[:200]})
+    clk_s.__exit__(None, None, None)
+    sweep_clocks = clk_s.summary() if sweep else None
     n_rays, n_nodes = int(op.info.n_rays), op.n_nodes
     op.close()
-
-    # kerr256, batch 8 (the autograd reconstruction step's workload)
-    k256 = run_kerr256(args, world, device)
 
     value = job_value(world, BATCH, ms_step)
     out = {
@@ -443,6 +461,7 @@ def run_ours(args, rank, world, device):
         "bf16_weights": bf16,
         "cuda_graph": graph,
         "sweep": sweep,
+        "sweep_clocks": sweep_clocks,
         "kerr256": k256,
         "clocks": clocks,
         "gpu_launches": launches_per_step(BATCH) * args.steps,

@@ -281,6 +281,43 @@ def test_quad_lane_forward_same_bits(which, small, schw, B):
     assert c.op.status(clear=True) == 0
 
 
+@pytest.fixture(scope="module")
+def eighth():
+    """small_kerr with a frame step of 1/8 hat step (the periodic kernels' P = 8)."""
+    import dataclasses
+    w = I.small_kerr(spin=0.5, incl_deg=50.0, nx=40, n_r=10, n_phi=20, n_frames=300, n_hats=40, ss=2)
+    w = dataclasses.replace(w, time=I.TimeGrid(300, 0.5, 40, t_end=149.5))
+    return Case(w)
+
+
+@pytest.mark.parametrize("B", [4, 8, 16, 32])
+def test_periodic_kernels_at_eighth_hat_step(eighth, B):
+    """P = 8 frames per hat step: every periodic forward (5-8) and adjoint
+    (2-4) kernel, including the TMA adjoint of 4 columns, which needs P = 8,
+    and the 32-column-pass adjoint, gives the staged and general kernels'
+    bits, which match the oracle."""
+    c = eighth
+    assert c.w.time.hat_step / c.w.time.cadence == 8.0
+    x = torch.from_numpy(I.uniform_batch(c.w, range(B)).astype(np.float32)).cuda()
+    c.op.set_variant(B, 1, min(B, 32), 0, 1)
+    y0 = c.op.apply_A(x)
+    g0 = c.op.apply_AT(y0)
+    if B == 8:
+        _cmp(y0.cpu().numpy().astype(np.float64),
+             O.apply_A(c.w, c.tab, x.cpu().numpy().astype(np.float64), c.scale), TOL32)
+        _cmp(g0.cpu().numpy().astype(np.float64),
+             O.apply_AT(c.w, c.tab, y0.cpu().numpy().astype(np.float64), c.scale), TOL32)
+    for fk in (5, 6, 7, 8):
+        for half in (0, 1):
+            c.op.set_variant(B, fk, min(B, 16 if fk < 7 else 32), half, 1)
+            assert torch.equal(c.op.apply_A(x), y0), (fk, half)
+    for ak in (2, 3, 4):
+        c.op.set_variant(B, 1, min(B, 32), 0, ak)
+        assert torch.equal(c.op.apply_AT(y0), g0), ak
+    c.op.set_variant(B)
+    assert c.op.status(clear=True) == 0
+
+
 @pytest.mark.parametrize("which", ["small", "schw"])
 @pytest.mark.parametrize("B", [32, 64])
 def test_adjoint_32_column_passes_same_bits(which, small, schw, B):
