@@ -811,7 +811,8 @@ typedef struct {
                              4 staged with pipelined bulk corner copies, 5 periodic
                              staged with the whole batch in one chunk, 6 the same with
                              its table loads one task ahead, 7 periodic quad-lane, 8 the
-                             same with its table loads one task ahead */
+                             same with its table loads one task ahead, 9 quad-lane with
+                             the corner slabs staged one ray ahead */
     int32_t fwd_bc;       /* batch entries per forward task */
     int32_t fwd_frames_per_lane;
     int32_t fwd_staging;  /* staged forward: x items in flight per lane */
@@ -841,9 +842,11 @@ typedef struct {
                              columns, so every store instruction writes 512 contiguous
                              bytes (periodic cadences, chunks of 4..64 columns dividing
                              the batch; else staged), 8 kernel 7 with each task's table
-                             loads issued during the task before it */
+                             loads issued during the task before it, 9 kernel 7 with each
+                             ray's corner rows of x copied into shared memory (per-lane
+                             asynchronous copies) during the ray before it */
     int32_t fwd_bc;       /* batch entries per forward task: 1, 2, 4, 8, 16 or 32; 64 for
-                             fwd_kernel 7 and 8 */
+                             fwd_kernel 7 to 9 */
     int32_t fwd_half;     /* staged forward: 1 = half the frames per lane */
     int32_t adj_kernel;   /* adjoint: 1 general (any cadence, batch and precision; frames
                              staged by per-lane copies), 2 periodic (a frame step of 1/2,

@@ -1212,6 +1212,195 @@ fwd9_kernel(const ApplyArgs<float> a) {
     }
 }
 
+// Quad-lane periodic forward with the corner slabs of x staged one ray ahead
+// by per-lane asynchronous copies (fwd10).  The warp walks its tasks as a
+// flat sequence of slots (a ray of a task, or a task without rays): while
+// slot i is contracted, the copies of slot i + 1 (16 bytes per lane and item,
+// into the other of two shared-memory stages; hats outside [0, K) arrive as
+// zeros) and the table fields of slot i + 2 are on their way, so no register
+// holds a corner slab.  A lane combines the corner items it copied itself
+// (the interpolated history z of fwd7_ray, written in place of corner 0),
+// then the frames are fwd9's: the same values, order and bits.
+template <int BC, int NF, int P>
+struct Fwd10Shape {
+    static constexpr int Q = BC / 4;
+    static constexpr int R = 32 / Q;
+    static constexpr int FC = R * NF;
+    static constexpr int ZW = FC / P + 3;       // hats per window
+    static constexpr int SW = ZW * Q;           // 16-byte items per corner slab
+    static constexpr int NU = (SW + 31) / 32;   // items per lane
+    static constexpr int kStage = 4 * SW;       // 16-byte items per stage
+};
+constexpr int kFwd10Warps = 4;
+
+// a slot of the warp's walk: its task and (e < e_end) its ray
+struct Fwd10Slot {
+    int row_out, f_begin, b0, e, e_end;
+    bool valid;
+};
+
+template <int BC, int NF, int P>
+__global__ void __launch_bounds__(kFwd10Warps * 32, 4)
+fwd10_kernel(const ApplyArgs<float> a) {
+    static_assert(BC == 4 || BC == 8 || BC == 16 || BC == 32 || BC == 64, "16-byte quads");
+    wait_prior_grid();
+    using S = Fwd10Shape<BC, NF, P>;
+    constexpr int Q = S::Q, R = S::R, FC = S::FC, SW = S::SW, NU = S::NU;
+    static_assert(FC % P == 0, "chunks start on whole hat steps");
+    static_assert(FC / P <= 128, "remainders stay above -2^31");
+    constexpr int32_t D = kFracOne / P;
+    extern __shared__ __align__(16) float4 smem_f10[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float4* stages = smem_f10 + (size_t)warp * 2 * S::kStage;
+    const int s_l = lane / Q, c_l = lane % Q;  // the lane's hat row and column quad
+    const int64_t KB = (int64_t)a.K * a.B;
+    const int n_rows = a.seg.total;
+    // the walk
+    TaskWalk tw((int64_t)blockIdx.x * kFwd10Warps + warp, (int64_t)gridDim.x * kFwd10Warps, a.n_bchunk,
+                a.n_fchunk);
+    int w_row_out = 0, w_e = 0, w_ee = 0;
+    bool w_valid = tw.r < n_rows;
+    if (w_valid) {
+        int row;
+        task_row(a, tw.r, w_row_out, row);
+        w_e = a.row_ptr[row];
+        w_ee = a.row_ptr[row + 1];
+    }
+    auto take = [&](Fwd10Slot& sl) {  // the walk's current slot, then advance
+        sl.valid = w_valid;
+        sl.row_out = w_row_out;
+        sl.f_begin = tw.f * FC;
+        sl.b0 = tw.b * BC;
+        sl.e = w_e;
+        sl.e_end = w_ee;
+        if (!w_valid) return;
+        if (w_e + 1 < w_ee) {
+            ++w_e;
+            return;
+        }
+        tw.next();
+        w_valid = tw.r < n_rows;
+        if (w_valid) {
+            int row;
+            task_row(a, tw.r, w_row_out, row);
+            w_e = a.row_ptr[row];
+            w_ee = a.row_ptr[row + 1];
+        }
+    };
+    // the copies of a slot's ray into stage st (its window as in fwd9_ray)
+    auto issue = [&](const Fwd10Slot& sl, const Fwd7Ray& rf, int st) {
+        if (sl.valid && sl.e < sl.e_end) {
+            const int k_top = rf.K0 - sl.f_begin / P;
+            const int k_lo = k_top - FC / P + ((rf.F0 + D) >> kFracBits);
+            float4* dst0 = stages + st * S::kStage;
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                const int o = lane + 32 * u;
+                if (u < NU - 1 || o < SW) {
+                    const int k = k_lo + s_l + R * u;
+                    const bool in = k >= 0 && k < a.K;
+#pragma unroll
+                    for (int cn = 0; cn < 4; ++cn) {
+                        const int node = (cn < 2 ? rf.n00 : rf.n01) + (cn & 1) * a.n_phi;
+                        const float* src = in ? a.in + (int64_t)node * KB + (int64_t)k * a.B + sl.b0 + 4 * c_l
+                                              : a.in;
+                        const uint32_t dst = smem_u32(dst0 + cn * SW + o);
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                                     "r"(in ? 16 : 0)
+                                     : "memory");
+                    }
+                }
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    auto fields = [&](const Fwd10Slot& sl) -> Fwd7Ray {
+        Fwd7Ray r{};
+        if (sl.valid && sl.e < sl.e_end) r = fwd7_load_ray(a, sl.e);
+        return r;
+    };
+    Fwd10Slot s0, s1, s2;
+    take(s0);
+    take(s1);
+    Fwd7Ray f0 = fields(s0), f1 = fields(s1);
+    take(s2);
+    issue(s0, f0, 0);
+    float4 acc[NF];
+#pragma unroll
+    for (int j = 0; j < NF; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int st = 0;
+    while (s0.valid) {
+        issue(s1, f1, st ^ 1);
+        const Fwd7Ray f2 = fields(s2);  // two slots ahead
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+        const bool full = s0.f_begin + FC <= a.Tn;
+        if (s0.e < s0.e_end) {
+            float4* stg = stages + st * S::kStage;
+            const int k_top = f0.K0 - s0.f_begin / P;
+            const int k_lo = k_top - FC / P + ((f0.F0 + D) >> kFracBits);
+            const float4 wv = f0.w;
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                const int o = lane + 32 * u;
+                if (u < NU - 1 || o < SW) {
+                    const float4 v0 = stg[o], v1 = stg[SW + o], v2 = stg[2 * SW + o], v3 = stg[3 * SW + o];
+                    float2 r = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v0.x, v0.y));
+                    r = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v1.x, v1.y), r);
+                    r = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v2.x, v2.y), r);
+                    r = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v3.x, v3.y), r);
+                    float2 t = __fmul2_rn(make_float2(wv.x, wv.x), make_float2(v0.z, v0.w));
+                    t = __ffma2_rn(make_float2(wv.y, wv.y), make_float2(v1.z, v1.w), t);
+                    t = __ffma2_rn(make_float2(wv.z, wv.z), make_float2(v2.z, v2.w), t);
+                    t = __ffma2_rn(make_float2(wv.w, wv.w), make_float2(v3.z, v3.w), t);
+                    stg[o] = make_float4(r.x, r.y, t.x, t.y);
+                }
+            }
+            __syncwarp();
+            const float4* zc = stg + c_l;
+            const int32_t rem_s = f0.F0 - s_l * D;
+#pragma unroll
+            for (int j = 0; j < NF; ++j) {
+                if (full || s0.f_begin + s_l + R * j < a.Tn) {
+                    int k;
+                    float fr;
+                    if constexpr (R % P == 0) {
+                        k = k_top + (rem_s >> kFracBits) - j * (R / P);
+                        fr = (float)(rem_s & kFracMask) * (1.0f / (float)kFracOne);
+                    } else {
+                        const int32_t rem = rem_s - R * j * D;
+                        k = k_top + (rem >> kFracBits);
+                        fr = (float)(rem & kFracMask) * (1.0f / (float)kFracOne);
+                    }
+                    const float g = 1.0f - fr;
+                    const float2 g2 = make_float2(g, g), f2v = make_float2(fr, fr);
+                    const float4 p0 = zc[(k - k_lo) * Q];
+                    const float4 p1 = zc[(k + 1 - k_lo) * Q];
+                    float2 lo = make_float2(acc[j].x, acc[j].y);
+                    float2 hi = make_float2(acc[j].z, acc[j].w);
+                    lo = __ffma2_rn(g2, make_float2(p0.x, p0.y), lo);
+                    lo = __ffma2_rn(f2v, make_float2(p1.x, p1.y), lo);
+                    hi = __ffma2_rn(g2, make_float2(p0.z, p0.w), hi);
+                    hi = __ffma2_rn(f2v, make_float2(p1.z, p1.w), hi);
+                    acc[j] = make_float4(lo.x, lo.y, hi.x, hi.y);
+                }
+            }
+        }
+        __syncwarp();  // stage st is free for the copies issued next
+        if (s0.e + 1 >= s0.e_end) {  // the task's last slot: its outputs
+            fwd9_store<BC, NF>(a, s0.row_out, s0.b0, s0.f_begin, full, lane, acc);
+#pragma unroll
+            for (int j = 0; j < NF; ++j) acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        s0 = s1;
+        f0 = f1;
+        s1 = s2;
+        f1 = f2;
+        take(s2);
+        st ^= 1;
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+}
+
 // Forward with the corner slabs of x fetched by bulk asynchronous copies,
 // pipelined over the warp's stream of (task, ray) items.  Tasks, hat windows,
 // interpolation and accumulation order are those of fwd3_kernel<float, BC,
@@ -1707,6 +1896,33 @@ static cudaError_t launch_fwd9(ApplyArgs<float> a, cudaStream_t st, bool prefetc
     }
 }
 
+// quad-lane forward with asynchronous corner staging (fwd10); the same
+// conditions as launch_fwd9
+template <int BC, int NF>
+static cudaError_t launch_fwd10(ApplyArgs<float> a, cudaStream_t st) {
+    const int P = frames_per_hat(a.D);
+    constexpr int FC = Fwd9Shape<BC, NF>::FC;
+    const int cols = a.Bcols > 0 ? a.Bcols : a.B;
+    if (!vec_ok(a) || cols % BC != 0 || P == 0 || FC % P != 0) return cudaErrorNotSupported;
+    a.FC = FC;
+    a.n_fchunk = (a.Tn + FC - 1) / FC;
+    a.n_bchunk = cols / BC;
+    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk * a.n_bchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    auto go = [&](auto kern, int stage_items) -> cudaError_t {
+        const size_t smem = (size_t)kFwd10Warps * 2 * stage_items * 16;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        const int grid = resident_grid(kern, kFwd10Warps * 32, smem, a.n_tasks, kFwd10Warps);
+        return launch_dependent(kern, dim3(grid), dim3(kFwd10Warps * 32), smem, st, a);
+    };
+    switch (P) {
+        case 2: return go(fwd10_kernel<BC, NF, 2>, Fwd10Shape<BC, NF, 2>::kStage);
+        case 4: return go(fwd10_kernel<BC, NF, 4>, Fwd10Shape<BC, NF, 4>::kStage);
+        default: return go(fwd10_kernel<BC, NF, 8>, Fwd10Shape<BC, NF, 8>::kStage);
+    }
+}
+
 // the default quad-lane chunk for a batch: the largest of 32, 16, 8, 4 that
 // divides it (0 when the batch is not whole 16-byte records); 64-column chunks
 // (16-frame tasks) measured slower than 32 (stress1024, batch 64: 33.6 vs
@@ -1792,6 +2008,19 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
                 case 8: return launch_fwd4_any<8>(a, bc, st);
                 default: break;  // not a periodic cadence: staged kernel
             }
+        }
+        if (v.fwd == 9 && (bc == 4 || bc == 8 || bc == 16 || bc == 32 || bc == 64)) {
+            const bool half = v.fwd_half != 0;
+            cudaError_t e;
+            switch (bc) {
+                case 4: e = half ? launch_fwd10<4, 4>(a, st) : launch_fwd10<4, 8>(a, st); break;
+                case 8: e = half ? launch_fwd10<8, 4>(a, st) : launch_fwd10<8, 8>(a, st); break;
+                case 16: e = half ? launch_fwd10<16, 4>(a, st) : launch_fwd10<16, 8>(a, st); break;
+                case 32: e = half ? launch_fwd10<32, 4>(a, st) : launch_fwd10<32, 8>(a, st); break;
+                default: e = half ? launch_fwd10<64, 4>(a, st) : launch_fwd10<64, 8>(a, st); break;
+            }
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();  // clear the "not supported" marker, if any
         }
         if ((v.fwd == 7 || v.fwd == 8) && (bc == 4 || bc == 8 || bc == 16 || bc == 32 || bc == 64)) {
             const bool half = v.fwd_half != 0, pf = v.fwd == 8;

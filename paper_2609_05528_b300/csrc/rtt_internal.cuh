@@ -49,7 +49,8 @@ struct ApplyVariant {
                         // 3 TMA corner slabs (fwd5), 4 pipelined bulk corner copies
                         // (fwd6), 5 periodic one-chunk staged (fwd7), 6 the same with its
                         // table loads one task ahead (fwd8), 7 periodic quad-lane (fwd9),
-                        // 8 the same with its table loads one task ahead
+                        // 8 the same with its table loads one task ahead, 9 quad-lane with
+                        // the corner slabs staged one ray ahead (fwd10)
     int8_t fwd_bc = 0;  // batch entries per forward task (power of two)
     int8_t fwd_half = 0; // staged forward: half the frames per lane (fewer registers)
     int8_t fwd_su = 2;   // staged forward: staging items in flight per lane (1, 2 or 3)

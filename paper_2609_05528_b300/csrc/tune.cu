@@ -69,7 +69,7 @@ extern "C" rtt_status rtt_set_variant(rtt_op op, int batch, const rtt_variant* v
         return RTT_OK;
     }
     const int bc = v->fwd_bc;
-    if (v->fwd_kernel < 1 || v->fwd_kernel > 8 || bc < 1 || bc > 64 || (bc & (bc - 1)) != 0 ||
+    if (v->fwd_kernel < 1 || v->fwd_kernel > 9 || bc < 1 || bc > 64 || (bc & (bc - 1)) != 0 ||
         (bc > 32 && v->fwd_kernel < 7) ||
         v->fwd_half < 0 || v->fwd_half > 1 || v->adj_kernel < 1 || v->adj_kernel > 4) {
         set_error("invalid variant (fwd %d bc %d half %d adj %d)", v->fwd_kernel, bc, v->fwd_half,
@@ -218,7 +218,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
     if (periodic && x_vec) {
         int qbc = 64;
         while (B % qbc != 0) qbc >>= 1;
-        for (int kind = 7; kind <= 8; ++kind)
+        for (int kind = 7; kind <= 9; ++kind)
             for (int bc = qbc; bc >= 4 && bc >= qbc / 4; bc >>= 1)
                 for (int half = 0; half <= 1; ++half) {
                     ApplyVariant v = rule;

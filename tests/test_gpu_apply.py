@@ -175,7 +175,7 @@ def test_autotune_keeps_bits(B):
     g0 = c.op.apply_AT(y0)
     r = c.op.autotune(B)
     assert r["batch"] == B and r["candidates"] >= 4
-    assert r["fwd_kernel"] in range(1, 9) and r["adj_kernel"] in (1, 2, 3, 4)
+    assert r["fwd_kernel"] in range(1, 10) and r["adj_kernel"] in (1, 2, 3, 4)
     if B % 4:
         assert r["adj_kernel"] <= 2  # the TMA adjoint needs 16-byte frame records
     assert 0 < r["fwd_ms"] <= r["fwd_ms_rule"] and 0 < r["adj_ms"] <= r["adj_ms_rule"]
@@ -205,7 +205,7 @@ def test_every_variant_same_bits(which, small, schw, B):
     while bc_max < min(B, 32):
         bc_max *= 2
     n = 0
-    for fk in (1, 2, 3, 4, 5, 6, 7, 8):
+    for fk in (1, 2, 3, 4, 5, 6, 7, 8, 9):
         for bc in sorted({bc_max, max(1, bc_max // 2), max(1, bc_max // 4)}):
             for half in (0, 1):
                 for su in ((1, 2, 3) if (fk == 1 and half == 0 and bc in (4, 8)) else (2,)):
@@ -224,7 +224,7 @@ def test_every_variant_same_bits(which, small, schw, B):
     for ak in (1, 2, 3, 4):
         c.op.set_variant(B, 1, bc_max, 0, ak)
         assert torch.equal(c.op.apply_AT(y1, arm_mask=1), g1), ak
-    for fk in (1, 3, 4, 5, 7):
+    for fk in (1, 3, 4, 5, 7, 9):
         for order in (0, 1):
             c.op.set_variant(B, fk, bc_max, 0, 1, fwd_order=order)
             assert torch.equal(c.op.apply_A(x, arm_mask=1), y1), (fk, order)
@@ -268,7 +268,7 @@ def test_quad_lane_forward_same_bits(which, small, schw, B):
             sub = c.tab.select(_arm_orders(mask))
             _cmp(y0.cpu().numpy().astype(np.float64),
                  O.apply_A(c.w, sub, x.cpu().numpy().astype(np.float64), c.scale), TOL32)
-        for fk in (7, 8):
+        for fk in (7, 8, 9):
             for bc in (qbc, qbc // 2, qbc // 4):
                 if bc < 4:
                     continue
@@ -307,7 +307,7 @@ def test_periodic_kernels_at_eighth_hat_step(eighth, B):
              O.apply_A(c.w, c.tab, x.cpu().numpy().astype(np.float64), c.scale), TOL32)
         _cmp(g0.cpu().numpy().astype(np.float64),
              O.apply_AT(c.w, c.tab, y0.cpu().numpy().astype(np.float64), c.scale), TOL32)
-    for fk in (5, 6, 7, 8):
+    for fk in (5, 6, 7, 8, 9):
         for half in (0, 1):
             c.op.set_variant(B, fk, min(B, 16 if fk < 7 else 32), half, 1)
             assert torch.equal(c.op.apply_A(x), y0), (fk, half)

@@ -68,7 +68,7 @@ def test_bf16_weights_against_oracle_and_variants(case, B):
     bc = 1
     while bc < min(B, 16):
         bc *= 2
-    for fk in (1, 2, 3, 4, 5, 6, 7, 8):
+    for fk in (1, 2, 3, 4, 5, 6, 7, 8, 9):
         op.set_variant(B, fk, bc, 0, 1)
         assert torch.equal(op.apply_A(xt), y), fk
     for ak in (1, 2, 3, 4):
