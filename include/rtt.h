@@ -856,8 +856,9 @@ typedef struct {
                              (TMA: the whole batch of 4, 8 or 16 entries in one chunk with
                              whole frames per 128-byte line; at batches of whole 32-column
                              passes both run the TMA kernel of 32-column passes, 16-hat
-                             items with two lanes per hat); where the call does not allow
-                             the choice, the next one down runs */
+                             items with two lanes per hat; at batches of 1 or 2 columns both
+                             run the direct-load kernel, 32- or 64-hat items); where the call
+                             does not allow the choice, the next one down runs */
     int32_t fwd_staging;  /* staged forward: x items in flight per lane, 1, 2 or 3
                              (0 = 2; other values than 2 only at 4 or 8 entries) */
     int32_t fwd_order;    /* forward task rows: 0 in (order, pixel) order, 1 in source-cell

@@ -28,6 +28,7 @@
 // work items are handed out by an atomic ticket counter (integer, so the
 // order in which warps take items changes no bit); the gather resets it.
 #include <algorithm>
+#include <type_traits>
 #include <cub/cub.cuh>
 #include <vector>
 
@@ -641,6 +642,88 @@ adj_cell_tma32_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a
             derive(s1, c1);
             issue(s1, c1, n_issued++ & 1);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Direct-load kernel for batches of one or two columns (FP32, a periodic
+// cadence of P in {2, 4, 8} frames per hat step).  A frame record is 4 or 8
+// bytes, too small for the staged kernels' 16-byte pieces, so each lane (a
+// hat of the item's 32 HG) reads its 2P taps straight from y through L1
+// (neighbouring lanes' windows overlap by half); the taps of the next ray
+// step are loaded while the current one is contracted.  Taps outside the
+// observation read as zero, as the TMA kernels' out-of-bounds fill.  The
+// walk, tap weights, fused multiply-add chains, accumulators and records are
+// adj_cell_tma_kernel's: the same bits.
+// ---------------------------------------------------------------------------
+template <int BC, int P, int HG>
+__global__ void __launch_bounds__(kCellWarps * 32, 4)
+adj_cell_direct_kernel(const CellArgs a) {
+    static_assert(BC == 1 || BC == 2, "one or two columns");
+    wait_prior_grid();
+    constexpr int HATS = 32 * HG;
+    constexpr int NT = 2 * P;  // taps per hat
+    const int lane = threadIdx.x & 31;
+    const float* y = reinterpret_cast<const float*>(a.y);
+    const int32_t D32 = a.D;
+    // the taps of a ray step: hat kg0 + lane + 32 h reads frames fbase - P k + j
+    auto load_taps = [&](const Step& s, float (&t)[HG][NT][BC]) {
+        const float* yr = y + (int64_t)s.row_out * a.Tn * BC;
+        const int kg0 = HATS * s.g;
+#pragma unroll
+        for (int h = 0; h < HG; ++h) {
+            const int f0 = s.h0 - P * (kg0 + lane + 32 * h);
+            const bool inside = f0 >= 0 && f0 + NT <= a.Tn;
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const int f = f0 + j;
+                const bool ok = inside || (f >= 0 && f < a.Tn);
+#pragma unroll
+                for (int b = 0; b < BC; ++b) t[h][j][b] = ok ? __ldg(yr + (int64_t)f * BC + b) : 0.0f;
+            }
+        }
+    };
+    Walk wk;
+    ColAcc<float, HG, BC> A;
+    A.zero_all();
+    int jc = 0;
+    Step s0 = walk_next(a, wk, lane);
+    Step s1 = s0.kind ? walk_next(a, wk, lane) : s0;
+    float t0[HG][NT][BC], t1[HG][NT][BC];
+    if (s0.kind == 1) load_taps(s0, t0);
+    EmitAt at{0, 0, BC, 32, false};
+    while (s0.kind) {
+        if (s1.kind == 1) load_taps(s1, t1);  // the next step's taps, in flight during this one
+        at.kbase = HATS * s0.g;
+        if (s0.kind == 1) {
+            float wt[NT];
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+                wt[j] = 1.0f - (float)abs(s0.h1 - j * D32) * (1.0f / (float)kFracOne);
+            float z[HG][BC];
+#pragma unroll
+            for (int h = 0; h < HG; ++h)
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    float acc = 0.0f;
+#pragma unroll
+                    for (int j = 0; j < NT; ++j) acc = __fmaf_rn(wt[j], t0[h][j][b], acc);
+                    z[h][b] = acc;
+                }
+            for (; jc < s0.col; ++jc) next_column(a, A, s0.rec0 + 2 * jc, at, lane);
+            const float4 w = corner_weights(a.c_W, a.c_W16, s0.pos);
+            A.add(z, w.x, w.y, w.z, w.w);
+        } else {
+            finish_item(a, A, jc, s0, at, lane);
+        }
+        s0 = s1;
+#pragma unroll
+        for (int h = 0; h < HG; ++h)
+#pragma unroll
+            for (int j = 0; j < NT; ++j)
+#pragma unroll
+                for (int b = 0; b < BC; ++b) t0[h][j][b] = t1[h][j][b];
+        s1 = s0.kind ? walk_next(a, wk, lane) : s0;
     }
 }
 
@@ -1383,6 +1466,48 @@ static cudaError_t dispatch_tma32(const rtt_op_s* op, const CellArgs& a, const f
     }
 }
 
+// a 1- or 2-column batch through adj_cell_direct_kernel; cudaErrorNotSupported
+// unless the cadence is periodic (P in {2, 4, 8})
+template <int BC, int P, int HG>
+static cudaError_t launch_cell_direct(CellArgs a, const int32_t* op_fb, const int32_t* op_r0,
+                                      cudaStream_t st) {
+    if (a.seg.total <= 0 || a.B != BC || a.Bp != BC) return cudaErrorNotSupported;
+    a.n_hg = (a.K + 32 * HG - 1) / (32 * HG);
+    a.n_bc = 1;
+    a.hw = 32 * HG;
+    a.c_h0 = op_fb;  // the periodic tap tables (cell_tables)
+    a.c_h1 = op_r0;
+    a.n_items = (int64_t)a.n_hg * a.n_items;  // n_items holds the segment count on entry
+    const int grid =
+        resident_grid(adj_cell_direct_kernel<BC, P, HG>, kCellWarps * 32, 0, a.n_items, kCellWarps);
+    return launch_dependent(adj_cell_direct_kernel<BC, P, HG>, dim3(grid), dim3(kCellWarps * 32), 0, st,
+                            a);
+}
+
+static cudaError_t dispatch_direct(const rtt_op_s* op, const CellArgs& a, int B, int P, int hg,
+                                   cudaStream_t st) {
+    const int32_t *fb = op->c_fb, *r0 = op->c_r0;
+    auto go = [&](auto b_tag, auto p_tag) -> cudaError_t {
+        constexpr int BC = decltype(b_tag)::value, PP = decltype(p_tag)::value;
+        return hg == 2 ? launch_cell_direct<BC, PP, 2>(a, fb, r0, st)
+                       : launch_cell_direct<BC, PP, 1>(a, fb, r0, st);
+    };
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    using I4 = std::integral_constant<int, 4>;
+    using I8 = std::integral_constant<int, 8>;
+    if (B == 1) {
+        if (P == 2) return go(I1{}, I2{});
+        if (P == 4) return go(I1{}, I4{});
+        if (P == 8) return go(I1{}, I8{});
+    } else if (B == 2) {
+        if (P == 2) return go(I2{}, I2{});
+        if (P == 4) return go(I2{}, I4{});
+        if (P == 8) return go(I2{}, I8{});
+    }
+    return cudaErrorNotSupported;
+}
+
 // staged-frame capacity of the general kernel's buffers
 constexpr int kGenFrameCap = 192;
 
@@ -1514,6 +1639,7 @@ int adjoint_best_kind(const rtt_op_s* op, int batch) {
     int hg = 0;
     if (tma_shape(op, batch, P, &hg)) return hg == 2 ? 4 : 3;
     if (P > 0 && batch % 32 == 0) return 4;  // 32-column passes by the TMA kernel
+    if (P > 0 && batch <= 2) return 4;       // the direct-load kernel (kinds 3 and 4: 32- or 64-hat items)
     return P > 0 ? 2 : 1;
 }
 
@@ -1544,7 +1670,9 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         a.n_items = op->n_seg;
         cudaError_t e = cudaErrorNotSupported;
         if constexpr (sizeof(T) == 4) {
-            if (kind >= 3 && Bp == B && B <= 16)
+            if (kind >= 3 && B <= 2)
+                e = dispatch_direct(op, a, B, frames_per_hat(op->frame_D), kind == 4 ? 2 : 1, st);
+            else if (kind >= 3 && Bp == B && B <= 16)
                 e = dispatch_tma(op, a, (const float*)y, B, frames_per_hat(op->frame_D), kind == 4 ? 2 : 1,
                                  st);
             else if (kind >= 3 && Bp == 32 && B % 32 == 0)

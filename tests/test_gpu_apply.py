@@ -187,7 +187,7 @@ def test_autotune_keeps_bits(B):
 
 
 @pytest.mark.parametrize("which", ["small", "schw"])
-@pytest.mark.parametrize("B", [1, 3, 4, 8, 16])
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 8, 16])
 def test_every_variant_same_bits(which, small, schw, B):
     """Every kernel variant (rtt_set_variant) of the FP32 forward and adjoint
     gives the same bits as the default rule, which matches the oracle; the
@@ -290,7 +290,7 @@ def eighth():
     return Case(w)
 
 
-@pytest.mark.parametrize("B", [4, 8, 16, 32])
+@pytest.mark.parametrize("B", [1, 2, 4, 8, 16, 32])
 def test_periodic_kernels_at_eighth_hat_step(eighth, B):
     """P = 8 frames per hat step: every periodic forward (5-8) and adjoint
     (2-4) kernel, including the TMA adjoint of 4 columns, which needs P = 8,
