@@ -841,7 +841,9 @@ typedef struct {
                              fwd_bc / 4 lanes share a frame, each holding 4 of its
                              columns, so every store instruction writes 512 contiguous
                              bytes (periodic cadences, chunks of 4..64 columns dividing
-                             the batch; else staged), 8 kernel 7 with each task's table
+                             the batch; at batches of 1 or 2 columns a lane holds 4 / B
+                             consecutive frames instead; else staged), 8 kernel 7 with
+                             each task's table
                              loads issued during the task before it, 9 kernel 7 with each
                              ray's corner rows of x copied into shared memory (per-lane
                              asynchronous copies) during the ray before it */

@@ -1212,6 +1212,197 @@ fwd9_kernel(const ApplyArgs<float> a) {
     }
 }
 
+// Periodic forward for batches of one or two columns (forward kernels 7 and
+// 8 there): each lane holds one 16-byte unit of y, the G = 4 / BC
+// consecutive frames f_begin + G lane + i + 32 G j (i < G, j < NF) of all BC
+// columns, so a warp's store instruction writes 512 contiguous bytes, as in
+// the quad-lane kernels.  The hat window, the staged history z (one hat
+// record per lane and item: a coalesced 4- or 8-byte read of each corner
+// row), the ray order and each output's fused multiply-add chain are fwd7's:
+// the same bits.
+template <int BC, int NF>
+struct Fwd11Shape {
+    static constexpr int G = 4 / BC;            // frames per lane unit
+    static constexpr int FC = 32 * G * NF;      // frames per task
+};
+
+template <int BC, int NF, int P>
+__device__ __forceinline__ void fwd11_ray(const ApplyArgs<float>& a, const Fwd7Ray& rf, int hb,
+                                          int f_begin, bool full, int lane, float* zs,
+                                          float (&acc)[NF][4]) {
+    constexpr int G = Fwd11Shape<BC, NF>::G;
+    constexpr int FC = Fwd11Shape<BC, NF>::FC;
+    constexpr int ZW = FC / P + 3;          // hats staged per task window
+    constexpr int NU = (ZW + 31) / 32;      // hats per lane
+    constexpr int32_t D = kFracOne / P;
+    const int64_t KB = (int64_t)a.K * BC;  // floats per node row of x (B = BC)
+    const int k_top = rf.K0 - hb;
+    const int k_lo = k_top - FC / P + ((rf.F0 + D) >> kFracBits);
+    const float* b00 = a.in + (int64_t)rf.n00 * KB;
+    const float* b01 = a.in + (int64_t)rf.n01 * KB;
+    const int64_t rstep = (int64_t)a.n_phi * KB;  // the radial neighbour's row
+    const float4 wv = rf.w;
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int o = lane + 32 * u;
+        const int k = k_lo + o;
+        if (u < NU - 1 || o < ZW) {
+            const bool ok = k >= 0 && k < a.K;
+#pragma unroll
+            for (int b = 0; b < BC; ++b) {
+                float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f;
+                if (ok) {
+                    const int64_t off = (int64_t)k * BC + b;
+                    v0 = __ldg(b00 + off);
+                    v1 = __ldg(b00 + rstep + off);
+                    v2 = __ldg(b01 + off);
+                    v3 = __ldg(b01 + rstep + off);
+                }
+                float r = __fmul_rn(wv.x, v0);
+                r = __fmaf_rn(wv.y, v1, r);
+                r = __fmaf_rn(wv.z, v2, r);
+                r = __fmaf_rn(wv.w, v3, r);
+                zs[o * BC + b] = r;
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            const int fl = G * lane + i + 32 * G * j;  // frame offset in the chunk
+            if (full || f_begin + fl < a.Tn) {
+                const int32_t rem = rf.F0 - fl * D;
+                const int k = k_top + (rem >> kFracBits);
+                const float fr = (float)(rem & kFracMask) * (1.0f / (float)kFracOne);
+                const float g = 1.0f - fr;
+#pragma unroll
+                for (int b = 0; b < BC; ++b) {
+                    const float p0 = zs[(k - k_lo) * BC + b];
+                    const float p1 = zs[(k + 1 - k_lo) * BC + b];
+                    float c = acc[j][i * BC + b];
+                    c = __fmaf_rn(g, p0, c);
+                    c = __fmaf_rn(fr, p1, c);
+                    acc[j][i * BC + b] = c;
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <int BC, int NF>
+__device__ __forceinline__ void fwd11_store(const ApplyArgs<float>& a, int row_out, int f_begin, bool full,
+                                            int lane, const float (&acc)[NF][4]) {
+    constexpr int G = Fwd11Shape<BC, NF>::G;
+    float* base = a.out + ((int64_t)row_out * a.Tn + f_begin + G * lane) * BC;
+#pragma unroll
+    for (int j = 0; j < NF; ++j) {
+        float* o = base + (int64_t)32 * G * j * BC;
+        const int f0 = f_begin + G * lane + 32 * G * j;
+        if (full || f0 + G <= a.Tn) {
+            *reinterpret_cast<float4*>(o) = make_float4(acc[j][0], acc[j][1], acc[j][2], acc[j][3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < G; ++i)
+                if (f0 + i < a.Tn)
+#pragma unroll
+                    for (int b = 0; b < BC; ++b) o[i * BC + b] = acc[j][i * BC + b];
+        }
+    }
+}
+
+// PF: the table loads one task (and, inside a task, one ray) ahead, as fwd8
+template <int BC, int NF, int P, bool PF>
+__global__ void __launch_bounds__(kFwd9Warps * 32, 4)
+fwd11_kernel(const ApplyArgs<float> a) {
+    static_assert(BC == 1 || BC == 2, "one or two columns");
+    wait_prior_grid();
+    constexpr int FC = Fwd11Shape<BC, NF>::FC;
+    static_assert(FC % P == 0, "chunks start on whole hat steps");
+    static_assert(FC / P <= 128, "remainders stay above -2^31");
+    constexpr int ZW = FC / P + 3;
+    __shared__ float zs_all[kFwd9Warps][ZW * BC];
+    float* zs = zs_all[threadIdx.x >> 5];
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = (int64_t)blockIdx.x * kFwd9Warps + (threadIdx.x >> 5);
+    const int64_t n_warps = (int64_t)gridDim.x * kFwd9Warps;
+    const int n_rows = a.seg.total;
+    auto zero = [&](float (&acc)[NF][4]) {
+#pragma unroll
+        for (int j = 0; j < NF; ++j)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[j][q] = 0.0f;
+    };
+    if constexpr (!PF) {
+        for (TaskWalk tw(warp_global, n_warps, 1, a.n_fchunk); tw.r < n_rows; tw.next()) {
+            int row_out, row;
+            task_row(a, tw.r, row_out, row);
+            const int f_begin = tw.f * FC;
+            const bool full = f_begin + FC <= a.Tn;
+            const int hb = f_begin / P;
+            float acc[NF][4];
+            zero(acc);
+            const int e_begin = a.row_ptr[row], e_end = a.row_ptr[row + 1];
+            for (int e = e_begin; e < e_end; ++e)
+                fwd11_ray<BC, NF, P>(a, fwd7_load_ray(a, e), hb, f_begin, full, lane, zs, acc);
+            fwd11_store<BC, NF>(a, row_out, f_begin, full, lane, acc);
+        }
+    } else {
+        TaskWalk tw(warp_global, n_warps, 1, a.n_fchunk);
+        if (tw.r >= n_rows) return;
+        int row_out, row;
+        task_row(a, tw.r, row_out, row);
+        int eb = a.row_ptr[row], ee = a.row_ptr[row + 1];
+        TaskWalk tn = tw;
+        tn.next();
+        int row_out_n = 0, eb_n = 0, ee_n = 0;
+        if (tn.r < n_rows) {
+            int rn;
+            task_row(a, tn.r, row_out_n, rn);
+            eb_n = a.row_ptr[rn];
+            ee_n = a.row_ptr[rn + 1];
+        }
+        Fwd7Ray cur{};
+        if (eb < ee) cur = fwd7_load_ray(a, eb);
+        while (true) {
+            Fwd7Ray nxt{};
+            if (tn.r < n_rows && eb_n < ee_n) nxt = fwd7_load_ray(a, eb_n);
+            TaskWalk tnn = tn;
+            tnn.next();
+            int row_out_nn = 0, eb_nn = 0, ee_nn = 0;
+            if (tnn.r < n_rows) {
+                int r2;
+                task_row(a, tnn.r, row_out_nn, r2);
+                eb_nn = a.row_ptr[r2];
+                ee_nn = a.row_ptr[r2 + 1];
+            }
+            const int f_begin = tw.f * FC;
+            const bool full = f_begin + FC <= a.Tn;
+            const int hb = f_begin / P;
+            float acc[NF][4];
+            zero(acc);
+            for (int e = eb; e < ee; ++e) {
+                const Fwd7Ray rf = cur;
+                if (e + 1 < ee) cur = fwd7_load_ray(a, e + 1);
+                fwd11_ray<BC, NF, P>(a, rf, hb, f_begin, full, lane, zs, acc);
+            }
+            fwd11_store<BC, NF>(a, row_out, f_begin, full, lane, acc);
+            if (tn.r >= n_rows) break;
+            tw = tn;
+            row_out = row_out_n;
+            eb = eb_n;
+            ee = ee_n;
+            cur = nxt;
+            tn = tnn;
+            row_out_n = row_out_nn;
+            eb_n = eb_nn;
+            ee_n = ee_nn;
+        }
+    }
+}
+
 // Quad-lane periodic forward with the corner slabs of x staged one ray ahead
 // by per-lane asynchronous copies (fwd10).  The warp walks its tasks as a
 // flat sequence of slots (a ray of a task, or a task without rays): while
@@ -1896,6 +2087,39 @@ static cudaError_t launch_fwd9(ApplyArgs<float> a, cudaStream_t st, bool prefetc
     }
 }
 
+// the forward of a 1- or 2-column batch (fwd11); cudaErrorNotSupported
+// unless the cadence is periodic, B = BC and a data row's frames are whole
+// 16-byte units (T BC a multiple of 4)
+template <int BC, int NF>
+static cudaError_t launch_fwd11(ApplyArgs<float> a, cudaStream_t st, bool prefetch) {
+    const int P = frames_per_hat(a.D);
+    constexpr int FC = Fwd11Shape<BC, NF>::FC;
+    if (a.B != BC || a.Bcols > 0 || P == 0 || FC % P != 0 || ((int64_t)a.Tn * BC) % 4 != 0 ||
+        ((uintptr_t)a.out % 16) != 0)
+        return cudaErrorNotSupported;
+    a.FC = FC;
+    a.n_fchunk = (a.Tn + FC - 1) / FC;
+    a.n_bchunk = 1;
+    a.n_tasks = (int64_t)a.seg.total * a.n_fchunk;
+    if (a.n_tasks == 0) return cudaSuccess;
+    auto go = [&](auto kern) {
+        const int grid = resident_grid(kern, kFwd9Warps * 32, 0, a.n_tasks, kFwd9Warps);
+        return launch_dependent(kern, dim3(grid), dim3(kFwd9Warps * 32), 0, st, a);
+    };
+    if (prefetch) {
+        switch (P) {
+            case 2: return go(fwd11_kernel<BC, NF, 2, true>);
+            case 4: return go(fwd11_kernel<BC, NF, 4, true>);
+            default: return go(fwd11_kernel<BC, NF, 8, true>);
+        }
+    }
+    switch (P) {
+        case 2: return go(fwd11_kernel<BC, NF, 2, false>);
+        case 4: return go(fwd11_kernel<BC, NF, 4, false>);
+        default: return go(fwd11_kernel<BC, NF, 8, false>);
+    }
+}
+
 // quad-lane forward with asynchronous corner staging (fwd10); the same
 // conditions as launch_fwd9
 template <int BC, int NF>
@@ -1948,6 +2172,9 @@ ApplyVariant variant_for(const rtt_op_s* op, int batch) {
     if (P > 0 && batch % 4 == 0) {
         v.fwd = 7;
         v.fwd_bc = (int8_t)quad_bc(batch);
+    } else if (P > 0 && batch <= 2) {  // 16-byte units of G = 4 / B frames
+        v.fwd = 7;
+        v.fwd_bc = (int8_t)batch;
     } else {
         v.fwd = 1;
         v.fwd_bc = (int8_t)pick_bc(batch);
@@ -2019,6 +2246,15 @@ cudaError_t launch_forward(const rtt_op_s* op, const T* x, T* y, int B, const Ar
                 case 32: e = half ? launch_fwd10<32, 4>(a, st) : launch_fwd10<32, 8>(a, st); break;
                 default: e = half ? launch_fwd10<64, 4>(a, st) : launch_fwd10<64, 8>(a, st); break;
             }
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();  // clear the "not supported" marker, if any
+        }
+        if ((v.fwd == 7 || v.fwd == 8) && (bc == 1 || bc == 2) && B == bc) {
+            // frames of one or two columns in 16-byte units: NF = 2 (BC = 1) or 4
+            // (BC = 2) units per lane, 256 frames per task (half: 128)
+            const bool half = v.fwd_half != 0, pf = v.fwd == 8;
+            const cudaError_t e = bc == 1 ? (half ? launch_fwd11<1, 1>(a, st, pf) : launch_fwd11<1, 2>(a, st, pf))
+                                          : (half ? launch_fwd11<2, 2>(a, st, pf) : launch_fwd11<2, 4>(a, st, pf));
             if (e != cudaErrorNotSupported) return e;
             cudaGetLastError();  // clear the "not supported" marker, if any
         }

@@ -236,6 +236,24 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                     }
                 }
     }
+    // the same kernels for 1- or 2-column batches (16-byte units of 4 / B frames)
+    if (periodic && B <= 2)
+        for (int kind = 7; kind <= 8; ++kind)
+            for (int half = 0; half <= 1; ++half) {
+                ApplyVariant v = rule;
+                v.fwd = (int8_t)kind;
+                v.fwd_bc = (int8_t)B;
+                v.fwd_half = (int8_t)half;
+                v.fwd_su = 2;
+                const float ms = time_it(v, false);
+                if (ms < fwd_best) {
+                    fwd_best = ms;
+                    best.fwd = v.fwd;
+                    best.fwd_bc = v.fwd_bc;
+                    best.fwd_half = v.fwd_half;
+                    best.fwd_su = v.fwd_su;
+                }
+            }
     // forward task rows in source-cell order, for the chosen kernel
     {
         ApplyVariant v = best;
