@@ -597,9 +597,11 @@ def job_value(world: int, batch: int, ms: float) -> float:
 
 
 def launches_per_step(B: int) -> int:
-    """Kernel launches of one A + A^T pair: one forward launch; per 32-column
-    batch pass one cell kernel and one gather launch."""
-    return 1 + 2 * ((B + 31) // 32)
+    """Kernel launches of one A + A^T pair: one forward launch; per batch pass
+    of the adjoint (32 columns, 64 at batches of whole 64-column passes) one
+    cell kernel and one gather launch."""
+    pc = 64 if B % 64 == 0 else 32
+    return 1 + 2 * ((B + pc - 1) // pc)
 
 
 def run_sweep(device, batches=(1, 2, 4, 8, 16, 32, 64), reps: int = 5):

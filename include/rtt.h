@@ -823,7 +823,8 @@ typedef struct {
     int32_t candidates;             /* configurations timed */
     int32_t fwd_order;    /* forward task rows: 0 (order, pixel), 1 source-cell order */
     int32_t fwd_cols;     /* forward column passes (0: all columns at once) */
-    int32_t adj_cols;     /* adjoint columns per pass (0: 32 in FP32) */
+    int32_t adj_cols;     /* adjoint columns per pass (0: 32 in FP32, 64 at batches of whole
+                             64-column passes) */
 } rtt_tune_result;
 
 rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* stream, rtt_tune_result* out);
@@ -857,8 +858,9 @@ typedef struct {
                              tensor copies with 32-hat items, 4 the same with 64-hat items
                              (TMA: the whole batch of 4, 8 or 16 entries in one chunk with
                              whole frames per 128-byte line; at batches of whole 32-column
-                             passes both run the TMA kernel of 32-column passes, 16-hat
-                             items with two lanes per hat; at batches of 1 or 2 columns both
+                             passes both run the TMA kernel of 32- or (batches of whole
+                             64-column passes) 64-column passes, 16- or 8-hat items with
+                             two or four lanes per hat; at batches of 1 or 2 columns both
                              run the direct-load kernel, 32- or 64-hat items); where the call
                              does not allow the choice, the next one down runs */
     int32_t fwd_staging;  /* staged forward: x items in flight per lane, 1, 2 or 3
@@ -871,8 +873,9 @@ typedef struct {
                              launch, or a multiple of 4 dividing the batch = the whole
                              operator for that many columns at a time (bounds x's and
                              y's working set for large batches); 0..64 */
-    int32_t adj_cols;     /* adjoint columns per pass (0 = 32; else 4..32, a multiple of
-                             4): the partial records hold one pass */
+    int32_t adj_cols;     /* adjoint columns per pass (0 = 32, or 64 at batches of whole
+                             64-column passes; else 4..32, a multiple of 4): the partial
+                             records hold one pass */
 } rtt_variant;
 
 /*

@@ -487,41 +487,45 @@ adj_cell_tma_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) 
 }
 
 // ---------------------------------------------------------------------------
-// TMA kernel for 32-column passes (FP32; any batch of whole 32-column passes,
-// a periodic cadence of P in {2, 4, 8} frames per hat step).  A pass's frame
-// record is one 128-byte line, so a ray step's frames arrive by one 3D tensor
-// copy of the pass's columns (the tensor map's line stride is the batch's
-// frame stride) under the 128-byte swizzle, as in adj_cell_tma_kernel.  Two
-// lanes share a hat: lane (h, c) = (lane / 2, lane % 2) holds the 16 columns
-// 16 c .. 16 c + 15 of hat h of the item's 16, so its accumulators are those
-// of the 16-column kernel.  Its register quad q holds column quad q ^ (h & 3)
-// of its half: consecutive hats' taps lie P lines apart, and with the quads
-// spread this way a warp's reads of a quad meet all eight bank groups.  Each
-// output's tap chain, the walk and the records are the other kernels' (the
-// same bits).
+// TMA kernel for 32- and 64-column passes (FP32; any batch of whole passes, a
+// periodic cadence of P in {2, 4, 8} frames per hat step).  A pass's frame
+// record is PW / 32 whole 128-byte lines, so a ray step's frames arrive by
+// one tensor copy of the pass's columns (the tensor map's frame stride is
+// the batch's) under the 128-byte swizzle, as in adj_cell_tma_kernel.
+// PW / 16 lanes share a hat: lane (h, c) = (lane / L, lane % L) holds the
+// 16 columns 16 c .. 16 c + 15 of hat h of the item's 32 / L, so its
+// accumulators are those of the 16-column kernel.  Its register quad q holds
+// column quad q ^ (h & 3) of its 16: consecutive hats' taps lie P frames
+// apart, and with the quads spread this way a warp's reads of a quad meet all
+// eight bank groups (at P = 2, 4 and 8).  Each output's tap chain, the walk
+// and the records are the other kernels' (the same bits).
 // ---------------------------------------------------------------------------
-template <int P>
-struct CellBox32 {
-    static constexpr int kW = 16;               // hats per item
-    static constexpr int kRows = (kW + 1) * P;  // frames (128-byte lines) per ray step
-    static constexpr uint32_t kBytes = (uint32_t)kRows * 128;
+template <int PW, int P>
+struct CellBoxPass {
+    static constexpr int kL = PW / 16;            // lanes per hat
+    static constexpr int kW = 32 / kL;            // hats per item
+    static constexpr int kG = PW / 32;            // 128-byte lines per frame
+    static constexpr int kFrames = (kW + 1) * P;  // frames per ray step
+    static constexpr uint32_t kBytes = (uint32_t)kFrames * kG * 128;
     static constexpr uint32_t kStride = (kBytes + 1023) & ~1023u;
 };
 
-template <int P>
+template <int PW, int P>
 __global__ void __launch_bounds__(kCellWarps * 32, 2)
-adj_cell_tma32_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) {
+adj_cell_tma_pass_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a) {
+    static_assert(PW == 32 || PW == 64, "32- or 64-column passes");
     wait_prior_grid();
-    constexpr int W = CellBox32<P>::kW;
-    constexpr uint32_t BOX_BYTES = CellBox32<P>::kBytes;
-    constexpr uint32_t BUF_STRIDE = CellBox32<P>::kStride;
-    extern __shared__ unsigned char smem_cell32_raw[];
-    const uint32_t raw_u32 = smem_u32(smem_cell32_raw);
+    using Box = CellBoxPass<PW, P>;
+    constexpr int L = Box::kL, W = Box::kW, G = Box::kG;
+    constexpr uint32_t BOX_BYTES = Box::kBytes;
+    constexpr uint32_t BUF_STRIDE = Box::kStride;
+    extern __shared__ unsigned char smem_cellp_raw[];
+    const uint32_t raw_u32 = smem_u32(smem_cellp_raw);
     const uint32_t base_u32 = (raw_u32 + 1023) & ~1023u;  // swizzle atom alignment
-    unsigned char* base = smem_cell32_raw + (base_u32 - raw_u32);
+    unsigned char* base = smem_cellp_raw + (base_u32 - raw_u32);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int h = lane >> 1, c = lane & 1;  // the lane's hat in the item and its 16-column half
-    const int qx = h & 3;                    // register quad q holds column quad q ^ qx of the half
+    const int h = lane / L, c = lane % L;  // the lane's hat in the item and its 16 columns
+    const int qx = h & 3;                   // register quad q holds column quad q ^ qx of them
     const unsigned char* bufp0 = base + (size_t)(2 * warp) * BUF_STRIDE;
     const uint32_t buf0 = base_u32 + (2 * warp) * BUF_STRIDE;
     const uint32_t bar0 = base_u32 + kCellWarps * 2 * BUF_STRIDE + 16 * warp;
@@ -550,11 +554,19 @@ adj_cell_tma32_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
                      "r"(BOX_BYTES)
                      : "memory");
-        asm volatile(
-            "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-            " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-            "l"(tmap), "r"(0), "r"(cp.R), "r"(s.row_out), "r"(bar)
-            : "memory");
+        if constexpr (G == 1) {
+            asm volatile(
+                "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+                "l"(tmap), "r"(0), "r"(cp.R), "r"(s.row_out), "r"(bar)
+                : "memory");
+        } else {
+            asm volatile(
+                "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+                "l"(tmap), "r"(0), "r"(0), "r"(cp.R), "r"(s.row_out), "r"(bar)
+                : "memory");
+        }
     };
     // records of the current column: hat kbase + h, columns 16 c .. of the pass
     auto emit = [&](const float (&lo)[1][16], const float (&up)[1][16], int rec, int kbase) {
@@ -603,16 +615,16 @@ adj_cell_tma32_kernel(const __grid_constant__ CUtensorMap ymap, const CellArgs a
             for (int j = 0; j < 2 * P; ++j)
                 wt[j] = 1.0f - (float)abs(c0.r0 - j * D32) * (1.0f / (float)kFracOne);
             const unsigned char* buf = bufp0 + b * BUF_STRIDE;
-            const int fb0 = P * (W - 1 - h);  // box line of the lane's first tap
+            const int fb0 = P * (W - 1 - h);  // box frame of the lane's first tap
             float z[1][16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) z[0][k] = 0.0f;
 #pragma unroll
             for (int j = 0; j < 2 * P; ++j) {
-                const uint32_t line = (uint32_t)(fb0 + j);
+                const uint32_t line = (uint32_t)(G * (fb0 + j) + (c >> 1));
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const uint32_t chunk = (uint32_t)(4 * c + (q ^ qx)) ^ (line & 7u);
+                    const uint32_t chunk = (uint32_t)(4 * (c & 1) + (q ^ qx)) ^ (line & 7u);
                     const float4 v = *reinterpret_cast<const float4*>(buf + line * 128u + chunk * 16u);
                     fmac2x2(wt[j], v, z[0][4 * q + 0], z[0][4 * q + 1], z[0][4 * q + 2], z[0][4 * q + 3]);
                 }
@@ -1129,10 +1141,15 @@ adj_gather4_kernel(const int32_t* gslot, const float* part, float* x, int64_t n_
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static int pass_cols(int elem) { return elem == 8 ? kPassCols64 : kPassCols32; }
+// batch columns per pass: 16 in FP64, 32 in FP32 (64 at batches of whole
+// 64-column passes, which the TMA pass kernel reads as two lines per frame)
+static int pass_cols(int elem, int batch) {
+    if (elem == 8) return kPassCols64;
+    return batch % 64 == 0 ? 2 * kPassCols32 : kPassCols32;
+}
 
 size_t adjoint_scratch_bytes(const rtt_op_s* op, int batch, int elem) {
-    const int bp = batch < pass_cols(elem) ? batch : pass_cols(elem);
+    const int bp = batch < pass_cols(elem, batch) ? batch : pass_cols(elem, batch);
     return (size_t)op->n_rec * op->time.n_hats * (size_t)bp * (size_t)elem;
 }
 
@@ -1418,50 +1435,68 @@ static cudaError_t dispatch_tma(const rtt_op_s* op, const CellArgs& a, const flo
     return cudaErrorNotSupported;
 }
 
-// one 32-column pass through adj_cell_tma32_kernel; cudaErrorNotSupported
-// unless the pass has 32 columns of a batch of whole passes and the periodic
-// cadence P in {2, 4, 8}
-template <int P>
-static cudaError_t launch_cell_tma32(CellArgs a, const float* y, const int32_t* op_fb,
-                                     const int32_t* op_r0, cudaStream_t st) {
-    constexpr int ROWS = CellBox32<P>::kRows;
-    static_assert(ROWS <= 256, "TMA box rows");
+// one 32- or 64-column pass through adj_cell_tma_pass_kernel;
+// cudaErrorNotSupported unless the pass has PW columns of a batch of whole
+// passes and the periodic cadence P in {2, 4, 8}
+template <int PW, int P>
+static cudaError_t launch_cell_tma_pass(CellArgs a, const float* y, const int32_t* op_fb,
+                                        const int32_t* op_r0, cudaStream_t st) {
+    using Box = CellBoxPass<PW, P>;
+    static_assert(Box::kFrames <= 256, "TMA box rows");
     const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     const float* yp = y + a.b0;
-    if (!enc || a.seg.total <= 0 || a.Bp != 32 || a.B % 32 != 0 || ((uintptr_t)yp % 16) != 0)
+    if (!enc || a.seg.total <= 0 || a.Bp != PW || a.B % PW != 0 || ((uintptr_t)yp % 16) != 0)
         return cudaErrorNotSupported;
     CUtensorMap m;
-    // (the pass's 32 floats = one 128-byte line, frames of a data row, data rows)
-    cuuint64_t dims[3] = {32, (cuuint64_t)a.Tn, (cuuint64_t)a.seg.total};
-    cuuint64_t strides[2] = {(cuuint64_t)a.B * 4, (cuuint64_t)a.Tn * a.B * 4};
-    cuuint32_t box[3] = {32, (cuuint32_t)ROWS, 1};
-    cuuint32_t es[3] = {1, 1, 1};
-    if (enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(yp), dims, strides, box, es,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return cudaErrorNotSupported;
-    constexpr int W = CellBox32<P>::kW;
-    a.n_hg = (a.K + W - 1) / W;
+    CUresult r;
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    if constexpr (Box::kG == 1) {
+        // (the pass's 32 floats = one 128-byte line, frames of a data row, data rows)
+        cuuint64_t dims[3] = {32, (cuuint64_t)a.Tn, (cuuint64_t)a.seg.total};
+        cuuint64_t strides[2] = {(cuuint64_t)a.B * 4, (cuuint64_t)a.Tn * a.B * 4};
+        cuuint32_t box[3] = {32, (cuuint32_t)Box::kFrames, 1};
+        r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(yp), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        // (32 floats = one 128-byte line, the pass's two lines of a frame, frames, data rows)
+        cuuint64_t dims[4] = {32, 2, (cuuint64_t)a.Tn, (cuuint64_t)a.seg.total};
+        cuuint64_t strides[3] = {128, (cuuint64_t)a.B * 4, (cuuint64_t)a.Tn * a.B * 4};
+        cuuint32_t box[4] = {32, 2, (cuuint32_t)Box::kFrames, 1};
+        r = enc(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(yp), dims, strides, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (r != CUDA_SUCCESS) return cudaErrorNotSupported;
+    a.n_hg = (a.K + Box::kW - 1) / Box::kW;
     a.n_bc = 1;
-    a.hw = W;
+    a.hw = Box::kW;
     a.c_h0 = op_fb;  // the periodic tap tables (cell_tables)
     a.c_h1 = op_r0;
     a.n_items = (int64_t)a.n_hg * a.n_items;  // n_items holds the segment count on entry
-    const size_t smem = 1024 + (size_t)kCellWarps * 2 * CellBox32<P>::kStride + kCellWarps * 16;
-    cudaError_t e = cudaFuncSetAttribute(adj_cell_tma32_kernel<P>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = 1024 + (size_t)kCellWarps * 2 * Box::kStride + kCellWarps * 16;
+    auto kern = adj_cell_tma_pass_kernel<PW, P>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int grid = resident_grid(adj_cell_tma32_kernel<P>, kCellWarps * 32, smem, a.n_items, kCellWarps);
-    return launch_dependent(adj_cell_tma32_kernel<P>, dim3(grid), dim3(kCellWarps * 32), smem, st, m, a);
+    const int grid = resident_grid(kern, kCellWarps * 32, smem, a.n_items, kCellWarps);
+    return launch_dependent(kern, dim3(grid), dim3(kCellWarps * 32), smem, st, m, a);
 }
 
-static cudaError_t dispatch_tma32(const rtt_op_s* op, const CellArgs& a, const float* y, int P,
-                                  cudaStream_t st) {
+static cudaError_t dispatch_tma_pass(const rtt_op_s* op, const CellArgs& a, const float* y, int P,
+                                     cudaStream_t st) {
     const int32_t *fb = op->c_fb, *r0 = op->c_r0;
+    if (a.Bp == 64) {
+        switch (P) {
+            case 2: return launch_cell_tma_pass<64, 2>(a, y, fb, r0, st);
+            case 4: return launch_cell_tma_pass<64, 4>(a, y, fb, r0, st);
+            case 8: return launch_cell_tma_pass<64, 8>(a, y, fb, r0, st);
+            default: return cudaErrorNotSupported;
+        }
+    }
     switch (P) {
-        case 2: return launch_cell_tma32<2>(a, y, fb, r0, st);
-        case 4: return launch_cell_tma32<4>(a, y, fb, r0, st);
-        case 8: return launch_cell_tma32<8>(a, y, fb, r0, st);
+        case 2: return launch_cell_tma_pass<32, 2>(a, y, fb, r0, st);
+        case 4: return launch_cell_tma_pass<32, 4>(a, y, fb, r0, st);
+        case 8: return launch_cell_tma_pass<32, 8>(a, y, fb, r0, st);
         default: return cudaErrorNotSupported;
     }
 }
@@ -1638,7 +1673,7 @@ int adjoint_best_kind(const rtt_op_s* op, int batch) {
     const int P = frames_per_hat(op->frame_D);
     int hg = 0;
     if (tma_shape(op, batch, P, &hg)) return hg == 2 ? 4 : 3;
-    if (P > 0 && batch % 32 == 0) return 4;  // 32-column passes by the TMA kernel
+    if (P > 0 && batch % 32 == 0) return 4;  // 32- or 64-column passes by the TMA kernel
     if (P > 0 && batch <= 2) return 4;       // the direct-load kernel (kinds 3 and 4: 32- or 64-hat items)
     return P > 0 ? 2 : 1;
 }
@@ -1653,7 +1688,7 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
         set_error("adjoint scratch not prepared for batch %d", B);
         return cudaErrorInvalidValue;
     }
-    int PC = pass_cols((int)sizeof(T));
+    int PC = pass_cols((int)sizeof(T), B);
     int kind = frames_per_hat(op->frame_D) > 0 ? 2 : 1;  // FP64: periodic when the cadence allows
     if constexpr (sizeof(T) == 4) {
         const ApplyVariant v = variant_for(op, B);
@@ -1675,8 +1710,8 @@ cudaError_t launch_adjoint(const rtt_op_s* op, const T* y, T* x, int B, const Ar
             else if (kind >= 3 && Bp == B && B <= 16)
                 e = dispatch_tma(op, a, (const float*)y, B, frames_per_hat(op->frame_D), kind == 4 ? 2 : 1,
                                  st);
-            else if (kind >= 3 && Bp == 32 && B % 32 == 0)
-                e = dispatch_tma32(op, a, (const float*)y, frames_per_hat(op->frame_D), st);
+            else if (kind >= 3 && (Bp == 32 || Bp == 64) && B % Bp == 0)
+                e = dispatch_tma_pass(op, a, (const float*)y, frames_per_hat(op->frame_D), st);
         }
         if (e == cudaErrorNotSupported && kind >= 2) {
             cudaGetLastError();  // clear the "not supported" marker, if any

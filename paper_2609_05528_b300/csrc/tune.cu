@@ -287,8 +287,9 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
             best.adj = v.adj;
         }
     }
-    // adjoint passes of 8 or 16 columns (large batches)
-    for (int pc = 8; pc <= 16 && B > pc; pc *= 2) {
+    // adjoint passes of 8, 16 or 32 columns (large batches; 32 where the
+    // default is 64-column passes)
+    for (int pc = 8; pc <= 32 && B > pc; pc *= 2) {
         ApplyVariant v = best;
         v.adj_cols = (int8_t)pc;
         const float ms = time_it(v, true);

@@ -64,7 +64,7 @@ def test_algorithmic_bytes_of_the_benchmark_workload():
 def test_job_value_and_launch_count():
     assert bench.job_value(1, 8, 0.25) == pytest.approx(32000.0)
     assert bench.job_value(4, 8, 0.25) == pytest.approx(128000.0)  # weak scaling
-    assert [bench.launches_per_step(b) for b in (1, 8, 32, 33, 64)] == [3, 3, 3, 5, 5]
+    assert [bench.launches_per_step(b) for b in (1, 8, 32, 33, 64, 96)] == [3, 3, 3, 5, 3, 7]
 
 
 @pytest.mark.parametrize("workload", ["stress1024", "kerr256"])
