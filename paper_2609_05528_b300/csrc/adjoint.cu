@@ -37,9 +37,12 @@
 namespace rtt {
 
 // segment of a strip: at most this many columns and (unless one column alone
-// has more) this many rays
-constexpr int kSegMaxCols = 16;
-constexpr int kSegMaxRays = 16;
+// has more) this many rays.  Longer segments write fewer partial records
+// (2 (n + 1) node rows per n columns); 64 and 64 measured best (stress1024
+// batch 8: 2.76 -> 2.67 ms, kerr256 0.134 -> 0.120 ms; at 128 the smaller
+// workload runs out of items to balance)
+constexpr int kSegMaxCols = 64;
+constexpr int kSegMaxRays = 64;
 // batch columns per pass (records hold one pass)
 constexpr int kPassCols32 = 32;
 constexpr int kPassCols64 = 16;
