@@ -155,10 +155,11 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel: str, workload: str = "kerr256"):
+def recorded_traffic(kernel: str, workload: str = "kerr256", variant=None):
     """DRAM bytes per launch of `kernel` (the apply A or AT) from the committed
-    ncu record of `workload` at batch 8, or None when the record is missing or
-    was taken on other kernel sources."""
+    ncu record of `workload` at batch 8, or None when the record is missing,
+    was taken on other kernel sources, or (variant given) on another kernel
+    variant of the apply."""
     p = os.path.join(ROOT, "profiles", f"traffic_{workload}_b8.json")
     try:
         with open(p) as fh:
@@ -167,6 +168,11 @@ def recorded_traffic(kernel: str, workload: str = "kerr256"):
         return None
     if rec.get("source_hash") != kernel_source_hash():
         return None
+    if variant is not None and "variant" in rec:
+        keys = ("fwd_kernel", "fwd_bc", "fwd_half", "fwd_order", "fwd_cols") if kernel == "A" else \
+               ("adj_kernel", "adj_cols")
+        if any(int(rec["variant"].get(k, -1)) != int(variant.get(k, -2)) for k in keys):
+            return None
     return rec.get("traffic_bytes", {}).get(kernel)
 
 
@@ -204,15 +210,16 @@ def time_loop(stream, fn, n, flush=None):
 
 
 def roofline_of(op, B, mA, mAT, traffic_key=None):
-    """traffic_key: the workload name of the committed ncu traffic record."""
+    """traffic_key: the workload name of the committed ncu traffic record
+    (used when it was taken on the variants op runs at batch B)."""
     ab = algorithmic_bytes(op, B)
     dom, dom_ms = ("A", mA) if mA >= mAT else ("AT", mAT)
     peak, peak_kind = measured_peaks()
     achieved = ab[dom] / (dom_ms * 1e-3) / 1e9
     return ab, {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": recorded_traffic(dom, traffic_key) if traffic_key else None,
-                "traffic_other": recorded_traffic("AT" if dom == "A" else "A", traffic_key)
+                "traffic": recorded_traffic(dom, traffic_key, op.get_variant(B)) if traffic_key else None,
+                "traffic_other": recorded_traffic("AT" if dom == "A" else "A", traffic_key, op.get_variant(B))
                 if traffic_key else None,
                 "algorithmic_bytes": ab[dom], "source_hash": kernel_source_hash(),
                 "A_frac": ab["A"] / (mA * 1e-3) / 1e9 / peak,
@@ -552,7 +559,13 @@ def run_profile_case(args, device):
     from paper_2609_05528_b300 import inputs as I
     w = I.stress1024(0.94) if args.profile == "stress1024" else I.kerr256()
     B = args.batch
-    _, op, x = build_workload(device, w, B, seed0=100)
+    # --variant pins the kernel variant (the one an autotuned run without the
+    # profiler printed): a tuner timing its candidates under a profiler could
+    # choose differently
+    _, op, x = build_workload(device, w, B, seed0=100, tune=not args.variant)
+    if args.variant:
+        fk, bc, half, ak, order, fcols, acols = (int(v) for v in args.variant.split(","))
+        op.set_variant(B, fk, bc, half, ak, fwd_order=order, fwd_cols=fcols, adj_cols=acols)
     y = torch.empty((op.arm_rows(7), op.n_frames, B), dtype=torch.float32, device=device)
     g = torch.empty_like(x)
     for _ in range(max(args.warmup, 3)):
@@ -1132,6 +1145,9 @@ def main():
                     help="time rtt_gemm_tn_f64 (C = A^T B, A: K x M, B: K x N, N(0,1) FP64) against "
                          "cuBLAS DGEMM, print one JSON line and exit")
     ap.add_argument("--batch", type=int, default=8, help="history batch of the --profile step")
+    ap.add_argument("--variant", default="",
+                    help="--profile: fwd_kernel,fwd_bc,fwd_half,adj_kernel,fwd_order,fwd_cols,adj_cols "
+                         "instead of autotuning")
     ap.add_argument("--profile", choices=["stress1024", "kerr256"],
                     help="for ncu: build the workload at batch 8, autotune, warm up, run --steps "
                          "A + A^T steps inside the NVTX range bench_timed, and exit")

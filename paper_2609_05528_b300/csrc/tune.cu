@@ -21,6 +21,11 @@ namespace {
 
 constexpr int kTuneReps = 3;
 
+// a candidate replaces the best so far only when it is at least 1% faster:
+// near-ties (run-to-run noise) keep the earlier, simpler choice, so the
+// tuner picks the same variant from run to run
+inline bool better(float ms, float best) { return ms < 0.99f * best; }
+
 // installs v as the operator's variant for batch B (replacing an entry)
 void set_variant(rtt_op_s* op, int B, const ApplyVariant& v) {
     for (int i = 0; i < op->n_tuned; ++i)
@@ -204,7 +209,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                     if (su != 2 && (kind != 1 || half || (bc != 4 && bc != 8))) continue;
                     v.fwd_su = (int8_t)su;
                     const float ms = time_it(v, false);
-                    if (ms < fwd_best) {
+                    if (better(ms, fwd_best)) {
                         fwd_best = ms;
                         best.fwd = v.fwd;
                         best.fwd_bc = v.fwd_bc;
@@ -227,7 +232,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                     v.fwd_half = (int8_t)half;
                     v.fwd_su = 2;
                     const float ms = time_it(v, false);
-                    if (ms < fwd_best) {
+                    if (better(ms, fwd_best)) {
                         fwd_best = ms;
                         best.fwd = v.fwd;
                         best.fwd_bc = v.fwd_bc;
@@ -246,7 +251,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
                 v.fwd_half = (int8_t)half;
                 v.fwd_su = 2;
                 const float ms = time_it(v, false);
-                if (ms < fwd_best) {
+                if (better(ms, fwd_best)) {
                     fwd_best = ms;
                     best.fwd = v.fwd;
                     best.fwd_bc = v.fwd_bc;
@@ -259,7 +264,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
         ApplyVariant v = best;
         v.fwd_order = 1;
         const float ms = time_it(v, false);
-        if (ms < fwd_best) {
+        if (better(ms, fwd_best)) {
             fwd_best = ms;
             best.fwd_order = 1;
         }
@@ -269,7 +274,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
         ApplyVariant v = best;
         v.fwd_cols = 8;
         const float ms = time_it(v, false);
-        if (ms < fwd_best) {
+        if (better(ms, fwd_best)) {
             fwd_best = ms;
             best.fwd_cols = 8;
         }
@@ -282,7 +287,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
         ApplyVariant v = best;
         v.adj = (int8_t)k;
         const float ms = time_it(v, true);
-        if (ms < adj_best) {
+        if (better(ms, adj_best)) {
             adj_best = ms;
             best.adj = v.adj;
         }
@@ -293,7 +298,7 @@ extern "C" rtt_status rtt_autotune(rtt_op op, int batch, int arm_mask, void* str
         ApplyVariant v = best;
         v.adj_cols = (int8_t)pc;
         const float ms = time_it(v, true);
-        if (ms < adj_best) {
+        if (better(ms, adj_best)) {
             adj_best = ms;
             best.adj_cols = (int8_t)pc;
         }

@@ -73,6 +73,15 @@ def test_traffic_record_only_for_its_sources(monkeypatch, workload):
     if rec is None:
         pytest.skip(f"no {workload} traffic record for the current apply sources")
     assert rec > 0
+    # only for the kernel variant it was taken on
+    import json
+    with open(os.path.join(ROOT, "profiles", f"traffic_{workload}_b8.json")) as fh:
+        v = dict(json.load(fh).get("variant", {}))
+    if v:
+        assert bench.recorded_traffic("AT", workload, v) == rec
+        other = dict(v, adj_kernel=v["adj_kernel"] % 4 + 1)
+        assert bench.recorded_traffic("AT", workload, other) is None
+        assert bench.recorded_traffic("A", workload, other) is not None  # the forward's own keys
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0000000000000000")
     assert bench.recorded_traffic("AT", workload) is None
     assert bench.recorded_traffic("A", workload) is None
