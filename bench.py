@@ -275,6 +275,7 @@ def run_ours(args, rank, world, device):
     try:
         y_ref = y[::101].clone()  # y of the last FP32-weight forward above
         op.set_weight_precision(rtt.WEIGHTS_BF16)
+        tune16 = op.autotune(BATCH)  # the variants for these tables (bit-neutral)
         op.apply_A(x, y)
         op.apply_AT(y, g)
         mA16 = float(np.median(time_loop(stream, lambda: op.apply_A(x, y), args.steps)))
@@ -282,10 +283,12 @@ def run_ours(args, rank, world, device):
         op.apply_A(x, y)
         rel = float(torch.linalg.vector_norm(y[::101] - y_ref) / torch.linalg.vector_norm(y_ref))
         op.set_weight_precision(rtt.WEIGHTS_FP32)
+        op.tune = op.autotune(BATCH)  # back to the FP32 tables' variants
         ab16 = algorithmic_bytes(op, BATCH, weight_bytes=8)
         peak16, _ = measured_peaks()
         bf16 = {"ms_per_step": mA16 + mAT16, "value": job_value(world, BATCH, mA16 + mAT16),
                 "A_ms": mA16, "AT_ms": mAT16,
+                "variant": [tune16["fwd_kernel"], tune16["fwd_bc"], tune16["adj_kernel"]],
                 "A_frac": ab16["A"] / (mA16 * 1e-3) / 1e9 / peak16,
                 "AT_frac": ab16["AT"] / (mAT16 * 1e-3) / 1e9 / peak16,
                 "y_rel_l2_vs_fp32_weights": rel, "rows_compared": int(y_ref.shape[0])}
@@ -425,8 +428,9 @@ def run_ours(args, rank, world, device):
                    "AT_frac": abb["AT"] / (tT * 1e-3) / 1e9 / peak,
                    "history_applies_per_s": B / ((tA + tT) * 1e-3),
                    "variant": {k: tune[k] for k in ("fwd_kernel", "fwd_bc", "fwd_order", "adj_kernel")}}
-            # the BF16-weight table variant beside the FP32 one
+            # the BF16-weight table variant beside the FP32 one, tuned for its tables
             op.set_weight_precision(rtt.WEIGHTS_BF16)
+            tune16 = op.autotune(B)
             op.apply_A(xb, yb)
             op.apply_AT(yb, gb)
             tA16 = float(np.median(time_loop(stream, lambda: op.apply_A(xb, yb), reps)))
@@ -434,6 +438,7 @@ def run_ours(args, rank, world, device):
             op.set_weight_precision(rtt.WEIGHTS_FP32)
             ab16 = algorithmic_bytes(op, B, weight_bytes=8)
             row["bf16_weights"] = {"A_ms": tA16, "AT_ms": tT16,
+                                   "variant": [tune16["fwd_kernel"], tune16["fwd_bc"], tune16["adj_kernel"]],
                                    "A_frac": ab16["A"] / (tA16 * 1e-3) / 1e9 / peak,
                                    "AT_frac": ab16["AT"] / (tT16 * 1e-3) / 1e9 / peak,
                                    "history_applies_per_s": B / ((tA16 + tT16) * 1e-3)}
