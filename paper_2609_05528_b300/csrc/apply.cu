@@ -69,6 +69,7 @@ struct ApplyArgs {
     const double* W64;
     const int32_t* K0;
     const int32_t* F0;
+    const float4* ray_rec;   // per ray (K0, F0, node00, node01 as int bits), W; or null
     const double* F64;
     const T* in;
     T* out;
@@ -739,11 +740,20 @@ struct Fwd7Ray {
 
 __device__ __forceinline__ Fwd7Ray fwd7_load_ray(const ApplyArgs<float>& a, int e) {
     Fwd7Ray r;
-    r.K0 = a.K0[e];
-    r.F0 = a.F0[e];
-    r.w = corner_weights(a.W, a.W16, e);
-    r.n00 = a.node00[e];
-    r.n01 = a.node01[e];
+    if (a.ray_rec) {  // one 32-byte record: two loads from one sector
+        const float4 f = a.ray_rec[2 * (int64_t)e];
+        r.K0 = __float_as_int(f.x);
+        r.F0 = __float_as_int(f.y);
+        r.n00 = __float_as_int(f.z);
+        r.n01 = __float_as_int(f.w);
+        r.w = a.ray_rec[2 * (int64_t)e + 1];
+    } else {
+        r.K0 = a.K0[e];
+        r.F0 = a.F0[e];
+        r.n00 = a.node00[e];
+        r.n01 = a.node01[e];
+        r.w = corner_weights(a.W, a.W16, e);
+    }
     return r;
 }
 
@@ -1908,6 +1918,7 @@ static ApplyArgs<T> base_args(const rtt_op_s* op, const T* in, T* out, int B, co
     a.W16 = op->W16;
     a.W64 = op->W64;
     a.K0 = op->K0;
+    a.ray_rec = op->ray_rec;
     a.F0 = op->F0;
     a.F64 = op->F64;
     a.in = in;

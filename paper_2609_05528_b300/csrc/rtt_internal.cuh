@@ -100,6 +100,8 @@ struct rtt_op_s {
     int weight_precision = 0;     // RTT_WEIGHTS_FP32 or RTT_WEIGHTS_BF16
     int32_t* K0 = nullptr;        // [E] floor(u0)
     int32_t* F0 = nullptr;        // [E] floor(frac(u0) * 2^24)
+    float4* ray_rec = nullptr;    // [2E] a ray's forward fields in one 32-byte record:
+                                  // (K0, F0, node00, node01) as int bits, then W
     double* F64 = nullptr;        // [E] frac(u0) exactly
     double* r = nullptr;          // [E] FP64 copies for probes and quantiles
     double* phi = nullptr;        // [E] source azimuth (localized probes)
